@@ -1,0 +1,18 @@
+"""Plain FP64 CPU oracle for the nonlinear FAS multigrid method of Lee, Hamon, Castelletto, Vassilevski, White,
+"Nonlinear multigrid based on local spectral coarsening for heterogeneous diffusion problems".
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product library imports, links or runs this package; only the tests,
+the package entry point's smoke check and the CPU-baseline leg of the benchmark use it. It shares no code with the
+CUDA path: it is written directly from the paper's equations with numpy/scipy, slowly and obviously.
+
+Modules:
+  tpfa       - fine-level TPFA flux, mixed and reduced residuals, Jacobian (Sec. 2.1, eqs. TPFA_flux, FV_matrix)
+  newton     - brute-force damped Newton with a sparse direct solve: the definitional solution p*
+  aggregation- deterministic greedy graph aggregation (stands in for METIS, Sec. 3.1 / App. A.1)
+  hierarchy  - spectral pressure bases, coarse flux space, Q, D, static local M, Pi~ weights (App. A, B)
+  coarse     - level operators A^l(x) (eq. structure, Prop. 1) and the Picard step (eq. picardian_system)
+  fas        - Algorithm 1 (backtracking), the fine nonlinear Jacobi smoother, Algorithm 2 (FAS V-cycle)
+  baselines  - single-level Picard and Newton (Sec. 2.2)
+
+Every function whose result is not pinned by a test to something other than itself says "parity unpinned".
+"""

@@ -1,0 +1,194 @@
+"""Backtracking (Algorithm 1), smoothers and the FAS V-cycle (Algorithm 2) in FP64 (oracle; test only).
+
+Level 0 is evaluated in the equivalent reduced cell-centred form (Remark after eq. FV_matrix): its state is p, the
+flux is the TPFA flux sigma(p) (eq. TPFA_flux), so the flux rows of the mixed fine residual vanish and the mixed
+residual is [0; -R(p)]. Coarse levels are mixed, with the operators of oracle.coarse.
+
+Algorithm 2, per level l (l = 0 finest):
+  coarsest: up to `coarsest_steps` Picard smoothing steps, stopping at the tolerances of the outer solve measured
+            against that level's initial residual;
+  otherwise: pre-smooth; x^{l+1} = Q x^l; b^{l+1} = A^{l+1}(x^{l+1}) - R (A^l(x^l) - b^l) with R = P^T
+            (eq. coarse_level_residual); recurse; x^l = Backtracking(x^l, P (y^{l+1} - x^{l+1})); post-smooth.
+Smoothing on level 0 is, by default, one Picard step (Sec. 3.3.1): the frozen-coefficient system
+A(kappa(p_k)) dp = -R(p_k), which is the mixed Picard system of eq. picardian_system with the diagonal M eliminated.
+The alternative smoother ("jacobi") is nu damped nonlinear (point-Newton) Jacobi sweeps
+p_K <- p_K - omega R_K / J~_KK with J~_KK = max(dR_K/dp_K, d_K / 2), d_K the frozen-coefficient diagonal.
+Either update then passes through the pressure-change clamp (Sec. 4.1: max |dp| <= dp_clamp) and Algorithm 1. Smoothing on coarse levels is one Picard
+step (Sec. 3.3.1) followed by the clamp (applied to the aggregate means Pi~ dp) and Algorithm 1.
+Residual comparisons in Algorithm 1 use the Euclidean norm of the level residual, with a strict ">".
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse.linalg as spla
+
+from . import coarse, newton, tpfa
+
+
+def backtracking(res_norm, x, dx, r_x, nmax, theta):
+    """Algorithm 1. res_norm(x) -> ||r(x)||; r_x = ||r(x)||. Returns (x + s dx, ||r(x + s dx)||, s, n)."""
+    s = 1.0
+    n = 0
+    r_s = res_norm(x + s * dx)
+    while r_s > r_x and n < nmax:
+        r_half = res_norm(x + 0.5 * s * dx)
+        if r_half > theta * r_s:
+            break
+        s *= 0.5
+        n += 1
+        r_s = r_half
+    return x + s * dx, r_s, s, n
+
+
+@dataclass
+class Stats:
+    cycles: int = 0
+    history: list = field(default_factory=list)
+    early_exit: bool = False
+    fine_evals: int = 0
+
+
+class FAS:
+    """FAS solver over an oracle hierarchy for one problem (mesh, kappa, data, options)."""
+
+    def __init__(self, H, mesh, kind, a, f_cell, g_face, opts):
+        self.H, self.mesh, self.kind, self.a = H, mesh, kind, a
+        self.f, self.g, self.o = f_cell, g_face, opts
+        self.dofs = tpfa.flux_dofs(mesh)
+        self.stats = Stats()
+
+    # ---- level 0 (reduced form) --------------------------------------------------------------------------------
+    def R(self, p):
+        self.stats.fine_evals += 1
+        return tpfa.reduced_residual(self.mesh, self.kind, self.a, p, self.f, self.g)
+
+    def Rnorm(self, p):
+        return float(np.linalg.norm(self.R(p)))
+
+    def jacobi_diag(self, p):
+        J = tpfa.reduced_jacobian(self.mesh, self.kind, self.a, p, self.g).diagonal()
+        d = tpfa.picard_diagonal(self.mesh, self.kind, self.a, p)
+        return np.maximum(J, 0.5 * d)
+
+    def picard_matrix0(self, p):
+        """The frozen-coefficient TPFA matrix A(kappa(p)) with A(kappa(p)) p - rhs(kappa(p)) = R(p)."""
+        return newton.picard_matrix(self.mesh, self.kind, self.a, p)
+
+    def smooth0(self, p, nu, r_p=None):
+        """One smoothing step on level 0: a Picard step (Sec. 3.3.1, default) or nu nonlinear Jacobi sweeps."""
+        o = self.o
+        if o.get("smoother", "picard") == "picard":
+            Rp = self.R(p)
+            dp = -spla.spsolve(self.picard_matrix0(p).tocsc(), Rp)
+            r_p = float(np.linalg.norm(Rp)) if r_p is None else r_p
+        else:
+            q = p.copy()
+            for _ in range(nu):
+                q = q - o["omega"] * self.R(q) / self.jacobi_diag(q)
+            dp = q - p
+        mx = np.max(np.abs(dp)) if dp.size else 0.0
+        if o["dp_clamp"] > 0 and mx > o["dp_clamp"]:
+            dp = dp * (o["dp_clamp"] / mx)
+        r_p = self.Rnorm(p) if r_p is None else r_p
+        pn, rn, _, _ = backtracking(self.Rnorm, p, dp, r_p, o["bt_nmax"], o["bt_theta"])
+        return pn, rn
+
+    def sigma0(self, p):
+        return tpfa.face_fluxes(self.mesh, self.kind, self.a, p, self.g)[self.dofs]
+
+    # ---- coarse levels (mixed) ---------------------------------------------------------------------------------
+    def split(self, l, x):
+        nf = self.H.levels[l].n_flux
+        return x[:nf], x[nf:]
+
+    def res(self, l, x, b):
+        lev = self.H.levels[l]
+        s, p = self.split(l, x)
+        return coarse.operator(lev, self.kind, self.a, s, p) - b
+
+    def picard_smooth(self, l, x, b, r_x=None):
+        lev = self.H.levels[l]
+        o = self.o
+        s, p = self.split(l, x)
+        sP, pP = coarse.picard_solve(lev, self.kind, self.a, s, p, b)
+        dx = np.concatenate([sP, pP]) - x
+        if o["dp_clamp"] > 0:
+            mx = np.max(np.abs(coarse.pbar(lev, dx[lev.n_flux:])))
+            if mx > o["dp_clamp"]:
+                dx = dx * (o["dp_clamp"] / mx)
+        nrm = lambda y: float(np.linalg.norm(self.res(l, y, b)))
+        r_x = nrm(x) if r_x is None else r_x
+        xn, rn, _, _ = backtracking(nrm, x, dx, r_x, o["bt_nmax"], o["bt_theta"])
+        return xn, rn
+
+    def coarsest(self, l, x, b):
+        o = self.o
+        r = float(np.linalg.norm(self.res(l, x, b)))
+        r0 = r
+        for _ in range(o["coarsest_steps"]):
+            if r <= o["tol_rel"] * r0 or r <= o["tol_abs"]:
+                break
+            x, r = self.picard_smooth(l, x, b, r)
+        return x
+
+    def cycle_coarse(self, l, x, b):
+        """Algorithm 2 on a mixed level l >= 1."""
+        if l == len(self.H.levels) - 1:
+            return self.coarsest(l, x, b)
+        lev, tr, levc = self.H.levels[l], self.H.transfers[l], self.H.levels[l + 1]
+        x, _ = self.picard_smooth(l, x, b)
+        s, p = self.split(l, x)
+        r = self.res(l, x, b)
+        rs, rp = r[:lev.n_flux], r[lev.n_flux:]
+        xc = np.concatenate([tr.Qsigma @ s, tr.Qp @ p])
+        bc = coarse.operator(levc, self.kind, self.a, xc[:levc.n_flux], xc[levc.n_flux:]) \
+            - np.concatenate([tr.Psigma.T @ rs, tr.Pp.T @ rp])
+        yc = self.cycle_coarse(l + 1, xc, bc)
+        e = yc - xc
+        dx = np.concatenate([tr.Psigma @ e[:levc.n_flux], tr.Pp @ e[levc.n_flux:]])
+        nrm = lambda y: float(np.linalg.norm(self.res(l, y, b)))
+        x, _, _, _ = backtracking(nrm, x, dx, nrm(x), self.o["bt_nmax"], self.o["bt_theta"])
+        x, _ = self.picard_smooth(l, x, b)
+        return x
+
+    def vcycle(self, p, r0):
+        """One Algorithm 2 cycle from level 0. Returns (p, ||R(p)||, stopped_after_presmoothing)."""
+        o = self.o
+        H = self.H
+        p, rn = self.smooth0(p, o["nu_pre"])
+        if rn <= o["tol_rel"] * r0 or rn <= o["tol_abs"]:
+            return p, rn, True
+        if len(H.levels) == 1:
+            p, rn = self.smooth0(p, o["nu_post"], rn)
+            return p, rn, False
+        tr, levc = H.transfers[0], H.levels[1]
+        Rp = self.R(p)
+        xc = np.concatenate([tr.Qsigma @ self.sigma0(p), tr.Qp @ p])
+        # mixed fine residual is [0; -R(p)]; R r^0 = [0; P_p^T (-R(p))]
+        bc = coarse.operator(levc, self.kind, self.a, xc[:levc.n_flux], xc[levc.n_flux:]) \
+            - np.concatenate([np.zeros(levc.n_flux), tr.Pp.T @ (-Rp)])
+        yc = self.cycle_coarse(1, xc, bc)
+        dp = tr.Pp @ (yc - xc)[levc.n_flux:]
+        p, rn, _, _ = backtracking(self.Rnorm, p, dp, float(np.linalg.norm(Rp)), o["bt_nmax"], o["bt_theta"])
+        p, rn = self.smooth0(p, o["nu_post"], rn)
+        return p, rn, False
+
+    def solve(self, p0=None, max_cycles=None):
+        o = self.o
+        p = np.zeros(self.mesh.n_cells) if p0 is None else np.array(p0, dtype=np.float64)
+        r0 = self.Rnorm(p)
+        rn = r0
+        self.stats.history = [r0]
+        maxc = o["max_cycles"] if max_cycles is None else max_cycles
+        for _ in range(maxc):
+            if rn <= o["tol_rel"] * r0 or rn <= o["tol_abs"]:
+                break
+            p, rn, early = self.vcycle(p, r0)
+            self.stats.cycles += 1
+            self.stats.history.append(rn)
+            if early:
+                self.stats.early_exit = True
+                break
+        return p

@@ -1,0 +1,189 @@
+"""Seeded Cartesian meshes, permeability fields and boundary data (no solver arithmetic here).
+
+The cell graph follows the paper's finite-volume setting (Sec. 2.1): one pressure unknown per cell, one flux per
+interface, interior interfaces stored once with K < L, boundary interfaces carrying either a prescribed pressure
+(Dirichlet) or a prescribed normal flux (Neumann). The geometric half transmissibility of a cell towards an interface
+(eq. half-transmissibility) is |eps| K_0 / dist(x_K, x_eps) for a scalar K_0 on an orthogonal grid, whose collocation
+point is the face centre (Remark on collocation points).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BC_INTERIOR, BC_DIRICHLET, BC_NEUMANN = 0, 1, 2
+KAPPA_EXP, KAPPA_INV1P2 = 0, 1
+
+
+@dataclass
+class Mesh:
+    """A cell graph with geometric data; every array is a plain numpy array in the layout the C ABI takes."""
+    n_cells: int
+    cell_volume: np.ndarray          # [N] float64
+    face_cells: np.ndarray           # [F, 2] int32, K < L, L = -1 on boundary faces
+    half_trans: np.ndarray           # [F, 2] float64, (Ups_K, Ups_L); Ups_L = 0 on boundary faces
+    face_bc: np.ndarray              # [F] uint8: 0 interior, 1 Dirichlet, 2 Neumann
+    face_area: np.ndarray            # [F] float64
+    shape: tuple = ()
+    perm: np.ndarray | None = None   # [N] K_0 per cell (for reference only)
+
+    @property
+    def n_faces(self) -> int:
+        return int(self.face_cells.shape[0])
+
+
+def _lin(shape):
+    return np.arange(int(np.prod(shape)), dtype=np.int64).reshape(shape[::-1]).T  # index = i + nx*(j + ny*k)
+
+
+def cartesian_mesh(shape, K, dirichlet_x=True):
+    """Unit square/cube split into shape cells; K is [N] in lexicographic order (x fastest).
+
+    Boundary faces on x = 0 and x = 1 are Dirichlet, all others Neumann (no-flow unless data says otherwise).
+    """
+    shape = tuple(int(s) for s in shape)
+    d = len(shape)
+    h = np.array([1.0 / s for s in shape])
+    idx = _lin(shape)
+    N = idx.size
+    vol = np.full(N, float(np.prod(h)))
+    K = np.asarray(K, dtype=np.float64).reshape(-1)
+    fc, ht, bc, area = [], [], [], []
+    for ax in range(d):
+        a_face = float(np.prod(np.delete(h, ax)))
+        dist = h[ax] / 2.0
+        lo = np.take(idx, np.arange(shape[ax] - 1), axis=ax).reshape(-1, order="F")
+        hi = np.take(idx, np.arange(1, shape[ax]), axis=ax).reshape(-1, order="F")
+        order = np.argsort(lo, kind="stable")
+        lo, hi = lo[order], hi[order]
+        fc.append(np.stack([lo, hi], 1))
+        ht.append(np.stack([a_face * K[lo] / dist, a_face * K[hi] / dist], 1))
+        bc.append(np.zeros(lo.size, np.uint8))
+        area.append(np.full(lo.size, a_face))
+    for ax in range(d):
+        a_face = float(np.prod(np.delete(h, ax)))
+        dist = h[ax] / 2.0
+        for side in (0, shape[ax] - 1):
+            cells = np.sort(np.take(idx, side, axis=ax).reshape(-1))
+            fc.append(np.stack([cells, np.full(cells.size, -1)], 1))
+            ht.append(np.stack([a_face * K[cells] / dist, np.zeros(cells.size)], 1))
+            kind = BC_DIRICHLET if (ax == 0 and dirichlet_x) else BC_NEUMANN
+            bc.append(np.full(cells.size, kind, np.uint8))
+            area.append(np.full(cells.size, a_face))
+    return Mesh(n_cells=N, cell_volume=vol,
+                face_cells=np.concatenate(fc).astype(np.int32),
+                half_trans=np.concatenate(ht).astype(np.float64),
+                face_bc=np.concatenate(bc), face_area=np.concatenate(area), shape=shape, perm=K)
+
+
+def gaussian_random_field(shape, corr_cells, rng):
+    """Zero-mean, unit-variance field with a Gaussian covariance of correlation length corr_cells (in cells).
+
+    White noise on a grid padded to twice the size is filtered in Fourier space by the square root of the
+    Gaussian spectral density, then cropped and standardised.
+    """
+    pad = tuple(2 * s for s in shape)
+    noise = rng.standard_normal(pad)
+    ks = np.meshgrid(*[np.fft.fftfreq(n) * 2 * np.pi for n in pad], indexing="ij")
+    k2 = sum(k * k for k in ks)
+    filt = np.exp(-0.25 * k2 * corr_cells ** 2)
+    field_ = np.real(np.fft.ifftn(np.fft.fftn(noise) * filt))
+    field_ = field_[tuple(slice(0, s) for s in shape)]
+    field_ = (field_ - field_.mean()) / field_.std()
+    return field_
+
+
+def _to_lex(arr):
+    """[nx, ny(, nz)] array -> lexicographic [N] vector with x fastest."""
+    return np.asarray(arr).reshape(-1, order="F")
+
+
+def lognormal_field(shape, sigma, corr_cells, seed):
+    """K_0 = exp(sigma * g), g a standardised Gaussian random field."""
+    rng = np.random.default_rng(seed)
+    return _to_lex(np.exp(sigma * gaussian_random_field(shape, corr_cells, rng)))
+
+
+def channelized_field(shape, decades, n_channels, seed, corr_cells=4.0):
+    """log10 K_0 = GRF background + sinuous Gaussian channels (+3 decades) in horizontal layers, then rescaled
+    affinely so that log10 K_0 spans [-decades/2, decades/2]."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    logk = gaussian_random_field(shape, corr_cells, rng)
+    x = np.arange(nx)[:, None, None] + 0.5
+    y = np.arange(ny)[None, :, None] + 0.5
+    z = np.arange(nz)[None, None, :] + 0.5
+    for _ in range(n_channels):
+        width = rng.uniform(2.0, 4.0)
+        z0 = rng.uniform(0, nz)
+        y0 = rng.uniform(0, ny)
+        amp = rng.uniform(0.1, 0.3) * ny
+        lam = rng.uniform(0.5, 1.5) * nx
+        phase = rng.uniform(0, 2 * np.pi)
+        yc = y0 + amp * np.sin(2 * np.pi * x / lam + phase)
+        dist2 = (y - yc) ** 2 + (z - z0) ** 2
+        logk = logk + 3.0 * np.exp(-dist2 / (2.0 * (width / 2.0) ** 2))
+    lo, hi = logk.min(), logk.max()
+    logk = (logk - lo) / (hi - lo) * decades - decades / 2.0
+    return _to_lex(10.0 ** logk)
+
+
+@dataclass
+class Problem:
+    """A mesh plus nonlinearity, data and hierarchy options: one solve request."""
+    mesh: Mesh
+    kappa_kind: int
+    kappa_a: float
+    f_cell: np.ndarray               # [N] source density f|_K
+    g_face: np.ndarray               # [F] Dirichlet value or Neumann flux density
+    opts: dict = field(default_factory=dict)
+    name: str = ""
+
+
+def default_options(**kw):
+    """Hierarchy and smoother options; the backtracking constants are the paper's (n_max = 4, theta = 0.9)."""
+    o = dict(n_levels=2, agg_size=[16, 8, 8, 8, 8, 8, 8], modes=[2, 2, 2, 2, 2, 2, 2], nu_pre=2, nu_post=2,
+             omega=0.8, bt_nmax=4, bt_theta=0.9, dp_clamp=0.0, coarsest_steps=10, tol_rel=1e-8, tol_abs=1e-10,
+             max_cycles=50, lin_tol=1e-12, lin_maxit=2000)
+    o.update(kw)
+    return o
+
+
+def _dirichlet_data(mesh, g_left, g_right):
+    g = np.zeros(mesh.n_faces)
+    dir_faces = np.where(mesh.face_bc == BC_DIRICHLET)[0]
+    # x-coordinate of the owning cell decides left/right
+    nx = mesh.shape[0]
+    i = mesh.face_cells[dir_faces, 0] % nx
+    g[dir_faces] = np.where(i == 0, g_left, g_right)
+    return g
+
+
+def problem_config(name, scale=None):
+    """Problems named by the workloads they stand in for.
+
+    cart2d_32: 32x32 quadrilaterals, ln K ~ GRF(0,1) with correlation length 4 cells, kappa = exp(0.5 p),
+      p = 1 left / 0 right, f = 0, aggregates of about 16 cells, 2 modes, 2 levels.
+    chan3d_64: 64^3 hexahedra, channelized K over 6 decades, kappa = exp(2 p), aggregates of about 64 then 8
+      cells, 4 modes, 3 levels. `scale` replaces 64 by a smaller side for tests.
+    """
+    if name == "cart2d_32":
+        n = scale or 32
+        K = lognormal_field((n, n), 1.0, 4.0, seed=1)
+        mesh = cartesian_mesh((n, n), K)
+        g = _dirichlet_data(mesh, 1.0, 0.0)
+        opts = default_options(n_levels=2, agg_size=[16, 8, 8, 8], modes=[2, 2, 2, 2])
+        return Problem(mesh, KAPPA_EXP, 0.5, np.zeros(mesh.n_cells), g, opts, name)
+    if name == "chan3d_64":
+        n = scale or 64
+        K = channelized_field((n, n, n), 6.0, 12, seed=2)
+        mesh = cartesian_mesh((n, n, n), K)
+        g = _dirichlet_data(mesh, 1.0, 0.0)
+        opts = default_options(n_levels=3, agg_size=[64, 8, 8, 8], modes=[4, 4, 4, 4],
+                               dp_clamp=float(np.log(1.5) / 2.0))
+        return Problem(mesh, KAPPA_EXP, 2.0, np.zeros(mesh.n_cells), g, opts, name)
+    raise KeyError(name)
+
+
+CONFIGS = ("cart2d_32", "chan3d_64")

@@ -1,0 +1,146 @@
+"""Pins of the fine-level oracle (TPFA residual, Jacobian, Newton) to facts fixed outside the oracle itself."""
+import numpy as np
+import pytest
+
+from oracle import newton, tpfa
+from synth.grids import cartesian_mesh, lognormal_field, problem_config, KAPPA_EXP, KAPPA_INV1P2
+
+
+def _dirichlet(mesh, left, right):
+    g = np.zeros(mesh.n_faces)
+    d = np.where(mesh.face_bc == 1)[0]
+    i = mesh.face_cells[d, 0] % mesh.shape[0]
+    g[d] = np.where(i == 0, left, right)
+    return g
+
+
+@pytest.mark.parametrize("kind,a", [(KAPPA_EXP, 2.0), (KAPPA_INV1P2, 0.0)])
+def test_constant_state_has_zero_net_flux(kind, a):
+    """Sec. 2.1: with p = c everywhere, g_D = c and f = 0 every flux vanishes, so R = 0 exactly."""
+    mesh = cartesian_mesh((6, 5, 4), lognormal_field((6, 5, 4), 2.0, 2.0, seed=3))
+    c = 0.37
+    g = np.where(mesh.face_bc == 1, c, 0.0)
+    r = tpfa.reduced_residual(mesh, kind, a, np.full(mesh.n_cells, c), np.zeros(mesh.n_cells), g)
+    assert np.all(r == 0.0)
+
+
+def test_reduced_equals_mixed_with_sigma_eliminated():
+    """Remark after eq. FV_matrix: R(p) = -(D sigma + [f]) with sigma = -M^-1 (D^T p + g) from the mixed matrices."""
+    pr = problem_config("cart2d_32", scale=12)
+    m = pr.mesh
+    rng = np.random.default_rng(5)
+    p = rng.uniform(-1, 1, m.n_cells)
+    f = rng.uniform(-1, 1, m.n_cells)
+    g = rng.uniform(-1, 1, m.n_faces)
+    M, D, gv, fv, _ = tpfa.mixed_matrices(m, KAPPA_EXP, 1.3, p, f, g)
+    sigma = -(D.T @ p + gv) / M.diagonal()
+    r_mixed = D @ sigma + fv
+    r = tpfa.reduced_residual(m, KAPPA_EXP, 1.3, p, f, g)
+    assert np.allclose(r, -r_mixed, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind,a", [(KAPPA_EXP, 2.0), (KAPPA_INV1P2, 0.0)])
+def test_jacobian_matches_central_differences(kind, a):
+    mesh = cartesian_mesh((5, 4, 3), lognormal_field((5, 4, 3), 1.0, 2.0, seed=4))
+    rng = np.random.default_rng(1)
+    p = rng.uniform(-0.5, 1.0, mesh.n_cells)
+    g = _dirichlet(mesh, 1.0, 0.0)
+    f = rng.uniform(-1, 1, mesh.n_cells)
+    J = tpfa.reduced_jacobian(mesh, kind, a, p, g).toarray()
+    h = 1e-6
+    Jfd = np.zeros_like(J)
+    for j in range(mesh.n_cells):
+        e = np.zeros(mesh.n_cells)
+        e[j] = h
+        Jfd[:, j] = (tpfa.reduced_residual(mesh, kind, a, p + e, f, g)
+                     - tpfa.reduced_residual(mesh, kind, a, p - e, f, g)) / (2 * h)
+    assert np.max(np.abs(J - Jfd)) <= 1e-7 * np.max(np.abs(J))
+
+
+def test_linear_homogeneous_solution_is_exact_linear_profile():
+    """kappa = 1 (a = 0), K_0 = 1, p = 1 at x = 0 and p = 0 at x = 1: TPFA reproduces p = 1 - x exactly."""
+    n = 8
+    mesh = cartesian_mesh((n, n), np.ones(n * n))
+    g = _dirichlet(mesh, 1.0, 0.0)
+    x = (np.arange(mesh.n_cells) % n + 0.5) / n
+    p_exact = 1.0 - x
+    r = tpfa.reduced_residual(mesh, KAPPA_EXP, 0.0, p_exact, np.zeros(mesh.n_cells), g)
+    assert np.max(np.abs(r)) < 1e-13
+    p, _ = newton.solve(mesh, KAPPA_EXP, 0.0, np.zeros(mesh.n_cells), g)
+    assert np.max(np.abs(p - p_exact)) < 1e-13
+
+
+def _brute_force_1d(nx, ups_half, a, gl, gr):
+    """Dense Newton written with plain loops for the 1D TPFA problem kappa = exp(a p)."""
+    p = [gl + (gr - gl) * (i + 0.5) / nx for i in range(nx)]      # start from the linear profile
+    for _ in range(100):
+        R = [0.0] * nx
+        J = [[0.0] * nx for _ in range(nx)]
+        for i in range(nx):
+            k = np.exp(a * p[i])
+            dk = a * k
+            nbrs = []
+            if i > 0:
+                nbrs.append(i - 1)
+            if i < nx - 1:
+                nbrs.append(i + 1)
+            for j in nbrs:
+                kj = np.exp(a * p[j])
+                hi, hj = k * ups_half, kj * ups_half
+                u = 1.0 / (1.0 / hi + 1.0 / hj)
+                du_i = u * u / (hi * hi) * dk * ups_half
+                du_j = u * u / (hj * hj) * a * kj * ups_half
+                R[i] += u * (p[i] - p[j])
+                J[i][i] += u + du_i * (p[i] - p[j])
+                J[i][j] += -u + du_j * (p[i] - p[j])
+            for gb, edge in ((gl, 0), (gr, nx - 1)):
+                if i == edge:
+                    R[i] += k * ups_half * (p[i] - gb)
+                    J[i][i] += dk * ups_half * (p[i] - gb) + k * ups_half
+        if max(abs(v) for v in R) < 1e-15:
+            break
+        dp = np.linalg.solve(np.array(J), -np.array(R))
+        p = [p[i] + dp[i] for i in range(nx)]
+    return np.array(p)
+
+
+def test_1d_reducible_problem_matches_brute_force():
+    """K_0 uniform, Dirichlet only in x, no-flow elsewhere: every row of the 2D solution is the 1D solution."""
+    nx, ny = 10, 4
+    mesh = cartesian_mesh((nx, ny), np.full(nx * ny, 1.0))
+    g = _dirichlet(mesh, 1.0, 0.0)
+    a = 1.5
+    p, _ = newton.solve(mesh, KAPPA_EXP, a, np.zeros(mesh.n_cells), g)
+    ups_half = (1.0 / ny) * 1.0 / (0.5 / nx)       # |eps| K / (h/2)
+    p1 = _brute_force_1d(nx, ups_half, a, 1.0, 0.0)
+    for j in range(ny):
+        assert np.allclose(p[j * nx:(j + 1) * nx], p1, rtol=0, atol=1e-12)
+
+
+def test_solution_is_unique_from_three_starts():
+    pr = problem_config("cart2d_32", scale=10)
+    m = pr.mesh
+    sols = []
+    for x0 in (np.zeros(m.n_cells), np.full(m.n_cells, 1.0), np.linspace(-0.5, 1.5, m.n_cells)):
+        p, _ = newton.solve(m, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, p0=x0)
+        sols.append(p)
+    assert np.allclose(sols[0], sols[1], atol=1e-12) and np.allclose(sols[0], sols[2], atol=1e-12)
+
+
+def test_frozen_matrix_is_m_matrix_and_reproduces_residual():
+    """Remark on monotonicity: the frozen-coefficient TPFA matrix is an M-matrix; A(kappa(p)) p - rhs = R(p)."""
+    pr = problem_config("chan3d_64", scale=6)
+    m = pr.mesh
+    rng = np.random.default_rng(2)
+    p = rng.uniform(0, 1, m.n_cells)
+    A = newton.picard_matrix(m, pr.kappa_kind, pr.kappa_a, p).toarray()
+    off = A - np.diag(np.diag(A))
+    assert np.all(off <= 0)
+    assert np.all(np.diag(A) >= -off.sum(1) - 1e-12)
+    # constant-free part: R(p) - R(0*p) is linear in p with matrix A only for frozen kappa, so compare A p - rhs
+    kp = tpfa.kappa(p, pr.kappa_kind, pr.kappa_a)
+    d = np.where(m.face_bc == 1)[0]
+    rhs = tpfa.rhs_cell(m, pr.f_cell, pr.g_face)
+    np.add.at(rhs, m.face_cells[d, 0], kp[m.face_cells[d, 0]] * m.half_trans[d, 0] * pr.g_face[d])
+    assert np.allclose(A @ p - rhs, tpfa.reduced_residual(m, pr.kappa_kind, pr.kappa_a, p, pr.f_cell, pr.g_face),
+                       rtol=1e-12, atol=1e-10)
