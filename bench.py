@@ -1,0 +1,283 @@
+#!/usr/bin/env python
+"""Benchmark: FP64 FAS solves of the 64^3 channelized TPFA problem on GB300, through the C ABI.
+
+One step = one full nonlinear solve (FAS V-cycles, Algorithm 2) from p = 0 to relative residual 1e-8 on
+device-resident inputs; the hierarchy is built once before timing (setup time reported separately). Prints one JSON
+line. `--impl reference` times the FP64 CPU oracle instead (on a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s to rel. residual 1e-8 (batched mixed vs plain FP64); V-cycle DOF/s"
+WORKLOAD = ("chan3d_64: 64^3 hexahedral TPFA, channelized K over 6 decades, kappa = exp(2 p), 3-level FAS "
+            "(aggregates 64 then 8, 4 modes), FP64 Picard smoothing, tol 1e-8")
+SAMPLE_SCALE = 16          # side of the bounded CPU sample of the same generator
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            sm = [float(r[1]) for r in rows]
+            mx = float(rows[0][2])
+            reasons = set()
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for r in rows:
+                for k, nme in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nme)
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                    "samples": len(rows)}
+        except Exception as e:  # no nvidia-smi
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": str(e)[:80]}
+
+
+def oracle_sample_seconds(steps=1):
+    """Times the FP64 oracle FAS solve (hierarchy excluded) on the 16^3 instance of the same generator."""
+    from synth.grids import problem_config
+    from oracle import fas, hierarchy
+    pr = problem_config("chan3d_64", scale=SAMPLE_SCALE)
+    H = hierarchy.build(pr.mesh, pr.opts)
+    times, cycles = [], []
+    for _ in range(steps):
+        S = fas.FAS(H, pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, pr.opts)
+        t0 = time.perf_counter()
+        S.solve()
+        times.append(time.perf_counter() - t0)
+        cycles.append(S.stats.cycles)
+    return times, cycles, pr.mesh.n_cells
+
+
+def cpu_baseline_dict(full_cells):
+    times, cycles, n = oracle_sample_seconds(1)
+    per_solve = times[0] * (full_cells / n)          # linear-in-cells extrapolation (favours the CPU)
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": "one oracle FAS solve of chan3d at %d^3 (%d cells, %d cycles, %.2f s, SuperLU direct "
+                      "solves, single thread), extrapolated linearly in cells to 64^3" %
+                      (SAMPLE_SCALE, n, cycles[0], times[0])}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    from synth.grids import problem_config
+    from oracle import fas, hierarchy
+    pr = problem_config("chan3d_64", scale=SAMPLE_SCALE)
+    H = hierarchy.build(pr.mesh, pr.opts)
+    full = 64 ** 3
+
+    def step():
+        S = fas.FAS(H, pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, pr.opts)
+        t0 = time.perf_counter()
+        S.solve()
+        return time.perf_counter() - t0, S.stats.cycles
+
+    for _ in range(args.warmup):
+        step()
+    ts, cyc = [], []
+    for _ in range(args.steps):
+        t, c = step()
+        ts.append(t)
+        cyc.append(c)
+    per = sum(ts) / len(ts) * (full / pr.mesh.n_cells)
+    value = 1.0 / per
+    sample = ("oracle FAS solves of chan3d at %d^3 (%d cells), hierarchy excluded, single thread; time extrapolated "
+              "linearly in cells to 64^3" % (SAMPLE_SCALE, pr.mesh.n_cells))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": full, "sample_cells": pr.mesh.n_cells},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2005_01275_gb300 import build, nlmg
+    build.build()
+    from synth.grids import problem_config
+    pr = problem_config("chan3d_64", scale=args.scale)
+    N = pr.mesh.n_cells
+    t0 = time.perf_counter()
+    ctx = nlmg.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.opts)
+    setup_s = time.perf_counter() - t0
+    dev = torch.device("cuda", local_rank)
+    f_d = torch.from_numpy(pr.f_cell).to(dev)
+    g_d = torch.from_numpy(pr.g_face).to(dev)
+    p_d = torch.zeros(N, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    torch.cuda.synchronize()
+
+    def solve_dev():
+        rep, st = ctx.solve_device(f_d.data_ptr(), g_d.data_ptr(), 0, p_d.data_ptr(), 1e-8, 1e-10, 60)
+        if st != nlmg.OK:
+            raise RuntimeError("solve failed with status %d: %s" % (st, rep))
+        return rep
+
+    for _ in range(args.warmup):
+        solve_dev()
+    # timed region: K device-resident solves, L2 flushed between steps (outside each step's event pair)
+    ctx.profile(True)
+    reps = []
+    with Clocks(local_rank) as clk:
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            reps.append(solve_dev())
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        wall = time.perf_counter() - w0
+    clocks = clk.summary()
+    spmv = ctx.profile_read(0)
+    upd = ctx.profile_read(1)
+    res = ctx.profile_read(2)
+    ctx.profile(False)
+    dev_ms = sum(r["solve_ms"] for r in reps)
+    if dist is not None:
+        t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = float(t.item())
+    # end to end through the host-pointer C-ABI call: H2D of f and g from pinned memory, D2H of p
+    f_h = torch.from_numpy(pr.f_cell).pin_memory()
+    g_h = torch.from_numpy(pr.g_face).pin_memory()
+    p_h = torch.zeros(N, dtype=torch.float64).pin_memory()
+    e2e_t = []
+    for _ in range(max(1, args.steps)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rep, st = ctx.solve_ptr(f_h.data_ptr(), g_h.data_ptr(), p_h.data_ptr())
+        e2e_t.append(time.perf_counter() - t1)
+        if st != nlmg.OK:
+            raise RuntimeError("e2e solve failed %d" % st)
+    e2e_s = sum(e2e_t)
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+    peak, peak_kind = _peaks()
+    ms_step = dev_ms / args.steps
+    cycles = sum(r["cycles"] for r in reps) / len(reps)
+    value = world * args.steps / (dev_ms / 1e3)
+    n_sp, ms_sp, by_sp = spmv
+    avg_sp = ms_sp / max(n_sp, 1)
+    achieved = by_sp / (avg_sp / 1e3) / 1e9 if n_sp else None
+    cpu = cpu_baseline_dict(N) if (args.cpu_baseline and world == 1) else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": N, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "256 MiB buffer written between steps, outside each step's CUDA-event pair",
+                   "setup_s": round(setup_s, 3)},
+        "vcycle_dof_per_s": N * cycles * world / (ms_step / 1e3),
+        "cycles_per_solve": cycles,
+        "lin_iters_per_solve": sum(r["lin_iters"] for r in reps) / len(reps),
+        "wall_s_timed_region": wall,
+        "roofline": {"bound": "hbm", "kernel": "k_fine_spmv (CG matrix product, frozen TPFA matrix)",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "bytes_per_launch": by_sp, "avg_launch_us": avg_sp * 1e3, "launches": n_sp,
+                     "share_of_solve": ms_sp / dev_ms if dev_ms else None,
+                     "others": {"k_pcg_update": {"launches": upd[0], "avg_us": upd[1] / max(upd[0], 1) * 1e3,
+                                                 "GB/s": upd[2] / (upd[1] / max(upd[0], 1) / 1e3) / 1e9
+                                                 if upd[0] else None},
+                                "k_residual": {"launches": res[0], "avg_us": res[1] / max(res[0], 1) * 1e3,
+                                               "GB/s": res[2] / (res[1] / max(res[0], 1) / 1e3) / 1e9
+                                               if res[0] else None}}},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * len(e2e_t) / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * (N + len(pr.g_face)),
+                "d2h_bytes_per_step": 8 * N},
+        "gpu_launches": int(sum(r["kernel_launches"] for r in reps)),
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="nlmg", choices=["nlmg", "reference"])
+    ap.add_argument("--scale", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus if "RANK" in os.environ else 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    return run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/* nlmg.h - C ABI of the GB300 FAS multigrid library for heterogeneous nonlinear diffusion.
+ *
+ * Method: Lee, Hamon, Castelletto, Vassilevski, White, "Nonlinear multigrid based on local spectral coarsening for
+ * heterogeneous diffusion problems". Problem (Sec. 2): div(-K0(x) kappa(p) grad p) = f with Dirichlet / Neumann
+ * data, discretised by cell-centred TPFA finite volumes (eqs. TPFA_flux, half-transmissibility, FV_matrix); solved by
+ * FAS V-cycles (Algorithm 2) with backtracking (Algorithm 1) on a hierarchy built by local spectral coarsening
+ * (Sec. 3.1, App. A) whose coarse operators use one coefficient per aggregate (eq. structure, Prop. 1).
+ *
+ * Conventions (all calls):
+ *   - every pointer argument is a HOST pointer unless the name ends in _dev (device pointer on the context's
+ *     device); host arrays are read or written during the call only and stay owned by the caller;
+ *   - the context owns all device memory it allocates; nothing is thrown across the ABI; every call returns a
+ *     status and, on error, nlmg_last_error(ctx) describes it;
+ *   - indices are int32, values float64 (IEEE binary64). Cells 0..n_cells-1, faces 0..n_faces-1;
+ *   - a context is used by one host thread at a time; its device work runs on the context's own CUDA stream.
+ */
+#ifndef NLMG_H
+#define NLMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nlmg_ctx nlmg_ctx;
+
+typedef enum {
+  NLMG_OK = 0,
+  NLMG_EINVAL = 1,        /* invalid argument or mesh */
+  NLMG_ENOMEM = 2,        /* device allocation failed */
+  NLMG_ENOCONV = 3,       /* tolerance not reached within max_cycles (best iterate still written) */
+  NLMG_EDIVERGED = 4,     /* NaN/Inf residual */
+  NLMG_ETIMEOUT = 5,
+  NLMG_ECUDA = 6,         /* CUDA runtime error */
+  NLMG_EUNSUPPORTED = 7
+} nlmg_status;
+
+/* kappa(p) multiplying K0 (eq. kappa): NLMG_KAPPA_EXP is exp(a p) (eq. permeability_pressure_relationship);
+ * NLMG_KAPPA_INV1P2 is 1 / (1 + p^2) (a is ignored). */
+typedef enum { NLMG_KAPPA_EXP = 0, NLMG_KAPPA_INV1P2 = 1 } nlmg_kappa_kind;
+typedef struct {
+  int32_t kind;
+  double a;
+} nlmg_kappa;
+
+/* Face boundary tags. */
+enum { NLMG_FACE_INTERIOR = 0, NLMG_FACE_DIRICHLET = 1, NLMG_FACE_NEUMANN = 2 };
+
+/* The cell graph of Sec. 2.1. face_cells[2f] = K, face_cells[2f+1] = L with K < L for an interior face and L = -1 for
+ * a boundary face; half_trans[2f + i] is the geometric half transmissibility Ups_bar of eq. half-transmissibility of
+ * cell K (i = 0) and L (i = 1, ignored on boundary faces); face_bc[f] is a NLMG_FACE_* tag; face_area[f] = |eps|;
+ * cell_volume[K] = |tau_K|. The flux of face f is oriented out of K. */
+typedef struct {
+  int32_t n_cells;
+  const double* cell_volume;
+  int32_t n_faces;
+  const int32_t* face_cells;
+  const double* half_trans;
+  const uint8_t* face_bc;
+  const double* face_area;
+} nlmg_mesh;
+
+/* Smoother on level 0. */
+enum { NLMG_SMOOTH_PICARD = 0, NLMG_SMOOTH_JACOBI = 1 };
+
+typedef struct {
+  int32_t n_levels;          /* hierarchy levels including the fine one (1..8) */
+  int32_t agg_size[8];       /* target aggregate size of coarsening step l -> l+1 */
+  int32_t modes[8];          /* spectral pressure modes per aggregate of step l -> l+1 */
+  int32_t smoother;          /* NLMG_SMOOTH_* for level 0; coarse levels always take a Picard step */
+  int32_t nu_pre, nu_post;   /* Jacobi sweeps per smoothing step (Jacobi smoother only) */
+  double omega;              /* Jacobi damping */
+  int32_t bt_nmax;           /* Algorithm 1: maximum halvings (paper: 4) */
+  double bt_theta;           /* Algorithm 1: theta (paper: 0.9) */
+  double dp_clamp;           /* Sec. 4.1 pressure-change clamp; <= 0 disables */
+  int32_t coarsest_steps;    /* Picard steps on the coarsest level (paper: <= 10) */
+  double lin_tol;            /* relative tolerance of the PCG solves inside Picard steps */
+  int32_t lin_maxit;         /* iteration cap of those solves */
+  int32_t setup_threads;     /* host threads for the setup (0 = all) */
+  int32_t reserved[7];
+} nlmg_options;
+
+typedef struct {
+  int32_t cycles;            /* V-cycles (or Picard iterations for nlmg_solve_picard) */
+  int32_t early_exit;        /* last cycle stopped after pre-smoothing */
+  double res0, res;          /* ||R(p_0)||_2, ||R(p_final)||_2 */
+  double solve_ms;           /* device wall time of the solve */
+  int64_t fine_evals;        /* fine residual evaluations */
+  int64_t lin_iters;         /* PCG iterations, all levels */
+  int64_t kernel_launches;   /* CUDA kernels launched by the solve */
+  int32_t history_len;
+  double history[64];        /* ||R|| after each cycle (first entry = res0) */
+} nlmg_report;
+
+typedef struct {
+  int32_t n_cells, n_flux, n_p, n_lambda;
+} nlmg_level_info;
+
+/* Fills *opt with the paper's constants (n_max = 4, theta = 0.9, <= 10 coarsest steps) and library defaults. */
+void nlmg_default_options(nlmg_options* opt);
+
+/* Builds the hierarchy (host C++: aggregation, spectral bases, coarse flux space, static local matrices;
+ * App. A-C) and uploads it and the mesh to the current CUDA device. *out receives a new context, to be released
+ * with nlmg_destroy. Errors: NLMG_EINVAL (bad mesh/options), NLMG_ENOMEM, NLMG_ECUDA. */
+nlmg_status nlmg_setup(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlmg_options* opt, nlmg_ctx** out);
+
+/* Host-only variant of nlmg_setup: builds the same hierarchy without touching any CUDA device. The context then
+ * serves the hierarchy export calls below (nlmg_level_info_get, nlmg_get_aggregates, nlmg_get_transfer_dense)
+ * and nothing else; every device call on it returns NLMG_EINVAL. */
+nlmg_status nlmg_setup_host(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlmg_options* opt,
+                            nlmg_ctx** out);
+
+/* Sets the problem data: f_cell[n_cells] (source density f|_K) and g_face[n_faces] (Dirichlet pressure or Neumann
+ * flux density per boundary face, ignored on interior faces). [f]_K = |tau_K| f_K + sum_Neumann |eps| g_N
+ * (definitions under eq. FV_matrix). */
+nlmg_status nlmg_set_data(nlmg_ctx* ctx, const double* f_cell, const double* g_face);
+
+/* FAS solve (Algorithm 2 cycles from level 0) from x0[n_cells] (NULL = 0) until ||R|| <= tol_rel ||R(x0)|| or
+ * ||R|| <= tol_abs (Sec. 4), at most max_cycles cycles; p_out[n_cells]. Host buffers: data are copied in and the
+ * solution out inside the call. Returns NLMG_ENOCONV if the tolerance was not met (p_out holds the last iterate). */
+nlmg_status nlmg_solve(nlmg_ctx* ctx, const double* f_cell, const double* g_face, const double* x0, double tol_rel,
+                       double tol_abs, int32_t max_cycles, double* p_out, nlmg_report* rep);
+
+/* Same on device-resident buffers (f_dev[n_cells], g_dev[n_faces], x0_dev may be NULL, p_dev[n_cells] output). */
+nlmg_status nlmg_solve_device(nlmg_ctx* ctx, const double* f_dev, const double* g_dev, const double* x0_dev,
+                              double tol_rel, double tol_abs, int32_t max_cycles, double* p_dev, nlmg_report* rep);
+
+/* Single-level Picard baseline (Sec. 2.2): frozen-coefficient TPFA solves (PCG) + clamp + Algorithm 1. Host buffers;
+ * max_cycles bounds the Picard iterations. */
+nlmg_status nlmg_solve_picard(nlmg_ctx* ctx, const double* f_cell, const double* g_face, const double* x0,
+                              double tol_rel, double tol_abs, int32_t max_cycles, double* p_out, nlmg_report* rep);
+
+/* ---- single steps of the path, for parity tests (host buffers; problem data from nlmg_set_data) ------------ */
+
+/* R(p) (reduced TPFA residual, net outgoing flux minus [f]) at p[n_cells] -> r_out[n_cells]. */
+nlmg_status nlmg_fine_residual(nlmg_ctx* ctx, const double* p, double* r_out);
+
+/* TPFA fluxes on the level-0 flux unknowns (interior + Dirichlet faces in face order) -> sigma_out[n_flux(0)]. */
+nlmg_status nlmg_fine_flux(nlmg_ctx* ctx, const double* p, double* sigma_out);
+
+/* A^l(x) = [M^l(Pi~ p) sigma + D^T p ; D sigma] (eq. structure) on a coarse level l >= 1; x = [sigma; p] of length
+ * n_flux(l) + n_p(l) -> out (same length). */
+nlmg_status nlmg_level_apply(nlmg_ctx* ctx, int32_t level, const double* x, double* out);
+
+/* Intergrid transfers between level l and l+1 (Sec. 3.1): op 0 = projection Q x, 1 = restriction P^T r,
+ * 2 = prolongation P e. Vectors are [sigma; p]; on level 0 they hold p only, and the projection takes p and uses the
+ * TPFA fluxes of p (the data of nlmg_set_data) for the flux part. */
+enum { NLMG_PROJECT = 0, NLMG_RESTRICT = 1, NLMG_PROLONG = 2 };
+nlmg_status nlmg_transfer(nlmg_ctx* ctx, int32_t level, int32_t op, const double* in, double* out);
+
+/* The Picard update on level l: dx solving the frozen-coefficient system of eq. picardian_system,
+ * A_frozen(x) dx = b - A(x) (level 0: A(kappa(p)) dp = -R(p), b ignored), by PCG to lin_tol. */
+nlmg_status nlmg_picard_update(nlmg_ctx* ctx, int32_t level, const double* x, const double* b, double* dx_out,
+                               int32_t* iters);
+
+/* One FAS cycle from level 0 (Algorithm 2) from p_in; r0 is the reference ||R(p_0)|| for the early exit. */
+nlmg_status nlmg_vcycle(nlmg_ctx* ctx, const double* p_in, double r0, double* p_out, double* res_out,
+                        int32_t* early_exit);
+
+/* ---- hierarchy export, for tests -------------------------------------------------------------------------- */
+nlmg_status nlmg_level_info_get(nlmg_ctx* ctx, int32_t level, nlmg_level_info* out);
+/* Aggregates of coarsening step l -> l+1: agg_of[n_cells(l)]; m_out[n_cells(l+1)] modes per aggregate. */
+nlmg_status nlmg_get_aggregates(nlmg_ctx* ctx, int32_t level, int32_t* agg_of, int32_t* m_out);
+/* Dense export of a transfer matrix of step l -> l+1: which 0 = P_p (n_p(l) x n_p(l+1)), 1 = P_sigma
+ * (n_flux(l) x n_flux(l+1)), 2 = Q_sigma (n_flux(l+1) x n_flux(l)); row-major into dense (caller-sized). */
+nlmg_status nlmg_get_transfer_dense(nlmg_ctx* ctx, int32_t level, int32_t which, double* dense);
+
+/* ---- measurement ----------------------------------------------------------------------------------------- */
+/* Enables (1) or disables (0) CUDA-event timing of the hot kernels on the context stream and clears the counters.
+ * Kernel ids: 0 = fine CG matrix product (k_fine_spmv), 1 = fine CG vector update (k_pcg_update),
+ * 2 = fine TPFA residual (k_residual). */
+nlmg_status nlmg_profile(nlmg_ctx* ctx, int32_t enable);
+/* Launch count, summed event time and algorithmic bytes per launch (each streamed array counted once; the
+ * gathered neighbour values counted once) of a profiled kernel since nlmg_profile(ctx, 1). */
+nlmg_status nlmg_profile_read(nlmg_ctx* ctx, int32_t kernel, int64_t* launches, double* total_ms,
+                              double* bytes_per_launch);
+
+const char* nlmg_last_error(const nlmg_ctx* ctx);
+void nlmg_destroy(nlmg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

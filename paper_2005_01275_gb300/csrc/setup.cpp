@@ -1,0 +1,737 @@
+// Host-side construction of the spectral multilevel hierarchy (App. A-C of the paper), FP64.
+//
+// Per coarsening step l -> l+1 (m_f = 1 flux unknown per coarse interface):
+//  * aggregates of the level-l cell graph by the deterministic greedy rule (stands in for METIS, Sec. 3.1);
+//  * P_A: the m smallest eigenvectors of D_N M_N^-1 D_N^T on the extended aggregate N(A) at kappa = 1
+//    (eq. local-eigenvalue-problem), restricted to A, with q_PV = 1^l|_A / ||1^l|_A|| projected out and the
+//    remaining directions orthonormalised by an SVD, q_PV first (eqs. structure_pressure_interpolation,
+//    definition_q_pv); singular values <= 1e-10 of the largest are dropped;
+//  * one flux basis function per coarse interface F = (a, b): sigma from the local saddle on A_a U A_b with pressure
+//    data -1/||1_a||^2 on a, +1/||1_b||^2 on b (eq. local_problem_to_define_sigma_pv); with m_f = 1 its
+//    restriction to each aggregate is also the trace extension of eq. local_neumann_boundary_value_problem (the two
+//    problems have the same unique flux), so the whole local solution is the basis function;
+//  * one boundary basis function per aggregate owning Dirichlet unknowns: the local saddle on A with those unknowns
+//    kept and pressure data -1/||1_A||^2;
+//  * m_A - 1 bubbles per aggregate: the Neumann saddle on A with pressure data q (each NPV column);
+//  * Q_sigma: interface / boundary coefficient = outflow of the aggregate through the interface divided by that of
+//    the basis function; bubble coefficients = P_NPV^T (D sigma)|_A; D^{l+1} = P_p^T D^l P_sigma;
+//  * static local matrices M_a^{l+1} = P_sigma,a^T M_A^l P_sigma,a (Prop. 1, App. C) and the Pi~ weights
+//    w_a = |A|^-1 sum_{c in a} |c| w_c^T P_a[rows of c] (eq. pwc_projector, applied recursively).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <deque>
+#include <functional>
+#include <map>
+#include <thread>
+
+#include "dense.hpp"
+#include "hier.hpp"
+
+namespace nlmg {
+
+namespace {
+
+void parallel_for(int n, int threads, const std::function<void(int, int, int)>& body) {
+  // body(begin, end, worker) over contiguous chunks claimed dynamically; results must not depend on the order
+  if (threads <= 1 || n < 2) {
+    body(0, n, 0);
+    return;
+  }
+  std::atomic<int> next(0);
+  const int chunk = std::max(1, n / (threads * 8));
+  std::vector<std::thread> pool;
+  for (int t = 0; t < threads; ++t)
+    pool.emplace_back([&, t]() {
+      for (;;) {
+        int b = next.fetch_add(chunk);
+        if (b >= n) break;
+        body(b, std::min(n, b + chunk), t);
+      }
+    });
+  for (auto& th : pool) th.join();
+}
+
+// Per-thread scratch: stamped membership and position maps so that sets can be built without clearing.
+struct Scratch {
+  std::vector<int> cell_stamp, flux_stamp, flux_pos;
+  int token = 0;
+  void init(int nc, int nf) {
+    cell_stamp.assign(nc, 0);
+    flux_stamp.assign(nf, 0);
+    flux_pos.assign(nf, -1);
+    token = 0;
+  }
+  int next() { return ++token; }
+};
+
+// A local mixed problem on a set of cells S with flux unknowns U (sorted).
+struct LocalProblem {
+  std::vector<int> cells, U, prow;   // prow[k] = first local pressure row of cells[k]
+  int np = 0;
+  std::vector<double> M, D, ones;    // M: |U| x |U|, D: np x |U|
+};
+
+void assemble_local(const Level& L, const std::vector<int>& cells, const std::vector<int>& U, Scratch& sc,
+                    LocalProblem& lp) {
+  lp.cells = cells;
+  lp.U = U;
+  const int ns = (int)U.size();
+  int tok = sc.next();
+  for (int k = 0; k < ns; ++k) {
+    sc.flux_stamp[U[k]] = tok;
+    sc.flux_pos[U[k]] = k;
+  }
+  lp.prow.resize(cells.size());
+  lp.np = 0;
+  for (size_t k = 0; k < cells.size(); ++k) {
+    lp.prow[k] = lp.np;
+    lp.np += L.m[cells[k]];
+  }
+  lp.M.assign((size_t)ns * ns, 0.0);
+  lp.D.assign((size_t)lp.np * ns, 0.0);
+  lp.ones.assign(lp.np, 0.0);
+  for (size_t k = 0; k < cells.size(); ++k) {
+    int c = cells[k];
+    int nl = L.nloc(c), mc = L.m[c];
+    const int* lc = &L.loc[L.loc_off[c]];
+    const double* Mc = &L.Mloc[L.mat_off[c]];
+    const double* Dc = &L.Dloc[L.dmat_off[c]];
+    for (int r = 0; r < mc; ++r) lp.ones[lp.prow[k] + r] = L.ones[L.p_off[c] + r];
+    for (int s = 0; s < nl; ++s) {
+      if (sc.flux_stamp[lc[s]] != tok) continue;
+      int ps = sc.flux_pos[lc[s]];
+      for (int t = 0; t < nl; ++t) {
+        if (sc.flux_stamp[lc[t]] != tok) continue;
+        lp.M[(size_t)ps * ns + sc.flux_pos[lc[t]]] += Mc[(size_t)s * nl + t];
+      }
+      for (int r = 0; r < mc; ++r) lp.D[(size_t)(lp.prow[k] + r) * ns + ps] += Dc[(size_t)r * nl + s];
+    }
+  }
+}
+
+// Flux unknowns whose owners all lie in the stamped cell set: interfaces with both owners inside, bubbles.
+std::vector<int> internal_flux(const Level& L, const std::vector<int>& cells, Scratch& sc) {
+  int tok = sc.next();
+  for (int c : cells) sc.cell_stamp[c] = tok;
+  std::vector<int> U;
+  for (int c : cells)
+    for (int k = L.loc_off[c]; k < L.loc_off[c + 1]; ++k) {
+      int i = L.loc[k];
+      if (L.fkind[i] == KIND_IFACE) {
+        if (sc.cell_stamp[L.fown0[i]] == tok && sc.cell_stamp[L.fown1[i]] == tok) U.push_back(i);
+      } else if (L.fkind[i] == KIND_BUBBLE) {
+        U.push_back(i);
+      }
+    }
+  std::sort(U.begin(), U.end());
+  U.erase(std::unique(U.begin(), U.end()), U.end());
+  return U;
+}
+
+// Schur complement S = D M^-1 D^T and X = M^-1 D^T (|U| x np); returns false if M is not SPD.
+bool schur(const LocalProblem& lp, std::vector<double>& S, std::vector<double>& X) {
+  const int ns = (int)lp.U.size(), np = lp.np;
+  X.assign((size_t)ns * np, 0.0);
+  bool diag = true;
+  for (int i = 0; i < ns && diag; ++i)
+    for (int j = 0; j < ns; ++j)
+      if (i != j && lp.M[(size_t)i * ns + j] != 0.0) { diag = false; break; }
+  if (diag) {
+    for (int i = 0; i < ns; ++i) {
+      double mi = lp.M[(size_t)i * ns + i];
+      if (!(mi > 0)) return false;
+      for (int r = 0; r < np; ++r) X[(size_t)i * np + r] = lp.D[(size_t)r * ns + i] / mi;
+    }
+  } else {
+    std::vector<double> Lc(lp.M);
+    if (!chol_factor(ns, Lc.data())) return false;
+    std::vector<double> col(ns);
+    for (int r = 0; r < np; ++r) {
+      for (int i = 0; i < ns; ++i) col[i] = lp.D[(size_t)r * ns + i];
+      chol_solve(ns, Lc.data(), col.data());
+      for (int i = 0; i < ns; ++i) X[(size_t)i * np + r] = col[i];
+    }
+  }
+  S.assign((size_t)np * np, 0.0);
+  for (int r = 0; r < np; ++r) {
+    const double* Dr = &lp.D[(size_t)r * ns];
+    for (int i = 0; i < ns; ++i) {
+      double d = Dr[i];
+      if (d == 0.0) continue;
+      const double* Xi = &X[(size_t)i * np];
+      double* Sr = &S[(size_t)r * np];
+      for (int q = 0; q < np; ++q) Sr[q] += d * Xi[q];
+    }
+  }
+  for (int r = 0; r < np; ++r)
+    for (int q = r + 1; q < np; ++q) {
+      double a = 0.5 * (S[(size_t)r * np + q] + S[(size_t)q * np + r]);
+      S[(size_t)r * np + q] = S[(size_t)q * np + r] = a;
+    }
+  return true;
+}
+
+// Factor for repeated local solves [M D^T; D 0][s; p] = [0; rp] (optionally bordered by ones^T p = 0).
+struct LocalSolver {
+  const LocalProblem* lp = nullptr;
+  std::vector<double> X, K;   // X = M^-1 D^T ; K = LU of [S 1; 1^T 0] (bordered) or S
+  std::vector<int> piv;
+  bool bordered = true;
+  int nk = 0;
+  bool init(const LocalProblem& p, bool border) {
+    lp = &p;
+    bordered = border;
+    std::vector<double> S;
+    if (!schur(p, S, X)) return false;
+    int np = p.np;
+    nk = np + (border ? 1 : 0);
+    K.assign((size_t)nk * nk, 0.0);
+    for (int r = 0; r < np; ++r)
+      for (int q = 0; q < np; ++q) K[(size_t)r * nk + q] = S[(size_t)r * np + q];
+    if (border)
+      for (int r = 0; r < np; ++r) {
+        K[(size_t)r * nk + np] = p.ones[r];
+        K[(size_t)np * nk + r] = p.ones[r];
+      }
+    piv.assign(nk, 0);
+    return lu_factor(nk, K.data(), piv.data());
+  }
+  // rs = 0: S p = -rp ; sigma = -X p
+  void solve_p_rhs(const std::vector<double>& rp, std::vector<double>& sigma) const {
+    int np = lp->np, ns = (int)lp->U.size();
+    std::vector<double> b(nk, 0.0);
+    for (int r = 0; r < np; ++r) b[r] = -rp[r];
+    lu_solve(nk, K.data(), piv.data(), b.data());
+    sigma.assign(ns, 0.0);
+    for (int i = 0; i < ns; ++i) {
+      double s = 0.0;
+      for (int r = 0; r < np; ++r) s += X[(size_t)i * np + r] * b[r];
+      sigma[i] = -s;
+    }
+  }
+};
+
+void sort_unique(std::vector<int>& v) {
+  std::sort(v.begin(), v.end());
+  v.erase(std::unique(v.begin(), v.end()), v.end());
+}
+
+}  // namespace
+
+std::vector<int> aggregate_graph(int n, const std::vector<int>& nb_off, const std::vector<int>& nb, int target) {
+  std::vector<int> agg(n, -1);
+  int nagg = 0;
+  std::deque<int> q;
+  for (int s = 0; s < n; ++s) {
+    if (agg[s] != -1) continue;
+    int id = nagg++;
+    agg[s] = id;
+    int count = 1;
+    q.clear();
+    q.push_back(s);
+    while (!q.empty() && count < target) {
+      int v = q.front();
+      q.pop_front();
+      for (int k = nb_off[v]; k < nb_off[v + 1]; ++k) {
+        if (count >= target) break;
+        int u = nb[k];
+        if (agg[u] == -1) {
+          agg[u] = id;
+          ++count;
+          q.push_back(u);
+        }
+      }
+    }
+  }
+  // members per aggregate, kept current as merges happen
+  std::vector<std::vector<int>> members(nagg);
+  for (int v = 0; v < n; ++v) members[agg[v]].push_back(v);
+  for (int id = 0; id < nagg; ++id) {
+    auto& mem = members[id];
+    if (mem.empty() || 2 * (long)mem.size() >= target) continue;
+    std::map<int, int> shared;
+    for (int v : mem)
+      for (int k = nb_off[v]; k < nb_off[v + 1]; ++k) {
+        int b = agg[nb[k]];
+        if (b != id) shared[b] += 1;
+      }
+    if (shared.empty()) continue;
+    int best = -1, bestc = -1;
+    for (auto& kv : shared)                          // ascending id: first maximum wins ties
+      if (kv.second > bestc) { bestc = kv.second; best = kv.first; }
+    for (int v : mem) agg[v] = best;
+    auto& dst = members[best];
+    dst.insert(dst.end(), mem.begin(), mem.end());
+    mem.clear();
+  }
+  std::vector<int> remap(nagg, -1);
+  int next = 0;
+  for (int id = 0; id < nagg; ++id)
+    if (!members[id].empty()) remap[id] = next++;
+  for (int v = 0; v < n; ++v) agg[v] = remap[agg[v]];
+  return agg;
+}
+
+Level make_level0(const FineMesh& fm) {
+  Level L;
+  L.n_cells = fm.n_cells;
+  std::vector<std::vector<std::pair<int, int>>> per(fm.n_cells);
+  for (int f = 0; f < fm.n_faces; ++f) {
+    if (fm.bc[f] == 2) continue;
+    int j = L.n_flux++;
+    L.face_of_flux.push_back(f);
+    bool itf = fm.bc[f] == 0;
+    L.fkind.push_back(itf ? KIND_IFACE : KIND_BDRY);
+    L.fown0.push_back(fm.fk[f]);
+    L.fown1.push_back(itf ? fm.fl[f] : -1);
+    per[fm.fk[f]].push_back({j, 0});
+    if (itf) per[fm.fl[f]].push_back({j, 1});
+  }
+  L.m.assign(fm.n_cells, 1);
+  L.p_off.resize(fm.n_cells + 1);
+  L.loc_off.assign(1, 0);
+  L.mat_off.assign(1, 0);
+  L.dmat_off.assign(1, 0);
+  for (int c = 0; c < fm.n_cells; ++c) {
+    L.p_off[c] = c;
+    auto& it = per[c];
+    std::sort(it.begin(), it.end());
+    int nl = (int)it.size();
+    for (auto& e : it) L.loc.push_back(e.first);
+    size_t mo = L.Mloc.size();
+    L.Mloc.resize(mo + (size_t)nl * nl, 0.0);
+    for (int s = 0; s < nl; ++s) {
+      int f = L.face_of_flux[it[s].first];
+      double ups = it[s].second == 0 ? fm.ups0[f] : fm.ups1[f];
+      L.Mloc[mo + (size_t)s * nl + s] = 1.0 / ups;
+      L.Dloc.push_back(it[s].second == 0 ? -1.0 : 1.0);
+    }
+    L.loc_off.push_back((int)L.loc.size());
+    L.mat_off.push_back((int)L.Mloc.size());
+    L.dmat_off.push_back((int)L.Dloc.size());
+  }
+  L.p_off[fm.n_cells] = fm.n_cells;
+  L.w.assign(fm.n_cells, 1.0);
+  L.vol = fm.vol;
+  L.ones.assign(fm.n_cells, 1.0);
+  return L;
+}
+
+// One coarsening step.
+static bool coarsen(const Level& L, int target, int modes, int threads, Level& C, Transfer& T, std::string& err) {
+  const int n = L.n_cells;
+  // ---- cell graph ----------------------------------------------------------------------------------------------
+  std::vector<std::vector<int>> nbv(n);
+  for (int i = 0; i < L.n_flux; ++i)
+    if (L.fkind[i] == KIND_IFACE) {
+      nbv[L.fown0[i]].push_back(L.fown1[i]);
+      nbv[L.fown1[i]].push_back(L.fown0[i]);
+    }
+  std::vector<int> nb_off(n + 1, 0), nb;
+  for (int v = 0; v < n; ++v) {
+    sort_unique(nbv[v]);
+    nb_off[v + 1] = nb_off[v] + (int)nbv[v].size();
+    nb.insert(nb.end(), nbv[v].begin(), nbv[v].end());
+  }
+  T.agg_of = aggregate_graph(n, nb_off, nb, target);
+  int na = 0;
+  for (int a : T.agg_of) na = std::max(na, a + 1);
+  T.agg_off.assign(na + 1, 0);
+  for (int v = 0; v < n; ++v) T.agg_off[T.agg_of[v] + 1]++;
+  for (int a = 0; a < na; ++a) T.agg_off[a + 1] += T.agg_off[a];
+  T.agg_cells.assign(n, 0);
+  {
+    std::vector<int> fill(T.agg_off.begin(), T.agg_off.end() - 1);
+    for (int v = 0; v < n; ++v) T.agg_cells[fill[T.agg_of[v]]++] = v;
+  }
+  auto cells_of = [&](int a) { return std::vector<int>(&T.agg_cells[T.agg_off[a]], &T.agg_cells[T.agg_off[a + 1]]); };
+  auto np_of = [&](int a) {
+    int s = 0;
+    for (int k = T.agg_off[a]; k < T.agg_off[a + 1]; ++k) s += L.m[T.agg_cells[k]];
+    return s;
+  };
+  std::vector<Scratch> scr(std::max(threads, 1));
+  for (auto& s : scr) s.init(n, L.n_flux);
+  // ---- spectral pressure bases ---------------------------------------------------------------------------------
+  std::vector<std::vector<double>> PA(na);
+  std::vector<int> ma(na, 1);
+  T.eig_gap.assign(na, 0.0);
+  std::atomic<bool> fail(false);
+  parallel_for(na, threads, [&](int b, int e, int w) {
+    Scratch& sc = scr[w];
+    for (int a = b; a < e; ++a) {
+      std::vector<int> cA = cells_of(a);
+      std::vector<int> cN(cA);
+      for (int c : cA) cN.insert(cN.end(), &nb[nb_off[c]], &nb[nb_off[c + 1]]);
+      sort_unique(cN);
+      std::vector<int> UN = internal_flux(L, cN, sc);
+      LocalProblem lp;
+      assemble_local(L, cN, UN, sc, lp);
+      std::vector<double> S, X;
+      if (!schur(lp, S, X)) { fail = true; continue; }
+      int npA = np_of(a);
+      int m = std::min(modes, npA);
+      std::vector<double> vals, vecs;
+      double nextv = 0.0;
+      sym_eig_smallest(lp.np, S, m, vals, vecs, &nextv);
+      T.eig_gap[a] = nextv - vals[m - 1];
+      // rows of A's pressure unknowns inside N(A)
+      std::vector<int> rows;
+      for (size_t k = 0, j = 0; k < cN.size(); ++k) {
+        if (j < cA.size() && cN[k] == cA[j]) {
+          for (int r = 0; r < L.m[cN[k]]; ++r) rows.push_back(lp.prow[k] + r);
+          ++j;
+        }
+      }
+      std::vector<double> q(npA);
+      double qn = 0.0;
+      {
+        int t = 0;
+        for (int c : cA)
+          for (int r = 0; r < L.m[c]; ++r) { q[t] = L.ones[L.p_off[c] + r]; qn += q[t] * q[t]; ++t; }
+      }
+      qn = std::sqrt(qn);
+      for (auto& x : q) x /= qn;
+      std::vector<double> V((size_t)npA * m);
+      for (int i = 0; i < npA; ++i)
+        for (int j = 0; j < m; ++j) V[(size_t)i * m + j] = vecs[(size_t)rows[i] * m + j];
+      for (int j = 0; j < m; ++j) {
+        double d = 0.0;
+        for (int i = 0; i < npA; ++i) d += q[i] * V[(size_t)i * m + j];
+        for (int i = 0; i < npA; ++i) V[(size_t)i * m + j] -= d * q[i];
+      }
+      std::vector<std::vector<double>> cols;
+      cols.push_back(q);
+      if (m > 1) {
+        std::vector<double> U, sv;
+        jacobi_svd(npA, m, V, U, sv);
+        int keep = 0;
+        if (sv[0] > 0)
+          for (int j = 0; j < m; ++j)
+            if (sv[j] > 1e-10 * sv[0]) keep++;
+        keep = std::min(keep, std::min(m - 1, npA - 1));
+        for (int j = 0; j < keep; ++j) {
+          std::vector<double> u(npA);
+          int imax = 0;
+          for (int i = 0; i < npA; ++i) {
+            u[i] = U[(size_t)i * m + j];
+            if (std::fabs(u[i]) > std::fabs(u[imax])) imax = i;
+          }
+          if (u[imax] < 0)
+            for (auto& x : u) x = -x;
+          cols.push_back(u);
+        }
+      }
+      ma[a] = (int)cols.size();
+      PA[a].assign((size_t)npA * ma[a], 0.0);
+      for (int i = 0; i < npA; ++i)
+        for (int j = 0; j < ma[a]; ++j) PA[a][(size_t)i * ma[a] + j] = cols[j][i];
+    }
+  });
+  if (fail) { err = "local flux mass matrix not SPD in an eigenproblem"; return false; }
+  T.pblk_off.assign(na + 1, 0);
+  for (int a = 0; a < na; ++a) T.pblk_off[a + 1] = T.pblk_off[a] + (int)PA[a].size();
+  T.Pblk.resize(T.pblk_off[na]);
+  for (int a = 0; a < na; ++a) std::copy(PA[a].begin(), PA[a].end(), T.Pblk.begin() + T.pblk_off[a]);
+  C.n_cells = na;
+  C.m = ma;
+  C.p_off.assign(na + 1, 0);
+  for (int a = 0; a < na; ++a) C.p_off[a + 1] = C.p_off[a] + ma[a];
+  C.ones.assign(C.p_off[na], 0.0);
+  for (int a = 0; a < na; ++a) {
+    int npA = np_of(a), t = 0;
+    for (int k = T.agg_off[a]; k < T.agg_off[a + 1]; ++k) {
+      int c = T.agg_cells[k];
+      for (int r = 0; r < L.m[c]; ++r, ++t)
+        for (int j = 0; j < ma[a]; ++j)
+          C.ones[C.p_off[a] + j] += PA[a][(size_t)t * ma[a] + j] * L.ones[L.p_off[c] + r];
+    }
+    (void)npA;
+  }
+  // ---- coarse interfaces, boundary sets ------------------------------------------------------------------------
+  std::map<std::pair<int, int>, std::vector<int>> pairs;
+  std::vector<std::vector<int>> bd(na);
+  for (int i = 0; i < L.n_flux; ++i) {
+    if (L.fkind[i] == KIND_IFACE) {
+      int a = T.agg_of[L.fown0[i]], b = T.agg_of[L.fown1[i]];
+      if (a != b) pairs[{std::min(a, b), std::max(a, b)}].push_back(i);
+    } else if (L.fkind[i] == KIND_BDRY) {
+      bd[T.agg_of[L.fown0[i]]].push_back(i);
+    }
+  }
+  std::vector<std::pair<int, int>> plist;
+  std::vector<std::vector<int>> Fdofs;
+  for (auto& kv : pairs) {
+    plist.push_back(kv.first);
+    Fdofs.push_back(kv.second);
+    sort_unique(Fdofs.back());
+  }
+  std::vector<int> bagg;
+  for (int a = 0; a < na; ++a)
+    if (!bd[a].empty()) bagg.push_back(a);
+  const int nF = (int)plist.size(), nB = (int)bagg.size();
+  std::vector<int> bub_off(na + 1, 0);
+  for (int a = 0; a < na; ++a) bub_off[a + 1] = bub_off[a] + (ma[a] - 1);
+  const int nC = nF + nB + bub_off[na];
+  // basis functions as sparse columns (level-l flux id, value) and Q_sigma rows
+  std::vector<std::vector<std::pair<int, double>>> psi(nC), qrow(nC);
+  // outflow functional of aggregate a over a set of flux ids: t_i = -(1_a^T D)_i
+  auto outflow_coef = [&](int a, const std::vector<int>& ids, Scratch& sc) {
+    int tok = sc.next();
+    for (int k = 0; k < (int)ids.size(); ++k) { sc.flux_stamp[ids[k]] = tok; sc.flux_pos[ids[k]] = k; }
+    std::vector<double> t(ids.size(), 0.0);
+    for (int k = T.agg_off[a]; k < T.agg_off[a + 1]; ++k) {
+      int c = T.agg_cells[k], nl = L.nloc(c);
+      for (int s = 0; s < nl; ++s) {
+        int i = L.loc[L.loc_off[c] + s];
+        if (sc.flux_stamp[i] != tok) continue;
+        double acc = 0.0;
+        for (int r = 0; r < L.m[c]; ++r) acc += L.ones[L.p_off[c] + r] * L.Dloc[L.dmat_off[c] + (size_t)r * nl + s];
+        t[sc.flux_pos[i]] -= acc;
+      }
+    }
+    return t;
+  };
+  auto finish_trace = [&](int J, int a, const std::vector<int>& U, const std::vector<double>& sig,
+                          const std::vector<int>& Fd, Scratch& sc) {
+    for (size_t k = 0; k < U.size(); ++k) psi[J].push_back({U[k], sig[k]});
+    std::vector<double> t = outflow_coef(a, Fd, sc);
+    // value of the basis function on Fd
+    double tot = 0.0;
+    for (size_t k = 0; k < Fd.size(); ++k) {
+      size_t pos = std::lower_bound(U.begin(), U.end(), Fd[k]) - U.begin();
+      tot += t[k] * sig[pos];
+    }
+    for (size_t k = 0; k < Fd.size(); ++k) qrow[J].push_back({Fd[k], t[k] / tot});
+    return tot != 0.0;
+  };
+  parallel_for(nF, threads, [&](int b, int e, int w) {
+    Scratch& sc = scr[w];
+    for (int J = b; J < e; ++J) {
+      int a = plist[J].first, bb = plist[J].second;
+      std::vector<int> cU = cells_of(a), cb = cells_of(bb);
+      cU.insert(cU.end(), cb.begin(), cb.end());
+      sort_unique(cU);
+      std::vector<int> U = internal_flux(L, cU, sc);
+      LocalProblem lp;
+      assemble_local(L, cU, U, sc, lp);
+      LocalSolver ls;
+      if (!ls.init(lp, true)) { fail = true; continue; }
+      double na2 = 0.0, nb2 = 0.0;
+      for (int c : cells_of(a))
+        for (int r = 0; r < L.m[c]; ++r) na2 += L.ones[L.p_off[c] + r] * L.ones[L.p_off[c] + r];
+      for (int c : cells_of(bb))
+        for (int r = 0; r < L.m[c]; ++r) nb2 += L.ones[L.p_off[c] + r] * L.ones[L.p_off[c] + r];
+      std::vector<double> rp(lp.np);
+      for (size_t k = 0; k < cU.size(); ++k) {
+        int c = cU[k];
+        bool inA = T.agg_of[c] == a;
+        for (int r = 0; r < L.m[c]; ++r)
+          rp[lp.prow[k] + r] = (inA ? -1.0 / na2 : 1.0 / nb2) * L.ones[L.p_off[c] + r];
+      }
+      std::vector<double> sig;
+      ls.solve_p_rhs(rp, sig);
+      if (!finish_trace(J, a, U, sig, Fdofs[J], sc)) fail = true;
+    }
+  });
+  parallel_for(nB, threads, [&](int b, int e, int w) {
+    Scratch& sc = scr[w];
+    for (int k = b; k < e; ++k) {
+      int a = bagg[k], J = nF + k;
+      std::vector<int> cA = cells_of(a);
+      std::vector<int> U = internal_flux(L, cA, sc);
+      std::vector<int> Bd = bd[a];
+      sort_unique(Bd);
+      U.insert(U.end(), Bd.begin(), Bd.end());
+      sort_unique(U);
+      LocalProblem lp;
+      assemble_local(L, cA, U, sc, lp);
+      LocalSolver ls;
+      if (!ls.init(lp, false)) { fail = true; continue; }
+      double n2 = 0.0;
+      for (double x : lp.ones) n2 += x * x;
+      std::vector<double> rp(lp.np);
+      for (int r = 0; r < lp.np; ++r) rp[r] = -lp.ones[r] / n2;
+      std::vector<double> sig;
+      ls.solve_p_rhs(rp, sig);
+      if (!finish_trace(J, a, U, sig, Bd, sc)) fail = true;
+    }
+  });
+  parallel_for(na, threads, [&](int b, int e, int w) {
+    Scratch& sc = scr[w];
+    for (int a = b; a < e; ++a) {
+      if (ma[a] <= 1) continue;
+      std::vector<int> cA = cells_of(a);
+      std::vector<int> U = internal_flux(L, cA, sc);
+      LocalProblem lp;
+      assemble_local(L, cA, U, sc, lp);
+      LocalSolver ls;
+      if (!ls.init(lp, true)) { fail = true; continue; }
+      // (D sigma)|_A coefficients: for every flux id touching A, row r of Dloc scattered to global ids
+      std::vector<int> touch;
+      for (int c : cA) touch.insert(touch.end(), &L.loc[L.loc_off[c]], &L.loc[L.loc_off[c + 1]]);
+      sort_unique(touch);
+      for (int j = 1; j < ma[a]; ++j) {
+        int J = nF + nB + bub_off[a] + (j - 1);
+        std::vector<double> qj(lp.np);
+        for (int r = 0; r < lp.np; ++r) qj[r] = PA[a][(size_t)r * ma[a] + j];
+        std::vector<double> sig;
+        ls.solve_p_rhs(qj, sig);                        // M sigma + D^T p = 0, D sigma = q_j
+        for (size_t k = 0; k < U.size(); ++k) psi[J].push_back({U[k], sig[k]});
+        std::vector<double> row(touch.size(), 0.0);
+        for (size_t k = 0; k < cA.size(); ++k) {
+          int c = cA[k], nl = L.nloc(c);
+          for (int s = 0; s < nl; ++s) {
+            int i = L.loc[L.loc_off[c] + s];
+            size_t pos = std::lower_bound(touch.begin(), touch.end(), i) - touch.begin();
+            double acc = 0.0;
+            for (int r = 0; r < L.m[c]; ++r) acc += qj[lp.prow[k] + r] * L.Dloc[L.dmat_off[c] + (size_t)r * nl + s];
+            row[pos] += acc;
+          }
+        }
+        for (size_t k = 0; k < touch.size(); ++k)
+          if (row[k] != 0.0) qrow[J].push_back({touch[k], row[k]});
+      }
+    }
+  });
+  if (fail) { err = "singular local problem while building the coarse flux space"; return false; }
+  // ---- coarse level description ---------------------------------------------------------------------------------
+  C.n_flux = nC;
+  C.fkind.assign(nC, KIND_BUBBLE);
+  C.fown0.assign(nC, -1);
+  C.fown1.assign(nC, -1);
+  for (int J = 0; J < nF; ++J) { C.fkind[J] = KIND_IFACE; C.fown0[J] = plist[J].first; C.fown1[J] = plist[J].second; }
+  for (int k = 0; k < nB; ++k) { C.fkind[nF + k] = KIND_BDRY; C.fown0[nF + k] = bagg[k]; }
+  for (int a = 0; a < na; ++a)
+    for (int j = 1; j < ma[a]; ++j) C.fown0[nF + nB + bub_off[a] + j - 1] = a;
+  std::vector<std::vector<int>> locs(na);
+  for (int J = 0; J < nC; ++J) {
+    locs[C.fown0[J]].push_back(J);
+    if (C.fown1[J] >= 0) locs[C.fown1[J]].push_back(J);
+  }
+  C.loc_off.assign(na + 1, 0);
+  for (int a = 0; a < na; ++a) {
+    sort_unique(locs[a]);
+    C.loc_off[a + 1] = C.loc_off[a] + (int)locs[a].size();
+    C.loc.insert(C.loc.end(), locs[a].begin(), locs[a].end());
+  }
+  // P_sigma in both orientations and Q_sigma
+  {
+    std::vector<std::vector<std::pair<int, double>>> rowsP(L.n_flux);
+    T.PsT.nrows = nC;
+    T.PsT.ncols = L.n_flux;
+    T.PsT.off.assign(1, 0);
+    for (int J = 0; J < nC; ++J) {
+      auto col = psi[J];
+      std::sort(col.begin(), col.end());
+      for (auto& e : col) {
+        T.PsT.col.push_back(e.first);
+        T.PsT.val.push_back(e.second);
+        rowsP[e.first].push_back({J, e.second});
+      }
+      T.PsT.off.push_back((int)T.PsT.col.size());
+    }
+    T.Ps.nrows = L.n_flux;
+    T.Ps.ncols = nC;
+    T.Ps.off.assign(1, 0);
+    for (int i = 0; i < L.n_flux; ++i) {
+      for (auto& e : rowsP[i]) { T.Ps.col.push_back(e.first); T.Ps.val.push_back(e.second); }
+      T.Ps.off.push_back((int)T.Ps.col.size());
+    }
+    T.Qs.nrows = nC;
+    T.Qs.ncols = L.n_flux;
+    T.Qs.off.assign(1, 0);
+    for (int J = 0; J < nC; ++J) {
+      auto r = qrow[J];
+      std::sort(r.begin(), r.end());
+      for (auto& e : r) { T.Qs.col.push_back(e.first); T.Qs.val.push_back(e.second); }
+      T.Qs.off.push_back((int)T.Qs.col.size());
+    }
+  }
+  // static local matrices, divergence blocks, Pi~ weights
+  C.mat_off.assign(na + 1, 0);
+  C.dmat_off.assign(na + 1, 0);
+  for (int a = 0; a < na; ++a) {
+    int nl = C.loc_off[a + 1] - C.loc_off[a];
+    C.mat_off[a + 1] = C.mat_off[a] + nl * nl;
+    C.dmat_off[a + 1] = C.dmat_off[a] + ma[a] * nl;
+  }
+  C.Mloc.assign(C.mat_off[na], 0.0);
+  C.Dloc.assign(C.dmat_off[na], 0.0);
+  C.w.assign(C.p_off[na], 0.0);
+  C.vol.assign(na, 0.0);
+  parallel_for(na, threads, [&](int b, int e, int) {
+    for (int a = b; a < e; ++a) {
+      int nl = C.loc_off[a + 1] - C.loc_off[a];
+      const int* la = &C.loc[C.loc_off[a]];
+      double vol = 0.0;
+      for (int k = T.agg_off[a]; k < T.agg_off[a + 1]; ++k) vol += L.vol[T.agg_cells[k]];
+      C.vol[a] = vol;
+      int t = 0;  // running row of P_a
+      for (int k = T.agg_off[a]; k < T.agg_off[a + 1]; ++k) {
+        int c = T.agg_cells[k], nlc = L.nloc(c), mc = L.m[c];
+        const int* lc = &L.loc[L.loc_off[c]];
+        // Pc = P_sigma[loc_c, loc_a] (nlc x nl)
+        std::vector<double> Pc((size_t)nlc * nl, 0.0);
+        for (int s = 0; s < nlc; ++s) {
+          int i = lc[s];
+          for (int q = T.Ps.off[i]; q < T.Ps.off[i + 1]; ++q) {
+            const int* pos = std::lower_bound(la, la + nl, T.Ps.col[q]);
+            if (pos != la + nl && *pos == T.Ps.col[q]) Pc[(size_t)s * nl + (pos - la)] += T.Ps.val[q];
+          }
+        }
+        const double* Mc = &L.Mloc[L.mat_off[c]];
+        std::vector<double> MP((size_t)nlc * nl, 0.0);
+        for (int s = 0; s < nlc; ++s)
+          for (int u = 0; u < nlc; ++u) {
+            double mv = Mc[(size_t)s * nlc + u];
+            if (mv == 0.0) continue;
+            for (int j = 0; j < nl; ++j) MP[(size_t)s * nl + j] += mv * Pc[(size_t)u * nl + j];
+          }
+        for (int s = 0; s < nlc; ++s)
+          for (int i = 0; i < nl; ++i) {
+            double ps = Pc[(size_t)s * nl + i];
+            if (ps == 0.0) continue;
+            for (int j = 0; j < nl; ++j) C.Mloc[C.mat_off[a] + (size_t)i * nl + j] += ps * MP[(size_t)s * nl + j];
+          }
+        // Dloc_a += P_a[rows_c]^T Dloc_c Pc
+        const double* Dc = &L.Dloc[L.dmat_off[c]];
+        std::vector<double> DP((size_t)mc * nl, 0.0);
+        for (int r = 0; r < mc; ++r)
+          for (int s = 0; s < nlc; ++s) {
+            double dv = Dc[(size_t)r * nlc + s];
+            if (dv == 0.0) continue;
+            for (int j = 0; j < nl; ++j) DP[(size_t)r * nl + j] += dv * Pc[(size_t)s * nl + j];
+          }
+        for (int r = 0; r < mc; ++r) {
+          const double* Prow = &T.Pblk[T.pblk_off[a] + (size_t)(t + r) * ma[a]];
+          for (int i = 0; i < ma[a]; ++i)
+            for (int j = 0; j < nl; ++j) C.Dloc[C.dmat_off[a] + (size_t)i * nl + j] += Prow[i] * DP[(size_t)r * nl + j];
+          double wcr = L.w[L.p_off[c] + r] * L.vol[c];
+          for (int i = 0; i < ma[a]; ++i) C.w[C.p_off[a] + i] += wcr * Prow[i];
+        }
+        t += mc;
+      }
+      for (int i = 0; i < ma[a]; ++i) C.w[C.p_off[a] + i] /= vol;
+    }
+  });
+  return true;
+}
+
+bool build_hierarchy(const FineMesh& fm, const Options& opt, Hierarchy& H, std::string& err) {
+  int threads = opt.threads > 0 ? opt.threads : (int)std::max(1u, std::thread::hardware_concurrency());
+  H.levels.clear();
+  H.transfers.clear();
+  H.levels.push_back(make_level0(fm));
+  for (int l = 0; l + 1 < opt.n_levels; ++l) {
+    Level C;
+    Transfer T;
+    if (!coarsen(H.levels.back(), opt.agg_size[l], opt.modes[l], threads, C, T, err)) return false;
+    H.levels.push_back(std::move(C));
+    H.transfers.push_back(std::move(T));
+  }
+  return true;
+}
+
+}  // namespace nlmg

@@ -1,0 +1,1143 @@
+// nlmg: context, device upload of the hierarchy, FAS cycle (Algorithm 2), backtracking (Algorithm 1), Picard
+// smoothing steps, and the C ABI of include/nlmg.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/nlmg.h"
+#include "dense.hpp"
+#include "hier.hpp"
+#include "kernels.cuh"
+
+using namespace nlmg;
+
+namespace {
+
+struct Error : std::runtime_error {
+  nlmg_status code;
+  Error(nlmg_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define CK(call)                                                                                         \
+  do {                                                                                                   \
+    cudaError_t e_ = (call);                                                                             \
+    if (e_ != cudaSuccess)                                                                               \
+      throw Error(e_ == cudaErrorMemoryAllocation ? NLMG_ENOMEM : NLMG_ECUDA,                            \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                                   \
+  } while (0)
+
+// Per coarse level work buffers.
+struct CoarseBuf {
+  double *x = nullptr, *b = nullptr, *r = nullptr, *dx = nullptr, *nb = nullptr, *xt1 = nullptr, *xt2 = nullptr;
+  double *xc = nullptr, *yl = nullptr, *kapc = nullptr, *ptmp = nullptr;
+  double *ylam = nullptr, *lam = nullptr, *lr = nullptr, *lz = nullptr, *lpa = nullptr, *lpb = nullptr,
+         *lq = nullptr, *ldinv = nullptr, *xi = nullptr;
+  double rn = 0.0;  // ||A(x) - b|| at the current x (valid after coarse_res)
+};
+
+// Optional CUDA-event timing of selected kernels on the context stream (pairs of events around each launch).
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kid;
+  int used = 0;
+  double ms[8] = {0};
+  long long n[8] = {0};
+};
+
+// Fine-level state: iterate, its kappa and residual.
+struct FineState {
+  double *p = nullptr, *kap = nullptr, *R = nullptr;
+  double rn = 0.0;
+};
+
+}  // namespace
+
+struct nlmg_ctx {
+  std::string err;
+  nlmg_options opt{};
+  int kind = 0;
+  double a = 0.0;
+  FineMesh fm;
+  Hierarchy H;
+  cudaStream_t st = nullptr;
+  std::vector<void*> allocs;
+  FineDev F;
+  std::vector<LevelDev> LD;
+  std::vector<TransferDev> TD;
+  std::vector<CoarseBuf> CB;
+  double* d_partial = nullptr;
+  unsigned* d_cnt = nullptr;
+  double* d_sc = nullptr;
+  double* h_sc = nullptr;   // pinned
+  // fine buffers
+  double *f = nullptr, *g = nullptr, *rhs = nullptr, *dkap = nullptr, *Tval = nullptr, *dinv = nullptr,
+         *diagT = nullptr, *jdiag = nullptr, *sig0 = nullptr, *ptr_e = nullptr, *fdp = nullptr;
+  double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cpa = nullptr, *cpb = nullptr, *cq = nullptr;
+  FineState cur, t1, t2;
+  bool have_data = false;
+  double tol_rel = 1e-8, tol_abs = 1e-10;   // outer tolerances, also used on the coarsest level
+  // statistics of the running solve
+  long long fine_evals = 0, lin_iters = 0;
+  Prof prof;
+  int prof_begin(int k) {
+    if (!prof.on) return -1;
+    if (prof.used * 2 + 2 > (int)prof.ev.size()) prof_flush();
+    int i = prof.used++;
+    prof.kid[i] = k;
+    CK(cudaEventRecord(prof.ev[2 * i], st));
+    return i;
+  }
+  void prof_end(int i) {
+    if (i >= 0) CK(cudaEventRecord(prof.ev[2 * i + 1], st));
+  }
+  void prof_flush() {
+    if (prof.used == 0) return;
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < prof.used; ++i) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, prof.ev[2 * i], prof.ev[2 * i + 1]));
+      prof.ms[prof.kid[i]] += ms;
+      prof.n[prof.kid[i]] += 1;
+    }
+    prof.used = 0;
+  }
+
+  template <class T>
+  T* dalloc(size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    CK(cudaMalloc(&p, n * sizeof(T)));
+    allocs.push_back(p);
+    return (T*)p;
+  }
+  template <class T>
+  T* upload(const std::vector<T>& v) {
+    T* p = dalloc<T>(v.size());
+    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return p;
+  }
+  Reduce red(int slot) { return Reduce{d_partial, d_cnt, d_sc + slot}; }
+  double read_sc(int slot) {
+    CK(cudaMemcpyAsync(h_sc, d_sc + slot, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return *h_sc;
+  }
+  void read_sc2(int s0, double& v0, double& v1) {  // two consecutive slots
+    CK(cudaMemcpyAsync(h_sc, d_sc + s0, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    v0 = h_sc[0];
+    v1 = h_sc[1];
+  }
+  int nlev() const { return (int)H.levels.size(); }
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------------------------
+// upload
+
+void upload_fine(nlmg_ctx* c) {
+  const FineMesh& fm = c->fm;
+  const int N = fm.n_cells;
+  std::vector<std::vector<int>> rows(N);
+  std::vector<int> off(N + 1, 0), nbr, doff(N + 1, 0), dface, noff(N + 1, 0), nface;
+  std::vector<double> us, un, dups, narea;
+  std::vector<std::vector<int>> dl(N), nl(N);
+  for (int f = 0; f < fm.n_faces; ++f) {
+    if (fm.bc[f] == 0) {
+      rows[fm.fk[f]].push_back(f);
+      rows[fm.fl[f]].push_back(f);
+    } else if (fm.bc[f] == 1) {
+      dl[fm.fk[f]].push_back(f);
+    } else {
+      nl[fm.fk[f]].push_back(f);
+    }
+  }
+  for (int K = 0; K < N; ++K) {
+    for (int f : rows[K]) {
+      bool own = fm.fk[f] == K;
+      nbr.push_back(own ? fm.fl[f] : fm.fk[f]);
+      us.push_back(own ? fm.ups0[f] : fm.ups1[f]);
+      un.push_back(own ? fm.ups1[f] : fm.ups0[f]);
+    }
+    off[K + 1] = (int)nbr.size();
+    for (int f : dl[K]) { dface.push_back(f); dups.push_back(fm.ups0[f]); }
+    doff[K + 1] = (int)dface.size();
+    for (int f : nl[K]) { nface.push_back(f); narea.push_back(fm.area[f]); }
+    noff[K + 1] = (int)nface.size();
+  }
+  FineDev& F = c->F;
+  F.N = N;
+  F.nnz = (int)nbr.size();
+  F.row_off = c->upload(off);
+  F.nbr = c->upload(nbr);
+  F.ups_s = c->upload(us);
+  F.ups_n = c->upload(un);
+  F.dir_off = c->upload(doff);
+  F.dir_face = c->upload(dface);
+  F.dir_ups = c->upload(dups);
+  F.neu_off = c->upload(noff);
+  F.neu_face = c->upload(nface);
+  F.neu_area = c->upload(narea);
+  F.vol = c->upload(fm.vol);
+  const Level& L0 = c->H.levels[0];
+  std::vector<int> flk, fll, flf;
+  std::vector<double> u0, u1;
+  for (int j = 0; j < L0.n_flux; ++j) {
+    int f = L0.face_of_flux[j];
+    flk.push_back(fm.fk[f]);
+    fll.push_back(fm.bc[f] == 0 ? fm.fl[f] : -1);
+    flf.push_back(f);
+    u0.push_back(fm.ups0[f]);
+    u1.push_back(fm.bc[f] == 0 ? fm.ups1[f] : 0.0);
+  }
+  F.nflux = L0.n_flux;
+  F.fl_k = c->upload(flk);
+  F.fl_l = c->upload(fll);
+  F.fl_face = c->upload(flf);
+  F.fl_u0 = c->upload(u0);
+  F.fl_u1 = c->upload(u1);
+}
+
+void upload_level(nlmg_ctx* c, int l) {
+  const Level& L = c->H.levels[l];
+  LevelDev& D = c->LD[l];
+  D.nc = L.n_cells;
+  D.nflux = L.n_flux;
+  D.np = L.n_p();
+  D.nyl = (int)L.loc.size();
+  for (int cc = 0; cc < L.n_cells; ++cc) {
+    if (L.nloc(cc) > kMaxLoc) throw Error(NLMG_EUNSUPPORTED, "a coarse cell has more than 64 flux unknowns");
+    if (L.m[cc] > kMaxM) throw Error(NLMG_EUNSUPPORTED, "more than 8 modes per aggregate");
+  }
+  D.m = c->upload(L.m);
+  D.p_off = c->upload(L.p_off);
+  D.loc_off = c->upload(L.loc_off);
+  D.loc = c->upload(L.loc);
+  D.mat_off = c->upload(L.mat_off);
+  D.dmat_off = c->upload(L.dmat_off);
+  D.Mloc = c->upload(L.Mloc);
+  D.Dloc = c->upload(L.Dloc);
+  D.w = c->upload(L.w);
+  std::vector<int> fy0(L.n_flux, -1), fy1(L.n_flux, -1), own0(L.loc.size(), 0);
+  for (int cc = 0; cc < L.n_cells; ++cc)
+    for (int k = L.loc_off[cc]; k < L.loc_off[cc + 1]; ++k) {
+      int i = L.loc[k];
+      if (L.fown0[i] == cc) { fy0[i] = k; own0[k] = 1; } else { fy1[i] = k; }
+    }
+  D.f_y0 = c->upload(fy0);
+  D.f_y1 = c->upload(fy1);
+  D.own0 = c->upload(own0);
+  // hybridization data
+  std::vector<int> lam_of(L.n_flux, -1);
+  int nlam = 0;
+  for (int i = 0; i < L.n_flux; ++i)
+    if (L.fkind[i] == KIND_IFACE) lam_of[i] = nlam++;
+  D.nlam = nlam;
+  std::vector<int> sad_off(L.n_cells + 1, 0), if_off(L.n_cells + 1, 0), if_slot, if_lam, hc_off(L.n_cells + 1, 0);
+  std::vector<double> Sinv, if_sign, Hc;
+  std::vector<int> ly0(nlam, -1), ly1(nlam, -1);
+  for (int cc = 0; cc < L.n_cells; ++cc) {
+    int nl = L.nloc(cc), mc = L.m[cc], n = nl + mc;
+    std::vector<double> K((size_t)n * n, 0.0), Ki((size_t)n * n, 0.0);
+    for (int s = 0; s < nl; ++s)
+      for (int t = 0; t < nl; ++t) K[(size_t)s * n + t] = L.Mloc[L.mat_off[cc] + (size_t)s * nl + t];
+    for (int r = 0; r < mc; ++r)
+      for (int s = 0; s < nl; ++s) {
+        double d = L.Dloc[L.dmat_off[cc] + (size_t)r * nl + s];
+        K[(size_t)(nl + r) * n + s] = d;
+        K[(size_t)s * n + nl + r] = d;
+      }
+    if (!invert(n, K.data(), Ki.data())) throw Error(NLMG_EINVAL, "singular local saddle on a coarse cell");
+    sad_off[cc + 1] = sad_off[cc] + n * n;
+    Sinv.insert(Sinv.end(), Ki.begin(), Ki.end());
+    std::vector<int> slots;
+    for (int s = 0; s < nl; ++s) {
+      int i = L.loc[L.loc_off[cc] + s];
+      if (lam_of[i] < 0) continue;
+      int k = (int)if_slot.size();
+      slots.push_back(s);
+      if_slot.push_back(s);
+      if_lam.push_back(lam_of[i]);
+      bool first = L.fown0[i] == cc;
+      if_sign.push_back(first ? 1.0 : -1.0);
+      (first ? ly0 : ly1)[lam_of[i]] = k;
+    }
+    if_off[cc + 1] = (int)if_slot.size();
+    int ni = (int)slots.size();
+    hc_off[cc + 1] = hc_off[cc] + ni * ni;
+    for (int k = 0; k < ni; ++k)
+      for (int j = 0; j < ni; ++j)
+        Hc.push_back(if_sign[if_off[cc] + k] * if_sign[if_off[cc] + j] * Ki[(size_t)slots[k] * n + slots[j]]);
+  }
+  D.nif = (int)if_slot.size();
+  D.sad_off = c->upload(sad_off);
+  D.Sinv = c->upload(Sinv);
+  D.if_off = c->upload(if_off);
+  D.if_slot = c->upload(if_slot);
+  D.if_lam = c->upload(if_lam);
+  D.if_sign = c->upload(if_sign);
+  D.hc_off = c->upload(hc_off);
+  D.Hc = c->upload(Hc);
+  D.lam_y0 = c->upload(ly0);
+  D.lam_y1 = c->upload(ly1);
+  CoarseBuf& B = c->CB[l];
+  int nx = D.nflux + D.np;
+  B.x = c->dalloc<double>(nx);
+  B.b = c->dalloc<double>(nx);
+  B.r = c->dalloc<double>(nx);
+  B.dx = c->dalloc<double>(nx);
+  B.nb = c->dalloc<double>(nx);
+  B.xt1 = c->dalloc<double>(nx);
+  B.xt2 = c->dalloc<double>(nx);
+  B.xc = c->dalloc<double>(nx);
+  B.yl = c->dalloc<double>(D.nyl);
+  B.kapc = c->dalloc<double>(D.nc);
+  B.ptmp = c->dalloc<double>(nx);
+  B.ylam = c->dalloc<double>(D.nif);
+  B.lam = c->dalloc<double>(nlam);
+  B.lr = c->dalloc<double>(nlam);
+  B.lz = c->dalloc<double>(nlam);
+  B.lpa = c->dalloc<double>(nlam);
+  B.lpb = c->dalloc<double>(nlam);
+  B.lq = c->dalloc<double>(nlam);
+  B.ldinv = c->dalloc<double>(nlam);
+  B.xi = c->dalloc<double>(nlam);
+}
+
+void upload_transfer(nlmg_ctx* c, int l) {
+  const Level& L = c->H.levels[l];
+  const Level& C = c->H.levels[l + 1];
+  const Transfer& T = c->H.transfers[l];
+  TransferDev& D = c->TD[l];
+  D.na = C.n_cells;
+  D.nrows = L.n_p();
+  std::vector<int> roff(D.na + 1, 0), rows, pd_agg(D.nrows), pd_row(D.nrows);
+  for (int a = 0; a < D.na; ++a) {
+    int t = 0;
+    for (int k = T.agg_off[a]; k < T.agg_off[a + 1]; ++k) {
+      int cc = T.agg_cells[k];
+      for (int r = 0; r < L.m[cc]; ++r, ++t) {
+        int i = L.p_off[cc] + r;
+        rows.push_back(i);
+        pd_agg[i] = a;
+        pd_row[i] = t;
+      }
+    }
+    roff[a + 1] = (int)rows.size();
+  }
+  D.rows_off = c->upload(roff);
+  D.rows = c->upload(rows);
+  D.pblk_off = c->upload(T.pblk_off);
+  D.Pblk = c->upload(T.Pblk);
+  D.mc = c->upload(C.m);
+  D.pc_off = c->upload(C.p_off);
+  D.pd_agg = c->upload(pd_agg);
+  D.pd_row = c->upload(pd_row);
+  D.ps_n = T.Ps.nrows;
+  D.ps_off = c->upload(T.Ps.off);
+  D.ps_col = c->upload(T.Ps.col);
+  D.ps_val = c->upload(T.Ps.val);
+  D.pst_n = T.PsT.nrows;
+  D.pst_off = c->upload(T.PsT.off);
+  D.pst_col = c->upload(T.PsT.col);
+  D.pst_val = c->upload(T.PsT.val);
+  D.qs_n = T.Qs.nrows;
+  D.qs_off = c->upload(T.Qs.off);
+  D.qs_col = c->upload(T.Qs.col);
+  D.qs_val = c->upload(T.Qs.val);
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// level 0
+
+double fine_eval(nlmg_ctx* c, const double* p, const double* dp, double s, FineState& out) {
+  launch_kappa(c->st, c->F.N, p, dp, s, out.p, out.kap, nullptr, c->kind, c->a);
+  int pi = c->prof_begin(2);
+  launch_residual(c->st, c->F, out.p, out.kap, nullptr, c->g, c->rhs, out.R, nullptr, nullptr, nullptr, nullptr,
+                  c->red(S_NORM2));
+  c->prof_end(pi);
+  c->fine_evals++;
+  out.rn = std::sqrt(c->read_sc(S_NORM2));
+  return out.rn;
+}
+
+// Algorithm 1 on level 0 from c->cur along dp (scaled by s0); the accepted trial becomes c->cur.
+void backtrack0(nlmg_ctx* c, const double* dp, double s0) {
+  const nlmg_options& o = c->opt;
+  double s = 1.0;
+  int n = 0;
+  double r_s = fine_eval(c, c->cur.p, dp, s * s0, c->t1);
+  while (r_s > c->cur.rn && n < o.bt_nmax) {
+    double r_half = fine_eval(c, c->cur.p, dp, 0.5 * s * s0, c->t2);
+    if (r_half > o.bt_theta * r_s) break;
+    s *= 0.5;
+    ++n;
+    r_s = r_half;
+    std::swap(c->t1, c->t2);
+  }
+  std::swap(c->cur, c->t1);
+}
+
+// PCG on the frozen fine matrix (Tval, diagT, dinv): A dx = -R ; result in c->cx. Returns iterations.
+int fine_pcg(nlmg_ctx* c, const double* R) {
+  const int N = c->F.N;
+  launch_pcg_init(c->st, N, R, -1.0, c->dinv, c->cx, c->cr, c->cz, c->d_sc, c->red(S_SCRATCH));
+  double rr0 = c->read_sc(S_RR0);
+  if (!(rr0 > 0.0)) return 0;
+  const double tol2 = c->opt.lin_tol * c->opt.lin_tol * rr0;
+  double* pa = c->cpa;
+  double* pb = c->cpb;
+  int it = 0;
+  for (; it < c->opt.lin_maxit;) {
+    int pi = c->prof_begin(0);
+    launch_fine_spmv(c->st, c->F, c->Tval, c->diagT, c->cz, pa, pb, c->cq, c->d_sc, it == 0, c->red(S_SCRATCH));
+    c->prof_end(pi);
+    pi = c->prof_begin(1);
+    launch_pcg_update(c->st, N, c->cx, c->cr, c->cz, pb, c->cq, c->dinv, c->d_sc, c->red(S_SCRATCH));
+    c->prof_end(pi);
+    std::swap(pa, pb);
+    ++it;
+    if (it % 8 == 0 || it == c->opt.lin_maxit) {
+      double rr = c->read_sc(S_RR);
+      if (!(rr > tol2)) break;
+    }
+  }
+  c->lin_iters += it;
+  return it;
+}
+
+// One smoothing step on level 0 (Picard or nonlinear Jacobi), then the clamp and Algorithm 1.
+void smooth0(nlmg_ctx* c, int nu) {
+  const nlmg_options& o = c->opt;
+  const int N = c->F.N;
+  const double* dp = nullptr;
+  if (o.smoother == NLMG_SMOOTH_PICARD) {
+    launch_residual(c->st, c->F, c->cur.p, c->cur.kap, nullptr, c->g, c->rhs, c->t2.R, c->Tval, c->dinv, c->diagT,
+                    nullptr, c->red(S_NORM2B));
+    fine_pcg(c, c->cur.R);
+    dp = c->cx;
+  } else {
+    // nu sweeps q <- q - omega R(q) / max(J_qq, d_q / 2) from q = p, then dp = q - p
+    double* q = c->cpa;
+    double* qn = c->cpb;
+    CK(cudaMemcpyAsync(q, c->cur.p, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    for (int k = 0; k < nu; ++k) {
+      launch_kappa(c->st, N, q, nullptr, 0.0, q, c->t2.kap, c->dkap, c->kind, c->a);
+      launch_residual(c->st, c->F, q, c->t2.kap, c->dkap, c->g, c->rhs, c->t2.R, nullptr, nullptr, c->diagT,
+                      c->jdiag, c->red(S_NORM2B));
+      launch_jacobi_update(c->st, N, q, c->t2.R, c->jdiag, c->diagT, o.omega, qn);
+      std::swap(q, qn);
+      c->fine_evals++;
+    }
+    launch_sub(c->st, N, q, c->cur.p, c->cx);
+    dp = c->cx;
+  }
+  double s0 = 1.0;
+  if (o.dp_clamp > 0) {
+    launch_max_abs(c->st, N, dp, c->red(S_MAX));
+    double mx = c->read_sc(S_MAX);
+    if (mx > o.dp_clamp) s0 = o.dp_clamp / mx;
+  }
+  backtrack0(c, dp, s0);
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// coarse levels
+
+// r = A^l(x) - b (b may be null), kapc; returns ||r||.
+double coarse_res(nlmg_ctx* c, int l, const double* x, const double* b, double* r) {
+  const LevelDev& L = c->LD[l];
+  CoarseBuf& B = c->CB[l];
+  launch_coarse_cell(c->st, L, x, x + L.nflux, b ? b + L.nflux : nullptr, B.yl, r + L.nflux, B.kapc, c->kind, c->a,
+                     c->red(S_NORM2));
+  launch_coarse_flux(c->st, L, B.yl, b, r, c->red(S_NORM2B));
+  double v0, v1;
+  c->read_sc2(S_NORM2, v0, v1);
+  return std::sqrt(v0 + v1);
+}
+
+void backtrack_coarse(nlmg_ctx* c, int l, const double* dx, double s0) {
+  const nlmg_options& o = c->opt;
+  const LevelDev& L = c->LD[l];
+  CoarseBuf& B = c->CB[l];
+  const int nx = L.nflux + L.np;
+  double s = 1.0;
+  int n = 0;
+  launch_axpy(c->st, nx, B.x, s * s0, dx, B.xt1);
+  double r_s = coarse_res(c, l, B.xt1, B.b, B.ptmp);
+  while (r_s > B.rn && n < o.bt_nmax) {
+    launch_axpy(c->st, nx, B.x, 0.5 * s * s0, dx, B.xt2);
+    double r_half = coarse_res(c, l, B.xt2, B.b, B.ptmp);
+    if (r_half > o.bt_theta * r_s) break;
+    s *= 0.5;
+    ++n;
+    r_s = r_half;
+    std::swap(B.xt1, B.xt2);
+  }
+  std::swap(B.x, B.xt1);
+  B.rn = r_s;
+}
+
+// Solve the frozen-coefficient saddle A_frozen(x) dx = -r (r, kapc current) by hybridization + PCG -> B.dx.
+int coarse_linear(nlmg_ctx* c, int l) {
+  const LevelDev& L = c->LD[l];
+  CoarseBuf& B = c->CB[l];
+  const int nx = L.nflux + L.np;
+  launch_axpy(c->st, nx, B.r, -2.0, B.r, B.nb);   // nb = -r
+  const double* bs = B.nb;
+  const double* bp = B.nb + L.nflux;
+  int it = 0;
+  if (L.nlam > 0) {
+    launch_hyb_diag(c->st, L, B.kapc, B.ylam, B.ldinv);
+    launch_hyb_rhs(c->st, L, B.kapc, bs, bp, B.ylam, B.xi);
+    launch_pcg_init(c->st, L.nlam, B.xi, 1.0, B.ldinv, B.lam, B.lr, B.lz, c->d_sc, c->red(S_SCRATCH));
+    double rr0 = c->read_sc(S_RR0);
+    if (rr0 > 0.0) {
+      const double tol2 = c->opt.lin_tol * c->opt.lin_tol * rr0;
+      double* pa = B.lpa;
+      double* pb = B.lpb;
+      for (; it < c->opt.lin_maxit;) {
+        launch_hyb_spmv(c->st, L, B.kapc, B.lz, pa, pb, B.lq, B.ylam, c->d_sc, it == 0, c->red(S_SCRATCH));
+        launch_pcg_update(c->st, L.nlam, B.lam, B.lr, B.lz, pb, B.lq, B.ldinv, c->d_sc, c->red(S_SCRATCH));
+        std::swap(pa, pb);
+        ++it;
+        if (it % 8 == 0 || it == c->opt.lin_maxit) {
+          double rr = c->read_sc(S_RR);
+          if (!(rr > tol2)) break;
+        }
+      }
+    }
+  }
+  launch_hyb_recover(c->st, L, B.kapc, bs, bp, B.lam, B.dx, B.dx + L.nflux);
+  c->lin_iters += it;
+  return it;
+}
+
+// One Picard smoothing step on coarse level l (Sec. 3.3.1) + clamp on Pi~ dp + Algorithm 1.
+void picard_coarse(nlmg_ctx* c, int l) {
+  const LevelDev& L = c->LD[l];
+  CoarseBuf& B = c->CB[l];
+  B.rn = coarse_res(c, l, B.x, B.b, B.r);
+  coarse_linear(c, l);
+  double s0 = 1.0;
+  if (c->opt.dp_clamp > 0) {
+    launch_coarse_pbar_max(c->st, L, B.dx + L.nflux, c->red(S_MAX));
+    double mx = c->read_sc(S_MAX);
+    if (mx > c->opt.dp_clamp) s0 = c->opt.dp_clamp / mx;
+  }
+  backtrack_coarse(c, l, B.dx, s0);
+}
+
+// x_{l+1} = Q x_l, b_{l+1} = A_{l+1}(x_{l+1}) - P^T r_l (r_l = [r_sigma; r_p] of level l >= 1 in CB[l].r)
+void make_coarse_problem(nlmg_ctx* c, int l) {
+  const TransferDev& T = c->TD[l];
+  const LevelDev& C = c->LD[l + 1];
+  CoarseBuf& Bc = c->CB[l + 1];
+  if (l == 0) {
+    launch_kappa(c->st, c->F.N, c->cur.p, nullptr, 0.0, c->cur.p, c->cur.kap, nullptr, c->kind, c->a);
+    launch_fine_flux(c->st, c->F, c->cur.p, c->cur.kap, c->g, c->sig0);
+    launch_csr(c->st, T.qs_n, T.qs_off, T.qs_col, T.qs_val, c->sig0, Bc.x, 1.0, 0.0);
+    // projection of p and restriction of the mixed pressure residual -R
+    launch_restrict_p(c->st, T, c->cur.p, Bc.x + C.nflux, 1.0, c->cur.R, Bc.ptmp + C.nflux);
+    coarse_res(c, l + 1, Bc.x, nullptr, Bc.b);
+    // b_p += P^T R   (R r^0 = [0; P^T (-R)])
+    launch_axpy(c->st, C.np, Bc.b + C.nflux, 1.0, Bc.ptmp + C.nflux, Bc.b + C.nflux);
+  } else {
+    const LevelDev& L = c->LD[l];
+    CoarseBuf& B = c->CB[l];
+    launch_csr(c->st, T.qs_n, T.qs_off, T.qs_col, T.qs_val, B.x, Bc.x, 1.0, 0.0);
+    launch_restrict_p(c->st, T, B.x + L.nflux, Bc.x + C.nflux, 1.0, B.r + L.nflux, Bc.ptmp + C.nflux);
+    coarse_res(c, l + 1, Bc.x, nullptr, Bc.b);
+    launch_csr(c->st, T.pst_n, T.pst_off, T.pst_col, T.pst_val, B.r, Bc.b, -1.0, 1.0);
+    launch_axpy(c->st, C.np, Bc.b + C.nflux, -1.0, Bc.ptmp + C.nflux, Bc.b + C.nflux);
+  }
+  CK(cudaMemcpyAsync(Bc.xc, Bc.x, (size_t)(C.nflux + C.np) * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+}
+
+void coarse_cycle(nlmg_ctx* c, int l) {
+  const nlmg_options& o = c->opt;
+  CoarseBuf& B = c->CB[l];
+  const LevelDev& L = c->LD[l];
+  if (l == c->nlev() - 1) {
+    B.rn = coarse_res(c, l, B.x, B.b, B.r);
+    const double r0 = B.rn;
+    for (int k = 0; k < o.coarsest_steps; ++k) {
+      if (B.rn <= c->tol_rel * r0 || B.rn <= c->tol_abs) break;
+      picard_coarse(c, l);
+    }
+    return;
+  }
+  picard_coarse(c, l);
+  B.rn = coarse_res(c, l, B.x, B.b, B.r);
+  make_coarse_problem(c, l);
+  coarse_cycle(c, l + 1);
+  const LevelDev& C = c->LD[l + 1];
+  CoarseBuf& Bc = c->CB[l + 1];
+  const TransferDev& T = c->TD[l];
+  launch_sub(c->st, C.nflux + C.np, Bc.x, Bc.xc, Bc.ptmp);
+  launch_csr(c->st, T.ps_n, T.ps_off, T.ps_col, T.ps_val, Bc.ptmp, B.dx, 1.0, 0.0);
+  launch_prolong_p(c->st, T, Bc.ptmp + C.nflux, B.dx + L.nflux);
+  backtrack_coarse(c, l, B.dx, 1.0);
+  picard_coarse(c, l);
+}
+
+// One FAS cycle from level 0 (Algorithm 2). Returns true if it stopped after pre-smoothing.
+bool vcycle(nlmg_ctx* c, double r0, double tol_rel, double tol_abs) {
+  const nlmg_options& o = c->opt;
+  smooth0(c, o.nu_pre);
+  if (c->cur.rn <= tol_rel * r0 || c->cur.rn <= tol_abs) return true;
+  if (c->nlev() > 1) {
+    make_coarse_problem(c, 0);
+    coarse_cycle(c, 1);
+    const LevelDev& C = c->LD[1];
+    CoarseBuf& Bc = c->CB[1];
+    launch_sub(c->st, C.nflux + C.np, Bc.x, Bc.xc, Bc.ptmp);
+    launch_prolong_p(c->st, c->TD[0], Bc.ptmp + C.nflux, c->fdp);
+    backtrack0(c, c->fdp, 1.0);
+  }
+  smooth0(c, o.nu_post);
+  return false;
+}
+
+void alloc_fine(nlmg_ctx* c) {
+  const int N = c->F.N;
+  c->f = c->dalloc<double>(N);
+  c->g = c->dalloc<double>(c->fm.n_faces);
+  c->rhs = c->dalloc<double>(N);
+  c->dkap = c->dalloc<double>(N);
+  c->Tval = c->dalloc<double>(c->F.nnz);
+  c->dinv = c->dalloc<double>(N);
+  c->diagT = c->dalloc<double>(N);
+  c->jdiag = c->dalloc<double>(N);
+  c->sig0 = c->dalloc<double>(c->F.nflux);
+  c->fdp = c->dalloc<double>(N);
+  c->cx = c->dalloc<double>(N);
+  c->cr = c->dalloc<double>(N);
+  c->cz = c->dalloc<double>(N);
+  c->cpa = c->dalloc<double>(N);
+  c->cpb = c->dalloc<double>(N);
+  c->cq = c->dalloc<double>(N);
+  for (FineState* s : {&c->cur, &c->t1, &c->t2}) {
+    s->p = c->dalloc<double>(N);
+    s->kap = c->dalloc<double>(N);
+    s->R = c->dalloc<double>(N);
+  }
+}
+
+nlmg_status fail(nlmg_ctx* c, nlmg_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+template <class F>
+nlmg_status guarded(nlmg_ctx* c, F&& fn) {
+  if (!c) return NLMG_EINVAL;
+  try {
+    return fn();
+  } catch (const Error& e) {
+    return fail(c, e.code, e.what());
+  } catch (const std::exception& e) {
+    return fail(c, NLMG_EINVAL, e.what());
+  }
+}
+
+void set_data_dev(nlmg_ctx* c, const double* f_dev, const double* g_dev) {
+  if (f_dev != c->f)
+    CK(cudaMemcpyAsync(c->f, f_dev, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  if (g_dev != c->g)
+    CK(cudaMemcpyAsync(c->g, g_dev, (size_t)c->fm.n_faces * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  launch_rhs(c->st, c->F, c->f, c->g, c->rhs);
+  c->have_data = true;
+}
+
+void set_data_host(nlmg_ctx* c, const double* f, const double* g) {
+  CK(cudaMemcpyAsync(c->f, f, (size_t)c->F.N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->g, g, (size_t)c->fm.n_faces * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  set_data_dev(c, c->f, c->g);
+}
+
+// Full solve on device data already set; x0 device pointer or null. Returns status.
+nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double tol_abs, int max_cycles,
+                       double* p_dev, nlmg_report* rep, bool picard_only) {
+  const int N = c->F.N;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, c->st));
+  c->fine_evals = 0;
+  c->lin_iters = 0;
+  const long long launches0 = launch_count();
+  c->tol_rel = tol_rel;
+  c->tol_abs = tol_abs;
+  if (x0_dev)
+    CK(cudaMemcpyAsync(c->cur.p, x0_dev, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  else
+    CK(cudaMemsetAsync(c->cur.p, 0, (size_t)N * sizeof(double), c->st));
+  double r0 = fine_eval(c, c->cur.p, nullptr, 0.0, c->cur);
+  nlmg_report R{};
+  R.res0 = r0;
+  R.history[0] = r0;
+  R.history_len = 1;
+  int cycles = 0;
+  bool early = false;
+  nlmg_status st = NLMG_OK;
+  const int saved_smoother = c->opt.smoother;
+  if (picard_only) c->opt.smoother = NLMG_SMOOTH_PICARD;
+  while (true) {
+    double rn = c->cur.rn;
+    if (!std::isfinite(rn)) { st = NLMG_EDIVERGED; break; }
+    if (rn <= tol_rel * r0 || rn <= tol_abs) break;
+    if (cycles >= max_cycles) { st = NLMG_ENOCONV; break; }
+    if (picard_only) {
+      smooth0(c, 1);
+    } else {
+      early = vcycle(c, r0, tol_rel, tol_abs);
+    }
+    ++cycles;
+    if (R.history_len < 64) R.history[R.history_len++] = c->cur.rn;
+    if (early) {
+      if (!std::isfinite(c->cur.rn)) st = NLMG_EDIVERGED;
+      break;
+    }
+  }
+  c->opt.smoother = saved_smoother;
+  CK(cudaMemcpyAsync(p_dev, c->cur.p, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaEventRecord(e1, c->st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  R.cycles = cycles;
+  R.early_exit = early ? 1 : 0;
+  R.res = c->cur.rn;
+  R.solve_ms = ms;
+  R.fine_evals = c->fine_evals;
+  R.lin_iters = c->lin_iters;
+  R.kernel_launches = launch_count() - launches0;
+  c->prof_flush();
+  if (rep) *rep = R;
+  return st;
+}
+
+void need_device(nlmg_ctx* c) {
+  if (!c->st) throw Error(NLMG_EINVAL, "context was built by nlmg_setup_host: no device data");
+}
+
+void need_data(nlmg_ctx* c) {
+  need_device(c);
+  if (!c->have_data) throw Error(NLMG_EINVAL, "call nlmg_set_data first");
+}
+
+}  // namespace
+
+// ===================================================================================================================
+// C ABI
+
+extern "C" {
+
+void nlmg_default_options(nlmg_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->n_levels = 2;
+  for (int l = 0; l < 8; ++l) {
+    o->agg_size[l] = l == 0 ? 64 : 8;
+    o->modes[l] = 4;
+  }
+  o->smoother = NLMG_SMOOTH_PICARD;
+  o->nu_pre = o->nu_post = 2;
+  o->omega = 0.8;
+  o->bt_nmax = 4;
+  o->bt_theta = 0.9;
+  o->dp_clamp = 0.0;
+  o->coarsest_steps = 10;
+  o->lin_tol = 1e-8;
+  o->lin_maxit = 5000;
+  o->setup_threads = 0;
+}
+
+static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlmg_options* opt,
+                              nlmg_ctx** out, bool device);
+
+nlmg_status nlmg_setup(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlmg_options* opt, nlmg_ctx** out) {
+  return setup_impl(mesh, kappa, opt, out, true);
+}
+
+nlmg_status nlmg_setup_host(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlmg_options* opt,
+                            nlmg_ctx** out) {
+  return setup_impl(mesh, kappa, opt, out, false);
+}
+
+static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlmg_options* opt,
+                              nlmg_ctx** out, bool device) {
+  if (!out) return NLMG_EINVAL;
+  *out = nullptr;
+  if (!mesh || !kappa || !opt || mesh->n_cells <= 0 || mesh->n_faces < 0 || !mesh->cell_volume ||
+      !mesh->face_cells || !mesh->half_trans || !mesh->face_bc || !mesh->face_area)
+    return NLMG_EINVAL;
+  if (opt->n_levels < 1 || opt->n_levels > 8 || (kappa->kind != 0 && kappa->kind != 1)) return NLMG_EINVAL;
+  nlmg_ctx* c = new nlmg_ctx();
+  nlmg_status s = guarded(c, [&]() -> nlmg_status {
+    c->opt = *opt;
+    c->kind = kappa->kind;
+    c->a = kappa->a;
+    FineMesh& fm = c->fm;
+    fm.n_cells = mesh->n_cells;
+    fm.n_faces = mesh->n_faces;
+    fm.vol.assign(mesh->cell_volume, mesh->cell_volume + mesh->n_cells);
+    fm.area.assign(mesh->face_area, mesh->face_area + mesh->n_faces);
+    fm.bc.assign(mesh->face_bc, mesh->face_bc + mesh->n_faces);
+    fm.fk.resize(mesh->n_faces);
+    fm.fl.resize(mesh->n_faces);
+    fm.ups0.resize(mesh->n_faces);
+    fm.ups1.resize(mesh->n_faces);
+    for (int f = 0; f < mesh->n_faces; ++f) {
+      int K = mesh->face_cells[2 * f], L = mesh->face_cells[2 * f + 1];
+      uint8_t b = fm.bc[f];
+      if (b > 2 || K < 0 || K >= mesh->n_cells) throw Error(NLMG_EINVAL, "bad face " + std::to_string(f));
+      if (b == 0 && (L <= K || L >= mesh->n_cells)) throw Error(NLMG_EINVAL, "interior face needs K < L");
+      fm.fk[f] = K;
+      fm.fl[f] = b == 0 ? L : -1;
+      fm.ups0[f] = mesh->half_trans[2 * f];
+      fm.ups1[f] = mesh->half_trans[2 * f + 1];
+      if (b != 2 && !(fm.ups0[f] > 0)) throw Error(NLMG_EINVAL, "half transmissibility must be positive");
+      if (b == 0 && !(fm.ups1[f] > 0)) throw Error(NLMG_EINVAL, "half transmissibility must be positive");
+    }
+    Options ho;
+    ho.n_levels = opt->n_levels;
+    for (int l = 0; l < 8; ++l) {
+      ho.agg_size[l] = opt->agg_size[l];
+      ho.modes[l] = opt->modes[l];
+      if (l + 1 < opt->n_levels && (opt->agg_size[l] < 2 || opt->modes[l] < 1 || opt->modes[l] > kMaxM))
+        throw Error(NLMG_EINVAL, "agg_size >= 2 and 1 <= modes <= 8 per level");
+    }
+    ho.threads = opt->setup_threads;
+    std::string err;
+    if (!build_hierarchy(fm, ho, c->H, err)) throw Error(NLMG_EINVAL, err);
+    if (!device) return NLMG_OK;
+    CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
+    CK(cudaMallocHost(&c->h_sc, 16 * sizeof(double)));
+    c->d_partial = c->dalloc<double>((size_t)kMaxBlocks * 4);
+    c->d_cnt = c->dalloc<unsigned>(16);
+    CK(cudaMemsetAsync(c->d_cnt, 0, 16 * sizeof(unsigned), c->st));
+    c->d_sc = c->dalloc<double>(64);
+    CK(cudaMemsetAsync(c->d_sc, 0, 64 * sizeof(double), c->st));
+    upload_fine(c);
+    alloc_fine(c);
+    c->LD.resize(c->nlev());
+    c->CB.resize(c->nlev());
+    c->TD.resize(std::max(0, c->nlev() - 1));
+    for (int l = 1; l < c->nlev(); ++l) upload_level(c, l);
+    for (int l = 0; l + 1 < c->nlev(); ++l) upload_transfer(c, l);
+    CK(cudaStreamSynchronize(c->st));
+    return NLMG_OK;
+  });
+  if (s != NLMG_OK) {
+    // keep the context so that the caller could read the message; here we free and return the status
+    nlmg_destroy(c);
+    return s;
+  }
+  *out = c;
+  return NLMG_OK;
+}
+
+nlmg_status nlmg_set_data(nlmg_ctx* c, const double* f_cell, const double* g_face) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_device(c);
+    if (!f_cell || !g_face) throw Error(NLMG_EINVAL, "null data");
+    set_data_host(c, f_cell, g_face);
+    CK(cudaStreamSynchronize(c->st));
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_solve(nlmg_ctx* c, const double* f_cell, const double* g_face, const double* x0, double tol_rel,
+                       double tol_abs, int32_t max_cycles, double* p_out, nlmg_report* rep) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_device(c);
+    if (!f_cell || !g_face || !p_out) throw Error(NLMG_EINVAL, "null argument");
+    set_data_host(c, f_cell, g_face);
+    const double* x0d = nullptr;
+    if (x0) {
+      CK(cudaMemcpyAsync(c->fdp, x0, (size_t)c->F.N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      x0d = c->fdp;
+    }
+    nlmg_status s = solve_core(c, x0d, tol_rel, tol_abs, max_cycles, c->cx, rep, false);
+    CK(cudaMemcpyAsync(p_out, c->cur.p, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return s;
+  });
+}
+
+nlmg_status nlmg_solve_device(nlmg_ctx* c, const double* f_dev, const double* g_dev, const double* x0_dev,
+                              double tol_rel, double tol_abs, int32_t max_cycles, double* p_dev, nlmg_report* rep) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_device(c);
+    if (!f_dev || !g_dev || !p_dev) throw Error(NLMG_EINVAL, "null argument");
+    set_data_dev(c, f_dev, g_dev);
+    nlmg_status s = solve_core(c, x0_dev, tol_rel, tol_abs, max_cycles, p_dev, rep, false);
+    CK(cudaStreamSynchronize(c->st));
+    return s;
+  });
+}
+
+nlmg_status nlmg_solve_picard(nlmg_ctx* c, const double* f_cell, const double* g_face, const double* x0,
+                              double tol_rel, double tol_abs, int32_t max_cycles, double* p_out, nlmg_report* rep) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_device(c);
+    if (!f_cell || !g_face || !p_out) throw Error(NLMG_EINVAL, "null argument");
+    set_data_host(c, f_cell, g_face);
+    const double* x0d = nullptr;
+    if (x0) {
+      CK(cudaMemcpyAsync(c->fdp, x0, (size_t)c->F.N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      x0d = c->fdp;
+    }
+    nlmg_status s = solve_core(c, x0d, tol_rel, tol_abs, max_cycles, c->cx, rep, true);
+    CK(cudaMemcpyAsync(p_out, c->cur.p, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return s;
+  });
+}
+
+
+nlmg_status nlmg_fine_residual(nlmg_ctx* c, const double* p, double* r_out) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_data(c);
+    CK(cudaMemcpyAsync(c->cpa, p, (size_t)c->F.N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    fine_eval(c, c->cpa, nullptr, 0.0, c->t1);
+    CK(cudaMemcpyAsync(r_out, c->t1.R, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_fine_flux(nlmg_ctx* c, const double* p, double* sigma_out) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_data(c);
+    CK(cudaMemcpyAsync(c->cpa, p, (size_t)c->F.N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    launch_kappa(c->st, c->F.N, c->cpa, nullptr, 0.0, c->cpa, c->t1.kap, nullptr, c->kind, c->a);
+    launch_fine_flux(c->st, c->F, c->cpa, c->t1.kap, c->g, c->sig0);
+    CK(cudaMemcpyAsync(sigma_out, c->sig0, (size_t)c->F.nflux * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_level_apply(nlmg_ctx* c, int32_t level, const double* x, double* out) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_device(c);
+    if (level < 1 || level >= c->nlev()) throw Error(NLMG_EINVAL, "level must be a coarse level");
+    const LevelDev& L = c->LD[level];
+    CoarseBuf& B = c->CB[level];
+    size_t nx = (size_t)L.nflux + L.np;
+    CK(cudaMemcpyAsync(B.xt2, x, nx * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    coarse_res(c, level, B.xt2, nullptr, B.ptmp);
+    CK(cudaMemcpyAsync(out, B.ptmp, nx * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_transfer(nlmg_ctx* c, int32_t level, int32_t op, const double* in, double* out) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_device(c);
+    if (level < 0 || level + 1 >= c->nlev()) throw Error(NLMG_EINVAL, "no coarser level");
+    const TransferDev& T = c->TD[level];
+    const LevelDev& C = c->LD[level + 1];
+    CoarseBuf& Bc = c->CB[level + 1];
+    const size_t ncx = (size_t)C.nflux + C.np;
+    size_t nfx;
+    if (level == 0) nfx = c->F.N; else nfx = (size_t)c->LD[level].nflux + c->LD[level].np;
+    const int nfs = level == 0 ? 0 : c->LD[level].nflux;   // flux length on the fine side
+    double* fin = level == 0 ? c->cpa : c->CB[level].xt2;
+    double* fout = level == 0 ? c->cpb : c->CB[level].ptmp;
+    if (op == NLMG_PROJECT || op == NLMG_RESTRICT) {
+      CK(cudaMemcpyAsync(fin, in, nfx * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      if (op == NLMG_PROJECT) {
+        if (level == 0) {
+          need_data(c);
+          launch_kappa(c->st, c->F.N, fin, nullptr, 0.0, fin, c->t1.kap, nullptr, c->kind, c->a);
+          launch_fine_flux(c->st, c->F, fin, c->t1.kap, c->g, c->sig0);
+          launch_csr(c->st, T.qs_n, T.qs_off, T.qs_col, T.qs_val, c->sig0, Bc.xt2, 1.0, 0.0);
+        } else {
+          launch_csr(c->st, T.qs_n, T.qs_off, T.qs_col, T.qs_val, fin, Bc.xt2, 1.0, 0.0);
+        }
+      } else {
+        if (level == 0)
+          CK(cudaMemsetAsync(Bc.xt2, 0, C.nflux * sizeof(double), c->st));
+        else
+          launch_csr(c->st, T.pst_n, T.pst_off, T.pst_col, T.pst_val, fin, Bc.xt2, 1.0, 0.0);
+      }
+      launch_restrict_p(c->st, T, fin + nfs, Bc.xt2 + C.nflux, 1.0, nullptr, nullptr);
+      CK(cudaMemcpyAsync(out, Bc.xt2, ncx * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    } else if (op == NLMG_PROLONG) {
+      CK(cudaMemcpyAsync(Bc.xt2, in, ncx * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      if (level > 0) launch_csr(c->st, T.ps_n, T.ps_off, T.ps_col, T.ps_val, Bc.xt2, fout, 1.0, 0.0);
+      launch_prolong_p(c->st, T, Bc.xt2 + C.nflux, fout + nfs);
+      CK(cudaMemcpyAsync(out, fout, nfx * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    } else {
+      throw Error(NLMG_EINVAL, "unknown transfer op");
+    }
+    CK(cudaStreamSynchronize(c->st));
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_picard_update(nlmg_ctx* c, int32_t level, const double* x, const double* b, double* dx_out,
+                               int32_t* iters) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_device(c);
+    if (level < 0 || level >= c->nlev()) throw Error(NLMG_EINVAL, "bad level");
+    int it = 0;
+    if (level == 0) {
+      need_data(c);
+      CK(cudaMemcpyAsync(c->cpa, x, (size_t)c->F.N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      fine_eval(c, c->cpa, nullptr, 0.0, c->t1);
+      launch_residual(c->st, c->F, c->t1.p, c->t1.kap, nullptr, c->g, c->rhs, c->t2.R, c->Tval, c->dinv, c->diagT,
+                      nullptr, c->red(S_NORM2B));
+      it = fine_pcg(c, c->t1.R);
+      CK(cudaMemcpyAsync(dx_out, c->cx, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    } else {
+      const LevelDev& L = c->LD[level];
+      CoarseBuf& B = c->CB[level];
+      size_t nx = (size_t)L.nflux + L.np;
+      CK(cudaMemcpyAsync(B.x, x, nx * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(B.b, b, nx * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      coarse_res(c, level, B.x, B.b, B.r);
+      it = coarse_linear(c, level);
+      CK(cudaMemcpyAsync(dx_out, B.dx, nx * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+    if (iters) *iters = it;
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_vcycle(nlmg_ctx* c, const double* p_in, double r0, double* p_out, double* res_out,
+                        int32_t* early_exit) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_data(c);
+    CK(cudaMemcpyAsync(c->fdp, p_in, (size_t)c->F.N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    fine_eval(c, c->fdp, nullptr, 0.0, c->cur);
+    c->tol_rel = 1e-8;
+    c->tol_abs = 1e-10;
+    bool e = vcycle(c, r0, c->tol_rel, c->tol_abs);
+    CK(cudaMemcpyAsync(p_out, c->cur.p, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (res_out) *res_out = c->cur.rn;
+    if (early_exit) *early_exit = e ? 1 : 0;
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_level_info_get(nlmg_ctx* c, int32_t level, nlmg_level_info* out) {
+  return guarded(c, [&]() -> nlmg_status {
+    if (level < 0 || level >= c->nlev() || !out) throw Error(NLMG_EINVAL, "bad level");
+    const Level& L = c->H.levels[level];
+    out->n_cells = L.n_cells;
+    out->n_flux = L.n_flux;
+    out->n_p = L.n_p();
+    out->n_lambda = 0;
+    if (level > 0)
+      for (int8_t k : L.fkind) out->n_lambda += (k == KIND_IFACE);
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_get_aggregates(nlmg_ctx* c, int32_t level, int32_t* agg_of, int32_t* m_out) {
+  return guarded(c, [&]() -> nlmg_status {
+    if (level < 0 || level + 1 >= c->nlev()) throw Error(NLMG_EINVAL, "bad level");
+    const Transfer& T = c->H.transfers[level];
+    if (agg_of) std::copy(T.agg_of.begin(), T.agg_of.end(), agg_of);
+    if (m_out) std::copy(c->H.levels[level + 1].m.begin(), c->H.levels[level + 1].m.end(), m_out);
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_get_transfer_dense(nlmg_ctx* c, int32_t level, int32_t which, double* dense) {
+  return guarded(c, [&]() -> nlmg_status {
+    if (level < 0 || level + 1 >= c->nlev() || !dense) throw Error(NLMG_EINVAL, "bad level");
+    const Level& L = c->H.levels[level];
+    const Level& C = c->H.levels[level + 1];
+    const Transfer& T = c->H.transfers[level];
+    if (which == 0) {
+      size_t nc = C.n_p();
+      std::fill(dense, dense + (size_t)L.n_p() * nc, 0.0);
+      for (int a = 0; a < C.n_cells; ++a) {
+        int t = 0;
+        for (int k = T.agg_off[a]; k < T.agg_off[a + 1]; ++k) {
+          int cc = T.agg_cells[k];
+          for (int r = 0; r < L.m[cc]; ++r, ++t)
+            for (int j = 0; j < C.m[a]; ++j)
+              dense[(size_t)(L.p_off[cc] + r) * nc + C.p_off[a] + j] = T.Pblk[T.pblk_off[a] + (size_t)t * C.m[a] + j];
+        }
+      }
+    } else {
+      const Csr& M = which == 1 ? T.Ps : T.Qs;
+      if (which != 1 && which != 2) throw Error(NLMG_EINVAL, "which");
+      std::fill(dense, dense + (size_t)M.nrows * M.ncols, 0.0);
+      for (int r = 0; r < M.nrows; ++r)
+        for (int k = M.off[r]; k < M.off[r + 1]; ++k) dense[(size_t)r * M.ncols + M.col[k]] += M.val[k];
+    }
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_profile(nlmg_ctx* c, int32_t enable) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_device(c);
+    c->prof_flush();
+    if (enable && c->prof.ev.empty()) {
+      c->prof.ev.resize(2 * 4096);
+      c->prof.kid.resize(4096);
+      for (auto& e : c->prof.ev) CK(cudaEventCreate(&e));
+    }
+    c->prof.on = enable != 0;
+    for (int k = 0; k < 8; ++k) { c->prof.ms[k] = 0.0; c->prof.n[k] = 0; }
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_profile_read(nlmg_ctx* c, int32_t kernel, int64_t* launches, double* total_ms,
+                              double* bytes_per_launch) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_device(c);
+    if (kernel < 0 || kernel > 2) throw Error(NLMG_EINVAL, "kernel id");
+    c->prof_flush();
+    if (launches) *launches = c->prof.n[kernel];
+    if (total_ms) *total_ms = c->prof.ms[kernel];
+    // algorithmic bytes: every array the kernel streams, read or written once; gathered neighbour values are
+    // counted once (they are the same vector)
+    const double N = c->F.N, nnz = c->F.nnz, ndir = c->F.N > 0 ? 0.0 : 0.0;
+    (void)ndir;
+    double b = 0.0;
+    if (kernel == 0) b = 4.0 * (N + 1) + 12.0 * nnz + 8.0 * N * 5;          // row_off, nbr+Tval, diag,z,pold,pnew,q
+    if (kernel == 1) b = 8.0 * N * 9;                                       // x,r,z,p,q,dinv read; x,r,z written
+    if (kernel == 2) b = 4.0 * (N + 1) + 20.0 * nnz + 8.0 * N * 4;          // row_off, nbr+2 ups, q,kap,rhs,R
+    if (bytes_per_launch) *bytes_per_launch = b;
+    return NLMG_OK;
+  });
+}
+
+const char* nlmg_last_error(const nlmg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void nlmg_destroy(nlmg_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->h_sc) cudaFreeHost(c->h_sc);
+  if (c->st) cudaStreamDestroy(c->st);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports every declared symbol, and its host-side
+hierarchy setup (aggregation, spectral bases, flux space) agrees with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import hierarchy
+from synth.grids import problem_config
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "nlmg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nlmg_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(nlmg_lib):
+    import ctypes
+    L = ctypes.CDLL(nlmg_lib.LIB_PATH)
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(nlmg_lib.SIGNATURES), set(names) ^ set(nlmg_lib.SIGNATURES)
+
+
+def test_default_options_are_the_papers(nlmg_lib):
+    o = nlmg_lib.default_options()
+    assert o.bt_nmax == 4 and abs(o.bt_theta - 0.9) < 1e-15 and o.coarsest_steps == 10
+
+
+def test_setup_rejects_bad_mesh(nlmg_lib):
+    pr = problem_config("cart2d_32", scale=4)
+    m = pr.mesh
+    bad = m.face_cells.copy()
+    bad[0] = bad[0][::-1]                  # K > L on an interior face
+    m2 = type(m)(m.n_cells, m.cell_volume, bad, m.half_trans, m.face_bc, m.face_area, m.shape)
+    with pytest.raises(nlmg_lib.NlmgError):
+        nlmg_lib.Context(m2, pr.kappa_kind, pr.kappa_a, pr.opts, device=False)
+
+
+CASES = [("cart2d_32", None, {}), ("cart2d_32", 13, dict(agg_size=[9, 4], modes=[3, 2])),
+         ("chan3d_64", 8, dict(agg_size=[16, 4, 4], modes=[3, 3, 3])),
+         ("chan3d_64", 12, dict(n_levels=3, agg_size=[27, 6, 4], modes=[4, 3, 3]))]
+
+
+@pytest.mark.parametrize("name,scale,upd", CASES)
+def test_host_hierarchy_matches_oracle(nlmg_lib, name, scale, upd):
+    pr = problem_config(name, scale=scale)
+    opts = dict(pr.opts, **upd)
+    H = hierarchy.build(pr.mesh, opts)
+    ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, opts, device=False)
+    for l, tr in enumerate(H.transfers):
+        agg, m = ctx.aggregates(l)
+        assert np.array_equal(agg, tr.agg_of)                   # bit-exact aggregation
+        assert np.array_equal(m, H.levels[l + 1].m)
+        info = ctx.level_info(l + 1)
+        assert info["n_flux"] == H.levels[l + 1].n_flux and info["n_p"] == H.levels[l + 1].n_p
+        Pp, Ppo = ctx.transfer_dense(l, 0), tr.Pp.toarray()
+        assert np.abs(Pp @ Pp.T - Ppo @ Ppo.T).max() < 1e-10
+        gap = tr.extra["eig_gap"]
+        assert np.all(gap[np.isfinite(gap)] > 1e-8)            # bases unique up to sign (C7 reading)
+        Ps, Qs = ctx.transfer_dense(l, 1), ctx.transfer_dense(l, 2)
+        scale_ = max(1.0, np.abs(tr.Psigma).max())
+        assert np.abs(Ps - tr.Psigma.toarray()).max() < 1e-9 * scale_
+        assert np.abs(Qs @ Ps - np.eye(Ps.shape[1])).max() < 1e-10
+        assert np.abs(Qs - tr.Qsigma.toarray()).max() < 1e-9 * max(1.0, np.abs(tr.Qsigma).max())
