@@ -155,6 +155,10 @@ def run_gpu(args, rank, world, local_rank):
     from synth.grids import problem_config
     pr = problem_config("chan3d_64", scale=args.scale)
     N = pr.mesh.n_cells
+    if args.lin_tol is not None:
+        pr.opts["lin_tol"] = args.lin_tol
+    if args.coarse_lin_tol is not None:
+        pr.opts["coarse_lin_tol"] = args.coarse_lin_tol
     t0 = time.perf_counter()
     ctx = nlmg.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.opts)
     setup_s = time.perf_counter() - t0
@@ -224,9 +228,44 @@ def run_gpu(args, rank, world, local_rank):
     ms_step = dev_ms / args.steps
     cycles = sum(r["cycles"] for r in reps) / len(reps)
     value = world * args.steps / (dev_ms / 1e3)
-    n_sp, ms_sp, by_sp = spmv
-    avg_sp = ms_sp / max(n_sp, 1)
-    achieved = by_sp / (avg_sp / 1e3) / 1e9 if n_sp else None
+    n_cg, ms_cg, by_cg, fl_cg = spmv
+    avg_cg = ms_cg / max(n_cg, 1)
+    fp64_peak_gflops = 1250.0   # 152 SMs x 2 FP64 FMA/clk x 2 flop x ~2.06 GHz (nominal)
+    roof = {"bound": "alu", "kernel": "kp_fine_cg<double> (persistent Jacobi-scaled CG of the level-0 Picard step)",
+            "achieved": fl_cg / (avg_cg / 1e3) / 1e9 if n_cg else None, "peak": fp64_peak_gflops,
+            "peak_kind": "nominal FP64 (no measured FP64 peak)", "unit": "GFLOP/s",
+            "frac": (fl_cg / (avg_cg / 1e3) / 1e9) / fp64_peak_gflops if n_cg else None, "traffic": None,
+            "flops_per_launch": fl_cg, "bytes_per_launch": by_cg, "avg_launch_us": avg_cg * 1e3, "launches": n_cg,
+            "memory_view": {"achieved_GBs": by_cg / (avg_cg / 1e3) / 1e9 if n_cg else None, "peak_GBs": peak,
+                            "peak_kind": peak_kind,
+                            "frac": by_cg / (avg_cg / 1e3) / 1e9 / peak if n_cg else None},
+            "share_of_solve": ms_cg / dev_ms if dev_ms else None,
+            "others": {"kp_hyb_solve": {"launches": upd[0], "avg_us": upd[1] / max(upd[0], 1) * 1e3,
+                                        "share_of_solve": upd[1] / dev_ms if dev_ms else None,
+                                        "GB/s": upd[2] / (upd[1] / max(upd[0], 1) / 1e3) / 1e9 if upd[0] else None},
+                       "k_residual": {"launches": res[0], "avg_us": res[1] / max(res[0], 1) * 1e3,
+                                      "GB/s": res[2] / (res[1] / max(res[0], 1) / 1e3) / 1e9 if res[0] else None}}}
+    mixed = None
+    if args.mixed:
+        mopts = dict(pr.opts, lin_precision=1)
+        mctx = nlmg.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, mopts)
+        pm_d = torch.zeros(N, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            mctx.solve_device(f_d.data_ptr(), g_d.data_ptr(), 0, pm_d.data_ptr(), 1e-8, 1e-10, 60)
+        mms, mrep = 0.0, None
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            mrep, st = mctx.solve_device(f_d.data_ptr(), g_d.data_ptr(), 0, pm_d.data_ptr(), 1e-8, 1e-10, 60)
+            if st != nlmg.OK:
+                raise RuntimeError("mixed solve failed %d" % st)
+            mms += mrep["solve_ms"]
+        diff = float(torch.linalg.norm(pm_d - p_d) / torch.linalg.norm(p_d))
+        mixed = {"value": world * args.steps / (mms / 1e3), "unit": "solves/s", "ms_per_step": mms / args.steps,
+                 "cycles_per_solve": mrep["cycles"], "rel_residual": mrep["res"] / mrep["res0"],
+                 "rel_diff_vs_fp64_solution": diff, "lin_iters_level": mrep["lin_iters_level"][:3],
+                 "what": "same FP64 FAS (residuals, transfers, coarse operators, convergence test in FP64); the CG "
+                         "solves inside the Picard steps in FP32 (tolerances floored at 1e-6)"}
     cpu = cpu_baseline_dict(N) if (args.cpu_baseline and world == 1) else None
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -234,22 +273,15 @@ def run_gpu(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": N, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "256 MiB buffer written between steps, outside each step's CUDA-event pair",
-                   "setup_s": round(setup_s, 3)},
+                   "setup_s": round(setup_s, 3), "lin_tol": pr.opts.get("lin_tol", 1e-8),
+                   "coarse_lin_tol": pr.opts.get("coarse_lin_tol", pr.opts.get("lin_tol", 1e-8))},
         "vcycle_dof_per_s": N * cycles * world / (ms_step / 1e3),
         "cycles_per_solve": cycles,
         "lin_iters_per_solve": sum(r["lin_iters"] for r in reps) / len(reps),
+        "lin_iters_level": reps[-1]["lin_iters_level"][:3],
         "wall_s_timed_region": wall,
-        "roofline": {"bound": "hbm", "kernel": "k_fine_spmv (CG matrix product, frozen TPFA matrix)",
-                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "bytes_per_launch": by_sp, "avg_launch_us": avg_sp * 1e3, "launches": n_sp,
-                     "share_of_solve": ms_sp / dev_ms if dev_ms else None,
-                     "others": {"k_pcg_update": {"launches": upd[0], "avg_us": upd[1] / max(upd[0], 1) * 1e3,
-                                                 "GB/s": upd[2] / (upd[1] / max(upd[0], 1) / 1e3) / 1e9
-                                                 if upd[0] else None},
-                                "k_residual": {"launches": res[0], "avg_us": res[1] / max(res[0], 1) * 1e3,
-                                               "GB/s": res[2] / (res[1] / max(res[0], 1) / 1e3) / 1e9
-                                               if res[0] else None}}},
+        "roofline": roof,
+        "mixed": mixed,
         "cpu_baseline": cpu,
         "e2e": {"value": world * len(e2e_t) / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * (N + len(pr.g_face)),
                 "d2h_bytes_per_step": 8 * N},
@@ -270,6 +302,9 @@ def main():
     ap.add_argument("--impl", default="nlmg", choices=["nlmg", "reference"])
     ap.add_argument("--scale", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--lin-tol", type=float, default=None, help="level-0 CG tolerance (default: library's)")
+    ap.add_argument("--coarse-lin-tol", type=float, default=None, help="coarse CG tolerance")
+    ap.add_argument("--no-mixed", dest="mixed", action="store_false", help="skip the FP32-CG variant")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if "RANK" in os.environ else 1))

@@ -76,10 +76,13 @@ typedef struct {
   double bt_theta;           /* Algorithm 1: theta (paper: 0.9) */
   double dp_clamp;           /* Sec. 4.1 pressure-change clamp; <= 0 disables */
   int32_t coarsest_steps;    /* Picard steps on the coarsest level (paper: <= 10) */
-  double lin_tol;            /* relative tolerance of the PCG solves inside Picard steps */
-  int32_t lin_maxit;         /* iteration cap of those solves */
+  double lin_tol;            /* relative tolerance of the level-0 CG solves inside Picard steps */
+  int32_t lin_maxit;         /* iteration cap of the CG solves */
+  double coarse_lin_tol;     /* relative tolerance of the coarse-level (hybridized) CG solves */
+  int32_t lin_precision;     /* 0: CG in FP64; 1: CG vectors and matrices in FP32 (tolerances floored at 1e-6),
+                                inside the FP64 nonlinear iteration */
   int32_t setup_threads;     /* host threads for the setup (0 = all) */
-  int32_t reserved[7];
+  int32_t reserved[6];
 } nlmg_options;
 
 typedef struct {
@@ -90,6 +93,7 @@ typedef struct {
   int64_t fine_evals;        /* fine residual evaluations */
   int64_t lin_iters;         /* PCG iterations, all levels */
   int64_t kernel_launches;   /* CUDA kernels launched by the solve */
+  int64_t lin_iters_level[8];/* PCG iterations per level */
   int32_t history_len;
   double history[64];        /* ||R|| after each cycle (first entry = res0) */
 } nlmg_report;
@@ -169,13 +173,14 @@ nlmg_status nlmg_get_transfer_dense(nlmg_ctx* ctx, int32_t level, int32_t which,
 
 /* ---- measurement ----------------------------------------------------------------------------------------- */
 /* Enables (1) or disables (0) CUDA-event timing of the hot kernels on the context stream and clears the counters.
- * Kernel ids: 0 = fine CG matrix product (k_fine_spmv), 1 = fine CG vector update (k_pcg_update),
+ * Kernel ids: 0 = persistent fine CG solve (kp_fine_cg), 1 = persistent hybridized coarse solve (kp_hyb_solve),
  * 2 = fine TPFA residual (k_residual). */
 nlmg_status nlmg_profile(nlmg_ctx* ctx, int32_t enable);
-/* Launch count, summed event time and algorithmic bytes per launch (each streamed array counted once; the
- * gathered neighbour values counted once) of a profiled kernel since nlmg_profile(ctx, 1). */
+/* Launch count, summed event time, algorithmic bytes per launch (each streamed array counted once; the gathered
+ * neighbour values counted once) and arithmetic per launch (FMA = 2 flops; kernel 0 only) of a profiled kernel
+ * since nlmg_profile(ctx, 1). Any output pointer may be NULL. */
 nlmg_status nlmg_profile_read(nlmg_ctx* ctx, int32_t kernel, int64_t* launches, double* total_ms,
-                              double* bytes_per_launch);
+                              double* bytes_per_launch, double* flops_per_launch);
 
 const char* nlmg_last_error(const nlmg_ctx* ctx);
 void nlmg_destroy(nlmg_ctx* ctx);

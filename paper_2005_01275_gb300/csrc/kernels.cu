@@ -123,8 +123,9 @@ __global__ void __launch_bounds__(kThreads) k_residual(FineDev F, const double* 
     const double qK = q[K], kK = kap[K];
     const double dkK = jdiag ? dkap[K] : 0.0;
     double flux = 0.0, dsum = 0.0, jd = 0.0;
-    const int e1 = F.row_off[K + 1];
-    for (int e = F.row_off[K]; e < e1; ++e) {
+    const int w = F.sell_w[K >> 5];
+    int e = F.sell_off[K >> 5] + (K & 31);
+    for (int j = 0; j < w; ++j, e += 32) {
       const int L = F.nbr[e];
       const double us = F.ups_s[e];
       const double ha = kK * us, hb = kap[L] * F.ups_n[e];
@@ -153,83 +154,28 @@ __global__ void __launch_bounds__(kThreads) k_residual(FineDev F, const double* 
   grid_reduce<1, false>(acc, red);
 }
 
+// S = diag(A)^-1/2 of the frozen matrix, then the scaled off-diagonal entries Ts = S_K T S_L (SELL layout)
+__global__ void k_sdiag(int n, const double* __restrict__ diagT, double* __restrict__ sdiag) {
+  GRID_STRIDE(i, n) sdiag[i] = 1.0 / sqrt(diagT[i]);
+}
+
+template <class T>
+__global__ void k_scale_sell(FineDev F, const double* __restrict__ Tval, const double* __restrict__ sdiag,
+                             T* __restrict__ Ts) {
+  GRID_STRIDE(K, F.N) {
+    const int w = F.sell_w[K >> 5];
+    const double sK = sdiag[K];
+    int e = F.sell_off[K >> 5] + (K & 31);
+    for (int j = 0; j < w; ++j, e += 32) Ts[e] = (T)(Tval[e] * sK * sdiag[F.nbr[e]]);
+  }
+}
+
 __global__ void k_jacobi_update(int n, const double* __restrict__ q, const double* __restrict__ R,
                                 const double* __restrict__ jdiag, const double* __restrict__ diagT, double omega,
                                 double* __restrict__ qnew) {
   GRID_STRIDE(i, n) {
     double d = fmax(jdiag[i], 0.5 * diagT[i]);
     qnew[i] = q[i] - omega * R[i] / d;
-  }
-}
-
-// CG direction update fused into the matrix product: p_new = z + beta p_old (computed for the row and its
-// neighbours alike), q = A p_new, and the reduction p_new . q; the last block sets alpha = (r.z) / (p.q).
-__global__ void __launch_bounds__(kThreads) k_fine_spmv(FineDev F, const double* __restrict__ Tval,
-                                                        const double* __restrict__ diagT,
-                                                        const double* __restrict__ z,
-                                                        const double* __restrict__ pold, double* __restrict__ pnew,
-                                                        double* __restrict__ q, double* sc, int first, Reduce red) {
-  const double beta = first ? 0.0 : sc[S_BETA];
-  double acc[1] = {0.0};
-  GRID_STRIDE(K, F.N) {
-    const double pK = first ? z[K] : fma(beta, pold[K], z[K]);
-    double y = diagT[K] * pK;
-    const int e1 = F.row_off[K + 1];
-    for (int e = F.row_off[K]; e < e1; ++e) {
-      const int L = F.nbr[e];
-      const double pL = first ? z[L] : fma(beta, pold[L], z[L]);
-      y = fma(-Tval[e], pL, y);
-    }
-    pnew[K] = pK;
-    q[K] = y;
-    acc[0] = fma(pK, y, acc[0]);
-  }
-  if (grid_reduce<1, false>(acc, red) && threadIdx.x == 0) {
-    sc[S_PQ] = acc[0];
-    sc[S_ALPHA] = acc[0] != 0.0 ? sc[S_RZ] / acc[0] : 0.0;
-  }
-}
-
-__global__ void k_pcg_init(int n, const double* __restrict__ b, double bscale, const double* __restrict__ dinv,
-                           double* __restrict__ x, double* __restrict__ r, double* __restrict__ z, double* sc,
-                           Reduce red) {
-  double acc[2] = {0.0, 0.0};
-  GRID_STRIDE(i, n) {
-    double ri = bscale * b[i];
-    double zi = ri * dinv[i];
-    x[i] = 0.0;
-    r[i] = ri;
-    z[i] = zi;
-    acc[0] = fma(ri, zi, acc[0]);
-    acc[1] = fma(ri, ri, acc[1]);
-  }
-  if (grid_reduce<2, false>(acc, red) && threadIdx.x == 0) {
-    sc[S_RZ] = acc[0];
-    sc[S_RR0] = acc[1];
-    sc[S_RR] = acc[1];
-    sc[S_BETA] = 0.0;
-  }
-}
-
-__global__ void k_pcg_update(int n, double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
-                             const double* __restrict__ p, const double* __restrict__ q,
-                             const double* __restrict__ dinv, double* sc, Reduce red) {
-  const double alpha = sc[S_ALPHA];
-  double acc[2] = {0.0, 0.0};
-  GRID_STRIDE(i, n) {
-    x[i] = fma(alpha, p[i], x[i]);
-    double ri = fma(-alpha, q[i], r[i]);
-    double zi = ri * dinv[i];
-    r[i] = ri;
-    z[i] = zi;
-    acc[0] = fma(ri, zi, acc[0]);
-    acc[1] = fma(ri, ri, acc[1]);
-  }
-  if (grid_reduce<2, false>(acc, red) && threadIdx.x == 0) {
-    double rz_old = sc[S_RZ];
-    sc[S_BETA] = rz_old != 0.0 ? acc[0] / rz_old : 0.0;
-    sc[S_RZ] = acc[0];
-    sc[S_RR] = acc[1];
   }
 }
 
@@ -330,40 +276,49 @@ __global__ void k_csr(int nrows, const int* __restrict__ off, const int* __restr
 
 // ---- coarse levels ---------------------------------------------------------------------------------------------
 
-// Per coarse cell c (Prop. 1, eq. structure): pbar = w_c . p_c, s = 1 / kappa(pbar);
-// yl[slots of c] = s Mloc_c sigma_c + Dloc_c^T p_c ; r_p,c = Dloc_c sigma_c - b_p,c.
-__global__ void k_coarse_cell(LevelDev L, const double* __restrict__ sig, const double* __restrict__ p,
-                              const double* __restrict__ bp, double* __restrict__ yl, double* __restrict__ rp,
-                              double* __restrict__ kapc, int kind, double a, Reduce red) {
-  double acc[1] = {0.0};
+// Coarse operator (Prop. 1, eq. structure) on cell c: pbar = w_c . p_c, s = 1 / kappa(pbar);
+// yl[slots of c] = s Mloc_c sigma_c + Dloc_c^T p_c (one thread per local flux slot) and
+// r_p,c = Dloc_c sigma_c - b_p,c (one thread per pressure unknown).
+__global__ void k_coarse_kappa(LevelDev L, const double* __restrict__ p, double* __restrict__ kapc, int kind,
+                               double a) {
   GRID_STRIDE(c, L.nc) {
-    const int mc = L.m[c], lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c];
-    const double* pc = p + po;
+    const int po = L.p_off[c];
     double pb = 0.0;
-    for (int r = 0; r < mc; ++r) pb = fma(L.w[po + r], pc[r], pb);
-    const double kp = kappa_of(pb, kind, a);
-    const double s = 1.0 / kp;
-    if (kapc) kapc[c] = kp;
-    double sl[kMaxLoc];
-    for (int t = 0; t < nl; ++t) sl[t] = sig[L.loc[lo + t]];
-    const double* M = L.Mloc + L.mat_off[c];
-    const double* D = L.Dloc + L.dmat_off[c];
-    for (int u = 0; u < nl; ++u) {
-      double y = 0.0;
-      for (int t = 0; t < nl; ++t) y = fma(M[u * nl + t], sl[t], y);
-      y *= s;
-      for (int r = 0; r < mc; ++r) y = fma(D[r * nl + u], pc[r], y);
-      yl[lo + u] = y;
-    }
-    for (int r = 0; r < mc; ++r) {
-      double v = 0.0;
-      for (int t = 0; t < nl; ++t) v = fma(D[r * nl + t], sl[t], v);
-      if (bp) v -= bp[po + r];
-      rp[po + r] = v;
-      acc[0] = fma(v, v, acc[0]);
-    }
+    for (int r = 0; r < L.m[c]; ++r) pb = fma(L.w[po + r], p[po + r], pb);
+    kapc[c] = kappa_of(pb, kind, a);
   }
-  grid_reduce<1, false>(acc, red);
+}
+
+__global__ void k_coarse_slots(LevelDev L, const double* __restrict__ sig, const double* __restrict__ p,
+                               const double* __restrict__ kapc, double* __restrict__ yl) {
+  GRID_STRIDE(y, L.nyl) {
+    const int c = L.slot_cell[y];
+    const int mc = L.m[c], lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c];
+    const int u = y - lo;
+    const double* Mu = L.Mloc + L.mat_off[c] + (size_t)u * nl;
+    const double* D = L.Dloc + L.dmat_off[c];
+    double acc = 0.0;
+    for (int t = 0; t < nl; ++t) acc = fma(Mu[t], sig[L.loc[lo + t]], acc);
+    acc /= kapc[c];
+    for (int r = 0; r < mc; ++r) acc = fma(D[r * nl + u], p[po + r], acc);
+    yl[y] = acc;
+  }
+}
+
+__global__ void k_coarse_prows(LevelDev L, const double* __restrict__ sig, const double* __restrict__ bp,
+                               double* __restrict__ rp, Reduce red) {
+  double acc2[1] = {0.0};
+  GRID_STRIDE(i, L.np) {
+    const int c = L.p_cell[i];
+    const int lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c];
+    const double* Dr = L.Dloc + L.dmat_off[c] + (size_t)(i - po) * nl;
+    double v = 0.0;
+    for (int t = 0; t < nl; ++t) v = fma(Dr[t], sig[L.loc[lo + t]], v);
+    if (bp) v -= bp[i];
+    rp[i] = v;
+    acc2[0] = fma(v, v, acc2[0]);
+  }
+  grid_reduce<1, false>(acc2, red);
 }
 
 // r_sigma,i = (sum over the <= 2 owners of yl) - b_sigma,i
@@ -391,115 +346,13 @@ __global__ void k_coarse_pbar_max(LevelDev L, const double* __restrict__ dp, Red
   grid_reduce<1, true>(acc, red);
 }
 
-// Hybridization (Sec. 3.4): local saddles [s M D^T; D 0] with s = 1/kappa_c have the inverse
-// [kappa A, B; B^T, C / kappa] where [A B; B^T C] is the stored kappa = 1 inverse.
-// Right-hand side of H lambda = xi: per cell u = kappa A bhat + B b_p, scattered with the interface signs.
-__global__ void k_hyb_rhs(LevelDev L, const double* __restrict__ kapc, const double* __restrict__ bs,
-                          const double* __restrict__ bp, double* __restrict__ ylam) {
-  GRID_STRIDE(c, L.nc) {
-    const int mc = L.m[c], lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c], n = nl + mc;
-    const double kp = kapc[c];
-    const double* S = L.Sinv + L.sad_off[c];
-    double bh[kMaxLoc];
-    for (int t = 0; t < nl; ++t) bh[t] = L.own0[lo + t] ? bs[L.loc[lo + t]] : 0.0;
-    for (int k = L.if_off[c]; k < L.if_off[c + 1]; ++k) {
-      const int u = L.if_slot[k];
-      double a1 = 0.0, a2 = 0.0;
-      for (int t = 0; t < nl; ++t) a1 = fma(S[u * n + t], bh[t], a1);
-      for (int r = 0; r < mc; ++r) a2 = fma(S[u * n + nl + r], bp[po + r], a2);
-      ylam[k] = L.if_sign[k] * fma(kp, a1, a2);
-    }
-  }
-}
-
-__global__ void k_lam_gather(LevelDev L, const double* __restrict__ ylam, double* __restrict__ out, int invert) {
-  GRID_STRIDE(l, L.nlam) {
-    double v = ylam[L.lam_y0[l]] + ylam[L.lam_y1[l]];
-    out[l] = invert ? 1.0 / v : v;
-  }
-}
-
-__global__ void k_hyb_diag_cells(LevelDev L, const double* __restrict__ kapc, double* __restrict__ ylam) {
-  GRID_STRIDE(c, L.nc) {
-    const int k0 = L.if_off[c], ni = L.if_off[c + 1] - k0;
-    const double* H = L.Hc + L.hc_off[c];
-    for (int k = 0; k < ni; ++k) ylam[k0 + k] = kapc[c] * H[k * ni + k];
-  }
-}
-
-// per cell: ylam[k] = kappa_c sum_j Hc[k, j] pnew_j, with pnew = z + beta pold formed on the fly
-__global__ void k_hyb_apply_cells(LevelDev L, const double* __restrict__ kapc, const double* __restrict__ z,
-                                  const double* __restrict__ pold, const double* sc, int first,
-                                  double* __restrict__ ylam) {
-  const double beta = first ? 0.0 : sc[S_BETA];
-  GRID_STRIDE(c, L.nc) {
-    const int k0 = L.if_off[c], ni = L.if_off[c + 1] - k0;
-    const double* H = L.Hc + L.hc_off[c];
-    double v[kMaxLoc];
-    for (int j = 0; j < ni; ++j) {
-      const int l = L.if_lam[k0 + j];
-      v[j] = first ? z[l] : fma(beta, pold[l], z[l]);
-    }
-    const double kp = kapc[c];
-    for (int k = 0; k < ni; ++k) {
-      double y = 0.0;
-      for (int j = 0; j < ni; ++j) y = fma(H[k * ni + j], v[j], y);
-      ylam[k0 + k] = kp * y;
-    }
-  }
-}
-
-__global__ void k_hyb_gather_dot(LevelDev L, const double* __restrict__ ylam, const double* __restrict__ z,
-                                 const double* __restrict__ pold, double* __restrict__ pnew, double* __restrict__ q,
-                                 double* sc, int first, Reduce red) {
-  const double beta = first ? 0.0 : sc[S_BETA];
-  double acc[1] = {0.0};
-  GRID_STRIDE(l, L.nlam) {
-    const double pl = first ? z[l] : fma(beta, pold[l], z[l]);
-    const double y = ylam[L.lam_y0[l]] + ylam[L.lam_y1[l]];
-    pnew[l] = pl;
-    q[l] = y;
-    acc[0] = fma(pl, y, acc[0]);
-  }
-  if (grid_reduce<1, false>(acc, red) && threadIdx.x == 0) {
-    sc[S_PQ] = acc[0];
-    sc[S_ALPHA] = acc[0] != 0.0 ? sc[S_RZ] / acc[0] : 0.0;
-  }
-}
-
-// sigma^c = kappa A w + B b_p, p_c = B^T w + C b_p / kappa with w = bhat - C^T lambda
-__global__ void k_hyb_recover(LevelDev L, const double* __restrict__ kapc, const double* __restrict__ bs,
-                              const double* __restrict__ bp, const double* __restrict__ lam,
-                              double* __restrict__ dsig, double* __restrict__ dp) {
-  GRID_STRIDE(c, L.nc) {
-    const int mc = L.m[c], lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c], n = nl + mc;
-    const double kp = kapc[c];
-    const double* S = L.Sinv + L.sad_off[c];
-    double w[kMaxLoc];
-    for (int t = 0; t < nl; ++t) w[t] = L.own0[lo + t] ? bs[L.loc[lo + t]] : 0.0;
-    for (int k = L.if_off[c]; k < L.if_off[c + 1]; ++k) w[L.if_slot[k]] -= L.if_sign[k] * lam[L.if_lam[k]];
-    for (int u = 0; u < nl; ++u) {
-      if (!L.own0[lo + u]) continue;
-      double a1 = 0.0, a2 = 0.0;
-      for (int t = 0; t < nl; ++t) a1 = fma(S[u * n + t], w[t], a1);
-      for (int r = 0; r < mc; ++r) a2 = fma(S[u * n + nl + r], bp[po + r], a2);
-      dsig[L.loc[lo + u]] = fma(kp, a1, a2);
-    }
-    for (int r = 0; r < mc; ++r) {
-      double a1 = 0.0, a2 = 0.0;
-      for (int t = 0; t < nl; ++t) a1 = fma(S[(nl + r) * n + t], w[t], a1);
-      for (int q = 0; q < mc; ++q) a2 = fma(S[(nl + r) * n + nl + q], bp[po + q], a2);
-      dp[po + r] = a1 + a2 / kp;
-    }
-  }
-}
-
 }  // namespace
 
 // ---- launchers ---------------------------------------------------------------------------------------------------
 
 static std::atomic<long long> g_launches(0);
 long long launch_count() { return g_launches.load(); }
+void count_launch(int n) { g_launches.fetch_add(n); }
 #define COUNT(n) g_launches.fetch_add(n)
 
 void launch_kappa(cudaStream_t st, int n, const double* p, const double* dp, double s, double* q, double* kap,
@@ -521,21 +374,6 @@ void launch_jacobi_update(cudaStream_t st, int n, const double* q, const double*
                           const double* diagT, double omega, double* qnew) {
   COUNT(1);
   k_jacobi_update<<<grid_for(n), kThreads, 0, st>>>(n, q, R, jdiag, diagT, omega, qnew);
-}
-void launch_fine_spmv(cudaStream_t st, const FineDev& F, const double* Tval, const double* diagT, const double* z,
-                      const double* pold, double* pnew, double* q, double* sc, int first, Reduce red) {
-  COUNT(1);
-  k_fine_spmv<<<grid_for(F.N), kThreads, 0, st>>>(F, Tval, diagT, z, pold, pnew, q, sc, first, red);
-}
-void launch_pcg_init(cudaStream_t st, int n, const double* b, double bscale, const double* dinv, double* x,
-                     double* r, double* z, double* sc, Reduce red) {
-  COUNT(1);
-  k_pcg_init<<<grid_for(n), kThreads, 0, st>>>(n, b, bscale, dinv, x, r, z, sc, red);
-}
-void launch_pcg_update(cudaStream_t st, int n, double* x, double* r, double* z, const double* p, const double* q,
-                       const double* dinv, double* sc, Reduce red) {
-  COUNT(1);
-  k_pcg_update<<<grid_for(n), kThreads, 0, st>>>(n, x, r, z, p, q, dinv, sc, red);
 }
 void launch_max_abs(cudaStream_t st, int n, const double* x, Reduce red) {
   COUNT(1);
@@ -571,9 +409,22 @@ void launch_csr(cudaStream_t st, int nrows, const int* off, const int* col, cons
 }
 void launch_coarse_cell(cudaStream_t st, const LevelDev& L, const double* sig, const double* p, const double* bp,
                         double* yl, double* rp, double* kapc, int kind, double a, Reduce red) {
-  COUNT(1);
-  k_coarse_cell<<<grid_for(L.nc), kThreads, 0, st>>>(L, sig, p, bp, yl, rp, kapc, kind, a, red);
+  COUNT(3);
+  k_coarse_kappa<<<grid_for(L.nc), kThreads, 0, st>>>(L, p, kapc, kind, a);
+  k_coarse_slots<<<grid_for(L.nyl), kThreads, 0, st>>>(L, sig, p, kapc, yl);
+  k_coarse_prows<<<grid_for(L.np), kThreads, 0, st>>>(L, sig, bp, rp, red);
 }
+void launch_sdiag(cudaStream_t st, int n, const double* diagT, double* sdiag) {
+  COUNT(1);
+  k_sdiag<<<grid_for(n), kThreads, 0, st>>>(n, diagT, sdiag);
+}
+template <class T>
+void launch_scale_sell(cudaStream_t st, const FineDev& F, const double* Tval, const double* sdiag, T* Ts) {
+  COUNT(1);
+  k_scale_sell<T><<<grid_for(F.N), kThreads, 0, st>>>(F, Tval, sdiag, Ts);
+}
+template void launch_scale_sell<double>(cudaStream_t, const FineDev&, const double*, const double*, double*);
+template void launch_scale_sell<float>(cudaStream_t, const FineDev&, const double*, const double*, float*);
 void launch_coarse_flux(cudaStream_t st, const LevelDev& L, const double* yl, const double* bs, double* rs,
                         Reduce red) {
   COUNT(1);
@@ -582,28 +433,6 @@ void launch_coarse_flux(cudaStream_t st, const LevelDev& L, const double* yl, co
 void launch_coarse_pbar_max(cudaStream_t st, const LevelDev& L, const double* dp, Reduce red) {
   COUNT(1);
   k_coarse_pbar_max<<<grid_for(L.nc), kThreads, 0, st>>>(L, dp, red);
-}
-void launch_hyb_rhs(cudaStream_t st, const LevelDev& L, const double* kapc, const double* bs, const double* bp,
-                    double* ylam, double* xi) {
-  COUNT(2);
-  k_hyb_rhs<<<grid_for(L.nc), kThreads, 0, st>>>(L, kapc, bs, bp, ylam);
-  k_lam_gather<<<grid_for(L.nlam), kThreads, 0, st>>>(L, ylam, xi, 0);
-}
-void launch_hyb_diag(cudaStream_t st, const LevelDev& L, const double* kapc, double* ylam, double* dinv) {
-  COUNT(2);
-  k_hyb_diag_cells<<<grid_for(L.nc), kThreads, 0, st>>>(L, kapc, ylam);
-  k_lam_gather<<<grid_for(L.nlam), kThreads, 0, st>>>(L, ylam, dinv, 1);
-}
-void launch_hyb_spmv(cudaStream_t st, const LevelDev& L, const double* kapc, const double* z, const double* pold,
-                     double* pnew, double* q, double* ylam, double* sc, int first, Reduce red) {
-  COUNT(2);
-  k_hyb_apply_cells<<<grid_for(L.nc), kThreads, 0, st>>>(L, kapc, z, pold, sc, first, ylam);
-  k_hyb_gather_dot<<<grid_for(L.nlam), kThreads, 0, st>>>(L, ylam, z, pold, pnew, q, sc, first, red);
-}
-void launch_hyb_recover(cudaStream_t st, const LevelDev& L, const double* kapc, const double* bs, const double* bp,
-                        const double* lam, double* dsig, double* dp) {
-  COUNT(1);
-  k_hyb_recover<<<grid_for(L.nc), kThreads, 0, st>>>(L, kapc, bs, bp, lam, dsig, dp);
 }
 
 }  // namespace nlmg

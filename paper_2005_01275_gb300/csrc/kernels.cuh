@@ -23,8 +23,10 @@ struct Reduce {
 // ---------------------------------------------------------------------------------------------------------------
 // Fine level (reduced TPFA, Sec. 2.1)
 struct FineDev {
-  int N = 0, nnz = 0, nflux = 0;
-  int *row_off = nullptr, *nbr = nullptr;          // interior neighbours per cell (CSR)
+  int N = 0, nnz = 0, nflux = 0, nslice = 0;
+  // interior neighbours per cell in SELL-32 layout: slice s = cells 32 s .. 32 s + 31, width sell_w[s]; entry j of
+  // cell K sits at sell_off[s] + 32 j + (K & 31). Padding entries point to the cell itself with Ups = (1, 0).
+  int *sell_off = nullptr, *sell_w = nullptr, *nbr = nullptr;
   double *ups_s = nullptr, *ups_n = nullptr;       // own / neighbour half transmissibility per entry
   int *dir_off = nullptr, *dir_face = nullptr;     // Dirichlet faces per cell (CSR)
   double* dir_ups = nullptr;
@@ -50,6 +52,10 @@ struct LevelDev {
   int* hc_off = nullptr;                           // per cell: nif x nif block of C S_ss C^T (kappa = 1)
   double* Hc = nullptr;
   int *lam_y0 = nullptr, *lam_y1 = nullptr;        // per lambda: its two entries in the per-interface buffer
+  int* if_cell = nullptr;                          // per interface slot: its cell
+  int* slot_cell = nullptr;                        // per local flux slot: its cell
+  int* p_cell = nullptr;                           // per pressure unknown: its cell
+  float *Hc32 = nullptr, *Sinv32 = nullptr;        // FP32 copies for the mixed-precision solves
 };
 
 // Transfer between level l and l+1
@@ -75,6 +81,7 @@ inline int grid_for(long n) {
 
 // number of kernels launched by this process through the launchers below
 long long launch_count();
+void count_launch(int n);
 
 // launchers (kernels.cu)
 void launch_kappa(cudaStream_t st, int n, const double* p, const double* dp, double s, double* q, double* kap,
@@ -85,12 +92,6 @@ void launch_residual(cudaStream_t st, const FineDev& F, const double* q, const d
                      double* jdiag, Reduce red);
 void launch_jacobi_update(cudaStream_t st, int n, const double* q, const double* R, const double* jdiag,
                           const double* diagT, double omega, double* qnew);
-void launch_fine_spmv(cudaStream_t st, const FineDev& F, const double* Tval, const double* diagT, const double* z,
-                      const double* pold, double* pnew, double* q, double* sc, int first, Reduce red);
-void launch_pcg_init(cudaStream_t st, int n, const double* b, double bscale, const double* dinv, double* x,
-                     double* r, double* z, double* sc, Reduce red);
-void launch_pcg_update(cudaStream_t st, int n, double* x, double* r, double* z, const double* p, const double* q,
-                       const double* dinv, double* sc, Reduce red);
 void launch_max_abs(cudaStream_t st, int n, const double* x, Reduce red);
 void launch_axpy(cudaStream_t st, int n, const double* x, double s, const double* dx, double* out);
 void launch_sub(cudaStream_t st, int n, const double* y, const double* x, double* out);
@@ -103,15 +104,11 @@ void launch_csr(cudaStream_t st, int nrows, const int* off, const int* col, cons
                 double* y, double alpha, double beta);
 void launch_coarse_cell(cudaStream_t st, const LevelDev& L, const double* sig, const double* p, const double* bp,
                         double* yl, double* rp, double* kapc, int kind, double a, Reduce red);
+void launch_sdiag(cudaStream_t st, int n, const double* diagT, double* sdiag);
+template <class T>
+void launch_scale_sell(cudaStream_t st, const FineDev& F, const double* Tval, const double* sdiag, T* Ts);
 void launch_coarse_flux(cudaStream_t st, const LevelDev& L, const double* yl, const double* bs, double* rs,
                         Reduce red);
 void launch_coarse_pbar_max(cudaStream_t st, const LevelDev& L, const double* dp, Reduce red);
-void launch_hyb_rhs(cudaStream_t st, const LevelDev& L, const double* kapc, const double* bs, const double* bp,
-                    double* ylam, double* xi);
-void launch_hyb_diag(cudaStream_t st, const LevelDev& L, const double* kapc, double* ylam, double* dinv);
-void launch_hyb_spmv(cudaStream_t st, const LevelDev& L, const double* kapc, const double* z, const double* pold,
-                     double* pnew, double* q, double* ylam, double* sc, int first, Reduce red);
-void launch_hyb_recover(cudaStream_t st, const LevelDev& L, const double* kapc, const double* bs, const double* bp,
-                        const double* lam, double* dsig, double* dp);
 
 }  // namespace nlmg

@@ -1,0 +1,422 @@
+// Persistent (cooperative) conjugate-gradient kernels: one launch runs a whole Picard linear solve, with
+// device-side scalars and convergence test, so the CG iterations pay neither launch gaps nor host round trips.
+//
+// Grid-wide synchronisation uses a counter/generation barrier whose wait is bounded: after ~2 s of spinning the
+// kernel records an error flag and every block leaves. The launch goes through cudaLaunchCooperativeKernel with at
+// most the co-resident number of blocks, so in a correct run every wait ends.
+//
+// Data written by one block and read by another inside the same launch (CG vectors, per-interface buffers) is read
+// with ld.global.cg (L2, bypassing the non-coherent L1), after the barrier that orders the write.
+//
+// Reductions stay deterministic: each block writes one partial; after the barrier every block sums all partials in
+// block order with the same fixed tree, so all blocks hold bit-identical scalars and take the same decisions.
+#include <cmath>
+
+#include "kernels.cuh"
+#include "persist.cuh"
+
+namespace nlmg {
+
+namespace {
+
+constexpr unsigned long long kSpinLimit = 1ull << 26;   // x ~32 ns sleeps ~ 2 s
+constexpr int kPThreads = 512;                           // threads per block of the persistent kernels
+
+// Bounded grid barrier: blocks arrive on gs.count; the last one to arrive runs `last` (a block-wide callback),
+// then bumps the generation that the others poll. Returns false (and sets *err) if a wait gave up.
+template <class LastFn>
+__device__ __forceinline__ bool grid_barrier_ex(const GridSync& gs, LastFn&& last) {
+  __shared__ int ok, is_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* gen = gs.gen;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(gs.count, 1u);
+    is_last = arrived == gridDim.x - 1;
+    if (!is_last) {
+      unsigned long long spins = 0;
+      while (*gen == g) {
+        __nanosleep(32);
+        if ((++spins & 1023u) == 0 && (spins > kSpinLimit || *((volatile int*)gs.err) != 0)) {
+          atomicExch(gs.err, 1);
+          ok = 0;
+          break;
+        }
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  if (is_last) {
+    __threadfence();
+    last();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *gs.count = 0u;
+      __threadfence();
+      atomicAdd(gs.gen, 1u);
+    }
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(const GridSync& gs) {
+  return grid_barrier_ex(gs, []() {});
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sm[k * 32 + warp] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      v[k] = lane < nw ? sm[k * 32 + lane] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    }
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sm[k * 32] = v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = sm[k * 32];
+  __syncthreads();
+}
+
+// Grid sums of NV values: every block publishes its block sum; the last block to arrive adds the partials in block
+// order (fixed tree) and stores the result to `out`; after the barrier every thread reads `out`.
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partial, double* out, const GridSync& gs,
+                                         double* sm) {
+  block_sum<NV>(v, sm);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partial[blockIdx.x * NV + k] = v[k];
+  const bool ok = grid_barrier_ex(gs, [&]() {
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) acc[k] += __ldcg(&partial[b * NV + k]);
+    block_sum<NV>(acc, sm);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) out[k] = acc[k];
+    __threadfence();
+  });
+  if (!ok) return false;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = __ldcg(&out[k]);
+  return true;
+}
+
+#define GSTRIDE(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+
+// ---- fine level: A dx = bscale * b with the frozen TPFA matrix --------------------------------------------------
+// CG on the symmetrically Jacobi-scaled system (S A S) y = S bscale b, dx = S y, S = diag(A)^-1/2, so the scaled
+// matrix has a unit diagonal and only its off-diagonal entries Ts (SELL-32 layout, type T) are read. T = double is
+// the FP64 path; T = float runs the Krylov vectors and the matrix in FP32 (dot products still accumulate in FP64)
+// inside the FP64 nonlinear iteration. The stopping test is on the scaled residual, ||S r|| <= tol ||S r_0||
+// (the r.z of Jacobi-preconditioned CG).
+template <class T>
+__global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __restrict__ Ts,
+                                                        const double* __restrict__ sdiag,
+                                                        const double* __restrict__ b, double bscale,
+                                                        double* __restrict__ dx, T* __restrict__ y,
+                                                        T* __restrict__ r, T* pa, T* pb, T* __restrict__ q,
+                                                        double* partial, GridSync gs, double tol, int maxit,
+                                                        PcgResult* res) {
+  __shared__ double sm[2 * 32];
+  double* part0 = partial;
+  double* part1 = partial + 2 * gridDim.x;
+  double a1[1] = {0.0};
+  GSTRIDE(i, F.N) {
+    const T ri = (T)(sdiag[i] * bscale * b[i]);
+    y[i] = (T)0;
+    r[i] = ri;
+    a1[0] = fma((double)ri, (double)ri, a1[0]);
+  }
+  if (!grid_sum<1>(a1, part1, gs.out + 0, gs, sm)) return;
+  const double rr0 = a1[0];
+  double rr = rr0;
+  const double tol2 = tol * tol * rr0;
+  T beta = (T)0;
+  T* pold = pa;
+  T* pnew = pb;
+  int it = 0;
+  bool first = true;
+  while (rr0 > 0.0 && rr > tol2 && it < maxit) {
+    // q = (S A S) p_new with p_new = r + beta p_old formed for the row and its neighbours alike
+    double pq[1] = {0.0};
+    GSTRIDE(K, F.N) {
+      const int s = K >> 5, lane = K & 31;
+      const T pK = first ? __ldcg(&r[K]) : beta * __ldcg(&pold[K]) + __ldcg(&r[K]);
+      T acc = pK;
+      const int w = F.sell_w[s];
+      int e = F.sell_off[s] + lane;
+      int j = 0;
+      if (w <= 8) {
+        int Ls[8];
+        T Tv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (u < w) {
+            Ls[u] = F.nbr[e + 32 * u];
+            Tv[u] = Ts[e + 32 * u];
+          }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (u < w) {
+            const int L = Ls[u];
+            const T pL = first ? __ldcg(&r[L]) : beta * __ldcg(&pold[L]) + __ldcg(&r[L]);
+            acc -= Tv[u] * pL;
+          }
+        j = w;
+      }
+      for (e += 32 * j; j < w; ++j, e += 32) {
+        const int L = F.nbr[e];
+        const T pL = first ? __ldcg(&r[L]) : beta * __ldcg(&pold[L]) + __ldcg(&r[L]);
+        acc -= Ts[e] * pL;
+      }
+      pnew[K] = pK;
+      q[K] = acc;
+      pq[0] = fma((double)pK, (double)acc, pq[0]);
+    }
+    if (!grid_sum<1>(pq, part0, gs.out + 2, gs, sm)) return;
+    const double alpha_d = pq[0] != 0.0 ? rr / pq[0] : 0.0;
+    const T alpha = (T)alpha_d;
+    double rn[1] = {0.0};
+    GSTRIDE(i, F.N) {
+      y[i] = alpha * pnew[i] + y[i];
+      const T ri = r[i] - alpha * q[i];
+      r[i] = ri;
+      rn[0] = fma((double)ri, (double)ri, rn[0]);
+    }
+    if (!grid_sum<1>(rn, part1, gs.out + 4, gs, sm)) return;
+    beta = (T)(rr != 0.0 ? rn[0] / rr : 0.0);
+    rr = rn[0];
+    T* t = pold;
+    pold = pnew;
+    pnew = t;
+    first = false;
+    ++it;
+    if (!(alpha_d != 0.0)) break;   // breakdown (p.Ap = 0): stop with the current iterate
+  }
+  GSTRIDE(i, F.N) dx[i] = sdiag[i] * (double)y[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    res->iters = it;
+    res->rr0 = rr0;
+    res->rr = rr;
+  }
+}
+
+// ---- coarse level: hybridized saddle solve (rhs, Jacobi diagonal, CG on H lambda = xi, local recovery) ------
+template <class T>
+__global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* __restrict__ Hc,
+                                                         const T* __restrict__ Sinv,
+                                                         const double* __restrict__ kapc,
+                                                         const double* __restrict__ bs,
+                                                         const double* __restrict__ bp, T* ylam,
+                                                         T* ydiag, T* lam, T* lr, T* lz,
+                                                         T* pa, T* pb, T* lq, T* ldinv,
+                                                         double* __restrict__ dsig, double* __restrict__ dp,
+                                                         double* partial, GridSync gs, double tol, int maxit,
+                                                         PcgResult* res) {
+  __shared__ double sm[2 * 32];
+  double* part0 = partial;
+  double* part1 = partial + 2 * gridDim.x;
+  // phase 0: per interface slot k of cell c, u_k = kappa A[k,:] bhat + B[k,:] b_p (signed) and kappa Hc[k,k]
+  GSTRIDE(k, L.nif) {
+    const int c = L.if_cell[k];
+    const int mc = L.m[c], lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c], n = nl + mc;
+    const double kp = kapc[c];
+    const int u = L.if_slot[k];
+    const T* Su = Sinv + L.sad_off[c] + (size_t)u * n;
+    T a1 = 0, a2_ = 0;
+    for (int t = 0; t < nl; ++t)
+      if (L.own0[lo + t]) a1 += Su[t] * (T)bs[L.loc[lo + t]];
+    for (int q = 0; q < mc; ++q) a2_ += Su[nl + q] * (T)bp[po + q];
+    ylam[k] = (T)L.if_sign[k] * ((T)kp * a1 + a2_);
+    const int k0 = L.if_off[c], ni = L.if_off[c + 1] - k0;
+    ydiag[k] = (T)kp * Hc[L.hc_off[c] + (k - k0) * ni + (k - k0)];
+  }
+  if (!grid_barrier(gs)) return;
+  double a2[2] = {0.0, 0.0};
+  GSTRIDE(l, L.nlam) {
+    const T xi = __ldcg(&ylam[L.lam_y0[l]]) + __ldcg(&ylam[L.lam_y1[l]]);
+    const T di = (T)1 / (__ldcg(&ydiag[L.lam_y0[l]]) + __ldcg(&ydiag[L.lam_y1[l]]));
+    ldinv[l] = di;
+    lam[l] = (T)0;
+    lr[l] = xi;
+    const T zi = xi * di;
+    lz[l] = zi;
+    a2[0] = fma((double)xi, (double)zi, a2[0]);
+    a2[1] = fma((double)xi, (double)xi, a2[1]);
+  }
+  if (!grid_sum<2>(a2, part1, gs.out + 0, gs, sm)) return;
+  double rz = a2[0];
+  const double rr0 = a2[1];
+  double rr = rr0;
+  const double tol2 = tol * tol * rr0;
+  T beta = (T)0;
+  T* pold = pa;
+  T* pnew = pb;
+  int it = 0;
+  bool first = true;
+  while (rr0 > 0.0 && rr > tol2 && it < maxit) {
+    // ylam[k] = kappa_c sum_j Hc[k, j] p_new(lambda_j): one thread per interface slot, rows read contiguously
+    GSTRIDE(k, L.nif) {
+      const int c = L.if_cell[k];
+      const int k0 = L.if_off[c], ni = L.if_off[c + 1] - k0;
+      const T* Hk = Hc + L.hc_off[c] + (size_t)(k - k0) * ni;
+      T y = 0;
+      for (int j = 0; j < ni; ++j) {
+        const int l = L.if_lam[k0 + j];
+        const T v = first ? __ldcg(&lz[l]) : beta * __ldcg(&pold[l]) + __ldcg(&lz[l]);
+        y += Hk[j] * v;
+      }
+      ylam[k] = (T)kapc[c] * y;
+    }
+    if (!grid_barrier(gs)) return;
+    double a1[1] = {0.0};
+    GSTRIDE(l, L.nlam) {
+      const T pl = first ? __ldcg(&lz[l]) : beta * __ldcg(&pold[l]) + __ldcg(&lz[l]);
+      const T y = __ldcg(&ylam[L.lam_y0[l]]) + __ldcg(&ylam[L.lam_y1[l]]);
+      pnew[l] = pl;
+      lq[l] = y;
+      a1[0] = fma((double)pl, (double)y, a1[0]);
+    }
+    if (!grid_sum<1>(a1, part0, gs.out + 2, gs, sm)) return;
+    const double alpha_d = a1[0] != 0.0 ? rz / a1[0] : 0.0;
+    const T alpha = (T)alpha_d;
+    a2[0] = a2[1] = 0.0;
+    GSTRIDE(l, L.nlam) {
+      lam[l] = alpha * pnew[l] + lam[l];
+      const T ri = lr[l] - alpha * lq[l];
+      const T zi = ri * ldinv[l];
+      lr[l] = ri;
+      lz[l] = zi;
+      a2[0] = fma((double)ri, (double)zi, a2[0]);
+      a2[1] = fma((double)ri, (double)ri, a2[1]);
+    }
+    if (!grid_sum<2>(a2, part1, gs.out + 4, gs, sm)) return;
+    beta = (T)(rz != 0.0 ? a2[0] / rz : 0.0);
+    rz = a2[0];
+    rr = a2[1];
+    T* t = pold;
+    pold = pnew;
+    pnew = t;
+    first = false;
+    ++it;
+    if (!(alpha_d != 0.0)) break;
+  }
+  // recovery: sigma^c = kappa A w + B b_p, p_c = B^T w + C b_p / kappa with w = bhat - C^T lambda; one thread per
+  // owned local flux slot, then one per pressure unknown
+  GSTRIDE(y, L.nyl) {
+    if (!L.own0[y]) continue;
+    const int c = L.slot_cell[y];
+    const int mc = L.m[c], lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c], n = nl + mc;
+    const int u = y - lo;
+    const T* Su = Sinv + L.sad_off[c] + (size_t)u * n;
+    T a1 = 0, a2_ = 0;
+    for (int t = 0; t < nl; ++t)
+      if (L.own0[lo + t]) a1 += Su[t] * (T)bs[L.loc[lo + t]];
+    for (int k = L.if_off[c]; k < L.if_off[c + 1]; ++k)
+      a1 -= Su[L.if_slot[k]] * (T)L.if_sign[k] * __ldcg(&lam[L.if_lam[k]]);
+    for (int q = 0; q < mc; ++q) a2_ += Su[nl + q] * (T)bp[po + q];
+    dsig[L.loc[y]] = (double)((T)kapc[c] * a1 + a2_);
+  }
+  GSTRIDE(i, L.np) {
+    const int c = L.p_cell[i];
+    const int mc = L.m[c], lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c], n = nl + mc;
+    const T* Sr = Sinv + L.sad_off[c] + (size_t)(nl + i - po) * n;
+    T a1 = 0, a2_ = 0;
+    for (int t = 0; t < nl; ++t)
+      if (L.own0[lo + t]) a1 += Sr[t] * (T)bs[L.loc[lo + t]];
+    for (int k = L.if_off[c]; k < L.if_off[c + 1]; ++k)
+      a1 -= Sr[L.if_slot[k]] * (T)L.if_sign[k] * __ldcg(&lam[L.if_lam[k]]);
+    for (int q = 0; q < mc; ++q) a2_ += Sr[nl + q] * (T)bp[po + q];
+    dp[i] = (double)a1 + (double)a2_ / kapc[c];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    res->iters = it;
+    res->rr0 = rr0;
+    res->rr = rr;
+  }
+}
+
+int coop_grid(const void* fn, int n_items) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPThreads, 0);
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 2) per_sm = 2;                   // few, wide blocks: cheap barriers and partial sums
+  int maxb = sms * per_sm;
+  int need = (n_items + kPThreads - 1) / kPThreads;
+  if (need < 1) need = 1;
+  return need < maxb ? need : maxb;
+}
+
+}  // namespace
+
+template <class T>
+cudaError_t launch_fine_cg(cudaStream_t st, const FineDev& F, const T* Ts, const double* sdiag, const double* b,
+                           double bscale, double* dx, T* y, T* r, T* pa, T* pb, T* q, double* partial, GridSync gs,
+                           double tol, int maxit, PcgResult* res) {
+  const void* fn = (const void*)kp_fine_cg<T>;
+  int grid = coop_grid(fn, F.N);
+  void* args[] = {(void*)&F, (void*)&Ts, (void*)&sdiag, (void*)&b, (void*)&bscale, (void*)&dx, (void*)&y,
+                  (void*)&r, (void*)&pa, (void*)&pb, (void*)&q, (void*)&partial, (void*)&gs, (void*)&tol,
+                  (void*)&maxit, (void*)&res};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
+}
+template cudaError_t launch_fine_cg<double>(cudaStream_t, const FineDev&, const double*, const double*,
+                                            const double*, double, double*, double*, double*, double*, double*,
+                                            double*, double*, GridSync, double, int, PcgResult*);
+template cudaError_t launch_fine_cg<float>(cudaStream_t, const FineDev&, const float*, const double*, const double*,
+                                           double, double*, float*, float*, float*, float*, float*, double*,
+                                           GridSync, double, int, PcgResult*);
+
+template <class T>
+cudaError_t launch_hyb_solve(cudaStream_t st, const LevelDev& L, const T* Hc, const T* Sinv, const double* kapc,
+                             const double* bs, const double* bp, T* ylam, T* ydiag, T* lam, T* lr, T* lz, T* pa,
+                             T* pb, T* lq, T* ldinv, double* dsig, double* dp, double* partial, GridSync gs,
+                             double tol, int maxit, PcgResult* res) {
+  int items = L.nlam > L.nif ? L.nlam : L.nif;
+  if (L.nyl > items) items = L.nyl;
+  const void* fn = (const void*)kp_hyb_solve<T>;
+  int grid = coop_grid(fn, items);
+  void* args[] = {(void*)&L, (void*)&Hc, (void*)&Sinv, (void*)&kapc, (void*)&bs, (void*)&bp, (void*)&ylam,
+                  (void*)&ydiag, (void*)&lam, (void*)&lr, (void*)&lz, (void*)&pa, (void*)&pb, (void*)&lq,
+                  (void*)&ldinv, (void*)&dsig, (void*)&dp, (void*)&partial, (void*)&gs, (void*)&tol, (void*)&maxit,
+                  (void*)&res};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
+}
+template cudaError_t launch_hyb_solve<double>(cudaStream_t, const LevelDev&, const double*, const double*,
+                                              const double*, const double*, const double*, double*, double*,
+                                              double*, double*, double*, double*, double*, double*, double*,
+                                              double*, double*, double*, GridSync, double, int, PcgResult*);
+template cudaError_t launch_hyb_solve<float>(cudaStream_t, const LevelDev&, const float*, const float*,
+                                             const double*, const double*, const double*, float*, float*, float*,
+                                             float*, float*, float*, float*, float*, float*, double*, double*,
+                                             double*, GridSync, double, int, PcgResult*);
+
+}  // namespace nlmg

@@ -14,6 +14,7 @@
 #include "dense.hpp"
 #include "hier.hpp"
 #include "kernels.cuh"
+#include "persist.cuh"
 
 using namespace nlmg;
 
@@ -36,8 +37,10 @@ struct Error : std::runtime_error {
 struct CoarseBuf {
   double *x = nullptr, *b = nullptr, *r = nullptr, *dx = nullptr, *nb = nullptr, *xt1 = nullptr, *xt2 = nullptr;
   double *xc = nullptr, *yl = nullptr, *kapc = nullptr, *ptmp = nullptr;
-  double *ylam = nullptr, *lam = nullptr, *lr = nullptr, *lz = nullptr, *lpa = nullptr, *lpb = nullptr,
+  double *ylam = nullptr, *ydiag = nullptr, *lam = nullptr, *lr = nullptr, *lz = nullptr, *lpa = nullptr, *lpb = nullptr,
          *lq = nullptr, *ldinv = nullptr, *xi = nullptr;
+  float *f_ylam = nullptr, *f_ydiag = nullptr, *f_lam = nullptr, *f_lr = nullptr, *f_lz = nullptr,
+        *f_lpa = nullptr, *f_lpb = nullptr, *f_lq = nullptr, *f_ldinv = nullptr;
   double rn = 0.0;  // ||A(x) - b|| at the current x (valid after coarse_res)
 };
 
@@ -49,6 +52,8 @@ struct Prof {
   int used = 0;
   double ms[8] = {0};
   long long n[8] = {0};
+  double bytes[8] = {0};
+  double flops[8] = {0};
 };
 
 // Fine-level state: iterate, its kappa and residual.
@@ -80,12 +85,20 @@ struct nlmg_ctx {
   double *f = nullptr, *g = nullptr, *rhs = nullptr, *dkap = nullptr, *Tval = nullptr, *dinv = nullptr,
          *diagT = nullptr, *jdiag = nullptr, *sig0 = nullptr, *ptr_e = nullptr, *fdp = nullptr;
   double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cpa = nullptr, *cpb = nullptr, *cq = nullptr;
+  double *sdiag = nullptr, *Ts64 = nullptr;
+  float *Ts32 = nullptr, *fy = nullptr, *fr = nullptr, *fpa = nullptr, *fpb = nullptr, *fq = nullptr;
   FineState cur, t1, t2;
   bool have_data = false;
   double tol_rel = 1e-8, tol_abs = 1e-10;   // outer tolerances, also used on the coarsest level
   // statistics of the running solve
   long long fine_evals = 0, lin_iters = 0;
+  long long lin_iters_level[8] = {0};
+  long long nnz_real = 0;
+  double hyb_bytes_per_iter[8] = {0};
   Prof prof;
+  PcgResult* d_res = nullptr;   // device result of the persistent CG kernels
+  PcgResult* h_res = nullptr;   // pinned copy
+  unsigned* d_bar = nullptr;    // grid barrier count / generation
   int prof_begin(int k) {
     if (!prof.on) return -1;
     if (prof.used * 2 + 2 > (int)prof.ev.size()) prof_flush();
@@ -176,11 +189,36 @@ void upload_fine(nlmg_ctx* c) {
   }
   FineDev& F = c->F;
   F.N = N;
-  F.nnz = (int)nbr.size();
-  F.row_off = c->upload(off);
-  F.nbr = c->upload(nbr);
-  F.ups_s = c->upload(us);
-  F.ups_n = c->upload(un);
+  F.nslice = (N + 31) / 32;
+  std::vector<int> soff(F.nslice + 1, 0), sw(F.nslice, 0);
+  for (int sl = 0; sl < F.nslice; ++sl) {
+    int w = 0;
+    for (int K = 32 * sl; K < std::min(N, 32 * sl + 32); ++K) w = std::max(w, off[K + 1] - off[K]);
+    sw[sl] = w;
+    soff[sl + 1] = soff[sl] + 32 * w;
+  }
+  std::vector<int> snbr(soff[F.nslice], 0);
+  std::vector<double> sus(soff[F.nslice], 1.0), sun(soff[F.nslice], 0.0);
+  for (int K = 0; K < N; ++K) {
+    int sl = K >> 5, lane = K & 31, deg = off[K + 1] - off[K];
+    for (int j = 0; j < sw[sl]; ++j) {
+      int e = soff[sl] + 32 * j + lane;
+      if (j < deg) {
+        snbr[e] = nbr[off[K] + j];
+        sus[e] = us[off[K] + j];
+        sun[e] = un[off[K] + j];
+      } else {
+        snbr[e] = K;   // padding: Ups = (1, 0) gives a zero transmissibility
+      }
+    }
+  }
+  F.nnz = soff[F.nslice];
+  c->nnz_real = (long long)nbr.size();
+  F.sell_off = c->upload(soff);
+  F.sell_w = c->upload(sw);
+  F.nbr = c->upload(snbr);
+  F.ups_s = c->upload(sus);
+  F.ups_n = c->upload(sun);
   F.dir_off = c->upload(doff);
   F.dir_face = c->upload(dface);
   F.dir_ups = c->upload(dups);
@@ -287,8 +325,19 @@ void upload_level(nlmg_ctx* c, int l) {
   D.if_sign = c->upload(if_sign);
   D.hc_off = c->upload(hc_off);
   D.Hc = c->upload(Hc);
+  D.Hc32 = c->upload(std::vector<float>(Hc.begin(), Hc.end()));
+  D.Sinv32 = c->upload(std::vector<float>(Sinv.begin(), Sinv.end()));
   D.lam_y0 = c->upload(ly0);
   D.lam_y1 = c->upload(ly1);
+  std::vector<int> ifc(if_slot.size()), slc(L.loc.size()), pc(L.n_p());
+  for (int cc = 0; cc < L.n_cells; ++cc) {
+    for (int k = if_off[cc]; k < if_off[cc + 1]; ++k) ifc[k] = cc;
+    for (int k = L.loc_off[cc]; k < L.loc_off[cc + 1]; ++k) slc[k] = cc;
+    for (int k = L.p_off[cc]; k < L.p_off[cc + 1]; ++k) pc[k] = cc;
+  }
+  D.if_cell = c->upload(ifc);
+  D.slot_cell = c->upload(slc);
+  D.p_cell = c->upload(pc);
   CoarseBuf& B = c->CB[l];
   int nx = D.nflux + D.np;
   B.x = c->dalloc<double>(nx);
@@ -303,6 +352,13 @@ void upload_level(nlmg_ctx* c, int l) {
   B.kapc = c->dalloc<double>(D.nc);
   B.ptmp = c->dalloc<double>(nx);
   B.ylam = c->dalloc<double>(D.nif);
+  B.ydiag = c->dalloc<double>(D.nif);
+  B.f_ylam = c->dalloc<float>(D.nif);
+  B.f_ydiag = c->dalloc<float>(D.nif);
+  for (float** pp : {&B.f_lam, &B.f_lr, &B.f_lz, &B.f_lpa, &B.f_lpb, &B.f_lq, &B.f_ldinv}) *pp = c->dalloc<float>(nlam);
+  // algorithmic bytes of one CG iteration of the hybridized solve: H blocks, their lambda ids, the per-interface
+  // buffer written and read, the lambda vectors (z, p_old gathered once; CG update 5 reads + 3 writes)
+  c->hyb_bytes_per_iter[l] = 8.0 * (double)Hc.size() + 12.0 * D.nif + 8.0 * D.nc + 16.0 * D.nif + 136.0 * nlam;
   B.lam = c->dalloc<double>(nlam);
   B.lr = c->dalloc<double>(nlam);
   B.lz = c->dalloc<double>(nlam);
@@ -387,31 +443,43 @@ void backtrack0(nlmg_ctx* c, const double* dp, double s0) {
   std::swap(c->cur, c->t1);
 }
 
-// PCG on the frozen fine matrix (Tval, diagT, dinv): A dx = -R ; result in c->cx. Returns iterations.
+// Persistent CG on the frozen fine matrix (Tval, diagT): A dx = -R with symmetric Jacobi scaling; dx -> c->cx.
+// lin_precision 0 runs it in FP64, 1 in FP32 (vectors and matrix; dot products accumulate in FP64).
 int fine_pcg(nlmg_ctx* c, const double* R) {
-  const int N = c->F.N;
-  launch_pcg_init(c->st, N, R, -1.0, c->dinv, c->cx, c->cr, c->cz, c->d_sc, c->red(S_SCRATCH));
-  double rr0 = c->read_sc(S_RR0);
-  if (!(rr0 > 0.0)) return 0;
-  const double tol2 = c->opt.lin_tol * c->opt.lin_tol * rr0;
-  double* pa = c->cpa;
-  double* pb = c->cpb;
-  int it = 0;
-  for (; it < c->opt.lin_maxit;) {
-    int pi = c->prof_begin(0);
-    launch_fine_spmv(c->st, c->F, c->Tval, c->diagT, c->cz, pa, pb, c->cq, c->d_sc, it == 0, c->red(S_SCRATCH));
-    c->prof_end(pi);
-    pi = c->prof_begin(1);
-    launch_pcg_update(c->st, N, c->cx, c->cr, c->cz, pb, c->cq, c->dinv, c->d_sc, c->red(S_SCRATCH));
-    c->prof_end(pi);
-    std::swap(pa, pb);
-    ++it;
-    if (it % 8 == 0 || it == c->opt.lin_maxit) {
-      double rr = c->read_sc(S_RR);
-      if (!(rr > tol2)) break;
-    }
+  GridSync gs{c->d_bar, c->d_bar + 32, &c->d_res->err, c->d_sc + 32};
+  CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->st));
+  CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
+  launch_sdiag(c->st, c->F.N, c->diagT, c->sdiag);
+  const bool fp32 = c->opt.lin_precision == 1;
+  int pi;
+  if (fp32) {
+    launch_scale_sell<float>(c->st, c->F, c->Tval, c->sdiag, c->Ts32);
+    pi = c->prof_begin(0);
+    CK(launch_fine_cg<float>(c->st, c->F, c->Ts32, c->sdiag, R, -1.0, c->cx, c->fy, c->fr, c->fpa, c->fpb, c->fq,
+                             c->d_partial, gs, std::max(c->opt.lin_tol, 1e-6), c->opt.lin_maxit, c->d_res));
+  } else {
+    launch_scale_sell<double>(c->st, c->F, c->Tval, c->sdiag, c->Ts64);
+    pi = c->prof_begin(0);
+    CK(launch_fine_cg<double>(c->st, c->F, c->Ts64, c->sdiag, R, -1.0, c->cx, c->cz, c->cr, c->cpa, c->cpb, c->cq,
+                              c->d_partial, gs, c->opt.lin_tol, c->opt.lin_maxit, c->d_res));
+  }
+  c->prof_end(pi);
+  count_launch(1);
+  CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(PcgResult), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (c->h_res->err) throw Error(NLMG_ETIMEOUT, "grid barrier wait gave up in the fine CG kernel");
+  const int it = c->h_res->iters;
+  if (pi >= 0) {
+    // per iteration: the scaled matrix entries and their indices, p and r read, p_new and q written (phase A);
+    // p_new, y, r, q read and y, r written (phase B); once: b and S read, y and r written, then S and y read and
+    // dx written. Gathered neighbour values of a vector are counted once.
+    const double N = c->F.N, nnz = (double)c->nnz_real, v = fp32 ? 4.0 : 8.0;
+    c->prof.bytes[0] += (8.0 + 8.0) * N + 2.0 * v * N + 8.0 * N + v * N + 8.0 * N +
+                        it * ((4.0 + v) * nnz + 4.0 * v * N + 6.0 * v * N);
+    c->prof.flops[0] += it * (4.0 * nnz + 10.0 * N);   // FMAs count 2: p on the fly + product per entry
   }
   c->lin_iters += it;
+  c->lin_iters_level[0] += it;
   return it;
 }
 
@@ -487,7 +555,8 @@ void backtrack_coarse(nlmg_ctx* c, int l, const double* dx, double s0) {
   B.rn = r_s;
 }
 
-// Solve the frozen-coefficient saddle A_frozen(x) dx = -r (r, kapc current) by hybridization + PCG -> B.dx.
+// Solve the frozen-coefficient saddle A_frozen(x) dx = -r (r, kapc current) by hybridization + persistent CG
+// -> B.dx. Returns iterations.
 int coarse_linear(nlmg_ctx* c, int l) {
   const LevelDev& L = c->LD[l];
   CoarseBuf& B = c->CB[l];
@@ -495,30 +564,27 @@ int coarse_linear(nlmg_ctx* c, int l) {
   launch_axpy(c->st, nx, B.r, -2.0, B.r, B.nb);   // nb = -r
   const double* bs = B.nb;
   const double* bp = B.nb + L.nflux;
-  int it = 0;
-  if (L.nlam > 0) {
-    launch_hyb_diag(c->st, L, B.kapc, B.ylam, B.ldinv);
-    launch_hyb_rhs(c->st, L, B.kapc, bs, bp, B.ylam, B.xi);
-    launch_pcg_init(c->st, L.nlam, B.xi, 1.0, B.ldinv, B.lam, B.lr, B.lz, c->d_sc, c->red(S_SCRATCH));
-    double rr0 = c->read_sc(S_RR0);
-    if (rr0 > 0.0) {
-      const double tol2 = c->opt.lin_tol * c->opt.lin_tol * rr0;
-      double* pa = B.lpa;
-      double* pb = B.lpb;
-      for (; it < c->opt.lin_maxit;) {
-        launch_hyb_spmv(c->st, L, B.kapc, B.lz, pa, pb, B.lq, B.ylam, c->d_sc, it == 0, c->red(S_SCRATCH));
-        launch_pcg_update(c->st, L.nlam, B.lam, B.lr, B.lz, pb, B.lq, B.ldinv, c->d_sc, c->red(S_SCRATCH));
-        std::swap(pa, pb);
-        ++it;
-        if (it % 8 == 0 || it == c->opt.lin_maxit) {
-          double rr = c->read_sc(S_RR);
-          if (!(rr > tol2)) break;
-        }
-      }
-    }
-  }
-  launch_hyb_recover(c->st, L, B.kapc, bs, bp, B.lam, B.dx, B.dx + L.nflux);
+  GridSync gs{c->d_bar, c->d_bar + 32, &c->d_res->err, c->d_sc + 32};
+  CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->st));
+  CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
+  int pi = c->prof_begin(1);
+  if (c->opt.lin_precision == 1)
+    CK(launch_hyb_solve<float>(c->st, L, L.Hc32, L.Sinv32, B.kapc, bs, bp, B.f_ylam, B.f_ydiag, B.f_lam, B.f_lr,
+                               B.f_lz, B.f_lpa, B.f_lpb, B.f_lq, B.f_ldinv, B.dx, B.dx + L.nflux, c->d_partial, gs,
+                               std::max(c->opt.coarse_lin_tol, 1e-6), c->opt.lin_maxit, c->d_res));
+  else
+    CK(launch_hyb_solve<double>(c->st, L, L.Hc, L.Sinv, B.kapc, bs, bp, B.ylam, B.ydiag, B.lam, B.lr, B.lz, B.lpa,
+                                B.lpb, B.lq, B.ldinv, B.dx, B.dx + L.nflux, c->d_partial, gs, c->opt.coarse_lin_tol,
+                                c->opt.lin_maxit, c->d_res));
+  c->prof_end(pi);
+  count_launch(1);
+  CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(PcgResult), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (c->h_res->err) throw Error(NLMG_ETIMEOUT, "grid barrier wait gave up in the coarse CG kernel");
+  const int it = c->h_res->iters;
+  if (pi >= 0) c->prof.bytes[1] += (double)it * c->hyb_bytes_per_iter[l] * (c->opt.lin_precision == 1 ? 0.5 : 1.0);
   c->lin_iters += it;
+  c->lin_iters_level[l] += it;
   return it;
 }
 
@@ -626,6 +692,10 @@ void alloc_fine(nlmg_ctx* c) {
   c->cpa = c->dalloc<double>(N);
   c->cpb = c->dalloc<double>(N);
   c->cq = c->dalloc<double>(N);
+  c->sdiag = c->dalloc<double>(N);
+  c->Ts64 = c->dalloc<double>(c->F.nnz);
+  c->Ts32 = c->dalloc<float>(c->F.nnz);
+  for (float** pp : {&c->fy, &c->fr, &c->fpa, &c->fpb, &c->fq}) *pp = c->dalloc<float>(N);
   for (FineState* s : {&c->cur, &c->t1, &c->t2}) {
     s->p = c->dalloc<double>(N);
     s->kap = c->dalloc<double>(N);
@@ -675,6 +745,7 @@ nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double
   CK(cudaEventRecord(e0, c->st));
   c->fine_evals = 0;
   c->lin_iters = 0;
+  for (auto& v : c->lin_iters_level) v = 0;
   const long long launches0 = launch_count();
   c->tol_rel = tol_rel;
   c->tol_abs = tol_abs;
@@ -724,6 +795,7 @@ nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double
   R.fine_evals = c->fine_evals;
   R.lin_iters = c->lin_iters;
   R.kernel_launches = launch_count() - launches0;
+  for (int l = 0; l < 8; ++l) R.lin_iters_level[l] = c->lin_iters_level[l];
   c->prof_flush();
   if (rep) *rep = R;
   return st;
@@ -762,6 +834,8 @@ void nlmg_default_options(nlmg_options* o) {
   o->coarsest_steps = 10;
   o->lin_tol = 1e-8;
   o->lin_maxit = 5000;
+  o->coarse_lin_tol = 1e-8;
+  o->lin_precision = 0;
   o->setup_threads = 0;
 }
 
@@ -830,6 +904,10 @@ static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, co
     c->d_cnt = c->dalloc<unsigned>(16);
     CK(cudaMemsetAsync(c->d_cnt, 0, 16 * sizeof(unsigned), c->st));
     c->d_sc = c->dalloc<double>(64);
+    c->d_res = c->dalloc<PcgResult>(1);
+    c->d_bar = c->dalloc<unsigned>(64);   // count and generation on separate 128-byte lines
+    CK(cudaMemsetAsync(c->d_bar, 0, 64 * sizeof(unsigned), c->st));
+    CK(cudaMallocHost(&c->h_res, sizeof(PcgResult)));
     CK(cudaMemsetAsync(c->d_sc, 0, 64 * sizeof(double), c->st));
     upload_fine(c);
     alloc_fine(c);
@@ -1102,13 +1180,13 @@ nlmg_status nlmg_profile(nlmg_ctx* c, int32_t enable) {
       for (auto& e : c->prof.ev) CK(cudaEventCreate(&e));
     }
     c->prof.on = enable != 0;
-    for (int k = 0; k < 8; ++k) { c->prof.ms[k] = 0.0; c->prof.n[k] = 0; }
+    for (int k = 0; k < 8; ++k) { c->prof.ms[k] = 0.0; c->prof.n[k] = 0; c->prof.bytes[k] = 0.0; c->prof.flops[k] = 0.0; }
     return NLMG_OK;
   });
 }
 
 nlmg_status nlmg_profile_read(nlmg_ctx* c, int32_t kernel, int64_t* launches, double* total_ms,
-                              double* bytes_per_launch) {
+                              double* bytes_per_launch, double* flops_per_launch) {
   return guarded(c, [&]() -> nlmg_status {
     need_device(c);
     if (kernel < 0 || kernel > 2) throw Error(NLMG_EINVAL, "kernel id");
@@ -1116,14 +1194,13 @@ nlmg_status nlmg_profile_read(nlmg_ctx* c, int32_t kernel, int64_t* launches, do
     if (launches) *launches = c->prof.n[kernel];
     if (total_ms) *total_ms = c->prof.ms[kernel];
     // algorithmic bytes: every array the kernel streams, read or written once; gathered neighbour values are
-    // counted once (they are the same vector)
-    const double N = c->F.N, nnz = c->F.nnz, ndir = c->F.N > 0 ? 0.0 : 0.0;
-    (void)ndir;
+    // counted once (they are the same vector); SELL padding is not counted
+    const double N = c->F.N, nnz = (double)c->nnz_real;
     double b = 0.0;
-    if (kernel == 0) b = 4.0 * (N + 1) + 12.0 * nnz + 8.0 * N * 5;          // row_off, nbr+Tval, diag,z,pold,pnew,q
-    if (kernel == 1) b = 8.0 * N * 9;                                       // x,r,z,p,q,dinv read; x,r,z written
-    if (kernel == 2) b = 4.0 * (N + 1) + 20.0 * nnz + 8.0 * N * 4;          // row_off, nbr+2 ups, q,kap,rhs,R
+    if (kernel == 0 || kernel == 1) b = c->prof.n[kernel] ? c->prof.bytes[kernel] / c->prof.n[kernel] : 0.0;
+    if (kernel == 2) b = 20.0 * nnz + 8.0 * N * 4;                          // nbr + 2 ups, q, kap, rhs, R
     if (bytes_per_launch) *bytes_per_launch = b;
+    if (flops_per_launch) *flops_per_launch = c->prof.n[kernel] ? c->prof.flops[kernel] / c->prof.n[kernel] : 0.0;
     return NLMG_OK;
   });
 }
@@ -1136,6 +1213,7 @@ void nlmg_destroy(nlmg_ctx* c) {
   for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_sc) cudaFreeHost(c->h_sc);
+  if (c->h_res) cudaFreeHost(c->h_res);
   if (c->st) cudaStreamDestroy(c->st);
   delete c;
 }

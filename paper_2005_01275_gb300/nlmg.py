@@ -36,19 +36,20 @@ class Options(C.Structure):
                 ("smoother", C.c_int32), ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("omega", C.c_double),
                 ("bt_nmax", C.c_int32), ("bt_theta", C.c_double), ("dp_clamp", C.c_double),
                 ("coarsest_steps", C.c_int32), ("lin_tol", C.c_double), ("lin_maxit", C.c_int32),
-                ("setup_threads", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("coarse_lin_tol", C.c_double), ("lin_precision", C.c_int32),
+                ("setup_threads", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class Report(C.Structure):
     _fields_ = [("cycles", C.c_int32), ("early_exit", C.c_int32), ("res0", C.c_double), ("res", C.c_double),
                 ("solve_ms", C.c_double), ("fine_evals", C.c_int64), ("lin_iters", C.c_int64),
-                ("kernel_launches", C.c_int64),
+                ("kernel_launches", C.c_int64), ("lin_iters_level", C.c_int64 * 8),
                 ("history_len", C.c_int32), ("history", C.c_double * 64)]
 
     def as_dict(self):
         return dict(cycles=self.cycles, early_exit=bool(self.early_exit), res0=self.res0, res=self.res,
                     solve_ms=self.solve_ms, fine_evals=self.fine_evals, lin_iters=self.lin_iters,
-                    kernel_launches=self.kernel_launches,
+                    kernel_launches=self.kernel_launches, lin_iters_level=list(self.lin_iters_level),
                     history=list(self.history[:self.history_len]))
 
 
@@ -80,7 +81,7 @@ SIGNATURES = {
     "nlmg_get_aggregates": (C.c_int, [_P, C.c_int32, _I, _I]),
     "nlmg_get_transfer_dense": (C.c_int, [_P, C.c_int32, C.c_int32, _D]),
     "nlmg_profile": (C.c_int, [_P, C.c_int32]),
-    "nlmg_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), _D, _D]),
+    "nlmg_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), _D, _D, _D]),
     "nlmg_last_error": (C.c_char_p, [_P]),
     "nlmg_destroy": (None, [_P]),
 }
@@ -134,7 +135,10 @@ def default_options(**kw):
 def options_from_dict(d):
     """Options from the dictionary used by the synthetic problem configurations."""
     keep = {k: d[k] for k in ("n_levels", "agg_size", "modes", "nu_pre", "nu_post", "omega", "bt_nmax", "bt_theta",
-                              "dp_clamp", "coarsest_steps", "lin_tol", "lin_maxit") if k in d}
+                              "dp_clamp", "coarsest_steps", "lin_tol", "lin_maxit", "coarse_lin_tol",
+                              "lin_precision") if k in d}
+    if "lin_tol" in d and "coarse_lin_tol" not in d:
+        keep["coarse_lin_tol"] = d["lin_tol"]
     if "smoother" in d:
         keep["smoother"] = SMOOTH_PICARD if d["smoother"] == "picard" else SMOOTH_JACOBI
     return default_options(**keep)
@@ -277,8 +281,9 @@ class Context:
         n = C.c_int64(0)
         ms = C.c_double(0)
         by = C.c_double(0)
-        self._check(lib().nlmg_profile_read(self.h, kernel, C.byref(n), C.byref(ms), C.byref(by)))
-        return n.value, ms.value, by.value
+        fl = C.c_double(0)
+        self._check(lib().nlmg_profile_read(self.h, kernel, C.byref(n), C.byref(ms), C.byref(by), C.byref(fl)))
+        return n.value, ms.value, by.value, fl.value
 
     def solve_ptr(self, f_ptr, g_ptr, p_ptr, tol_rel=1e-8, tol_abs=1e-10, max_cycles=50):
         """Host-pointer solve (e.g. pinned torch tensors): the library copies inputs in and p out."""
@@ -286,6 +291,9 @@ class Context:
         st = lib().nlmg_solve(self.h, C.cast(f_ptr, _D), C.cast(g_ptr, _D), None, tol_rel, tol_abs, max_cycles,
                               C.cast(p_ptr, _D), C.byref(rep))
         return rep.as_dict(), st
+
+    def last_error(self):
+        return lib().nlmg_last_error(self.h).decode()
 
     def solve_device(self, f_ptr, g_ptr, x0_ptr, p_ptr, tol_rel=1e-8, tol_abs=1e-10, max_cycles=50):
         """Device-resident solve on raw device pointers (ints), e.g. torch tensor.data_ptr()."""

@@ -189,7 +189,7 @@ def test_other_nonlinearity_and_single_level(nlmg_lib):
     for levels in (1, 2):
         opts = dict(problem_config("cart2d_32").opts, n_levels=levels, agg_size=[27, 8], modes=[3, 3], **TIGHT)
         ctx = nlmg_lib.Context(mesh, KAPPA_INV1P2, 0.0, opts)
-        p, rep, st = ctx.solve(f, g, tol_rel=1e-12, tol_abs=1e-300, max_cycles=80)
+        p, rep, st = ctx.solve(f, g, tol_rel=1e-13, tol_abs=1e-300, max_cycles=80)
         assert st == 0, rep
         assert _rel(p, pstar) <= 1e-10
 
@@ -207,3 +207,15 @@ def test_degenerate_tiny_meshes(nlmg_lib):
         p, rep, st = ctx.solve(f, g, tol_rel=1e-12, tol_abs=1e-300, max_cycles=40)
         assert st == 0, (shape, rep)
         assert _rel(p, pstar) <= 1e-10
+
+
+def test_mixed_precision_cg_reaches_fp64_solution(nlmg_lib):
+    """FP32 CG inside the FP64 nonlinear iteration: the FAS still converges to the FP64 solution p* (the north
+    star's bar for the mixed path: <= 1e-8 relative error after the FP64 outer residual check)."""
+    pr, H, ctx = _setup(nlmg_lib, "chan3d_16", lin_precision=1, lin_tol=1e-6, coarse_lin_tol=1e-6)
+    pstar, _ = newton.solve(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, dp_clamp=pr.opts["dp_clamp"])
+    p, rep, st = ctx.solve(pr.f_cell, pr.g_face, tol_rel=1e-11, tol_abs=1e-300, max_cycles=80)
+    assert st == 0, rep
+    r = tpfa.reduced_residual(pr.mesh, pr.kappa_kind, pr.kappa_a, p, pr.f_cell, pr.g_face)
+    assert np.linalg.norm(r) <= 2e-11 * rep["res0"]
+    assert _rel(p, pstar) <= 1e-8
