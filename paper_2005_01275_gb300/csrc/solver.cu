@@ -14,6 +14,7 @@
 #include "dense.hpp"
 #include "hier.hpp"
 #include "kernels.cuh"
+#include "noalloc.cuh"
 #include "persist.cuh"
 
 using namespace nlmg;
@@ -1201,6 +1202,26 @@ nlmg_status nlmg_profile_read(nlmg_ctx* c, int32_t kernel, int64_t* launches, do
     if (kernel == 2) b = 20.0 * nnz + 8.0 * N * 4;                          // nbr + 2 ups, q, kap, rhs, R
     if (bytes_per_launch) *bytes_per_launch = b;
     if (flops_per_launch) *flops_per_launch = c->prof.n[kernel] ? c->prof.flops[kernel] / c->prof.n[kernel] : 0.0;
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_fine_residual_noalloc(nlmg_ctx* c, const double* p_dev, double* r_dev, double* norm2_dev,
+                                       void* stream) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_data(c);
+    if (!p_dev || !r_dev || !norm2_dev) throw Error(NLMG_EINVAL, "null device pointer");
+    if (c->F.N > kNoallocMaxCells)
+      throw Error(NLMG_EINVAL, "nlmg_fine_residual_noalloc: mesh has " + std::to_string(c->F.N) +
+                                   " cells, more than its fixed scratch holds (" + std::to_string(kNoallocMaxCells) +
+                                   ")");
+    void* scratch = nullptr;
+    std::string err;
+    if (!noalloc_scratch_address(&scratch, err)) throw Error(NLMG_ECUDA, err);
+    // g and [f] are ready: nlmg_set_data synchronizes the context stream before it returns
+    if (!noalloc_residual((cudaStream_t)stream, scratch, c->F, p_dev, c->g, c->rhs, r_dev, norm2_dev, c->kind, c->a,
+                          err))
+      throw Error(NLMG_ECUDA, err);
     return NLMG_OK;
   });
 }

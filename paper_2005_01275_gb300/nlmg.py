@@ -82,6 +82,7 @@ SIGNATURES = {
     "nlmg_get_transfer_dense": (C.c_int, [_P, C.c_int32, C.c_int32, _D]),
     "nlmg_profile": (C.c_int, [_P, C.c_int32]),
     "nlmg_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), _D, _D, _D]),
+    "nlmg_fine_residual_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "nlmg_last_error": (C.c_char_p, [_P]),
     "nlmg_destroy": (None, [_P]),
 }
@@ -291,6 +292,12 @@ class Context:
         st = lib().nlmg_solve(self.h, C.cast(f_ptr, _D), C.cast(g_ptr, _D), None, tol_rel, tol_abs, max_cycles,
                               C.cast(p_ptr, _D), C.byref(rep))
         return rep.as_dict(), st
+
+    def fine_residual_noalloc(self, p_ptr, r_ptr, norm2_ptr, stream_ptr=0):
+        """Allocation-free residual on caller device buffers (raw device pointers); enqueued on stream_ptr."""
+        st = lib().nlmg_fine_residual_noalloc(self.h, _P(p_ptr), _P(r_ptr), _P(norm2_ptr),
+                                               _P(stream_ptr) if stream_ptr else None)
+        return st
 
     def last_error(self):
         return lib().nlmg_last_error(self.h).decode()
