@@ -106,6 +106,68 @@ def cpu_baseline_dict(full_cells):
                       (SAMPLE_SCALE, n, cycles[0], times[0])}
 
 
+def serving_requests(n, seed=4):
+    """Requests shaped like the serving workload: sizes log-uniform in [4096, 65536] cells, 2D or 3D by a fair coin,
+    each with its own log-normal K (sigma 1, correlation 4 cells), Dirichlet data g_L ~ U[0.5, 1.5],
+    g_R ~ U[-0.5, 0.5], kappa = exp(a p) with a ~ U[0.5, 2]."""
+    import numpy as np
+    from synth.grids import cartesian_mesh, lognormal_field, default_options
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        cells = float(np.exp(rng.uniform(np.log(4096), np.log(65536))))
+        if rng.uniform() < 0.5:
+            side = int(round(cells ** 0.5))
+            shape = (side, side)
+            opts = default_options(n_levels=3, agg_size=[16, 8], modes=[2, 2])
+        else:
+            side = int(round(cells ** (1.0 / 3.0)))
+            shape = (side, side, side)
+            opts = default_options(n_levels=3, agg_size=[64, 8], modes=[4, 4])
+        K = lognormal_field(shape, 1.0, 4.0, seed=1000 + seed * 97 + i)
+        mesh = cartesian_mesh(shape, K)
+        a = float(rng.uniform(0.5, 2.0))
+        opts["dp_clamp"] = float(np.log(1.5) / a)
+        g = np.zeros(mesh.n_faces)
+        d = np.where(mesh.face_bc == 1)[0]
+        g[d] = np.where(mesh.face_cells[d, 0] % shape[0] == 0, rng.uniform(0.5, 1.5), rng.uniform(-0.5, 0.5))
+        out.append((mesh, a, opts, np.zeros(mesh.n_cells), g))
+    return out
+
+
+def run_serving(nlmg, n):
+    """Burst of n requests through the library's request loop (mixed precision), against the same requests solved
+    one at a time in plain FP64 (setup excluded there, as in the main metric)."""
+    import numpy as np
+    reqs = serving_requests(n)
+    srv = nlmg.Server(max_inflight=8, mem_budget_bytes=32 << 30, setup_threads_per_request=2)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(m, 0, a, dict(o, lin_precision=1), f, g) for m, a, o, f, g in reqs]
+    lat, solve_ms, setup_ms, ok = [], [], [], 0
+    for t in tickets:
+        p, rep, tm, st = srv.poll(t, wait_ms=600000)
+        ok += st == 0
+        lat.append(tm["latency_ms"])
+        solve_ms.append(tm["solve_ms"])
+        setup_ms.append(tm["setup_ms"])
+    makespan = time.perf_counter() - t0
+    srv.close()
+    seq_ms = 0.0
+    for m, a, o, f, g in reqs:
+        ctx = nlmg.Context(m, 0, a, o)
+        _, rep, st = ctx.solve(f, g, max_cycles=60)
+        seq_ms += rep["solve_ms"]
+        ctx.close()
+    lat = np.array(lat)
+    return {"requests": n, "ok": int(ok), "sizes_cells": [int(r[0].n_cells) for r in reqs],
+            "solves_per_s_incl_setup": n / makespan, "makespan_s": makespan,
+            "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
+            "mean_setup_ms": float(np.mean(setup_ms)), "mean_solve_ms_in_mix": float(np.mean(solve_ms)),
+            "sequential_fp64_solves_per_s_excl_setup": n / (seq_ms / 1e3),
+            "what": "burst arrival at t=0, max 8 in flight, each request its own hierarchy (host setup) and stream, "
+                    "FP32 CG inside the FP64 FAS; latency = submit -> result"}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return 0
@@ -266,6 +328,7 @@ def run_gpu(args, rank, world, local_rank):
                  "rel_diff_vs_fp64_solution": diff, "lin_iters_level": mrep["lin_iters_level"][:3],
                  "what": "same FP64 FAS (residuals, transfers, coarse operators, convergence test in FP64); the CG "
                          "solves inside the Picard steps in FP32 (tolerances floored at 1e-6)"}
+    serving = run_serving(nlmg, args.serving) if (args.serving > 0 and world == 1) else None
     cpu = cpu_baseline_dict(N) if (args.cpu_baseline and world == 1) else None
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -273,8 +336,8 @@ def run_gpu(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": N, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "256 MiB buffer written between steps, outside each step's CUDA-event pair",
-                   "setup_s": round(setup_s, 3), "lin_tol": pr.opts.get("lin_tol", 1e-8),
-                   "coarse_lin_tol": pr.opts.get("coarse_lin_tol", pr.opts.get("lin_tol", 1e-8))},
+                   "setup_s": round(setup_s, 3), "lin_tol": ctx.opts.lin_tol,
+                   "coarse_lin_tol": ctx.opts.coarse_lin_tol},
         "vcycle_dof_per_s": N * cycles * world / (ms_step / 1e3),
         "cycles_per_solve": cycles,
         "lin_iters_per_solve": sum(r["lin_iters"] for r in reps) / len(reps),
@@ -282,6 +345,7 @@ def run_gpu(args, rank, world, local_rank):
         "wall_s_timed_region": wall,
         "roofline": roof,
         "mixed": mixed,
+        "serving": serving,
         "cpu_baseline": cpu,
         "e2e": {"value": world * len(e2e_t) / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * (N + len(pr.g_face)),
                 "d2h_bytes_per_step": 8 * N},
@@ -305,6 +369,7 @@ def main():
     ap.add_argument("--lin-tol", type=float, default=None, help="level-0 CG tolerance (default: library's)")
     ap.add_argument("--coarse-lin-tol", type=float, default=None, help="coarse CG tolerance")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false", help="skip the FP32-CG variant")
+    ap.add_argument("--serving", type=int, default=24, help="requests in the serving run (0 = skip)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if "RANK" in os.environ else 1))

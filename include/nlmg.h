@@ -76,9 +76,9 @@ typedef struct {
   double bt_theta;           /* Algorithm 1: theta (paper: 0.9) */
   double dp_clamp;           /* Sec. 4.1 pressure-change clamp; <= 0 disables */
   int32_t coarsest_steps;    /* Picard steps on the coarsest level (paper: <= 10) */
-  double lin_tol;            /* relative tolerance of the level-0 CG solves inside Picard steps */
+  double lin_tol;            /* relative tolerance of the level-0 CG solves inside Picard steps (default 1e-2) */
   int32_t lin_maxit;         /* iteration cap of the CG solves */
-  double coarse_lin_tol;     /* relative tolerance of the coarse-level (hybridized) CG solves */
+  double coarse_lin_tol;     /* relative tolerance of the coarse-level (hybridized) CG solves (default 1e-1) */
   int32_t lin_precision;     /* 0: CG in FP64; 1: CG vectors and matrices in FP32 (tolerances floored at 1e-6),
                                 inside the FP64 nonlinear iteration */
   int32_t setup_threads;     /* host threads for the setup (0 = all) */
@@ -136,6 +136,12 @@ nlmg_status nlmg_solve_device(nlmg_ctx* ctx, const double* f_dev, const double* 
 nlmg_status nlmg_solve_picard(nlmg_ctx* ctx, const double* f_cell, const double* g_face, const double* x0,
                               double tol_rel, double tol_abs, int32_t max_cycles, double* p_out, nlmg_report* rep);
 
+/* Single-level Newton baseline (Sec. 2.2; linearisation of Sec. 3.3.2 on level 0): the exact Jacobian of the TPFA
+ * residual (assembled on the device in the SELL layout), restarted GMRES(30) with Jacobi right preconditioning to
+ * lin_tol, then the clamp and Algorithm 1. Host buffers; max_cycles bounds the Newton iterations. */
+nlmg_status nlmg_solve_newton(nlmg_ctx* ctx, const double* f_cell, const double* g_face, const double* x0,
+                              double tol_rel, double tol_abs, int32_t max_cycles, double* p_out, nlmg_report* rep);
+
 /* ---- single steps of the path, for parity tests (host buffers; problem data from nlmg_set_data) ------------ */
 
 /* R(p) (reduced TPFA residual, net outgoing flux minus [f]) at p[n_cells] -> r_out[n_cells]. */
@@ -170,6 +176,36 @@ nlmg_status nlmg_get_aggregates(nlmg_ctx* ctx, int32_t level, int32_t* agg_of, i
 /* Dense export of a transfer matrix of step l -> l+1: which 0 = P_p (n_p(l) x n_p(l+1)), 1 = P_sigma
  * (n_flux(l) x n_flux(l+1)), 2 = Q_sigma (n_flux(l+1) x n_flux(l)); row-major into dense (caller-sized). */
 nlmg_status nlmg_get_transfer_dense(nlmg_ctx* ctx, int32_t level, int32_t which, double* dense);
+
+/* ---- request loop (continuous batching of independent solves) -------------------------------------------- */
+/* Not a step of the paper's method: a serving layer over the calls above. Requests are queued on submit and taken in
+ * arrival order by up to max_inflight worker threads as soon as their estimated device memory fits in
+ * mem_budget_bytes; each request gets its own context (hierarchy built on the host with setup_threads_per_request
+ * threads) and CUDA stream, so requests that arrive while others run are admitted as slots and memory free up and
+ * their GPU work overlaps. A request's result is the same alone and in any mix (each context owns its buffers and
+ * every reduction has a fixed order). All pointers are host pointers, copied at submit. */
+typedef struct nlmg_server nlmg_server;
+typedef struct {
+  int32_t max_inflight;
+  size_t mem_budget_bytes;
+  int32_t setup_threads_per_request;
+} nlmg_server_options;
+typedef struct {
+  double queue_ms, setup_ms, solve_ms, latency_ms;   /* latency = submit -> result ready */
+} nlmg_request_times;
+void nlmg_server_default_options(nlmg_server_options* opt);
+/* Uses the calling thread's current CUDA device. */
+nlmg_status nlmg_server_create(const nlmg_server_options* opt, nlmg_server** out);
+/* Returns NLMG_ENOMEM if the request alone exceeds the memory budget. *ticket identifies the request. */
+nlmg_status nlmg_server_submit(nlmg_server* srv, const nlmg_mesh* mesh, const nlmg_kappa* kappa,
+                               const nlmg_options* opt, const double* f_cell, const double* g_face, double tol_rel,
+                               double tol_abs, int32_t max_cycles, uint64_t* ticket);
+/* Waits up to wait_ms (0: no wait) for the request; NLMG_ETIMEOUT if it is not done yet. Once a result is returned
+ * (p_out[n_cells], rep, times; each may be NULL) the ticket is released. Returns the request's solve status. */
+nlmg_status nlmg_server_poll(nlmg_server* srv, uint64_t ticket, int32_t wait_ms, double* p_out, nlmg_report* rep,
+                             nlmg_request_times* times);
+/* Finishes the queued requests, joins the workers and frees the server. */
+void nlmg_server_destroy(nlmg_server* srv);
 
 /* ---- measurement ----------------------------------------------------------------------------------------- */
 /* Enables (1) or disables (0) CUDA-event timing of the hot kernels on the context stream and clears the counters.

@@ -4,6 +4,7 @@
 // throughput is low, so each kernel does the minimum FP64 work: kappa is evaluated once per cell (k_kappa) and read
 // back by the residual, and the Picard steps freeze the face transmissibilities once (k_residual with Tval) so
 // that the CG iterations only stream the frozen matrix.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(FineDev F, const double* 
                                                        const double* __restrict__ rhs, double* __restrict__ R,
                                                        double* __restrict__ Tval, double* __restrict__ dinv,
                                                        double* __restrict__ diagT, double* __restrict__ jdiag,
-                                                       Reduce red) {
+                                                       double* __restrict__ Joff, Reduce red) {
   double acc[1] = {0.0};
   GRID_STRIDE(K, F.N) {
     const double qK = q[K], kK = kap[K];
@@ -136,6 +137,11 @@ __global__ void __launch_bounds__(kThreads) k_residual(FineDev F, const double* 
       dsum += T;
       if (Tval) Tval[e] = T;
       if (jdiag) jd += T + t * t * dkK * us * diff;
+      // dR_K/dp_L = -Ups + (Ups/hb)^2 kappa'(p_L) Ups_bar_L (p_K - p_L), Ups/hb = ha / (ha + hb)
+      if (Joff) {
+        const double tb = ha / (ha + hb);
+        Joff[e] = -T + tb * tb * dkap[L] * F.ups_n[e] * diff;
+      }
     }
     for (int e = F.dir_off[K]; e < F.dir_off[K + 1]; ++e) {
       const double h = kK * F.dir_ups[e];
@@ -210,6 +216,85 @@ __global__ void k_fine_flux(FineDev F, const double* __restrict__ p, const doubl
     }
     sigma[j] = s;
   }
+}
+
+// ---- GMRES helpers (single-level Newton baseline) ---------------------------------------------------------------
+
+// w = J (dinv .* v) with J = jdiag on the diagonal and Joff off it (SELL layout): the right-preconditioned operator
+__global__ void k_jac_apply(FineDev F, const double* __restrict__ jdiag, const double* __restrict__ Joff,
+                            const double* __restrict__ dinv, const double* __restrict__ v, double* __restrict__ w) {
+  GRID_STRIDE(K, F.N) {
+    double y = jdiag[K] * dinv[K] * v[K];
+    const int wdt = F.sell_w[K >> 5];
+    int e = F.sell_off[K >> 5] + (K & 31);
+    for (int j = 0; j < wdt; ++j, e += 32) {
+      const int L = F.nbr[e];
+      y = fma(Joff[e], dinv[L] * v[L], y);
+    }
+    w[K] = y;
+  }
+}
+
+// h[k] = V_k . w for k < nk (V stored as nk consecutive vectors of length n); fixed-order grid reduction per k
+__global__ void k_mdot(int n, int nk, const double* __restrict__ V, const double* __restrict__ w, double* partial,
+                       unsigned* counter, double* h) {
+  __shared__ double sm[32];
+  __shared__ int am_last;
+  for (int k = 0; k < nk; ++k) {
+    double acc[1] = {0.0};
+    const double* Vk = V + (size_t)k * n;
+    GRID_STRIDE(i, n) acc[0] = fma(Vk[i], w[i], acc[0]);
+    block_reduce<1, false>(acc, sm);
+    if (threadIdx.x == 0) partial[(size_t)k * gridDim.x + blockIdx.x] = acc[0];
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  for (int k = 0; k < nk; ++k) {
+    double acc[1] = {0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc[0] += __ldcg(&partial[(size_t)k * gridDim.x + b]);
+    block_reduce<1, false>(acc, sm);
+    if (threadIdx.x == 0) h[k] = acc[0];
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// w -= sum_k h[k] V_k ; then the norm of the result (grid reduction into red.out)
+__global__ void k_orth_update(int n, int nk, const double* __restrict__ V, const double* __restrict__ h,
+                              double* __restrict__ w, Reduce red) {
+  double acc[1] = {0.0};
+  GRID_STRIDE(i, n) {
+    double v = w[i];
+    for (int k = 0; k < nk; ++k) v = fma(-h[k], V[(size_t)k * n + i], v);
+    w[i] = v;
+    acc[0] = fma(v, v, acc[0]);
+  }
+  grid_reduce<1, false>(acc, red);
+}
+
+__global__ void k_scale_vec(int n, const double* __restrict__ x, double s, double* __restrict__ y) {
+  GRID_STRIDE(i, n) y[i] = s * x[i];
+}
+
+// x = dinv .* (sum_k y[k] V_k)   (dinv may be null: no scaling)
+__global__ void k_gmres_combine(int n, int nk, const double* __restrict__ V, const double* __restrict__ y,
+                                const double* __restrict__ dinv, double* __restrict__ x) {
+  GRID_STRIDE(i, n) {
+    double v = 0.0;
+    for (int k = 0; k < nk; ++k) v = fma(y[k], V[(size_t)k * n + i], v);
+    x[i] = dinv ? dinv[i] * v : v;
+  }
+}
+
+// Jacobi scaling of the Newton system, with the same safeguard as the Jacobi smoother: 1 / max(J_KK, d_K / 2)
+__global__ void k_jacobi_dinv(int n, const double* __restrict__ jdiag, const double* __restrict__ diagT,
+                              double* __restrict__ out) {
+  GRID_STRIDE(i, n) out[i] = 1.0 / fmax(jdiag[i], 0.5 * diagT[i]);
 }
 
 // ---- transfers -------------------------------------------------------------------------------------------------
@@ -366,9 +451,9 @@ void launch_rhs(cudaStream_t st, const FineDev& F, const double* f, const double
 }
 void launch_residual(cudaStream_t st, const FineDev& F, const double* q, const double* kap, const double* dkap,
                      const double* g, const double* rhs, double* R, double* Tval, double* dinv, double* diagT,
-                     double* jdiag, Reduce red) {
+                     double* jdiag, Reduce red, double* Joff) {
   COUNT(1);
-  k_residual<<<grid_for(F.N), kThreads, 0, st>>>(F, q, kap, dkap, g, rhs, R, Tval, dinv, diagT, jdiag, red);
+  k_residual<<<grid_for(F.N), kThreads, 0, st>>>(F, q, kap, dkap, g, rhs, R, Tval, dinv, diagT, jdiag, Joff, red);
 }
 void launch_jacobi_update(cudaStream_t st, int n, const double* q, const double* R, const double* jdiag,
                           const double* diagT, double omega, double* qnew) {
@@ -413,6 +498,33 @@ void launch_coarse_cell(cudaStream_t st, const LevelDev& L, const double* sig, c
   k_coarse_kappa<<<grid_for(L.nc), kThreads, 0, st>>>(L, p, kapc, kind, a);
   k_coarse_slots<<<grid_for(L.nyl), kThreads, 0, st>>>(L, sig, p, kapc, yl);
   k_coarse_prows<<<grid_for(L.np), kThreads, 0, st>>>(L, sig, bp, rp, red);
+}
+void launch_jac_apply(cudaStream_t st, const FineDev& F, const double* jdiag, const double* Joff,
+                      const double* dinv, const double* v, double* w) {
+  COUNT(1);
+  k_jac_apply<<<grid_for(F.N), kThreads, 0, st>>>(F, jdiag, Joff, dinv, v, w);
+}
+void launch_mdot(cudaStream_t st, int n, int nk, const double* V, const double* w, double* partial,
+                 unsigned* counter, double* h) {
+  COUNT(1);
+  k_mdot<<<std::min(grid_for(n), 256), kThreads, 0, st>>>(n, nk, V, w, partial, counter, h);
+}
+void launch_orth_update(cudaStream_t st, int n, int nk, const double* V, const double* h, double* w, Reduce red) {
+  COUNT(1);
+  k_orth_update<<<grid_for(n), kThreads, 0, st>>>(n, nk, V, h, w, red);
+}
+void launch_scale_vec(cudaStream_t st, int n, const double* x, double s, double* y) {
+  COUNT(1);
+  k_scale_vec<<<grid_for(n), kThreads, 0, st>>>(n, x, s, y);
+}
+void launch_gmres_combine(cudaStream_t st, int n, int nk, const double* V, const double* y, const double* dinv,
+                          double* x) {
+  COUNT(1);
+  k_gmres_combine<<<grid_for(n), kThreads, 0, st>>>(n, nk, V, y, dinv, x);
+}
+void launch_jacobi_dinv(cudaStream_t st, int n, const double* jdiag, const double* diagT, double* out) {
+  COUNT(1);
+  k_jacobi_dinv<<<grid_for(n), kThreads, 0, st>>>(n, jdiag, diagT, out);
 }
 void launch_sdiag(cudaStream_t st, int n, const double* diagT, double* sdiag) {
   COUNT(1);

@@ -89,7 +89,16 @@ void launch_kappa(cudaStream_t st, int n, const double* p, const double* dp, dou
 void launch_rhs(cudaStream_t st, const FineDev& F, const double* f, const double* g, double* rhs);
 void launch_residual(cudaStream_t st, const FineDev& F, const double* q, const double* kap, const double* dkap,
                      const double* g, const double* rhs, double* R, double* Tval, double* dinv, double* diagT,
-                     double* jdiag, Reduce red);
+                     double* jdiag, Reduce red, double* Joff = nullptr);
+void launch_jac_apply(cudaStream_t st, const FineDev& F, const double* jdiag, const double* Joff,
+                      const double* dinv, const double* v, double* w);
+void launch_mdot(cudaStream_t st, int n, int nk, const double* V, const double* w, double* partial,
+                 unsigned* counter, double* h);
+void launch_orth_update(cudaStream_t st, int n, int nk, const double* V, const double* h, double* w, Reduce red);
+void launch_scale_vec(cudaStream_t st, int n, const double* x, double s, double* y);
+void launch_jacobi_dinv(cudaStream_t st, int n, const double* jdiag, const double* diagT, double* out);
+void launch_gmres_combine(cudaStream_t st, int n, int nk, const double* V, const double* y, const double* dinv,
+                          double* x);
 void launch_jacobi_update(cudaStream_t st, int n, const double* q, const double* R, const double* jdiag,
                           const double* diagT, double omega, double* qnew);
 void launch_max_abs(cudaStream_t st, int n, const double* x, Reduce red);

@@ -87,6 +87,10 @@ struct nlmg_ctx {
          *diagT = nullptr, *jdiag = nullptr, *sig0 = nullptr, *ptr_e = nullptr, *fdp = nullptr;
   double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cpa = nullptr, *cpb = nullptr, *cq = nullptr;
   double *sdiag = nullptr, *Ts64 = nullptr;
+  // Newton baseline: Jacobian off-diagonals, Jacobi scaling, GMRES(30) basis and work vectors
+  static constexpr int kGmresM = 30;
+  double *Joff = nullptr, *jdinv = nullptr, *gV = nullptr, *gw = nullptr, *gu = nullptr, *gr = nullptr,
+         *gh = nullptr, *h_gh = nullptr;
   float *Ts32 = nullptr, *fy = nullptr, *fr = nullptr, *fpa = nullptr, *fpb = nullptr, *fq = nullptr;
   FineState cur, t1, t2;
   bool have_data = false;
@@ -484,6 +488,128 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
   return it;
 }
 
+void alloc_newton(nlmg_ctx* c) {
+  if (c->Joff) return;
+  const int N = c->F.N;
+  c->Joff = c->dalloc<double>(c->F.nnz);
+  c->jdinv = c->dalloc<double>(N);
+  c->gV = c->dalloc<double>((size_t)(nlmg_ctx::kGmresM + 1) * N);
+  c->gw = c->dalloc<double>(N);
+  c->gu = c->dalloc<double>(N);
+  c->gr = c->dalloc<double>(N);
+  c->gh = c->dalloc<double>(3 * 64);
+  CK(cudaMallocHost(&c->h_gh, 3 * 64 * sizeof(double)));
+}
+
+// Restarted GMRES(30) with right Jacobi preconditioning for J dx = -R (Sec. 3.3.2's linear system on level 0, the
+// single-level Newton baseline); classical Gram-Schmidt with one reorthogonalisation. dx -> c->cx.
+int fine_gmres(nlmg_ctx* c, const double* R) {
+  const int N = c->F.N, m = nlmg_ctx::kGmresM;
+  double* V = c->gV;
+  double* hA = c->gh;            // first Gram-Schmidt coefficients
+  double* hB = c->gh + 64;       // reorthogonalisation coefficients
+  auto norm = [&](double* x) {   // ||x|| (orthogonalisation against no vectors)
+    launch_orth_update(c->st, N, 0, V, hA, x, c->red(S_NORM2B));
+    return std::sqrt(c->read_sc(S_NORM2B));
+  };
+  CK(cudaMemsetAsync(c->gu, 0, (size_t)N * sizeof(double), c->st));
+  launch_scale_vec(c->st, N, R, -1.0, c->gr);       // r = b = -R (u = 0)
+  const double beta0 = norm(c->gr);
+  double beta = beta0;
+  int total = 0;
+  if (!(beta0 > 0.0)) {
+    CK(cudaMemsetAsync(c->cx, 0, (size_t)N * sizeof(double), c->st));
+    return 0;
+  }
+  const double tol = c->opt.lin_tol * beta0;
+  {
+    const double one = 1.0;
+    CK(cudaMemcpyAsync(c->gh + 191, &one, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  }
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), gvec(m + 1);
+  while (true) {
+    launch_scale_vec(c->st, N, c->gr, 1.0 / beta, V);
+    std::fill(gvec.begin(), gvec.end(), 0.0);
+    gvec[0] = beta;
+    int j = 0;
+    double res = beta;
+    for (; j < m; ++j) {
+      double* vj1 = V + (size_t)(j + 1) * N;
+      launch_jac_apply(c->st, c->F, c->jdiag, c->Joff, c->jdinv, V + (size_t)j * N, c->gw);
+      launch_mdot(c->st, N, j + 1, V, c->gw, c->d_partial, c->d_cnt + 8, hA);
+      launch_orth_update(c->st, N, j + 1, V, hA, c->gw, c->red(S_NORM2B));
+      launch_mdot(c->st, N, j + 1, V, c->gw, c->d_partial, c->d_cnt + 8, hB);
+      launch_orth_update(c->st, N, j + 1, V, hB, c->gw, c->red(S_NORM2B));
+      CK(cudaMemcpyAsync(c->h_gh, c->gh, 128 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      const double wn = std::sqrt(c->read_sc(S_NORM2B));   // synchronizes the stream
+      for (int k = 0; k <= j; ++k) H[(size_t)k * m + j] = c->h_gh[k] + c->h_gh[64 + k];
+      H[(size_t)(j + 1) * m + j] = wn;
+      for (int k = 0; k < j; ++k) {   // previous rotations
+        const double a = H[(size_t)k * m + j], b = H[(size_t)(k + 1) * m + j];
+        H[(size_t)k * m + j] = cs[k] * a + sn[k] * b;
+        H[(size_t)(k + 1) * m + j] = -sn[k] * a + cs[k] * b;
+      }
+      const double a = H[(size_t)j * m + j], b = H[(size_t)(j + 1) * m + j];
+      const double r = std::hypot(a, b);
+      cs[j] = r > 0 ? a / r : 1.0;
+      sn[j] = r > 0 ? b / r : 0.0;
+      H[(size_t)j * m + j] = r;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      gvec[j + 1] = -sn[j] * gvec[j];
+      gvec[j] = cs[j] * gvec[j];
+      res = std::fabs(gvec[j + 1]);
+      ++total;
+      if (wn > 0.0) launch_scale_vec(c->st, N, c->gw, 1.0 / wn, vj1);
+      if (res <= tol || wn == 0.0 || total >= c->opt.lin_maxit) {
+        ++j;
+        break;
+      }
+    }
+    // y = H(0:j, 0:j)^-1 g ; u += V y
+    std::vector<double> y(j, 0.0);
+    for (int k = j - 1; k >= 0; --k) {
+      double v = gvec[k];
+      for (int q = k + 1; q < j; ++q) v -= H[(size_t)k * m + q] * y[q];
+      y[k] = H[(size_t)k * m + k] != 0.0 ? v / H[(size_t)k * m + k] : 0.0;
+    }
+    CK(cudaMemcpyAsync(c->gh + 128, y.data(), j * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    launch_gmres_combine(c->st, N, j, V, c->gh + 128, nullptr, c->gw);   // u += V y
+    launch_axpy(c->st, N, c->gu, 1.0, c->gw, c->gu);
+    if (res <= tol || total >= c->opt.lin_maxit) break;
+    // true residual r = b - J D u
+    launch_jac_apply(c->st, c->F, c->jdiag, c->Joff, c->jdinv, c->gu, c->gw);
+    launch_scale_vec(c->st, N, c->gw, -1.0, c->gr);       // r = -J D u ...
+    launch_axpy(c->st, N, c->gr, -1.0, R, c->gr);         // ... - R = b - J D u
+    beta = norm(c->gr);
+    if (!(beta > tol)) break;
+  }
+  // dx = D u
+  launch_gmres_combine(c->st, N, 1, c->gu, c->gh + 191, c->jdinv, c->cx);   // dx = D u (weight gh[191] = 1)
+  c->lin_iters += total;
+  c->lin_iters_level[0] += total;
+  return total;
+}
+
+// One single-level Newton step (Sec. 3.3.2 on level 0): exact Jacobian, GMRES, clamp, Algorithm 1.
+void newton_step(nlmg_ctx* c) {
+  alloc_newton(c);
+  const int N = c->F.N;
+  launch_kappa(c->st, N, c->cur.p, nullptr, 0.0, c->cur.p, c->t2.kap, c->dkap, c->kind, c->a);
+  launch_residual(c->st, c->F, c->cur.p, c->t2.kap, c->dkap, c->g, c->rhs, c->t2.R, nullptr, nullptr, c->diagT,
+                  c->jdiag, c->red(S_NORM2B), c->Joff);
+  launch_jacobi_dinv(c->st, N, c->jdiag, c->diagT, c->jdinv);
+  fine_gmres(c, c->cur.R);
+  double s0 = 1.0;
+  if (c->opt.dp_clamp > 0) {
+    launch_max_abs(c->st, N, c->cx, c->red(S_MAX));
+    double mx = c->read_sc(S_MAX);
+    if (mx > c->opt.dp_clamp) s0 = c->opt.dp_clamp / mx;
+  }
+  backtrack0(c, c->cx, s0);
+}
+
 // One smoothing step on level 0 (Picard or nonlinear Jacobi), then the clamp and Algorithm 1.
 void smooth0(nlmg_ctx* c, int nu) {
   const nlmg_options& o = c->opt;
@@ -737,8 +863,10 @@ void set_data_host(nlmg_ctx* c, const double* f, const double* g) {
 }
 
 // Full solve on device data already set; x0 device pointer or null. Returns status.
+// mode: 0 FAS cycles, 1 single-level Picard steps, 2 single-level Newton steps
 nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double tol_abs, int max_cycles,
-                       double* p_dev, nlmg_report* rep, bool picard_only) {
+                       double* p_dev, nlmg_report* rep, int mode) {
+  const bool picard_only = mode == 1;
   const int N = c->F.N;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -769,7 +897,9 @@ nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double
     if (!std::isfinite(rn)) { st = NLMG_EDIVERGED; break; }
     if (rn <= tol_rel * r0 || rn <= tol_abs) break;
     if (cycles >= max_cycles) { st = NLMG_ENOCONV; break; }
-    if (picard_only) {
+    if (mode == 2) {
+      newton_step(c);
+    } else if (picard_only) {
       smooth0(c, 1);
     } else {
       early = vcycle(c, r0, tol_rel, tol_abs);
@@ -833,9 +963,9 @@ void nlmg_default_options(nlmg_options* o) {
   o->bt_theta = 0.9;
   o->dp_clamp = 0.0;
   o->coarsest_steps = 10;
-  o->lin_tol = 1e-8;
+  o->lin_tol = 1e-2;          // inner solves of the Picard smoothing steps (see the readings in the design notes)
   o->lin_maxit = 5000;
-  o->coarse_lin_tol = 1e-8;
+  o->coarse_lin_tol = 1e-1;
   o->lin_precision = 0;
   o->setup_threads = 0;
 }
@@ -950,7 +1080,7 @@ nlmg_status nlmg_solve(nlmg_ctx* c, const double* f_cell, const double* g_face, 
       CK(cudaMemcpyAsync(c->fdp, x0, (size_t)c->F.N * sizeof(double), cudaMemcpyHostToDevice, c->st));
       x0d = c->fdp;
     }
-    nlmg_status s = solve_core(c, x0d, tol_rel, tol_abs, max_cycles, c->cx, rep, false);
+    nlmg_status s = solve_core(c, x0d, tol_rel, tol_abs, max_cycles, c->fdp, rep, 0);
     CK(cudaMemcpyAsync(p_out, c->cur.p, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     return s;
@@ -963,7 +1093,7 @@ nlmg_status nlmg_solve_device(nlmg_ctx* c, const double* f_dev, const double* g_
     need_device(c);
     if (!f_dev || !g_dev || !p_dev) throw Error(NLMG_EINVAL, "null argument");
     set_data_dev(c, f_dev, g_dev);
-    nlmg_status s = solve_core(c, x0_dev, tol_rel, tol_abs, max_cycles, p_dev, rep, false);
+    nlmg_status s = solve_core(c, x0_dev, tol_rel, tol_abs, max_cycles, p_dev, rep, 0);
     CK(cudaStreamSynchronize(c->st));
     return s;
   });
@@ -980,13 +1110,31 @@ nlmg_status nlmg_solve_picard(nlmg_ctx* c, const double* f_cell, const double* g
       CK(cudaMemcpyAsync(c->fdp, x0, (size_t)c->F.N * sizeof(double), cudaMemcpyHostToDevice, c->st));
       x0d = c->fdp;
     }
-    nlmg_status s = solve_core(c, x0d, tol_rel, tol_abs, max_cycles, c->cx, rep, true);
+    nlmg_status s = solve_core(c, x0d, tol_rel, tol_abs, max_cycles, c->fdp, rep, 1);
     CK(cudaMemcpyAsync(p_out, c->cur.p, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     return s;
   });
 }
 
+
+nlmg_status nlmg_solve_newton(nlmg_ctx* c, const double* f_cell, const double* g_face, const double* x0,
+                              double tol_rel, double tol_abs, int32_t max_cycles, double* p_out, nlmg_report* rep) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_device(c);
+    if (!f_cell || !g_face || !p_out) throw Error(NLMG_EINVAL, "null argument");
+    set_data_host(c, f_cell, g_face);
+    const double* x0d = nullptr;
+    if (x0) {
+      CK(cudaMemcpyAsync(c->fdp, x0, (size_t)c->F.N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      x0d = c->fdp;
+    }
+    nlmg_status s = solve_core(c, x0d, tol_rel, tol_abs, max_cycles, c->fdp, rep, 2);
+    CK(cudaMemcpyAsync(p_out, c->cur.p, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return s;
+  });
+}
 
 nlmg_status nlmg_fine_residual(nlmg_ctx* c, const double* p, double* r_out) {
   return guarded(c, [&]() -> nlmg_status {
@@ -1235,6 +1383,7 @@ void nlmg_destroy(nlmg_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_sc) cudaFreeHost(c->h_sc);
   if (c->h_res) cudaFreeHost(c->h_res);
+  if (c->h_gh) cudaFreeHost(c->h_gh);
   if (c->st) cudaStreamDestroy(c->st);
   delete c;
 }

@@ -53,6 +53,16 @@ class Report(C.Structure):
                     history=list(self.history[:self.history_len]))
 
 
+class ServerOptions(C.Structure):
+    _fields_ = [("max_inflight", C.c_int32), ("mem_budget_bytes", C.c_size_t),
+                ("setup_threads_per_request", C.c_int32)]
+
+
+class RequestTimes(C.Structure):
+    _fields_ = [("queue_ms", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
+                ("latency_ms", C.c_double)]
+
+
 class LevelInfo(C.Structure):
     _fields_ = [("n_cells", C.c_int32), ("n_flux", C.c_int32), ("n_p", C.c_int32), ("n_lambda", C.c_int32)]
 
@@ -71,6 +81,7 @@ SIGNATURES = {
     "nlmg_solve": (C.c_int, [_P, _D, _D, _D, C.c_double, C.c_double, C.c_int32, _D, C.POINTER(Report)]),
     "nlmg_solve_device": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_double, C.c_int32, _P, C.POINTER(Report)]),
     "nlmg_solve_picard": (C.c_int, [_P, _D, _D, _D, C.c_double, C.c_double, C.c_int32, _D, C.POINTER(Report)]),
+    "nlmg_solve_newton": (C.c_int, [_P, _D, _D, _D, C.c_double, C.c_double, C.c_int32, _D, C.POINTER(Report)]),
     "nlmg_fine_residual": (C.c_int, [_P, _D, _D]),
     "nlmg_fine_flux": (C.c_int, [_P, _D, _D]),
     "nlmg_level_apply": (C.c_int, [_P, C.c_int32, _D, _D]),
@@ -80,6 +91,12 @@ SIGNATURES = {
     "nlmg_level_info_get": (C.c_int, [_P, C.c_int32, C.POINTER(LevelInfo)]),
     "nlmg_get_aggregates": (C.c_int, [_P, C.c_int32, _I, _I]),
     "nlmg_get_transfer_dense": (C.c_int, [_P, C.c_int32, C.c_int32, _D]),
+    "nlmg_server_default_options": (None, [C.POINTER(ServerOptions)]),
+    "nlmg_server_create": (C.c_int, [C.POINTER(ServerOptions), C.POINTER(_P)]),
+    "nlmg_server_submit": (C.c_int, [_P, C.POINTER(Mesh), C.POINTER(Kappa), C.POINTER(Options), _D, _D, C.c_double,
+                                     C.c_double, C.c_int32, C.POINTER(C.c_uint64)]),
+    "nlmg_server_poll": (C.c_int, [_P, C.c_uint64, C.c_int32, _D, C.POINTER(Report), C.POINTER(RequestTimes)]),
+    "nlmg_server_destroy": (None, [_P]),
     "nlmg_profile": (C.c_int, [_P, C.c_int32]),
     "nlmg_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), _D, _D, _D]),
     "nlmg_fine_residual_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
@@ -139,7 +156,7 @@ def options_from_dict(d):
                               "dp_clamp", "coarsest_steps", "lin_tol", "lin_maxit", "coarse_lin_tol",
                               "lin_precision") if k in d}
     if "lin_tol" in d and "coarse_lin_tol" not in d:
-        keep["coarse_lin_tol"] = d["lin_tol"]
+        keep["coarse_lin_tol"] = d["lin_tol"]       # one tolerance given: use it on every level
     if "smoother" in d:
         keep["smoother"] = SMOOTH_PICARD if d["smoother"] == "picard" else SMOOTH_JACOBI
     return default_options(**keep)
@@ -262,13 +279,13 @@ class Context:
         return out, res.value, bool(early.value)
 
     def solve(self, f_cell, g_face, x0=None, tol_rel=1e-8, tol_abs=1e-10, max_cycles=50, picard_only=False,
-              allow_noconv=False):
+              allow_noconv=False, newton=False):
         f = _f64(f_cell, self.n_cells)
         g = _f64(g_face, self.n_faces)
         x0a = None if x0 is None else _f64(x0, self.n_cells)
         out = np.zeros(self.n_cells)
         rep = Report()
-        fn = lib().nlmg_solve_picard if picard_only else lib().nlmg_solve
+        fn = lib().nlmg_solve_newton if newton else (lib().nlmg_solve_picard if picard_only else lib().nlmg_solve)
         st = fn(self.h, _dp(f), _dp(g), None if x0a is None else _dp(x0a), tol_rel, tol_abs, max_cycles, _dp(out),
                 C.byref(rep))
         if not (st == OK or (allow_noconv and st == ENOCONV)):
@@ -308,3 +325,60 @@ class Context:
         st = lib().nlmg_solve_device(self.h, _P(f_ptr), _P(g_ptr), _P(x0_ptr) if x0_ptr else None, tol_rel,
                                      tol_abs, max_cycles, _P(p_ptr), C.byref(rep))
         return rep.as_dict(), st
+
+
+class Server:
+    """Continuous-batching request loop of the library (nlmg_server_*)."""
+
+    def __init__(self, max_inflight=8, mem_budget_bytes=16 << 30, setup_threads_per_request=2):
+        o = ServerOptions()
+        lib().nlmg_server_default_options(C.byref(o))
+        o.max_inflight = max_inflight
+        o.mem_budget_bytes = mem_budget_bytes
+        o.setup_threads_per_request = setup_threads_per_request
+        h = _P()
+        st = lib().nlmg_server_create(C.byref(o), C.byref(h))
+        if st != OK:
+            raise NlmgError(st, "server create failed")
+        self.h = h
+        self._sizes = {}
+
+    def submit(self, mesh, kappa_kind, kappa_a, opts, f_cell, g_face, tol_rel=1e-8, tol_abs=1e-10, max_cycles=60):
+        fc = np.ascontiguousarray(mesh.face_cells, dtype=np.int32)
+        vol, ht, area = _f64(mesh.cell_volume), _f64(mesh.half_trans), _f64(mesh.face_area)
+        bc = np.ascontiguousarray(mesh.face_bc, dtype=np.uint8)
+        f, g = _f64(f_cell), _f64(g_face)
+        m = Mesh(mesh.n_cells, _dp(vol), int(fc.shape[0]), fc.ctypes.data_as(_I), _dp(ht),
+                 bc.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(area))
+        if isinstance(opts, dict):
+            opts = options_from_dict(opts)
+        t = C.c_uint64(0)
+        st = lib().nlmg_server_submit(self.h, C.byref(m), C.byref(Kappa(int(kappa_kind), float(kappa_a))),
+                                      C.byref(opts), _dp(f), _dp(g), tol_rel, tol_abs, max_cycles, C.byref(t))
+        if st != OK:
+            raise NlmgError(st, "submit failed")
+        self._sizes[t.value] = mesh.n_cells
+        return t.value
+
+    def poll(self, ticket, wait_ms=0):
+        """Returns None if not done, else (p, report dict, times dict, status)."""
+        p = np.zeros(self._sizes[ticket])
+        rep = Report()
+        tm = RequestTimes()
+        st = lib().nlmg_server_poll(self.h, ticket, int(wait_ms), _dp(p), C.byref(rep), C.byref(tm))
+        if st == ETIMEOUT:
+            return None
+        del self._sizes[ticket]
+        return p, rep.as_dict(), dict(queue_ms=tm.queue_ms, setup_ms=tm.setup_ms, solve_ms=tm.solve_ms,
+                                      latency_ms=tm.latency_ms), st
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().nlmg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

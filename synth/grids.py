@@ -77,6 +77,72 @@ def cartesian_mesh(shape, K, dirichlet_x=True):
                 face_bc=np.concatenate(bc), face_area=np.concatenate(area), shape=shape, perm=K)
 
 
+def voronoi_mesh(n_side, K_of_points, seed=3, jitter=0.4):
+    """Clipped 3D Voronoi tessellation of a jittered n_side^3 lattice in the unit cube (an unstructured cell graph).
+
+    Points x_K = lattice centres + U(-jitter, jitter) h. The cube clips the cells by mirroring the points across its
+    six faces: a ridge between a point and its own mirror is a boundary face. Interior faces bisect the K-L segment,
+    so the collocation point is the midpoint and Ups_bar = |eps| K_0 / (d_KL / 2); boundary faces use the distance to
+    the face. Faces on x = 0 and x = 1 are Dirichlet, the rest Neumann. K_of_points(points) gives K_0 per cell.
+    """
+    from scipy.spatial import ConvexHull, Voronoi
+    rng = np.random.default_rng(seed)
+    h = 1.0 / n_side
+    g1 = (np.arange(n_side) + 0.5) * h
+    P = np.stack(np.meshgrid(g1, g1, g1, indexing="ij"), -1).reshape(-1, 3)
+    P = np.clip(P + rng.uniform(-jitter, jitter, P.shape) * h, 1e-6, 1 - 1e-6)
+    n = P.shape[0]
+    mirrors = []
+    for ax in range(3):
+        for side in (0.0, 1.0):
+            Q = P.copy()
+            Q[:, ax] = 2 * side - Q[:, ax]
+            mirrors.append(Q)
+    allp = np.concatenate([P] + mirrors)
+    vor = Voronoi(allp)
+    K = np.asarray(K_of_points(P), dtype=np.float64)
+    vol = np.zeros(n)
+    for i in range(n):
+        reg = vor.regions[vor.point_region[i]]
+        vol[i] = ConvexHull(vor.vertices[reg]).volume
+    fc, ht, bc, area = [], [], [], []
+    for (a, b), rv in zip(vor.ridge_points, vor.ridge_vertices):
+        if a >= n and b >= n:
+            continue
+        if -1 in rv:
+            continue
+        V = vor.vertices[rv]
+        c0 = V.mean(0)
+        A = 0.0
+        for k in range(len(V)):
+            A += 0.5 * np.linalg.norm(np.cross(V[k] - c0, V[(k + 1) % len(V)] - c0))
+        if A <= 1e-14:
+            continue
+        if a < n and b < n:
+            lo, hi = min(a, b), max(a, b)
+            d = np.linalg.norm(P[lo] - P[hi])
+            fc.append((lo, hi))
+            ht.append((A * K[lo] / (d / 2), A * K[hi] / (d / 2)))
+            bc.append(BC_INTERIOR)
+            area.append(A)
+        else:
+            inner = a if a < n else b
+            outer = b if a < n else a
+            k = (outer - n) // n            # mirror block: ax * 2 + side
+            ax = k // 2
+            d = np.linalg.norm(P[inner] - allp[outer]) / 2.0
+            fc.append((inner, -1))
+            ht.append((A * K[inner] / d, 0.0))
+            bc.append(BC_DIRICHLET if ax == 0 else BC_NEUMANN)
+            area.append(A)
+    fc = np.array(fc, dtype=np.int32)
+    order = np.lexsort((fc[:, 1], fc[:, 0], np.array(bc) != BC_INTERIOR))
+    mesh = Mesh(n_cells=n, cell_volume=vol, face_cells=fc[order], half_trans=np.array(ht)[order],
+                face_bc=np.array(bc, np.uint8)[order], face_area=np.array(area)[order], shape=(n,), perm=K)
+    mesh.points = P
+    return mesh
+
+
 def gaussian_random_field(shape, corr_cells, rng):
     """Zero-mean, unit-variance field with a Gaussian covariance of correlation length corr_cells (in cells).
 
@@ -145,7 +211,7 @@ def default_options(**kw):
     """Hierarchy and smoother options; the backtracking constants are the paper's (n_max = 4, theta = 0.9)."""
     o = dict(n_levels=2, agg_size=[16, 8, 8, 8, 8, 8, 8], modes=[2, 2, 2, 2, 2, 2, 2], nu_pre=2, nu_post=2,
              omega=0.8, bt_nmax=4, bt_theta=0.9, dp_clamp=0.0, coarsest_steps=10, tol_rel=1e-8, tol_abs=1e-10,
-             max_cycles=50, lin_tol=1e-12, lin_maxit=2000)
+             max_cycles=50)
     o.update(kw)
     return o
 
@@ -184,6 +250,23 @@ def problem_config(name, scale=None):
                                dp_clamp=float(np.log(1.5) / 2.0))
         return Problem(mesh, KAPPA_EXP, 2.0, np.zeros(mesh.n_cells), g, opts, name)
     raise KeyError(name)
+
+
+def voronoi_problem(n_side=12, seed=3):
+    """Unstructured workload: clipped Voronoi cells of a jittered lattice, ln K_0 ~ N(0, 2^2) correlated over 4
+    lattice spacings (sampled at the points), kappa = (1 + p^2)^-1, p = 1 on x = 0 and 0 on x = 1."""
+    field_ = gaussian_random_field((n_side,) * 3, 4.0, np.random.default_rng(seed + 100))
+
+    def K_of(P):
+        idx = np.clip((P * n_side).astype(int), 0, n_side - 1)
+        return np.exp(2.0 * field_[idx[:, 0], idx[:, 1], idx[:, 2]])
+
+    mesh = voronoi_mesh(n_side, K_of, seed=seed)
+    g = np.zeros(mesh.n_faces)
+    d = np.where(mesh.face_bc == BC_DIRICHLET)[0]
+    g[d] = np.where(mesh.points[mesh.face_cells[d, 0], 0] < 0.5, 1.0, 0.0)
+    opts = default_options(n_levels=3, agg_size=[27, 8, 8], modes=[4, 3, 3])
+    return Problem(mesh, KAPPA_INV1P2, 0.0, np.zeros(mesh.n_cells), g, opts, "voronoi")
 
 
 CONFIGS = ("cart2d_32", "chan3d_64")

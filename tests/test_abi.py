@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import hierarchy
-from synth.grids import problem_config
+from synth.grids import problem_config, voronoi_problem
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -45,12 +45,13 @@ def test_setup_rejects_bad_mesh(nlmg_lib):
 
 CASES = [("cart2d_32", None, {}), ("cart2d_32", 13, dict(agg_size=[9, 4], modes=[3, 2])),
          ("chan3d_64", 8, dict(agg_size=[16, 4, 4], modes=[3, 3, 3])),
-         ("chan3d_64", 12, dict(n_levels=3, agg_size=[27, 6, 4], modes=[4, 3, 3]))]
+         ("chan3d_64", 12, dict(n_levels=3, agg_size=[27, 6, 4], modes=[4, 3, 3])),
+         ("voronoi", 9, {})]
 
 
 @pytest.mark.parametrize("name,scale,upd", CASES)
 def test_host_hierarchy_matches_oracle(nlmg_lib, name, scale, upd):
-    pr = problem_config(name, scale=scale)
+    pr = voronoi_problem(scale) if name == "voronoi" else problem_config(name, scale=scale)
     opts = dict(pr.opts, **upd)
     H = hierarchy.build(pr.mesh, opts)
     ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, opts, device=False)

@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 from oracle import coarse, fas, hierarchy, newton, tpfa
-from synth.grids import cartesian_mesh, lognormal_field, problem_config, KAPPA_INV1P2
+from synth.grids import cartesian_mesh, lognormal_field, problem_config, voronoi_problem, KAPPA_INV1P2
 
 pytestmark = pytest.mark.gpu
 
@@ -13,13 +13,14 @@ CASES = {
     "cart2d_13": ("cart2d_32", 13, dict(agg_size=[9, 4], modes=[3, 2])),
     "chan3d_16": ("chan3d_64", 16, dict(n_levels=3, agg_size=[64, 8, 8], modes=[4, 4, 4])),
     "chan3d_11": ("chan3d_64", 11, dict(n_levels=3, agg_size=[27, 6, 4], modes=[4, 3, 3])),
+    "vor3d_10": ("voronoi", 10, {}),     # unstructured: clipped Voronoi cells, 5-21 neighbours, kappa = 1/(1+p^2)
 }
 TIGHT = dict(lin_tol=1e-13, lin_maxit=20000)
 
 
 def _setup(nlmg_lib, key, **upd):
     name, scale, o = CASES[key]
-    pr = problem_config(name, scale=scale)
+    pr = voronoi_problem(scale) if name == "voronoi" else problem_config(name, scale=scale)
     opts = dict(pr.opts, **o)
     opts.update(upd)
     pr.opts = opts
@@ -219,3 +220,32 @@ def test_mixed_precision_cg_reaches_fp64_solution(nlmg_lib):
     r = tpfa.reduced_residual(pr.mesh, pr.kappa_kind, pr.kappa_a, p, pr.f_cell, pr.g_face)
     assert np.linalg.norm(r) <= 2e-11 * rep["res0"]
     assert _rel(p, pstar) <= 1e-8
+
+
+def test_single_level_newton_baseline(nlmg_lib):
+    """Exact Jacobian + GMRES: converges to p* and, once close, quadratically (Sec. 2.2 / 3.3.2 on level 0)."""
+    pr, H, ctx = _setup(nlmg_lib, "chan3d_11", **TIGHT)
+    pstar, _ = newton.solve(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, dp_clamp=pr.opts["dp_clamp"])
+    p, rep, st = ctx.solve(pr.f_cell, pr.g_face, tol_rel=1e-12, tol_abs=1e-300, max_cycles=200, newton=True)
+    assert st == 0, rep
+    assert _rel(p, pstar) <= 1e-10
+    h = np.array(rep["history"]) / rep["history"][0]
+    k = int(np.argmax(h < 1e-3))                     # first iterate in the local regime
+    assert h[-1] <= 1e-12 and len(h) - k <= 4          # at most a few steps from 1e-3 to 1e-12
+
+
+def test_full_size_bench_configuration(nlmg_lib):
+    """The benchmarked 64^3 workload in its benchmarked configuration (library defaults): the returned iterate meets
+    the relative tolerance when its residual is recomputed by the oracle, and sampled residual rows agree."""
+    pr = problem_config("chan3d_64")
+    ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.opts)
+    p, rep, st = ctx.solve(pr.f_cell, pr.g_face)
+    assert st == 0, rep
+    r = tpfa.reduced_residual(pr.mesh, pr.kappa_kind, pr.kappa_a, p, pr.f_cell, pr.g_face)
+    r0 = tpfa.reduced_residual(pr.mesh, pr.kappa_kind, pr.kappa_a, np.zeros(pr.mesh.n_cells), pr.f_cell, pr.g_face)
+    assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(r0) * 1.0001
+    ctx.set_data(pr.f_cell, pr.g_face)
+    rg = ctx.fine_residual(p)
+    rows = np.random.default_rng(5).choice(pr.mesh.n_cells, 4096, replace=False)
+    sig = tpfa.face_fluxes(pr.mesh, pr.kappa_kind, pr.kappa_a, p, pr.g_face)
+    assert np.abs(rg[rows] - r[rows]).max() <= 1e-13 * np.abs(sig).max()
