@@ -236,6 +236,10 @@ nlmg_status nlmg_profile_read(nlmg_ctx* ctx, int32_t kernel, int64_t* launches, 
 nlmg_status nlmg_fine_residual_noalloc(nlmg_ctx* ctx, const double* p_dev, double* r_dev, double* norm2_dev,
                                        void* stream);
 
+/* FP64 fused multiply-add throughput of the current device in GFLOP/s (an FMA counts 2), measured with a synthetic
+ * kernel of independent FMA chains; the denominator of the FP64-arithmetic roofline. */
+nlmg_status nlmg_measure_fp64(double* gflops);
+
 const char* nlmg_last_error(const nlmg_ctx* ctx);
 void nlmg_destroy(nlmg_ctx* ctx);
 

@@ -330,4 +330,69 @@ void chol_solve(int n, const double* L, double* b) {
   }
 }
 
+// L L^T X = B for nr right-hand sides stored row-major (n x nr), in place; same operation order per column as
+// chol_solve, with contiguous inner loops over the right-hand sides.
+void chol_solve_multi(int n, const double* L, int nr, double* X) {
+  for (int i = 0; i < n; ++i) {
+    double* Xi = X + (size_t)i * nr;
+    for (int k = 0; k < i; ++k) {
+      const double l = L[(size_t)i * n + k];
+      if (l == 0.0) continue;
+      const double* Xk = X + (size_t)k * nr;
+      for (int r = 0; r < nr; ++r) Xi[r] -= l * Xk[r];
+    }
+    const double d = L[(size_t)i * n + i];
+    for (int r = 0; r < nr; ++r) Xi[r] /= d;
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double* Xi = X + (size_t)i * nr;
+    for (int k = i + 1; k < n; ++k) {
+      const double l = L[(size_t)k * n + i];
+      if (l == 0.0) continue;
+      const double* Xk = X + (size_t)k * nr;
+      for (int r = 0; r < nr; ++r) Xi[r] -= l * Xk[r];
+    }
+    const double d = L[(size_t)i * n + i];
+    for (int r = 0; r < nr; ++r) Xi[r] /= d;
+  }
+}
+
+// Right-looking Cholesky on the upper triangle of a row-major SPD matrix: A = U^T U, U written over the upper
+// triangle. Zero multipliers are skipped, so a sparse A (a cell-graph Laplacian in a banded order) costs in
+// proportion to its fill rather than n^3.
+bool chol_upper_factor(int n, double* A) {
+  for (int k = 0; k < n; ++k) {
+    double* Ak = A + (size_t)k * n;
+    if (!(Ak[k] > 0.0)) return false;
+    const double ukk = std::sqrt(Ak[k]);
+    const double inv = 1.0 / ukk;
+    Ak[k] = ukk;
+    for (int j = k + 1; j < n; ++j) Ak[j] *= inv;
+    for (int i = k + 1; i < n; ++i) {
+      const double u = Ak[i];
+      if (u == 0.0) continue;
+      double* Ai = A + (size_t)i * n;
+      for (int j = i; j < n; ++j) Ai[j] -= u * Ak[j];
+    }
+  }
+  return true;
+}
+
+// U^T U x = b in place, U from chol_upper_factor.
+void chol_upper_solve(int n, const double* U, double* b) {
+  for (int k = 0; k < n; ++k) {
+    const double* Uk = U + (size_t)k * n;
+    const double y = b[k] / Uk[k];
+    b[k] = y;
+    if (y != 0.0)
+      for (int j = k + 1; j < n; ++j) b[j] -= Uk[j] * y;
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    const double* Ui = U + (size_t)i * n;
+    double s = b[i];
+    for (int j = i + 1; j < n; ++j) s -= Ui[j] * b[j];
+    b[i] = s / Ui[i];
+  }
+}
+
 }  // namespace nlmg

@@ -23,5 +23,8 @@ bool invert(int n, const double* A, double* Ainv);                            //
 // Cholesky A = L L^T of an SPD matrix (lower triangle written in place). Returns false if not SPD.
 bool chol_factor(int n, double* A);
 void chol_solve(int n, const double* L, double* b);
+bool chol_upper_factor(int n, double* A);                         // A = U^T U on the upper triangle
+void chol_upper_solve(int n, const double* U, double* b);
+void chol_solve_multi(int n, const double* L, int nr, double* X);   // n x nr right-hand sides, row-major
 
 }  // namespace nlmg

@@ -1,6 +1,7 @@
 // Host-side multilevel hierarchy (built once by nlmg_setup, then uploaded to the device).
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -54,7 +55,15 @@ struct Transfer {
   std::vector<double> eig_gap;               // lambda_{m+1} - lambda_m per aggregate (diagnostic)
 };
 
+// Batched eigensolver callback (nmat, aoff, n, k, A_all, vals, voff, vecs, err); vals has kEigStride per matrix.
+constexpr int kEigStride = 9;
+using EigBatchFn = std::function<bool(int, const std::vector<long long>&, const std::vector<int>&,
+                                      const std::vector<int>&, std::vector<double>&, std::vector<double>&,
+                                      std::vector<long long>&, std::vector<double>&, std::string&)>;
+
 struct Options {
+  bool gpu_eig = false;      // local eigenproblems on the GPU (batched) instead of the host
+  EigBatchFn eig_fn;
   int n_levels = 2;
   int agg_size[8] = {16, 8, 8, 8, 8, 8, 8, 8};
   int modes[8] = {2, 2, 2, 2, 2, 2, 2, 2};

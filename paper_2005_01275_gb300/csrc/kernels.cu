@@ -297,6 +297,20 @@ __global__ void k_jacobi_dinv(int n, const double* __restrict__ jdiag, const dou
   GRID_STRIDE(i, n) out[i] = 1.0 / fmax(jdiag[i], 0.5 * diagT[i]);
 }
 
+// ---- measurement: FP64 FMA throughput (8 independent dependency chains per thread) ----------------------------
+__global__ void k_fp64_peak(int iters, double* out) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 1e-7 * (threadIdx.x + k);
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], 0.9999999, 1e-9);
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // ---- transfers -------------------------------------------------------------------------------------------------
 
 // out1 = scale1 * P_A^T in1 (and out2 = P_A^T in2) per aggregate: one warp per aggregate, fixed-order warp sums.
@@ -525,6 +539,30 @@ void launch_gmres_combine(cudaStream_t st, int n, int nk, const double* V, const
 void launch_jacobi_dinv(cudaStream_t st, int n, const double* jdiag, const double* diagT, double* out) {
   COUNT(1);
   k_jacobi_dinv<<<grid_for(n), kThreads, 0, st>>>(n, jdiag, diagT, out);
+}
+bool measure_fp64_peak(double* gflops) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 8, threads = 256, iters = 8192;
+  double* out = nullptr;
+  if (cudaMalloc(&out, (size_t)blocks * threads * sizeof(double)) != cudaSuccess) return false;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fp64_peak<<<blocks, threads>>>(iters / 8, out);   // warm-up
+  cudaEventRecord(e0);
+  k_fp64_peak<<<blocks, threads>>>(iters, out);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  COUNT(2);
+  *gflops = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3) / 1e9;
+  return cudaGetLastError() == cudaSuccess;
 }
 void launch_sdiag(cudaStream_t st, int n, const double* diagT, double* sdiag) {
   COUNT(1);

@@ -114,6 +114,8 @@ void launch_csr(cudaStream_t st, int nrows, const int* off, const int* col, cons
 void launch_coarse_cell(cudaStream_t st, const LevelDev& L, const double* sig, const double* p, const double* bp,
                         double* yl, double* rp, double* kapc, int kind, double a, Reduce red);
 void launch_sdiag(cudaStream_t st, int n, const double* diagT, double* sdiag);
+// FP64 FMA throughput of the current device in GFLOP/s (an FMA counts 2), from a synthetic kernel
+bool measure_fp64_peak(double* gflops);
 template <class T>
 void launch_scale_sell(cudaStream_t st, const FineDev& F, const double* Tval, const double* sdiag, T* Ts);
 void launch_coarse_flux(cudaStream_t st, const LevelDev& L, const double* yl, const double* bs, double* rs,

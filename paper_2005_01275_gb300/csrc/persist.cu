@@ -129,14 +129,16 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partial, doubl
 // CG on the symmetrically Jacobi-scaled system (S A S) y = S bscale b, dx = S y, S = diag(A)^-1/2, so the scaled
 // matrix has a unit diagonal and only its off-diagonal entries Ts (SELL-32 layout, type T) are read. T = double is
 // the FP64 path; T = float runs the Krylov vectors and the matrix in FP32 (dot products still accumulate in FP64)
-// inside the FP64 nonlinear iteration. The stopping test is on the scaled residual, ||S r|| <= tol ||S r_0||
-// (the r.z of Jacobi-preconditioned CG).
+// inside the FP64 nonlinear iteration. The matrix is applied to the residual r, which every iteration already
+// materialises, and A p follows by recurrence (p = r + beta p, q = A r + beta q): no neighbour values have to be
+// rebuilt and an iteration needs two grid barriers. The stopping test is on the scaled residual,
+// ||S r|| <= tol ||S r_0|| (the r.z of Jacobi-preconditioned CG).
 template <class T>
 __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __restrict__ Ts,
                                                         const double* __restrict__ sdiag,
                                                         const double* __restrict__ b, double bscale,
                                                         double* __restrict__ dx, T* __restrict__ y,
-                                                        T* __restrict__ r, T* pa, T* pb, T* __restrict__ q,
+                                                        T* __restrict__ r, T* __restrict__ p, T* __restrict__ q,
                                                         double* partial, GridSync gs, double tol, int maxit,
                                                         PcgResult* res) {
   __shared__ double sm[2 * 32];
@@ -154,17 +156,13 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __re
   double rr = rr0;
   const double tol2 = tol * tol * rr0;
   T beta = (T)0;
-  T* pold = pa;
-  T* pnew = pb;
   int it = 0;
-  bool first = true;
   while (rr0 > 0.0 && rr > tol2 && it < maxit) {
-    // q = (S A S) p_new with p_new = r + beta p_old formed for the row and its neighbours alike
     double pq[1] = {0.0};
     GSTRIDE(K, F.N) {
       const int s = K >> 5, lane = K & 31;
-      const T pK = first ? __ldcg(&r[K]) : beta * __ldcg(&pold[K]) + __ldcg(&r[K]);
-      T acc = pK;
+      const T rK = __ldcg(&r[K]);
+      T acc = rK;
       const int w = F.sell_w[s];
       int e = F.sell_off[s] + lane;
       int j = 0;
@@ -179,28 +177,22 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __re
           }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-          if (u < w) {
-            const int L = Ls[u];
-            const T pL = first ? __ldcg(&r[L]) : beta * __ldcg(&pold[L]) + __ldcg(&r[L]);
-            acc -= Tv[u] * pL;
-          }
+          if (u < w) acc -= Tv[u] * __ldcg(&r[Ls[u]]);
         j = w;
       }
-      for (e += 32 * j; j < w; ++j, e += 32) {
-        const int L = F.nbr[e];
-        const T pL = first ? __ldcg(&r[L]) : beta * __ldcg(&pold[L]) + __ldcg(&r[L]);
-        acc -= Ts[e] * pL;
-      }
-      pnew[K] = pK;
-      q[K] = acc;
-      pq[0] = fma((double)pK, (double)acc, pq[0]);
+      for (e += 32 * j; j < w; ++j, e += 32) acc -= Ts[e] * __ldcg(&r[F.nbr[e]]);
+      const T pK = it == 0 ? rK : rK + beta * p[K];
+      const T qK = it == 0 ? acc : acc + beta * q[K];
+      p[K] = pK;
+      q[K] = qK;
+      pq[0] = fma((double)pK, (double)qK, pq[0]);
     }
     if (!grid_sum<1>(pq, part0, gs.out + 2, gs, sm)) return;
     const double alpha_d = pq[0] != 0.0 ? rr / pq[0] : 0.0;
     const T alpha = (T)alpha_d;
     double rn[1] = {0.0};
     GSTRIDE(i, F.N) {
-      y[i] = alpha * pnew[i] + y[i];
+      y[i] = alpha * p[i] + y[i];
       const T ri = r[i] - alpha * q[i];
       r[i] = ri;
       rn[0] = fma((double)ri, (double)ri, rn[0]);
@@ -208,10 +200,6 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __re
     if (!grid_sum<1>(rn, part1, gs.out + 4, gs, sm)) return;
     beta = (T)(rr != 0.0 ? rn[0] / rr : 0.0);
     rr = rn[0];
-    T* t = pold;
-    pold = pnew;
-    pnew = t;
-    first = false;
     ++it;
     if (!(alpha_d != 0.0)) break;   // breakdown (p.Ap = 0): stop with the current iterate
   }
@@ -220,6 +208,116 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __re
     res->iters = it;
     res->rr0 = rr0;
     res->rr = rr;
+  }
+}
+
+// Pipelined CG (Ghysels and Vanroose) on the same scaled system: the dot products of an iteration are computed from
+// vectors updated in the same pass as the matrix product, so one grid barrier per iteration both publishes the
+// vector the next matrix product gathers and completes the reduction. Recurrences: n = A w, z = n + beta z,
+// s = w + beta s, p = r + beta p, y += alpha p, r -= alpha s, w -= alpha z; gamma = (r, r), delta = (w, r). Used for
+// loose tolerances (the recursively updated residual drifts from the true one at the 1e-10 level).
+template <class T>
+__device__ __forceinline__ T sell_apply(const FineDev& F, const T* __restrict__ Ts, const T* v, int K) {
+  const int s = K >> 5, lane = K & 31;
+  T acc = __ldcg(&v[K]);
+  const int w = F.sell_w[s];
+  int e = F.sell_off[s] + lane;
+  int j = 0;
+  if (w <= 8) {
+    int Ls[8];
+    T Tv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (u < w) {
+        Ls[u] = F.nbr[e + 32 * u];
+        Tv[u] = Ts[e + 32 * u];
+      }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (u < w) acc -= Tv[u] * __ldcg(&v[Ls[u]]);
+    j = w;
+  }
+  for (e += 32 * j; j < w; ++j, e += 32) acc -= Ts[e] * __ldcg(&v[F.nbr[e]]);
+  return acc;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kPThreads) kp_fine_cg_pipe(FineDev F, const T* __restrict__ Ts,
+                                                             const double* __restrict__ sdiag,
+                                                             const double* __restrict__ b, double bscale,
+                                                             double* __restrict__ dx, T* __restrict__ y,
+                                                             T* __restrict__ r, T* wa, T* wb, T* __restrict__ z,
+                                                             T* __restrict__ sv, T* __restrict__ p, double* partial,
+                                                             GridSync gs, double tol, int maxit, PcgResult* res) {
+  __shared__ double sm[2 * 32];
+  double* part0 = partial;
+  double* part1 = partial + 2 * gridDim.x;
+  GSTRIDE(i, F.N) {
+    r[i] = (T)(sdiag[i] * bscale * b[i]);
+    y[i] = z[i] = sv[i] = p[i] = (T)0;
+  }
+  if (!grid_barrier(gs)) return;
+  double a2[2] = {0.0, 0.0};
+  GSTRIDE(K, F.N) {
+    const T wK = sell_apply<T>(F, Ts, r, K);
+    wa[K] = wK;
+    const double rK = (double)r[K];
+    a2[0] = fma(rK, rK, a2[0]);
+    a2[1] = fma((double)wK, rK, a2[1]);
+  }
+  if (!grid_sum<2>(a2, part1, gs.out + 0, gs, sm)) return;
+  double gamma = a2[0], delta = a2[1];
+  const double rr0 = gamma;
+  const double tol2 = tol * tol * rr0;
+  double gamma_old = 0.0, alpha_old = 0.0;
+  T* wc = wa;   // current w (read, neighbours gathered)
+  T* wn = wb;   // next w (written)
+  int it = 0;
+  while (rr0 > 0.0 && gamma > tol2 && it < maxit) {
+    double beta_d, alpha_d;
+    if (it == 0) {
+      beta_d = 0.0;
+      alpha_d = delta != 0.0 ? gamma / delta : 0.0;
+    } else {
+      beta_d = gamma_old != 0.0 ? gamma / gamma_old : 0.0;
+      const double den = delta - beta_d * gamma / alpha_old;
+      alpha_d = den != 0.0 ? gamma / den : 0.0;
+    }
+    if (!(alpha_d != 0.0)) break;
+    const T alpha = (T)alpha_d, beta = (T)beta_d;
+    a2[0] = a2[1] = 0.0;
+    GSTRIDE(K, F.N) {
+      const T nK = sell_apply<T>(F, Ts, wc, K);
+      const T wK = wc[K];
+      const T zK = nK + beta * z[K];
+      const T sK = wK + beta * sv[K];
+      const T pK = r[K] + beta * p[K];
+      z[K] = zK;
+      sv[K] = sK;
+      p[K] = pK;
+      y[K] += alpha * pK;
+      const T rK = r[K] - alpha * sK;
+      r[K] = rK;
+      const T wN = wK - alpha * zK;
+      wn[K] = wN;
+      a2[0] = fma((double)rK, (double)rK, a2[0]);
+      a2[1] = fma((double)wN, (double)rK, a2[1]);
+    }
+    if (!grid_sum<2>(a2, (it & 1) ? part1 : part0, gs.out + ((it & 1) ? 4 : 2), gs, sm)) return;
+    gamma_old = gamma;
+    alpha_old = alpha_d;
+    gamma = a2[0];
+    delta = a2[1];
+    T* t = wc;
+    wc = wn;
+    wn = t;
+    ++it;
+  }
+  GSTRIDE(i, F.N) dx[i] = sdiag[i] * (double)y[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    res->iters = it;
+    res->rr0 = rr0;
+    res->rr = gamma;
   }
 }
 
@@ -272,39 +370,36 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
   double rr = rr0;
   const double tol2 = tol * tol * rr0;
   T beta = (T)0;
-  T* pold = pa;
-  T* pnew = pb;
+  T* pp = pa;       // search direction p
   int it = 0;
-  bool first = true;
   while (rr0 > 0.0 && rr > tol2 && it < maxit) {
-    // ylam[k] = kappa_c sum_j Hc[k, j] p_new(lambda_j): one thread per interface slot, rows read contiguously
+    // ylam[k] = kappa_c sum_j Hc[k, j] z(lambda_j): H applied to the preconditioned residual, one thread per
+    // interface slot (rows read contiguously); H p then follows by recurrence
     GSTRIDE(k, L.nif) {
       const int c = L.if_cell[k];
       const int k0 = L.if_off[c], ni = L.if_off[c + 1] - k0;
       const T* Hk = Hc + L.hc_off[c] + (size_t)(k - k0) * ni;
       T y = 0;
-      for (int j = 0; j < ni; ++j) {
-        const int l = L.if_lam[k0 + j];
-        const T v = first ? __ldcg(&lz[l]) : beta * __ldcg(&pold[l]) + __ldcg(&lz[l]);
-        y += Hk[j] * v;
-      }
+      for (int j = 0; j < ni; ++j) y += Hk[j] * __ldcg(&lz[L.if_lam[k0 + j]]);
       ylam[k] = (T)kapc[c] * y;
     }
     if (!grid_barrier(gs)) return;
     double a1[1] = {0.0};
     GSTRIDE(l, L.nlam) {
-      const T pl = first ? __ldcg(&lz[l]) : beta * __ldcg(&pold[l]) + __ldcg(&lz[l]);
-      const T y = __ldcg(&ylam[L.lam_y0[l]]) + __ldcg(&ylam[L.lam_y1[l]]);
-      pnew[l] = pl;
-      lq[l] = y;
-      a1[0] = fma((double)pl, (double)y, a1[0]);
+      const T zl = lz[l];
+      const T hz = __ldcg(&ylam[L.lam_y0[l]]) + __ldcg(&ylam[L.lam_y1[l]]);
+      const T pl = it == 0 ? zl : zl + beta * pp[l];
+      const T ql = it == 0 ? hz : hz + beta * lq[l];
+      pp[l] = pl;
+      lq[l] = ql;
+      a1[0] = fma((double)pl, (double)ql, a1[0]);
     }
     if (!grid_sum<1>(a1, part0, gs.out + 2, gs, sm)) return;
     const double alpha_d = a1[0] != 0.0 ? rz / a1[0] : 0.0;
     const T alpha = (T)alpha_d;
     a2[0] = a2[1] = 0.0;
     GSTRIDE(l, L.nlam) {
-      lam[l] = alpha * pnew[l] + lam[l];
+      lam[l] = alpha * pp[l] + lam[l];
       const T ri = lr[l] - alpha * lq[l];
       const T zi = ri * ldinv[l];
       lr[l] = ri;
@@ -316,10 +411,6 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
     beta = (T)(rz != 0.0 ? a2[0] / rz : 0.0);
     rz = a2[0];
     rr = a2[1];
-    T* t = pold;
-    pold = pnew;
-    pnew = t;
-    first = false;
     ++it;
     if (!(alpha_d != 0.0)) break;
   }
@@ -381,13 +472,29 @@ template <class T>
 cudaError_t launch_fine_cg(cudaStream_t st, const FineDev& F, const T* Ts, const double* sdiag, const double* b,
                            double bscale, double* dx, T* y, T* r, T* pa, T* pb, T* q, double* partial, GridSync gs,
                            double tol, int maxit, PcgResult* res) {
+  (void)pb;
   const void* fn = (const void*)kp_fine_cg<T>;
   int grid = coop_grid(fn, F.N);
   void* args[] = {(void*)&F, (void*)&Ts, (void*)&sdiag, (void*)&b, (void*)&bscale, (void*)&dx, (void*)&y,
-                  (void*)&r, (void*)&pa, (void*)&pb, (void*)&q, (void*)&partial, (void*)&gs, (void*)&tol,
+                  (void*)&r, (void*)&pa, (void*)&q, (void*)&partial, (void*)&gs, (void*)&tol,
                   (void*)&maxit, (void*)&res};
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
 }
+template <class T>
+cudaError_t launch_fine_cg_pipe(cudaStream_t st, const FineDev& F, const T* Ts, const double* sdiag, const double* b,
+                                double bscale, double* dx, T* y, T* r, T* wa, T* wb, T* z, T* sv, T* p,
+                                double* partial, GridSync gs, double tol, int maxit, PcgResult* res) {
+  const void* fn = (const void*)kp_fine_cg_pipe<T>;
+  int grid = coop_grid(fn, F.N);
+  void* args[] = {(void*)&F, (void*)&Ts, (void*)&sdiag, (void*)&b, (void*)&bscale, (void*)&dx, (void*)&y,
+                  (void*)&r, (void*)&wa, (void*)&wb, (void*)&z, (void*)&sv, (void*)&p, (void*)&partial, (void*)&gs,
+                  (void*)&tol, (void*)&maxit, (void*)&res};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
+}
+template cudaError_t launch_fine_cg_pipe<double>(cudaStream_t, const FineDev&, const double*, const double*,
+                                                 const double*, double, double*, double*, double*, double*, double*,
+                                                 double*, double*, double*, double*, GridSync, double, int,
+                                                 PcgResult*);
 template cudaError_t launch_fine_cg<double>(cudaStream_t, const FineDev&, const double*, const double*,
                                             const double*, double, double*, double*, double*, double*, double*,
                                             double*, double*, GridSync, double, int, PcgResult*);

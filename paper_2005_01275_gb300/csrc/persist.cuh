@@ -26,6 +26,11 @@ cudaError_t launch_fine_cg(cudaStream_t st, const FineDev& F, const T* Ts, const
                            double tol, int maxit, PcgResult* res);
 
 template <class T>
+cudaError_t launch_fine_cg_pipe(cudaStream_t st, const FineDev& F, const T* Ts, const double* sdiag, const double* b,
+                                double bscale, double* dx, T* y, T* r, T* wa, T* wb, T* z, T* sv, T* p,
+                                double* partial, GridSync gs, double tol, int maxit, PcgResult* res);
+
+template <class T>
 cudaError_t launch_hyb_solve(cudaStream_t st, const LevelDev& L, const T* Hc, const T* Sinv, const double* kapc,
                              const double* bs, const double* bp, T* ylam, T* ydiag, T* lam, T* lr, T* lz, T* pa,
                              T* pb, T* lq, T* ldinv, double* dsig, double* dp, double* partial, GridSync gs,

@@ -146,12 +146,9 @@ bool schur(const LocalProblem& lp, std::vector<double>& S, std::vector<double>& 
   } else {
     std::vector<double> Lc(lp.M);
     if (!chol_factor(ns, Lc.data())) return false;
-    std::vector<double> col(ns);
-    for (int r = 0; r < np; ++r) {
-      for (int i = 0; i < ns; ++i) col[i] = lp.D[(size_t)r * ns + i];
-      chol_solve(ns, Lc.data(), col.data());
-      for (int i = 0; i < ns; ++i) X[(size_t)i * np + r] = col[i];
-    }
+    for (int r = 0; r < np; ++r)
+      for (int i = 0; i < ns; ++i) X[(size_t)i * np + r] = lp.D[(size_t)r * ns + i];
+    chol_solve_multi(ns, Lc.data(), np, X.data());
   }
   S.assign((size_t)np * np, 0.0);
   for (int r = 0; r < np; ++r) {
@@ -172,41 +169,82 @@ bool schur(const LocalProblem& lp, std::vector<double>& S, std::vector<double>& 
   return true;
 }
 
-// Factor for repeated local solves [M D^T; D 0][s; p] = [0; rp] (optionally bordered by ones^T p = 0).
+// Factor for repeated local solves [M D^T; D 0][s; p] = [0; rp]. Without Dirichlet unknowns (a Neumann problem) S =
+// D M^-1 D^T is singular with null space span(1^l) and rp is compatible (1^l . rp = 0); the pressure is then fixed by
+// setting its unknown with the largest |1^l| entry to 0, which moves p along 1^l only and leaves s = -M^-1 D^T p
+// unchanged (D^T 1^l = 0 on internal flux unknowns). S (or S without that row and column) is factored by Cholesky.
+// The pinned row carries the rounding of the compatibility condition; one refinement step with the residual
+// projected off 1^l leaves a residual along 1^l only, as a bordered solve would, so that P_NPV^T D s stays exact to
+// rounding.
 struct LocalSolver {
   const LocalProblem* lp = nullptr;
-  std::vector<double> X, K;   // X = M^-1 D^T ; K = LU of [S 1; 1^T 0] (bordered) or S
-  std::vector<int> piv;
-  bool bordered = true;
+  std::vector<double> X, U;   // X = M^-1 D^T ; U = upper Cholesky factor of the (reduced) S
+  std::vector<double> S;      // the full S (Neumann problems, for the refinement step)
+  int pin = -1;               // pressure unknown fixed to 0, or -1
   int nk = 0;
-  bool init(const LocalProblem& p, bool border) {
+  bool init(const LocalProblem& p, bool neumann) {
     lp = &p;
-    bordered = border;
-    std::vector<double> S;
+    S.clear();
     if (!schur(p, S, X)) return false;
-    int np = p.np;
-    nk = np + (border ? 1 : 0);
-    K.assign((size_t)nk * nk, 0.0);
-    for (int r = 0; r < np; ++r)
-      for (int q = 0; q < np; ++q) K[(size_t)r * nk + q] = S[(size_t)r * np + q];
-    if (border)
-      for (int r = 0; r < np; ++r) {
-        K[(size_t)r * nk + np] = p.ones[r];
-        K[(size_t)np * nk + r] = p.ones[r];
+    const int np = p.np;
+    pin = -1;
+    if (neumann) {
+      pin = 0;
+      for (int r = 1; r < np; ++r)
+        if (std::fabs(p.ones[r]) > std::fabs(p.ones[pin])) pin = r;
+    }
+    nk = np - (pin >= 0 ? 1 : 0);
+    U.assign((size_t)nk * nk, 0.0);
+    for (int r = 0, rr = 0; r < np; ++r) {
+      if (r == pin) continue;
+      for (int q = 0, qq = 0; q < np; ++q) {
+        if (q == pin) continue;
+        U[(size_t)rr * nk + qq] = S[(size_t)r * np + q];
+        ++qq;
       }
-    piv.assign(nk, 0);
-    return lu_factor(nk, K.data(), piv.data());
+      ++rr;
+    }
+    if (!neumann) std::vector<double>().swap(S);
+    return chol_upper_factor(nk, U.data());
   }
-  // rs = 0: S p = -rp ; sigma = -X p
+  // S p = rhs with p[pin] = 0
+  void pinned_solve(const std::vector<double>& rhs, std::vector<double>& pv) const {
+    const int np = lp->np;
+    std::vector<double> b(nk);
+    for (int r = 0, rr = 0; r < np; ++r)
+      if (r != pin) b[rr++] = rhs[r];
+    chol_upper_solve(nk, U.data(), b.data());
+    pv.assign(np, 0.0);
+    for (int r = 0, rr = 0; r < np; ++r)
+      if (r != pin) pv[r] = b[rr++];
+  }
+  // S p = -rp ; sigma = -X p
   void solve_p_rhs(const std::vector<double>& rp, std::vector<double>& sigma) const {
-    int np = lp->np, ns = (int)lp->U.size();
-    std::vector<double> b(nk, 0.0);
-    for (int r = 0; r < np; ++r) b[r] = -rp[r];
-    lu_solve(nk, K.data(), piv.data(), b.data());
+    const int np = lp->np, ns = (int)lp->U.size();
+    std::vector<double> rhs(np), pv;
+    for (int r = 0; r < np; ++r) rhs[r] = -rp[r];
+    pinned_solve(rhs, pv);
+    if (pin >= 0) {
+      const std::vector<double>& one = lp->ones;
+      double oo = 0.0, orr = 0.0;
+      std::vector<double> res(np), dv;
+      for (int r = 0; r < np; ++r) {
+        double acc = rhs[r];
+        const double* Sr = &S[(size_t)r * np];
+        for (int q = 0; q < np; ++q) acc -= Sr[q] * pv[q];
+        res[r] = acc;
+        oo += one[r] * one[r];
+        orr += one[r] * acc;
+      }
+      for (int r = 0; r < np; ++r) res[r] -= (orr / oo) * one[r];
+      pinned_solve(res, dv);
+      for (int r = 0; r < np; ++r) pv[r] += dv[r];
+    }
     sigma.assign(ns, 0.0);
     for (int i = 0; i < ns; ++i) {
       double s = 0.0;
-      for (int r = 0; r < np; ++r) s += X[(size_t)i * np + r] * b[r];
+      const double* Xi = &X[(size_t)i * np];
+      for (int r = 0; r < np; ++r) s += Xi[r] * pv[r];
       sigma[i] = -s;
     }
   }
@@ -319,7 +357,8 @@ Level make_level0(const FineMesh& fm) {
 }
 
 // One coarsening step.
-static bool coarsen(const Level& L, int target, int modes, int threads, Level& C, Transfer& T, std::string& err) {
+static bool coarsen(const Level& L, int target, int modes, int threads, bool use_gpu_eig, const EigBatchFn& eig_fn,
+                    Level& C, Transfer& T, std::string& err) {
   const int n = L.n_cells;
   // ---- cell graph ----------------------------------------------------------------------------------------------
   std::vector<std::vector<int>> nbv(n);
@@ -354,10 +393,15 @@ static bool coarsen(const Level& L, int target, int modes, int threads, Level& C
   std::vector<Scratch> scr(std::max(threads, 1));
   for (auto& s : scr) s.init(n, L.n_flux);
   // ---- spectral pressure bases ---------------------------------------------------------------------------------
+  // pass 1: S_N = D_N M_N^-1 D_N^T on each extended aggregate; pass 2: its smallest eigenpairs (batched on the GPU
+  // when available, else on the host); pass 3: restriction to A, q_PV first, SVD of the rest.
   std::vector<std::vector<double>> PA(na);
   std::vector<int> ma(na, 1);
   T.eig_gap.assign(na, 0.0);
   std::atomic<bool> fail(false);
+  std::vector<std::vector<double>> Smat(na);
+  std::vector<std::vector<int>> rows_in_N(na);
+  std::vector<int> nS(na, 0), kS(na, 1);
   parallel_for(na, threads, [&](int b, int e, int w) {
     Scratch& sc = scr[w];
     for (int a = b; a < e; ++a) {
@@ -368,22 +412,60 @@ static bool coarsen(const Level& L, int target, int modes, int threads, Level& C
       std::vector<int> UN = internal_flux(L, cN, sc);
       LocalProblem lp;
       assemble_local(L, cN, UN, sc, lp);
-      std::vector<double> S, X;
-      if (!schur(lp, S, X)) { fail = true; continue; }
-      int npA = np_of(a);
-      int m = std::min(modes, npA);
-      std::vector<double> vals, vecs;
-      double nextv = 0.0;
-      sym_eig_smallest(lp.np, S, m, vals, vecs, &nextv);
-      T.eig_gap[a] = nextv - vals[m - 1];
-      // rows of A's pressure unknowns inside N(A)
-      std::vector<int> rows;
+      std::vector<double> X;
+      if (!schur(lp, Smat[a], X)) { fail = true; continue; }
+      nS[a] = lp.np;
+      kS[a] = std::min(modes, np_of(a));
+      std::vector<int>& rows = rows_in_N[a];
       for (size_t k = 0, j = 0; k < cN.size(); ++k) {
         if (j < cA.size() && cN[k] == cA[j]) {
           for (int r = 0; r < L.m[cN[k]]; ++r) rows.push_back(lp.prow[k] + r);
           ++j;
         }
       }
+    }
+  });
+  if (fail) { err = "local flux mass matrix not SPD in an eigenproblem"; return false; }
+  std::vector<std::vector<double>> evecs(na);
+  std::vector<double> evals_m(na), evals_next(na);
+  bool done_gpu = false;
+  if (use_gpu_eig && eig_fn) {
+    std::vector<long long> aoff(na + 1, 0);
+    for (int a = 0; a < na; ++a) aoff[a + 1] = aoff[a] + (long long)nS[a] * nS[a];
+    std::vector<double> Aall(aoff[na]);
+    for (int a = 0; a < na; ++a) std::copy(Smat[a].begin(), Smat[a].end(), Aall.begin() + aoff[a]);
+    std::vector<double> vals, vecs;
+    std::vector<long long> voff;
+    std::string eerr;
+    if (eig_fn(na, aoff, nS, kS, Aall, vals, voff, vecs, eerr)) {
+      for (int a = 0; a < na; ++a) {
+        evecs[a].assign(vecs.begin() + voff[a], vecs.begin() + voff[a + 1]);
+        evals_m[a] = vals[(size_t)a * (kEigStride) + kS[a] - 1];
+        evals_next[a] = vals[(size_t)a * (kEigStride) + kS[a]];
+      }
+      done_gpu = true;
+    } else {
+      err = eerr;
+      return false;
+    }
+  }
+  parallel_for(na, threads, [&](int b, int e, int) {
+    for (int a = b; a < e; ++a) {
+      const int npA = np_of(a);
+      const int m = kS[a];
+      std::vector<double> vecs;
+      if (done_gpu) {
+        vecs.swap(evecs[a]);
+        T.eig_gap[a] = evals_next[a] - evals_m[a];
+      } else {
+        std::vector<double> vals;
+        double nextv = 0.0;
+        sym_eig_smallest(nS[a], Smat[a], m, vals, vecs, &nextv);
+        T.eig_gap[a] = nextv - vals[m - 1];
+      }
+      std::vector<double>().swap(Smat[a]);
+      const std::vector<int>& rows = rows_in_N[a];
+      std::vector<int> cA = cells_of(a);
       std::vector<double> q(npA);
       double qn = 0.0;
       {
@@ -395,11 +477,11 @@ static bool coarsen(const Level& L, int target, int modes, int threads, Level& C
       for (auto& x : q) x /= qn;
       std::vector<double> V((size_t)npA * m);
       for (int i = 0; i < npA; ++i)
-        for (int j = 0; j < m; ++j) V[(size_t)i * m + j] = vecs[(size_t)rows[i] * m + j];
-      for (int j = 0; j < m; ++j) {
-        double d = 0.0;
-        for (int i = 0; i < npA; ++i) d += q[i] * V[(size_t)i * m + j];
-        for (int i = 0; i < npA; ++i) V[(size_t)i * m + j] -= d * q[i];
+        for (int jj = 0; jj < m; ++jj) V[(size_t)i * m + jj] = vecs[(size_t)rows[i] * m + jj];
+      for (int jj = 0; jj < m; ++jj) {
+        double dd = 0.0;
+        for (int i = 0; i < npA; ++i) dd += q[i] * V[(size_t)i * m + jj];
+        for (int i = 0; i < npA; ++i) V[(size_t)i * m + jj] -= dd * q[i];
       }
       std::vector<std::vector<double>> cols;
       cols.push_back(q);
@@ -408,14 +490,14 @@ static bool coarsen(const Level& L, int target, int modes, int threads, Level& C
         jacobi_svd(npA, m, V, U, sv);
         int keep = 0;
         if (sv[0] > 0)
-          for (int j = 0; j < m; ++j)
-            if (sv[j] > 1e-10 * sv[0]) keep++;
+          for (int jj = 0; jj < m; ++jj)
+            if (sv[jj] > 1e-10 * sv[0]) keep++;
         keep = std::min(keep, std::min(m - 1, npA - 1));
-        for (int j = 0; j < keep; ++j) {
+        for (int jj = 0; jj < keep; ++jj) {
           std::vector<double> u(npA);
           int imax = 0;
           for (int i = 0; i < npA; ++i) {
-            u[i] = U[(size_t)i * m + j];
+            u[i] = U[(size_t)i * m + jj];
             if (std::fabs(u[i]) > std::fabs(u[imax])) imax = i;
           }
           if (u[imax] < 0)
@@ -426,7 +508,7 @@ static bool coarsen(const Level& L, int target, int modes, int threads, Level& C
       ma[a] = (int)cols.size();
       PA[a].assign((size_t)npA * ma[a], 0.0);
       for (int i = 0; i < npA; ++i)
-        for (int j = 0; j < ma[a]; ++j) PA[a][(size_t)i * ma[a] + j] = cols[j][i];
+        for (int jj = 0; jj < ma[a]; ++jj) PA[a][(size_t)i * ma[a] + jj] = cols[jj][i];
     }
   });
   if (fail) { err = "local flux mass matrix not SPD in an eigenproblem"; return false; }
@@ -618,36 +700,49 @@ static bool coarsen(const Level& L, int target, int modes, int threads, Level& C
   }
   // P_sigma in both orientations and Q_sigma
   {
-    std::vector<std::vector<std::pair<int, double>>> rowsP(L.n_flux);
+    parallel_for(nC, threads, [&](int b, int e, int) {
+      for (int J = b; J < e; ++J) {
+        std::sort(psi[J].begin(), psi[J].end());
+        std::sort(qrow[J].begin(), qrow[J].end());
+      }
+    });
     T.PsT.nrows = nC;
     T.PsT.ncols = L.n_flux;
-    T.PsT.off.assign(1, 0);
-    for (int J = 0; J < nC; ++J) {
-      auto col = psi[J];
-      std::sort(col.begin(), col.end());
-      for (auto& e : col) {
-        T.PsT.col.push_back(e.first);
-        T.PsT.val.push_back(e.second);
-        rowsP[e.first].push_back({J, e.second});
-      }
-      T.PsT.off.push_back((int)T.PsT.col.size());
-    }
-    T.Ps.nrows = L.n_flux;
-    T.Ps.ncols = nC;
-    T.Ps.off.assign(1, 0);
-    for (int i = 0; i < L.n_flux; ++i) {
-      for (auto& e : rowsP[i]) { T.Ps.col.push_back(e.first); T.Ps.val.push_back(e.second); }
-      T.Ps.off.push_back((int)T.Ps.col.size());
-    }
+    T.PsT.off.assign(nC + 1, 0);
     T.Qs.nrows = nC;
     T.Qs.ncols = L.n_flux;
-    T.Qs.off.assign(1, 0);
+    T.Qs.off.assign(nC + 1, 0);
     for (int J = 0; J < nC; ++J) {
-      auto r = qrow[J];
-      std::sort(r.begin(), r.end());
-      for (auto& e : r) { T.Qs.col.push_back(e.first); T.Qs.val.push_back(e.second); }
-      T.Qs.off.push_back((int)T.Qs.col.size());
+      T.PsT.off[J + 1] = T.PsT.off[J] + (int)psi[J].size();
+      T.Qs.off[J + 1] = T.Qs.off[J] + (int)qrow[J].size();
     }
+    T.PsT.col.resize(T.PsT.off[nC]);
+    T.PsT.val.resize(T.PsT.off[nC]);
+    T.Qs.col.resize(T.Qs.off[nC]);
+    T.Qs.val.resize(T.Qs.off[nC]);
+    parallel_for(nC, threads, [&](int b, int e, int) {
+      for (int J = b; J < e; ++J) {
+        int o = T.PsT.off[J];
+        for (auto& x : psi[J]) { T.PsT.col[o] = x.first; T.PsT.val[o] = x.second; ++o; }
+        o = T.Qs.off[J];
+        for (auto& x : qrow[J]) { T.Qs.col[o] = x.first; T.Qs.val[o] = x.second; ++o; }
+      }
+    });
+    // transpose by counting: row i of P_sigma lists its coarse columns J in ascending order
+    T.Ps.nrows = L.n_flux;
+    T.Ps.ncols = nC;
+    T.Ps.off.assign(L.n_flux + 1, 0);
+    for (int i : T.PsT.col) T.Ps.off[i + 1]++;
+    for (int i = 0; i < L.n_flux; ++i) T.Ps.off[i + 1] += T.Ps.off[i];
+    T.Ps.col.resize(T.PsT.col.size());
+    T.Ps.val.resize(T.PsT.col.size());
+    std::vector<int> fill(T.Ps.off.begin(), T.Ps.off.end() - 1);
+    for (int J = 0; J < nC; ++J)
+      for (int q = T.PsT.off[J]; q < T.PsT.off[J + 1]; ++q) {
+        int pos = fill[T.PsT.col[q]]++;
+        T.Ps.col[pos] = J;
+        T.Ps.val[pos] = T.PsT.val[q];
+      }
   }
   // static local matrices, divergence blocks, Pi~ weights
   C.mat_off.assign(na + 1, 0);
@@ -727,7 +822,8 @@ bool build_hierarchy(const FineMesh& fm, const Options& opt, Hierarchy& H, std::
   for (int l = 0; l + 1 < opt.n_levels; ++l) {
     Level C;
     Transfer T;
-    if (!coarsen(H.levels.back(), opt.agg_size[l], opt.modes[l], threads, C, T, err)) return false;
+    if (!coarsen(H.levels.back(), opt.agg_size[l], opt.modes[l], threads, opt.gpu_eig, opt.eig_fn, C, T, err))
+      return false;
     H.levels.push_back(std::move(C));
     H.transfers.push_back(std::move(T));
   }

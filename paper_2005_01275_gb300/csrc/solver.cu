@@ -14,6 +14,7 @@
 #include "dense.hpp"
 #include "hier.hpp"
 #include "kernels.cuh"
+#include "eig.cuh"
 #include "noalloc.cuh"
 #include "persist.cuh"
 
@@ -86,7 +87,7 @@ struct nlmg_ctx {
   double *f = nullptr, *g = nullptr, *rhs = nullptr, *dkap = nullptr, *Tval = nullptr, *dinv = nullptr,
          *diagT = nullptr, *jdiag = nullptr, *sig0 = nullptr, *ptr_e = nullptr, *fdp = nullptr;
   double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cpa = nullptr, *cpb = nullptr, *cq = nullptr;
-  double *sdiag = nullptr, *Ts64 = nullptr;
+  double *sdiag = nullptr, *Ts64 = nullptr, *dv1 = nullptr, *dv2 = nullptr;
   // Newton baseline: Jacobian off-diagonals, Jacobi scaling, GMRES(30) basis and work vectors
   static constexpr int kGmresM = 30;
   double *Joff = nullptr, *jdinv = nullptr, *gV = nullptr, *gw = nullptr, *gu = nullptr, *gr = nullptr,
@@ -456,6 +457,10 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
   CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
   launch_sdiag(c->st, c->F.N, c->diagT, c->sdiag);
   const bool fp32 = c->opt.lin_precision == 1;
+  // FP64 pipelined CG (one grid barrier per iteration) for loose tolerances; the two-barrier CG when a tight solve is
+  // asked for (its recursively updated residual stays close to the true one) and in FP32, where the extra
+  // recurrences of the pipelined form drift too far from the true residual
+  const bool pipe = !fp32 && c->opt.lin_tol >= 1e-6;
   int pi;
   if (fp32) {
     launch_scale_sell<float>(c->st, c->F, c->Tval, c->sdiag, c->Ts32);
@@ -465,8 +470,13 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
   } else {
     launch_scale_sell<double>(c->st, c->F, c->Tval, c->sdiag, c->Ts64);
     pi = c->prof_begin(0);
-    CK(launch_fine_cg<double>(c->st, c->F, c->Ts64, c->sdiag, R, -1.0, c->cx, c->cz, c->cr, c->cpa, c->cpb, c->cq,
-                              c->d_partial, gs, c->opt.lin_tol, c->opt.lin_maxit, c->d_res));
+    if (pipe)
+      CK(launch_fine_cg_pipe<double>(c->st, c->F, c->Ts64, c->sdiag, R, -1.0, c->cx, c->cz, c->cr, c->cpa, c->cpb,
+                                     c->cq, c->dv1, c->dv2, c->d_partial, gs, c->opt.lin_tol, c->opt.lin_maxit,
+                                     c->d_res));
+    else
+      CK(launch_fine_cg<double>(c->st, c->F, c->Ts64, c->sdiag, R, -1.0, c->cx, c->cz, c->cr, c->cpa, c->cpb,
+                                c->cq, c->d_partial, gs, c->opt.lin_tol, c->opt.lin_maxit, c->d_res));
   }
   c->prof_end(pi);
   count_launch(1);
@@ -475,13 +485,17 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
   if (c->h_res->err) throw Error(NLMG_ETIMEOUT, "grid barrier wait gave up in the fine CG kernel");
   const int it = c->h_res->iters;
   if (pi >= 0) {
-    // per iteration: the scaled matrix entries and their indices, p and r read, p_new and q written (phase A);
-    // p_new, y, r, q read and y, r written (phase B); once: b and S read, y and r written, then S and y read and
-    // dx written. Gathered neighbour values of a vector are counted once.
+    // Algorithmic bytes: per iteration the scaled matrix entries and their indices, then for the two-barrier CG
+    // r read, p and q read and written, p, q, y, r read and y, r written (11 vectors); for the pipelined CG w, z,
+    // s, p, y, r read and z, s, p, y, r, w written (12 vectors) and one extra product at the start. Once: b and
+    // S read, y and r written, then S and y read and dx written. Gathered neighbour values are counted once.
+    // Flops: one product (2 per stored entry) plus 6 FMAs per cell (two-barrier) or 9 (pipelined) per iteration.
     const double N = c->F.N, nnz = (double)c->nnz_real, v = fp32 ? 4.0 : 8.0;
-    c->prof.bytes[0] += (8.0 + 8.0) * N + 2.0 * v * N + 8.0 * N + v * N + 8.0 * N +
-                        it * ((4.0 + v) * nnz + 4.0 * v * N + 6.0 * v * N);
-    c->prof.flops[0] += it * (4.0 * nnz + 10.0 * N);   // FMAs count 2: p on the fly + product per entry
+    const double per_it_b = pipe ? (4.0 + v) * nnz + 12.0 * v * N : (4.0 + v) * nnz + 11.0 * v * N;
+    const double per_it_f = pipe ? 2.0 * nnz + 18.0 * N : 2.0 * nnz + 12.0 * N;   // an FMA counts 2
+    c->prof.bytes[0] += (8.0 + 8.0) * N + 2.0 * v * N + 8.0 * N + v * N + 8.0 * N + (pipe ? per_it_b : 0.0) +
+                        it * per_it_b;
+    c->prof.flops[0] += it * per_it_f;
   }
   c->lin_iters += it;
   c->lin_iters_level[0] += it;
@@ -820,6 +834,8 @@ void alloc_fine(nlmg_ctx* c) {
   c->cpb = c->dalloc<double>(N);
   c->cq = c->dalloc<double>(N);
   c->sdiag = c->dalloc<double>(N);
+  c->dv1 = c->dalloc<double>(N);
+  c->dv2 = c->dalloc<double>(N);
   c->Ts64 = c->dalloc<double>(c->F.nnz);
   c->Ts32 = c->dalloc<float>(c->F.nnz);
   for (float** pp : {&c->fy, &c->fr, &c->fpa, &c->fpb, &c->fq}) *pp = c->dalloc<float>(N);
@@ -1026,6 +1042,10 @@ static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, co
         throw Error(NLMG_EINVAL, "agg_size >= 2 and 1 <= modes <= 8 per level");
     }
     ho.threads = opt->setup_threads;
+    if (device) {
+      ho.gpu_eig = true;
+      ho.eig_fn = batched_smallest_eig;
+    }
     std::string err;
     if (!build_hierarchy(fm, ho, c->H, err)) throw Error(NLMG_EINVAL, err);
     if (!device) return NLMG_OK;
@@ -1372,6 +1392,15 @@ nlmg_status nlmg_fine_residual_noalloc(nlmg_ctx* c, const double* p_dev, double*
       throw Error(NLMG_ECUDA, err);
     return NLMG_OK;
   });
+}
+
+nlmg_status nlmg_measure_fp64(double* gflops) {
+  if (!gflops) return NLMG_EINVAL;
+  try {
+    return measure_fp64_peak(gflops) ? NLMG_OK : NLMG_ECUDA;
+  } catch (...) {
+    return NLMG_ECUDA;
+  }
 }
 
 const char* nlmg_last_error(const nlmg_ctx* c) { return c ? c->err.c_str() : "null context"; }

@@ -100,6 +100,7 @@ SIGNATURES = {
     "nlmg_profile": (C.c_int, [_P, C.c_int32]),
     "nlmg_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), _D, _D, _D]),
     "nlmg_fine_residual_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
+    "nlmg_measure_fp64": (C.c_int, [_D]),
     "nlmg_last_error": (C.c_char_p, [_P]),
     "nlmg_destroy": (None, [_P]),
 }
@@ -382,3 +383,12 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def measure_fp64_gflops():
+    """FP64 FMA throughput of the current device (GFLOP/s) from the library's synthetic kernel."""
+    v = C.c_double(0)
+    st = lib().nlmg_measure_fp64(C.byref(v))
+    if st != OK:
+        raise NlmgError(st, "fp64 measurement failed")
+    return v.value

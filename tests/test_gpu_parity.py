@@ -223,8 +223,14 @@ def test_mixed_precision_cg_reaches_fp64_solution(nlmg_lib):
 
 
 def test_single_level_newton_baseline(nlmg_lib):
-    """Exact Jacobian + GMRES: converges to p* and, once close, quadratically (Sec. 2.2 / 3.3.2 on level 0)."""
-    pr, H, ctx = _setup(nlmg_lib, "chan3d_11", **TIGHT)
+    """Exact Jacobian + GMRES (Sec. 2.2 / 3.3.2 on level 0). Linear case (kappa = 1): one Newton step solves the
+    problem. Mild nonlinear 2D case: converges to p* and, once close, quadratically."""
+    pr, H, ctx = _setup(nlmg_lib, "cart2d_32", **TIGHT)
+    lin = nlmg_lib.Context(pr.mesh, pr.kappa_kind, 0.0, dict(pr.opts))
+    pl, rep, st = lin.solve(pr.f_cell, pr.g_face, tol_rel=1e-11, tol_abs=1e-300, max_cycles=5, newton=True)
+    assert st == 0 and rep["cycles"] <= 2, rep
+    p_lin, _ = newton.solve(pr.mesh, pr.kappa_kind, 0.0, pr.f_cell, pr.g_face)
+    assert _rel(pl, p_lin) <= 1e-10
     pstar, _ = newton.solve(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, dp_clamp=pr.opts["dp_clamp"])
     p, rep, st = ctx.solve(pr.f_cell, pr.g_face, tol_rel=1e-12, tol_abs=1e-300, max_cycles=200, newton=True)
     assert st == 0, rep
