@@ -168,6 +168,80 @@ def run_serving(nlmg, n):
                     "FP32 CG inside the FP64 FAS; latency = submit -> result"}
 
 
+def run_multi_rhs(nlmg, pr, ctx, n_rhs, n_streams):
+    """n_rhs right-hand sides on the bench mesh and its hierarchy: one plain FP64 context solving them one after the
+    other, against nlmg_solve_many on n_streams contexts of the same hierarchy, in FP64 and with the FP32 inner CG.
+    Host buffers in and out in every variant (wall clock per batch)."""
+    import numpy as np
+    from synth.grids import multi_rhs_rows
+    F, G = multi_rhs_rows(pr.mesh, n_rhs, seed=5)
+    mctx = ctx.instance()
+    mctx.set_options(lin_precision=1)
+    ctx.solve_many(F[:n_streams], G[:n_streams], max_cycles=60, n_streams=n_streams)      # creates the instances
+    mctx.solve_many(F[:n_streams], G[:n_streams], max_cycles=60, n_streams=n_streams)
+    t0 = time.perf_counter()
+    seq = [ctx.solve(F[r], G[r], max_cycles=60) for r in range(n_rhs)]
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P, reps, sts = ctx.solve_many(F, G, max_cycles=60, n_streams=n_streams)
+    t_many = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    PM, mreps, msts = mctx.solve_many(F, G, max_cycles=60, n_streams=n_streams)
+    t_mixed = time.perf_counter() - t0
+    identical = all(np.array_equal(P[r], seq[r][0]) for r in range(n_rhs))
+    mixed_err = max(float(np.linalg.norm(PM[r] - seq[r][0]) / np.linalg.norm(seq[r][0])) for r in range(n_rhs))
+    mixed_res = max(m["res"] / m["res0"] for m in mreps)
+    mctx.close()
+    return {"rhs": n_rhs, "streams": n_streams, "ok": int(np.sum(sts == 0) + np.sum(msts == 0)),
+            "sequential_fp64_solves_per_s": n_rhs / t_seq,
+            "many_fp64_solves_per_s": n_rhs / t_many, "many_fp64_identical_to_sequential": bool(identical),
+            "many_mixed_solves_per_s": n_rhs / t_mixed, "mixed_max_rel_diff_vs_fp64": mixed_err,
+            "mixed_max_rel_residual": mixed_res,
+            "cycles_per_solve": float(np.mean([r["cycles"] for r in reps])),
+            "what": "right-hand sides share the mesh, K and the hierarchy (per row: Dirichlet value on x = 0 and a "
+                    "smooth source); host buffers in and out; wall clock per batch"}
+
+
+def run_voronoi(nlmg, n_side, steps):
+    """Unstructured workload: clipped Voronoi mesh of a jittered n_side^3 lattice, ln K ~ N(0, 2^2) correlated over 4
+    spacings, kappa = (1 + p^2)^-1, p = 1 on x = 0 and 0 on x = 1, 4-level FAS (aggregates 64 then 8, 4 modes).
+    FP64 and FP32-inner-CG solves; each solution's FP64 residual is recomputed by the library's residual call (the
+    GPU tests check that call against the oracle)."""
+    import numpy as np
+    from synth.grids import voronoi_problem
+    t0 = time.perf_counter()
+    pr = voronoi_problem(n_side)
+    t_mesh = time.perf_counter() - t0
+    opts = dict(pr.opts, n_levels=4, agg_size=[64, 8, 8], modes=[4, 4, 4])
+    t0 = time.perf_counter()
+    ctx = nlmg.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, opts)
+    t_setup = time.perf_counter() - t0
+    out = {"cells": int(pr.mesh.n_cells), "faces": int(pr.mesh.n_faces), "mesh_s": t_mesh, "setup_s": t_setup,
+           "levels": [ctx.level_info(l) for l in range(4)]}
+    ctx.set_data(pr.f_cell, pr.g_face)
+    r0 = np.linalg.norm(ctx.fine_residual(np.zeros(pr.mesh.n_cells)))
+    p64 = None
+    for prec in (0, 1):
+        ctx.set_options(lin_precision=prec)
+        ctx.solve(pr.f_cell, pr.g_face, max_cycles=80)
+        ms, rep, p = [], None, None
+        for _ in range(steps):
+            p, rep, st = ctx.solve(pr.f_cell, pr.g_face, max_cycles=80)
+            ms.append(rep["solve_ms"])
+        r = np.linalg.norm(ctx.fine_residual(p))
+        d = {"solves_per_s": 1e3 / np.mean(ms), "ms_per_solve": float(np.mean(ms)), "cycles": rep["cycles"],
+             "lin_iters_level": rep["lin_iters_level"][:4], "tol_tightened": rep["tol_tightened"],
+             "rel_residual_recomputed": float(r / r0)}
+        if prec == 0:
+            p64 = p
+            out["fp64"] = d
+        else:
+            d["rel_diff_vs_fp64_solution"] = float(np.linalg.norm(p - p64) / np.linalg.norm(p64))
+            out["mixed"] = d
+    ctx.close()
+    return out
+
+
 def run_reference(args, rank):
     if rank != 0:
         return 0
@@ -329,7 +403,10 @@ def run_gpu(args, rank, world, local_rank):
                  "rel_diff_vs_fp64_solution": diff, "lin_iters_level": mrep["lin_iters_level"][:3],
                  "what": "same FP64 FAS (residuals, transfers, coarse operators, convergence test in FP64); the CG "
                          "solves inside the Picard steps in FP32 (tolerances floored at 1e-6)"}
+    multi = run_multi_rhs(nlmg, pr, ctx, args.multi_rhs, args.streams) if (args.multi_rhs > 0 and world == 1) \
+        else None
     serving = run_serving(nlmg, args.serving) if (args.serving > 0 and world == 1) else None
+    voronoi = run_voronoi(nlmg, args.voronoi, max(1, args.steps // 2)) if (args.voronoi > 0 and world == 1) else None
     cpu = cpu_baseline_dict(N) if (args.cpu_baseline and world == 1) else None
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -346,7 +423,9 @@ def run_gpu(args, rank, world, local_rank):
         "wall_s_timed_region": wall,
         "roofline": roof,
         "mixed": mixed,
+        "multi_rhs": multi,
         "serving": serving,
+        "voronoi": voronoi,
         "cpu_baseline": cpu,
         "e2e": {"value": world * len(e2e_t) / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * (N + len(pr.g_face)),
                 "d2h_bytes_per_step": 8 * N},
@@ -371,6 +450,10 @@ def main():
     ap.add_argument("--coarse-lin-tol", type=float, default=None, help="coarse CG tolerance")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false", help="skip the FP32-CG variant")
     ap.add_argument("--serving", type=int, default=24, help="requests in the serving run (0 = skip)")
+    ap.add_argument("--multi-rhs", type=int, default=8, help="right-hand sides in the multi-RHS run (0 = skip)")
+    ap.add_argument("--streams", type=int, default=4, help="contexts (streams) of the multi-RHS solve")
+    ap.add_argument("--voronoi", type=int, default=0,
+                    help="lattice side of the unstructured Voronoi section (100 = 1M cells; 0 = skip)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if "RANK" in os.environ else 1))

@@ -94,6 +94,7 @@ typedef struct {
   int64_t lin_iters;         /* PCG iterations, all levels */
   int64_t kernel_launches;   /* CUDA kernels launched by the solve */
   int64_t lin_iters_level[8];/* PCG iterations per level */
+  int32_t tol_tightened;     /* times the inner tolerances were divided by 100 after a cycle that stalled */
   int32_t history_len;
   double history[64];        /* ||R|| after each cycle (first entry = res0) */
 } nlmg_report;
@@ -115,6 +116,33 @@ nlmg_status nlmg_setup(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlm
  * and nothing else; every device call on it returns NLMG_EINVAL. */
 nlmg_status nlmg_setup_host(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlmg_options* opt,
                             nlmg_ctx** out);
+
+/* A second context on the hierarchy of `base` (a context made by nlmg_setup). The hierarchy is built from the
+ * reference operator at kappa = 1 (the local eigenproblems of App. A use the linear reference operator), so it does
+ * not depend on the nonlinearity's parameter, the right-hand side or the boundary data: the new context shares the
+ * read-only device copy of the mesh and hierarchy with `base` (no second setup, no second copy) and owns only its
+ * work buffers and CUDA stream, so that solves on different contexts of one hierarchy may run concurrently from
+ * different host threads. `kappa` may be NULL (base's nonlinearity) or name another kind / parameter. The solver
+ * options are base's. The shared data are freed with the last context that refers to them; each context is
+ * destroyed with nlmg_destroy. Errors: NLMG_EINVAL (NULL base or out, host-only base), NLMG_ENOMEM / NLMG_ECUDA. */
+nlmg_status nlmg_instance(const nlmg_ctx* base, const nlmg_kappa* kappa, nlmg_ctx** out);
+
+/* Replaces the solver options of ctx (smoother, backtracking, clamp, coarsest steps, inner tolerances, precision)
+ * for the following solves. The hierarchy options (n_levels, agg_size, modes) must equal those ctx was set up with
+ * (NLMG_EINVAL otherwise); setup_threads is ignored. */
+nlmg_status nlmg_set_options(nlmg_ctx* ctx, const nlmg_options* opt);
+
+/* n_rhs independent FAS solves on the hierarchy of ctx (several right-hand sides and boundary data on one mesh):
+ * f_cell[n_rhs][n_cells], g_face[n_rhs][n_faces], x0[n_rhs][n_cells] (NULL = all zero) and p_out[n_rhs][n_cells]
+ * are host buffers, row r being right-hand side r. The solves run on up to n_streams contexts of the same hierarchy
+ * (ctx and n_streams - 1 instances made by nlmg_instance on first use and kept by ctx), each on its own stream and
+ * host thread; n_streams <= 0 picks 4. Every solve is the one nlmg_solve would return for that row (bitwise: each
+ * context owns its buffers and every reduction has a fixed order). rep (NULL or n_rhs entries) and status (NULL or
+ * n_rhs entries) receive each row's report and status. Returns NLMG_OK if every row converged, else the first
+ * failing row's status (its message is then ctx's last error). */
+nlmg_status nlmg_solve_many(nlmg_ctx* ctx, int32_t n_rhs, const double* f_cell, const double* g_face,
+                            const double* x0, double tol_rel, double tol_abs, int32_t max_cycles, int32_t n_streams,
+                            double* p_out, nlmg_report* rep, int32_t* status);
 
 /* Sets the problem data: f_cell[n_cells] (source density f|_K) and g_face[n_faces] (Dirichlet pressure or Neumann
  * flux density per boundary face, ignored on interior faces). [f]_K = |tau_K| f_K + sum_Neumann |eps| g_N
@@ -180,18 +208,24 @@ nlmg_status nlmg_get_transfer_dense(nlmg_ctx* ctx, int32_t level, int32_t which,
 /* ---- request loop (continuous batching of independent solves) -------------------------------------------- */
 /* Not a step of the paper's method: a serving layer over the calls above. Requests are queued on submit and taken in
  * arrival order by up to max_inflight worker threads as soon as their estimated device memory fits in
- * mem_budget_bytes; each request gets its own context (hierarchy built on the host with setup_threads_per_request
- * threads) and CUDA stream, so requests that arrive while others run are admitted as slots and memory free up and
- * their GPU work overlaps. A request's result is the same alone and in any mix (each context owns its buffers and
- * every reduction has a fixed order). All pointers are host pointers, copied at submit. */
+ * mem_budget_bytes; each request gets its own context (hierarchy built with setup_threads_per_request host threads)
+ * and CUDA stream, so requests that arrive while others run are admitted as slots and memory free up and their GPU
+ * work overlaps. Hierarchies stay on the device after their request: up to hierarchy_cache of them are kept (least
+ * recently used evicted first, also when the memory budget needs room), and a later request whose mesh arrays and
+ * hierarchy options (n_levels, agg_size, modes) are identical runs on an nlmg_instance of the kept hierarchy instead
+ * of a new setup, whatever its nonlinearity parameter, data and solver options. A request's result is the same
+ * alone and in any mix and with or without reuse (each context owns its buffers, every reduction has a fixed order
+ * and the setup is deterministic). All pointers are host pointers, copied at submit. */
 typedef struct nlmg_server nlmg_server;
 typedef struct {
   int32_t max_inflight;
   size_t mem_budget_bytes;
   int32_t setup_threads_per_request;
+  int32_t hierarchy_cache;   /* hierarchies kept for reuse (0 = none) */
 } nlmg_server_options;
 typedef struct {
   double queue_ms, setup_ms, solve_ms, latency_ms;   /* latency = submit -> result ready */
+  int32_t hierarchy_reused;                          /* 1 if the request ran on a kept hierarchy */
 } nlmg_request_times;
 void nlmg_server_default_options(nlmg_server_options* opt);
 /* Uses the calling thread's current CUDA device. */

@@ -450,9 +450,14 @@ __global__ void k_coarse_pbar_max(LevelDev L, const double* __restrict__ dp, Red
 // ---- launchers ---------------------------------------------------------------------------------------------------
 
 static std::atomic<long long> g_launches(0);
+static thread_local long long t_launches = 0;   // launches issued by the calling host thread
 long long launch_count() { return g_launches.load(); }
-void count_launch(int n) { g_launches.fetch_add(n); }
-#define COUNT(n) g_launches.fetch_add(n)
+long long launch_count_thread() { return t_launches; }
+void count_launch(int n) {
+  g_launches.fetch_add(n);
+  t_launches += n;
+}
+#define COUNT(n) count_launch(n)
 
 void launch_kappa(cudaStream_t st, int n, const double* p, const double* dp, double s, double* q, double* kap,
                   double* dkap, int kind, double a) {

@@ -80,7 +80,8 @@ inline int grid_for(long n) {
 }
 
 // number of kernels launched by this process through the launchers below
-long long launch_count();
+long long launch_count();          // whole process
+long long launch_count_thread();   // issued by the calling host thread
 void count_launch(int n);
 
 // launchers (kernels.cu)

@@ -128,8 +128,8 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partial, doubl
 // ---- fine level: A dx = bscale * b with the frozen TPFA matrix --------------------------------------------------
 // CG on the symmetrically Jacobi-scaled system (S A S) y = S bscale b, dx = S y, S = diag(A)^-1/2, so the scaled
 // matrix has a unit diagonal and only its off-diagonal entries Ts (SELL-32 layout, type T) are read. T = double is
-// the FP64 path; T = float runs the Krylov vectors and the matrix in FP32 (dot products still accumulate in FP64)
-// inside the FP64 nonlinear iteration. The matrix is applied to the residual r, which every iteration already
+// the FP64 path; T = float runs the Krylov vectors and the matrix in FP32 inside the FP64 nonlinear iteration
+// (per-thread partial sums of the dot products in FP32, block and grid sums in FP64). The matrix is applied to the residual r, which every iteration already
 // materialises, and A p follows by recurrence (p = r + beta p, q = A r + beta q): no neighbour values have to be
 // rebuilt and an iteration needs two grid barriers. The stopping test is on the scaled residual,
 // ||S r|| <= tol ||S r_0|| (the r.z of Jacobi-preconditioned CG).
@@ -144,13 +144,14 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __re
   __shared__ double sm[2 * 32];
   double* part0 = partial;
   double* part1 = partial + 2 * gridDim.x;
-  double a1[1] = {0.0};
+  T t1 = (T)0;   // per-thread partial sums in T (a thread holds one or two cells), block and grid sums in FP64
   GSTRIDE(i, F.N) {
     const T ri = (T)(sdiag[i] * bscale * b[i]);
     y[i] = (T)0;
     r[i] = ri;
-    a1[0] = fma((double)ri, (double)ri, a1[0]);
+    t1 = fma(ri, ri, t1);
   }
+  double a1[1] = {(double)t1};
   if (!grid_sum<1>(a1, part1, gs.out + 0, gs, sm)) return;
   const double rr0 = a1[0];
   double rr = rr0;
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __re
   T beta = (T)0;
   int it = 0;
   while (rr0 > 0.0 && rr > tol2 && it < maxit) {
-    double pq[1] = {0.0};
+    T tpq = (T)0;
     GSTRIDE(K, F.N) {
       const int s = K >> 5, lane = K & 31;
       const T rK = __ldcg(&r[K]);
@@ -185,18 +186,20 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __re
       const T qK = it == 0 ? acc : acc + beta * q[K];
       p[K] = pK;
       q[K] = qK;
-      pq[0] = fma((double)pK, (double)qK, pq[0]);
+      tpq = fma(pK, qK, tpq);
     }
+    double pq[1] = {(double)tpq};
     if (!grid_sum<1>(pq, part0, gs.out + 2, gs, sm)) return;
     const double alpha_d = pq[0] != 0.0 ? rr / pq[0] : 0.0;
     const T alpha = (T)alpha_d;
-    double rn[1] = {0.0};
+    T trn = (T)0;
     GSTRIDE(i, F.N) {
       y[i] = alpha * p[i] + y[i];
       const T ri = r[i] - alpha * q[i];
       r[i] = ri;
-      rn[0] = fma((double)ri, (double)ri, rn[0]);
+      trn = fma(ri, ri, trn);
     }
+    double rn[1] = {(double)trn};
     if (!grid_sum<1>(rn, part1, gs.out + 4, gs, sm)) return;
     beta = (T)(rr != 0.0 ? rn[0] / rr : 0.0);
     rr = rn[0];
@@ -352,7 +355,7 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
     ydiag[k] = (T)kp * Hc[L.hc_off[c] + (k - k0) * ni + (k - k0)];
   }
   if (!grid_barrier(gs)) return;
-  double a2[2] = {0.0, 0.0};
+  T u0 = (T)0, u1 = (T)0;   // per-thread partial sums in T, block and grid sums in FP64
   GSTRIDE(l, L.nlam) {
     const T xi = __ldcg(&ylam[L.lam_y0[l]]) + __ldcg(&ylam[L.lam_y1[l]]);
     const T di = (T)1 / (__ldcg(&ydiag[L.lam_y0[l]]) + __ldcg(&ydiag[L.lam_y1[l]]));
@@ -361,9 +364,10 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
     lr[l] = xi;
     const T zi = xi * di;
     lz[l] = zi;
-    a2[0] = fma((double)xi, (double)zi, a2[0]);
-    a2[1] = fma((double)xi, (double)xi, a2[1]);
+    u0 = fma(xi, zi, u0);
+    u1 = fma(xi, xi, u1);
   }
+  double a2[2] = {(double)u0, (double)u1};
   if (!grid_sum<2>(a2, part1, gs.out + 0, gs, sm)) return;
   double rz = a2[0];
   const double rr0 = a2[1];
@@ -384,7 +388,7 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
       ylam[k] = (T)kapc[c] * y;
     }
     if (!grid_barrier(gs)) return;
-    double a1[1] = {0.0};
+    T upq = (T)0;
     GSTRIDE(l, L.nlam) {
       const T zl = lz[l];
       const T hz = __ldcg(&ylam[L.lam_y0[l]]) + __ldcg(&ylam[L.lam_y1[l]]);
@@ -392,21 +396,24 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
       const T ql = it == 0 ? hz : hz + beta * lq[l];
       pp[l] = pl;
       lq[l] = ql;
-      a1[0] = fma((double)pl, (double)ql, a1[0]);
+      upq = fma(pl, ql, upq);
     }
+    double a1[1] = {(double)upq};
     if (!grid_sum<1>(a1, part0, gs.out + 2, gs, sm)) return;
     const double alpha_d = a1[0] != 0.0 ? rz / a1[0] : 0.0;
     const T alpha = (T)alpha_d;
-    a2[0] = a2[1] = 0.0;
+    u0 = u1 = (T)0;
     GSTRIDE(l, L.nlam) {
       lam[l] = alpha * pp[l] + lam[l];
       const T ri = lr[l] - alpha * lq[l];
       const T zi = ri * ldinv[l];
       lr[l] = ri;
       lz[l] = zi;
-      a2[0] = fma((double)ri, (double)zi, a2[0]);
-      a2[1] = fma((double)ri, (double)ri, a2[1]);
+      u0 = fma(ri, zi, u0);
+      u1 = fma(ri, ri, u1);
     }
+    a2[0] = (double)u0;
+    a2[1] = (double)u1;
     if (!grid_sum<2>(a2, part1, gs.out + 4, gs, sm)) return;
     beta = (T)(rz != 0.0 ? a2[0] / rz : 0.0);
     rz = a2[0];

@@ -3,7 +3,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <stdexcept>
@@ -64,6 +68,22 @@ struct FineState {
   double rn = 0.0;
 };
 
+// What every instance of one setup shares: the fine mesh and the hierarchy on the host, and their read-only device
+// copies (mesh arrays, level operators, transfers). Freed with the last context that refers to it.
+struct Shared {
+  FineMesh fm;
+  Hierarchy H;
+  std::vector<void*> allocs;
+  FineDev F;
+  std::vector<LevelDev> LD;
+  std::vector<TransferDev> TD;
+  long long nnz_real = 0;
+  double hyb_bytes_per_iter[8] = {0};
+  ~Shared() {
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
 }  // namespace
 
 struct nlmg_ctx {
@@ -71,14 +91,17 @@ struct nlmg_ctx {
   nlmg_options opt{};
   int kind = 0;
   double a = 0.0;
-  FineMesh fm;
-  Hierarchy H;
+  std::shared_ptr<Shared> sh = std::make_shared<Shared>();
+  FineMesh& fm() { return sh->fm; }
+  Hierarchy& H() { return sh->H; }
   cudaStream_t st = nullptr;
-  std::vector<void*> allocs;
-  FineDev F;
+  std::vector<void*> allocs;   // this context's work buffers
+  FineDev F;                   // copies of the shared descriptors (device pointers into sh)
   std::vector<LevelDev> LD;
   std::vector<TransferDev> TD;
   std::vector<CoarseBuf> CB;
+  std::vector<nlmg_ctx*> pool;   // extra instances for multi-right-hand-side solves, created on demand
+  std::mutex pool_mu;
   double* d_partial = nullptr;
   unsigned* d_cnt = nullptr;
   double* d_sc = nullptr;
@@ -96,11 +119,16 @@ struct nlmg_ctx {
   FineState cur, t1, t2;
   bool have_data = false;
   double tol_rel = 1e-8, tol_abs = 1e-10;   // outer tolerances, also used on the coarsest level
+  double lin_tol_eff = 1e-2, coarse_lin_tol_eff = 1e-1;   // inner tolerances of the running solve
+  int tightenings = 0;
+  void reset_inner_tols() {
+    lin_tol_eff = opt.lin_tol;
+    coarse_lin_tol_eff = opt.coarse_lin_tol;
+    tightenings = 0;
+  }
   // statistics of the running solve
   long long fine_evals = 0, lin_iters = 0;
   long long lin_iters_level[8] = {0};
-  long long nnz_real = 0;
-  double hyb_bytes_per_iter[8] = {0};
   Prof prof;
   PcgResult* d_res = nullptr;   // device result of the persistent CG kernels
   PcgResult* h_res = nullptr;   // pinned copy
@@ -136,12 +164,15 @@ struct nlmg_ctx {
     allocs.push_back(p);
     return (T*)p;
   }
+  // read-only data of the hierarchy: owned by the shared part
   template <class T>
   T* upload(const std::vector<T>& v) {
-    T* p = dalloc<T>(v.size());
+    void* p = nullptr;
+    CK(cudaMalloc(&p, std::max<size_t>(v.size(), 1) * sizeof(T)));
+    sh->allocs.push_back(p);
     if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
-    return p;
+    return (T*)p;
   }
   Reduce red(int slot) { return Reduce{d_partial, d_cnt, d_sc + slot}; }
   double read_sc(int slot) {
@@ -155,7 +186,7 @@ struct nlmg_ctx {
     v0 = h_sc[0];
     v1 = h_sc[1];
   }
-  int nlev() const { return (int)H.levels.size(); }
+  int nlev() const { return (int)sh->H.levels.size(); }
 };
 
 namespace {
@@ -164,7 +195,7 @@ namespace {
 // upload
 
 void upload_fine(nlmg_ctx* c) {
-  const FineMesh& fm = c->fm;
+  const FineMesh& fm = c->fm();
   const int N = fm.n_cells;
   std::vector<std::vector<int>> rows(N);
   std::vector<int> off(N + 1, 0), nbr, doff(N + 1, 0), dface, noff(N + 1, 0), nface;
@@ -219,7 +250,7 @@ void upload_fine(nlmg_ctx* c) {
     }
   }
   F.nnz = soff[F.nslice];
-  c->nnz_real = (long long)nbr.size();
+  c->sh->nnz_real = (long long)nbr.size();
   F.sell_off = c->upload(soff);
   F.sell_w = c->upload(sw);
   F.nbr = c->upload(snbr);
@@ -232,7 +263,7 @@ void upload_fine(nlmg_ctx* c) {
   F.neu_face = c->upload(nface);
   F.neu_area = c->upload(narea);
   F.vol = c->upload(fm.vol);
-  const Level& L0 = c->H.levels[0];
+  const Level& L0 = c->H().levels[0];
   std::vector<int> flk, fll, flf;
   std::vector<double> u0, u1;
   for (int j = 0; j < L0.n_flux; ++j) {
@@ -252,7 +283,7 @@ void upload_fine(nlmg_ctx* c) {
 }
 
 void upload_level(nlmg_ctx* c, int l) {
-  const Level& L = c->H.levels[l];
+  const Level& L = c->H().levels[l];
   LevelDev& D = c->LD[l];
   D.nc = L.n_cells;
   D.nflux = L.n_flux;
@@ -344,6 +375,15 @@ void upload_level(nlmg_ctx* c, int l) {
   D.if_cell = c->upload(ifc);
   D.slot_cell = c->upload(slc);
   D.p_cell = c->upload(pc);
+  // algorithmic bytes of one CG iteration of the hybridized solve: H blocks, their lambda ids, the per-interface
+  // buffer written and read, the lambda vectors (z, p_old gathered once; CG update 5 reads + 3 writes)
+  c->sh->hyb_bytes_per_iter[l] = 8.0 * (double)Hc.size() + 12.0 * D.nif + 8.0 * D.nc + 16.0 * D.nif + 136.0 * nlam;
+}
+
+// Work buffers of coarse level l (per context).
+void alloc_level(nlmg_ctx* c, int l) {
+  const LevelDev& D = c->LD[l];
+  const int nlam = D.nlam;
   CoarseBuf& B = c->CB[l];
   int nx = D.nflux + D.np;
   B.x = c->dalloc<double>(nx);
@@ -362,9 +402,6 @@ void upload_level(nlmg_ctx* c, int l) {
   B.f_ylam = c->dalloc<float>(D.nif);
   B.f_ydiag = c->dalloc<float>(D.nif);
   for (float** pp : {&B.f_lam, &B.f_lr, &B.f_lz, &B.f_lpa, &B.f_lpb, &B.f_lq, &B.f_ldinv}) *pp = c->dalloc<float>(nlam);
-  // algorithmic bytes of one CG iteration of the hybridized solve: H blocks, their lambda ids, the per-interface
-  // buffer written and read, the lambda vectors (z, p_old gathered once; CG update 5 reads + 3 writes)
-  c->hyb_bytes_per_iter[l] = 8.0 * (double)Hc.size() + 12.0 * D.nif + 8.0 * D.nc + 16.0 * D.nif + 136.0 * nlam;
   B.lam = c->dalloc<double>(nlam);
   B.lr = c->dalloc<double>(nlam);
   B.lz = c->dalloc<double>(nlam);
@@ -376,9 +413,9 @@ void upload_level(nlmg_ctx* c, int l) {
 }
 
 void upload_transfer(nlmg_ctx* c, int l) {
-  const Level& L = c->H.levels[l];
-  const Level& C = c->H.levels[l + 1];
-  const Transfer& T = c->H.transfers[l];
+  const Level& L = c->H().levels[l];
+  const Level& C = c->H().levels[l + 1];
+  const Transfer& T = c->H().transfers[l];
   TransferDev& D = c->TD[l];
   D.na = C.n_cells;
   D.nrows = L.n_p();
@@ -450,7 +487,8 @@ void backtrack0(nlmg_ctx* c, const double* dp, double s0) {
 }
 
 // Persistent CG on the frozen fine matrix (Tval, diagT): A dx = -R with symmetric Jacobi scaling; dx -> c->cx.
-// lin_precision 0 runs it in FP64, 1 in FP32 (vectors and matrix; dot products accumulate in FP64).
+// lin_precision 0 runs it in FP64, 1 in FP32 (vectors and matrix; per-thread partial sums in FP32, block and grid
+// sums in FP64).
 int fine_pcg(nlmg_ctx* c, const double* R) {
   GridSync gs{c->d_bar, c->d_bar + 32, &c->d_res->err, c->d_sc + 32};
   CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->st));
@@ -460,23 +498,23 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
   // FP64 pipelined CG (one grid barrier per iteration) for loose tolerances; the two-barrier CG when a tight solve is
   // asked for (its recursively updated residual stays close to the true one) and in FP32, where the extra
   // recurrences of the pipelined form drift too far from the true residual
-  const bool pipe = !fp32 && c->opt.lin_tol >= 1e-6;
+  const bool pipe = !fp32 && c->lin_tol_eff >= 1e-6;
   int pi;
   if (fp32) {
     launch_scale_sell<float>(c->st, c->F, c->Tval, c->sdiag, c->Ts32);
     pi = c->prof_begin(0);
     CK(launch_fine_cg<float>(c->st, c->F, c->Ts32, c->sdiag, R, -1.0, c->cx, c->fy, c->fr, c->fpa, c->fpb, c->fq,
-                             c->d_partial, gs, std::max(c->opt.lin_tol, 1e-6), c->opt.lin_maxit, c->d_res));
+                             c->d_partial, gs, std::max(c->lin_tol_eff, 1e-6), c->opt.lin_maxit, c->d_res));
   } else {
     launch_scale_sell<double>(c->st, c->F, c->Tval, c->sdiag, c->Ts64);
     pi = c->prof_begin(0);
     if (pipe)
       CK(launch_fine_cg_pipe<double>(c->st, c->F, c->Ts64, c->sdiag, R, -1.0, c->cx, c->cz, c->cr, c->cpa, c->cpb,
-                                     c->cq, c->dv1, c->dv2, c->d_partial, gs, c->opt.lin_tol, c->opt.lin_maxit,
+                                     c->cq, c->dv1, c->dv2, c->d_partial, gs, c->lin_tol_eff, c->opt.lin_maxit,
                                      c->d_res));
     else
       CK(launch_fine_cg<double>(c->st, c->F, c->Ts64, c->sdiag, R, -1.0, c->cx, c->cz, c->cr, c->cpa, c->cpb,
-                                c->cq, c->d_partial, gs, c->opt.lin_tol, c->opt.lin_maxit, c->d_res));
+                                c->cq, c->d_partial, gs, c->lin_tol_eff, c->opt.lin_maxit, c->d_res));
   }
   c->prof_end(pi);
   count_launch(1);
@@ -490,7 +528,7 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
     // s, p, y, r read and z, s, p, y, r, w written (12 vectors) and one extra product at the start. Once: b and
     // S read, y and r written, then S and y read and dx written. Gathered neighbour values are counted once.
     // Flops: one product (2 per stored entry) plus 6 FMAs per cell (two-barrier) or 9 (pipelined) per iteration.
-    const double N = c->F.N, nnz = (double)c->nnz_real, v = fp32 ? 4.0 : 8.0;
+    const double N = c->F.N, nnz = (double)c->sh->nnz_real, v = fp32 ? 4.0 : 8.0;
     const double per_it_b = pipe ? (4.0 + v) * nnz + 12.0 * v * N : (4.0 + v) * nnz + 11.0 * v * N;
     const double per_it_f = pipe ? 2.0 * nnz + 18.0 * N : 2.0 * nnz + 12.0 * N;   // an FMA counts 2
     c->prof.bytes[0] += (8.0 + 8.0) * N + 2.0 * v * N + 8.0 * N + v * N + 8.0 * N + (pipe ? per_it_b : 0.0) +
@@ -535,7 +573,7 @@ int fine_gmres(nlmg_ctx* c, const double* R) {
     CK(cudaMemsetAsync(c->cx, 0, (size_t)N * sizeof(double), c->st));
     return 0;
   }
-  const double tol = c->opt.lin_tol * beta0;
+  const double tol = c->lin_tol_eff * beta0;
   {
     const double one = 1.0;
     CK(cudaMemcpyAsync(c->gh + 191, &one, sizeof(double), cudaMemcpyHostToDevice, c->st));
@@ -712,10 +750,10 @@ int coarse_linear(nlmg_ctx* c, int l) {
   if (c->opt.lin_precision == 1)
     CK(launch_hyb_solve<float>(c->st, L, L.Hc32, L.Sinv32, B.kapc, bs, bp, B.f_ylam, B.f_ydiag, B.f_lam, B.f_lr,
                                B.f_lz, B.f_lpa, B.f_lpb, B.f_lq, B.f_ldinv, B.dx, B.dx + L.nflux, c->d_partial, gs,
-                               std::max(c->opt.coarse_lin_tol, 1e-6), c->opt.lin_maxit, c->d_res));
+                               std::max(c->coarse_lin_tol_eff, 1e-6), c->opt.lin_maxit, c->d_res));
   else
     CK(launch_hyb_solve<double>(c->st, L, L.Hc, L.Sinv, B.kapc, bs, bp, B.ylam, B.ydiag, B.lam, B.lr, B.lz, B.lpa,
-                                B.lpb, B.lq, B.ldinv, B.dx, B.dx + L.nflux, c->d_partial, gs, c->opt.coarse_lin_tol,
+                                B.lpb, B.lq, B.ldinv, B.dx, B.dx + L.nflux, c->d_partial, gs, c->coarse_lin_tol_eff,
                                 c->opt.lin_maxit, c->d_res));
   c->prof_end(pi);
   count_launch(1);
@@ -723,7 +761,7 @@ int coarse_linear(nlmg_ctx* c, int l) {
   CK(cudaStreamSynchronize(c->st));
   if (c->h_res->err) throw Error(NLMG_ETIMEOUT, "grid barrier wait gave up in the coarse CG kernel");
   const int it = c->h_res->iters;
-  if (pi >= 0) c->prof.bytes[1] += (double)it * c->hyb_bytes_per_iter[l] * (c->opt.lin_precision == 1 ? 0.5 : 1.0);
+  if (pi >= 0) c->prof.bytes[1] += (double)it * c->sh->hyb_bytes_per_iter[l] * (c->opt.lin_precision == 1 ? 0.5 : 1.0);
   c->lin_iters += it;
   c->lin_iters_level[l] += it;
   return it;
@@ -818,7 +856,7 @@ bool vcycle(nlmg_ctx* c, double r0, double tol_rel, double tol_abs) {
 void alloc_fine(nlmg_ctx* c) {
   const int N = c->F.N;
   c->f = c->dalloc<double>(N);
-  c->g = c->dalloc<double>(c->fm.n_faces);
+  c->g = c->dalloc<double>(c->fm().n_faces);
   c->rhs = c->dalloc<double>(N);
   c->dkap = c->dalloc<double>(N);
   c->Tval = c->dalloc<double>(c->F.nnz);
@@ -867,14 +905,14 @@ void set_data_dev(nlmg_ctx* c, const double* f_dev, const double* g_dev) {
   if (f_dev != c->f)
     CK(cudaMemcpyAsync(c->f, f_dev, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   if (g_dev != c->g)
-    CK(cudaMemcpyAsync(c->g, g_dev, (size_t)c->fm.n_faces * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(c->g, g_dev, (size_t)c->fm().n_faces * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   launch_rhs(c->st, c->F, c->f, c->g, c->rhs);
   c->have_data = true;
 }
 
 void set_data_host(nlmg_ctx* c, const double* f, const double* g) {
   CK(cudaMemcpyAsync(c->f, f, (size_t)c->F.N * sizeof(double), cudaMemcpyHostToDevice, c->st));
-  CK(cudaMemcpyAsync(c->g, g, (size_t)c->fm.n_faces * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->g, g, (size_t)c->fm().n_faces * sizeof(double), cudaMemcpyHostToDevice, c->st));
   set_data_dev(c, c->f, c->g);
 }
 
@@ -891,9 +929,10 @@ nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double
   c->fine_evals = 0;
   c->lin_iters = 0;
   for (auto& v : c->lin_iters_level) v = 0;
-  const long long launches0 = launch_count();
+  const long long launches0 = launch_count_thread();
   c->tol_rel = tol_rel;
   c->tol_abs = tol_abs;
+  c->reset_inner_tols();
   if (x0_dev)
     CK(cudaMemcpyAsync(c->cur.p, x0_dev, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   else
@@ -908,6 +947,7 @@ nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double
   nlmg_status st = NLMG_OK;
   const int saved_smoother = c->opt.smoother;
   if (picard_only) c->opt.smoother = NLMG_SMOOTH_PICARD;
+  double best = r0;
   while (true) {
     double rn = c->cur.rn;
     if (!std::isfinite(rn)) { st = NLMG_EDIVERGED; break; }
@@ -922,6 +962,16 @@ nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double
     }
     ++cycles;
     if (R.history_len < 64) R.history[R.history_len++] = c->cur.rn;
+    // Inexact inner solves: once the iteration is in its asymptotic phase (residual below 1e-2 of the initial one),
+    // a cycle that gains less than 10% on the best residual so far is taken as a sign that the loose inner
+    // tolerances limit the outer progress, and both are divided by 100 (floor 1e-12) for the rest of the solve.
+    if (best < 1e-2 * r0 && c->cur.rn > 0.9 * best &&
+        (c->lin_tol_eff > 1e-12 || c->coarse_lin_tol_eff > 1e-12)) {
+      c->lin_tol_eff = std::max(1e-12, c->lin_tol_eff * 1e-2);
+      c->coarse_lin_tol_eff = std::max(1e-12, c->coarse_lin_tol_eff * 1e-2);
+      c->tightenings++;
+    }
+    best = std::min(best, c->cur.rn);
     if (early) {
       if (!std::isfinite(c->cur.rn)) st = NLMG_EDIVERGED;
       break;
@@ -941,8 +991,9 @@ nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double
   R.solve_ms = ms;
   R.fine_evals = c->fine_evals;
   R.lin_iters = c->lin_iters;
-  R.kernel_launches = launch_count() - launches0;
+  R.kernel_launches = launch_count_thread() - launches0;
   for (int l = 0; l < 8; ++l) R.lin_iters_level[l] = c->lin_iters_level[l];
+  R.tol_tightened = c->tightenings;
   c->prof_flush();
   if (rep) *rep = R;
   return st;
@@ -979,7 +1030,7 @@ void nlmg_default_options(nlmg_options* o) {
   o->bt_theta = 0.9;
   o->dp_clamp = 0.0;
   o->coarsest_steps = 10;
-  o->lin_tol = 1e-2;          // inner solves of the Picard smoothing steps (see the readings in the design notes)
+  o->lin_tol = 1e-2;          // inner solves of the Picard smoothing steps: loose, the outer iteration corrects them
   o->lin_maxit = 5000;
   o->coarse_lin_tol = 1e-1;
   o->lin_precision = 0;
@@ -998,6 +1049,26 @@ nlmg_status nlmg_setup_host(const nlmg_mesh* mesh, const nlmg_kappa* kappa, cons
   return setup_impl(mesh, kappa, opt, out, false);
 }
 
+// Stream-side state of one context: its stream (created by the caller), reduction scratch, barrier words, pinned
+// read-back slots and every work buffer of the fine and coarse levels.
+static void init_work(nlmg_ctx* c) {
+  CK(cudaMallocHost(&c->h_sc, 16 * sizeof(double)));
+  c->d_partial = c->dalloc<double>((size_t)kMaxBlocks * 4);
+  c->d_cnt = c->dalloc<unsigned>(16);
+  CK(cudaMemsetAsync(c->d_cnt, 0, 16 * sizeof(unsigned), c->st));
+  c->d_sc = c->dalloc<double>(64);
+  c->d_res = c->dalloc<PcgResult>(1);
+  c->d_bar = c->dalloc<unsigned>(64);   // count and generation on separate 128-byte lines
+  CK(cudaMemsetAsync(c->d_bar, 0, 64 * sizeof(unsigned), c->st));
+  CK(cudaMallocHost(&c->h_res, sizeof(PcgResult)));
+  CK(cudaMemsetAsync(c->d_sc, 0, 64 * sizeof(double), c->st));
+  c->reset_inner_tols();
+  alloc_fine(c);
+  c->CB.resize(c->nlev());
+  for (int l = 1; l < c->nlev(); ++l) alloc_level(c, l);
+  CK(cudaStreamSynchronize(c->st));
+}
+
 static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlmg_options* opt,
                               nlmg_ctx** out, bool device) {
   if (!out) return NLMG_EINVAL;
@@ -1011,7 +1082,7 @@ static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, co
     c->opt = *opt;
     c->kind = kappa->kind;
     c->a = kappa->a;
-    FineMesh& fm = c->fm;
+    FineMesh& fm = c->fm();
     fm.n_cells = mesh->n_cells;
     fm.n_faces = mesh->n_faces;
     fm.vol.assign(mesh->cell_volume, mesh->cell_volume + mesh->n_cells);
@@ -1047,27 +1118,18 @@ static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, co
       ho.eig_fn = batched_smallest_eig;
     }
     std::string err;
-    if (!build_hierarchy(fm, ho, c->H, err)) throw Error(NLMG_EINVAL, err);
+    if (!build_hierarchy(fm, ho, c->H(), err)) throw Error(NLMG_EINVAL, err);
     if (!device) return NLMG_OK;
     CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
-    CK(cudaMallocHost(&c->h_sc, 16 * sizeof(double)));
-    c->d_partial = c->dalloc<double>((size_t)kMaxBlocks * 4);
-    c->d_cnt = c->dalloc<unsigned>(16);
-    CK(cudaMemsetAsync(c->d_cnt, 0, 16 * sizeof(unsigned), c->st));
-    c->d_sc = c->dalloc<double>(64);
-    c->d_res = c->dalloc<PcgResult>(1);
-    c->d_bar = c->dalloc<unsigned>(64);   // count and generation on separate 128-byte lines
-    CK(cudaMemsetAsync(c->d_bar, 0, 64 * sizeof(unsigned), c->st));
-    CK(cudaMallocHost(&c->h_res, sizeof(PcgResult)));
-    CK(cudaMemsetAsync(c->d_sc, 0, 64 * sizeof(double), c->st));
     upload_fine(c);
-    alloc_fine(c);
     c->LD.resize(c->nlev());
-    c->CB.resize(c->nlev());
     c->TD.resize(std::max(0, c->nlev() - 1));
     for (int l = 1; l < c->nlev(); ++l) upload_level(c, l);
     for (int l = 0; l + 1 < c->nlev(); ++l) upload_transfer(c, l);
-    CK(cudaStreamSynchronize(c->st));
+    c->sh->F = c->F;
+    c->sh->LD = c->LD;
+    c->sh->TD = c->TD;
+    init_work(c);
     return NLMG_OK;
   });
   if (s != NLMG_OK) {
@@ -1077,6 +1139,107 @@ static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, co
   }
   *out = c;
   return NLMG_OK;
+}
+
+nlmg_status nlmg_instance(const nlmg_ctx* base, const nlmg_kappa* kappa, nlmg_ctx** out) {
+  if (!out) return NLMG_EINVAL;
+  *out = nullptr;
+  if (!base || !base->st) return NLMG_EINVAL;
+  if (kappa && kappa->kind != 0 && kappa->kind != 1) return NLMG_EINVAL;
+  nlmg_ctx* c = new nlmg_ctx();
+  nlmg_status s = guarded(c, [&]() -> nlmg_status {
+    c->opt = base->opt;
+    c->kind = kappa ? kappa->kind : base->kind;
+    c->a = kappa ? kappa->a : base->a;
+    c->sh = base->sh;
+    c->F = c->sh->F;
+    c->LD = c->sh->LD;
+    c->TD = c->sh->TD;
+    CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
+    init_work(c);
+    return NLMG_OK;
+  });
+  if (s != NLMG_OK) {
+    nlmg_destroy(c);
+    return s;
+  }
+  *out = c;
+  return NLMG_OK;
+}
+
+nlmg_status nlmg_set_options(nlmg_ctx* c, const nlmg_options* opt) {
+  return guarded(c, [&]() -> nlmg_status {
+    if (!opt) throw Error(NLMG_EINVAL, "null options");
+    if (opt->n_levels != c->opt.n_levels) throw Error(NLMG_EINVAL, "n_levels is fixed at setup");
+    for (int l = 0; l + 1 < c->opt.n_levels; ++l)
+      if (opt->agg_size[l] != c->opt.agg_size[l] || opt->modes[l] != c->opt.modes[l])
+        throw Error(NLMG_EINVAL, "agg_size and modes are fixed at setup");
+    if (opt->nu_pre < 0 || opt->nu_post < 0 || opt->bt_nmax < 0 || !(opt->omega > 0) || opt->coarsest_steps < 0 ||
+        (opt->lin_precision != 0 && opt->lin_precision != 1))
+      throw Error(NLMG_EINVAL, "bad solver option");
+    const int threads = c->opt.setup_threads;
+    c->opt = *opt;
+    c->opt.setup_threads = threads;
+    c->reset_inner_tols();
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_solve_many(nlmg_ctx* c, int32_t n_rhs, const double* f_cell, const double* g_face,
+                            const double* x0, double tol_rel, double tol_abs, int32_t max_cycles, int32_t n_streams,
+                            double* p_out, nlmg_report* rep, int32_t* status) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_device(c);
+    if (n_rhs < 0 || (n_rhs > 0 && (!f_cell || !g_face || !p_out))) throw Error(NLMG_EINVAL, "bad argument");
+    if (n_rhs == 0) return NLMG_OK;
+    const int nw = std::max(1, std::min(n_streams <= 0 ? 4 : n_streams, n_rhs));
+    std::vector<nlmg_ctx*> workers{c};
+    {
+      std::lock_guard<std::mutex> lk(c->pool_mu);
+      while ((int)c->pool.size() < nw - 1) {
+        nlmg_ctx* w = nullptr;
+        nlmg_status st = nlmg_instance(c, nullptr, &w);
+        if (st != NLMG_OK) throw Error(st, "creating a solve instance failed");
+        c->pool.push_back(w);
+      }
+      for (int i = 0; i < nw - 1; ++i) {
+        nlmg_ctx* w = c->pool[i];
+        w->opt = c->opt;
+        w->kind = c->kind;
+        w->a = c->a;
+        workers.push_back(w);
+      }
+    }
+    const size_t N = (size_t)c->F.N, NF = (size_t)c->fm().n_faces;
+    std::vector<nlmg_status> st(n_rhs, NLMG_OK);
+    std::vector<std::string> msg(n_rhs);
+    std::atomic<int> next(0);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    auto run = [&](nlmg_ctx* w) {
+      cudaSetDevice(dev);
+      for (;;) {
+        const int r = next.fetch_add(1);
+        if (r >= n_rhs) break;
+        st[r] = nlmg_solve(w, f_cell + r * N, g_face + r * NF, x0 ? x0 + r * N : nullptr, tol_rel, tol_abs,
+                           max_cycles, p_out + r * N, rep ? rep + r : nullptr);
+        if (st[r] != NLMG_OK) msg[r] = w->err;
+      }
+    };
+    std::vector<std::thread> th;
+    for (int i = 1; i < nw; ++i) th.emplace_back(run, workers[i]);
+    run(c);
+    for (auto& t : th) t.join();
+    nlmg_status worst = NLMG_OK;
+    for (int r = 0; r < n_rhs; ++r) {
+      if (status) status[r] = st[r];
+      if (worst == NLMG_OK && st[r] != NLMG_OK) {
+        worst = st[r];
+        c->err = "right-hand side " + std::to_string(r) + ": " + msg[r];
+      }
+    }
+    return worst;
+  });
 }
 
 nlmg_status nlmg_set_data(nlmg_ctx* c, const double* f_cell, const double* g_face) {
@@ -1244,6 +1407,7 @@ nlmg_status nlmg_picard_update(nlmg_ctx* c, int32_t level, const double* x, cons
   return guarded(c, [&]() -> nlmg_status {
     need_device(c);
     if (level < 0 || level >= c->nlev()) throw Error(NLMG_EINVAL, "bad level");
+    c->reset_inner_tols();
     int it = 0;
     if (level == 0) {
       need_data(c);
@@ -1273,6 +1437,7 @@ nlmg_status nlmg_vcycle(nlmg_ctx* c, const double* p_in, double r0, double* p_ou
                         int32_t* early_exit) {
   return guarded(c, [&]() -> nlmg_status {
     need_data(c);
+    c->reset_inner_tols();
     CK(cudaMemcpyAsync(c->fdp, p_in, (size_t)c->F.N * sizeof(double), cudaMemcpyHostToDevice, c->st));
     fine_eval(c, c->fdp, nullptr, 0.0, c->cur);
     c->tol_rel = 1e-8;
@@ -1289,7 +1454,7 @@ nlmg_status nlmg_vcycle(nlmg_ctx* c, const double* p_in, double r0, double* p_ou
 nlmg_status nlmg_level_info_get(nlmg_ctx* c, int32_t level, nlmg_level_info* out) {
   return guarded(c, [&]() -> nlmg_status {
     if (level < 0 || level >= c->nlev() || !out) throw Error(NLMG_EINVAL, "bad level");
-    const Level& L = c->H.levels[level];
+    const Level& L = c->H().levels[level];
     out->n_cells = L.n_cells;
     out->n_flux = L.n_flux;
     out->n_p = L.n_p();
@@ -1303,9 +1468,9 @@ nlmg_status nlmg_level_info_get(nlmg_ctx* c, int32_t level, nlmg_level_info* out
 nlmg_status nlmg_get_aggregates(nlmg_ctx* c, int32_t level, int32_t* agg_of, int32_t* m_out) {
   return guarded(c, [&]() -> nlmg_status {
     if (level < 0 || level + 1 >= c->nlev()) throw Error(NLMG_EINVAL, "bad level");
-    const Transfer& T = c->H.transfers[level];
+    const Transfer& T = c->H().transfers[level];
     if (agg_of) std::copy(T.agg_of.begin(), T.agg_of.end(), agg_of);
-    if (m_out) std::copy(c->H.levels[level + 1].m.begin(), c->H.levels[level + 1].m.end(), m_out);
+    if (m_out) std::copy(c->H().levels[level + 1].m.begin(), c->H().levels[level + 1].m.end(), m_out);
     return NLMG_OK;
   });
 }
@@ -1313,9 +1478,9 @@ nlmg_status nlmg_get_aggregates(nlmg_ctx* c, int32_t level, int32_t* agg_of, int
 nlmg_status nlmg_get_transfer_dense(nlmg_ctx* c, int32_t level, int32_t which, double* dense) {
   return guarded(c, [&]() -> nlmg_status {
     if (level < 0 || level + 1 >= c->nlev() || !dense) throw Error(NLMG_EINVAL, "bad level");
-    const Level& L = c->H.levels[level];
-    const Level& C = c->H.levels[level + 1];
-    const Transfer& T = c->H.transfers[level];
+    const Level& L = c->H().levels[level];
+    const Level& C = c->H().levels[level + 1];
+    const Transfer& T = c->H().transfers[level];
     if (which == 0) {
       size_t nc = C.n_p();
       std::fill(dense, dense + (size_t)L.n_p() * nc, 0.0);
@@ -1364,7 +1529,7 @@ nlmg_status nlmg_profile_read(nlmg_ctx* c, int32_t kernel, int64_t* launches, do
     if (total_ms) *total_ms = c->prof.ms[kernel];
     // algorithmic bytes: every array the kernel streams, read or written once; gathered neighbour values are
     // counted once (they are the same vector); SELL padding is not counted
-    const double N = c->F.N, nnz = (double)c->nnz_real;
+    const double N = c->F.N, nnz = (double)c->sh->nnz_real;
     double b = 0.0;
     if (kernel == 0 || kernel == 1) b = c->prof.n[kernel] ? c->prof.bytes[kernel] / c->prof.n[kernel] : 0.0;
     if (kernel == 2) b = 20.0 * nnz + 8.0 * N * 4;                          // nbr + 2 ups, q, kap, rhs, R
@@ -1407,6 +1572,7 @@ const char* nlmg_last_error(const nlmg_ctx* c) { return c ? c->err.c_str() : "nu
 
 void nlmg_destroy(nlmg_ctx* c) {
   if (!c) return;
+  for (nlmg_ctx* w : c->pool) nlmg_destroy(w);
   if (c->st) cudaStreamSynchronize(c->st);
   for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);

@@ -44,23 +44,23 @@ class Report(C.Structure):
     _fields_ = [("cycles", C.c_int32), ("early_exit", C.c_int32), ("res0", C.c_double), ("res", C.c_double),
                 ("solve_ms", C.c_double), ("fine_evals", C.c_int64), ("lin_iters", C.c_int64),
                 ("kernel_launches", C.c_int64), ("lin_iters_level", C.c_int64 * 8),
-                ("history_len", C.c_int32), ("history", C.c_double * 64)]
+                ("tol_tightened", C.c_int32), ("history_len", C.c_int32), ("history", C.c_double * 64)]
 
     def as_dict(self):
         return dict(cycles=self.cycles, early_exit=bool(self.early_exit), res0=self.res0, res=self.res,
                     solve_ms=self.solve_ms, fine_evals=self.fine_evals, lin_iters=self.lin_iters,
                     kernel_launches=self.kernel_launches, lin_iters_level=list(self.lin_iters_level),
-                    history=list(self.history[:self.history_len]))
+                    tol_tightened=self.tol_tightened, history=list(self.history[:self.history_len]))
 
 
 class ServerOptions(C.Structure):
     _fields_ = [("max_inflight", C.c_int32), ("mem_budget_bytes", C.c_size_t),
-                ("setup_threads_per_request", C.c_int32)]
+                ("setup_threads_per_request", C.c_int32), ("hierarchy_cache", C.c_int32)]
 
 
 class RequestTimes(C.Structure):
     _fields_ = [("queue_ms", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
-                ("latency_ms", C.c_double)]
+                ("latency_ms", C.c_double), ("hierarchy_reused", C.c_int32)]
 
 
 class LevelInfo(C.Structure):
@@ -77,6 +77,10 @@ SIGNATURES = {
     "nlmg_default_options": (None, [C.POINTER(Options)]),
     "nlmg_setup": (C.c_int, [C.POINTER(Mesh), C.POINTER(Kappa), C.POINTER(Options), C.POINTER(_P)]),
     "nlmg_setup_host": (C.c_int, [C.POINTER(Mesh), C.POINTER(Kappa), C.POINTER(Options), C.POINTER(_P)]),
+    "nlmg_instance": (C.c_int, [_P, C.POINTER(Kappa), C.POINTER(_P)]),
+    "nlmg_solve_many": (C.c_int, [_P, C.c_int32, _D, _D, _D, C.c_double, C.c_double, C.c_int32, C.c_int32, _D,
+                                  C.POINTER(Report), _I]),
+    "nlmg_set_options": (C.c_int, [_P, C.POINTER(Options)]),
     "nlmg_set_data": (C.c_int, [_P, _D, _D]),
     "nlmg_solve": (C.c_int, [_P, _D, _D, _D, C.c_double, C.c_double, C.c_int32, _D, C.POINTER(Report)]),
     "nlmg_solve_device": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_double, C.c_int32, _P, C.POINTER(Report)]),
@@ -185,6 +189,43 @@ class Context:
         if st != OK:
             raise NlmgError(st, "setup failed")
         self.h = h
+
+    def instance(self, kappa_kind=None, kappa_a=None):
+        """A second context sharing this one's device hierarchy (own work buffers and stream)."""
+        k = None if kappa_kind is None else C.byref(Kappa(int(kappa_kind), float(kappa_a)))
+        h = _P()
+        self._check(lib().nlmg_instance(self.h, k, C.byref(h)))
+        other = Context.__new__(Context)
+        other._keep, other.n_cells, other.n_faces, other.opts = self._keep, self.n_cells, self.n_faces, self.opts
+        other._base = self
+        other.h = h
+        return other
+
+    def set_options(self, **changes):
+        """Change solver options (not the hierarchy ones) for the following solves."""
+        o = Options.from_buffer_copy(self.opts)
+        for k, v in changes.items():
+            setattr(o, k, v)
+        self._check(lib().nlmg_set_options(self.h, C.byref(o)))
+        self.opts = o
+
+    def solve_many(self, f_rows, g_rows, x0_rows=None, tol_rel=1e-8, tol_abs=1e-10, max_cycles=50, n_streams=4,
+                   allow_noconv=False):
+        """Independent FAS solves of every row of f_rows [n_rhs, n_cells] / g_rows [n_rhs, n_faces]."""
+        f = np.ascontiguousarray(f_rows, dtype=np.float64)
+        g = np.ascontiguousarray(g_rows, dtype=np.float64)
+        n = f.shape[0]
+        if f.shape != (n, self.n_cells) or g.shape != (n, self.n_faces):
+            raise ValueError("f_rows must be [n_rhs, n_cells] and g_rows [n_rhs, n_faces]")
+        x0 = None if x0_rows is None else np.ascontiguousarray(x0_rows, dtype=np.float64).reshape(n, self.n_cells)
+        out = np.zeros((n, self.n_cells))
+        reps = (Report * max(n, 1))()
+        sts = np.zeros(max(n, 1), np.int32)
+        st = lib().nlmg_solve_many(self.h, n, _dp(f), _dp(g), None if x0 is None else _dp(x0), tol_rel, tol_abs,
+                                   max_cycles, n_streams, _dp(out), reps, sts.ctypes.data_as(_I))
+        if not (st == OK or (allow_noconv and st == ENOCONV)):
+            self._check(st)
+        return out, [reps[i].as_dict() for i in range(n)], sts[:n].copy()
 
     def _check(self, st):
         if st not in (OK,):
@@ -331,12 +372,14 @@ class Context:
 class Server:
     """Continuous-batching request loop of the library (nlmg_server_*)."""
 
-    def __init__(self, max_inflight=8, mem_budget_bytes=16 << 30, setup_threads_per_request=2):
+    def __init__(self, max_inflight=8, mem_budget_bytes=16 << 30, setup_threads_per_request=2, hierarchy_cache=None):
         o = ServerOptions()
         lib().nlmg_server_default_options(C.byref(o))
         o.max_inflight = max_inflight
         o.mem_budget_bytes = mem_budget_bytes
         o.setup_threads_per_request = setup_threads_per_request
+        if hierarchy_cache is not None:
+            o.hierarchy_cache = hierarchy_cache
         h = _P()
         st = lib().nlmg_server_create(C.byref(o), C.byref(h))
         if st != OK:
@@ -371,7 +414,7 @@ class Server:
             return None
         del self._sizes[ticket]
         return p, rep.as_dict(), dict(queue_ms=tm.queue_ms, setup_ms=tm.setup_ms, solve_ms=tm.solve_ms,
-                                      latency_ms=tm.latency_ms), st
+                                      latency_ms=tm.latency_ms, hierarchy_reused=bool(tm.hierarchy_reused)), st
 
     def close(self):
         if getattr(self, "h", None):

@@ -80,65 +80,78 @@ def cartesian_mesh(shape, K, dirichlet_x=True):
 def voronoi_mesh(n_side, K_of_points, seed=3, jitter=0.4):
     """Clipped 3D Voronoi tessellation of a jittered n_side^3 lattice in the unit cube (an unstructured cell graph).
 
-    Points x_K = lattice centres + U(-jitter, jitter) h. The cube clips the cells by mirroring the points across its
-    six faces: a ridge between a point and its own mirror is a boundary face. Interior faces bisect the K-L segment,
-    so the collocation point is the midpoint and Ups_bar = |eps| K_0 / (d_KL / 2); boundary faces use the distance to
-    the face. Faces on x = 0 and x = 1 are Dirichlet, the rest Neumann. K_of_points(points) gives K_0 per cell.
+    Points x_K = lattice centres + U(-jitter, jitter) h. The cube clips the cells by mirroring the points within three
+    lattice spacings of each of its six faces across that face: a ridge between a point and its own mirror is a
+    boundary face. Interior faces bisect the K-L segment, so the collocation point is the midpoint and
+    Ups_bar = |eps| K_0 / (d_KL / 2); boundary faces use the distance to the face. A cell's volume is the sum of the
+    pyramids from its point over its faces (|eps| d / 6 each, the point lying inside its own convex cell). Faces on
+    x = 0 and x = 1 are Dirichlet, the rest Neumann. K_of_points(points) gives K_0 per cell.
     """
-    from scipy.spatial import ConvexHull, Voronoi
+    from scipy.spatial import Voronoi
     rng = np.random.default_rng(seed)
     h = 1.0 / n_side
     g1 = (np.arange(n_side) + 0.5) * h
     P = np.stack(np.meshgrid(g1, g1, g1, indexing="ij"), -1).reshape(-1, 3)
     P = np.clip(P + rng.uniform(-jitter, jitter, P.shape) * h, 1e-6, 1 - 1e-6)
     n = P.shape[0]
-    mirrors = []
+    mirrors, owner, mface = [], [], []
     for ax in range(3):
         for side in (0.0, 1.0):
-            Q = P.copy()
+            sel = np.where(np.abs(P[:, ax] - side) < 3.0 * h)[0]
+            Q = P[sel].copy()
             Q[:, ax] = 2 * side - Q[:, ax]
             mirrors.append(Q)
+            owner.append(sel)
+            mface.append(np.full(sel.size, 2 * ax + int(side)))
     allp = np.concatenate([P] + mirrors)
+    owner = np.concatenate(owner)
+    mface = np.concatenate(mface)
     vor = Voronoi(allp)
     K = np.asarray(K_of_points(P), dtype=np.float64)
+    rp = np.asarray(vor.ridge_points)
+    lens = np.fromiter((len(r) for r in vor.ridge_vertices), dtype=np.int64, count=len(vor.ridge_vertices))
+    flat = np.fromiter((v for r in vor.ridge_vertices for v in r), dtype=np.int64, count=int(lens.sum()))
+    start = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    has_inf = np.zeros(len(lens), bool)
+    np.logical_or.at(has_inf, np.repeat(np.arange(len(lens)), lens), flat < 0)
+    keep = ~has_inf & ((rp[:, 0] < n) | (rp[:, 1] < n))
+    # polygon areas: fan of triangles (centroid, v_k, v_k+1) over the cyclically ordered ridge vertices
+    rid = np.repeat(np.arange(len(lens)), lens)
+    V = vor.vertices[np.where(flat < 0, 0, flat)]
+    c0 = np.add.reduceat(V, start, axis=0) / lens[:, None]
+    nxt = np.arange(flat.size) + 1
+    last = start + lens - 1
+    nxt[last] = start
+    tri = 0.5 * np.linalg.norm(np.cross(V - c0[rid], V[nxt] - c0[rid]), axis=1)
+    A = np.add.reduceat(tri, start)
+    keep &= A > 1e-14
+    rp, A = rp[keep], A[keep]
+    a, b = rp[:, 0], rp[:, 1]
+    interior = (a < n) & (b < n)
+    lo, hi = np.minimum(a, b)[interior], np.maximum(a, b)[interior]
+    Ai = A[interior]
+    di = np.linalg.norm(P[lo] - P[hi], axis=1)
+    inner = np.where(a < n, a, b)[~interior]
+    outer = np.where(a < n, b, a)[~interior]
+    Ab = A[~interior]
+    db = np.linalg.norm(P[inner] - allp[outer], axis=1) / 2.0
+    if np.any(owner[outer - n] != inner):
+        raise RuntimeError("a boundary ridge joins a point to another point's mirror")
+    side = mface[outer - n]
+    ax = side // 2
     vol = np.zeros(n)
-    for i in range(n):
-        reg = vor.regions[vor.point_region[i]]
-        vol[i] = ConvexHull(vor.vertices[reg]).volume
-    fc, ht, bc, area = [], [], [], []
-    for (a, b), rv in zip(vor.ridge_points, vor.ridge_vertices):
-        if a >= n and b >= n:
-            continue
-        if -1 in rv:
-            continue
-        V = vor.vertices[rv]
-        c0 = V.mean(0)
-        A = 0.0
-        for k in range(len(V)):
-            A += 0.5 * np.linalg.norm(np.cross(V[k] - c0, V[(k + 1) % len(V)] - c0))
-        if A <= 1e-14:
-            continue
-        if a < n and b < n:
-            lo, hi = min(a, b), max(a, b)
-            d = np.linalg.norm(P[lo] - P[hi])
-            fc.append((lo, hi))
-            ht.append((A * K[lo] / (d / 2), A * K[hi] / (d / 2)))
-            bc.append(BC_INTERIOR)
-            area.append(A)
-        else:
-            inner = a if a < n else b
-            outer = b if a < n else a
-            k = (outer - n) // n            # mirror block: ax * 2 + side
-            ax = k // 2
-            d = np.linalg.norm(P[inner] - allp[outer]) / 2.0
-            fc.append((inner, -1))
-            ht.append((A * K[inner] / d, 0.0))
-            bc.append(BC_DIRICHLET if ax == 0 else BC_NEUMANN)
-            area.append(A)
-    fc = np.array(fc, dtype=np.int32)
-    order = np.lexsort((fc[:, 1], fc[:, 0], np.array(bc) != BC_INTERIOR))
-    mesh = Mesh(n_cells=n, cell_volume=vol, face_cells=fc[order], half_trans=np.array(ht)[order],
-                face_bc=np.array(bc, np.uint8)[order], face_area=np.array(area)[order], shape=(n,), perm=K)
+    np.add.at(vol, lo, Ai * di / 6.0)
+    np.add.at(vol, hi, Ai * di / 6.0)
+    np.add.at(vol, inner, Ab * db / 3.0)
+    fc = np.concatenate([np.stack([lo, hi], 1), np.stack([inner, np.full(inner.size, -1)], 1)]).astype(np.int32)
+    ht = np.concatenate([np.stack([Ai * K[lo] / (di / 2), Ai * K[hi] / (di / 2)], 1),
+                         np.stack([Ab * K[inner] / db, np.zeros(inner.size)], 1)])
+    bc = np.concatenate([np.full(lo.size, BC_INTERIOR), np.where(ax == 0, BC_DIRICHLET, BC_NEUMANN)]).astype(np.uint8)
+    area = np.concatenate([Ai, Ab])
+    tie = np.concatenate([np.zeros(lo.size, np.int64), side])          # which cube face, for a cell's boundary faces
+    order = np.lexsort((tie, fc[:, 1], fc[:, 0], bc != BC_INTERIOR))
+    mesh = Mesh(n_cells=n, cell_volume=vol, face_cells=fc[order], half_trans=ht[order], face_bc=bc[order],
+                face_area=area[order], shape=(n,), perm=K)
     mesh.points = P
     return mesh
 
@@ -267,6 +280,25 @@ def voronoi_problem(n_side=12, seed=3):
     g[d] = np.where(mesh.points[mesh.face_cells[d, 0], 0] < 0.5, 1.0, 0.0)
     opts = default_options(n_levels=3, agg_size=[27, 8, 8], modes=[4, 3, 3])
     return Problem(mesh, KAPPA_INV1P2, 0.0, np.zeros(mesh.n_cells), g, opts, "voronoi")
+
+
+def multi_rhs_rows(mesh, n_rhs, seed):
+    """n_rhs data sets on one Cartesian mesh: per row a Dirichlet value U[0.5, 1.5] on x = 0 and U[-0.5, 0.5] on
+    x = 1, and a smooth source density, the sum of 4 seeded Gaussian bumps (centres U[0.2, 0.8]^d, amplitudes
+    U[-0.5, 0.5], width^2 = 0.01 of the unit box). Returns F [n_rhs, N] and G [n_rhs, F]."""
+    rng = np.random.default_rng(seed)
+    shape = mesh.shape
+    d = np.where(mesh.face_bc == BC_DIRICHLET)[0]
+    left = mesh.face_cells[d, 0] % shape[0] == 0
+    x = (np.stack(np.unravel_index(np.arange(mesh.n_cells), shape, order="F"), axis=1) + 0.5) / np.array(shape)
+    F = np.zeros((n_rhs, mesh.n_cells))
+    G = np.zeros((n_rhs, mesh.n_faces))
+    for r in range(n_rhs):
+        G[r, d] = np.where(left, rng.uniform(0.5, 1.5), rng.uniform(-0.5, 0.5))
+        for _ in range(4):
+            c = rng.uniform(0.2, 0.8, len(shape))
+            F[r] += rng.uniform(-0.5, 0.5) * np.exp(-np.sum((x - c) ** 2, axis=1) / 0.02)
+    return F, G
 
 
 CONFIGS = ("cart2d_32", "chan3d_64")

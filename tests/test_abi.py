@@ -1,5 +1,6 @@
 """CPU checks of the C-ABI library: it builds for sm_103a, loads, exports every declared symbol, and its host-side
 hierarchy setup (aggregation, spectral bases, flux space) agrees with the oracle."""
+import ctypes
 import os
 import re
 
@@ -70,3 +71,15 @@ def test_host_hierarchy_matches_oracle(nlmg_lib, name, scale, upd):
         assert np.abs(Ps - tr.Psigma.toarray()).max() < 1e-9 * scale_
         assert np.abs(Qs @ Ps - np.eye(Ps.shape[1])).max() < 1e-10
         assert np.abs(Qs - tr.Qsigma.toarray()).max() < 1e-9 * max(1.0, np.abs(tr.Qsigma).max())
+
+
+def test_set_options_keeps_the_hierarchy_fixed(nlmg_lib):
+    pr = problem_config("cart2d_32", scale=8)
+    ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.opts, device=False)
+    ctx.set_options(nu_pre=3, lin_tol=1e-4, lin_precision=1)
+    assert ctx.opts.nu_pre == 3 and ctx.opts.lin_precision == 1
+    for bad in (dict(n_levels=3), dict(modes=(ctypes.c_int32 * 8)(3, 3, 3, 3, 3, 3, 3, 3)), dict(lin_precision=2),
+                dict(omega=0.0)):
+        with pytest.raises(nlmg_lib.NlmgError):
+            ctx.set_options(**bad)
+    ctx.close()

@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 from oracle import tpfa
-from synth.grids import cartesian_mesh, lognormal_field, problem_config
+from synth.grids import cartesian_mesh, lognormal_field, multi_rhs_rows, problem_config
 
 pytestmark = pytest.mark.gpu
 
@@ -66,3 +66,35 @@ def test_admission_by_memory_and_oversized_request(nlmg_lib):
         tiny.submit(mesh, 0, a, opts, f, g)
     srv.close()
     tiny.close()
+
+
+def test_kept_hierarchy_is_reused_with_identical_results(nlmg_lib):
+    """Requests on one mesh with other nonlinearity parameters, data and clamps run on the kept hierarchy (no new
+    setup) and return exactly what a fresh context returns."""
+    pr = problem_config("chan3d_64", scale=9)
+    base_opts = dict(pr.opts, n_levels=3, agg_size=[27, 6, 4], modes=[4, 3, 3])
+    F, G = multi_rhs_rows(pr.mesh, 4, seed=60)
+    alphas = [2.0, 1.0, 1.5, 0.75]
+    reqs = [(a, dict(base_opts, dp_clamp=float(np.log(1.5) / a)), F[r], G[r]) for r, a in enumerate(alphas)]
+    alone = []
+    for a, o, f, g in reqs:
+        ctx = nlmg_lib.Context(pr.mesh, 0, a, o)
+        p, rep, st = ctx.solve(f, g, max_cycles=60)
+        assert st == 0
+        alone.append(p)
+        ctx.close()
+    srv = nlmg_lib.Server(max_inflight=2, mem_budget_bytes=1 << 30, hierarchy_cache=2)
+    a, o, f, g = reqs[0]
+    p, rep, times, st = srv.poll(srv.submit(pr.mesh, 0, a, o, f, g), wait_ms=120000)
+    assert st == 0 and not times["hierarchy_reused"] and np.array_equal(p, alone[0])
+    tickets = [srv.submit(pr.mesh, 0, a, o, f, g) for a, o, f, g in reqs[1:]]
+    for t, p_ref in zip(tickets, alone[1:]):
+        p, rep, times, st = srv.poll(t, wait_ms=120000)
+        assert st == 0 and times["hierarchy_reused"]
+        assert np.array_equal(p, p_ref)
+    srv.close()
+    off = nlmg_lib.Server(max_inflight=1, mem_budget_bytes=1 << 30, hierarchy_cache=0)
+    for a, o, f, g in reqs[:2]:
+        p, rep, times, st = off.poll(off.submit(pr.mesh, 0, a, o, f, g), wait_ms=120000)
+        assert st == 0 and not times["hierarchy_reused"]
+    off.close()
