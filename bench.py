@@ -188,18 +188,20 @@ def run_multi_rhs(nlmg, pr, ctx, n_rhs, n_streams):
     t0 = time.perf_counter()
     PM, mreps, msts = mctx.solve_many(F, G, max_cycles=60, n_streams=n_streams)
     t_mixed = time.perf_counter() - t0
-    identical = all(np.array_equal(P[r], seq[r][0]) for r in range(n_rhs))
+    diff64 = max(float(np.linalg.norm(P[r] - seq[r][0]) / np.linalg.norm(seq[r][0])) for r in range(n_rhs))
     mixed_err = max(float(np.linalg.norm(PM[r] - seq[r][0]) / np.linalg.norm(seq[r][0])) for r in range(n_rhs))
     mixed_res = max(m["res"] / m["res0"] for m in mreps)
     mctx.close()
     return {"rhs": n_rhs, "streams": n_streams, "ok": int(np.sum(sts == 0) + np.sum(msts == 0)),
             "sequential_fp64_solves_per_s": n_rhs / t_seq,
-            "many_fp64_solves_per_s": n_rhs / t_many, "many_fp64_identical_to_sequential": bool(identical),
+            "many_fp64_solves_per_s": n_rhs / t_many, "many_fp64_max_rel_diff_vs_sequential": diff64,
             "many_mixed_solves_per_s": n_rhs / t_mixed, "mixed_max_rel_diff_vs_fp64": mixed_err,
             "mixed_max_rel_residual": mixed_res,
             "cycles_per_solve": float(np.mean([r["cycles"] for r in reps])),
             "what": "right-hand sides share the mesh, K and the hierarchy (per row: Dirichlet value on x = 0 and a "
-                    "smooth source); host buffers in and out; wall clock per batch"}
+                    "smooth source); sequential = one context on all SMs, one row after the other; many = "
+                    "nlmg_solve_many, each context's persistent kernels on SMs / min(streams, 4); host buffers in "
+                    "and out; wall clock per batch; both at relative residual 1e-8"}
 
 
 def run_voronoi(nlmg, n_side, steps):
@@ -450,8 +452,8 @@ def main():
     ap.add_argument("--coarse-lin-tol", type=float, default=None, help="coarse CG tolerance")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false", help="skip the FP32-CG variant")
     ap.add_argument("--serving", type=int, default=24, help="requests in the serving run (0 = skip)")
-    ap.add_argument("--multi-rhs", type=int, default=8, help="right-hand sides in the multi-RHS run (0 = skip)")
-    ap.add_argument("--streams", type=int, default=4, help="contexts (streams) of the multi-RHS solve")
+    ap.add_argument("--multi-rhs", type=int, default=16, help="right-hand sides in the multi-RHS run (0 = skip)")
+    ap.add_argument("--streams", type=int, default=8, help="contexts (streams) of the multi-RHS solve")
     ap.add_argument("--voronoi", type=int, default=0,
                     help="lattice side of the unstructured Voronoi section (100 = 1M cells; 0 = skip)")
     args = ap.parse_args()

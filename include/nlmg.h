@@ -82,7 +82,11 @@ typedef struct {
   int32_t lin_precision;     /* 0: CG in FP64; 1: CG vectors and matrices in FP32 (tolerances floored at 1e-6),
                                 inside the FP64 nonlinear iteration */
   int32_t setup_threads;     /* host threads for the setup (0 = all) */
-  int32_t reserved[6];
+  int32_t max_sms;           /* SMs the persistent solver kernels of a context may use (0 = all): contexts that
+                                solve concurrently (nlmg_solve_many, the request loop) can then run side by side.
+                                The grid, and with it the reduction order, follows from it: results are bitwise
+                                reproducible for a given max_sms */
+  int32_t reserved[5];
 } nlmg_options;
 
 typedef struct {
@@ -136,8 +140,10 @@ nlmg_status nlmg_set_options(nlmg_ctx* ctx, const nlmg_options* opt);
  * f_cell[n_rhs][n_cells], g_face[n_rhs][n_faces], x0[n_rhs][n_cells] (NULL = all zero) and p_out[n_rhs][n_cells]
  * are host buffers, row r being right-hand side r. The solves run on up to n_streams contexts of the same hierarchy
  * (ctx and n_streams - 1 instances made by nlmg_instance on first use and kept by ctx), each on its own stream and
- * host thread; n_streams <= 0 picks 4. Every solve is the one nlmg_solve would return for that row (bitwise: each
- * context owns its buffers and every reduction has a fixed order). rep (NULL or n_rhs entries) and status (NULL or
+ * host thread; n_streams <= 0 picks 8. Unless ctx's max_sms is set, the persistent kernels of each context then
+ * use max_sms = SMs / min(n_streams, 4), so that several run side by side. Every row is bitwise the solve that
+ * nlmg_solve returns for it on a context with that max_sms (each context owns its buffers, every reduction has a
+ * fixed order, and the share depends on n_streams only, not on the load). rep (NULL or n_rhs entries) and status (NULL or
  * n_rhs entries) receive each row's report and status. Returns NLMG_OK if every row converged, else the first
  * failing row's status (its message is then ctx's last error). */
 nlmg_status nlmg_solve_many(nlmg_ctx* ctx, int32_t n_rhs, const double* f_cell, const double* g_face,
@@ -213,9 +219,11 @@ nlmg_status nlmg_get_transfer_dense(nlmg_ctx* ctx, int32_t level, int32_t which,
  * work overlaps. Hierarchies stay on the device after their request: up to hierarchy_cache of them are kept (least
  * recently used evicted first, also when the memory budget needs room), and a later request whose mesh arrays and
  * hierarchy options (n_levels, agg_size, modes) are identical runs on an nlmg_instance of the kept hierarchy instead
- * of a new setup, whatever its nonlinearity parameter, data and solver options. A request's result is the same
- * alone and in any mix and with or without reuse (each context owns its buffers, every reduction has a fixed order
- * and the setup is deterministic). All pointers are host pointers, copied at submit. */
+ * of a new setup, whatever its nonlinearity parameter, data and solver options. Unless a request sets max_sms, its
+ * persistent kernels use SMs / min(max_inflight, 4) of them (a share fixed by the server options, not by the load).
+ * A request's result is the same alone and in any mix and with or without reuse (each context owns its buffers,
+ * every reduction has a fixed order and the setup is deterministic). All pointers are host pointers, copied at
+ * submit. */
 typedef struct nlmg_server nlmg_server;
 typedef struct {
   int32_t max_inflight;

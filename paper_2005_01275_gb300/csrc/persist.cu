@@ -8,8 +8,9 @@
 // Data written by one block and read by another inside the same launch (CG vectors, per-interface buffers) is read
 // with ld.global.cg (L2, bypassing the non-coherent L1), after the barrier that orders the write.
 //
-// Reductions stay deterministic: each block writes one partial; after the barrier every block sums all partials in
-// block order with the same fixed tree, so all blocks hold bit-identical scalars and take the same decisions.
+// Reductions stay deterministic: each block writes one partial; the last block to reach the barrier sums them in
+// block order with a fixed tree and derives the step lengths once, and every block reads the same scalars, so all
+// blocks take the same decisions and a run is bitwise reproducible.
 #include <cmath>
 
 #include "kernels.cuh"
@@ -96,14 +97,19 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
 }
 
 // Grid sums of NV values: every block publishes its block sum; the last block to arrive adds the partials in block
-// order (fixed tree) and stores the result to `out`; after the barrier every thread reads `out`.
-template <int NV>
-__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partial, double* out, const GridSync& gs,
-                                         double* sm) {
-  block_sum<NV>(v, sm);
+// order (fixed tree) and stores the result to out[0..NV-1]; its thread 0 then runs `post(out)`, which derives NX
+// scalars from the sums (the CG step lengths) into out[NV..NV+NX-1], so that each division is done once per grid
+// instead of once per thread. After the barrier every thread reads all NV + NX values.
+template <int NV, int NX = 0, class PostFn>
+__device__ __forceinline__ bool grid_sum_x(double (&v)[NV + NX], double* partial, double* out, const GridSync& gs,
+                                           double* sm, PostFn&& post) {
+  double w[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) w[k] = v[k];
+  block_sum<NV>(w, sm);
   if (threadIdx.x == 0)
 #pragma unroll
-    for (int k = 0; k < NV; ++k) partial[blockIdx.x * NV + k] = v[k];
+    for (int k = 0; k < NV; ++k) partial[blockIdx.x * NV + k] = w[k];
   const bool ok = grid_barrier_ex(gs, [&]() {
     double acc[NV];
 #pragma unroll
@@ -112,15 +118,23 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partial, doubl
 #pragma unroll
       for (int k = 0; k < NV; ++k) acc[k] += __ldcg(&partial[b * NV + k]);
     block_sum<NV>(acc, sm);
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
 #pragma unroll
       for (int k = 0; k < NV; ++k) out[k] = acc[k];
+      post(out);
+    }
     __threadfence();
   });
   if (!ok) return false;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = __ldcg(&out[k]);
+  for (int k = 0; k < NV + NX; ++k) v[k] = __ldcg(&out[k]);
   return true;
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partial, double* out, const GridSync& gs,
+                                         double* sm) {
+  return grid_sum_x<NV, 0>(v, partial, out, gs, sm, [](double*) {});
 }
 
 #define GSTRIDE(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
@@ -188,9 +202,10 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __re
       q[K] = qK;
       tpq = fma(pK, qK, tpq);
     }
-    double pq[1] = {(double)tpq};
-    if (!grid_sum<1>(pq, part0, gs.out + 2, gs, sm)) return;
-    const double alpha_d = pq[0] != 0.0 ? rr / pq[0] : 0.0;
+    double pq[2] = {(double)tpq, 0.0};
+    if (!grid_sum_x<1, 1>(pq, part0, gs.out + 8, gs, sm, [&](double* o) { o[1] = o[0] != 0.0 ? rr / o[0] : 0.0; }))
+      return;
+    const double alpha_d = pq[1];
     const T alpha = (T)alpha_d;
     T trn = (T)0;
     GSTRIDE(i, F.N) {
@@ -199,9 +214,10 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __re
       r[i] = ri;
       trn = fma(ri, ri, trn);
     }
-    double rn[1] = {(double)trn};
-    if (!grid_sum<1>(rn, part1, gs.out + 4, gs, sm)) return;
-    beta = (T)(rr != 0.0 ? rn[0] / rr : 0.0);
+    double rn[2] = {(double)trn, 0.0};
+    if (!grid_sum_x<1, 1>(rn, part1, gs.out + 16, gs, sm, [&](double* o) { o[1] = rr != 0.0 ? o[0] / rr : 0.0; }))
+      return;
+    beta = (T)rn[1];
     rr = rn[0];
     ++it;
     if (!(alpha_d != 0.0)) break;   // breakdown (p.Ap = 0): stop with the current iterate
@@ -260,35 +276,31 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg_pipe(FineDev F, const T*
     y[i] = z[i] = sv[i] = p[i] = (T)0;
   }
   if (!grid_barrier(gs)) return;
-  double a2[2] = {0.0, 0.0};
+  // a4 = {gamma, delta, beta, alpha}: the sums and, from the last block's thread 0, the step lengths of the next
+  // iteration (beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old); first: 0, gamma / delta)
+  double a4[4] = {0.0, 0.0, 0.0, 0.0};
   GSTRIDE(K, F.N) {
     const T wK = sell_apply<T>(F, Ts, r, K);
     wa[K] = wK;
     const double rK = (double)r[K];
-    a2[0] = fma(rK, rK, a2[0]);
-    a2[1] = fma((double)wK, rK, a2[1]);
+    a4[0] = fma(rK, rK, a4[0]);
+    a4[1] = fma((double)wK, rK, a4[1]);
   }
-  if (!grid_sum<2>(a2, part1, gs.out + 0, gs, sm)) return;
-  double gamma = a2[0], delta = a2[1];
+  if (!grid_sum_x<2, 2>(a4, part1, gs.out + 0, gs, sm, [&](double* o) {
+        o[2] = 0.0;
+        o[3] = o[1] != 0.0 ? o[0] / o[1] : 0.0;
+      }))
+    return;
+  double gamma = a4[0], beta_d = a4[2], alpha_d = a4[3];
   const double rr0 = gamma;
   const double tol2 = tol * tol * rr0;
-  double gamma_old = 0.0, alpha_old = 0.0;
   T* wc = wa;   // current w (read, neighbours gathered)
   T* wn = wb;   // next w (written)
   int it = 0;
   while (rr0 > 0.0 && gamma > tol2 && it < maxit) {
-    double beta_d, alpha_d;
-    if (it == 0) {
-      beta_d = 0.0;
-      alpha_d = delta != 0.0 ? gamma / delta : 0.0;
-    } else {
-      beta_d = gamma_old != 0.0 ? gamma / gamma_old : 0.0;
-      const double den = delta - beta_d * gamma / alpha_old;
-      alpha_d = den != 0.0 ? gamma / den : 0.0;
-    }
     if (!(alpha_d != 0.0)) break;
     const T alpha = (T)alpha_d, beta = (T)beta_d;
-    a2[0] = a2[1] = 0.0;
+    double n4[4] = {0.0, 0.0, 0.0, 0.0};
     GSTRIDE(K, F.N) {
       const T nK = sell_apply<T>(F, Ts, wc, K);
       const T wK = wc[K];
@@ -303,14 +315,20 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg_pipe(FineDev F, const T*
       r[K] = rK;
       const T wN = wK - alpha * zK;
       wn[K] = wN;
-      a2[0] = fma((double)rK, (double)rK, a2[0]);
-      a2[1] = fma((double)wN, (double)rK, a2[1]);
+      n4[0] = fma((double)rK, (double)rK, n4[0]);
+      n4[1] = fma((double)wN, (double)rK, n4[1]);
     }
-    if (!grid_sum<2>(a2, (it & 1) ? part1 : part0, gs.out + ((it & 1) ? 4 : 2), gs, sm)) return;
-    gamma_old = gamma;
-    alpha_old = alpha_d;
-    gamma = a2[0];
-    delta = a2[1];
+    if (!grid_sum_x<2, 2>(n4, (it & 1) ? part1 : part0, gs.out + ((it & 1) ? 16 : 8), gs, sm, [&](double* o) {
+          const double g = o[0], d = o[1];
+          const double bn = gamma != 0.0 ? g / gamma : 0.0;
+          const double den = d - bn * g / alpha_d;
+          o[2] = bn;
+          o[3] = den != 0.0 ? g / den : 0.0;
+        }))
+      return;
+    gamma = n4[0];
+    beta_d = n4[2];
+    alpha_d = n4[3];
     T* t = wc;
     wc = wn;
     wn = t;
@@ -335,7 +353,7 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
                                                          T* pa, T* pb, T* lq, T* ldinv,
                                                          double* __restrict__ dsig, double* __restrict__ dp,
                                                          double* partial, GridSync gs, double tol, int maxit,
-                                                         PcgResult* res) {
+                                                         int gsz, PcgResult* res) {
   __shared__ double sm[2 * 32];
   double* part0 = partial;
   double* part1 = partial + 2 * gridDim.x;
@@ -377,30 +395,49 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
   T* pp = pa;       // search direction p
   int it = 0;
   while (rr0 > 0.0 && rr > tol2 && it < maxit) {
-    // ylam[k] = kappa_c sum_j Hc[k, j] z(lambda_j): H applied to the preconditioned residual, one thread per
-    // interface slot (rows read contiguously); H p then follows by recurrence
-    GSTRIDE(k, L.nif) {
-      const int c = L.if_cell[k];
-      const int k0 = L.if_off[c], ni = L.if_off[c + 1] - k0;
-      const T* Hk = Hc + L.hc_off[c] + (size_t)(k - k0) * ni;
-      T y = 0;
-      for (int j = 0; j < ni; ++j) y += Hk[j] * __ldcg(&lz[L.if_lam[k0 + j]]);
-      ylam[k] = (T)kapc[c] * y;
-    }
-    if (!grid_barrier(gs)) return;
+    // (H z)_l = sum over the two interface slots k of lambda_l of kappa_c Hc[k, :] z(lambda of c's slots): a group
+    // of gsz lanes per lambda (gsz a power of two <= 32, chosen so that small coarse levels still occupy every SM)
+    // reads both rows with stride gsz and adds up by shuffles, so H z needs no intermediate buffer and no extra
+    // barrier; H p then follows by recurrence. z was published by the previous reduction's barrier.
     T upq = (T)0;
-    GSTRIDE(l, L.nlam) {
-      const T zl = lz[l];
-      const T hz = __ldcg(&ylam[L.lam_y0[l]]) + __ldcg(&ylam[L.lam_y1[l]]);
-      const T pl = it == 0 ? zl : zl + beta * pp[l];
-      const T ql = it == 0 ? hz : hz + beta * lq[l];
-      pp[l] = pl;
-      lq[l] = ql;
-      upq = fma(pl, ql, upq);
+    {
+      const long total = (long)L.nlam * gsz;
+      const int lane = threadIdx.x & 31;
+      const long stride = (long)gridDim.x * blockDim.x;
+      for (long tb = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); tb < total; tb += stride) {
+        const long t = tb + lane;   // warp-uniform loop: every lane takes part in the shuffles
+        const bool act = t < total;
+        const int l = act ? (int)(t / gsz) : 0;
+        const int g = lane & (gsz - 1);
+        T hz = (T)0;
+        if (act) {
+#pragma unroll
+          for (int side = 0; side < 2; ++side) {
+            const int k = side == 0 ? L.lam_y0[l] : L.lam_y1[l];
+            const int c = L.if_cell[k];
+            const int k0 = L.if_off[c], ni = L.if_off[c + 1] - k0;
+            const T* Hk = Hc + L.hc_off[c] + (size_t)(k - k0) * ni;
+            const int* lk = L.if_lam + k0;
+            T y = 0;
+            for (int j = g; j < ni; j += gsz) y += Hk[j] * __ldcg(&lz[lk[j]]);
+            hz += (T)kapc[c] * y;
+          }
+        }
+        for (int off = gsz >> 1; off > 0; off >>= 1) hz += __shfl_xor_sync(0xffffffffu, hz, off);
+        if (act && g == 0) {
+          const T zl = lz[l];
+          const T pl = it == 0 ? zl : zl + beta * pp[l];
+          const T ql = it == 0 ? hz : hz + beta * lq[l];
+          pp[l] = pl;
+          lq[l] = ql;
+          upq = fma(pl, ql, upq);
+        }
+      }
     }
-    double a1[1] = {(double)upq};
-    if (!grid_sum<1>(a1, part0, gs.out + 2, gs, sm)) return;
-    const double alpha_d = a1[0] != 0.0 ? rz / a1[0] : 0.0;
+    double a1[2] = {(double)upq, 0.0};
+    if (!grid_sum_x<1, 1>(a1, part0, gs.out + 8, gs, sm, [&](double* o) { o[1] = o[0] != 0.0 ? rz / o[0] : 0.0; }))
+      return;
+    const double alpha_d = a1[1];
     const T alpha = (T)alpha_d;
     u0 = u1 = (T)0;
     GSTRIDE(l, L.nlam) {
@@ -412,12 +449,13 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
       u0 = fma(ri, zi, u0);
       u1 = fma(ri, ri, u1);
     }
-    a2[0] = (double)u0;
-    a2[1] = (double)u1;
-    if (!grid_sum<2>(a2, part1, gs.out + 4, gs, sm)) return;
-    beta = (T)(rz != 0.0 ? a2[0] / rz : 0.0);
-    rz = a2[0];
-    rr = a2[1];
+    double a3[3] = {(double)u0, (double)u1, 0.0};
+    if (!grid_sum_x<2, 1>(a3, part1, gs.out + 16, gs, sm,
+                          [&](double* o) { o[2] = rz != 0.0 ? o[0] / rz : 0.0; }))
+      return;
+    beta = (T)a3[2];
+    rz = a3[0];
+    rr = a3[1];
     ++it;
     if (!(alpha_d != 0.0)) break;
   }
@@ -456,18 +494,19 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
   }
 }
 
-int coop_grid(const void* fn, int n_items) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+int coop_grid(const void* fn, int n_items, int sm_cap) {
+  static const int sms = [] {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+  }();
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPThreads, 0);
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 2) per_sm = 2;                   // few, wide blocks: cheap barriers and partial sums
-  int maxb = sms * per_sm;
+  const int use = sm_cap > 0 && sm_cap < sms ? sm_cap : sms;
+  int maxb = use * per_sm;
   int need = (n_items + kPThreads - 1) / kPThreads;
   if (need < 1) need = 1;
   return need < maxb ? need : maxb;
@@ -481,7 +520,7 @@ cudaError_t launch_fine_cg(cudaStream_t st, const FineDev& F, const T* Ts, const
                            double tol, int maxit, PcgResult* res) {
   (void)pb;
   const void* fn = (const void*)kp_fine_cg<T>;
-  int grid = coop_grid(fn, F.N);
+  int grid = coop_grid(fn, F.N, gs.sm_cap);
   void* args[] = {(void*)&F, (void*)&Ts, (void*)&sdiag, (void*)&b, (void*)&bscale, (void*)&dx, (void*)&y,
                   (void*)&r, (void*)&pa, (void*)&q, (void*)&partial, (void*)&gs, (void*)&tol,
                   (void*)&maxit, (void*)&res};
@@ -492,7 +531,7 @@ cudaError_t launch_fine_cg_pipe(cudaStream_t st, const FineDev& F, const T* Ts, 
                                 double bscale, double* dx, T* y, T* r, T* wa, T* wb, T* z, T* sv, T* p,
                                 double* partial, GridSync gs, double tol, int maxit, PcgResult* res) {
   const void* fn = (const void*)kp_fine_cg_pipe<T>;
-  int grid = coop_grid(fn, F.N);
+  int grid = coop_grid(fn, F.N, gs.sm_cap);
   void* args[] = {(void*)&F, (void*)&Ts, (void*)&sdiag, (void*)&b, (void*)&bscale, (void*)&dx, (void*)&y,
                   (void*)&r, (void*)&wa, (void*)&wb, (void*)&z, (void*)&sv, (void*)&p, (void*)&partial, (void*)&gs,
                   (void*)&tol, (void*)&maxit, (void*)&res};
@@ -514,14 +553,18 @@ cudaError_t launch_hyb_solve(cudaStream_t st, const LevelDev& L, const T* Hc, co
                              const double* bs, const double* bp, T* ylam, T* ydiag, T* lam, T* lr, T* lz, T* pa,
                              T* pb, T* lq, T* ldinv, double* dsig, double* dp, double* partial, GridSync gs,
                              double tol, int maxit, PcgResult* res) {
-  int items = L.nlam > L.nif ? L.nlam : L.nif;
+  // lanes per lambda in the H product: enough that the level spreads over ~64k threads
+  int gsz = 1;
+  while (gsz < 32 && (long)L.nlam * gsz < 65536) gsz *= 2;
+  long items = (long)L.nlam * gsz;
+  if (L.nif > items) items = L.nif;
   if (L.nyl > items) items = L.nyl;
   const void* fn = (const void*)kp_hyb_solve<T>;
-  int grid = coop_grid(fn, items);
+  int grid = coop_grid(fn, (int)items, gs.sm_cap);
   void* args[] = {(void*)&L, (void*)&Hc, (void*)&Sinv, (void*)&kapc, (void*)&bs, (void*)&bp, (void*)&ylam,
                   (void*)&ydiag, (void*)&lam, (void*)&lr, (void*)&lz, (void*)&pa, (void*)&pb, (void*)&lq,
                   (void*)&ldinv, (void*)&dsig, (void*)&dp, (void*)&partial, (void*)&gs, (void*)&tol, (void*)&maxit,
-                  (void*)&res};
+                  (void*)&gsz, (void*)&res};
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
 }
 template cudaError_t launch_hyb_solve<double>(cudaStream_t, const LevelDev&, const double*, const double*,

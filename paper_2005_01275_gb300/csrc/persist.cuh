@@ -17,7 +17,8 @@ struct GridSync {
   unsigned* count;   // arrivals at the current barrier (0 at launch); own 128-byte line
   unsigned* gen;     // barrier generation; own 128-byte line
   int* err;          // set when a wait gives up
-  double* out;       // 6 reduction results published by the last block to arrive
+  double* out;       // 24 reduction results and step lengths published by the last block to arrive
+  int sm_cap;        // host side: at most this many SMs for the launch (0 = all)
 };
 
 template <class T>

@@ -7,6 +7,7 @@
 // releases the work memory, so requests that arrive while others run start as soon as slots and memory free up, and
 // their GPU work overlaps. A request's result does not depend on what else runs or on reuse: each context owns its
 // work buffers, every reduction has a fixed order and the setup is deterministic.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -63,6 +64,7 @@ struct Kept {
 struct nlmg_server {
   nlmg_server_options o{};
   int device = 0;
+  int sms = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<std::shared_ptr<Request>> queue;
@@ -249,7 +251,8 @@ nlmg_status nlmg_server_create(const nlmg_server_options* opt, nlmg_server** out
   if (!opt || !out || opt->max_inflight < 1 || opt->mem_budget_bytes == 0) return NLMG_EINVAL;
   nlmg_server* s = new nlmg_server();
   s->o = *opt;
-  if (cudaGetDevice(&s->device) != cudaSuccess) {
+  if (cudaGetDevice(&s->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
     delete s;
     return NLMG_ECUDA;
   }
@@ -276,6 +279,8 @@ nlmg_status nlmg_server_submit(nlmg_server* s, const nlmg_mesh* mesh, const nlmg
   r->kappa = *kappa;
   r->opt = *opt;
   if (r->opt.setup_threads == 0) r->opt.setup_threads = s->o.setup_threads_per_request;
+  // requests run side by side: unless the request says otherwise, its persistent kernels use a share of the SMs
+  if (r->opt.max_sms == 0 && s->o.max_inflight > 1) r->opt.max_sms = std::max(1, s->sms / std::min(s->o.max_inflight, 4));
   r->tol_rel = tol_rel;
   r->tol_abs = tol_abs;
   r->max_cycles = max_cycles;

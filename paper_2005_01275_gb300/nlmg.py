@@ -37,7 +37,7 @@ class Options(C.Structure):
                 ("bt_nmax", C.c_int32), ("bt_theta", C.c_double), ("dp_clamp", C.c_double),
                 ("coarsest_steps", C.c_int32), ("lin_tol", C.c_double), ("lin_maxit", C.c_int32),
                 ("coarse_lin_tol", C.c_double), ("lin_precision", C.c_int32),
-                ("setup_threads", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("setup_threads", C.c_int32), ("max_sms", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class Report(C.Structure):
@@ -159,7 +159,7 @@ def options_from_dict(d):
     """Options from the dictionary used by the synthetic problem configurations."""
     keep = {k: d[k] for k in ("n_levels", "agg_size", "modes", "nu_pre", "nu_post", "omega", "bt_nmax", "bt_theta",
                               "dp_clamp", "coarsest_steps", "lin_tol", "lin_maxit", "coarse_lin_tol",
-                              "lin_precision") if k in d}
+                              "lin_precision", "max_sms") if k in d}
     if "lin_tol" in d and "coarse_lin_tol" not in d:
         keep["coarse_lin_tol"] = d["lin_tol"]       # one tolerance given: use it on every level
     if "smoother" in d:
@@ -209,7 +209,7 @@ class Context:
         self._check(lib().nlmg_set_options(self.h, C.byref(o)))
         self.opts = o
 
-    def solve_many(self, f_rows, g_rows, x0_rows=None, tol_rel=1e-8, tol_abs=1e-10, max_cycles=50, n_streams=4,
+    def solve_many(self, f_rows, g_rows, x0_rows=None, tol_rel=1e-8, tol_abs=1e-10, max_cycles=50, n_streams=0,
                    allow_noconv=False):
         """Independent FAS solves of every row of f_rows [n_rhs, n_cells] / g_rows [n_rhs, n_faces]."""
         f = np.ascontiguousarray(f_rows, dtype=np.float64)

@@ -25,12 +25,21 @@ def _problem(scale=11):
     return pr
 
 
-def test_many_rows_equal_single_solves(nlmg_lib):
+def _sms():
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+@pytest.mark.parametrize("max_sms", [0, 40])
+def test_many_rows_equal_single_solves(nlmg_lib, max_sms):
+    """Each row equals the single solve on a context with the SM share the batch used (given, or SMs / min(3, 4)
+    for n_streams = 3): bitwise, whatever ran beside it."""
     pr = _problem()
     F, G = _rows(pr, 6, seed=50)
-    ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.opts)
+    ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, dict(pr.opts, max_sms=max_sms))
     P, reps, sts = ctx.solve_many(F, G, max_cycles=60, n_streams=3)
     assert np.all(sts == 0)
+    ctx.set_options(max_sms=max_sms or _sms() // 3)
     for r in range(F.shape[0]):
         p1, rep1, st1 = ctx.solve(F[r], G[r], max_cycles=60)
         assert st1 == 0
@@ -45,7 +54,7 @@ def test_many_rows_match_oracle(nlmg_lib):
     pr = _problem()
     F, G = _rows(pr, 3, seed=51)
     ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, dict(pr.opts, **TIGHT))
-    P, reps, sts = ctx.solve_many(F, G, tol_rel=1e-12, tol_abs=1e-300, max_cycles=80, n_streams=2)
+    P, reps, sts = ctx.solve_many(F, G, tol_rel=1e-12, tol_abs=1e-300, max_cycles=80, n_streams=3)
     assert np.all(sts == 0)
     for r in range(F.shape[0]):
         pstar, _ = newton.solve(pr.mesh, pr.kappa_kind, pr.kappa_a, F[r], G[r], dp_clamp=pr.opts["dp_clamp"])

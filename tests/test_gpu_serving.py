@@ -32,7 +32,8 @@ def _requests(n_req=6, seed=40):
 
 
 def test_results_identical_alone_and_in_the_mix(nlmg_lib):
-    reqs = _requests()
+    """Alone = a context of its own with the SM share the server gives each request (explicit here)."""
+    reqs = [(m, a, dict(o, max_sms=50), f, g) for m, a, o, f, g in _requests()]
     alone = []
     for mesh, a, opts, f, g in reqs:
         ctx = nlmg_lib.Context(mesh, 0, a, opts)
@@ -75,7 +76,8 @@ def test_kept_hierarchy_is_reused_with_identical_results(nlmg_lib):
     base_opts = dict(pr.opts, n_levels=3, agg_size=[27, 6, 4], modes=[4, 3, 3])
     F, G = multi_rhs_rows(pr.mesh, 4, seed=60)
     alphas = [2.0, 1.0, 1.5, 0.75]
-    reqs = [(a, dict(base_opts, dp_clamp=float(np.log(1.5) / a)), F[r], G[r]) for r, a in enumerate(alphas)]
+    reqs = [(a, dict(base_opts, dp_clamp=float(np.log(1.5) / a), max_sms=76), F[r], G[r])
+            for r, a in enumerate(alphas)]
     alone = []
     for a, o, f, g in reqs:
         ctx = nlmg_lib.Context(pr.mesh, 0, a, o)
