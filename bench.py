@@ -379,7 +379,7 @@ def run_gpu(args, rank, world, local_rank):
                             "peak_kind": peak_kind,
                             "frac": by_cg / (avg_cg / 1e3) / 1e9 / peak if n_cg else None},
             "share_of_solve": ms_cg / dev_ms if dev_ms else None,
-            "others": {"kp_hyb_solve": {"launches": upd[0], "avg_us": upd[1] / max(upd[0], 1) * 1e3,
+            "others": {"kp_coarse_step": {"launches": upd[0], "avg_us": upd[1] / max(upd[0], 1) * 1e3,
                                         "share_of_solve": upd[1] / dev_ms if dev_ms else None,
                                         "GB/s": upd[2] / (upd[1] / max(upd[0], 1) / 1e3) / 1e9 if upd[0] else None},
                        "k_residual": {"launches": res[0], "avg_us": res[1] / max(res[0], 1) * 1e3,

@@ -251,7 +251,8 @@ void nlmg_server_destroy(nlmg_server* srv);
 
 /* ---- measurement ----------------------------------------------------------------------------------------- */
 /* Enables (1) or disables (0) CUDA-event timing of the hot kernels on the context stream and clears the counters.
- * Kernel ids: 0 = persistent fine CG solve (kp_fine_cg), 1 = persistent hybridized coarse solve (kp_hyb_solve),
+ * Kernel ids: 0 = persistent fine CG solve (kp_fine_cg*), 1 = persistent coarse Picard step (kp_coarse_step:
+ * coarse operator evaluations, hybridized CG, clamp and Algorithm 1 in one launch; kp_hyb_solve for the step calls),
  * 2 = fine TPFA residual (k_residual). */
 nlmg_status nlmg_profile(nlmg_ctx* ctx, int32_t enable);
 /* Launch count, summed event time, algorithmic bytes per launch (each streamed array counted once; the gathered

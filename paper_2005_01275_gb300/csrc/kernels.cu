@@ -14,14 +14,6 @@ namespace nlmg {
 
 namespace {
 
-__device__ __forceinline__ double kappa_of(double p, int kind, double a) {
-  return kind == 0 ? exp(a * p) : 1.0 / (1.0 + p * p);
-}
-__device__ __forceinline__ double dkappa_of(double p, int kind, double a) {
-  if (kind == 0) return a * exp(a * p);
-  double t = 1.0 + p * p;
-  return -2.0 * p / (t * t);
-}
 
 template <bool MAX>
 __device__ __forceinline__ double comb(double x, double y) {

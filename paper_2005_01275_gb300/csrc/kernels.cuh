@@ -37,6 +37,16 @@ struct FineDev {
   double *fl_u0 = nullptr, *fl_u1 = nullptr;
 };
 
+// The nonlinearity: kind 0 kappa = exp(a p), kind 1 kappa = (1 + p^2)^-1 (Sec. 4 examples), and its derivative.
+__device__ __forceinline__ double kappa_of(double p, int kind, double a) {
+  return kind == 0 ? exp(a * p) : 1.0 / (1.0 + p * p);
+}
+__device__ __forceinline__ double dkappa_of(double p, int kind, double a) {
+  if (kind == 0) return a * exp(a * p);
+  double t = 1.0 + p * p;
+  return -2.0 * p / (t * t);
+}
+
 // Coarse level (mixed, cell-by-cell: Prop. 1)
 struct LevelDev {
   int nc = 0, nflux = 0, np = 0, nlam = 0, nyl = 0, nif = 0;

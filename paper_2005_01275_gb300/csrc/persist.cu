@@ -23,22 +23,39 @@ namespace {
 constexpr unsigned long long kSpinLimit = 1ull << 26;   // x ~32 ns sleeps ~ 2 s
 constexpr int kPThreads = 512;                           // threads per block of the persistent kernels
 
-// Bounded grid barrier: blocks arrive on gs.count; the last one to arrive runs `last` (a block-wide callback),
-// then bumps the generation that the others poll. Returns false (and sets *err) if a wait gave up.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
+}
+
+// Bounded grid barrier: blocks arrive on gs.count (never reset inside a launch: barrier k completes with arrival
+// number (k + 1) * gridDim.x - 1); the last one to arrive runs `last` (a block-wide callback), then bumps the
+// generation that the others poll. Thread 0 of each block carries the block's ordering: __syncthreads, then an
+// acquire-release arrival (its release covers the block's earlier writes), the generation bump is a release and the
+// poll an acquire, so no separate fences are needed. Returns false (and sets *err) if a wait gave up.
 template <class LastFn>
 __device__ __forceinline__ bool grid_barrier_ex(const GridSync& gs, LastFn&& last) {
   __shared__ int ok, is_last;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    volatile unsigned* gen = gs.gen;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(gs.count, 1u);
-    is_last = arrived == gridDim.x - 1;
+    const unsigned g = ld_acquire_gpu(gs.gen);
+    const unsigned arrived = atom_add_acq_rel_gpu(gs.count, 1u);
+    is_last = (arrived + 1u) % gridDim.x == 0u;
     if (!is_last) {
       unsigned long long spins = 0;
-      while (*gen == g) {
+      while (ld_acquire_gpu(gs.gen) == g) {
         __nanosleep(32);
         if ((++spins & 1023u) == 0 && (spins > kSpinLimit || *((volatile int*)gs.err) != 0)) {
           atomicExch(gs.err, 1);
@@ -46,19 +63,13 @@ __device__ __forceinline__ bool grid_barrier_ex(const GridSync& gs, LastFn&& las
           break;
         }
       }
-      __threadfence();
     }
   }
   __syncthreads();
   if (is_last) {
-    __threadfence();
     last();
     __syncthreads();
-    if (threadIdx.x == 0) {
-      *gs.count = 0u;
-      __threadfence();
-      atomicAdd(gs.gen, 1u);
-    }
+    if (threadIdx.x == 0) red_add_release_gpu(gs.gen, 1u);
   }
   __syncthreads();
   return ok != 0;
@@ -123,7 +134,6 @@ __device__ __forceinline__ bool grid_sum_x(double (&v)[NV + NX], double* partial
       for (int k = 0; k < NV; ++k) out[k] = acc[k];
       post(out);
     }
-    __threadfence();
   });
   if (!ok) return false;
 #pragma unroll
@@ -342,37 +352,133 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg_pipe(FineDev F, const T*
   }
 }
 
-// ---- coarse level: hybridized saddle solve (rhs, Jacobi diagonal, CG on H lambda = xi, local recovery) ------
-template <class T>
-__global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* __restrict__ Hc,
-                                                         const T* __restrict__ Sinv,
-                                                         const double* __restrict__ kapc,
-                                                         const double* __restrict__ bs,
-                                                         const double* __restrict__ bp, T* ylam,
-                                                         T* ydiag, T* lam, T* lr, T* lz,
-                                                         T* pa, T* pb, T* lq, T* ldinv,
-                                                         double* __restrict__ dsig, double* __restrict__ dp,
-                                                         double* partial, GridSync gs, double tol, int maxit,
-                                                         int gsz, PcgResult* res) {
+// Register-resident pipelined CG. A persistent thread owns the same cells (at most R of them: K = k0 + u * stride)
+// for the whole solve, so y, r, p, s, z and w of its cells stay in FP64 registers; only w, which the neighbours
+// gather, is written to memory (double-buffered, type TM) each iteration. Per iteration: n = A w from the published
+// w, the recurrences of the pipelined CG above, the two dot products, one grid barrier. TM = double gives the FP64
+// path (bitwise the memory-resident kernel on the same grid). (TM = float, an FP32 matrix product inside FP64
+// recurrences, was measured to drift like the all-FP32 pipelined form and is not used.)
+template <class TM, int R>
+__global__ void __launch_bounds__(kPThreads) kp_fine_cg_reg(FineDev F, const TM* __restrict__ Ts,
+                                                            const double* __restrict__ sdiag,
+                                                            const double* __restrict__ b, double bscale,
+                                                            double* __restrict__ dx, TM* wa, TM* wb,
+                                                            double* partial, GridSync gs, double tol, int maxit,
+                                                            PcgResult* res) {
   __shared__ double sm[2 * 32];
+  double* part0 = partial;
+  double* part1 = partial + 2 * gridDim.x;
+  const int stride = gridDim.x * blockDim.x;
+  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+  double y[R], r[R], p[R], sv[R], z[R], w[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int K = k0 + u * stride;
+    y[u] = p[u] = sv[u] = z[u] = w[u] = 0.0;
+    r[u] = 0.0;
+    if (K < F.N) {
+      r[u] = sdiag[K] * bscale * b[K];
+      wa[K] = (TM)r[u];   // the first product is A r
+    }
+  }
+  if (!grid_barrier(gs)) return;
+  double a4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int K = k0 + u * stride;
+    if (K < F.N) {
+      w[u] = (double)sell_apply<TM>(F, Ts, wa, K);
+      wb[K] = (TM)w[u];
+      a4[0] = fma(r[u], r[u], a4[0]);
+      a4[1] = fma(w[u], r[u], a4[1]);
+    }
+  }
+  if (!grid_sum_x<2, 2>(a4, part1, gs.out + 0, gs, sm, [&](double* o) {
+        o[2] = 0.0;
+        o[3] = o[1] != 0.0 ? o[0] / o[1] : 0.0;
+      }))
+    return;
+  double gamma = a4[0], beta = a4[2], alpha = a4[3];
+  const double rr0 = gamma;
+  const double tol2 = tol * tol * rr0;
+  TM* wc = wb;   // published w of the current iteration
+  TM* wn = wa;   // next w
+  int it = 0;
+  while (rr0 > 0.0 && gamma > tol2 && it < maxit) {
+    if (!(alpha != 0.0)) break;
+    double n4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const int K = k0 + u * stride;
+      if (K < F.N) {
+        const double nK = (double)sell_apply<TM>(F, Ts, wc, K);
+        z[u] = nK + beta * z[u];
+        sv[u] = w[u] + beta * sv[u];
+        p[u] = r[u] + beta * p[u];
+        y[u] += alpha * p[u];
+        r[u] = r[u] - alpha * sv[u];
+        w[u] = w[u] - alpha * z[u];
+        wn[K] = (TM)w[u];
+        n4[0] = fma(r[u], r[u], n4[0]);
+        n4[1] = fma(w[u], r[u], n4[1]);
+      }
+    }
+    if (!grid_sum_x<2, 2>(n4, (it & 1) ? part1 : part0, gs.out + ((it & 1) ? 16 : 8), gs, sm, [&](double* o) {
+          const double g = o[0], d = o[1];
+          const double bn = gamma != 0.0 ? g / gamma : 0.0;
+          const double den = d - bn * g / alpha;
+          o[2] = bn;
+          o[3] = den != 0.0 ? g / den : 0.0;
+        }))
+      return;
+    gamma = n4[0];
+    beta = n4[2];
+    alpha = n4[3];
+    TM* t = wc;
+    wc = wn;
+    wn = t;
+    ++it;
+  }
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int K = k0 + u * stride;
+    if (K < F.N) dx[K] = sdiag[K] * y[u];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    res->iters = it;
+    res->rr0 = rr0;
+    res->rr = gamma;
+  }
+}
+
+// ---- coarse level: hybridized saddle solve (rhs, Jacobi diagonal, CG on H lambda = xi, local recovery) ------
+// The solve of one frozen-coefficient coarse saddle as a device function of a persistent grid (sm: 64 doubles of
+// shared memory). kapc, bs and bp may have been written earlier in the same launch, so they are read through L2.
+// Returns false if a grid barrier gave up; `iters` and `rr_out` receive the CG iterations and final (r, r).
+template <class T>
+__device__ bool hyb_solve_dev(const LevelDev& L, const T* __restrict__ Hc, const T* __restrict__ Sinv,
+                              const double* kapc, const double* bs, const double* bp, T* ylam, T* ydiag, T* lam,
+                              T* lr, T* lz, T* pa, T* pb, T* lq, T* ldinv, double* dsig, double* dp,
+                              double* partial, const GridSync& gs, double* sm, double tol, int maxit, int gsz,
+                              int& iters, double& rr0_out, double& rr_out) {
   double* part0 = partial;
   double* part1 = partial + 2 * gridDim.x;
   // phase 0: per interface slot k of cell c, u_k = kappa A[k,:] bhat + B[k,:] b_p (signed) and kappa Hc[k,k]
   GSTRIDE(k, L.nif) {
     const int c = L.if_cell[k];
     const int mc = L.m[c], lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c], n = nl + mc;
-    const double kp = kapc[c];
+    const double kp = __ldcg(&kapc[c]);
     const int u = L.if_slot[k];
     const T* Su = Sinv + L.sad_off[c] + (size_t)u * n;
     T a1 = 0, a2_ = 0;
     for (int t = 0; t < nl; ++t)
-      if (L.own0[lo + t]) a1 += Su[t] * (T)bs[L.loc[lo + t]];
-    for (int q = 0; q < mc; ++q) a2_ += Su[nl + q] * (T)bp[po + q];
+      if (L.own0[lo + t]) a1 += Su[t] * (T)__ldcg(&bs[L.loc[lo + t]]);
+    for (int q = 0; q < mc; ++q) a2_ += Su[nl + q] * (T)__ldcg(&bp[po + q]);
     ylam[k] = (T)L.if_sign[k] * ((T)kp * a1 + a2_);
     const int k0 = L.if_off[c], ni = L.if_off[c + 1] - k0;
     ydiag[k] = (T)kp * Hc[L.hc_off[c] + (k - k0) * ni + (k - k0)];
   }
-  if (!grid_barrier(gs)) return;
+  if (!grid_barrier(gs)) return false;
   T u0 = (T)0, u1 = (T)0;   // per-thread partial sums in T, block and grid sums in FP64
   GSTRIDE(l, L.nlam) {
     const T xi = __ldcg(&ylam[L.lam_y0[l]]) + __ldcg(&ylam[L.lam_y1[l]]);
@@ -386,7 +492,7 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
     u1 = fma(xi, xi, u1);
   }
   double a2[2] = {(double)u0, (double)u1};
-  if (!grid_sum<2>(a2, part1, gs.out + 0, gs, sm)) return;
+  if (!grid_sum<2>(a2, part1, gs.out + 0, gs, sm)) return false;
   double rz = a2[0];
   const double rr0 = a2[1];
   double rr = rr0;
@@ -420,7 +526,7 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
             const int* lk = L.if_lam + k0;
             T y = 0;
             for (int j = g; j < ni; j += gsz) y += Hk[j] * __ldcg(&lz[lk[j]]);
-            hz += (T)kapc[c] * y;
+            hz += (T)__ldcg(&kapc[c]) * y;
           }
         }
         for (int off = gsz >> 1; off > 0; off >>= 1) hz += __shfl_xor_sync(0xffffffffu, hz, off);
@@ -436,7 +542,7 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
     }
     double a1[2] = {(double)upq, 0.0};
     if (!grid_sum_x<1, 1>(a1, part0, gs.out + 8, gs, sm, [&](double* o) { o[1] = o[0] != 0.0 ? rz / o[0] : 0.0; }))
-      return;
+      return false;
     const double alpha_d = a1[1];
     const T alpha = (T)alpha_d;
     u0 = u1 = (T)0;
@@ -452,7 +558,7 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
     double a3[3] = {(double)u0, (double)u1, 0.0};
     if (!grid_sum_x<2, 1>(a3, part1, gs.out + 16, gs, sm,
                           [&](double* o) { o[2] = rz != 0.0 ? o[0] / rz : 0.0; }))
-      return;
+      return false;
     beta = (T)a3[2];
     rz = a3[0];
     rr = a3[1];
@@ -469,11 +575,11 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
     const T* Su = Sinv + L.sad_off[c] + (size_t)u * n;
     T a1 = 0, a2_ = 0;
     for (int t = 0; t < nl; ++t)
-      if (L.own0[lo + t]) a1 += Su[t] * (T)bs[L.loc[lo + t]];
+      if (L.own0[lo + t]) a1 += Su[t] * (T)__ldcg(&bs[L.loc[lo + t]]);
     for (int k = L.if_off[c]; k < L.if_off[c + 1]; ++k)
       a1 -= Su[L.if_slot[k]] * (T)L.if_sign[k] * __ldcg(&lam[L.if_lam[k]]);
-    for (int q = 0; q < mc; ++q) a2_ += Su[nl + q] * (T)bp[po + q];
-    dsig[L.loc[y]] = (double)((T)kapc[c] * a1 + a2_);
+    for (int q = 0; q < mc; ++q) a2_ += Su[nl + q] * (T)__ldcg(&bp[po + q]);
+    dsig[L.loc[y]] = (double)((T)__ldcg(&kapc[c]) * a1 + a2_);
   }
   GSTRIDE(i, L.np) {
     const int c = L.p_cell[i];
@@ -481,16 +587,206 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
     const T* Sr = Sinv + L.sad_off[c] + (size_t)(nl + i - po) * n;
     T a1 = 0, a2_ = 0;
     for (int t = 0; t < nl; ++t)
-      if (L.own0[lo + t]) a1 += Sr[t] * (T)bs[L.loc[lo + t]];
+      if (L.own0[lo + t]) a1 += Sr[t] * (T)__ldcg(&bs[L.loc[lo + t]]);
     for (int k = L.if_off[c]; k < L.if_off[c + 1]; ++k)
       a1 -= Sr[L.if_slot[k]] * (T)L.if_sign[k] * __ldcg(&lam[L.if_lam[k]]);
-    for (int q = 0; q < mc; ++q) a2_ += Sr[nl + q] * (T)bp[po + q];
-    dp[i] = (double)a1 + (double)a2_ / kapc[c];
+    for (int q = 0; q < mc; ++q) a2_ += Sr[nl + q] * (T)__ldcg(&bp[po + q]);
+    dp[i] = (double)a1 + (double)a2_ / __ldcg(&kapc[c]);
   }
+  iters = it;
+  rr0_out = rr0;
+  rr_out = rr;
+  return true;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* __restrict__ Hc,
+                                                         const T* __restrict__ Sinv, const double* kapc,
+                                                         const double* bs, const double* bp, T* ylam, T* ydiag,
+                                                         T* lam, T* lr, T* lz, T* pa, T* pb, T* lq, T* ldinv,
+                                                         double* dsig, double* dp, double* partial, GridSync gs,
+                                                         double tol, int maxit, int gsz, PcgResult* res) {
+  __shared__ double sm[2 * 32];
+  int it = 0;
+  double rr0 = 0.0, rr = 0.0;
+  if (!hyb_solve_dev<T>(L, Hc, Sinv, kapc, bs, bp, ylam, ydiag, lam, lr, lz, pa, pb, lq, ldinv, dsig, dp, partial,
+                        gs, sm, tol, maxit, gsz, it, rr0, rr))
+    return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     res->iters = it;
     res->rr0 = rr0;
     res->rr = rr;
+  }
+}
+
+// ---- fused coarse Picard step -------------------------------------------------------------------------------
+// Max over the grid of one value per thread (deterministic: max is exact), through the same last-block protocol.
+__device__ __forceinline__ bool grid_max(double& v, double* partial, double* out, const GridSync& gs, double* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double m = v;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+  if (lane == 0) sm[warp] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bm = sm[0];
+    for (int w = 1; w < nw; ++w) bm = fmax(bm, sm[w]);
+    partial[blockIdx.x] = bm;
+  }
+  const bool ok = grid_barrier_ex(gs, [&]() {
+    if (threadIdx.x == 0) {
+      double gm = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) gm = fmax(gm, __ldcg(&partial[b]));
+      out[0] = gm;
+    }
+  });
+  if (!ok) return false;
+  v = __ldcg(&out[0]);
+  return true;
+}
+
+// r = A^l(x) - b on a coarse level (Prop. 1, eq. structure): kapc = kappa(w_c . p_c) per cell, yl = per-cell
+// local flux products s Mloc sigma + Dloc^T p, r_p = Dloc sigma - b_p, r_sigma = sum of the owners' yl - b_sigma;
+// nb = -r if given. x and b may have been written earlier in the launch (read through L2). The caller has put a
+// grid barrier after the last write of x. Returns ||r|| in rn.
+__device__ bool coarse_residual_dev(const LevelDev& L, const double* x, const double* b, double* r, double* nb,
+                                    double* kapc, double* yl, int kind, double a, double* partial,
+                                    const GridSync& gs, double* sm, double& rn) {
+  const double* xs = x;
+  const double* xp = x + L.nflux;
+  GSTRIDE(c, L.nc) {
+    const int po = L.p_off[c];
+    double pb = 0.0;
+    for (int q = 0; q < L.m[c]; ++q) pb = fma(L.w[po + q], __ldcg(&xp[po + q]), pb);
+    kapc[c] = kappa_of(pb, kind, a);
+  }
+  if (!grid_barrier(gs)) return false;
+  double acc = 0.0;
+  GSTRIDE(y, L.nyl) {
+    const int c = L.slot_cell[y];
+    const int mc = L.m[c], lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c];
+    const int u = y - lo;
+    const double* Mu = L.Mloc + L.mat_off[c] + (size_t)u * nl;
+    const double* D = L.Dloc + L.dmat_off[c];
+    double v = 0.0;
+    for (int t = 0; t < nl; ++t) v = fma(Mu[t], __ldcg(&xs[L.loc[lo + t]]), v);
+    v /= __ldcg(&kapc[c]);
+    for (int q = 0; q < mc; ++q) v = fma(D[q * nl + u], __ldcg(&xp[po + q]), v);
+    yl[y] = v;
+  }
+  GSTRIDE(i, L.np) {
+    const int c = L.p_cell[i];
+    const int lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c];
+    const double* Dr = L.Dloc + L.dmat_off[c] + (size_t)(i - po) * nl;
+    double v = 0.0;
+    for (int t = 0; t < nl; ++t) v = fma(Dr[t], __ldcg(&xs[L.loc[lo + t]]), v);
+    if (b) v -= __ldcg(&b[L.nflux + i]);
+    r[L.nflux + i] = v;
+    if (nb) nb[L.nflux + i] = -v;
+    acc = fma(v, v, acc);
+  }
+  if (!grid_barrier(gs)) return false;
+  GSTRIDE(i, L.nflux) {
+    double v = __ldcg(&yl[L.f_y0[i]]);
+    if (L.f_y1[i] >= 0) v += __ldcg(&yl[L.f_y1[i]]);
+    if (b) v -= __ldcg(&b[i]);
+    r[i] = v;
+    if (nb) nb[i] = -v;
+    acc = fma(v, v, acc);
+  }
+  double s1[1] = {acc};
+  if (!grid_sum<1>(s1, partial, gs.out + 24, gs, sm)) return false;
+  rn = sqrt(s1[0]);
+  return true;
+}
+
+// Algorithm 1 on a coarse level along dx from step s0: trial x + s s0 dx, halving s while the half step is no worse
+// than theta times the current trial (at most bt_nmax times) as long as the trial is worse than ||r(x)||; x takes
+// the last trial and rn its residual norm.
+template <class T>
+__device__ bool coarse_backtrack_dev(const LevelDev& L, const CoarseStepBufs<T>& B, const CoarseStepParams& P,
+                                     double s0, double& rn, int& evals, double* partial, const GridSync& gs,
+                                     double* sm) {
+  const int nx = L.nflux + L.np;
+  double* t1 = B.xt1;
+  double* t2 = B.xt2;
+  double s = 1.0;
+  GSTRIDE(i, nx) t1[i] = fma(s * s0, __ldcg(&B.dx[i]), __ldcg(&B.x[i]));
+  if (!grid_barrier(gs)) return false;
+  double r_s = 0.0;
+  if (!coarse_residual_dev(L, t1, B.b, B.rt, nullptr, B.kapc, B.yl, P.kind, P.a, partial, gs, sm, r_s)) return false;
+  ++evals;
+  int n = 0;
+  while (r_s > rn && n < P.bt_nmax) {
+    GSTRIDE(i, nx) t2[i] = fma(0.5 * s * s0, __ldcg(&B.dx[i]), __ldcg(&B.x[i]));
+    if (!grid_barrier(gs)) return false;
+    double r_half = 0.0;
+    if (!coarse_residual_dev(L, t2, B.b, B.rt, nullptr, B.kapc, B.yl, P.kind, P.a, partial, gs, sm, r_half))
+      return false;
+    ++evals;
+    if (r_half > P.bt_theta * r_s) break;
+    s *= 0.5;
+    ++n;
+    r_s = r_half;
+    double* t = t1;
+    t1 = t2;
+    t2 = t;
+  }
+  GSTRIDE(i, nx) B.x[i] = __ldcg(&t1[i]);
+  if (!grid_barrier(gs)) return false;
+  rn = r_s;
+  return true;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kPThreads) kp_coarse_step(LevelDev L, const T* __restrict__ Hc,
+                                                           const T* __restrict__ Sinv, CoarseStepBufs<T> B,
+                                                           CoarseStepParams P, double* partial, GridSync gs,
+                                                           int gsz, CoarseStepResult* res) {
+  __shared__ double sm[2 * 32];
+  int iters = 0, steps = 0, evals = 0;
+  double rn = P.rn_in;
+  if (P.backtrack_first) {
+    if (!coarse_backtrack_dev<T>(L, B, P, 1.0, rn, evals, partial, gs, sm)) return;
+  }
+  double r0 = 0.0;
+  for (int k = 0; k < P.nsteps; ++k) {
+    if (!coarse_residual_dev(L, B.x, B.b, B.r, B.nb, B.kapc, B.yl, P.kind, P.a, partial, gs, sm, rn)) return;
+    ++evals;
+    if (k == 0) r0 = rn;
+    if (P.coarsest && (rn <= P.tol_rel * r0 || rn <= P.tol_abs)) break;
+    int it = 0;
+    double rr0 = 0.0, rr = 0.0;
+    if (!hyb_solve_dev<T>(L, Hc, Sinv, B.kapc, B.nb, B.nb + L.nflux, B.ylam, B.ydiag, B.lam, B.lr, B.lz, B.pa,
+                          B.pb, B.lq, B.ldinv, B.dx, B.dx + L.nflux, partial, gs, sm, P.lin_tol, P.maxit, gsz, it,
+                          rr0, rr))
+      return;
+    iters += it;
+    if (!grid_barrier(gs)) return;   // dx complete
+    double s0 = 1.0;
+    if (P.dp_clamp > 0.0) {
+      double m = 0.0;
+      GSTRIDE(c, L.nc) {
+        const int po = L.p_off[c];
+        double v = 0.0;
+        for (int q = 0; q < L.m[c]; ++q) v = fma(L.w[po + q], __ldcg(&B.dx[L.nflux + po + q]), v);
+        m = fmax(m, fabs(v));
+      }
+      if (!grid_max(m, partial, gs.out + 28, gs, sm)) return;
+      if (m > P.dp_clamp) s0 = P.dp_clamp / m;
+    }
+    if (!coarse_backtrack_dev<T>(L, B, P, s0, rn, evals, partial, gs, sm)) return;
+    ++steps;
+  }
+  if (P.final_residual) {
+    if (!coarse_residual_dev(L, B.x, B.b, B.r, nullptr, B.kapc, B.yl, P.kind, P.a, partial, gs, sm, rn)) return;
+    ++evals;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    res->rn = rn;
+    res->iters = iters;
+    res->steps = steps;
+    res->res_evals = evals;
   }
 }
 
@@ -537,6 +833,28 @@ cudaError_t launch_fine_cg_pipe(cudaStream_t st, const FineDev& F, const T* Ts, 
                   (void*)&tol, (void*)&maxit, (void*)&res};
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
 }
+// Register-resident pipelined CG if every thread holds at most 4 cells on the grid the launch gets; returns
+// cudaErrorNotSupported (nothing launched) otherwise.
+template <class TM>
+cudaError_t launch_fine_cg_reg(cudaStream_t st, const FineDev& F, const TM* Ts, const double* sdiag, const double* b,
+                               double bscale, double* dx, TM* wa, TM* wb, double* partial, GridSync gs, double tol,
+                               int maxit, PcgResult* res) {
+  const void* fns[3] = {(const void*)kp_fine_cg_reg<TM, 1>, (const void*)kp_fine_cg_reg<TM, 2>,
+                        (const void*)kp_fine_cg_reg<TM, 4>};
+  const int Rs[3] = {1, 2, 4};
+  for (int i = 0; i < 3; ++i) {
+    const int grid = coop_grid(fns[i], F.N, gs.sm_cap);
+    const long cap = (long)grid * kPThreads * Rs[i];
+    if (cap < F.N) continue;
+    void* args[] = {(void*)&F, (void*)&Ts, (void*)&sdiag, (void*)&b, (void*)&bscale, (void*)&dx, (void*)&wa,
+                    (void*)&wb, (void*)&partial, (void*)&gs, (void*)&tol, (void*)&maxit, (void*)&res};
+    return cudaLaunchCooperativeKernel(fns[i], dim3(grid), dim3(kPThreads), args, 0, st);
+  }
+  return cudaErrorNotSupported;
+}
+template cudaError_t launch_fine_cg_reg<double>(cudaStream_t, const FineDev&, const double*, const double*,
+                                                const double*, double, double*, double*, double*, double*, GridSync,
+                                                double, int, PcgResult*);
 template cudaError_t launch_fine_cg_pipe<double>(cudaStream_t, const FineDev&, const double*, const double*,
                                                  const double*, double, double*, double*, double*, double*, double*,
                                                  double*, double*, double*, double*, GridSync, double, int,
@@ -575,5 +893,27 @@ template cudaError_t launch_hyb_solve<float>(cudaStream_t, const LevelDev&, cons
                                              const double*, const double*, const double*, float*, float*, float*,
                                              float*, float*, float*, float*, float*, float*, double*, double*,
                                              double*, GridSync, double, int, PcgResult*);
+
+template <class T>
+cudaError_t launch_coarse_step(cudaStream_t st, const LevelDev& L, const T* Hc, const T* Sinv,
+                               const CoarseStepBufs<T>& B, const CoarseStepParams& P, double* partial, GridSync gs,
+                               CoarseStepResult* res) {
+  int gsz = 1;
+  while (gsz < 32 && (long)L.nlam * gsz < 65536) gsz *= 2;
+  long items = (long)L.nlam * gsz;
+  for (long v : {(long)L.nif, (long)L.nyl, (long)L.np, (long)L.nflux + L.np, (long)L.nc})
+    if (v > items) items = v;
+  const void* fn = (const void*)kp_coarse_step<T>;
+  int grid = coop_grid(fn, (int)items, gs.sm_cap);
+  void* args[] = {(void*)&L, (void*)&Hc, (void*)&Sinv, (void*)&B, (void*)&P, (void*)&partial, (void*)&gs,
+                  (void*)&gsz, (void*)&res};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
+}
+template cudaError_t launch_coarse_step<double>(cudaStream_t, const LevelDev&, const double*, const double*,
+                                                const CoarseStepBufs<double>&, const CoarseStepParams&, double*,
+                                                GridSync, CoarseStepResult*);
+template cudaError_t launch_coarse_step<float>(cudaStream_t, const LevelDev&, const float*, const float*,
+                                               const CoarseStepBufs<float>&, const CoarseStepParams&, double*,
+                                               GridSync, CoarseStepResult*);
 
 }  // namespace nlmg

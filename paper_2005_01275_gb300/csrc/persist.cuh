@@ -31,6 +31,52 @@ cudaError_t launch_fine_cg_pipe(cudaStream_t st, const FineDev& F, const T* Ts, 
                                 double bscale, double* dx, T* y, T* r, T* wa, T* wb, T* z, T* sv, T* p,
                                 double* partial, GridSync gs, double tol, int maxit, PcgResult* res);
 
+// Register-resident pipelined CG (TM = type of the matrix and of the exchanged vector, double; recurrences in FP64).
+// Returns cudaErrorNotSupported without launching when a thread would have to hold more than 4 cells.
+template <class TM>
+cudaError_t launch_fine_cg_reg(cudaStream_t st, const FineDev& F, const TM* Ts, const double* sdiag, const double* b,
+                               double bscale, double* dx, TM* wa, TM* wb, double* partial, GridSync gs, double tol,
+                               int maxit, PcgResult* res);
+
+// Device buffers of one coarse level used by the fused Picard step (all of length nflux + np unless noted).
+template <class T>
+struct CoarseStepBufs {
+  double *x, *b, *r, *nb, *dx, *xt1, *xt2, *rt;   // iterate, rhs, residual, -residual, step, trials, trial residual
+  double *kapc, *yl;                              // kappa per cell (nc), per-cell local flux products (nyl)
+  T *ylam, *ydiag, *lam, *lr, *lz, *pa, *pb, *lq, *ldinv;   // hybridized CG (nif / nlam)
+};
+
+struct CoarseStepParams {
+  int kind;
+  double a;
+  double dp_clamp;       // <= 0: off
+  int bt_nmax;
+  double bt_theta;
+  int backtrack_first;   // 1: first x <- Algorithm 1 along the given dx from s = 1 (rn_in = ||r(x)||)
+  double rn_in;
+  int nsteps;            // Picard steps after that
+  int coarsest;          // 1: stop the steps once ||r|| <= tol_rel ||r(x_entry)|| or ||r|| <= tol_abs
+  double tol_rel, tol_abs;
+  int final_residual;    // 1: r = A(x) - b at the final x
+  double lin_tol;
+  int maxit;
+};
+
+struct CoarseStepResult {
+  double rn;        // ||A(x) - b|| at the final x
+  int iters;        // hybridized CG iterations
+  int steps;        // Picard steps taken
+  int res_evals;    // coarse operator evaluations
+  int err;
+};
+
+// One launch: [Algorithm 1 along a given correction], up to nsteps coarse Picard steps (residual, frozen-kappa
+// hybridized solve, clamp on Pi~ dp, Algorithm 1), [final residual]; every decision is taken on the device.
+template <class T>
+cudaError_t launch_coarse_step(cudaStream_t st, const LevelDev& L, const T* Hc, const T* Sinv,
+                               const CoarseStepBufs<T>& B, const CoarseStepParams& P, double* partial, GridSync gs,
+                               CoarseStepResult* res);
+
 template <class T>
 cudaError_t launch_hyb_solve(cudaStream_t st, const LevelDev& L, const T* Hc, const T* Sinv, const double* kapc,
                              const double* bs, const double* bp, T* ylam, T* ydiag, T* lam, T* lr, T* lz, T* pa,

@@ -42,7 +42,7 @@ struct Error : std::runtime_error {
 // Per coarse level work buffers.
 struct CoarseBuf {
   double *x = nullptr, *b = nullptr, *r = nullptr, *dx = nullptr, *nb = nullptr, *xt1 = nullptr, *xt2 = nullptr;
-  double *xc = nullptr, *yl = nullptr, *kapc = nullptr, *ptmp = nullptr;
+  double *xc = nullptr, *yl = nullptr, *kapc = nullptr, *ptmp = nullptr, *rt = nullptr;
   double *ylam = nullptr, *ydiag = nullptr, *lam = nullptr, *lr = nullptr, *lz = nullptr, *lpa = nullptr, *lpb = nullptr,
          *lq = nullptr, *ldinv = nullptr, *xi = nullptr;
   float *f_ylam = nullptr, *f_ydiag = nullptr, *f_lam = nullptr, *f_lr = nullptr, *f_lz = nullptr,
@@ -79,6 +79,7 @@ struct Shared {
   std::vector<TransferDev> TD;
   long long nnz_real = 0;
   double hyb_bytes_per_iter[8] = {0};
+  double coarse_res_bytes[8] = {0};   // algorithmic bytes of one coarse operator evaluation per level
   ~Shared() {
     for (void* p : allocs) cudaFree(p);
   }
@@ -122,6 +123,7 @@ struct nlmg_ctx {
   double tol_rel = 1e-8, tol_abs = 1e-10;   // outer tolerances, also used on the coarsest level
   double lin_tol_eff = 1e-2, coarse_lin_tol_eff = 1e-1;   // inner tolerances of the running solve
   int tightenings = 0;
+  int last_fine_kind = 0;          // variant of the last level-0 CG launch (0 two-barrier, 1 pipelined, 2 registers)
   int auto_sm_cap = 0;            // SM share chosen by nlmg_solve_many while instances run side by side
   void reset_inner_tols() {
     sm_cap = opt.max_sms > 0 ? opt.max_sms : auto_sm_cap;
@@ -381,6 +383,10 @@ void upload_level(nlmg_ctx* c, int l) {
   // algorithmic bytes of one CG iteration of the hybridized solve: H blocks, their lambda ids, the per-interface
   // buffer written and read, the lambda vectors (z, p_old gathered once; CG update 5 reads + 3 writes)
   c->sh->hyb_bytes_per_iter[l] = 8.0 * (double)Hc.size() + 12.0 * D.nif + 8.0 * D.nc + 16.0 * D.nif + 136.0 * nlam;
+  // one evaluation of the coarse operator: the static local blocks and their index arrays, x read, kappa per cell
+  // written and read, the per-cell products written and read, r written
+  c->sh->coarse_res_bytes[l] = 8.0 * (double)(L.Mloc.size() + L.Dloc.size()) + 8.0 * (double)L.loc.size() +
+                               16.0 * (D.nflux + D.np) + 16.0 * D.nc + 16.0 * D.nyl + 8.0 * (D.nflux + D.np);
 }
 
 // Work buffers of coarse level l (per context).
@@ -400,6 +406,7 @@ void alloc_level(nlmg_ctx* c, int l) {
   B.yl = c->dalloc<double>(D.nyl);
   B.kapc = c->dalloc<double>(D.nc);
   B.ptmp = c->dalloc<double>(nx);
+  B.rt = c->dalloc<double>(nx);
   B.ylam = c->dalloc<double>(D.nif);
   B.ydiag = c->dalloc<double>(D.nif);
   B.f_ylam = c->dalloc<float>(D.nif);
@@ -498,10 +505,12 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
   CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
   launch_sdiag(c->st, c->F.N, c->diagT, c->sdiag);
   const bool fp32 = c->opt.lin_precision == 1;
-  // FP64 pipelined CG (one grid barrier per iteration) for loose tolerances; the two-barrier CG when a tight solve is
-  // asked for (its recursively updated residual stays close to the true one) and in FP32, where the extra
-  // recurrences of the pipelined form drift too far from the true residual
+  // FP64 at loose tolerances: pipelined CG (one grid barrier per iteration), register-resident when every thread
+  // holds at most 4 cells. Tight tolerances, and FP32: the two-barrier CG, whose updated residual tracks the true
+  // one more closely (the pipelined recurrences with an FP32 matrix product drift: measured 10,768 instead of 3,466
+  // fine iterations on the 64^3 workload, whether the recurrences run in FP32 or in FP64).
   const bool pipe = !fp32 && c->lin_tol_eff >= 1e-6;
+  int kind = 0;   // 0 two-barrier, 1 pipelined in memory, 2 pipelined in registers
   int pi;
   if (fp32) {
     launch_scale_sell<float>(c->st, c->F, c->Tval, c->sdiag, c->Ts32);
@@ -511,14 +520,25 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
   } else {
     launch_scale_sell<double>(c->st, c->F, c->Tval, c->sdiag, c->Ts64);
     pi = c->prof_begin(0);
+    cudaError_t e = cudaErrorNotSupported;
     if (pipe)
+      e = launch_fine_cg_reg<double>(c->st, c->F, c->Ts64, c->sdiag, R, -1.0, c->cx, c->dv1, c->dv2, c->d_partial,
+                                     gs, c->lin_tol_eff, c->opt.lin_maxit, c->d_res);
+    if (e == cudaSuccess) {
+      kind = 2;
+    } else if (e != cudaErrorNotSupported) {
+      CK(e);
+    } else if (pipe) {
+      kind = 1;
       CK(launch_fine_cg_pipe<double>(c->st, c->F, c->Ts64, c->sdiag, R, -1.0, c->cx, c->cz, c->cr, c->cpa, c->cpb,
                                      c->cq, c->dv1, c->dv2, c->d_partial, gs, c->lin_tol_eff, c->opt.lin_maxit,
                                      c->d_res));
-    else
+    } else {
       CK(launch_fine_cg<double>(c->st, c->F, c->Ts64, c->sdiag, R, -1.0, c->cx, c->cz, c->cr, c->cpa, c->cpb,
                                 c->cq, c->d_partial, gs, c->lin_tol_eff, c->opt.lin_maxit, c->d_res));
+    }
   }
+  c->last_fine_kind = kind;
   c->prof_end(pi);
   count_launch(1);
   CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(PcgResult), cudaMemcpyDeviceToHost, c->st));
@@ -527,14 +547,16 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
   const int it = c->h_res->iters;
   if (pi >= 0) {
     // Algorithmic bytes: per iteration the scaled matrix entries and their indices, then for the two-barrier CG
-    // r read, p and q read and written, p, q, y, r read and y, r written (11 vectors); for the pipelined CG w, z,
-    // s, p, y, r read and z, s, p, y, r, w written (12 vectors) and one extra product at the start. Once: b and
+    // r read, p and q read and written, p, q, y, r read and y, r written (11 vectors); for the pipelined CG in
+    // memory w, z, s, p, y, r read and z, s, p, y, r, w written (12 vectors); for the register-resident one only
+    // w gathered and w written (2 vectors). The pipelined forms take one extra product at the start. Once: b and
     // S read, y and r written, then S and y read and dx written. Gathered neighbour values are counted once.
     // Flops: one product (2 per stored entry) plus 6 FMAs per cell (two-barrier) or 9 (pipelined) per iteration.
     const double N = c->F.N, nnz = (double)c->sh->nnz_real, v = fp32 ? 4.0 : 8.0;
-    const double per_it_b = pipe ? (4.0 + v) * nnz + 12.0 * v * N : (4.0 + v) * nnz + 11.0 * v * N;
-    const double per_it_f = pipe ? 2.0 * nnz + 18.0 * N : 2.0 * nnz + 12.0 * N;   // an FMA counts 2
-    c->prof.bytes[0] += (8.0 + 8.0) * N + 2.0 * v * N + 8.0 * N + v * N + 8.0 * N + (pipe ? per_it_b : 0.0) +
+    const double nvec = kind == 2 ? 2.0 : kind == 1 ? 12.0 : 11.0;
+    const double per_it_b = (4.0 + v) * nnz + nvec * v * N;
+    const double per_it_f = kind ? 2.0 * nnz + 18.0 * N : 2.0 * nnz + 12.0 * N;   // an FMA counts 2
+    c->prof.bytes[0] += (8.0 + 8.0) * N + 2.0 * v * N + 8.0 * N + v * N + 8.0 * N + (kind ? per_it_b : 0.0) +
                         it * per_it_b;
     c->prof.flops[0] += it * per_it_f;
   }
@@ -715,28 +737,6 @@ double coarse_res(nlmg_ctx* c, int l, const double* x, const double* b, double* 
   return std::sqrt(v0 + v1);
 }
 
-void backtrack_coarse(nlmg_ctx* c, int l, const double* dx, double s0) {
-  const nlmg_options& o = c->opt;
-  const LevelDev& L = c->LD[l];
-  CoarseBuf& B = c->CB[l];
-  const int nx = L.nflux + L.np;
-  double s = 1.0;
-  int n = 0;
-  launch_axpy(c->st, nx, B.x, s * s0, dx, B.xt1);
-  double r_s = coarse_res(c, l, B.xt1, B.b, B.ptmp);
-  while (r_s > B.rn && n < o.bt_nmax) {
-    launch_axpy(c->st, nx, B.x, 0.5 * s * s0, dx, B.xt2);
-    double r_half = coarse_res(c, l, B.xt2, B.b, B.ptmp);
-    if (r_half > o.bt_theta * r_s) break;
-    s *= 0.5;
-    ++n;
-    r_s = r_half;
-    std::swap(B.xt1, B.xt2);
-  }
-  std::swap(B.x, B.xt1);
-  B.rn = r_s;
-}
-
 // Solve the frozen-coefficient saddle A_frozen(x) dx = -r (r, kapc current) by hybridization + persistent CG
 // -> B.dx. Returns iterations.
 int coarse_linear(nlmg_ctx* c, int l) {
@@ -770,21 +770,6 @@ int coarse_linear(nlmg_ctx* c, int l) {
   return it;
 }
 
-// One Picard smoothing step on coarse level l (Sec. 3.3.1) + clamp on Pi~ dp + Algorithm 1.
-void picard_coarse(nlmg_ctx* c, int l) {
-  const LevelDev& L = c->LD[l];
-  CoarseBuf& B = c->CB[l];
-  B.rn = coarse_res(c, l, B.x, B.b, B.r);
-  coarse_linear(c, l);
-  double s0 = 1.0;
-  if (c->opt.dp_clamp > 0) {
-    launch_coarse_pbar_max(c->st, L, B.dx + L.nflux, c->red(S_MAX));
-    double mx = c->read_sc(S_MAX);
-    if (mx > c->opt.dp_clamp) s0 = c->opt.dp_clamp / mx;
-  }
-  backtrack_coarse(c, l, B.dx, s0);
-}
-
 // x_{l+1} = Q x_l, b_{l+1} = A_{l+1}(x_{l+1}) - P^T r_l (r_l = [r_sigma; r_p] of level l >= 1 in CB[l].r)
 void make_coarse_problem(nlmg_ctx* c, int l) {
   const TransferDev& T = c->TD[l];
@@ -811,21 +796,66 @@ void make_coarse_problem(nlmg_ctx* c, int l) {
   CK(cudaMemcpyAsync(Bc.xc, Bc.x, (size_t)(C.nflux + C.np) * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
 }
 
+// One launch of the fused coarse Picard step on level l (see launch_coarse_step): optional Algorithm 1 along B.dx
+// from s = 1, then up to nsteps Picard steps, then optionally the residual at the final x. B.rn is updated.
+void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coarsest, bool final_residual) {
+  const LevelDev& L = c->LD[l];
+  CoarseBuf& B = c->CB[l];
+  CoarseStepParams P{};
+  P.kind = c->kind;
+  P.a = c->a;
+  P.dp_clamp = c->opt.dp_clamp;
+  P.bt_nmax = c->opt.bt_nmax;
+  P.bt_theta = c->opt.bt_theta;
+  P.backtrack_first = backtrack_first ? 1 : 0;
+  P.rn_in = B.rn;
+  P.nsteps = nsteps;
+  P.coarsest = coarsest ? 1 : 0;
+  P.tol_rel = c->tol_rel;
+  P.tol_abs = c->tol_abs;
+  P.final_residual = final_residual ? 1 : 0;
+  P.maxit = c->opt.lin_maxit;
+  GridSync gs{c->d_bar, c->d_bar + 32, &c->d_res->err, c->d_sc + 32, c->sm_cap};
+  CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->st));
+  CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
+  CoarseStepResult* dres = (CoarseStepResult*)(c->d_res + 1);
+  CK(cudaMemsetAsync(dres, 0, sizeof(CoarseStepResult), c->st));
+  int pi = c->prof_begin(1);
+  if (c->opt.lin_precision == 1) {
+    P.lin_tol = std::max(c->coarse_lin_tol_eff, 1e-6);
+    CoarseStepBufs<float> Bf{B.x, B.b, B.r, B.nb, B.dx, B.xt1, B.xt2, B.rt, B.kapc, B.yl, B.f_ylam, B.f_ydiag,
+                             B.f_lam, B.f_lr, B.f_lz, B.f_lpa, B.f_lpb, B.f_lq, B.f_ldinv};
+    CK(launch_coarse_step<float>(c->st, L, L.Hc32, L.Sinv32, Bf, P, c->d_partial, gs, dres));
+  } else {
+    P.lin_tol = c->coarse_lin_tol_eff;
+    CoarseStepBufs<double> Bd{B.x, B.b, B.r, B.nb, B.dx, B.xt1, B.xt2, B.rt, B.kapc, B.yl, B.ylam, B.ydiag,
+                              B.lam, B.lr, B.lz, B.lpa, B.lpb, B.lq, B.ldinv};
+    CK(launch_coarse_step<double>(c->st, L, L.Hc, L.Sinv, Bd, P, c->d_partial, gs, dres));
+  }
+  c->prof_end(pi);
+  count_launch(1);
+  CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(PcgResult) + sizeof(CoarseStepResult), cudaMemcpyDeviceToHost,
+                     c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (c->h_res->err) throw Error(NLMG_ETIMEOUT, "grid barrier wait gave up in the coarse step kernel");
+  const CoarseStepResult& R = *(const CoarseStepResult*)(c->h_res + 1);
+  B.rn = R.rn;
+  if (pi >= 0)
+    c->prof.bytes[1] += (double)R.iters * c->sh->hyb_bytes_per_iter[l] * (c->opt.lin_precision == 1 ? 0.5 : 1.0) +
+                        (double)R.res_evals * c->sh->coarse_res_bytes[l];
+  c->lin_iters += R.iters;
+  c->lin_iters_level[l] += R.iters;
+}
+
 void coarse_cycle(nlmg_ctx* c, int l) {
   const nlmg_options& o = c->opt;
   CoarseBuf& B = c->CB[l];
   const LevelDev& L = c->LD[l];
   if (l == c->nlev() - 1) {
-    B.rn = coarse_res(c, l, B.x, B.b, B.r);
-    const double r0 = B.rn;
-    for (int k = 0; k < o.coarsest_steps; ++k) {
-      if (B.rn <= c->tol_rel * r0 || B.rn <= c->tol_abs) break;
-      picard_coarse(c, l);
-    }
+    coarse_step(c, l, false, o.coarsest_steps, true, false);
     return;
   }
-  picard_coarse(c, l);
-  B.rn = coarse_res(c, l, B.x, B.b, B.r);
+  coarse_step(c, l, false, 1, false, true);   // pre-smoothing, then r at the smoothed x for the restriction
   make_coarse_problem(c, l);
   coarse_cycle(c, l + 1);
   const LevelDev& C = c->LD[l + 1];
@@ -834,8 +864,7 @@ void coarse_cycle(nlmg_ctx* c, int l) {
   launch_sub(c->st, C.nflux + C.np, Bc.x, Bc.xc, Bc.ptmp);
   launch_csr(c->st, T.ps_n, T.ps_off, T.ps_col, T.ps_val, Bc.ptmp, B.dx, 1.0, 0.0);
   launch_prolong_p(c->st, T, Bc.ptmp + C.nflux, B.dx + L.nflux);
-  backtrack_coarse(c, l, B.dx, 1.0);
-  picard_coarse(c, l);
+  coarse_step(c, l, true, 1, false, false);   // Algorithm 1 along the correction, then post-smoothing
 }
 
 // One FAS cycle from level 0 (Algorithm 2). Returns true if it stopped after pre-smoothing.
@@ -1060,10 +1089,11 @@ static void init_work(nlmg_ctx* c) {
   c->d_cnt = c->dalloc<unsigned>(16);
   CK(cudaMemsetAsync(c->d_cnt, 0, 16 * sizeof(unsigned), c->st));
   c->d_sc = c->dalloc<double>(64);
-  c->d_res = c->dalloc<PcgResult>(1);
+  static_assert(sizeof(CoarseStepResult) <= sizeof(PcgResult), "result slots");
+  c->d_res = c->dalloc<PcgResult>(2);   // the CG result, then the coarse-step result
   c->d_bar = c->dalloc<unsigned>(64);   // count and generation on separate 128-byte lines
   CK(cudaMemsetAsync(c->d_bar, 0, 64 * sizeof(unsigned), c->st));
-  CK(cudaMallocHost(&c->h_res, sizeof(PcgResult)));
+  CK(cudaMallocHost(&c->h_res, 2 * sizeof(PcgResult)));
   CK(cudaMemsetAsync(c->d_sc, 0, 64 * sizeof(double), c->st));
   c->reset_inner_tols();
   alloc_fine(c);
