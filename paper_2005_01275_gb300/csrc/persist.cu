@@ -35,48 +35,40 @@ __device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v
   return old;
 }
 
-__device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
-}
+// The synchronisation state one thread of a persistent kernel carries: the launch's barrier words, the two
+// buffers of per-block partial sums (used alternately by consecutive reductions), 64 doubles of shared memory and
+// the number of reductions so far (the same in every block).
+struct Grid {
+  GridSync gs;
+  double* partial;
+  double* sm;
+  unsigned seq;
+};
 
-// Bounded grid barrier: blocks arrive on gs.count (never reset inside a launch: barrier k completes with arrival
-// number (k + 1) * gridDim.x - 1); the last one to arrive runs `last` (a block-wide callback), then bumps the
-// generation that the others poll. Thread 0 of each block carries the block's ordering: __syncthreads, then an
-// acquire-release arrival (its release covers the block's earlier writes), the generation bump is a release and the
-// poll an acquire, so no separate fences are needed. Returns false (and sets *err) if a wait gave up.
-template <class LastFn>
-__device__ __forceinline__ bool grid_barrier_ex(const GridSync& gs, LastFn&& last) {
-  __shared__ int ok, is_last;
+// Bounded grid barrier with one atomic per block: every block adds 1 to gs.count except block 0, which adds
+// 2^31 - (gridDim.x - 1), so the counter's top bit flips exactly when the last block arrives and its low bits return
+// to 0 (barriers follow one another without a reset). Thread 0 arrives with an acquire-release atomic after
+// __syncthreads (its release covers the block's earlier writes) and polls the counter with acquire loads until the
+// top bit differs from the value it added to. Returns false (and sets *err) if the wait gave up after ~2 s.
+__device__ __forceinline__ bool grid_barrier(Grid& g) {
+  __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    const unsigned g = ld_acquire_gpu(gs.gen);
-    const unsigned arrived = atom_add_acq_rel_gpu(gs.count, 1u);
-    is_last = (arrived + 1u) % gridDim.x == 0u;
-    if (!is_last) {
-      unsigned long long spins = 0;
-      while (ld_acquire_gpu(gs.gen) == g) {
-        __nanosleep(32);
-        if ((++spins & 1023u) == 0 && (spins > kSpinLimit || *((volatile int*)gs.err) != 0)) {
-          atomicExch(gs.err, 1);
-          ok = 0;
-          break;
-        }
+    const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+    const unsigned old = atom_add_acq_rel_gpu(g.gs.count, inc);
+    unsigned long long spins = 0;
+    while (((ld_acquire_gpu(g.gs.count) ^ old) & 0x80000000u) == 0u) {
+      __nanosleep(32);
+      if ((++spins & 1023u) == 0 && (spins > kSpinLimit || *((volatile int*)g.gs.err) != 0)) {
+        atomicExch(g.gs.err, 1);
+        ok = 0;
+        break;
       }
     }
   }
   __syncthreads();
-  if (is_last) {
-    last();
-    __syncthreads();
-    if (threadIdx.x == 0) red_add_release_gpu(gs.gen, 1u);
-  }
-  __syncthreads();
   return ok != 0;
-}
-
-__device__ __forceinline__ bool grid_barrier(const GridSync& gs) {
-  return grid_barrier_ex(gs, []() {});
 }
 
 template <int NV>
@@ -107,44 +99,79 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
   __syncthreads();
 }
 
-// Grid sums of NV values: every block publishes its block sum; the last block to arrive adds the partials in block
-// order (fixed tree) and stores the result to out[0..NV-1]; its thread 0 then runs `post(out)`, which derives NX
-// scalars from the sums (the CG step lengths) into out[NV..NV+NX-1], so that each division is done once per grid
-// instead of once per thread. After the barrier every thread reads all NV + NX values.
+// Grid sums of NV values: every block publishes its block sum, and after the barrier every block adds all partials
+// in block order with the same fixed tree, so all blocks hold bit-identical sums; thread 0 then runs `post(o)`,
+// which derives NX scalars from the sums (the CG step lengths) into o[NV..NV+NX-1] in shared memory, so each
+// division is done once per block, not per thread. Consecutive reductions use the two partial buffers in turn: a
+// block can only overwrite a buffer after every block has passed the next barrier, i.e. has finished reading it.
 template <int NV, int NX = 0, class PostFn>
-__device__ __forceinline__ bool grid_sum_x(double (&v)[NV + NX], double* partial, double* out, const GridSync& gs,
-                                           double* sm, PostFn&& post) {
+__device__ __forceinline__ bool grid_sum_x(Grid& g, double (&v)[NV + NX], PostFn&& post) {
+  double* part = g.partial + (g.seq & 1u) * kPartStride;
+  ++g.seq;
   double w[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) w[k] = v[k];
-  block_sum<NV>(w, sm);
+  block_sum<NV>(w, g.sm);
   if (threadIdx.x == 0)
 #pragma unroll
-    for (int k = 0; k < NV; ++k) partial[blockIdx.x * NV + k] = w[k];
-  const bool ok = grid_barrier_ex(gs, [&]() {
-    double acc[NV];
+    for (int k = 0; k < NV; ++k) part[blockIdx.x * NV + k] = w[k];
+  if (!grid_barrier(g)) return false;
+  double acc[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
 #pragma unroll
-      for (int k = 0; k < NV; ++k) acc[k] += __ldcg(&partial[b * NV + k]);
-    block_sum<NV>(acc, sm);
-    if (threadIdx.x == 0) {
+    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(&part[b * NV + k]);
+  block_sum<NV>(acc, g.sm);
+  __shared__ double o[NV + NX];
+  if (threadIdx.x == 0) {
 #pragma unroll
-      for (int k = 0; k < NV; ++k) out[k] = acc[k];
-      post(out);
-    }
-  });
-  if (!ok) return false;
+    for (int k = 0; k < NV; ++k) o[k] = acc[k];
+    post(o);
+  }
+  __syncthreads();
 #pragma unroll
-  for (int k = 0; k < NV + NX; ++k) v[k] = __ldcg(&out[k]);
+  for (int k = 0; k < NV + NX; ++k) v[k] = o[k];
+  __syncthreads();
   return true;
 }
 
 template <int NV>
-__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partial, double* out, const GridSync& gs,
-                                         double* sm) {
-  return grid_sum_x<NV, 0>(v, partial, out, gs, sm, [](double*) {});
+__device__ __forceinline__ bool grid_sum(Grid& g, double (&v)[NV]) {
+  return grid_sum_x<NV, 0>(g, v, [](double*) {});
+}
+
+// Max over the grid of one value per thread (exact, hence deterministic), by the same protocol.
+__device__ __forceinline__ bool grid_max(Grid& g, double& v) {
+  double* part = g.partial + (g.seq & 1u) * kPartStride;
+  ++g.seq;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double m = v;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+  if (lane == 0) g.sm[warp] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bm = g.sm[0];
+    for (int w = 1; w < nw; ++w) bm = fmax(bm, g.sm[w]);
+    part[blockIdx.x] = bm;
+  }
+  if (!grid_barrier(g)) return false;
+  double gm = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) gm = fmax(gm, __ldcg(&part[b]));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) gm = fmax(gm, __shfl_down_sync(0xffffffffu, gm, off));
+  if (lane == 0) g.sm[warp] = gm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bm = g.sm[0];
+    for (int w = 1; w < nw; ++w) bm = fmax(bm, g.sm[w]);
+    g.sm[32] = bm;
+  }
+  __syncthreads();
+  v = g.sm[32];
+  __syncthreads();
+  return true;
 }
 
 #define GSTRIDE(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
@@ -166,8 +193,7 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __re
                                                         double* partial, GridSync gs, double tol, int maxit,
                                                         PcgResult* res) {
   __shared__ double sm[2 * 32];
-  double* part0 = partial;
-  double* part1 = partial + 2 * gridDim.x;
+  Grid g{gs, partial, sm, 0u};
   T t1 = (T)0;   // per-thread partial sums in T (a thread holds one or two cells), block and grid sums in FP64
   GSTRIDE(i, F.N) {
     const T ri = (T)(sdiag[i] * bscale * b[i]);
@@ -176,7 +202,7 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __re
     t1 = fma(ri, ri, t1);
   }
   double a1[1] = {(double)t1};
-  if (!grid_sum<1>(a1, part1, gs.out + 0, gs, sm)) return;
+  if (!grid_sum<1>(g, a1)) return;
   const double rr0 = a1[0];
   double rr = rr0;
   const double tol2 = tol * tol * rr0;
@@ -213,7 +239,7 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __re
       tpq = fma(pK, qK, tpq);
     }
     double pq[2] = {(double)tpq, 0.0};
-    if (!grid_sum_x<1, 1>(pq, part0, gs.out + 8, gs, sm, [&](double* o) { o[1] = o[0] != 0.0 ? rr / o[0] : 0.0; }))
+    if (!grid_sum_x<1, 1>(g, pq, [&](double* o) { o[1] = o[0] != 0.0 ? rr / o[0] : 0.0; }))
       return;
     const double alpha_d = pq[1];
     const T alpha = (T)alpha_d;
@@ -225,7 +251,7 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __re
       trn = fma(ri, ri, trn);
     }
     double rn[2] = {(double)trn, 0.0};
-    if (!grid_sum_x<1, 1>(rn, part1, gs.out + 16, gs, sm, [&](double* o) { o[1] = rr != 0.0 ? o[0] / rr : 0.0; }))
+    if (!grid_sum_x<1, 1>(g, rn, [&](double* o) { o[1] = rr != 0.0 ? o[0] / rr : 0.0; }))
       return;
     beta = (T)rn[1];
     rr = rn[0];
@@ -279,13 +305,12 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg_pipe(FineDev F, const T*
                                                              T* __restrict__ sv, T* __restrict__ p, double* partial,
                                                              GridSync gs, double tol, int maxit, PcgResult* res) {
   __shared__ double sm[2 * 32];
-  double* part0 = partial;
-  double* part1 = partial + 2 * gridDim.x;
+  Grid g{gs, partial, sm, 0u};
   GSTRIDE(i, F.N) {
     r[i] = (T)(sdiag[i] * bscale * b[i]);
     y[i] = z[i] = sv[i] = p[i] = (T)0;
   }
-  if (!grid_barrier(gs)) return;
+  if (!grid_barrier(g)) return;
   // a4 = {gamma, delta, beta, alpha}: the sums and, from the last block's thread 0, the step lengths of the next
   // iteration (beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old); first: 0, gamma / delta)
   double a4[4] = {0.0, 0.0, 0.0, 0.0};
@@ -296,7 +321,7 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg_pipe(FineDev F, const T*
     a4[0] = fma(rK, rK, a4[0]);
     a4[1] = fma((double)wK, rK, a4[1]);
   }
-  if (!grid_sum_x<2, 2>(a4, part1, gs.out + 0, gs, sm, [&](double* o) {
+  if (!grid_sum_x<2, 2>(g, a4, [&](double* o) {
         o[2] = 0.0;
         o[3] = o[1] != 0.0 ? o[0] / o[1] : 0.0;
       }))
@@ -328,7 +353,7 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg_pipe(FineDev F, const T*
       n4[0] = fma((double)rK, (double)rK, n4[0]);
       n4[1] = fma((double)wN, (double)rK, n4[1]);
     }
-    if (!grid_sum_x<2, 2>(n4, (it & 1) ? part1 : part0, gs.out + ((it & 1) ? 16 : 8), gs, sm, [&](double* o) {
+    if (!grid_sum_x<2, 2>(g, n4, [&](double* o) {
           const double g = o[0], d = o[1];
           const double bn = gamma != 0.0 ? g / gamma : 0.0;
           const double den = d - bn * g / alpha_d;
@@ -366,8 +391,7 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg_reg(FineDev F, const TM*
                                                             double* partial, GridSync gs, double tol, int maxit,
                                                             PcgResult* res) {
   __shared__ double sm[2 * 32];
-  double* part0 = partial;
-  double* part1 = partial + 2 * gridDim.x;
+  Grid g{gs, partial, sm, 0u};
   const int stride = gridDim.x * blockDim.x;
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
   double y[R], r[R], p[R], sv[R], z[R], w[R];
@@ -381,7 +405,7 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg_reg(FineDev F, const TM*
       wa[K] = (TM)r[u];   // the first product is A r
     }
   }
-  if (!grid_barrier(gs)) return;
+  if (!grid_barrier(g)) return;
   double a4[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
   for (int u = 0; u < R; ++u) {
@@ -393,7 +417,7 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg_reg(FineDev F, const TM*
       a4[1] = fma(w[u], r[u], a4[1]);
     }
   }
-  if (!grid_sum_x<2, 2>(a4, part1, gs.out + 0, gs, sm, [&](double* o) {
+  if (!grid_sum_x<2, 2>(g, a4, [&](double* o) {
         o[2] = 0.0;
         o[3] = o[1] != 0.0 ? o[0] / o[1] : 0.0;
       }))
@@ -423,7 +447,7 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg_reg(FineDev F, const TM*
         n4[1] = fma(w[u], r[u], n4[1]);
       }
     }
-    if (!grid_sum_x<2, 2>(n4, (it & 1) ? part1 : part0, gs.out + ((it & 1) ? 16 : 8), gs, sm, [&](double* o) {
+    if (!grid_sum_x<2, 2>(g, n4, [&](double* o) {
           const double g = o[0], d = o[1];
           const double bn = gamma != 0.0 ? g / gamma : 0.0;
           const double den = d - bn * g / alpha;
@@ -458,11 +482,8 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg_reg(FineDev F, const TM*
 template <class T>
 __device__ bool hyb_solve_dev(const LevelDev& L, const T* __restrict__ Hc, const T* __restrict__ Sinv,
                               const double* kapc, const double* bs, const double* bp, T* ylam, T* ydiag, T* lam,
-                              T* lr, T* lz, T* pa, T* pb, T* lq, T* ldinv, double* dsig, double* dp,
-                              double* partial, const GridSync& gs, double* sm, double tol, int maxit, int gsz,
-                              int& iters, double& rr0_out, double& rr_out) {
-  double* part0 = partial;
-  double* part1 = partial + 2 * gridDim.x;
+                              T* lr, T* lz, T* pa, T* pb, T* lq, T* ldinv, double* dsig, double* dp, Grid& g,
+                              double tol, int maxit, int gsz, int& iters, double& rr0_out, double& rr_out) {
   // phase 0: per interface slot k of cell c, u_k = kappa A[k,:] bhat + B[k,:] b_p (signed) and kappa Hc[k,k]
   GSTRIDE(k, L.nif) {
     const int c = L.if_cell[k];
@@ -478,7 +499,7 @@ __device__ bool hyb_solve_dev(const LevelDev& L, const T* __restrict__ Hc, const
     const int k0 = L.if_off[c], ni = L.if_off[c + 1] - k0;
     ydiag[k] = (T)kp * Hc[L.hc_off[c] + (k - k0) * ni + (k - k0)];
   }
-  if (!grid_barrier(gs)) return false;
+  if (!grid_barrier(g)) return false;
   T u0 = (T)0, u1 = (T)0;   // per-thread partial sums in T, block and grid sums in FP64
   GSTRIDE(l, L.nlam) {
     const T xi = __ldcg(&ylam[L.lam_y0[l]]) + __ldcg(&ylam[L.lam_y1[l]]);
@@ -492,7 +513,7 @@ __device__ bool hyb_solve_dev(const LevelDev& L, const T* __restrict__ Hc, const
     u1 = fma(xi, xi, u1);
   }
   double a2[2] = {(double)u0, (double)u1};
-  if (!grid_sum<2>(a2, part1, gs.out + 0, gs, sm)) return false;
+  if (!grid_sum<2>(g, a2)) return false;
   double rz = a2[0];
   const double rr0 = a2[1];
   double rr = rr0;
@@ -541,7 +562,7 @@ __device__ bool hyb_solve_dev(const LevelDev& L, const T* __restrict__ Hc, const
       }
     }
     double a1[2] = {(double)upq, 0.0};
-    if (!grid_sum_x<1, 1>(a1, part0, gs.out + 8, gs, sm, [&](double* o) { o[1] = o[0] != 0.0 ? rz / o[0] : 0.0; }))
+    if (!grid_sum_x<1, 1>(g, a1, [&](double* o) { o[1] = o[0] != 0.0 ? rz / o[0] : 0.0; }))
       return false;
     const double alpha_d = a1[1];
     const T alpha = (T)alpha_d;
@@ -556,8 +577,7 @@ __device__ bool hyb_solve_dev(const LevelDev& L, const T* __restrict__ Hc, const
       u1 = fma(ri, ri, u1);
     }
     double a3[3] = {(double)u0, (double)u1, 0.0};
-    if (!grid_sum_x<2, 1>(a3, part1, gs.out + 16, gs, sm,
-                          [&](double* o) { o[2] = rz != 0.0 ? o[0] / rz : 0.0; }))
+    if (!grid_sum_x<2, 1>(g, a3, [&](double* o) { o[2] = rz != 0.0 ? o[0] / rz : 0.0; }))
       return false;
     beta = (T)a3[2];
     rz = a3[0];
@@ -607,10 +627,11 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
                                                          double* dsig, double* dp, double* partial, GridSync gs,
                                                          double tol, int maxit, int gsz, PcgResult* res) {
   __shared__ double sm[2 * 32];
+  Grid g{gs, partial, sm, 0u};
   int it = 0;
   double rr0 = 0.0, rr = 0.0;
-  if (!hyb_solve_dev<T>(L, Hc, Sinv, kapc, bs, bp, ylam, ydiag, lam, lr, lz, pa, pb, lq, ldinv, dsig, dp, partial,
-                        gs, sm, tol, maxit, gsz, it, rr0, rr))
+  if (!hyb_solve_dev<T>(L, Hc, Sinv, kapc, bs, bp, ylam, ydiag, lam, lr, lz, pa, pb, lq, ldinv, dsig, dp, g, tol,
+                        maxit, gsz, it, rr0, rr))
     return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     res->iters = it;
@@ -620,38 +641,12 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
 }
 
 // ---- fused coarse Picard step -------------------------------------------------------------------------------
-// Max over the grid of one value per thread (deterministic: max is exact), through the same last-block protocol.
-__device__ __forceinline__ bool grid_max(double& v, double* partial, double* out, const GridSync& gs, double* sm) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double m = v;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
-  if (lane == 0) sm[warp] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double bm = sm[0];
-    for (int w = 1; w < nw; ++w) bm = fmax(bm, sm[w]);
-    partial[blockIdx.x] = bm;
-  }
-  const bool ok = grid_barrier_ex(gs, [&]() {
-    if (threadIdx.x == 0) {
-      double gm = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b) gm = fmax(gm, __ldcg(&partial[b]));
-      out[0] = gm;
-    }
-  });
-  if (!ok) return false;
-  v = __ldcg(&out[0]);
-  return true;
-}
-
 // r = A^l(x) - b on a coarse level (Prop. 1, eq. structure): kapc = kappa(w_c . p_c) per cell, yl = per-cell
 // local flux products s Mloc sigma + Dloc^T p, r_p = Dloc sigma - b_p, r_sigma = sum of the owners' yl - b_sigma;
 // nb = -r if given. x and b may have been written earlier in the launch (read through L2). The caller has put a
 // grid barrier after the last write of x. Returns ||r|| in rn.
 __device__ bool coarse_residual_dev(const LevelDev& L, const double* x, const double* b, double* r, double* nb,
-                                    double* kapc, double* yl, int kind, double a, double* partial,
-                                    const GridSync& gs, double* sm, double& rn) {
+                                    double* kapc, double* yl, int kind, double a, Grid& g, double& rn) {
   const double* xs = x;
   const double* xp = x + L.nflux;
   GSTRIDE(c, L.nc) {
@@ -660,7 +655,7 @@ __device__ bool coarse_residual_dev(const LevelDev& L, const double* x, const do
     for (int q = 0; q < L.m[c]; ++q) pb = fma(L.w[po + q], __ldcg(&xp[po + q]), pb);
     kapc[c] = kappa_of(pb, kind, a);
   }
-  if (!grid_barrier(gs)) return false;
+  if (!grid_barrier(g)) return false;
   double acc = 0.0;
   GSTRIDE(y, L.nyl) {
     const int c = L.slot_cell[y];
@@ -685,7 +680,7 @@ __device__ bool coarse_residual_dev(const LevelDev& L, const double* x, const do
     if (nb) nb[L.nflux + i] = -v;
     acc = fma(v, v, acc);
   }
-  if (!grid_barrier(gs)) return false;
+  if (!grid_barrier(g)) return false;
   GSTRIDE(i, L.nflux) {
     double v = __ldcg(&yl[L.f_y0[i]]);
     if (L.f_y1[i] >= 0) v += __ldcg(&yl[L.f_y1[i]]);
@@ -695,7 +690,7 @@ __device__ bool coarse_residual_dev(const LevelDev& L, const double* x, const do
     acc = fma(v, v, acc);
   }
   double s1[1] = {acc};
-  if (!grid_sum<1>(s1, partial, gs.out + 24, gs, sm)) return false;
+  if (!grid_sum<1>(g, s1)) return false;
   rn = sqrt(s1[0]);
   return true;
 }
@@ -705,23 +700,22 @@ __device__ bool coarse_residual_dev(const LevelDev& L, const double* x, const do
 // the last trial and rn its residual norm.
 template <class T>
 __device__ bool coarse_backtrack_dev(const LevelDev& L, const CoarseStepBufs<T>& B, const CoarseStepParams& P,
-                                     double s0, double& rn, int& evals, double* partial, const GridSync& gs,
-                                     double* sm) {
+                                     double s0, double& rn, int& evals, Grid& g) {
   const int nx = L.nflux + L.np;
   double* t1 = B.xt1;
   double* t2 = B.xt2;
   double s = 1.0;
   GSTRIDE(i, nx) t1[i] = fma(s * s0, __ldcg(&B.dx[i]), __ldcg(&B.x[i]));
-  if (!grid_barrier(gs)) return false;
+  if (!grid_barrier(g)) return false;
   double r_s = 0.0;
-  if (!coarse_residual_dev(L, t1, B.b, B.rt, nullptr, B.kapc, B.yl, P.kind, P.a, partial, gs, sm, r_s)) return false;
+  if (!coarse_residual_dev(L, t1, B.b, B.rt, nullptr, B.kapc, B.yl, P.kind, P.a, g, r_s)) return false;
   ++evals;
   int n = 0;
   while (r_s > rn && n < P.bt_nmax) {
     GSTRIDE(i, nx) t2[i] = fma(0.5 * s * s0, __ldcg(&B.dx[i]), __ldcg(&B.x[i]));
-    if (!grid_barrier(gs)) return false;
+    if (!grid_barrier(g)) return false;
     double r_half = 0.0;
-    if (!coarse_residual_dev(L, t2, B.b, B.rt, nullptr, B.kapc, B.yl, P.kind, P.a, partial, gs, sm, r_half))
+    if (!coarse_residual_dev(L, t2, B.b, B.rt, nullptr, B.kapc, B.yl, P.kind, P.a, g, r_half))
       return false;
     ++evals;
     if (r_half > P.bt_theta * r_s) break;
@@ -733,7 +727,7 @@ __device__ bool coarse_backtrack_dev(const LevelDev& L, const CoarseStepBufs<T>&
     t2 = t;
   }
   GSTRIDE(i, nx) B.x[i] = __ldcg(&t1[i]);
-  if (!grid_barrier(gs)) return false;
+  if (!grid_barrier(g)) return false;
   rn = r_s;
   return true;
 }
@@ -744,25 +738,26 @@ __global__ void __launch_bounds__(kPThreads) kp_coarse_step(LevelDev L, const T*
                                                            CoarseStepParams P, double* partial, GridSync gs,
                                                            int gsz, CoarseStepResult* res) {
   __shared__ double sm[2 * 32];
+  Grid g{gs, partial, sm, 0u};
   int iters = 0, steps = 0, evals = 0;
   double rn = P.rn_in;
   if (P.backtrack_first) {
-    if (!coarse_backtrack_dev<T>(L, B, P, 1.0, rn, evals, partial, gs, sm)) return;
+    if (!coarse_backtrack_dev<T>(L, B, P, 1.0, rn, evals, g)) return;
   }
   double r0 = 0.0;
   for (int k = 0; k < P.nsteps; ++k) {
-    if (!coarse_residual_dev(L, B.x, B.b, B.r, B.nb, B.kapc, B.yl, P.kind, P.a, partial, gs, sm, rn)) return;
+    if (!coarse_residual_dev(L, B.x, B.b, B.r, B.nb, B.kapc, B.yl, P.kind, P.a, g, rn)) return;
     ++evals;
     if (k == 0) r0 = rn;
     if (P.coarsest && (rn <= P.tol_rel * r0 || rn <= P.tol_abs)) break;
     int it = 0;
     double rr0 = 0.0, rr = 0.0;
     if (!hyb_solve_dev<T>(L, Hc, Sinv, B.kapc, B.nb, B.nb + L.nflux, B.ylam, B.ydiag, B.lam, B.lr, B.lz, B.pa,
-                          B.pb, B.lq, B.ldinv, B.dx, B.dx + L.nflux, partial, gs, sm, P.lin_tol, P.maxit, gsz, it,
+                          B.pb, B.lq, B.ldinv, B.dx, B.dx + L.nflux, g, P.lin_tol, P.maxit, gsz, it,
                           rr0, rr))
       return;
     iters += it;
-    if (!grid_barrier(gs)) return;   // dx complete
+    if (!grid_barrier(g)) return;   // dx complete
     double s0 = 1.0;
     if (P.dp_clamp > 0.0) {
       double m = 0.0;
@@ -772,14 +767,14 @@ __global__ void __launch_bounds__(kPThreads) kp_coarse_step(LevelDev L, const T*
         for (int q = 0; q < L.m[c]; ++q) v = fma(L.w[po + q], __ldcg(&B.dx[L.nflux + po + q]), v);
         m = fmax(m, fabs(v));
       }
-      if (!grid_max(m, partial, gs.out + 28, gs, sm)) return;
+      if (!grid_max(g, m)) return;
       if (m > P.dp_clamp) s0 = P.dp_clamp / m;
     }
-    if (!coarse_backtrack_dev<T>(L, B, P, s0, rn, evals, partial, gs, sm)) return;
+    if (!coarse_backtrack_dev<T>(L, B, P, s0, rn, evals, g)) return;
     ++steps;
   }
   if (P.final_residual) {
-    if (!coarse_residual_dev(L, B.x, B.b, B.r, nullptr, B.kapc, B.yl, P.kind, P.a, partial, gs, sm, rn)) return;
+    if (!coarse_residual_dev(L, B.x, B.b, B.r, nullptr, B.kapc, B.yl, P.kind, P.a, g, rn)) return;
     ++evals;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {

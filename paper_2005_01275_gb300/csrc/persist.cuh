@@ -13,11 +13,12 @@ struct PcgResult {
   double rr;      // ||r_final||^2
 };
 
+// The persistent kernels' reductions use two buffers of kPartStride per-block partial sums (>= blocks x values).
+constexpr int kPartStride = 8192;
+
 struct GridSync {
-  unsigned* count;   // arrivals at the current barrier (0 at launch); own 128-byte line
-  unsigned* gen;     // barrier generation; own 128-byte line
+  unsigned* count;   // barrier arrival counter (0 at launch); own 128-byte line
   int* err;          // set when a wait gives up
-  double* out;       // 24 reduction results and step lengths published by the last block to arrive
   int sm_cap;        // host side: at most this many SMs for the launch (0 = all)
 };
 

@@ -500,7 +500,7 @@ void backtrack0(nlmg_ctx* c, const double* dp, double s0) {
 // lin_precision 0 runs it in FP64, 1 in FP32 (vectors and matrix; per-thread partial sums in FP32, block and grid
 // sums in FP64).
 int fine_pcg(nlmg_ctx* c, const double* R) {
-  GridSync gs{c->d_bar, c->d_bar + 32, &c->d_res->err, c->d_sc + 32, c->sm_cap};
+  GridSync gs{c->d_bar, &c->d_res->err, c->sm_cap};
   CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->st));
   CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
   launch_sdiag(c->st, c->F.N, c->diagT, c->sdiag);
@@ -746,7 +746,7 @@ int coarse_linear(nlmg_ctx* c, int l) {
   launch_axpy(c->st, nx, B.r, -2.0, B.r, B.nb);   // nb = -r
   const double* bs = B.nb;
   const double* bp = B.nb + L.nflux;
-  GridSync gs{c->d_bar, c->d_bar + 32, &c->d_res->err, c->d_sc + 32, c->sm_cap};
+  GridSync gs{c->d_bar, &c->d_res->err, c->sm_cap};
   CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->st));
   CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
   int pi = c->prof_begin(1);
@@ -815,7 +815,7 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
   P.tol_abs = c->tol_abs;
   P.final_residual = final_residual ? 1 : 0;
   P.maxit = c->opt.lin_maxit;
-  GridSync gs{c->d_bar, c->d_bar + 32, &c->d_res->err, c->d_sc + 32, c->sm_cap};
+  GridSync gs{c->d_bar, &c->d_res->err, c->sm_cap};
   CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->st));
   CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
   CoarseStepResult* dres = (CoarseStepResult*)(c->d_res + 1);
@@ -1085,7 +1085,7 @@ nlmg_status nlmg_setup_host(const nlmg_mesh* mesh, const nlmg_kappa* kappa, cons
 // read-back slots and every work buffer of the fine and coarse levels.
 static void init_work(nlmg_ctx* c) {
   CK(cudaMallocHost(&c->h_sc, 16 * sizeof(double)));
-  c->d_partial = c->dalloc<double>((size_t)kMaxBlocks * 4);
+  c->d_partial = c->dalloc<double>((size_t)2 * kPartStride);   // also the partials of the one-shot reductions
   c->d_cnt = c->dalloc<unsigned>(16);
   CK(cudaMemsetAsync(c->d_cnt, 0, 16 * sizeof(unsigned), c->st));
   c->d_sc = c->dalloc<double>(64);
