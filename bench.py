@@ -24,6 +24,11 @@ WORKLOAD = ("chan3d_64: 64^3 hexahedral TPFA, channelized K over 6 decades, kapp
 SAMPLE_SCALE = 16          # side of the bounded CPU sample of the same generator
 
 
+# DRAM bytes (read + write) of one launch of the default level-0 CG kernel on the 64^3 workload
+# (kp_fine_cg_reg<double, 4>), from an ncu --set full capture: valid for that kernel and workload only.
+FINE_CG_DRAM_BYTES_64 = 23.015680e6 + 91.648e3
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -369,11 +374,18 @@ def run_gpu(args, rank, world, local_rank):
     n_cg, ms_cg, by_cg, fl_cg = spmv
     avg_cg = ms_cg / max(n_cg, 1)
     fp64_peak_gflops = nlmg.measure_fp64_gflops()
-    roof = {"bound": "alu", "kernel": "kp_fine_cg<double> (persistent Jacobi-scaled CG of the level-0 Picard step)",
+    default_fine = args.scale == 64 and args.lin_tol is None
+    roof = {"bound": "alu",
+            "kernel": "kp_fine_cg_reg<double, 4> (persistent register-resident pipelined Jacobi-scaled CG of the "
+                      "level-0 Picard step)" if default_fine else "kp_fine_cg* (level-0 Picard CG)",
             "achieved": fl_cg / (avg_cg / 1e3) / 1e9 if n_cg else None, "peak": fp64_peak_gflops,
             "peak_kind": "measured FP64 FMA throughput (nlmg_measure_fp64, independent FMA chains)",
             "unit": "GFLOP/s",
-            "frac": (fl_cg / (avg_cg / 1e3) / 1e9) / fp64_peak_gflops if n_cg else None, "traffic": None,
+            "frac": (fl_cg / (avg_cg / 1e3) / 1e9) / fp64_peak_gflops if n_cg else None,
+            "traffic": FINE_CG_DRAM_BYTES_64 if default_fine else None,
+            "traffic_note": "DRAM read + write bytes of one launch from an ncu --set full capture of this kernel on "
+                            "this workload (first launch of a step, caches flushed by ncu): the CG iterations run "
+                            "from L2" if default_fine else None,
             "flops_per_launch": fl_cg, "bytes_per_launch": by_cg, "avg_launch_us": avg_cg * 1e3, "launches": n_cg,
             "memory_view": {"achieved_GBs": by_cg / (avg_cg / 1e3) / 1e9 if n_cg else None, "peak_GBs": peak,
                             "peak_kind": peak_kind,

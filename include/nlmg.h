@@ -76,6 +76,9 @@ typedef struct {
   double bt_theta;           /* Algorithm 1: theta (paper: 0.9) */
   double dp_clamp;           /* Sec. 4.1 pressure-change clamp; <= 0 disables */
   int32_t coarsest_steps;    /* Picard steps on the coarsest level (paper: <= 10) */
+  double coarsest_tol;       /* the coarsest level counts as converged once its residual is <= coarsest_tol times
+                                its value on entry (or <= the absolute tolerance of the solve); <= 0: the relative
+                                tolerance of the solve */
   double lin_tol;            /* relative tolerance of the level-0 CG solves inside Picard steps (default 1e-2) */
   int32_t lin_maxit;         /* iteration cap of the CG solves */
   double coarse_lin_tol;     /* relative tolerance of the coarse-level (hybridized) CG solves (default 1e-1) */

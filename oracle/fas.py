@@ -5,8 +5,9 @@ flux is the TPFA flux sigma(p) (eq. TPFA_flux), so the flux rows of the mixed fi
 residual is [0; -R(p)]. Coarse levels are mixed, with the operators of oracle.coarse.
 
 Algorithm 2, per level l (l = 0 finest):
-  coarsest: up to `coarsest_steps` Picard smoothing steps, stopping at the tolerances of the outer solve measured
-            against that level's initial residual;
+  coarsest: up to `coarsest_steps` Picard smoothing steps, stopping once that level's residual is below
+            `coarsest_tol` (default: the relative tolerance of the outer solve) times its initial value, or below
+            the absolute tolerance;
   otherwise: pre-smooth; x^{l+1} = Q x^l; b^{l+1} = A^{l+1}(x^{l+1}) - R (A^l(x^l) - b^l) with R = P^T
             (eq. coarse_level_residual); recurse; x^l = Backtracking(x^l, P (y^{l+1} - x^{l+1})); post-smooth.
 Smoothing on level 0 is, by default, one Picard step (Sec. 3.3.1): the frozen-coefficient system
@@ -127,8 +128,9 @@ class FAS:
         o = self.o
         r = float(np.linalg.norm(self.res(l, x, b)))
         r0 = r
+        rel = o.get("coarsest_tol", 0.0) or o["tol_rel"]
         for _ in range(o["coarsest_steps"]):
-            if r <= o["tol_rel"] * r0 or r <= o["tol_abs"]:
+            if r <= rel * r0 or r <= o["tol_abs"]:
                 break
             x, r = self.picard_smooth(l, x, b, r)
         return x

@@ -811,7 +811,7 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
   P.rn_in = B.rn;
   P.nsteps = nsteps;
   P.coarsest = coarsest ? 1 : 0;
-  P.tol_rel = c->tol_rel;
+  P.tol_rel = c->opt.coarsest_tol > 0.0 ? c->opt.coarsest_tol : c->tol_rel;
   P.tol_abs = c->tol_abs;
   P.final_residual = final_residual ? 1 : 0;
   P.maxit = c->opt.lin_maxit;
@@ -1062,6 +1062,7 @@ void nlmg_default_options(nlmg_options* o) {
   o->bt_theta = 0.9;
   o->dp_clamp = 0.0;
   o->coarsest_steps = 10;
+  o->coarsest_tol = 0.0;
   o->lin_tol = 1e-2;          // inner solves of the Picard smoothing steps: loose, the outer iteration corrects them
   o->lin_maxit = 5000;
   o->coarse_lin_tol = 1e-1;

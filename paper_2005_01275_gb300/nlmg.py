@@ -35,7 +35,8 @@ class Options(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("agg_size", C.c_int32 * 8), ("modes", C.c_int32 * 8),
                 ("smoother", C.c_int32), ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("omega", C.c_double),
                 ("bt_nmax", C.c_int32), ("bt_theta", C.c_double), ("dp_clamp", C.c_double),
-                ("coarsest_steps", C.c_int32), ("lin_tol", C.c_double), ("lin_maxit", C.c_int32),
+                ("coarsest_steps", C.c_int32), ("coarsest_tol", C.c_double), ("lin_tol", C.c_double),
+                ("lin_maxit", C.c_int32),
                 ("coarse_lin_tol", C.c_double), ("lin_precision", C.c_int32),
                 ("setup_threads", C.c_int32), ("max_sms", C.c_int32), ("reserved", C.c_int32 * 5)]
 
@@ -158,7 +159,7 @@ def default_options(**kw):
 def options_from_dict(d):
     """Options from the dictionary used by the synthetic problem configurations."""
     keep = {k: d[k] for k in ("n_levels", "agg_size", "modes", "nu_pre", "nu_post", "omega", "bt_nmax", "bt_theta",
-                              "dp_clamp", "coarsest_steps", "lin_tol", "lin_maxit", "coarse_lin_tol",
+                              "dp_clamp", "coarsest_steps", "coarsest_tol", "lin_tol", "lin_maxit", "coarse_lin_tol",
                               "lin_precision", "max_sms") if k in d}
     if "lin_tol" in d and "coarse_lin_tol" not in d:
         keep["coarse_lin_tol"] = d["lin_tol"]       # one tolerance given: use it on every level
