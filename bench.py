@@ -285,6 +285,22 @@ def run_reference(args, rank):
     return 0
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest of the ranks' values of x (the slowest replica sets the job's time); x itself without
+    torch.distributed."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, steps, max_ms):
+    """Whole-job solves/s of `world` independent replicas that each ran `steps` solves, the slowest in max_ms."""
+    return world * steps / (max_ms / 1e3)
+
+
 def run_gpu(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -341,11 +357,7 @@ def run_gpu(args, rank, world, local_rank):
     upd = ctx.profile_read(1)
     res = ctx.profile_read(2)
     ctx.profile(False)
-    dev_ms = sum(r["solve_ms"] for r in reps)
-    if dist is not None:
-        t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = float(t.item())
+    dev_ms = max_over_ranks(sum(r["solve_ms"] for r in reps), dist, dev)
     # end to end through the host-pointer C-ABI call: H2D of f and g from pinned memory, D2H of p
     f_h = torch.from_numpy(pr.f_cell).pin_memory()
     g_h = torch.from_numpy(pr.g_face).pin_memory()
@@ -359,18 +371,14 @@ def run_gpu(args, rank, world, local_rank):
         e2e_t.append(time.perf_counter() - t1)
         if st != nlmg.OK:
             raise RuntimeError("e2e solve failed %d" % st)
-    e2e_s = sum(e2e_t)
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(sum(e2e_t), dist, dev)
     if rank != 0:
         dist.destroy_process_group()
         return 0
     peak, peak_kind = _peaks()
     ms_step = dev_ms / args.steps
     cycles = sum(r["cycles"] for r in reps) / len(reps)
-    value = world * args.steps / (dev_ms / 1e3)
+    value = replica_throughput(world, args.steps, dev_ms)
     n_cg, ms_cg, by_cg, fl_cg = spmv
     avg_cg = ms_cg / max(n_cg, 1)
     fp64_peak_gflops = nlmg.measure_fp64_gflops()
