@@ -108,6 +108,8 @@ typedef struct {
 
 typedef struct {
   int32_t n_cells, n_flux, n_p, n_lambda;
+  int32_t eig_host;   /* level >= 1: local eigenproblems of its coarsening solved on the host although a batched GPU
+                         solve was used (the GPU result of that matrix was not finite) */
 } nlmg_level_info;
 
 /* Fills *opt with the paper's constants (n_max = 4, theta = 0.9, <= 10 coarsest steps) and library defaults. */
@@ -286,6 +288,8 @@ nlmg_status nlmg_fine_residual_noalloc(nlmg_ctx* ctx, const double* p_dev, doubl
  * kernel of independent FMA chains; the denominator of the FP64-arithmetic roofline. */
 nlmg_status nlmg_measure_fp64(double* gflops);
 
+/* The message of the context's last failed call; with ctx = NULL, that of the calling thread's last failed
+ * nlmg_setup / nlmg_setup_host (whose context was freed). */
 const char* nlmg_last_error(const nlmg_ctx* ctx);
 void nlmg_destroy(nlmg_ctx* ctx);
 

@@ -53,6 +53,7 @@ struct Transfer {
   Csr PsT;                                   // P_sigma^T, rows = coarse flux unknowns
   Csr Qs;                                    // Q_sigma, rows = coarse flux unknowns
   std::vector<double> eig_gap;               // lambda_{m+1} - lambda_m per aggregate (diagnostic)
+  int eig_host = 0;                          // GPU eigensolves redone on the host (non-finite GPU result)
 };
 
 // Batched eigensolver callback (nmat, aoff, n, k, A_all, vals, voff, vecs, err); vals has kEigStride per matrix.

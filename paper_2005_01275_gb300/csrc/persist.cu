@@ -22,6 +22,8 @@ namespace {
 
 constexpr unsigned long long kSpinLimit = 1ull << 26;   // x ~32 ns sleeps ~ 2 s
 constexpr int kPThreads = 512;                           // threads per block of the persistent kernels
+constexpr int kMaxNV = 4;                                // values per block reduction at most
+constexpr int kSmDoubles = kMaxNV * 32;                  // block-reduction scratch: 32 warp sums per value
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
@@ -36,8 +38,8 @@ __device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v
 }
 
 // The synchronisation state one thread of a persistent kernel carries: the launch's barrier words, the two
-// buffers of per-block partial sums (used alternately by consecutive reductions), 64 doubles of shared memory and
-// the number of reductions so far (the same in every block).
+// buffers of per-block partial sums (used alternately by consecutive reductions), kSmDoubles doubles of shared
+// memory and the number of reductions so far (the same in every block).
 struct Grid {
   GridSync gs;
   double* partial;
@@ -73,6 +75,8 @@ __device__ __forceinline__ bool grid_barrier(Grid& g) {
 
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
+  static_assert(NV >= 1 && NV <= kMaxNV, "block_sum: sm holds kMaxNV x 32 values");
+  static_assert(kPThreads / 32 <= 32, "block_sum: at most 32 warps");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k)
@@ -192,7 +196,7 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg(FineDev F, const T* __re
                                                         T* __restrict__ r, T* __restrict__ p, T* __restrict__ q,
                                                         double* partial, GridSync gs, double tol, int maxit,
                                                         PcgResult* res) {
-  __shared__ double sm[2 * 32];
+  __shared__ double sm[kSmDoubles];
   Grid g{gs, partial, sm, 0u};
   T t1 = (T)0;   // per-thread partial sums in T (a thread holds one or two cells), block and grid sums in FP64
   GSTRIDE(i, F.N) {
@@ -304,7 +308,7 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg_pipe(FineDev F, const T*
                                                              T* __restrict__ r, T* wa, T* wb, T* __restrict__ z,
                                                              T* __restrict__ sv, T* __restrict__ p, double* partial,
                                                              GridSync gs, double tol, int maxit, PcgResult* res) {
-  __shared__ double sm[2 * 32];
+  __shared__ double sm[kSmDoubles];
   Grid g{gs, partial, sm, 0u};
   GSTRIDE(i, F.N) {
     r[i] = (T)(sdiag[i] * bscale * b[i]);
@@ -390,7 +394,7 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg_reg(FineDev F, const TM*
                                                             double* __restrict__ dx, TM* wa, TM* wb,
                                                             double* partial, GridSync gs, double tol, int maxit,
                                                             PcgResult* res) {
-  __shared__ double sm[2 * 32];
+  __shared__ double sm[kSmDoubles];
   Grid g{gs, partial, sm, 0u};
   const int stride = gridDim.x * blockDim.x;
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -475,15 +479,145 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg_reg(FineDev F, const TM*
   }
 }
 
+// (H v)_l for the lambdas of a warp-uniform group loop: a group of gsz lanes per lambda reads the two H rows of
+// lambda_l (one per interface slot k, scaled by kappa of the slot's cell) with stride gsz and adds up by shuffles;
+// v(lambda_j) is gathered through L2. Every lane returns the group sum.
+template <class T>
+__device__ __forceinline__ T hyb_row_product(const LevelDev& L, const T* __restrict__ Hc, const double* kapc,
+                                             const T* v, int l, int g, int gsz, bool act) {
+  T h = (T)0;
+  if (act) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int k = side == 0 ? L.lam_y0[l] : L.lam_y1[l];
+      const int c = L.if_cell[k];
+      const int k0 = L.if_off[c], ni = L.if_off[c + 1] - k0;
+      const T* Hk = Hc + L.hc_off[c] + (size_t)(k - k0) * ni;
+      const int* lk = L.if_lam + k0;
+      T y = 0;
+      for (int j = g; j < ni; j += gsz) y += Hk[j] * __ldcg(&v[lk[j]]);
+      h += (T)__ldcg(&kapc[c]) * y;
+    }
+  }
+  for (int off = gsz >> 1; off > 0; off >>= 1) h += __shfl_xor_sync(0xffffffffu, h, off);
+  return h;
+}
+
+// Pipelined (Ghysels-Vanroose) Jacobi-preconditioned CG on H lambda = xi, one grid synchronisation per iteration.
+// On entry lam = 0, r = xi, u = M r (M = diag(H)^-1) and rr0 = (r, r). State per lambda: lam, r, u, w = H u,
+// z = H q, q = M s, s = H p, p; the vector m = M w, which the product n = H m gathers, is published
+// double-buffered. Per iteration: n = H m; z = n + beta z; q = m + beta q; s = w + beta s; p = u + beta p;
+// lam += alpha p; r -= alpha s; u -= alpha q; w -= alpha z; then gamma = (r, u), delta = (w, u), (r, r) in one
+// reduction, from which the last step derives the next beta and alpha.
+template <class T>
+__device__ bool hyb_pipe_loop(const LevelDev& L, const T* __restrict__ Hc, const double* kapc, T* lam, T* lr, T* lu,
+                              T* pp, T* lq, T* ldinv, const HybPipeBufs<T>& P, Grid& g, int gsz, double tol2,
+                              double rr0, int maxit, int& it_out, double& rr_out) {
+  const long total = (long)L.nlam * gsz;
+  const int lane = threadIdx.x & 31;
+  const long stride = (long)gridDim.x * blockDim.x;
+  // w = H u, m = M w, and the first reduction
+  double d3[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  {
+    T a0 = (T)0, a1 = (T)0, a2 = (T)0;
+    for (long tb = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); tb < total; tb += stride) {
+      const long t = tb + lane;
+      const bool act = t < total;
+      const int l = act ? (int)(t / gsz) : 0;
+      const int gi = lane & (gsz - 1);
+      const T w = hyb_row_product<T>(L, Hc, kapc, lu, l, gi, gsz, act);
+      if (act && gi == 0) {
+        const T r = lr[l], u = lu[l];
+        P.w[l] = w;
+        P.ma[l] = ldinv[l] * w;
+        P.z[l] = (T)0;
+        P.s[l] = (T)0;
+        lq[l] = (T)0;
+        pp[l] = (T)0;
+        a0 = fma(r, u, a0);
+        a1 = fma(w, u, a1);
+        a2 = fma(r, r, a2);
+      }
+    }
+    d3[0] = (double)a0;
+    d3[1] = (double)a1;
+    d3[2] = (double)a2;
+  }
+  if (!grid_sum_x<3, 2>(g, d3, [&](double* o) {
+        o[3] = 0.0;
+        o[4] = o[1] != 0.0 ? o[0] / o[1] : 0.0;
+      }))
+    return false;
+  double gamma = d3[0], rr = d3[2], beta = d3[3], alpha = d3[4];
+  T* mc = P.ma;   // published m of the current iteration
+  T* mn = P.mb;
+  int it = 0;
+  while (rr0 > 0.0 && rr > tol2 && it < maxit) {
+    if (!(alpha != 0.0)) break;
+    const T a = (T)alpha, b = (T)beta;
+    T a0 = (T)0, a1 = (T)0, a2 = (T)0;
+    for (long tb = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); tb < total; tb += stride) {
+      const long t = tb + lane;
+      const bool act = t < total;
+      const int l = act ? (int)(t / gsz) : 0;
+      const int gi = lane & (gsz - 1);
+      const T n = hyb_row_product<T>(L, Hc, kapc, mc, l, gi, gsz, act);
+      if (act && gi == 0) {
+        const T w = P.w[l], m = ldinv[l] * w;
+        const T z = n + b * P.z[l];
+        const T q = m + b * lq[l];
+        const T sv = w + b * P.s[l];
+        const T p = lu[l] + b * pp[l];
+        P.z[l] = z;
+        lq[l] = q;
+        P.s[l] = sv;
+        pp[l] = p;
+        lam[l] = lam[l] + a * p;
+        const T r = lr[l] - a * sv;
+        const T u = lu[l] - a * q;
+        const T wn = w - a * z;
+        lr[l] = r;
+        lu[l] = u;
+        P.w[l] = wn;
+        mn[l] = ldinv[l] * wn;
+        a0 = fma(r, u, a0);
+        a1 = fma(wn, u, a1);
+        a2 = fma(r, r, a2);
+      }
+    }
+    double n5[5] = {(double)a0, (double)a1, (double)a2, 0.0, 0.0};
+    if (!grid_sum_x<3, 2>(g, n5, [&](double* o) {
+          const double gn = o[0], dn = o[1];
+          const double bn = gamma != 0.0 ? gn / gamma : 0.0;
+          const double den = dn - bn * gn / alpha;
+          o[3] = bn;
+          o[4] = den != 0.0 ? gn / den : 0.0;
+        }))
+      return false;
+    gamma = n5[0];
+    rr = n5[2];
+    beta = n5[3];
+    alpha = n5[4];
+    T* tmp = mc;
+    mc = mn;
+    mn = tmp;
+    ++it;
+  }
+  it_out = it;
+  rr_out = rr;
+  return true;
+}
+
 // ---- coarse level: hybridized saddle solve (rhs, Jacobi diagonal, CG on H lambda = xi, local recovery) ------
-// The solve of one frozen-coefficient coarse saddle as a device function of a persistent grid (sm: 64 doubles of
+// The solve of one frozen-coefficient coarse saddle as a device function of a persistent grid (g.sm: kSmDoubles of
 // shared memory). kapc, bs and bp may have been written earlier in the same launch, so they are read through L2.
 // Returns false if a grid barrier gave up; `iters` and `rr_out` receive the CG iterations and final (r, r).
 template <class T>
 __device__ bool hyb_solve_dev(const LevelDev& L, const T* __restrict__ Hc, const T* __restrict__ Sinv,
                               const double* kapc, const double* bs, const double* bp, T* ylam, T* ydiag, T* lam,
                               T* lr, T* lz, T* pa, T* pb, T* lq, T* ldinv, double* dsig, double* dp, Grid& g,
-                              double tol, int maxit, int gsz, int& iters, double& rr0_out, double& rr_out) {
+                              double tol, int maxit, int gsz, int& iters, double& rr0_out, double& rr_out,
+                              const HybPipeBufs<T>* pipe = nullptr) {
   // phase 0: per interface slot k of cell c, u_k = kappa A[k,:] bhat + B[k,:] b_p (signed) and kappa Hc[k,k]
   GSTRIDE(k, L.nif) {
     const int c = L.if_cell[k];
@@ -521,7 +655,11 @@ __device__ bool hyb_solve_dev(const LevelDev& L, const T* __restrict__ Hc, const
   T beta = (T)0;
   T* pp = pa;       // search direction p
   int it = 0;
-  while (rr0 > 0.0 && rr > tol2 && it < maxit) {
+  if (pipe) {
+    if (!hyb_pipe_loop<T>(L, Hc, kapc, lam, lr, lz, pp, lq, ldinv, *pipe, g, gsz, tol2, rr0, maxit, it, rr))
+      return false;
+  }
+  while (!pipe && rr0 > 0.0 && rr > tol2 && it < maxit) {
     // (H z)_l = sum over the two interface slots k of lambda_l of kappa_c Hc[k, :] z(lambda of c's slots): a group
     // of gsz lanes per lambda (gsz a power of two <= 32, chosen so that small coarse levels still occupy every SM)
     // reads both rows with stride gsz and adds up by shuffles, so H z needs no intermediate buffer and no extra
@@ -626,7 +764,7 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
                                                          T* lam, T* lr, T* lz, T* pa, T* pb, T* lq, T* ldinv,
                                                          double* dsig, double* dp, double* partial, GridSync gs,
                                                          double tol, int maxit, int gsz, PcgResult* res) {
-  __shared__ double sm[2 * 32];
+  __shared__ double sm[kSmDoubles];
   Grid g{gs, partial, sm, 0u};
   int it = 0;
   double rr0 = 0.0, rr = 0.0;
@@ -641,52 +779,80 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
 }
 
 // ---- fused coarse Picard step -------------------------------------------------------------------------------
-// r = A^l(x) - b on a coarse level (Prop. 1, eq. structure): kapc = kappa(w_c . p_c) per cell, yl = per-cell
-// local flux products s Mloc sigma + Dloc^T p, r_p = Dloc sigma - b_p, r_sigma = sum of the owners' yl - b_sigma;
-// nb = -r if given. x and b may have been written earlier in the launch (read through L2). The caller has put a
-// grid barrier after the last write of x. Returns ||r|| in rn.
-__device__ bool coarse_residual_dev(const LevelDev& L, const double* x, const double* b, double* r, double* nb,
-                                    double* kapc, double* yl, int kind, double a, Grid& g, double& rn) {
-  const double* xs = x;
-  const double* xp = x + L.nflux;
+// r = A^l(x) - b on a coarse level (Prop. 1, eq. structure), in two passes and two grid synchronisations:
+// (1) kappa_c = kappa(w_c . p_c) per cell; with dx given, the point is the trial x = x0 + alpha dx, formed in the
+//     same pass (x written, then used);
+// (2) per flux unknown, r_sigma = sum over its (one or two) owner slots of s_c Mloc_c[u, :] sigma_c + Dloc_c[:, u]^T
+//     p_c, minus b_sigma (one lane per slot, the two lanes of a flux unknown adjacent); per pressure unknown,
+//     r_p = Dloc_c[r, :] sigma_c - b_p; and ||r||^2.
+// nb = -r if given. Inputs written earlier in the launch are read through L2; the caller has put a grid barrier
+// after the last write of x0 (and dx).
+__device__ bool coarse_residual_dev(const LevelDev& L, double* x, const double* x0, const double* dx, double alpha,
+                                    const double* b, double* r, double* nb, double* kapc, int kind, double a,
+                                    Grid& g, double& rn) {
+  double* xs = x;
+  double* xp = x + L.nflux;
+  if (dx) {
+    GSTRIDE(i, L.nflux) xs[i] = fma(alpha, __ldcg(&dx[i]), __ldcg(&x0[i]));
+  }
   GSTRIDE(c, L.nc) {
     const int po = L.p_off[c];
     double pb = 0.0;
-    for (int q = 0; q < L.m[c]; ++q) pb = fma(L.w[po + q], __ldcg(&xp[po + q]), pb);
+    for (int q = 0; q < L.m[c]; ++q) {
+      double pq;
+      if (dx) {
+        pq = fma(alpha, __ldcg(&dx[L.nflux + po + q]), __ldcg(&x0[L.nflux + po + q]));
+        xp[po + q] = pq;
+      } else {
+        pq = __ldcg(&xp[po + q]);
+      }
+      pb = fma(L.w[po + q], pq, pb);
+    }
     kapc[c] = kappa_of(pb, kind, a);
   }
   if (!grid_barrier(g)) return false;
   double acc = 0.0;
-  GSTRIDE(y, L.nyl) {
-    const int c = L.slot_cell[y];
-    const int mc = L.m[c], lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c];
-    const int u = y - lo;
-    const double* Mu = L.Mloc + L.mat_off[c] + (size_t)u * nl;
-    const double* D = L.Dloc + L.dmat_off[c];
-    double v = 0.0;
-    for (int t = 0; t < nl; ++t) v = fma(Mu[t], __ldcg(&xs[L.loc[lo + t]]), v);
-    v /= __ldcg(&kapc[c]);
-    for (int q = 0; q < mc; ++q) v = fma(D[q * nl + u], __ldcg(&xp[po + q]), v);
-    yl[y] = v;
+  {
+    // one lane per (flux unknown, owner slot) pair, the pair on adjacent lanes of a warp: each lane computes its
+    // slot's product, a shuffle adds the pair (warp-uniform loop so that every lane takes part)
+    const long total = 2L * L.nflux;
+    const int lane = threadIdx.x & 31;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long tb = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); tb < total; tb += stride) {
+      const long t = tb + lane;
+      const bool act = t < total;
+      const int i = act ? (int)(t >> 1) : 0;
+      const int y = act ? ((t & 1) ? L.f_y1[i] : L.f_y0[i]) : -1;
+      double v = 0.0;
+      if (y >= 0) {
+        const int c = L.slot_cell[y];
+        const int mc = L.m[c], lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c];
+        const int u = y - lo;
+        const double* Mu = L.Mloc + L.mat_off[c] + (size_t)u * nl;
+        const double* D = L.Dloc + L.dmat_off[c];
+        for (int k = 0; k < nl; ++k) v = fma(Mu[k], __ldcg(&xs[L.loc[lo + k]]), v);
+        v /= __ldcg(&kapc[c]);
+        for (int q = 0; q < mc; ++q) v = fma(D[q * nl + u], __ldcg(&xp[po + q]), v);
+      }
+      const double other = __shfl_xor_sync(0xffffffffu, v, 1);
+      if (act && (t & 1) == 0) {
+        double vv = v + other;
+        if (b) vv -= __ldcg(&b[i]);
+        r[i] = vv;
+        if (nb) nb[i] = -vv;
+        acc = fma(vv, vv, acc);
+      }
+    }
   }
   GSTRIDE(i, L.np) {
     const int c = L.p_cell[i];
     const int lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c];
     const double* Dr = L.Dloc + L.dmat_off[c] + (size_t)(i - po) * nl;
     double v = 0.0;
-    for (int t = 0; t < nl; ++t) v = fma(Dr[t], __ldcg(&xs[L.loc[lo + t]]), v);
+    for (int k = 0; k < nl; ++k) v = fma(Dr[k], __ldcg(&xs[L.loc[lo + k]]), v);
     if (b) v -= __ldcg(&b[L.nflux + i]);
     r[L.nflux + i] = v;
     if (nb) nb[L.nflux + i] = -v;
-    acc = fma(v, v, acc);
-  }
-  if (!grid_barrier(g)) return false;
-  GSTRIDE(i, L.nflux) {
-    double v = __ldcg(&yl[L.f_y0[i]]);
-    if (L.f_y1[i] >= 0) v += __ldcg(&yl[L.f_y1[i]]);
-    if (b) v -= __ldcg(&b[i]);
-    r[i] = v;
-    if (nb) nb[i] = -v;
     acc = fma(v, v, acc);
   }
   double s1[1] = {acc};
@@ -696,67 +862,73 @@ __device__ bool coarse_residual_dev(const LevelDev& L, const double* x, const do
 }
 
 // Algorithm 1 on a coarse level along dx from step s0: trial x + s s0 dx, halving s while the half step is no worse
-// than theta times the current trial (at most bt_nmax times) as long as the trial is worse than ||r(x)||; x takes
-// the last trial and rn its residual norm.
+// than theta times the current trial (at most bt_nmax times) as long as the trial is worse than ||r(x)||; the
+// accepted trial becomes the iterate and rn its residual norm. The three buffers xb[0..2] rotate: xb[*cur] is the
+// iterate, the trials go to the other two, so no copy is needed.
 template <class T>
 __device__ bool coarse_backtrack_dev(const LevelDev& L, const CoarseStepBufs<T>& B, const CoarseStepParams& P,
-                                     double s0, double& rn, int& evals, Grid& g) {
-  const int nx = L.nflux + L.np;
-  double* t1 = B.xt1;
-  double* t2 = B.xt2;
+                                     double* const* xb, int& cur, double s0, double& rn, int& evals, Grid& g) {
+  int t1 = (cur + 1) % 3, t2 = (cur + 2) % 3;
   double s = 1.0;
-  GSTRIDE(i, nx) t1[i] = fma(s * s0, __ldcg(&B.dx[i]), __ldcg(&B.x[i]));
-  if (!grid_barrier(g)) return false;
   double r_s = 0.0;
-  if (!coarse_residual_dev(L, t1, B.b, B.rt, nullptr, B.kapc, B.yl, P.kind, P.a, g, r_s)) return false;
+  if (!coarse_residual_dev(L, xb[t1], xb[cur], B.dx, s * s0, B.b, B.rt, nullptr, B.kapc, P.kind, P.a, g, r_s))
+    return false;
   ++evals;
   int n = 0;
   while (r_s > rn && n < P.bt_nmax) {
-    GSTRIDE(i, nx) t2[i] = fma(0.5 * s * s0, __ldcg(&B.dx[i]), __ldcg(&B.x[i]));
-    if (!grid_barrier(g)) return false;
     double r_half = 0.0;
-    if (!coarse_residual_dev(L, t2, B.b, B.rt, nullptr, B.kapc, B.yl, P.kind, P.a, g, r_half))
+    if (!coarse_residual_dev(L, xb[t2], xb[cur], B.dx, 0.5 * s * s0, B.b, B.rt, nullptr, B.kapc, P.kind, P.a, g,
+                             r_half))
       return false;
     ++evals;
     if (r_half > P.bt_theta * r_s) break;
     s *= 0.5;
     ++n;
     r_s = r_half;
-    double* t = t1;
+    const int t = t1;
     t1 = t2;
     t2 = t;
   }
-  GSTRIDE(i, nx) B.x[i] = __ldcg(&t1[i]);
-  if (!grid_barrier(g)) return false;
+  cur = t1;
   rn = r_s;
   return true;
 }
 
 template <class T>
-__global__ void __launch_bounds__(kPThreads) kp_coarse_step(LevelDev L, const T* __restrict__ Hc,
+__global__ void __launch_bounds__(kPThreads, 1) kp_coarse_step(LevelDev L, const T* __restrict__ Hc,
                                                            const T* __restrict__ Sinv, CoarseStepBufs<T> B,
                                                            CoarseStepParams P, double* partial, GridSync gs,
                                                            int gsz, CoarseStepResult* res) {
-  __shared__ double sm[2 * 32];
+  __shared__ double sm[kSmDoubles];
   Grid g{gs, partial, sm, 0u};
-  int iters = 0, steps = 0, evals = 0;
+  double* const xb[3] = {B.x, B.xt1, B.xt2};
+  int cur = 0;
+  int iters = 0, steps = 0, evals = 0, bad = 0;
   double rn = P.rn_in;
   if (P.backtrack_first) {
-    if (!coarse_backtrack_dev<T>(L, B, P, 1.0, rn, evals, g)) return;
+    if (!coarse_backtrack_dev<T>(L, B, P, xb, cur, 1.0, rn, evals, g)) return;
   }
   double r0 = 0.0;
   for (int k = 0; k < P.nsteps; ++k) {
-    if (!coarse_residual_dev(L, B.x, B.b, B.r, B.nb, B.kapc, B.yl, P.kind, P.a, g, rn)) return;
+    if (!coarse_residual_dev(L, xb[cur], nullptr, nullptr, 0.0, B.b, B.r, B.nb, B.kapc, P.kind, P.a, g, rn)) return;
     ++evals;
+    if (!isfinite(rn)) {
+      bad = 1;
+      break;
+    }
     if (k == 0) r0 = rn;
     if (P.coarsest && (rn <= P.tol_rel * r0 || rn <= P.tol_abs)) break;
     int it = 0;
     double rr0 = 0.0, rr = 0.0;
     if (!hyb_solve_dev<T>(L, Hc, Sinv, B.kapc, B.nb, B.nb + L.nflux, B.ylam, B.ydiag, B.lam, B.lr, B.lz, B.pa,
-                          B.pb, B.lq, B.ldinv, B.dx, B.dx + L.nflux, g, P.lin_tol, P.maxit, gsz, it,
-                          rr0, rr))
+                          B.pb, B.lq, B.ldinv, B.dx, B.dx + L.nflux, g, P.lin_tol, P.maxit, gsz, it, rr0, rr,
+                          B.pipe.w ? &B.pipe : nullptr))
       return;
     iters += it;
+    if (!isfinite(rr)) {
+      bad = 2;
+      break;
+    }
     if (!grid_barrier(g)) return;   // dx complete
     double s0 = 1.0;
     if (P.dp_clamp > 0.0) {
@@ -770,18 +942,26 @@ __global__ void __launch_bounds__(kPThreads) kp_coarse_step(LevelDev L, const T*
       if (!grid_max(g, m)) return;
       if (m > P.dp_clamp) s0 = P.dp_clamp / m;
     }
-    if (!coarse_backtrack_dev<T>(L, B, P, s0, rn, evals, g)) return;
+    if (!coarse_backtrack_dev<T>(L, B, P, xb, cur, s0, rn, evals, g)) return;
     ++steps;
   }
   if (P.final_residual) {
-    if (!coarse_residual_dev(L, B.x, B.b, B.r, nullptr, B.kapc, B.yl, P.kind, P.a, g, rn)) return;
+    if (!coarse_residual_dev(L, xb[cur], nullptr, nullptr, 0.0, B.b, B.r, nullptr, B.kapc, P.kind, P.a, g, rn))
+      return;
     ++evals;
+  }
+  if (cur != 0) {
+    // the iterate ends in a trial buffer: copy it to x (every block has passed the last reduction, after which
+    // nothing reads it)
+    const int nx = L.nflux + L.np;
+    GSTRIDE(i, nx) B.x[i] = __ldcg(&xb[cur][i]);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     res->rn = rn;
     res->iters = iters;
     res->steps = steps;
     res->res_evals = evals;
+    res->bad = bad;
   }
 }
 

@@ -39,12 +39,19 @@ cudaError_t launch_fine_cg_reg(cudaStream_t st, const FineDev& F, const TM* Ts, 
                                double bscale, double* dx, TM* wa, TM* wb, double* partial, GridSync gs, double tol,
                                int maxit, PcgResult* res);
 
+// Extra per-lambda vectors of the pipelined hybridized CG (w = H u, z, s, and m = M w double-buffered).
+template <class T>
+struct HybPipeBufs {
+  T *w = nullptr, *z = nullptr, *s = nullptr, *ma = nullptr, *mb = nullptr;
+};
+
 // Device buffers of one coarse level used by the fused Picard step (all of length nflux + np unless noted).
 template <class T>
 struct CoarseStepBufs {
   double *x, *b, *r, *nb, *dx, *xt1, *xt2, *rt;   // iterate, rhs, residual, -residual, step, trials, trial residual
-  double *kapc, *yl;                              // kappa per cell (nc), per-cell local flux products (nyl)
+  double* kapc;                                   // kappa per cell (nc)
   T *ylam, *ydiag, *lam, *lr, *lz, *pa, *pb, *lq, *ldinv;   // hybridized CG (nif / nlam)
+  HybPipeBufs<T> pipe;   // set: pipelined hybridized CG (one grid synchronisation per iteration)
 };
 
 struct CoarseStepParams {
@@ -68,7 +75,7 @@ struct CoarseStepResult {
   int iters;        // hybridized CG iterations
   int steps;        // Picard steps taken
   int res_evals;    // coarse operator evaluations
-  int err;
+  int bad;          // 0, or where a non-finite value appeared: 1 residual, 2 hybridized CG
 };
 
 // One launch: [Algorithm 1 along a given correction], up to nsteps coarse Picard steps (residual, frozen-kappa

@@ -449,15 +449,24 @@ static bool coarsen(const Level& L, int target, int modes, int threads, bool use
       return false;
     }
   }
+  std::atomic<int> n_eig_host(0);
   parallel_for(na, threads, [&](int b, int e, int) {
     for (int a = b; a < e; ++a) {
       const int npA = np_of(a);
       const int m = kS[a];
       std::vector<double> vecs;
-      if (done_gpu) {
+      bool gpu_ok = done_gpu && std::isfinite(evals_m[a]) && std::isfinite(evals_next[a]);
+      if (gpu_ok)
+        for (double v : evecs[a])
+          if (!std::isfinite(v)) {
+            gpu_ok = false;
+            break;
+          }
+      if (gpu_ok) {
         vecs.swap(evecs[a]);
         T.eig_gap[a] = evals_next[a] - evals_m[a];
-      } else {
+      } else {   // host path, also for a matrix whose batched GPU solve returned a non-finite value
+        if (done_gpu) ++n_eig_host;
         std::vector<double> vals;
         double nextv = 0.0;
         sym_eig_smallest(nS[a], Smat[a], m, vals, vecs, &nextv);
@@ -512,6 +521,7 @@ static bool coarsen(const Level& L, int target, int modes, int threads, bool use
     }
   });
   if (fail) { err = "local flux mass matrix not SPD in an eigenproblem"; return false; }
+  T.eig_host = n_eig_host.load();
   T.pblk_off.assign(na + 1, 0);
   for (int a = 0; a < na; ++a) T.pblk_off[a + 1] = T.pblk_off[a] + (int)PA[a].size();
   T.Pblk.resize(T.pblk_off[na]);
@@ -814,6 +824,32 @@ static bool coarsen(const Level& L, int target, int modes, int threads, bool use
   return true;
 }
 
+// Every stored value of the hierarchy must be finite; returns false with the level and array otherwise.
+static bool check_finite(const Hierarchy& H, std::string& err) {
+  auto bad = [](const std::vector<double>& v) {
+    for (double x : v)
+      if (!std::isfinite(x)) return true;
+    return false;
+  };
+  for (size_t l = 0; l < H.levels.size(); ++l) {
+    const Level& L = H.levels[l];
+    const char* what = bad(L.Mloc) ? "Mloc" : bad(L.Dloc) ? "Dloc" : bad(L.w) ? "Pi~ weights" : nullptr;
+    if (what) {
+      err = "non-finite value in the hierarchy: level " + std::to_string(l) + " " + what;
+      return false;
+    }
+  }
+  for (size_t l = 0; l < H.transfers.size(); ++l) {
+    const Transfer& T = H.transfers[l];
+    const char* what = bad(T.Pblk) ? "P_p" : bad(T.Ps.val) ? "P_sigma" : bad(T.Qs.val) ? "Q_sigma" : nullptr;
+    if (what) {
+      err = "non-finite value in the hierarchy: transfer " + std::to_string(l) + " " + what;
+      return false;
+    }
+  }
+  return true;
+}
+
 bool build_hierarchy(const FineMesh& fm, const Options& opt, Hierarchy& H, std::string& err) {
   int threads = opt.threads > 0 ? opt.threads : (int)std::max(1u, std::thread::hardware_concurrency());
   H.levels.clear();
@@ -827,7 +863,7 @@ bool build_hierarchy(const FineMesh& fm, const Options& opt, Hierarchy& H, std::
     H.levels.push_back(std::move(C));
     H.transfers.push_back(std::move(T));
   }
-  return true;
+  return check_finite(H, err);
 }
 
 }  // namespace nlmg

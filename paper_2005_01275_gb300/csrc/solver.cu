@@ -45,6 +45,7 @@ struct CoarseBuf {
   double *xc = nullptr, *yl = nullptr, *kapc = nullptr, *ptmp = nullptr, *rt = nullptr;
   double *ylam = nullptr, *ydiag = nullptr, *lam = nullptr, *lr = nullptr, *lz = nullptr, *lpa = nullptr, *lpb = nullptr,
          *lq = nullptr, *ldinv = nullptr, *xi = nullptr;
+  double *hw = nullptr, *hz = nullptr, *hs = nullptr, *hma = nullptr, *hmb = nullptr;   // pipelined hybridized CG
   float *f_ylam = nullptr, *f_ydiag = nullptr, *f_lam = nullptr, *f_lr = nullptr, *f_lz = nullptr,
         *f_lpa = nullptr, *f_lpb = nullptr, *f_lq = nullptr, *f_ldinv = nullptr;
   double rn = 0.0;  // ||A(x) - b|| at the current x (valid after coarse_res)
@@ -420,6 +421,7 @@ void alloc_level(nlmg_ctx* c, int l) {
   B.lq = c->dalloc<double>(nlam);
   B.ldinv = c->dalloc<double>(nlam);
   B.xi = c->dalloc<double>(nlam);
+  for (double** pp : {&B.hw, &B.hz, &B.hs, &B.hma, &B.hmb}) *pp = c->dalloc<double>(nlam);
 }
 
 void upload_transfer(nlmg_ctx* c, int l) {
@@ -544,6 +546,7 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
   CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(PcgResult), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   if (c->h_res->err) throw Error(NLMG_ETIMEOUT, "grid barrier wait gave up in the fine CG kernel");
+  if (!std::isfinite(c->h_res->rr)) throw Error(NLMG_EDIVERGED, "non-finite value in the level-0 linear solve");
   const int it = c->h_res->iters;
   if (pi >= 0) {
     // Algorithmic bytes: per iteration the scaled matrix entries and their indices, then for the two-barrier CG
@@ -823,13 +826,14 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
   int pi = c->prof_begin(1);
   if (c->opt.lin_precision == 1) {
     P.lin_tol = std::max(c->coarse_lin_tol_eff, 1e-6);
-    CoarseStepBufs<float> Bf{B.x, B.b, B.r, B.nb, B.dx, B.xt1, B.xt2, B.rt, B.kapc, B.yl, B.f_ylam, B.f_ydiag,
-                             B.f_lam, B.f_lr, B.f_lz, B.f_lpa, B.f_lpb, B.f_lq, B.f_ldinv};
+    CoarseStepBufs<float> Bf{B.x, B.b, B.r, B.nb, B.dx, B.xt1, B.xt2, B.rt, B.kapc, B.f_ylam, B.f_ydiag,
+                             B.f_lam, B.f_lr, B.f_lz, B.f_lpa, B.f_lpb, B.f_lq, B.f_ldinv, HybPipeBufs<float>{}};
     CK(launch_coarse_step<float>(c->st, L, L.Hc32, L.Sinv32, Bf, P, c->d_partial, gs, dres));
   } else {
     P.lin_tol = c->coarse_lin_tol_eff;
-    CoarseStepBufs<double> Bd{B.x, B.b, B.r, B.nb, B.dx, B.xt1, B.xt2, B.rt, B.kapc, B.yl, B.ylam, B.ydiag,
-                              B.lam, B.lr, B.lz, B.lpa, B.lpb, B.lq, B.ldinv};
+    CoarseStepBufs<double> Bd{B.x, B.b, B.r, B.nb, B.dx, B.xt1, B.xt2, B.rt, B.kapc, B.ylam, B.ydiag,
+                              B.lam, B.lr, B.lz, B.lpa, B.lpb, B.lq, B.ldinv,
+                              HybPipeBufs<double>{B.hw, B.hz, B.hs, B.hma, B.hmb}};
     CK(launch_coarse_step<double>(c->st, L, L.Hc, L.Sinv, Bd, P, c->d_partial, gs, dres));
   }
   c->prof_end(pi);
@@ -839,6 +843,10 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
   CK(cudaStreamSynchronize(c->st));
   if (c->h_res->err) throw Error(NLMG_ETIMEOUT, "grid barrier wait gave up in the coarse step kernel");
   const CoarseStepResult& R = *(const CoarseStepResult*)(c->h_res + 1);
+  if (R.bad)
+    throw Error(NLMG_EDIVERGED, std::string("non-finite value in the ") +
+                                    (R.bad == 1 ? "residual" : "hybridized linear solve") + " of coarse level " +
+                                    std::to_string(l));
   B.rn = R.rn;
   if (pi >= 0)
     c->prof.bytes[1] += (double)R.iters * c->sh->hyb_bytes_per_iter[l] * (c->opt.lin_precision == 1 ? 0.5 : 1.0) +
@@ -1070,6 +1078,8 @@ void nlmg_default_options(nlmg_options* o) {
   o->setup_threads = 0;
 }
 
+static thread_local std::string g_setup_error;   // message of the calling thread's last failed setup
+
 static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlmg_options* opt,
                               nlmg_ctx** out, bool device);
 
@@ -1167,7 +1177,7 @@ static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, co
     return NLMG_OK;
   });
   if (s != NLMG_OK) {
-    // keep the context so that the caller could read the message; here we free and return the status
+    g_setup_error = c->err;   // the context is freed: its message stays readable through nlmg_last_error(NULL)
     nlmg_destroy(c);
     return s;
   }
@@ -1505,6 +1515,7 @@ nlmg_status nlmg_level_info_get(nlmg_ctx* c, int32_t level, nlmg_level_info* out
     out->n_flux = L.n_flux;
     out->n_p = L.n_p();
     out->n_lambda = 0;
+    out->eig_host = level > 0 ? c->H().transfers[level - 1].eig_host : 0;
     if (level > 0)
       for (int8_t k : L.fkind) out->n_lambda += (k == KIND_IFACE);
     return NLMG_OK;
@@ -1614,7 +1625,7 @@ nlmg_status nlmg_measure_fp64(double* gflops) {
   }
 }
 
-const char* nlmg_last_error(const nlmg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+const char* nlmg_last_error(const nlmg_ctx* c) { return c ? c->err.c_str() : g_setup_error.c_str(); }
 
 void nlmg_destroy(nlmg_ctx* c) {
   if (!c) return;

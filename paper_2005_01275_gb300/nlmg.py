@@ -65,7 +65,8 @@ class RequestTimes(C.Structure):
 
 
 class LevelInfo(C.Structure):
-    _fields_ = [("n_cells", C.c_int32), ("n_flux", C.c_int32), ("n_p", C.c_int32), ("n_lambda", C.c_int32)]
+    _fields_ = [("n_cells", C.c_int32), ("n_flux", C.c_int32), ("n_p", C.c_int32), ("n_lambda", C.c_int32),
+                ("eig_host", C.c_int32)]
 
 
 _lib = None
@@ -188,7 +189,7 @@ class Context:
         fn = L.nlmg_setup if device else L.nlmg_setup_host
         st = fn(C.byref(m), C.byref(Kappa(int(kappa_kind), float(kappa_a))), C.byref(opts), C.byref(h))
         if st != OK:
-            raise NlmgError(st, "setup failed")
+            raise NlmgError(st, "setup failed: " + L.nlmg_last_error(None).decode())
         self.h = h
 
     def instance(self, kappa_kind=None, kappa_a=None):
@@ -250,7 +251,8 @@ class Context:
     def level_info(self, l):
         out = LevelInfo()
         self._check(lib().nlmg_level_info_get(self.h, l, C.byref(out)))
-        return dict(n_cells=out.n_cells, n_flux=out.n_flux, n_p=out.n_p, n_lambda=out.n_lambda)
+        return dict(n_cells=out.n_cells, n_flux=out.n_flux, n_p=out.n_p, n_lambda=out.n_lambda,
+                    eig_host=out.eig_host)
 
     def aggregates(self, l):
         nf = self.level_info(l)["n_cells"]

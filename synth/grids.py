@@ -82,7 +82,7 @@ def voronoi_mesh(n_side, K_of_points, seed=3, jitter=0.4):
 
     Points x_K = lattice centres + U(-jitter, jitter) h. The cube clips the cells by mirroring the points within three
     lattice spacings of each of its six faces across that face: a ridge between a point and its own mirror is a
-    boundary face. Interior faces bisect the K-L segment, so the collocation point is the midpoint and
+    boundary face. Faces smaller than 1e-8 h^2 (slivers of the tessellation's round-off) are dropped. Interior faces bisect the K-L segment, so the collocation point is the midpoint and
     Ups_bar = |eps| K_0 / (d_KL / 2); boundary faces use the distance to the face. A cell's volume is the sum of the
     pyramids from its point over its faces (|eps| d / 6 each, the point lying inside its own convex cell). Faces on
     x = 0 and x = 1 are Dirichlet, the rest Neumann. K_of_points(points) gives K_0 per cell.
@@ -124,7 +124,7 @@ def voronoi_mesh(n_side, K_of_points, seed=3, jitter=0.4):
     nxt[last] = start
     tri = 0.5 * np.linalg.norm(np.cross(V - c0[rid], V[nxt] - c0[rid]), axis=1)
     A = np.add.reduceat(tri, start)
-    keep &= A > 1e-14
+    keep &= A > 1e-8 * h * h     # drop sliver faces (qhull round-off): < 1e-8 of a lattice face
     rp, A = rp[keep], A[keep]
     a, b = rp[:, 0], rp[:, 1]
     interior = (a < n) & (b < n)
