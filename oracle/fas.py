@@ -29,17 +29,23 @@ from . import coarse, newton, tpfa
 
 
 def backtracking(res_norm, x, dx, r_x, nmax, theta):
-    """Algorithm 1. res_norm(x) -> ||r(x)||; r_x = ||r(x)||. Returns (x + s dx, ||r(x + s dx)||, s, n)."""
+    """Algorithm 1. res_norm(x) -> ||r(x)||; r_x = ||r(x)||. Returns (x + s dx, ||r(x + s dx)||, s, n).
+
+    The algorithm presumes finite residual norms: a trial whose norm is not finite counts as +infinity, and if the
+    trial it would return is not finite, x is returned unchanged (s = 0)."""
+    fin = lambda v: v if np.isfinite(v) else np.inf
     s = 1.0
     n = 0
-    r_s = res_norm(x + s * dx)
+    r_s = fin(res_norm(x + s * dx))
     while r_s > r_x and n < nmax:
-        r_half = res_norm(x + 0.5 * s * dx)
+        r_half = fin(res_norm(x + 0.5 * s * dx))
         if r_half > theta * r_s:
             break
         s *= 0.5
         n += 1
         r_s = r_half
+    if not np.isfinite(r_s):
+        return x, r_x, 0.0, n
     return x + s * dx, r_s, s, n
 
 

@@ -863,8 +863,9 @@ __device__ bool coarse_residual_dev(const LevelDev& L, double* x, const double* 
 
 // Algorithm 1 on a coarse level along dx from step s0: trial x + s s0 dx, halving s while the half step is no worse
 // than theta times the current trial (at most bt_nmax times) as long as the trial is worse than ||r(x)||; the
-// accepted trial becomes the iterate and rn its residual norm. The three buffers xb[0..2] rotate: xb[*cur] is the
-// iterate, the trials go to the other two, so no copy is needed.
+// accepted trial becomes the iterate and rn its residual norm. A trial whose residual norm is not finite counts as
+// +infinity; if the returned trial is not finite, the iterate is kept. The three buffers xb[0..2] rotate: xb[cur]
+// is the iterate, the trials go to the other two, so no copy is needed.
 template <class T>
 __device__ bool coarse_backtrack_dev(const LevelDev& L, const CoarseStepBufs<T>& B, const CoarseStepParams& P,
                                      double* const* xb, int& cur, double s0, double& rn, int& evals, Grid& g) {
@@ -874,6 +875,7 @@ __device__ bool coarse_backtrack_dev(const LevelDev& L, const CoarseStepBufs<T>&
   if (!coarse_residual_dev(L, xb[t1], xb[cur], B.dx, s * s0, B.b, B.rt, nullptr, B.kapc, P.kind, P.a, g, r_s))
     return false;
   ++evals;
+  if (!isfinite(r_s)) r_s = HUGE_VAL;   // a non-finite trial counts as +infinity
   int n = 0;
   while (r_s > rn && n < P.bt_nmax) {
     double r_half = 0.0;
@@ -881,6 +883,7 @@ __device__ bool coarse_backtrack_dev(const LevelDev& L, const CoarseStepBufs<T>&
                              r_half))
       return false;
     ++evals;
+    if (!isfinite(r_half)) r_half = HUGE_VAL;
     if (r_half > P.bt_theta * r_s) break;
     s *= 0.5;
     ++n;
@@ -889,6 +892,7 @@ __device__ bool coarse_backtrack_dev(const LevelDev& L, const CoarseStepBufs<T>&
     t1 = t2;
     t2 = t;
   }
+  if (r_s == HUGE_VAL) return true;   // no finite trial: the iterate is kept
   cur = t1;
   rn = r_s;
   return true;

@@ -482,19 +482,23 @@ double fine_eval(nlmg_ctx* c, const double* p, const double* dp, double s, FineS
 }
 
 // Algorithm 1 on level 0 from c->cur along dp (scaled by s0); the accepted trial becomes c->cur.
+// Algorithm 1 on level 0. A trial whose residual norm is not finite counts as +infinity; if the trial the algorithm
+// returns is not finite, the iterate is kept.
 void backtrack0(nlmg_ctx* c, const double* dp, double s0) {
   const nlmg_options& o = c->opt;
+  auto fin = [](double v) { return std::isfinite(v) ? v : HUGE_VAL; };
   double s = 1.0;
   int n = 0;
-  double r_s = fine_eval(c, c->cur.p, dp, s * s0, c->t1);
+  double r_s = fin(fine_eval(c, c->cur.p, dp, s * s0, c->t1));
   while (r_s > c->cur.rn && n < o.bt_nmax) {
-    double r_half = fine_eval(c, c->cur.p, dp, 0.5 * s * s0, c->t2);
+    double r_half = fin(fine_eval(c, c->cur.p, dp, 0.5 * s * s0, c->t2));
     if (r_half > o.bt_theta * r_s) break;
     s *= 0.5;
     ++n;
     r_s = r_half;
     std::swap(c->t1, c->t2);
   }
+  if (r_s == HUGE_VAL) return;
   std::swap(c->cur, c->t1);
 }
 

@@ -267,7 +267,8 @@ def problem_config(name, scale=None):
 
 def voronoi_problem(n_side=12, seed=3):
     """Unstructured workload: clipped Voronoi cells of a jittered lattice, ln K_0 ~ N(0, 2^2) correlated over 4
-    lattice spacings (sampled at the points), kappa = (1 + p^2)^-1, p = 1 on x = 0 and 0 on x = 1."""
+    lattice spacings (sampled at the points), kappa = (1 + p^2)^-1, p = 1 on x = 0 and 0 on x = 1; pressure-change
+    clamp 0.5 (half the range of the boundary data)."""
     field_ = gaussian_random_field((n_side,) * 3, 4.0, np.random.default_rng(seed + 100))
 
     def K_of(P):
@@ -278,7 +279,7 @@ def voronoi_problem(n_side=12, seed=3):
     g = np.zeros(mesh.n_faces)
     d = np.where(mesh.face_bc == BC_DIRICHLET)[0]
     g[d] = np.where(mesh.points[mesh.face_cells[d, 0], 0] < 0.5, 1.0, 0.0)
-    opts = default_options(n_levels=3, agg_size=[27, 8, 8], modes=[4, 3, 3])
+    opts = default_options(n_levels=3, agg_size=[27, 8, 8], modes=[4, 3, 3], dp_clamp=0.5)
     return Problem(mesh, KAPPA_INV1P2, 0.0, np.zeros(mesh.n_cells), g, opts, "voronoi")
 
 

@@ -11,6 +11,19 @@ from synth.grids import problem_config
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
 
+def test_backtracking_non_finite_trials():
+    """A non-finite trial counts as +inf: the half step is taken if it is finite; if no trial is finite, x stays."""
+    def r(y):
+        return np.nan if y > 10.0 else abs(y - 1.0)
+    # the full step (y = 16) is NaN, i.e. +inf; the halves y = 8, 4, 2 are finite and each is accepted (7, 3, 1),
+    # halving stops once the trial is no worse than r(x) = 1: y = 2
+    xn, rn, s, n = fas.backtracking(r, 0.0, 16.0, 1.0, 4, 0.9)
+    assert xn == 2.0 and rn == 1.0 and s == 0.125 and n == 3
+    # every trial non-finite: the iterate is returned unchanged
+    xn, rn, s, n = fas.backtracking(lambda y: np.inf, 0.0, 1.0, 2.0, 4, 0.9)
+    assert xn == 0.0 and rn == 2.0 and s == 0.0
+
+
 def test_backtracking_hand_cases():
     rows = np.loadtxt(os.path.join(GOLD, "backtracking_quadratic.txt"))
     for x, dx, x_out, s_out, n_out in rows:
