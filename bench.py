@@ -140,37 +140,74 @@ def serving_requests(n, seed=4):
     return out
 
 
-def run_serving(nlmg, n):
-    """Burst of n requests through the library's request loop (mixed precision), against the same requests solved
-    one at a time in plain FP64 (setup excluded there, as in the main metric)."""
+def _serve(nlmg, reqs, arrivals=None, hierarchy_cache=8):
+    """Submits the requests (at the given arrival offsets in seconds, else all at once) to the library's request
+    loop and collects latency (submit -> result), setup and solve times."""
     import numpy as np
-    reqs = serving_requests(n)
-    srv = nlmg.Server(max_inflight=8, mem_budget_bytes=32 << 30, setup_threads_per_request=2)
+    srv = nlmg.Server(max_inflight=8, mem_budget_bytes=32 << 30, setup_threads_per_request=2,
+                      hierarchy_cache=hierarchy_cache)
     t0 = time.perf_counter()
-    tickets = [srv.submit(m, 0, a, dict(o, lin_precision=1), f, g) for m, a, o, f, g in reqs]
-    lat, solve_ms, setup_ms, ok = [], [], [], 0
+    tickets = []
+    for i, (m, a, o, f, g) in enumerate(reqs):
+        if arrivals is not None:
+            wait = t0 + arrivals[i] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+        tickets.append(srv.submit(m, 0, a, o, f, g))
+    lat, solve_ms, setup_ms, ok, reused = [], [], [], 0, 0
     for t in tickets:
         p, rep, tm, st = srv.poll(t, wait_ms=600000)
         ok += st == 0
         lat.append(tm["latency_ms"])
         solve_ms.append(tm["solve_ms"])
         setup_ms.append(tm["setup_ms"])
+        reused += bool(tm["hierarchy_reused"])
     makespan = time.perf_counter() - t0
     srv.close()
-    seq_ms = 0.0
-    for m, a, o, f, g in reqs:
+    lat = np.array(lat)
+    return {"ok": int(ok), "solves_per_s": len(reqs) / makespan, "makespan_s": makespan,
+            "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
+            "mean_setup_ms": float(np.mean(setup_ms)), "mean_solve_ms": float(np.mean(solve_ms)),
+            "hierarchies_reused": int(reused)}
+
+
+def run_serving(nlmg, n):
+    """The request loop (FP32 inner CG in the FP64 FAS, up to 8 requests in flight): a burst of n requests of their
+    own meshes, then the same requests arriving as a Poisson stream at 0.8 of the burst's throughput, then n
+    requests on one mesh and K with their own nonlinearity parameter and data (hierarchy reuse). Against: the same
+    requests one at a time on a plain FP64 context each, setup included and excluded."""
+    import numpy as np
+    from synth.grids import cartesian_mesh, lognormal_field, default_options, multi_rhs_rows
+    reqs = [(m, a, dict(o, lin_precision=1), f, g) for m, a, o, f, g in serving_requests(n)]
+    burst = _serve(nlmg, reqs)
+    rng = np.random.default_rng(7)
+    rate = 0.8 * burst["solves_per_s"]
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
+    poisson = _serve(nlmg, reqs, arrivals=arrivals)
+    poisson["arrival_rate_per_s"] = rate
+    seq_solve_ms, seq_total_s = 0.0, 0.0
+    for m, a, o, f, g in serving_requests(n):
+        t1 = time.perf_counter()
         ctx = nlmg.Context(m, 0, a, o)
         _, rep, st = ctx.solve(f, g, max_cycles=60)
-        seq_ms += rep["solve_ms"]
+        seq_total_s += time.perf_counter() - t1
+        seq_solve_ms += rep["solve_ms"]
         ctx.close()
-    lat = np.array(lat)
-    return {"requests": n, "ok": int(ok), "sizes_cells": [int(r[0].n_cells) for r in reqs],
-            "solves_per_s_incl_setup": n / makespan, "makespan_s": makespan,
-            "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
-            "mean_setup_ms": float(np.mean(setup_ms)), "mean_solve_ms_in_mix": float(np.mean(solve_ms)),
-            "sequential_fp64_solves_per_s_excl_setup": n / (seq_ms / 1e3),
-            "what": "burst arrival at t=0, max 8 in flight, each request its own hierarchy (host setup) and stream, "
-                    "FP32 CG inside the FP64 FAS; latency = submit -> result"}
+    # one reservoir: a 40^3 mesh and K, per request its own kappa = exp(a p), clamp and data
+    side = 40
+    mesh = cartesian_mesh((side,) * 3, lognormal_field((side,) * 3, 1.0, 4.0, seed=11))
+    F, G = multi_rhs_rows(mesh, n, seed=12)
+    alphas = rng.uniform(0.5, 2.0, n)
+    base = default_options(n_levels=3, agg_size=[64, 8], modes=[4, 4], lin_precision=1)
+    shared = [(mesh, float(a), dict(base, dp_clamp=float(np.log(1.5) / a)), F[i], G[i]) for i, a in enumerate(alphas)]
+    reuse = _serve(nlmg, shared)
+    no_reuse = _serve(nlmg, shared, hierarchy_cache=0)
+    return {"requests": n, "sizes_cells": [int(r[0].n_cells) for r in reqs], "burst": burst, "poisson": poisson,
+            "sequential_fp64_solves_per_s_incl_setup": n / seq_total_s,
+            "sequential_fp64_solves_per_s_excl_setup": n / (seq_solve_ms / 1e3),
+            "one_mesh_with_hierarchy_reuse": reuse, "one_mesh_without_reuse": no_reuse,
+            "what": "each request its own mesh and hierarchy (sizes log-uniform 4k-65k cells, 2D/3D) unless noted; "
+                    "latency = submit -> result; FP32 CG inside the FP64 FAS; max 8 in flight"}
 
 
 def run_multi_rhs(nlmg, pr, ctx, n_rhs, n_streams):
