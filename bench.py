@@ -471,7 +471,8 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": N, "parallelism": "replicas" if world > 1 else "single",
+        "config": {"workload": WORKLOAD if args.scale == 64 else WORKLOAD.replace("chan3d_64: 64^3", "chan3d_%d: %d^3" % (
+                       args.scale, args.scale)), "cells": N, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "256 MiB buffer written between steps, outside each step's CUDA-event pair",
                    "setup_s": round(setup_s, 3), "lin_tol": ctx.opts.lin_tol,
                    "coarse_lin_tol": ctx.opts.coarse_lin_tol},

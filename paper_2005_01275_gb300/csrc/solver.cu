@@ -516,13 +516,21 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
   // one more closely (the pipelined recurrences with an FP32 matrix product drift: measured 10,768 instead of 3,466
   // fine iterations on the 64^3 workload, whether the recurrences run in FP32 or in FP64).
   const bool pipe = !fp32 && c->lin_tol_eff >= 1e-6;
-  int kind = 0;   // 0 two-barrier, 1 pipelined in memory, 2 pipelined in registers
+  int kind = 0;   // 0 two-barrier, 1 pipelined in memory, 2 pipelined in registers, 3 two-barrier in registers
   int pi;
   if (fp32) {
     launch_scale_sell<float>(c->st, c->F, c->Tval, c->sdiag, c->Ts32);
     pi = c->prof_begin(0);
-    CK(launch_fine_cg<float>(c->st, c->F, c->Ts32, c->sdiag, R, -1.0, c->cx, c->fy, c->fr, c->fpa, c->fpb, c->fq,
-                             c->d_partial, gs, std::max(c->lin_tol_eff, 1e-6), c->opt.lin_maxit, c->d_res));
+    const cudaError_t e = launch_fine_cg2_reg<float>(c->st, c->F, c->Ts32, c->sdiag, R, -1.0, c->cx, c->fr,
+                                                     c->d_partial, gs, std::max(c->lin_tol_eff, 1e-6),
+                                                     c->opt.lin_maxit, c->d_res);
+    if (e == cudaSuccess) {
+      kind = 3;
+    } else {
+      if (e != cudaErrorNotSupported) CK(e);
+      CK(launch_fine_cg<float>(c->st, c->F, c->Ts32, c->sdiag, R, -1.0, c->cx, c->fy, c->fr, c->fpa, c->fpb, c->fq,
+                               c->d_partial, gs, std::max(c->lin_tol_eff, 1e-6), c->opt.lin_maxit, c->d_res));
+    }
   } else {
     launch_scale_sell<double>(c->st, c->F, c->Tval, c->sdiag, c->Ts64);
     pi = c->prof_begin(0);
@@ -555,15 +563,17 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
   if (pi >= 0) {
     // Algorithmic bytes: per iteration the scaled matrix entries and their indices, then for the two-barrier CG
     // r read, p and q read and written, p, q, y, r read and y, r written (11 vectors); for the pipelined CG in
-    // memory w, z, s, p, y, r read and z, s, p, y, r, w written (12 vectors); for the register-resident one only
-    // w gathered and w written (2 vectors). The pipelined forms take one extra product at the start. Once: b and
+    // memory w, z, s, p, y, r read and z, s, p, y, r, w written (12 vectors); for the register-resident forms only
+    // the exchanged vector (w, or r) gathered and written (2 vectors). The pipelined forms take one extra product
+    // at the start. Once: b and
     // S read, y and r written, then S and y read and dx written. Gathered neighbour values are counted once.
     // Flops: one product (2 per stored entry) plus 6 FMAs per cell (two-barrier) or 9 (pipelined) per iteration.
     const double N = c->F.N, nnz = (double)c->sh->nnz_real, v = fp32 ? 4.0 : 8.0;
-    const double nvec = kind == 2 ? 2.0 : kind == 1 ? 12.0 : 11.0;
+    const double nvec = kind >= 2 ? 2.0 : kind == 1 ? 12.0 : 11.0;
     const double per_it_b = (4.0 + v) * nnz + nvec * v * N;
-    const double per_it_f = kind ? 2.0 * nnz + 18.0 * N : 2.0 * nnz + 12.0 * N;   // an FMA counts 2
-    c->prof.bytes[0] += (8.0 + 8.0) * N + 2.0 * v * N + 8.0 * N + v * N + 8.0 * N + (kind ? per_it_b : 0.0) +
+    const bool pipelined = kind == 1 || kind == 2;
+    const double per_it_f = pipelined ? 2.0 * nnz + 18.0 * N : 2.0 * nnz + 12.0 * N;   // an FMA counts 2
+    c->prof.bytes[0] += (8.0 + 8.0) * N + 2.0 * v * N + 8.0 * N + v * N + 8.0 * N + (pipelined ? per_it_b : 0.0) +
                         it * per_it_b;
     c->prof.flops[0] += it * per_it_f;
   }
