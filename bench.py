@@ -212,38 +212,43 @@ def run_serving(nlmg, n):
 
 def run_multi_rhs(nlmg, pr, ctx, n_rhs, n_streams):
     """n_rhs right-hand sides on the bench mesh and its hierarchy: one plain FP64 context solving them one after the
-    other, against nlmg_solve_many on n_streams contexts of the same hierarchy, in FP64 and with the FP32 inner CG.
-    Host buffers in and out in every variant (wall clock per batch)."""
+    other, against nlmg_solve_many on n_streams contexts of the same hierarchy, in FP64 and with the FP32 inner CG,
+    each with the library's default SM share and with the share chosen by nlmg_tune_sm_share on the first n_streams
+    rows. Host buffers in and out in every variant (wall clock per batch)."""
     import numpy as np
     from synth.grids import multi_rhs_rows
     F, G = multi_rhs_rows(pr.mesh, n_rhs, seed=5)
     mctx = ctx.instance()
     mctx.set_options(lin_precision=1)
-    ctx.solve_many(F[:n_streams], G[:n_streams], max_cycles=60, n_streams=n_streams)      # creates the instances
-    mctx.solve_many(F[:n_streams], G[:n_streams], max_cycles=60, n_streams=n_streams)
+    ns = min(n_streams, n_rhs)
+    ctx.solve_many(F[:ns], G[:ns], max_cycles=60, n_streams=n_streams)      # creates the instances
+    mctx.solve_many(F[:ns], G[:ns], max_cycles=60, n_streams=n_streams)
     t0 = time.perf_counter()
     seq = [ctx.solve(F[r], G[r], max_cycles=60) for r in range(n_rhs)]
     t_seq = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    P, reps, sts = ctx.solve_many(F, G, max_cycles=60, n_streams=n_streams)
-    t_many = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    PM, mreps, msts = mctx.solve_many(F, G, max_cycles=60, n_streams=n_streams)
-    t_mixed = time.perf_counter() - t0
-    diff64 = max(float(np.linalg.norm(P[r] - seq[r][0]) / np.linalg.norm(seq[r][0])) for r in range(n_rhs))
-    mixed_err = max(float(np.linalg.norm(PM[r] - seq[r][0]) / np.linalg.norm(seq[r][0])) for r in range(n_rhs))
-    mixed_res = max(m["res"] / m["res0"] for m in mreps)
+    out = {"rhs": n_rhs, "streams": n_streams, "sequential_fp64_solves_per_s": n_rhs / t_seq}
+    for name, c in (("fp64", ctx), ("mixed", mctx)):
+        best, rates = c.tune_sm_share(F[:ns], G[:ns])
+        for mode, sms in (("default", 0), ("tuned", best)):
+            c.set_options(max_sms=sms)
+            t0 = time.perf_counter()
+            P, reps, sts = c.solve_many(F, G, max_cycles=60, n_streams=n_streams)
+            dt = time.perf_counter() - t0
+            diff = max(float(np.linalg.norm(P[r] - seq[r][0]) / np.linalg.norm(seq[r][0])) for r in range(n_rhs))
+            out["many_%s_%s" % (name, mode)] = {
+                "solves_per_s": n_rhs / dt, "max_sms": sms, "ok": int(np.sum(sts == 0)),
+                "max_rel_diff_vs_sequential_fp64": diff,
+                "max_rel_residual": max(r["res"] / r["res0"] for r in reps)}
+        out["tuner_%s" % name] = {"candidates_max_sms": "all, 1/2, 1/4, 1/8 of the SMs",
+                                  "solves_per_s": [float(x) for x in rates], "best_max_sms": best}
+        c.set_options(max_sms=0)
+    out["cycles_per_solve"] = float(np.mean([r[1]["cycles"] for r in seq]))
+    out["what"] = ("right-hand sides share the mesh, K and the hierarchy (per row: Dirichlet value on x = 0 and a "
+                   "smooth source); sequential = one context on all SMs, one row after the other; many = "
+                   "nlmg_solve_many; default share = SMs / min(streams, 4); tuned = nlmg_tune_sm_share on the first "
+                   "rows; host buffers in and out; wall clock per batch; all at relative residual 1e-8")
     mctx.close()
-    return {"rhs": n_rhs, "streams": n_streams, "ok": int(np.sum(sts == 0) + np.sum(msts == 0)),
-            "sequential_fp64_solves_per_s": n_rhs / t_seq,
-            "many_fp64_solves_per_s": n_rhs / t_many, "many_fp64_max_rel_diff_vs_sequential": diff64,
-            "many_mixed_solves_per_s": n_rhs / t_mixed, "mixed_max_rel_diff_vs_fp64": mixed_err,
-            "mixed_max_rel_residual": mixed_res,
-            "cycles_per_solve": float(np.mean([r["cycles"] for r in reps])),
-            "what": "right-hand sides share the mesh, K and the hierarchy (per row: Dirichlet value on x = 0 and a "
-                    "smooth source); sequential = one context on all SMs, one row after the other; many = "
-                    "nlmg_solve_many, each context's persistent kernels on SMs / min(streams, 4); host buffers in "
-                    "and out; wall clock per batch; both at relative residual 1e-8"}
+    return out
 
 
 def run_voronoi(nlmg, n_side, steps):

@@ -136,6 +136,17 @@ nlmg_status nlmg_setup_host(const nlmg_mesh* mesh, const nlmg_kappa* kappa, cons
  * destroyed with nlmg_destroy. Errors: NLMG_EINVAL (NULL base or out, host-only base), NLMG_ENOMEM / NLMG_ECUDA. */
 nlmg_status nlmg_instance(const nlmg_ctx* base, const nlmg_kappa* kappa, nlmg_ctx** out);
 
+/* Launch-shape autotuner for concurrent solves: times nlmg_solve_many of the n_streams given rows
+ * (f_cell[n_streams][n_cells], g_face[n_streams][n_faces], host buffers) on n_streams streams with the persistent
+ * kernels of every context capped at each of the SM shares {all, 1/2, 1/4, 1/8 of the SMs}, after one untimed run,
+ * and returns the fastest as *best_max_sms (0 = all SMs); solves_per_s (NULL or 4 entries) receives the measured
+ * throughput of each candidate. Not a step of the paper's method. The context's options are left as they were:
+ * set max_sms to the result (nlmg_set_options) to use it. Which candidate wins depends on the problem size (small
+ * solves are latency bound and run best side by side on a share of the GPU, large ones fill it) and on timing
+ * noise, so the result may differ from run to run; a fixed max_sms keeps results bitwise reproducible. */
+nlmg_status nlmg_tune_sm_share(nlmg_ctx* ctx, int32_t n_streams, const double* f_cell, const double* g_face,
+                               int32_t* best_max_sms, double* solves_per_s);
+
 /* Replaces the solver options of ctx (smoother, backtracking, clamp, coarsest steps, inner tolerances, precision)
  * for the following solves. The hierarchy options (n_levels, agg_size, modes) must equal those ctx was set up with
  * (NLMG_EINVAL otherwise); setup_threads is ignored. */

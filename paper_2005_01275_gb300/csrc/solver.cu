@@ -1225,6 +1225,52 @@ nlmg_status nlmg_instance(const nlmg_ctx* base, const nlmg_kappa* kappa, nlmg_ct
   return NLMG_OK;
 }
 
+nlmg_status nlmg_tune_sm_share(nlmg_ctx* c, int32_t n_streams, const double* f_cell, const double* g_face,
+                               int32_t* best_max_sms, double* solves_per_s) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_device(c);
+    if (n_streams < 1 || !f_cell || !g_face || !best_max_sms) throw Error(NLMG_EINVAL, "bad argument");
+    int sms = 0, dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int cand[4] = {0, std::max(1, sms / 2), std::max(1, sms / 4), std::max(1, sms / 8)};
+    const nlmg_options saved = c->opt;
+    const size_t N = (size_t)c->F.N;
+    std::vector<double> p(N * n_streams);
+    std::vector<nlmg_report> rep(n_streams);
+    std::vector<int32_t> st(n_streams);
+    double best = -1.0;
+    int best_i = 0;
+    nlmg_status result = NLMG_OK;
+    for (int i = 0; i < 4 && result == NLMG_OK; ++i) {
+      c->opt.max_sms = cand[i];
+      for (int run = 0; run < 2; ++run) {   // the first run is untimed (instances, caches)
+        const auto t0 = std::chrono::steady_clock::now();
+        const nlmg_status s = nlmg_solve_many(c, n_streams, f_cell, g_face, nullptr, c->tol_rel, c->tol_abs, 50,
+                                              n_streams, p.data(), rep.data(), st.data());
+        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (s != NLMG_OK && s != NLMG_ENOCONV) {
+          result = s;
+          break;
+        }
+        if (run == 1) {
+          const double v = n_streams / dt;
+          if (solves_per_s) solves_per_s[i] = v;
+          if (v > best) {
+            best = v;
+            best_i = i;
+          }
+        }
+      }
+    }
+    c->opt = saved;
+    c->reset_inner_tols();
+    if (result != NLMG_OK) return result;
+    *best_max_sms = cand[best_i];
+    return NLMG_OK;
+  });
+}
+
 nlmg_status nlmg_set_options(nlmg_ctx* c, const nlmg_options* opt) {
   return guarded(c, [&]() -> nlmg_status {
     if (!opt) throw Error(NLMG_EINVAL, "null options");

@@ -83,6 +83,7 @@ SIGNATURES = {
     "nlmg_solve_many": (C.c_int, [_P, C.c_int32, _D, _D, _D, C.c_double, C.c_double, C.c_int32, C.c_int32, _D,
                                   C.POINTER(Report), _I]),
     "nlmg_set_options": (C.c_int, [_P, C.POINTER(Options)]),
+    "nlmg_tune_sm_share": (C.c_int, [_P, C.c_int32, _D, _D, _I, _D]),
     "nlmg_set_data": (C.c_int, [_P, _D, _D]),
     "nlmg_solve": (C.c_int, [_P, _D, _D, _D, C.c_double, C.c_double, C.c_int32, _D, C.POINTER(Report)]),
     "nlmg_solve_device": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_double, C.c_int32, _P, C.POINTER(Report)]),
@@ -210,6 +211,16 @@ class Context:
             setattr(o, k, v)
         self._check(lib().nlmg_set_options(self.h, C.byref(o)))
         self.opts = o
+
+    def tune_sm_share(self, f_rows, g_rows):
+        """Times the SM-share candidates on these rows; returns (best max_sms, solves/s per candidate)."""
+        f = np.ascontiguousarray(f_rows, dtype=np.float64)
+        g = np.ascontiguousarray(g_rows, dtype=np.float64)
+        n = f.shape[0]
+        best = C.c_int32(0)
+        rates = np.zeros(4)
+        self._check(lib().nlmg_tune_sm_share(self.h, n, _dp(f), _dp(g), C.byref(best), _dp(rates)))
+        return best.value, rates
 
     def solve_many(self, f_rows, g_rows, x0_rows=None, tol_rel=1e-8, tol_abs=1e-10, max_cycles=50, n_streams=0,
                    allow_noconv=False):
