@@ -139,8 +139,8 @@ nlmg_status nlmg_instance(const nlmg_ctx* base, const nlmg_kappa* kappa, nlmg_ct
 /* Launch-shape autotuner for concurrent solves: times nlmg_solve_many of the n_streams given rows
  * (f_cell[n_streams][n_cells], g_face[n_streams][n_faces], host buffers) on n_streams streams with the persistent
  * kernels of every context capped at each of the SM shares {all, 1/2, 1/4, 1/8 of the SMs}, after one untimed run,
- * and returns the fastest as *best_max_sms (0 = all SMs); solves_per_s (NULL or 4 entries) receives the measured
- * throughput of each candidate. Not a step of the paper's method. The context's options are left as they were:
+ * and returns the fastest as *best_max_sms (an SM count; the full count for all of them); solves_per_s (NULL or 4
+ * entries) receives the measured throughput of each candidate. Not a step of the paper's method. The context's options are left as they were:
  * set max_sms to the result (nlmg_set_options) to use it. Which candidate wins depends on the problem size (small
  * solves are latency bound and run best side by side on a share of the GPU, large ones fill it) and on timing
  * noise, so the result may differ from run to run; a fixed max_sms keeps results bitwise reproducible. */

@@ -845,9 +845,11 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
     CK(launch_coarse_step<float>(c->st, L, L.Hc32, L.Sinv32, Bf, P, c->d_partial, gs, dres));
   } else {
     P.lin_tol = c->coarse_lin_tol_eff;
+    // pipelined hybridized CG at loose tolerances; the two-synchronisation CG when a tight solve is asked for
+    const bool pipe = c->coarse_lin_tol_eff >= 1e-6;
     CoarseStepBufs<double> Bd{B.x, B.b, B.r, B.nb, B.dx, B.xt1, B.xt2, B.rt, B.kapc, B.ylam, B.ydiag,
                               B.lam, B.lr, B.lz, B.lpa, B.lpb, B.lq, B.ldinv,
-                              HybPipeBufs<double>{B.hw, B.hz, B.hs, B.hma, B.hmb}};
+                              pipe ? HybPipeBufs<double>{B.hw, B.hz, B.hs, B.hma, B.hmb} : HybPipeBufs<double>{}};
     CK(launch_coarse_step<double>(c->st, L, L.Hc, L.Sinv, Bd, P, c->d_partial, gs, dres));
   }
   c->prof_end(pi);
@@ -1233,7 +1235,8 @@ nlmg_status nlmg_tune_sm_share(nlmg_ctx* c, int32_t n_streams, const double* f_c
     int sms = 0, dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int cand[4] = {0, std::max(1, sms / 2), std::max(1, sms / 4), std::max(1, sms / 8)};
+    // explicit SM counts: max_sms = 0 would mean the default share of nlmg_solve_many, not the whole GPU
+    const int cand[4] = {sms, std::max(1, sms / 2), std::max(1, sms / 4), std::max(1, sms / 8)};
     const nlmg_options saved = c->opt;
     const size_t N = (size_t)c->F.N;
     std::vector<double> p(N * n_streams);

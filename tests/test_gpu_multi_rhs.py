@@ -121,3 +121,19 @@ def test_loose_inner_tolerances_do_not_stall(nlmg_lib):
     pstar, _ = newton.solve(pr.mesh, pr.kappa_kind, pr.kappa_a, F[0], G[0], dp_clamp=pr.opts["dp_clamp"])
     assert np.linalg.norm(p - pstar) <= 1e-6 * np.linalg.norm(pstar)
     ctx.close()
+
+
+def test_sm_share_tuner_returns_a_candidate(nlmg_lib):
+    """The autotuner times the four SM shares and returns one of them; the context's options are left alone."""
+    pr = _problem(scale=8)
+    F, G = _rows(pr, 2, seed=53)
+    ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.opts)
+    p0, _, st = ctx.solve(F[0], G[0], max_cycles=60)
+    assert st == 0
+    best, rates = ctx.tune_sm_share(F, G)
+    sms = _sms()
+    assert best in (sms, sms // 2, sms // 4, sms // 8)
+    assert np.all(rates > 0)
+    p1, _, st = ctx.solve(F[0], G[0], max_cycles=60)
+    assert st == 0 and np.array_equal(p0, p1)      # same options as before the tuning
+    ctx.close()
