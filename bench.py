@@ -44,7 +44,8 @@ class Clocks:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), "nlmg_bench_clocks_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:

@@ -10,7 +10,7 @@ Builds, level by level, the objects of App. A of the paper with m_f = 1 flux unk
     local_neumann_boundary_value_problem, bubbles), D^{l+1} = P_p^T D^l P_sigma (Sec. 3.1), the static local
     matrices of Prop. 1 (App. C: M_A^{l+1} = P_sigma,A^T M_A^l P_sigma,A) and the Pi~ weights of eq. pwc_projector.
 
-Readings where the paper is silent (each listed with its reason in the design notes):
+Readings where the paper is silent:
   * the reference operator for the local eigenproblems is the one at kappa = 1 ("for a given discrete pressure");
   * M restricted to N(A) keeps the flux unknowns whose cells all lie in N(A): interfaces with both owners in N(A)
     and the bubbles of cells in N(A); boundary (Dirichlet) unknowns are not graph edges and are left out;

@@ -133,7 +133,7 @@ def test_one_vcycle_matches_oracle(case):
 
 
 def test_solve_matches_newton_solution(case):
-    """Spec bar: FP64 GPU solution within 1e-10 of p* when run to relative residual 1e-12."""
+    """The bar for the FP64 path: the GPU solution within 1e-10 of p* when run to relative residual 1e-12."""
     pr, H, ctx = case
     pstar, _ = newton.solve(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, dp_clamp=pr.opts["dp_clamp"])
     p, rep, st = ctx.solve(pr.f_cell, pr.g_face, tol_rel=1e-12, tol_abs=1e-300, max_cycles=60)

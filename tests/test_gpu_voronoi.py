@@ -44,3 +44,24 @@ def test_mixed_precision_reaches_the_fp64_solution(vor40):
     assert np.linalg.norm(p32 - p64) <= 1e-8 * np.linalg.norm(p64)
     r = np.linalg.norm(tpfa.reduced_residual(pr.mesh, pr.kappa_kind, pr.kappa_a, p32, pr.f_cell, pr.g_face))
     assert r <= 1e-11 * rep32["res0"] * 1.0001
+
+
+def test_full_size_unstructured_workload(nlmg_lib):
+    """The 1M-cell Voronoi workload as the bench runs it (4 levels, aggregates 64 then 8, 4 modes, clamp 0.5): the
+    oracle's FP64 residual of the GPU solution meets the tolerance, in FP64 and with the FP32 inner CG."""
+    pr = voronoi_problem(100)
+    opts = dict(pr.opts, n_levels=4, agg_size=[64, 8, 8], modes=[4, 4, 4])
+    ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, opts)
+    r0 = np.linalg.norm(tpfa.reduced_residual(pr.mesh, pr.kappa_kind, pr.kappa_a, np.zeros(pr.mesh.n_cells),
+                                              pr.f_cell, pr.g_face))
+    p64, rep, st = ctx.solve(pr.f_cell, pr.g_face, max_cycles=80)
+    assert st == 0, rep
+    r = np.linalg.norm(tpfa.reduced_residual(pr.mesh, pr.kappa_kind, pr.kappa_a, p64, pr.f_cell, pr.g_face))
+    assert r <= 1e-8 * r0 * 1.0001
+    ctx.set_options(lin_precision=1)
+    p32, rep, st = ctx.solve(pr.f_cell, pr.g_face, max_cycles=80)
+    assert st == 0, rep
+    r = np.linalg.norm(tpfa.reduced_residual(pr.mesh, pr.kappa_kind, pr.kappa_a, p32, pr.f_cell, pr.g_face))
+    assert r <= 1e-8 * r0 * 1.0001
+    assert np.linalg.norm(p32 - p64) <= 1e-5 * np.linalg.norm(p64)     # two solutions at relative residual 1e-8
+    ctx.close()
