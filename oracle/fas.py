@@ -183,12 +183,65 @@ class FAS:
         p, rn = self.smooth0(p, o["nu_post"], rn)
         return p, rn, False
 
-    def solve(self, p0=None, max_cycles=None):
+    def cascade(self, p):
+        """Nonlinear cascadic start (Sec. 4.2, Example 2): the FAS coarse problems of Algorithm 2 are formed top-down
+        at the current iterate; then, from the coarsest level up, each is solved nonlinearly by Picard smoothing steps
+        (at most `coarsest_steps`, stopping at the relative tolerance of the solve) from the point its finer level
+        projected, and its correction is carried to the finer level with Algorithm 1. Returns the new level-0
+        iterate."""
+        o, H = self.o, self.H
+        L = len(H.levels)
+        if L == 1:
+            return p
+        xs, bs, x0s = [None] * L, [None] * L, [None] * L
+        tr, levc = H.transfers[0], H.levels[1]
+        Rp = self.R(p)
+        xs[1] = np.concatenate([tr.Qsigma @ self.sigma0(p), tr.Qp @ p])
+        bs[1] = coarse.operator(levc, self.kind, self.a, xs[1][:levc.n_flux], xs[1][levc.n_flux:]) \
+            - np.concatenate([np.zeros(levc.n_flux), tr.Pp.T @ (-Rp)])
+        for l in range(1, L - 1):
+            lev, tr, levc = H.levels[l], H.transfers[l], H.levels[l + 1]
+            s, q = self.split(l, xs[l])
+            r = self.res(l, xs[l], bs[l])
+            xs[l + 1] = np.concatenate([tr.Qsigma @ s, tr.Qp @ q])
+            bs[l + 1] = coarse.operator(levc, self.kind, self.a, xs[l + 1][:levc.n_flux], xs[l + 1][levc.n_flux:]) \
+                - np.concatenate([tr.Psigma.T @ r[:lev.n_flux], tr.Pp.T @ r[lev.n_flux:]])
+        for l in range(1, L):
+            x0s[l] = xs[l].copy()
+
+        def solve_level(l, x, b):
+            r = float(np.linalg.norm(self.res(l, x, b)))
+            r_in = r
+            for _ in range(o["coarsest_steps"]):
+                if r <= o["tol_rel"] * r_in or r <= o["tol_abs"]:
+                    break
+                x, r = self.picard_smooth(l, x, b, r)
+            return x
+
+        ys = [None] * L
+        ys[L - 1] = solve_level(L - 1, xs[L - 1], bs[L - 1])
+        for l in range(L - 2, 0, -1):
+            tr, levc = H.transfers[l], H.levels[l + 1]
+            e = ys[l + 1] - x0s[l + 1]
+            dx = np.concatenate([tr.Psigma @ e[:levc.n_flux], tr.Pp @ e[levc.n_flux:]])
+            nrm = lambda y, l=l: float(np.linalg.norm(self.res(l, y, bs[l])))
+            x, _, _, _ = backtracking(nrm, xs[l], dx, nrm(xs[l]), o["bt_nmax"], o["bt_theta"])
+            ys[l] = solve_level(l, x, bs[l])
+        tr, levc = H.transfers[0], H.levels[1]
+        dp = tr.Pp @ (ys[1] - x0s[1])[levc.n_flux:]
+        p, _, _, _ = backtracking(self.Rnorm, p, dp, float(np.linalg.norm(Rp)), o["bt_nmax"], o["bt_theta"])
+        return p
+
+    def solve(self, p0=None, max_cycles=None, cascadic=False):
+        """FAS cycles (Algorithm 2) from p0 until the relative / absolute tolerance; with cascadic=True the cycles
+        start from the nonlinear cascadic iterate (cascade), the tolerance still relative to ||R(p0)||."""
         o = self.o
         p = np.zeros(self.mesh.n_cells) if p0 is None else np.array(p0, dtype=np.float64)
         r0 = self.Rnorm(p)
-        rn = r0
-        self.stats.history = [r0]
+        if cascadic:
+            p = self.cascade(p)
+        rn = self.Rnorm(p)
+        self.stats.history = [r0, rn] if cascadic else [r0]
         maxc = o["max_cycles"] if max_cycles is None else max_cycles
         for _ in range(maxc):
             if rn <= o["tol_rel"] * r0 or rn <= o["tol_abs"]:

@@ -100,3 +100,17 @@ def test_early_exit_after_presmoothing():
     S, p = _solve(pr, H)
     assert S.stats.early_exit
     assert S.stats.history[-1] <= 1e-8 * S.stats.history[0]
+
+
+def test_cascadic_start_reaches_the_newton_solution():
+    """The nonlinear cascadic start (coarse problems solved bottom-up, corrections carried up with Algorithm 1)
+    followed by FAS cycles converges to the same p* as Newton."""
+    from oracle import hierarchy, newton
+    from synth.grids import problem_config
+    pr = problem_config("cart2d_32", scale=16)
+    H = hierarchy.build(pr.mesh, pr.opts)
+    pstar, _ = newton.solve(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face)
+    S = fas.FAS(H, pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, dict(pr.opts, tol_rel=1e-11))
+    p = S.solve(cascadic=True)
+    assert S.stats.history[1] < S.stats.history[0]          # the cascadic iterate is better than p0 here
+    assert np.linalg.norm(p - pstar) <= 1e-9 * np.linalg.norm(pstar)
