@@ -14,7 +14,10 @@ Smoothing on level 0 is, by default, one Picard step (Sec. 3.3.1): the frozen-co
 A(kappa(p_k)) dp = -R(p_k), which is the mixed Picard system of eq. picardian_system with the diagonal M eliminated.
 The alternative smoother ("jacobi") is nu damped nonlinear (point-Newton) Jacobi sweeps
 p_K <- p_K - omega R_K / J~_KK with J~_KK = max(dR_K/dp_K, d_K / 2), d_K the frozen-coefficient diagonal.
-Either update then passes through the pressure-change clamp (Sec. 4.1: max |dp| <= dp_clamp) and Algorithm 1. Smoothing on coarse levels is one Picard
+The smoother "picard_newton" takes the Picard step while ||R(p_k)|| > newton_switch ||R(p_0)|| (p_0 the iterate the
+solve started from) and a Newton step afterwards (Sec. 3.3.2 on level 0): J(p_k) dp = -R(p_k) with the exact
+Jacobian of the reduced TPFA residual (the reduced form of eq. jacobian_system).
+Every update then passes through the pressure-change clamp (Sec. 4.1: max |dp| <= dp_clamp) and Algorithm 1. Smoothing on coarse levels is one Picard
 step (Sec. 3.3.1) followed by the clamp (applied to the aggregate means Pi~ dp) and Algorithm 1.
 Residual comparisons in Algorithm 1 use the Euclidean norm of the level residual, with a strict ">".
 """
@@ -55,6 +58,7 @@ class Stats:
     history: list = field(default_factory=list)
     early_exit: bool = False
     fine_evals: int = 0
+    newton_steps: int = 0
 
 
 class FAS:
@@ -65,6 +69,7 @@ class FAS:
         self.f, self.g, self.o = f_cell, g_face, opts
         self.dofs = tpfa.flux_dofs(mesh)
         self.stats = Stats()
+        self.r0_ref = 0.0         # ||R(p_0)|| of the current solve (set by vcycle; 0: no Newton step)
 
     # ---- level 0 (reduced form) --------------------------------------------------------------------------------
     def R(self, p):
@@ -83,13 +88,30 @@ class FAS:
         """The frozen-coefficient TPFA matrix A(kappa(p)) with A(kappa(p)) p - rhs(kappa(p)) = R(p)."""
         return newton.picard_matrix(self.mesh, self.kind, self.a, p)
 
-    def smooth0(self, p, nu, r_p=None):
-        """One smoothing step on level 0: a Picard step (Sec. 3.3.1, default) or nu nonlinear Jacobi sweeps."""
+    def newton_update0(self, p, Rp=None):
+        """The level-0 Newton update: dp solving J(p) dp = -R(p), J the exact Jacobian of R (Sec. 3.3.2)."""
+        Rp = self.R(p) if Rp is None else Rp
+        J = tpfa.reduced_jacobian(self.mesh, self.kind, self.a, p, self.g).tocsc()
+        return -spla.spsolve(J, Rp)
+
+    def use_newton0(self, r_p):
+        """picard_newton: Newton once ||R(p_k)|| <= newton_switch ||R(p_0)|| (r0_ref, set by the cycle)."""
         o = self.o
-        if o.get("smoother", "picard") == "picard":
+        return o.get("smoother", "picard") == "picard_newton" and r_p <= o.get("newton_switch", 1e-2) * self.r0_ref
+
+    def smooth0(self, p, nu, r_p=None):
+        """One smoothing step on level 0: a Picard step (Sec. 3.3.1, default), a Newton step (picard_newton, once
+        the residual is below newton_switch times the initial one) or nu nonlinear Jacobi sweeps."""
+        o = self.o
+        smoother = o.get("smoother", "picard")
+        if smoother in ("picard", "picard_newton"):
             Rp = self.R(p)
-            dp = -spla.spsolve(self.picard_matrix0(p).tocsc(), Rp)
             r_p = float(np.linalg.norm(Rp)) if r_p is None else r_p
+            if self.use_newton0(r_p):
+                dp = self.newton_update0(p, Rp)
+                self.stats.newton_steps += 1
+            else:
+                dp = -spla.spsolve(self.picard_matrix0(p).tocsc(), Rp)
         else:
             q = p.copy()
             for _ in range(nu):
@@ -165,6 +187,7 @@ class FAS:
         """One Algorithm 2 cycle from level 0. Returns (p, ||R(p)||, stopped_after_presmoothing)."""
         o = self.o
         H = self.H
+        self.r0_ref = r0
         p, rn = self.smooth0(p, o["nu_pre"])
         if rn <= o["tol_rel"] * r0 or rn <= o["tol_abs"]:
             return p, rn, True

@@ -114,3 +114,72 @@ def test_cascadic_start_reaches_the_newton_solution():
     p = S.solve(cascadic=True)
     assert S.stats.history[1] < S.stats.history[0]          # the cascadic iterate is better than p0 here
     assert np.linalg.norm(p - pstar) <= 1e-9 * np.linalg.norm(pstar)
+
+
+def _fas(pr, H, **kw):
+    return fas.FAS(H, pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, dict(pr.opts, **kw))
+
+
+def test_newton_update_is_the_linearised_zero():
+    """The level-0 Newton update (Sec. 3.3.2) zeroes the first-order model: R(p + e dp) = (1 - e) R(p) + O(e^2),
+    checked by the second-order behaviour of the remainder as e halves (a wrong sign, a transposed or a missing
+    Jacobian term leaves an O(e) remainder)."""
+    pr = problem_config("chan3d_64", scale=6)
+    H = hierarchy.build(pr.mesh, pr.opts)
+    S = _fas(pr, H)
+    rng = np.random.default_rng(3)
+    p = rng.uniform(0.0, 1.0, pr.mesh.n_cells)
+    Rp = S.R(p)
+    dp = S.newton_update0(p)
+    rem = []
+    for e in (1e-2, 5e-3, 2.5e-3):
+        rem.append(np.linalg.norm(S.R(p + e * dp) - (1.0 - e) * Rp))
+    assert 3.5 <= rem[0] / rem[1] <= 4.5 and 3.5 <= rem[1] / rem[2] <= 4.5
+
+
+def test_newton_smoothing_converges_quadratically_near_the_solution():
+    """From p* + a small perturbation, successive level-0 Newton smoothing steps (switch = inf) square the error:
+    log(r_{k+1}) / log(r_k) near 2 (Picard steps only contract linearly)."""
+    pr = problem_config("cart2d_32", scale=12)
+    H = hierarchy.build(pr.mesh, pr.opts)
+    pstar, _ = newton.solve(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face)
+    S = _fas(pr, H, smoother="picard_newton", newton_switch=np.inf)
+    S.r0_ref = 1.0
+    rng = np.random.default_rng(5)
+    p = pstar + 0.05 * rng.standard_normal(pstar.size)
+    r = [S.Rnorm(p)]
+    for _ in range(3):
+        p, rn = S.smooth0(p, 1)
+        r.append(rn)
+    rel = np.array(r) / r[0]
+    assert S.stats.newton_steps == 3
+    assert rel[2] <= 5.0 * rel[1] ** 2 and rel[3] <= 5.0 * rel[2] ** 2 and rel[3] < 1e-9
+    P = _fas(pr, H)
+    q = pstar + 0.05 * rng.standard_normal(pstar.size)
+    rq = [P.Rnorm(q)]
+    for _ in range(3):
+        q, rn = P.smooth0(q, 1)
+        rq.append(rn)
+    # Picard contracts linearly (consecutive ratios alike); Newton's ratio collapses from step to step
+    assert rq[3] / rq[2] > 0.2 * rq[2] / rq[1]
+    assert r[3] / r[2] < 0.01 * r[2] / r[1]
+
+
+def test_picard_newton_switch_extremes_and_fixed_point():
+    """newton_switch = 0: bitwise the Picard FAS (no Newton step); the default switch reaches Newton's p* with fewer
+    cycles on the channelized case, where the Newton steps remove the linear tail of the Picard iteration."""
+    pr = problem_config("chan3d_64", scale=10)
+    H = hierarchy.build(pr.mesh, pr.opts)
+    S0 = _fas(pr, H)
+    p0 = S0.solve()
+    S1 = _fas(pr, H, smoother="picard_newton", newton_switch=0.0)
+    p1 = S1.solve()
+    assert np.array_equal(p0, p1) and S1.stats.newton_steps == 0
+    S2 = _fas(pr, H, smoother="picard_newton", newton_switch=1e-2, tol_rel=1e-12, tol_abs=1e-300)
+    p2 = S2.solve(max_cycles=40)
+    assert S2.stats.newton_steps >= 1
+    pstar, _ = newton.solve(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, dp_clamp=pr.opts["dp_clamp"])
+    assert np.linalg.norm(p2 - pstar) <= 1e-10 * np.linalg.norm(pstar)
+    S3 = _fas(pr, H, smoother="picard_newton", newton_switch=1e-2)
+    S3.solve()
+    assert S3.stats.cycles < S0.stats.cycles
