@@ -16,7 +16,9 @@ The alternative smoother ("jacobi") is nu damped nonlinear (point-Newton) Jacobi
 p_K <- p_K - omega R_K / J~_KK with J~_KK = max(dR_K/dp_K, d_K / 2), d_K the frozen-coefficient diagonal.
 The smoother "picard_newton" takes the Picard step while ||R(p_k)|| > newton_switch ||R(p_0)|| (p_0 the iterate the
 solve started from) and a Newton step afterwards (Sec. 3.3.2 on level 0): J(p_k) dp = -R(p_k) with the exact
-Jacobian of the reduced TPFA residual (the reduced form of eq. jacobian_system).
+Jacobian of the reduced TPFA residual (the reduced form of eq. jacobian_system). A Newton step that leaves more than
+NEWTON_KEEP = 1/2 of the residual it started from shows that the iterate is outside Newton's region of fast
+convergence: the rest of the solve then takes Picard steps (the switch is not tried again).
 Every update then passes through the pressure-change clamp (Sec. 4.1: max |dp| <= dp_clamp) and Algorithm 1. Smoothing on coarse levels is one Picard
 step (Sec. 3.3.1) followed by the clamp (applied to the aggregate means Pi~ dp) and Algorithm 1.
 Residual comparisons in Algorithm 1 use the Euclidean norm of the level residual, with a strict ">".
@@ -29,6 +31,8 @@ import numpy as np
 import scipy.sparse.linalg as spla
 
 from . import coarse, newton, tpfa
+
+NEWTON_KEEP = 0.5     # a Newton smoothing step must reduce the residual at least this much, else Picard from then on
 
 
 def backtracking(res_norm, x, dx, r_x, nmax, theta):
@@ -70,6 +74,7 @@ class FAS:
         self.dofs = tpfa.flux_dofs(mesh)
         self.stats = Stats()
         self.r0_ref = 0.0         # ||R(p_0)|| of the current solve (set by vcycle; 0: no Newton step)
+        self.newton_off = False   # set once a Newton step reduced the residual by less than NEWTON_KEEP
 
     # ---- level 0 (reduced form) --------------------------------------------------------------------------------
     def R(self, p):
@@ -97,17 +102,21 @@ class FAS:
     def use_newton0(self, r_p):
         """picard_newton: Newton once ||R(p_k)|| <= newton_switch ||R(p_0)|| (r0_ref, set by the cycle)."""
         o = self.o
-        return o.get("smoother", "picard") == "picard_newton" and r_p <= o.get("newton_switch", 1e-2) * self.r0_ref
+        return (o.get("smoother", "picard") == "picard_newton" and not self.newton_off
+                and r_p <= o.get("newton_switch", 1e-3) * self.r0_ref)
 
     def smooth0(self, p, nu, r_p=None):
         """One smoothing step on level 0: a Picard step (Sec. 3.3.1, default), a Newton step (picard_newton, once
-        the residual is below newton_switch times the initial one) or nu nonlinear Jacobi sweeps."""
+        the residual is below newton_switch times the initial one and while no Newton step of the solve has failed
+        to halve the residual) or nu nonlinear Jacobi sweeps."""
         o = self.o
         smoother = o.get("smoother", "picard")
+        newton_step = False
         if smoother in ("picard", "picard_newton"):
             Rp = self.R(p)
             r_p = float(np.linalg.norm(Rp)) if r_p is None else r_p
-            if self.use_newton0(r_p):
+            newton_step = self.use_newton0(r_p)
+            if newton_step:
                 dp = self.newton_update0(p, Rp)
                 self.stats.newton_steps += 1
             else:
@@ -122,6 +131,8 @@ class FAS:
             dp = dp * (o["dp_clamp"] / mx)
         r_p = self.Rnorm(p) if r_p is None else r_p
         pn, rn, _, _ = backtracking(self.Rnorm, p, dp, r_p, o["bt_nmax"], o["bt_theta"])
+        if newton_step and not rn <= NEWTON_KEEP * r_p:
+            self.newton_off = True
         return pn, rn
 
     def sigma0(self, p):
@@ -260,6 +271,7 @@ class FAS:
         start from the nonlinear cascadic iterate (cascade), the tolerance still relative to ||R(p0)||."""
         o = self.o
         p = np.zeros(self.mesh.n_cells) if p0 is None else np.array(p0, dtype=np.float64)
+        self.newton_off = False
         r0 = self.Rnorm(p)
         if cascadic:
             p = self.cascade(p)

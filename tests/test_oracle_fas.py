@@ -183,3 +183,20 @@ def test_picard_newton_switch_extremes_and_fixed_point():
     S3 = _fas(pr, H, smoother="picard_newton", newton_switch=1e-2)
     S3.solve()
     assert S3.stats.cycles < S0.stats.cycles
+
+
+def test_failed_newton_step_returns_to_picard():
+    """switch = inf on the channelized case: the first smoothing step is a Newton step from p = 0, outside Newton's
+    region of fast convergence, so it does not halve the residual; every later step is a Picard step and the solve
+    still reaches p*."""
+    pr = problem_config("chan3d_64", scale=11)
+    pr.opts = dict(pr.opts, n_levels=3, agg_size=[27, 6, 4], modes=[4, 3, 3])
+    H = hierarchy.build(pr.mesh, pr.opts)
+    S = _fas(pr, H, smoother="picard_newton", newton_switch=np.inf, tol_rel=1e-12, tol_abs=1e-300)
+    p = S.solve(max_cycles=40)
+    assert S.stats.newton_steps == 1 and S.newton_off
+    assert S.stats.history[1] > 0.5 * S.stats.history[0]
+    pstar, _ = newton.solve(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, dp_clamp=pr.opts["dp_clamp"])
+    assert np.linalg.norm(p - pstar) <= 1e-10 * np.linalg.norm(pstar)
+    S.solve()                       # a new solve clears the latch
+    assert S.stats.newton_steps == 2
