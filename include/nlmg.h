@@ -62,8 +62,9 @@ typedef struct {
   const double* face_area;
 } nlmg_mesh;
 
-/* Smoother on level 0. */
-enum { NLMG_SMOOTH_PICARD = 0, NLMG_SMOOTH_JACOBI = 1 };
+/* Smoother on level 0: a Picard step (Sec. 3.3.1), nu nonlinear Jacobi sweeps, or Picard steps followed by Newton
+ * steps (Sec. 3.3.2) once the residual is below newton_switch times the initial one. */
+enum { NLMG_SMOOTH_PICARD = 0, NLMG_SMOOTH_JACOBI = 1, NLMG_SMOOTH_PICARD_NEWTON = 2 };
 
 typedef struct {
   int32_t n_levels;          /* hierarchy levels including the fine one (1..8) */
@@ -89,6 +90,12 @@ typedef struct {
                                 solve concurrently (nlmg_solve_many, the request loop) can then run side by side.
                                 The grid, and with it the reduction order, follows from it: results are bitwise
                                 reproducible for a given max_sms */
+  double newton_switch;      /* NLMG_SMOOTH_PICARD_NEWTON: a level-0 smoothing step at p_k is a Newton step (exact
+                                Jacobian, persistent FP64 BiCGStab to lin_tol, clamp, Algorithm 1) once
+                                ||R(p_k)|| <= newton_switch ||R(p_0)||, a Picard step before (default 1e-3; >= 0).
+                                A Newton step that does not halve the residual returns the rest of the solve to
+                                Picard steps (cleared by the next solve and by nlmg_set_options; consecutive
+                                nlmg_vcycle calls carry it) */
   int32_t reserved[5];
 } nlmg_options;
 
@@ -102,6 +109,7 @@ typedef struct {
   int64_t kernel_launches;   /* CUDA kernels launched by the solve */
   int64_t lin_iters_level[8];/* PCG iterations per level */
   int32_t tol_tightened;     /* times the inner tolerances were divided by 100 after a cycle that stalled */
+  int32_t newton_steps;      /* level-0 Newton smoothing steps (NLMG_SMOOTH_PICARD_NEWTON) */
   int32_t history_len;
   double history[64];        /* ||R|| after each cycle (first entry = res0) */
 } nlmg_report;
@@ -215,6 +223,11 @@ nlmg_status nlmg_transfer(nlmg_ctx* ctx, int32_t level, int32_t op, const double
 nlmg_status nlmg_picard_update(nlmg_ctx* ctx, int32_t level, const double* x, const double* b, double* dx_out,
                                int32_t* iters);
 
+/* The level-0 Newton update (Sec. 3.3.2 in the reduced form): dx solving J(p) dx = -R(p) with the exact Jacobian of
+ * the TPFA residual, by the persistent FP64 BiCGStab of the Picard-then-Newton smoother to lin_tol (relative, on the
+ * Jacobi-scaled residual). p and dx_out are host arrays of n_cells; *iters (may be NULL) receives the iterations. */
+nlmg_status nlmg_newton_update(nlmg_ctx* ctx, const double* p, double* dx_out, int32_t* iters);
+
 /* One FAS cycle from level 0 (Algorithm 2) from p_in; r0 is the reference ||R(p_0)|| for the early exit. */
 nlmg_status nlmg_vcycle(nlmg_ctx* ctx, const double* p_in, double r0, double* p_out, double* res_out,
                         int32_t* early_exit);
@@ -269,10 +282,11 @@ void nlmg_server_destroy(nlmg_server* srv);
 /* Enables (1) or disables (0) CUDA-event timing of the hot kernels on the context stream and clears the counters.
  * Kernel ids: 0 = persistent fine CG solve (kp_fine_cg*), 1 = persistent coarse Picard step (kp_coarse_step:
  * coarse operator evaluations, hybridized CG, clamp and Algorithm 1 in one launch; kp_hyb_solve for the step calls),
- * 2 = fine TPFA residual (k_residual). */
+ * 2 = fine TPFA residual (k_residual), 3 = persistent fine BiCGStab of the Newton smoothing steps
+ * (kp_fine_bicgstab). */
 nlmg_status nlmg_profile(nlmg_ctx* ctx, int32_t enable);
 /* Launch count, summed event time, algorithmic bytes per launch (each streamed array counted once; the gathered
- * neighbour values counted once) and arithmetic per launch (FMA = 2 flops; kernel 0 only) of a profiled kernel
+ * neighbour values counted once) and arithmetic per launch (FMA = 2 flops; kernels 0 and 3 only) of a profiled kernel
  * since nlmg_profile(ctx, 1). Any output pointer may be NULL. */
 nlmg_status nlmg_profile_read(nlmg_ctx* ctx, int32_t kernel, int64_t* launches, double* total_ms,
                               double* bytes_per_launch, double* flops_per_launch);

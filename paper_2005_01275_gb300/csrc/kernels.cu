@@ -289,6 +289,21 @@ __global__ void k_jacobi_dinv(int n, const double* __restrict__ jdiag, const dou
   GRID_STRIDE(i, n) out[i] = 1.0 / fmax(jdiag[i], 0.5 * diagT[i]);
 }
 
+// Scaled Newton system of the level-0 BiCGStab: with D = jdinv = 1 / max(J_KK, d_K / 2) and S = D^1/2,
+// sS = S, jd = J_KK D_K on the diagonal and Js = S_K J_KL S_L off it (SELL layout; padding entries stay 0).
+__global__ void k_scale_jac(FineDev F, const double* __restrict__ jdiag, const double* __restrict__ Joff,
+                            const double* __restrict__ jdinv, double* __restrict__ Js, double* __restrict__ jd,
+                            double* __restrict__ sS) {
+  GRID_STRIDE(K, F.N) {
+    const double sK = sqrt(jdinv[K]);
+    sS[K] = sK;
+    jd[K] = jdiag[K] * jdinv[K];
+    const int w = F.sell_w[K >> 5];
+    int e = F.sell_off[K >> 5] + (K & 31);
+    for (int j = 0; j < w; ++j, e += 32) Js[e] = Joff[e] * sK * sqrt(jdinv[F.nbr[e]]);
+  }
+}
+
 // ---- measurement: FP64 FMA throughput (8 independent dependency chains per thread) ----------------------------
 __global__ void k_fp64_peak(int iters, double* out) {
   double a[8];
@@ -536,6 +551,11 @@ void launch_gmres_combine(cudaStream_t st, int n, int nk, const double* V, const
 void launch_jacobi_dinv(cudaStream_t st, int n, const double* jdiag, const double* diagT, double* out) {
   COUNT(1);
   k_jacobi_dinv<<<grid_for(n), kThreads, 0, st>>>(n, jdiag, diagT, out);
+}
+void launch_scale_jac(cudaStream_t st, const FineDev& F, const double* jdiag, const double* Joff,
+                      const double* jdinv, double* Js, double* jd, double* sS) {
+  COUNT(1);
+  k_scale_jac<<<grid_for(F.N), kThreads, 0, st>>>(F, jdiag, Joff, jdinv, Js, jd, sS);
 }
 bool measure_fp64_peak(double* gflops) {
   int dev = 0, sms = 0;

@@ -108,6 +108,8 @@ void launch_mdot(cudaStream_t st, int n, int nk, const double* V, const double* 
 void launch_orth_update(cudaStream_t st, int n, int nk, const double* V, const double* h, double* w, Reduce red);
 void launch_scale_vec(cudaStream_t st, int n, const double* x, double s, double* y);
 void launch_jacobi_dinv(cudaStream_t st, int n, const double* jdiag, const double* diagT, double* out);
+void launch_scale_jac(cudaStream_t st, const FineDev& F, const double* jdiag, const double* Joff,
+                      const double* jdinv, double* Js, double* jd, double* sS);
 void launch_gmres_combine(cudaStream_t st, int n, int nk, const double* V, const double* y, const double* dinv,
                           double* x);
 void launch_jacobi_update(cudaStream_t st, int n, const double* q, const double* R, const double* jdiag,

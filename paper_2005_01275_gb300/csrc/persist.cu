@@ -686,6 +686,118 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg2_reg(FineDev F, const T*
   }
 }
 
+// ---- fine level: Newton update J dx = bscale * b with the exact Jacobian ---------------------------------------
+// Row K of the scaled Jacobian applied to v: jd_K v_K + sum_e Js_e v_L(e) (SELL-32 layout; padding entries are 0).
+__device__ __forceinline__ double jac_row(const FineDev& F, const double* __restrict__ Js, double jdK, const double* v,
+                                          int K) {
+  const int s = K >> 5, lane = K & 31;
+  double acc = jdK * __ldcg(&v[K]);
+  const int w = F.sell_w[s];
+  int e = F.sell_off[s] + lane;
+  int j = 0;
+  if (w <= 8) {
+    int Ls[8];
+    double Jv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (u < w) {
+        Ls[u] = F.nbr[e + 32 * u];
+        Jv[u] = Js[e + 32 * u];
+      }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (u < w) acc = fma(Jv[u], __ldcg(&v[Ls[u]]), acc);
+    j = w;
+  }
+  for (e += 32 * j; j < w; ++j, e += 32) acc = fma(Js[e], __ldcg(&v[F.nbr[e]]), acc);
+  return acc;
+}
+
+// BiCGStab (van der Vorst) in FP64 on the symmetrically scaled Newton system (S J S) y = S bscale b, dx = S y, with
+// S = D^1/2 and D = 1 / max(J_KK, d_K / 2) the weights of the nonlinear Jacobi smoother (d_K the frozen-coefficient
+// diagonal); jd = J_KK D_K and Js = S_K J_KL S_L are formed before the launch. The Jacobian is not symmetric, so CG
+// does not apply; BiCGStab's short recurrences keep the whole solve in one persistent launch with a fixed amount of
+// memory. One iteration: v = A p and (rh, v) give alpha; s = r - alpha v is published; t = A s, (t, s) and (t, t)
+// give omega; y += alpha p + omega s, r = s - omega t, (rh, r) and (r, r) give rho and beta; p = r + beta (p - omega
+// v) is published: three reductions and two plain barriers. The stopping test is ||r|| <= tol ||r_0|| on the scaled
+// residual, as for the CG; a breakdown (alpha, omega or rho zero) ends the solve with the current y.
+__global__ void __launch_bounds__(kPThreads) kp_fine_bicgstab(FineDev F, const double* __restrict__ Js,
+                                                              const double* __restrict__ jd,
+                                                              const double* __restrict__ sS,
+                                                              const double* __restrict__ b, double bscale,
+                                                              double* __restrict__ dx, double* __restrict__ y,
+                                                              double* __restrict__ r, double* __restrict__ rh,
+                                                              double* p, double* __restrict__ v, double* s,
+                                                              double* __restrict__ t, double* partial, GridSync gs,
+                                                              double tol, int maxit, PcgResult* res) {
+  __shared__ double sm[kSmDoubles];
+  Grid g{gs, partial, sm, 0u};
+  double a1[1] = {0.0};
+  GSTRIDE(i, F.N) {
+    const double ri = sS[i] * bscale * b[i];
+    y[i] = 0.0;
+    r[i] = ri;
+    rh[i] = ri;
+    p[i] = ri;
+    a1[0] = fma(ri, ri, a1[0]);
+  }
+  if (!grid_sum<1>(g, a1)) return;   // its barrier also publishes p
+  const double rr0 = a1[0];
+  double rr = rr0, rho = rr0;
+  const double tol2 = tol * tol * rr0;
+  int it = 0;
+  while (rr0 > 0.0 && rr > tol2 && it < maxit) {
+    double a2[2] = {0.0, 0.0};
+    GSTRIDE(K, F.N) {
+      const double vK = jac_row(F, Js, jd[K], p, K);
+      v[K] = vK;
+      a2[0] = fma(rh[K], vK, a2[0]);
+    }
+    if (!grid_sum_x<1, 1>(g, a2, [&](double* o) { o[1] = o[0] != 0.0 ? rho / o[0] : 0.0; })) return;
+    const double alpha = a2[1];
+    if (!(alpha != 0.0)) break;
+    GSTRIDE(K, F.N) s[K] = r[K] - alpha * v[K];
+    if (!grid_barrier(g)) return;
+    double a3[3] = {0.0, 0.0, 0.0};
+    GSTRIDE(K, F.N) {
+      const double tK = jac_row(F, Js, jd[K], s, K);
+      const double sK = s[K];
+      t[K] = tK;
+      a3[0] = fma(tK, sK, a3[0]);
+      a3[1] = fma(tK, tK, a3[1]);
+    }
+    if (!grid_sum_x<2, 1>(g, a3, [&](double* o) { o[2] = o[1] != 0.0 ? o[0] / o[1] : 0.0; })) return;
+    const double omega = a3[2];
+    double a4[3] = {0.0, 0.0, 0.0};
+    GSTRIDE(K, F.N) {
+      const double sK = s[K];
+      y[K] += alpha * p[K] + omega * sK;
+      const double rK = sK - omega * t[K];
+      r[K] = rK;
+      a4[0] = fma(rh[K], rK, a4[0]);
+      a4[1] = fma(rK, rK, a4[1]);
+    }
+    if (!grid_sum_x<2, 1>(g, a4, [&](double* o) {
+          o[2] = rho != 0.0 && omega != 0.0 ? (o[0] / rho) * (alpha / omega) : 0.0;
+        }))
+      return;
+    ++it;
+    rr = a4[1];
+    const double beta = a4[2];
+    const bool stop = !(omega != 0.0) || !(a4[0] != 0.0);
+    rho = a4[0];
+    if (stop) break;
+    GSTRIDE(K, F.N) p[K] = r[K] + beta * (p[K] - omega * v[K]);
+    if (!grid_barrier(g)) return;
+  }
+  GSTRIDE(i, F.N) dx[i] = sS[i] * y[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    res->iters = it;
+    res->rr0 = rr0;
+    res->rr = rr;
+  }
+}
+
 // ---- coarse level: hybridized saddle solve (rhs, Jacobi diagonal, CG on H lambda = xi, local recovery) ------
 // The solve of one frozen-coefficient coarse saddle as a device function of a persistent grid (g.sm: kSmDoubles of
 // shared memory). kapc, bs and bp may have been written earlier in the same launch, so they are read through L2.
@@ -1088,6 +1200,19 @@ cudaError_t launch_fine_cg_pipe(cudaStream_t st, const FineDev& F, const T* Ts, 
   void* args[] = {(void*)&F, (void*)&Ts, (void*)&sdiag, (void*)&b, (void*)&bscale, (void*)&dx, (void*)&y,
                   (void*)&r, (void*)&wa, (void*)&wb, (void*)&z, (void*)&sv, (void*)&p, (void*)&partial, (void*)&gs,
                   (void*)&tol, (void*)&maxit, (void*)&res};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
+}
+cudaError_t launch_fine_bicgstab(cudaStream_t st, const FineDev& F, const double* Js, const double* jd,
+                                 const double* sS, const double* b, double bscale, double* dx, double* work,
+                                 double* partial, GridSync gs, double tol, int maxit, PcgResult* res) {
+  const void* fn = (const void*)kp_fine_bicgstab;
+  const int grid = coop_grid(fn, F.N, gs.sm_cap);
+  const size_t n = (size_t)F.N;
+  double *y = work, *r = work + n, *rh = work + 2 * n, *p = work + 3 * n, *v = work + 4 * n, *s = work + 5 * n,
+         *t = work + 6 * n;
+  void* args[] = {(void*)&F, (void*)&Js, (void*)&jd, (void*)&sS, (void*)&b, (void*)&bscale, (void*)&dx,
+                  (void*)&y, (void*)&r, (void*)&rh, (void*)&p, (void*)&v, (void*)&s, (void*)&t, (void*)&partial,
+                  (void*)&gs, (void*)&tol, (void*)&maxit, (void*)&res};
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
 }
 // Register-resident pipelined CG if every thread holds at most 4 cells on the grid the launch gets; returns

@@ -46,6 +46,12 @@ cudaError_t launch_fine_cg2_reg(cudaStream_t st, const FineDev& F, const T* Ts, 
                                 double bscale, double* dx, T* rpub, double* partial, GridSync gs, double tol,
                                 int maxit, PcgResult* res);
 
+// Persistent FP64 BiCGStab for the level-0 Newton system J dx = bscale b on the scaled Jacobian (Js off the
+// diagonal in the SELL layout, jd on it, sS = S per cell); work holds 7 n_cells doubles.
+cudaError_t launch_fine_bicgstab(cudaStream_t st, const FineDev& F, const double* Js, const double* jd,
+                                 const double* sS, const double* b, double bscale, double* dx, double* work,
+                                 double* partial, GridSync gs, double tol, int maxit, PcgResult* res);
+
 // Extra per-lambda vectors of the pipelined hybridized CG (w = H u, z, s, and m = M w double-buffered).
 template <class T>
 struct HybPipeBufs {

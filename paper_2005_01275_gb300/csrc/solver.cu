@@ -118,12 +118,18 @@ struct nlmg_ctx {
   static constexpr int kGmresM = 30;
   double *Joff = nullptr, *jdinv = nullptr, *gV = nullptr, *gw = nullptr, *gu = nullptr, *gr = nullptr,
          *gh = nullptr, *h_gh = nullptr;
+  // Newton smoothing steps: the scaled Jacobian of the BiCGStab (off-diagonal, diagonal, S); its 7 work vectors
+  // are the first 7 of the GMRES basis
+  double *Js = nullptr, *jdS = nullptr, *jsS = nullptr;
   float *Ts32 = nullptr, *fy = nullptr, *fr = nullptr, *fpa = nullptr, *fpb = nullptr, *fq = nullptr;
   FineState cur, t1, t2;
   bool have_data = false;
   double tol_rel = 1e-8, tol_abs = 1e-10;   // outer tolerances, also used on the coarsest level
   double lin_tol_eff = 1e-2, coarse_lin_tol_eff = 1e-1;   // inner tolerances of the running solve
   int tightenings = 0;
+  double r0_ref = 0.0;             // ||R(p_0)|| of the running solve (the Picard-then-Newton switch)
+  bool newton_off = false;         // a Newton smoothing step of the running solve failed to halve the residual
+  long long newton_steps = 0;      // level-0 Newton smoothing steps of the running solve
   int last_fine_kind = 0;          // variant of the last level-0 CG launch (0 two-barrier, 1 pipelined, 2 registers)
   int auto_sm_cap = 0;            // SM share chosen by nlmg_solve_many while instances run side by side
   void reset_inner_tols() {
@@ -593,6 +599,53 @@ void alloc_newton(nlmg_ctx* c) {
   c->gr = c->dalloc<double>(N);
   c->gh = c->dalloc<double>(3 * 64);
   CK(cudaMallocHost(&c->h_gh, 3 * 64 * sizeof(double)));
+  c->Js = c->dalloc<double>(c->F.nnz);
+  c->jdS = c->dalloc<double>(N);
+  c->jsS = c->dalloc<double>(N);
+}
+
+// The exact Jacobian at c->cur.p (Sec. 3.3.2 on level 0): kappa and kappa' per cell, the residual kernel's
+// Jacobian diagonal and off-diagonal entries (SELL layout), the frozen diagonal d and the Jacobi weights
+// 1 / max(J_KK, d_K / 2).
+void newton_linearize(nlmg_ctx* c) {
+  alloc_newton(c);
+  const int N = c->F.N;
+  launch_kappa(c->st, N, c->cur.p, nullptr, 0.0, c->cur.p, c->t2.kap, c->dkap, c->kind, c->a);
+  launch_residual(c->st, c->F, c->cur.p, c->t2.kap, c->dkap, c->g, c->rhs, c->t2.R, nullptr, nullptr, c->diagT,
+                  c->jdiag, c->red(S_NORM2B), c->Joff);
+  launch_jacobi_dinv(c->st, N, c->jdiag, c->diagT, c->jdinv);
+}
+
+// Persistent FP64 BiCGStab on the Jacobi-scaled Newton system J dx = -R (J from newton_linearize) to lin_tol_eff;
+// dx -> c->cx.
+int fine_bicgstab(nlmg_ctx* c, const double* R) {
+  GridSync gs{c->d_bar, &c->d_res->err, c->sm_cap};
+  CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->st));
+  CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
+  launch_scale_jac(c->st, c->F, c->jdiag, c->Joff, c->jdinv, c->Js, c->jdS, c->jsS);
+  const int pi = c->prof_begin(3);
+  CK(launch_fine_bicgstab(c->st, c->F, c->Js, c->jdS, c->jsS, R, -1.0, c->cx, c->gV, c->d_partial, gs,
+                          c->lin_tol_eff, c->opt.lin_maxit, c->d_res));
+  c->prof_end(pi);
+  count_launch(1);
+  CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(PcgResult), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (c->h_res->err) throw Error(NLMG_ETIMEOUT, "grid barrier wait gave up in the fine BiCGStab kernel");
+  if (!std::isfinite(c->h_res->rr)) throw Error(NLMG_EDIVERGED, "non-finite value in the level-0 Newton solve");
+  const int it = c->h_res->iters;
+  if (pi >= 0) {
+    // Algorithmic bytes: once, b and S read, y, r, rh, p written, then S and y read and dx written (10 vectors).
+    // Per iteration the scaled Jacobian (values, indices, diagonal) twice, and the vectors of the five passes:
+    // p gathered, rh read, v written; r, v read, s written; s gathered, t written; s, y, p, t, rh read, y, r
+    // written; r, p, v read, p written (19 vectors). Flops: two products (2 per stored entry, diagonal included)
+    // and 11 FMAs per cell per iteration.
+    const double N = c->F.N, nnz = (double)c->sh->nnz_real;
+    c->prof.bytes[3] += 10.0 * 8.0 * N + it * (2.0 * (12.0 * nnz + 8.0 * N) + 19.0 * 8.0 * N);
+    c->prof.flops[3] += it * (4.0 * (nnz + N) + 22.0 * N);
+  }
+  c->lin_iters += it;
+  c->lin_iters_level[0] += it;
+  return it;
 }
 
 // Restarted GMRES(30) with right Jacobi preconditioning for J dx = -R (Sec. 3.3.2's linear system on level 0, the
@@ -688,12 +741,8 @@ int fine_gmres(nlmg_ctx* c, const double* R) {
 
 // One single-level Newton step (Sec. 3.3.2 on level 0): exact Jacobian, GMRES, clamp, Algorithm 1.
 void newton_step(nlmg_ctx* c) {
-  alloc_newton(c);
   const int N = c->F.N;
-  launch_kappa(c->st, N, c->cur.p, nullptr, 0.0, c->cur.p, c->t2.kap, c->dkap, c->kind, c->a);
-  launch_residual(c->st, c->F, c->cur.p, c->t2.kap, c->dkap, c->g, c->rhs, c->t2.R, nullptr, nullptr, c->diagT,
-                  c->jdiag, c->red(S_NORM2B), c->Joff);
-  launch_jacobi_dinv(c->st, N, c->jdiag, c->diagT, c->jdinv);
+  newton_linearize(c);
   fine_gmres(c, c->cur.R);
   double s0 = 1.0;
   if (c->opt.dp_clamp > 0) {
@@ -704,12 +753,26 @@ void newton_step(nlmg_ctx* c) {
   backtrack0(c, c->cx, s0);
 }
 
-// One smoothing step on level 0 (Picard or nonlinear Jacobi), then the clamp and Algorithm 1.
+// A Newton smoothing step that leaves more than this fraction of the residual it started from shows that the
+// iterate is outside Newton's region of fast convergence: the rest of the solve takes Picard steps.
+constexpr double kNewtonKeep = 0.5;
+
+// One smoothing step on level 0 (Picard, Newton or nonlinear Jacobi), then the clamp and Algorithm 1. With the
+// Picard-then-Newton smoother the step is a Newton step once ||R(p_k)|| <= newton_switch ||R(p_0)||, unless an
+// earlier Newton step of the solve failed to halve the residual.
 void smooth0(nlmg_ctx* c, int nu) {
   const nlmg_options& o = c->opt;
   const int N = c->F.N;
   const double* dp = nullptr;
-  if (o.smoother == NLMG_SMOOTH_PICARD) {
+  const double rn_in = c->cur.rn;
+  const bool newton =
+      o.smoother == NLMG_SMOOTH_PICARD_NEWTON && !c->newton_off && rn_in <= o.newton_switch * c->r0_ref;
+  if (newton) {
+    newton_linearize(c);
+    fine_bicgstab(c, c->cur.R);
+    dp = c->cx;
+    c->newton_steps++;
+  } else if (o.smoother == NLMG_SMOOTH_PICARD || o.smoother == NLMG_SMOOTH_PICARD_NEWTON) {
     launch_residual(c->st, c->F, c->cur.p, c->cur.kap, nullptr, c->g, c->rhs, c->t2.R, c->Tval, c->dinv, c->diagT,
                     nullptr, c->red(S_NORM2B));
     fine_pcg(c, c->cur.R);
@@ -737,6 +800,7 @@ void smooth0(nlmg_ctx* c, int nu) {
     if (mx > o.dp_clamp) s0 = o.dp_clamp / mx;
   }
   backtrack0(c, dp, s0);
+  if (newton && !(c->cur.rn <= kNewtonKeep * rn_in)) c->newton_off = true;
 }
 
 // ---------------------------------------------------------------------------------------------------------------
@@ -984,6 +1048,7 @@ nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double
   CK(cudaEventRecord(e0, c->st));
   c->fine_evals = 0;
   c->lin_iters = 0;
+  c->newton_steps = 0;
   for (auto& v : c->lin_iters_level) v = 0;
   const long long launches0 = launch_count_thread();
   c->tol_rel = tol_rel;
@@ -994,6 +1059,8 @@ nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double
   else
     CK(cudaMemsetAsync(c->cur.p, 0, (size_t)N * sizeof(double), c->st));
   double r0 = fine_eval(c, c->cur.p, nullptr, 0.0, c->cur);
+  c->r0_ref = r0;
+  c->newton_off = false;
   nlmg_report R{};
   R.res0 = r0;
   R.history[0] = r0;
@@ -1050,6 +1117,7 @@ nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double
   R.kernel_launches = launch_count_thread() - launches0;
   for (int l = 0; l < 8; ++l) R.lin_iters_level[l] = c->lin_iters_level[l];
   R.tol_tightened = c->tightenings;
+  R.newton_steps = (int32_t)c->newton_steps;
   c->prof_flush();
   if (rep) *rep = R;
   return st;
@@ -1092,9 +1160,17 @@ void nlmg_default_options(nlmg_options* o) {
   o->coarse_lin_tol = 1e-1;
   o->lin_precision = 0;
   o->setup_threads = 0;
+  o->newton_switch = 1e-3;
 }
 
 static thread_local std::string g_setup_error;   // message of the calling thread's last failed setup
+
+// The options a solve reads (those fixed at setup are checked there).
+static bool solver_options_ok(const nlmg_options& o) {
+  return o.nu_pre >= 0 && o.nu_post >= 0 && o.bt_nmax >= 0 && o.omega > 0 && o.coarsest_steps >= 0 &&
+         (o.lin_precision == 0 || o.lin_precision == 1) && o.max_sms >= 0 && o.smoother >= NLMG_SMOOTH_PICARD &&
+         o.smoother <= NLMG_SMOOTH_PICARD_NEWTON && o.newton_switch >= 0.0;
+}
 
 static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlmg_options* opt,
                               nlmg_ctx** out, bool device);
@@ -1137,6 +1213,10 @@ static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, co
       !mesh->face_cells || !mesh->half_trans || !mesh->face_bc || !mesh->face_area)
     return NLMG_EINVAL;
   if (opt->n_levels < 1 || opt->n_levels > 8 || (kappa->kind != 0 && kappa->kind != 1)) return NLMG_EINVAL;
+  if (!solver_options_ok(*opt)) {
+    g_setup_error = "bad solver option";
+    return NLMG_EINVAL;
+  }
   nlmg_ctx* c = new nlmg_ctx();
   nlmg_status s = guarded(c, [&]() -> nlmg_status {
     c->opt = *opt;
@@ -1281,13 +1361,12 @@ nlmg_status nlmg_set_options(nlmg_ctx* c, const nlmg_options* opt) {
     for (int l = 0; l + 1 < c->opt.n_levels; ++l)
       if (opt->agg_size[l] != c->opt.agg_size[l] || opt->modes[l] != c->opt.modes[l])
         throw Error(NLMG_EINVAL, "agg_size and modes are fixed at setup");
-    if (opt->nu_pre < 0 || opt->nu_post < 0 || opt->bt_nmax < 0 || !(opt->omega > 0) || opt->coarsest_steps < 0 ||
-        (opt->lin_precision != 0 && opt->lin_precision != 1) || opt->max_sms < 0)
-      throw Error(NLMG_EINVAL, "bad solver option");
+    if (!solver_options_ok(*opt)) throw Error(NLMG_EINVAL, "bad solver option");
     const int threads = c->opt.setup_threads;
     c->opt = *opt;
     c->opt.setup_threads = threads;
     c->reset_inner_tols();
+    c->newton_off = false;
     return NLMG_OK;
   });
 }
@@ -1552,6 +1631,22 @@ nlmg_status nlmg_picard_update(nlmg_ctx* c, int32_t level, const double* x, cons
   });
 }
 
+nlmg_status nlmg_newton_update(nlmg_ctx* c, const double* p, double* dx_out, int32_t* iters) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_data(c);
+    if (!p || !dx_out) throw Error(NLMG_EINVAL, "null argument");
+    c->reset_inner_tols();
+    CK(cudaMemcpyAsync(c->fdp, p, (size_t)c->F.N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    fine_eval(c, c->fdp, nullptr, 0.0, c->cur);
+    newton_linearize(c);
+    const int it = fine_bicgstab(c, c->cur.R);
+    CK(cudaMemcpyAsync(dx_out, c->cx, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (iters) *iters = it;
+    return NLMG_OK;
+  });
+}
+
 nlmg_status nlmg_vcycle(nlmg_ctx* c, const double* p_in, double r0, double* p_out, double* res_out,
                         int32_t* early_exit) {
   return guarded(c, [&]() -> nlmg_status {
@@ -1561,6 +1656,7 @@ nlmg_status nlmg_vcycle(nlmg_ctx* c, const double* p_in, double r0, double* p_ou
     fine_eval(c, c->fdp, nullptr, 0.0, c->cur);
     c->tol_rel = 1e-8;
     c->tol_abs = 1e-10;
+    c->r0_ref = r0;
     bool e = vcycle(c, r0, c->tol_rel, c->tol_abs);
     CK(cudaMemcpyAsync(p_out, c->cur.p, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
@@ -1643,7 +1739,7 @@ nlmg_status nlmg_profile_read(nlmg_ctx* c, int32_t kernel, int64_t* launches, do
                               double* bytes_per_launch, double* flops_per_launch) {
   return guarded(c, [&]() -> nlmg_status {
     need_device(c);
-    if (kernel < 0 || kernel > 2) throw Error(NLMG_EINVAL, "kernel id");
+    if (kernel < 0 || kernel > 3) throw Error(NLMG_EINVAL, "kernel id");
     c->prof_flush();
     if (launches) *launches = c->prof.n[kernel];
     if (total_ms) *total_ms = c->prof.ms[kernel];
@@ -1651,7 +1747,7 @@ nlmg_status nlmg_profile_read(nlmg_ctx* c, int32_t kernel, int64_t* launches, do
     // counted once (they are the same vector); SELL padding is not counted
     const double N = c->F.N, nnz = (double)c->sh->nnz_real;
     double b = 0.0;
-    if (kernel == 0 || kernel == 1) b = c->prof.n[kernel] ? c->prof.bytes[kernel] / c->prof.n[kernel] : 0.0;
+    if (kernel == 0 || kernel == 1 || kernel == 3) b = c->prof.n[kernel] ? c->prof.bytes[kernel] / c->prof.n[kernel] : 0.0;
     if (kernel == 2) b = 20.0 * nnz + 8.0 * N * 4;                          // nbr + 2 ups, q, kap, rhs, R
     if (bytes_per_launch) *bytes_per_launch = b;
     if (flops_per_launch) *flops_per_launch = c->prof.n[kernel] ? c->prof.flops[kernel] / c->prof.n[kernel] : 0.0;

@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libnlmg.so")
 
 OK, EINVAL, ENOMEM, ENOCONV, EDIVERGED, ETIMEOUT, ECUDA, EUNSUPPORTED = range(8)
 KAPPA_EXP, KAPPA_INV1P2 = 0, 1
-SMOOTH_PICARD, SMOOTH_JACOBI = 0, 1
+SMOOTH_PICARD, SMOOTH_JACOBI, SMOOTH_PICARD_NEWTON = 0, 1, 2
+_SMOOTHERS = {"picard": SMOOTH_PICARD, "jacobi": SMOOTH_JACOBI, "picard_newton": SMOOTH_PICARD_NEWTON}
 PROJECT, RESTRICT, PROLONG = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOCONV", 4: "EDIVERGED", 5: "ETIMEOUT", 6: "ECUDA",
                 7: "EUNSUPPORTED"}
@@ -38,20 +39,23 @@ class Options(C.Structure):
                 ("coarsest_steps", C.c_int32), ("coarsest_tol", C.c_double), ("lin_tol", C.c_double),
                 ("lin_maxit", C.c_int32),
                 ("coarse_lin_tol", C.c_double), ("lin_precision", C.c_int32),
-                ("setup_threads", C.c_int32), ("max_sms", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("setup_threads", C.c_int32), ("max_sms", C.c_int32), ("newton_switch", C.c_double),
+                ("reserved", C.c_int32 * 5)]
 
 
 class Report(C.Structure):
     _fields_ = [("cycles", C.c_int32), ("early_exit", C.c_int32), ("res0", C.c_double), ("res", C.c_double),
                 ("solve_ms", C.c_double), ("fine_evals", C.c_int64), ("lin_iters", C.c_int64),
                 ("kernel_launches", C.c_int64), ("lin_iters_level", C.c_int64 * 8),
-                ("tol_tightened", C.c_int32), ("history_len", C.c_int32), ("history", C.c_double * 64)]
+                ("tol_tightened", C.c_int32), ("newton_steps", C.c_int32), ("history_len", C.c_int32),
+                ("history", C.c_double * 64)]
 
     def as_dict(self):
         return dict(cycles=self.cycles, early_exit=bool(self.early_exit), res0=self.res0, res=self.res,
                     solve_ms=self.solve_ms, fine_evals=self.fine_evals, lin_iters=self.lin_iters,
                     kernel_launches=self.kernel_launches, lin_iters_level=list(self.lin_iters_level),
-                    tol_tightened=self.tol_tightened, history=list(self.history[:self.history_len]))
+                    tol_tightened=self.tol_tightened, newton_steps=self.newton_steps,
+                    history=list(self.history[:self.history_len]))
 
 
 class ServerOptions(C.Structure):
@@ -94,6 +98,7 @@ SIGNATURES = {
     "nlmg_level_apply": (C.c_int, [_P, C.c_int32, _D, _D]),
     "nlmg_transfer": (C.c_int, [_P, C.c_int32, C.c_int32, _D, _D]),
     "nlmg_picard_update": (C.c_int, [_P, C.c_int32, _D, _D, _D, _I]),
+    "nlmg_newton_update": (C.c_int, [_P, _D, _D, _I]),
     "nlmg_vcycle": (C.c_int, [_P, _D, C.c_double, _D, _D, _I]),
     "nlmg_level_info_get": (C.c_int, [_P, C.c_int32, C.POINTER(LevelInfo)]),
     "nlmg_get_aggregates": (C.c_int, [_P, C.c_int32, _I, _I]),
@@ -162,11 +167,11 @@ def options_from_dict(d):
     """Options from the dictionary used by the synthetic problem configurations."""
     keep = {k: d[k] for k in ("n_levels", "agg_size", "modes", "nu_pre", "nu_post", "omega", "bt_nmax", "bt_theta",
                               "dp_clamp", "coarsest_steps", "coarsest_tol", "lin_tol", "lin_maxit", "coarse_lin_tol",
-                              "lin_precision", "max_sms") if k in d}
+                              "lin_precision", "max_sms", "newton_switch") if k in d}
     if "lin_tol" in d and "coarse_lin_tol" not in d:
         keep["coarse_lin_tol"] = d["lin_tol"]       # one tolerance given: use it on every level
     if "smoother" in d:
-        keep["smoother"] = SMOOTH_PICARD if d["smoother"] == "picard" else SMOOTH_JACOBI
+        keep["smoother"] = _SMOOTHERS[d["smoother"]]
     return default_options(**keep)
 
 
@@ -208,7 +213,7 @@ class Context:
         """Change solver options (not the hierarchy ones) for the following solves."""
         o = Options.from_buffer_copy(self.opts)
         for k, v in changes.items():
-            setattr(o, k, v)
+            setattr(o, k, _SMOOTHERS[v] if k == "smoother" and isinstance(v, str) else v)
         self._check(lib().nlmg_set_options(self.h, C.byref(o)))
         self.opts = o
 
@@ -324,6 +329,14 @@ class Context:
         out = np.zeros_like(x)
         it = C.c_int32(0)
         self._check(lib().nlmg_picard_update(self.h, l, _dp(x), _dp(b), _dp(out), C.byref(it)))
+        return out, it.value
+
+    def newton_update(self, p):
+        """dx solving J(p) dx = -R(p) (level-0 Newton update by the persistent BiCGStab) and its iterations."""
+        p = _f64(p, self.n_cells)
+        out = np.zeros_like(p)
+        it = C.c_int32(0)
+        self._check(lib().nlmg_newton_update(self.h, _dp(p), _dp(out), C.byref(it)))
         return out, it.value
 
     def vcycle(self, p, r0):
