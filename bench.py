@@ -2,8 +2,10 @@
 """Benchmark: FP64 FAS solves of the 64^3 channelized TPFA problem on GB300, through the C ABI.
 
 One step = one full nonlinear solve (FAS V-cycles, Algorithm 2) from p = 0 to relative residual 1e-8 on
-device-resident inputs; the hierarchy is built once before timing (setup time reported separately). Prints one JSON
-line. `--impl reference` times the FP64 CPU oracle instead (on a bounded sample of the same workload).
+device-resident inputs; the hierarchy is built once before timing (setup time reported separately). Level-0
+smoothing is Picard steps, then Newton steps once the residual is below 1e-3 of the initial one (`--smoother
+picard` for Picard steps throughout; both numbers are reported). Prints one JSON line. `--impl reference` times the
+FP64 CPU oracle with the same smoother instead (on a bounded sample of the same workload).
 """
 from __future__ import annotations
 
@@ -19,14 +21,63 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "solves/s to rel. residual 1e-8 (batched mixed vs plain FP64); V-cycle DOF/s"
-WORKLOAD = ("chan3d_64: 64^3 hexahedral TPFA, channelized K over 6 decades, kappa = exp(2 p), 3-level FAS "
-            "(aggregates 64 then 8, 4 modes), FP64 Picard smoothing, tol 1e-8")
+SMOOTHER_TEXT = {"picard": "FP64 Picard smoothing",
+                 "picard_newton": "FP64 Picard-then-Newton level-0 smoothing (switch at 1e-3)"}
+
+
+def workload_name(scale, smoother):
+    return ("chan3d_%d: %d^3 hexahedral TPFA, channelized K over 6 decades, kappa = exp(2 p), 3-level FAS "
+            "(aggregates 64 then 8, 4 modes), %s, tol 1e-8" % (scale, scale, SMOOTHER_TEXT[smoother]))
 SAMPLE_SCALE = 16          # side of the bounded CPU sample of the same generator
 
 
-# DRAM bytes (read + write) of one launch of the default level-0 CG kernel on the 64^3 workload
-# (kp_fine_cg_reg<double, 4>), from an ncu --set full capture: valid for that kernel and workload only.
-FINE_CG_DRAM_BYTES_64 = 23.015680e6 + 91.648e3
+# DRAM bytes (read + write) per launch on the 64^3 workload with the default tolerances, from ncu captures of the
+# kernels as they are now (averaged over the launches of one solve where they differ): valid for that kernel, that
+# workload and those options only, else the traffic is reported as null.
+FINE_CG_DRAM_BYTES_64 = 23.015680e6 + 91.648e3          # kp_fine_cg_reg<double, 4>
+COARSE_STEP_DRAM_BYTES_64 = 25.4458e6                   # kp_coarse_step<double>, mean over the launches of a solve
+BICGSTAB_DRAM_BYTES_64 = 25.237e6                       # kp_fine_bicgstab
+DRAM_BYTES_64 = {0: FINE_CG_DRAM_BYTES_64, 1: COARSE_STEP_DRAM_BYTES_64, 3: BICGSTAB_DRAM_BYTES_64}
+
+KERNELS = {0: ("kp_fine_cg_reg<double, 4> (persistent register-resident pipelined Jacobi-scaled CG of the level-0 "
+               "Picard step)", "kp_fine_cg* (level-0 Picard CG)"),
+           1: ("kp_coarse_step<double> (fused coarse Picard step: coarse operator evaluations, pipelined hybridized "
+               "CG, clamp and Algorithm 1 in one persistent launch)",) * 2,
+           3: ("kp_fine_bicgstab (persistent FP64 BiCGStab of the level-0 Newton step)",) * 2}
+
+
+def roofline(prof, dev_ms, fp64_peak, hbm_peak, hbm_kind, default_case):
+    """The roofline object of the kernel with the largest share of the solve time among the persistent kernels
+    (0 level-0 CG, 1 + 4 coarse step: intermediate levels and the coarsest solve, 3 level-0 BiCGStab): FP64
+    arithmetic against the measured FMA rate (at 64^3 the kernels' vectors live in L2), with the memory view
+    beside it."""
+    def add(a, b):
+        return tuple(x + y for x, y in zip(a, b))
+    kern = {0: prof[0], 1: add(prof[1], prof[4]), 3: prof[3]}
+    kid = max((k for k in kern if kern[k][0]), key=lambda k: kern[k][1])
+    n, ms, by, fl = kern[kid]
+    avg_ms = ms / n
+    gfs = fl / (avg_ms / 1e3) / 1e9
+    gbs = by / (avg_ms / 1e3) / 1e9
+    traffic = DRAM_BYTES_64.get(kid) if default_case else None
+    out = {"bound": "alu", "kernel": KERNELS[kid][0 if default_case else 1], "achieved": gfs, "peak": fp64_peak,
+           "peak_kind": "measured FP64 FMA throughput (nlmg_measure_fp64, independent FMA chains)",
+           "unit": "GFLOP/s", "frac": gfs / fp64_peak, "traffic": traffic,
+           "traffic_note": "DRAM read + write bytes per launch from ncu captures of this kernel on this workload" if
+           traffic is not None else "no capture of this kernel in this configuration",
+           "flops_per_launch": fl, "bytes_per_launch": by, "avg_launch_us": avg_ms * 1e3, "launches": n,
+           "memory_view": {"achieved_GBs": gbs, "peak_GBs": hbm_peak, "peak_kind": hbm_kind, "frac": gbs / hbm_peak},
+           "share_of_solve": ms / dev_ms if dev_ms else None, "others": {}}
+    names = {0: "level0_cg", 1: "kp_coarse_step_intermediate_levels", 2: "k_residual", 3: "kp_fine_bicgstab",
+             4: "kp_coarse_step_coarsest_solve"}
+    for k in (0, 1, 2, 3, 4):
+        if k == kid or not prof[k][0]:
+            continue
+        n, ms, by, fl = prof[k]
+        avg = ms / n / 1e3
+        out["others"][names[k]] = {"launches": n, "avg_us": avg * 1e6, "share_of_solve": ms / dev_ms if dev_ms else None,
+                                   "GB/s": by / avg / 1e9, "GFLOP/s": fl / avg / 1e9 if fl else None}
+    return out
 
 
 def _peaks():
@@ -87,11 +138,12 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": str(e)[:80]}
 
 
-def oracle_sample_seconds(steps=1):
+def oracle_sample_seconds(smoother, steps=1):
     """Times the FP64 oracle FAS solve (hierarchy excluded) on the 16^3 instance of the same generator."""
     from synth.grids import problem_config
     from oracle import fas, hierarchy
     pr = problem_config("chan3d_64", scale=SAMPLE_SCALE)
+    pr.opts = dict(pr.opts, smoother=smoother)
     H = hierarchy.build(pr.mesh, pr.opts)
     times, cycles = [], []
     for _ in range(steps):
@@ -103,8 +155,8 @@ def oracle_sample_seconds(steps=1):
     return times, cycles, pr.mesh.n_cells
 
 
-def cpu_baseline_dict(full_cells):
-    times, cycles, n = oracle_sample_seconds(1)
+def cpu_baseline_dict(full_cells, smoother):
+    times, cycles, n = oracle_sample_seconds(smoother, 1)
     per_solve = times[0] * (full_cells / n)          # linear-in-cells extrapolation (favours the CPU)
     return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
             "sample": "one oracle FAS solve of chan3d at %d^3 (%d cells, %d cycles, %.2f s, SuperLU direct "
@@ -172,14 +224,14 @@ def _serve(nlmg, reqs, arrivals=None, hierarchy_cache=8):
             "hierarchies_reused": int(reused)}
 
 
-def run_serving(nlmg, n):
+def run_serving(nlmg, n, smoother):
     """The request loop (FP32 inner CG in the FP64 FAS, up to 8 requests in flight): a burst of n requests of their
     own meshes, then the same requests arriving as a Poisson stream at 0.8 of the burst's throughput, then n
     requests on one mesh and K with their own nonlinearity parameter and data (hierarchy reuse). Against: the same
     requests one at a time on a plain FP64 context each, setup included and excluded."""
     import numpy as np
     from synth.grids import cartesian_mesh, lognormal_field, default_options, multi_rhs_rows
-    reqs = [(m, a, dict(o, lin_precision=1), f, g) for m, a, o, f, g in serving_requests(n)]
+    reqs = [(m, a, dict(o, lin_precision=1, smoother=smoother), f, g) for m, a, o, f, g in serving_requests(n)]
     burst = _serve(nlmg, reqs)
     rng = np.random.default_rng(7)
     rate = 0.8 * burst["solves_per_s"]
@@ -189,7 +241,7 @@ def run_serving(nlmg, n):
     seq_solve_ms, seq_total_s = 0.0, 0.0
     for m, a, o, f, g in serving_requests(n):
         t1 = time.perf_counter()
-        ctx = nlmg.Context(m, 0, a, o)
+        ctx = nlmg.Context(m, 0, a, dict(o, smoother=smoother))
         _, rep, st = ctx.solve(f, g, max_cycles=60)
         seq_total_s += time.perf_counter() - t1
         seq_solve_ms += rep["solve_ms"]
@@ -199,7 +251,7 @@ def run_serving(nlmg, n):
     mesh = cartesian_mesh((side,) * 3, lognormal_field((side,) * 3, 1.0, 4.0, seed=11))
     F, G = multi_rhs_rows(mesh, n, seed=12)
     alphas = rng.uniform(0.5, 2.0, n)
-    base = default_options(n_levels=3, agg_size=[64, 8], modes=[4, 4], lin_precision=1)
+    base = default_options(n_levels=3, agg_size=[64, 8], modes=[4, 4], lin_precision=1, smoother=smoother)
     shared = [(mesh, float(a), dict(base, dp_clamp=float(np.log(1.5) / a)), F[i], G[i]) for i, a in enumerate(alphas)]
     reuse = _serve(nlmg, shared)
     no_reuse = _serve(nlmg, shared, hierarchy_cache=0)
@@ -208,7 +260,8 @@ def run_serving(nlmg, n):
             "sequential_fp64_solves_per_s_excl_setup": n / (seq_solve_ms / 1e3),
             "one_mesh_with_hierarchy_reuse": reuse, "one_mesh_without_reuse": no_reuse,
             "what": "each request its own mesh and hierarchy (sizes log-uniform 4k-65k cells, 2D/3D) unless noted; "
-                    "latency = submit -> result; FP32 CG inside the FP64 FAS; max 8 in flight"}
+                    "latency = submit -> result; FP32 CG inside the FP64 FAS; max 8 in flight; level-0 "
+                    "smoother: " + smoother}
 
 
 def run_multi_rhs(nlmg, pr, ctx, n_rhs, n_streams):
@@ -252,11 +305,11 @@ def run_multi_rhs(nlmg, pr, ctx, n_rhs, n_streams):
     return out
 
 
-def run_voronoi(nlmg, n_side, steps):
+def run_voronoi(nlmg, n_side, steps, smoother):
     """Unstructured workload: clipped Voronoi mesh of a jittered n_side^3 lattice, ln K ~ N(0, 2^2) correlated over 4
     spacings, kappa = (1 + p^2)^-1, p = 1 on x = 0 and 0 on x = 1, 4-level FAS (aggregates 64 then 8, 4 modes).
     FP64 and FP32-inner-CG solves; each solution's FP64 residual is recomputed by the library's residual call (the
-    GPU tests check that call against the oracle)."""
+    GPU tests check that call against the oracle). The FP64 solve is also timed with the other level-0 smoother."""
     import numpy as np
     from synth.grids import voronoi_problem
     t0 = time.perf_counter()
@@ -271,8 +324,9 @@ def run_voronoi(nlmg, n_side, steps):
     ctx.set_data(pr.f_cell, pr.g_face)
     r0 = np.linalg.norm(ctx.fine_residual(np.zeros(pr.mesh.n_cells)))
     p64 = None
-    for prec in (0, 1):
-        ctx.set_options(lin_precision=prec)
+    other = "picard" if smoother != "picard" else "picard_newton"
+    for key, prec, sm in (("fp64", 0, smoother), ("mixed", 1, smoother), ("fp64_" + other, 0, other)):
+        ctx.set_options(lin_precision=prec, smoother=sm)
         ctx.solve(pr.f_cell, pr.g_face, max_cycles=80)
         ms, rep, p = [], None, None
         for _ in range(steps):
@@ -280,14 +334,13 @@ def run_voronoi(nlmg, n_side, steps):
             ms.append(rep["solve_ms"])
         r = np.linalg.norm(ctx.fine_residual(p))
         d = {"solves_per_s": 1e3 / np.mean(ms), "ms_per_solve": float(np.mean(ms)), "cycles": rep["cycles"],
-             "lin_iters_level": rep["lin_iters_level"][:4], "tol_tightened": rep["tol_tightened"],
-             "rel_residual_recomputed": float(r / r0)}
-        if prec == 0:
+             "newton_steps": rep["newton_steps"], "lin_iters_level": rep["lin_iters_level"][:4],
+             "tol_tightened": rep["tol_tightened"], "rel_residual_recomputed": float(r / r0), "smoother": sm}
+        if key == "fp64":
             p64 = p
-            out["fp64"] = d
         else:
             d["rel_diff_vs_fp64_solution"] = float(np.linalg.norm(p - p64) / np.linalg.norm(p64))
-            out["mixed"] = d
+        out[key] = d
     ctx.close()
     return out
 
@@ -298,6 +351,7 @@ def run_reference(args, rank):
     from synth.grids import problem_config
     from oracle import fas, hierarchy
     pr = problem_config("chan3d_64", scale=SAMPLE_SCALE)
+    pr.opts = dict(pr.opts, smoother=args.smoother)
     H = hierarchy.build(pr.mesh, pr.opts)
     full = 64 ** 3
 
@@ -321,7 +375,7 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": full, "sample_cells": pr.mesh.n_cells},
+            "config": {"workload": workload_name(64, args.smoother), "cells": full, "sample_cells": pr.mesh.n_cells},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -356,6 +410,7 @@ def run_gpu(args, rank, world, local_rank):
     build.build()
     from synth.grids import problem_config
     pr = problem_config("chan3d_64", scale=args.scale)
+    pr.opts = dict(pr.opts, smoother=args.smoother)
     N = pr.mesh.n_cells
     if args.lin_tol is not None:
         pr.opts["lin_tol"] = args.lin_tol
@@ -396,11 +451,25 @@ def run_gpu(args, rank, world, local_rank):
             dist.barrier()
         wall = time.perf_counter() - w0
     clocks = clk.summary()
-    spmv = ctx.profile_read(0)
-    upd = ctx.profile_read(1)
-    res = ctx.profile_read(2)
+    prof = {k: ctx.profile_read(k) for k in (0, 1, 2, 3, 4)}
     ctx.profile(False)
     dev_ms = max_over_ranks(sum(r["solve_ms"] for r in reps), dist, dev)
+    picard = None
+    if args.smoother != "picard" and args.compare_picard:
+        # the same timed loop with Picard steps throughout, for comparison
+        ctx.set_options(smoother="picard")
+        solve_dev()
+        preps = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            preps.append(solve_dev())
+        ctx.set_options(smoother=args.smoother)
+        pms = max_over_ranks(sum(r["solve_ms"] for r in preps), dist, dev)
+        picard = {"value": replica_throughput(world, args.steps, pms), "unit": "solves/s",
+                  "ms_per_step": pms / args.steps, "cycles_per_solve": sum(r["cycles"] for r in preps) / len(preps),
+                  "lin_iters_level": preps[-1]["lin_iters_level"][:3],
+                  "what": "the same solves with Picard steps on level 0 throughout (Sec. 3.3.1 smoother)"}
     # end to end through the host-pointer C-ABI call: H2D of f and g from pinned memory, D2H of p
     f_h = torch.from_numpy(pr.f_cell).pin_memory()
     g_h = torch.from_numpy(pr.g_face).pin_memory()
@@ -422,31 +491,10 @@ def run_gpu(args, rank, world, local_rank):
     ms_step = dev_ms / args.steps
     cycles = sum(r["cycles"] for r in reps) / len(reps)
     value = replica_throughput(world, args.steps, dev_ms)
-    n_cg, ms_cg, by_cg, fl_cg = spmv
-    avg_cg = ms_cg / max(n_cg, 1)
     fp64_peak_gflops = nlmg.measure_fp64_gflops()
-    default_fine = args.scale == 64 and args.lin_tol is None
-    roof = {"bound": "alu",
-            "kernel": "kp_fine_cg_reg<double, 4> (persistent register-resident pipelined Jacobi-scaled CG of the "
-                      "level-0 Picard step)" if default_fine else "kp_fine_cg* (level-0 Picard CG)",
-            "achieved": fl_cg / (avg_cg / 1e3) / 1e9 if n_cg else None, "peak": fp64_peak_gflops,
-            "peak_kind": "measured FP64 FMA throughput (nlmg_measure_fp64, independent FMA chains)",
-            "unit": "GFLOP/s",
-            "frac": (fl_cg / (avg_cg / 1e3) / 1e9) / fp64_peak_gflops if n_cg else None,
-            "traffic": FINE_CG_DRAM_BYTES_64 if default_fine else None,
-            "traffic_note": "DRAM read + write bytes of one launch from an ncu --set full capture of this kernel on "
-                            "this workload (first launch of a step, caches flushed by ncu): the CG iterations run "
-                            "from L2" if default_fine else None,
-            "flops_per_launch": fl_cg, "bytes_per_launch": by_cg, "avg_launch_us": avg_cg * 1e3, "launches": n_cg,
-            "memory_view": {"achieved_GBs": by_cg / (avg_cg / 1e3) / 1e9 if n_cg else None, "peak_GBs": peak,
-                            "peak_kind": peak_kind,
-                            "frac": by_cg / (avg_cg / 1e3) / 1e9 / peak if n_cg else None},
-            "share_of_solve": ms_cg / dev_ms if dev_ms else None,
-            "others": {"kp_coarse_step": {"launches": upd[0], "avg_us": upd[1] / max(upd[0], 1) * 1e3,
-                                        "share_of_solve": upd[1] / dev_ms if dev_ms else None,
-                                        "GB/s": upd[2] / (upd[1] / max(upd[0], 1) / 1e3) / 1e9 if upd[0] else None},
-                       "k_residual": {"launches": res[0], "avg_us": res[1] / max(res[0], 1) * 1e3,
-                                      "GB/s": res[2] / (res[1] / max(res[0], 1) / 1e3) / 1e9 if res[0] else None}}}
+    default_case = (args.scale == 64 and args.lin_tol is None and args.coarse_lin_tol is None and
+                    args.smoother == "picard_newton")
+    roof = roofline(prof, dev_ms, fp64_peak_gflops, peak, peak_kind, default_case)
     mixed = None
     if args.mixed:
         mopts = dict(pr.opts, lin_precision=1)
@@ -467,18 +515,19 @@ def run_gpu(args, rank, world, local_rank):
                  "cycles_per_solve": mrep["cycles"], "rel_residual": mrep["res"] / mrep["res0"],
                  "rel_diff_vs_fp64_solution": diff, "lin_iters_level": mrep["lin_iters_level"][:3],
                  "what": "same FP64 FAS (residuals, transfers, coarse operators, convergence test in FP64); the CG "
-                         "solves inside the Picard steps in FP32 (tolerances floored at 1e-6)"}
+                         "solves inside the Picard steps in FP32 (tolerances floored at 1e-6); the Newton steps' "
+                         "BiCGStab stays FP64"}
     multi = run_multi_rhs(nlmg, pr, ctx, args.multi_rhs, args.streams) if (args.multi_rhs > 0 and world == 1) \
         else None
-    serving = run_serving(nlmg, args.serving) if (args.serving > 0 and world == 1) else None
-    voronoi = run_voronoi(nlmg, args.voronoi, max(1, args.steps // 2)) if (args.voronoi > 0 and world == 1) else None
-    cpu = cpu_baseline_dict(N) if (args.cpu_baseline and world == 1) else None
+    serving = run_serving(nlmg, args.serving, args.smoother) if (args.serving > 0 and world == 1) else None
+    voronoi = run_voronoi(nlmg, args.voronoi, max(1, args.steps // 2), args.smoother) \
+        if (args.voronoi > 0 and world == 1) else None
+    cpu = cpu_baseline_dict(N, args.smoother) if (args.cpu_baseline and world == 1) else None
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.scale == 64 else WORKLOAD.replace("chan3d_64: 64^3", "chan3d_%d: %d^3" % (
-                       args.scale, args.scale)), "cells": N, "parallelism": "replicas" if world > 1 else "single",
+        "config": {"workload": workload_name(args.scale, args.smoother), "cells": N, "smoother": args.smoother, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "256 MiB buffer written between steps, outside each step's CUDA-event pair",
                    "setup_s": round(setup_s, 3), "lin_tol": ctx.opts.lin_tol,
                    "coarse_lin_tol": ctx.opts.coarse_lin_tol},
@@ -488,6 +537,8 @@ def run_gpu(args, rank, world, local_rank):
         "lin_iters_level": reps[-1]["lin_iters_level"][:3],
         "wall_s_timed_region": wall,
         "roofline": roof,
+        "newton_steps_per_solve": sum(r["newton_steps"] for r in reps) / len(reps),
+        "picard_smoother": picard,
         "mixed": mixed,
         "multi_rhs": multi,
         "serving": serving,
@@ -518,6 +569,10 @@ def main():
     ap.add_argument("--serving", type=int, default=24, help="requests in the serving run (0 = skip)")
     ap.add_argument("--multi-rhs", type=int, default=16, help="right-hand sides in the multi-RHS run (0 = skip)")
     ap.add_argument("--streams", type=int, default=8, help="contexts (streams) of the multi-RHS solve")
+    ap.add_argument("--smoother", default="picard_newton", choices=["picard", "picard_newton"],
+                    help="level-0 smoother (Picard-then-Newton by default)")
+    ap.add_argument("--no-compare-picard", dest="compare_picard", action="store_false",
+                    help="skip the timed loop with Picard steps throughout")
     ap.add_argument("--voronoi", type=int, default=0,
                     help="lattice side of the unstructured Voronoi section (100 = 1M cells; 0 = skip)")
     args = ap.parse_args()

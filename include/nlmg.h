@@ -281,12 +281,13 @@ void nlmg_server_destroy(nlmg_server* srv);
 /* ---- measurement ----------------------------------------------------------------------------------------- */
 /* Enables (1) or disables (0) CUDA-event timing of the hot kernels on the context stream and clears the counters.
  * Kernel ids: 0 = persistent fine CG solve (kp_fine_cg*), 1 = persistent coarse Picard step (kp_coarse_step:
- * coarse operator evaluations, hybridized CG, clamp and Algorithm 1 in one launch; kp_hyb_solve for the step calls),
- * 2 = fine TPFA residual (k_residual), 3 = persistent fine BiCGStab of the Newton smoothing steps
- * (kp_fine_bicgstab). */
+ * coarse operator evaluations, hybridized CG, clamp and Algorithm 1 in one launch; kp_hyb_solve for the step calls)
+ * on the levels between the finest and the coarsest, 2 = fine TPFA residual (k_residual), 3 = persistent fine
+ * BiCGStab of the Newton smoothing steps (kp_fine_bicgstab), 4 = kp_coarse_step on the coarsest level (the whole
+ * coarsest solve in one launch). */
 nlmg_status nlmg_profile(nlmg_ctx* ctx, int32_t enable);
 /* Launch count, summed event time, algorithmic bytes per launch (each streamed array counted once; the gathered
- * neighbour values counted once) and arithmetic per launch (FMA = 2 flops; kernels 0 and 3 only) of a profiled kernel
+ * neighbour values counted once) and arithmetic per launch (FMA = 2 flops; every kernel but 2) of a profiled kernel
  * since nlmg_profile(ctx, 1). Any output pointer may be NULL. */
 nlmg_status nlmg_profile_read(nlmg_ctx* ctx, int32_t kernel, int64_t* launches, double* total_ms,
                               double* bytes_per_launch, double* flops_per_launch);

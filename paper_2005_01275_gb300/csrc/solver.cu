@@ -81,6 +81,9 @@ struct Shared {
   long long nnz_real = 0;
   double hyb_bytes_per_iter[8] = {0};
   double coarse_res_bytes[8] = {0};   // algorithmic bytes of one coarse operator evaluation per level
+  // algorithmic flops (FMA = 2) per level: one hybridized CG iteration, the fixed work of one hybridized solve
+  // (right-hand side per interface slot, local recovery), one coarse operator evaluation
+  double hyb_flops_per_iter[8] = {0}, hyb_flops_per_solve[8] = {0}, coarse_res_flops[8] = {0};
   ~Shared() {
     for (void* p : allocs) cudaFree(p);
   }
@@ -394,6 +397,19 @@ void upload_level(nlmg_ctx* c, int l) {
   // written and read, the per-cell products written and read, r written
   c->sh->coarse_res_bytes[l] = 8.0 * (double)(L.Mloc.size() + L.Dloc.size()) + 8.0 * (double)L.loc.size() +
                                16.0 * (D.nflux + D.np) + 16.0 * D.nc + 16.0 * D.nyl + 8.0 * (D.nflux + D.np);
+  // flops: H z (one FMA per stored H entry, kappa scaling per slot) and 9 FMAs per lambda of the pipelined CG;
+  // per solve, one row of the local saddle inverse per interface slot, owned flux slot and pressure unknown; per
+  // operator evaluation the local M and D blocks (D and D^T)
+  double per_solve = 0.0;
+  for (int cc = 0; cc < L.n_cells; ++cc) {
+    const int nl = L.nloc(cc), mc = L.m[cc], n = nl + mc;
+    int own = 0;
+    for (int k = L.loc_off[cc]; k < L.loc_off[cc + 1]; ++k) own += own0[k];
+    per_solve += 2.0 * n * ((if_off[cc + 1] - if_off[cc]) + own + mc);
+  }
+  c->sh->hyb_flops_per_iter[l] = 2.0 * (double)Hc.size() + 2.0 * D.nif + 18.0 * nlam;
+  c->sh->hyb_flops_per_solve[l] = per_solve;
+  c->sh->coarse_res_flops[l] = 2.0 * (double)L.Mloc.size() + 4.0 * (double)L.Dloc.size();
 }
 
 // Work buffers of coarse level l (per context).
@@ -901,7 +917,8 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
   CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
   CoarseStepResult* dres = (CoarseStepResult*)(c->d_res + 1);
   CK(cudaMemsetAsync(dres, 0, sizeof(CoarseStepResult), c->st));
-  int pi = c->prof_begin(1);
+  const int kid = coarsest ? 4 : 1;   // profile id: the coarsest solve apart from the other coarse steps
+  int pi = c->prof_begin(kid);
   if (c->opt.lin_precision == 1) {
     P.lin_tol = std::max(c->coarse_lin_tol_eff, 1e-6);
     CoarseStepBufs<float> Bf{B.x, B.b, B.r, B.nb, B.dx, B.xt1, B.xt2, B.rt, B.kapc, B.f_ylam, B.f_ydiag,
@@ -928,9 +945,13 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
                                     (R.bad == 1 ? "residual" : "hybridized linear solve") + " of coarse level " +
                                     std::to_string(l));
   B.rn = R.rn;
-  if (pi >= 0)
-    c->prof.bytes[1] += (double)R.iters * c->sh->hyb_bytes_per_iter[l] * (c->opt.lin_precision == 1 ? 0.5 : 1.0) +
-                        (double)R.res_evals * c->sh->coarse_res_bytes[l];
+  if (pi >= 0) {
+    c->prof.bytes[kid] += (double)R.iters * c->sh->hyb_bytes_per_iter[l] * (c->opt.lin_precision == 1 ? 0.5 : 1.0) +
+                          (double)R.res_evals * c->sh->coarse_res_bytes[l];
+    c->prof.flops[kid] += (double)R.iters * c->sh->hyb_flops_per_iter[l] +
+                        (double)R.steps * c->sh->hyb_flops_per_solve[l] +
+                        (double)R.res_evals * c->sh->coarse_res_flops[l];
+  }
   c->lin_iters += R.iters;
   c->lin_iters_level[l] += R.iters;
 }
@@ -1739,7 +1760,7 @@ nlmg_status nlmg_profile_read(nlmg_ctx* c, int32_t kernel, int64_t* launches, do
                               double* bytes_per_launch, double* flops_per_launch) {
   return guarded(c, [&]() -> nlmg_status {
     need_device(c);
-    if (kernel < 0 || kernel > 3) throw Error(NLMG_EINVAL, "kernel id");
+    if (kernel < 0 || kernel > 4) throw Error(NLMG_EINVAL, "kernel id");
     c->prof_flush();
     if (launches) *launches = c->prof.n[kernel];
     if (total_ms) *total_ms = c->prof.ms[kernel];
@@ -1747,7 +1768,7 @@ nlmg_status nlmg_profile_read(nlmg_ctx* c, int32_t kernel, int64_t* launches, do
     // counted once (they are the same vector); SELL padding is not counted
     const double N = c->F.N, nnz = (double)c->sh->nnz_real;
     double b = 0.0;
-    if (kernel == 0 || kernel == 1 || kernel == 3) b = c->prof.n[kernel] ? c->prof.bytes[kernel] / c->prof.n[kernel] : 0.0;
+    if (kernel != 2) b = c->prof.n[kernel] ? c->prof.bytes[kernel] / c->prof.n[kernel] : 0.0;
     if (kernel == 2) b = 20.0 * nnz + 8.0 * N * 4;                          // nbr + 2 ups, q, kap, rhs, R
     if (bytes_per_launch) *bytes_per_launch = b;
     if (flops_per_launch) *flops_per_launch = c->prof.n[kernel] ? c->prof.flops[kernel] / c->prof.n[kernel] : 0.0;
