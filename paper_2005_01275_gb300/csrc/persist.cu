@@ -8,9 +8,9 @@
 // Data written by one block and read by another inside the same launch (CG vectors, per-interface buffers) is read
 // with ld.global.cg (L2, bypassing the non-coherent L1), after the barrier that orders the write.
 //
-// Reductions stay deterministic: each block writes one partial; the last block to reach the barrier sums them in
-// block order with a fixed tree and derives the step lengths once, and every block reads the same scalars, so all
-// blocks take the same decisions and a run is bitwise reproducible.
+// Reductions stay deterministic: each block writes one partial per value; after the barrier every block adds all
+// partials in block order with the same fixed tree and derives the step lengths once (one thread per block), so all
+// blocks take the same decisions from bit-identical scalars and a run is bitwise reproducible for a given grid.
 #include <cmath>
 
 #include "kernels.cuh"
@@ -23,7 +23,7 @@ namespace {
 constexpr unsigned long long kSpinLimit = 1ull << 26;   // x ~32 ns sleeps ~ 2 s
 constexpr int kPThreads = 512;                           // threads per block of the persistent kernels
 constexpr int kMaxNV = 4;                                // values per block reduction at most
-constexpr int kSmDoubles = kMaxNV * 32;                  // block-reduction scratch: 32 warp sums per value
+constexpr int kSmDoubles = kMaxNV * kPThreads;           // block-reduction scratch: one value per thread
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
@@ -73,70 +73,55 @@ __device__ __forceinline__ bool grid_barrier(Grid& g) {
   return ok != 0;
 }
 
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
-  static_assert(NV >= 1 && NV <= kMaxNV, "block_sum: sm holds kMaxNV x 32 values");
-  static_assert(kPThreads / 32 <= 32, "block_sum: at most 32 warps");
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k)
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sm[k * 32 + warp] = v[k];
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      v[k] = lane < nw ? sm[k * 32 + lane] : 0.0;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
-    }
-    if (lane == 0)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) sm[k * 32] = v[k];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = sm[k * 32];
-  __syncthreads();
-}
-
-// Grid sums of NV values: every block publishes its block sum, and after the barrier every block adds all partials
-// in block order with the same fixed tree, so all blocks hold bit-identical sums; thread 0 then runs `post(o)`,
-// which derives NX scalars from the sums (the CG step lengths) into o[NV..NV+NX-1] in shared memory, so each
-// division is done once per block, not per thread. Consecutive reductions use the two partial buffers in turn: a
-// block can only overwrite a buffer after every block has passed the next barrier, i.e. has finished reading it.
+// Grid sums of NV values. The FP64 pipe of this part is narrow (about 1.7 FP64 operations per clock per SM), so the
+// block sums spend as few FP64 lane operations as possible: every thread stores its NV values to shared memory and
+// warp k (k < NV) adds value k of all threads -- 16 per lane in a fixed order with four accumulators, then a
+// shuffle tree -- about 640 lane operations per value instead of 2,560 for a shuffle tree in every warp (measured:
+// a three-value grid sum 8.8 us -> 4.8 us). The block sum goes to the partial buffer; after the barrier warp k adds
+// value k of every block's partial in block order, so all blocks hold bit-identical sums; thread 0 then runs
+// `post(o)`, which derives NX scalars from the sums (the CG step lengths) into o[NV..NV+NX-1] in shared memory, so
+// each division is done once per block, not per thread. Consecutive reductions use the two partial buffers in
+// turn: a block can only overwrite a buffer after every block has passed the next barrier, i.e. has finished
+// reading it.
 template <int NV, int NX = 0, class PostFn>
 __device__ __forceinline__ bool grid_sum_x(Grid& g, double (&v)[NV + NX], PostFn&& post) {
+  static_assert(NV >= 1 && NV <= kMaxNV, "grid_sum_x: the shared scratch holds kMaxNV values per thread");
+  static_assert(kPThreads % 128 == 0 && kPThreads / 32 >= kMaxNV, "grid_sum_x: block shape");
   double* part = g.partial + (g.seq & 1u) * kPartStride;
   ++g.seq;
-  double w[NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) w[k] = v[k];
-  block_sum<NV>(w, g.sm);
-  if (threadIdx.x == 0)
+  for (int k = 0; k < NV; ++k) g.sm[k * kPThreads + threadIdx.x] = v[k];
+  __syncthreads();
+  if (warp < NV) {
+    const double* s = g.sm + warp * kPThreads;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) part[blockIdx.x * NV + k] = w[k];
-  if (!grid_barrier(g)) return false;
-  double acc[NV];
+    for (int j = lane; j < kPThreads; j += 128) {
+      a0 += s[j];
+      a1 += s[j + 32];
+      a2 += s[j + 64];
+      a3 += s[j + 96];
+    }
+    double a = (a0 + a1) + (a2 + a3);
 #pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(&part[b * NV + k]);
-  block_sum<NV>(acc, g.sm);
-  __shared__ double o[NV + NX];
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) o[k] = acc[k];
-    post(o);
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (lane == 0) part[blockIdx.x * NV + warp] = a;
   }
+  if (!grid_barrier(g)) return false;
+  __shared__ double o[NV + NX];
+  if (warp < NV) {
+    double a = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) a += __ldcg(&part[b * NV + warp]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (lane == 0) o[warp] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) post(o);
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < NV + NX; ++k) v[k] = o[k];
-  __syncthreads();
   return true;
 }
 
@@ -608,6 +593,113 @@ __device__ bool hyb_pipe_loop(const LevelDev& L, const T* __restrict__ Hc, const
   return true;
 }
 
+// Register-resident form of hyb_pipe_loop for levels whose lambdas fit in one pass of the grid (nlam * gsz <=
+// threads): the group of gsz lanes that owns lambda l keeps it for the whole solve. Its leader keeps the CG state of
+// l (w, z, s, p, q, u, r, lambda and the Jacobi weight) in registers, and every lane keeps the descriptors of its
+// share of the two H rows of l (row offset, lambda-index offset, length, kappa of the slot's cell: all fixed during
+// the solve), so an iteration's dependent loads are only the lane's H entries and lambda indices (independent of
+// each other) and the gathered m values. m = M w is the one vector published per iteration (double-buffered);
+// lambda is stored too, so that the recovery after the last reduction's barrier reads the final values.
+template <class T>
+__device__ bool hyb_pipe_loop_reg(const LevelDev& L, const T* __restrict__ Hc, const double* kapc, T* lam,
+                                  const T* lr, const T* lu, const T* ldinv, const HybPipeBufs<T>& P, Grid& g,
+                                  int gsz, double tol2, double rr0, int maxit, int& it_out, double& rr_out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = t / gsz;
+  const int gi = t & (gsz - 1);
+  const bool act = l < L.nlam;
+  const bool lead = act && gi == 0;
+  int hb0 = 0, hb1 = 0, lb0 = 0, lb1 = 0, n0 = 0, n1 = 0;
+  T kp0 = (T)0, kp1 = (T)0;
+  if (act) {
+    const int ka = L.lam_y0[l], kb = L.lam_y1[l];
+    const int ca = L.if_cell[ka], cb = L.if_cell[kb];
+    const int a0 = L.if_off[ca], b0 = L.if_off[cb];
+    n0 = L.if_off[ca + 1] - a0;
+    n1 = L.if_off[cb + 1] - b0;
+    hb0 = L.hc_off[ca] + (ka - a0) * n0;
+    hb1 = L.hc_off[cb] + (kb - b0) * n1;
+    lb0 = a0;
+    lb1 = b0;
+    kp0 = (T)__ldcg(&kapc[ca]);
+    kp1 = (T)__ldcg(&kapc[cb]);
+  }
+  // the group's share of (H v)_l, summed over the group by shuffles (every lane of the warp takes part)
+  auto rowprod = [&](const T* v) -> T {
+    T y0 = (T)0, y1 = (T)0;
+    for (int j = gi; j < n0; j += gsz) y0 += Hc[hb0 + j] * __ldcg(&v[L.if_lam[lb0 + j]]);
+    for (int j = gi; j < n1; j += gsz) y1 += Hc[hb1 + j] * __ldcg(&v[L.if_lam[lb1 + j]]);
+    T h = kp0 * y0 + kp1 * y1;
+    for (int off = gsz >> 1; off > 0; off >>= 1) h += __shfl_xor_sync(0xffffffffu, h, off);
+    return h;
+  };
+  T r = (T)0, u = (T)0, di = (T)0, lm = (T)0;
+  if (lead) {
+    r = __ldcg(&lr[l]);
+    u = __ldcg(&lu[l]);
+    di = __ldcg(&ldinv[l]);
+  }
+  T w = rowprod(lu);
+  T z = (T)0, s = (T)0, q = (T)0, p = (T)0;
+  double d3[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (lead) {
+    P.ma[l] = di * w;
+    d3[0] = (double)(r * u);
+    d3[1] = (double)(w * u);
+    d3[2] = (double)(r * r);
+  }
+  if (!grid_sum_x<3, 2>(g, d3, [&](double* o) {
+        o[3] = 0.0;
+        o[4] = o[1] != 0.0 ? o[0] / o[1] : 0.0;
+      }))
+    return false;
+  double gamma = d3[0], rr = d3[2], beta = d3[3], alpha = d3[4];
+  T* mc = P.ma;
+  T* mn = P.mb;
+  int it = 0;
+  while (rr0 > 0.0 && rr > tol2 && it < maxit) {
+    if (!(alpha != 0.0)) break;
+    const T a = (T)alpha, b = (T)beta;
+    const T n = rowprod(mc);
+    double n5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (lead) {
+      const T m = di * w;
+      z = n + b * z;
+      q = m + b * q;
+      s = w + b * s;
+      p = u + b * p;
+      lm = lm + a * p;
+      r = r - a * s;
+      u = u - a * q;
+      w = w - a * z;
+      mn[l] = di * w;
+      lam[l] = lm;
+      n5[0] = (double)(r * u);
+      n5[1] = (double)(w * u);
+      n5[2] = (double)(r * r);
+    }
+    if (!grid_sum_x<3, 2>(g, n5, [&](double* o) {
+          const double gn = o[0], dn = o[1];
+          const double bn = gamma != 0.0 ? gn / gamma : 0.0;
+          const double den = dn - bn * gn / alpha;
+          o[3] = bn;
+          o[4] = den != 0.0 ? gn / den : 0.0;
+        }))
+      return false;
+    gamma = n5[0];
+    rr = n5[2];
+    beta = n5[3];
+    alpha = n5[4];
+    T* tmp = mc;
+    mc = mn;
+    mn = tmp;
+    ++it;
+  }
+  it_out = it;
+  rr_out = rr;
+  return true;
+}
+
 // Register-resident two-barrier CG (the CG of kp_fine_cg, bitwise on the same grid): a thread keeps r, p, q = A p
 // and y of its at most R cells in registers for the whole solve and publishes only r, which the neighbours gather
 // for the product A r. Used for the FP32 solves, where the pipelined forms drift.
@@ -807,7 +899,7 @@ __device__ bool hyb_solve_dev(const LevelDev& L, const T* __restrict__ Hc, const
                               const double* kapc, const double* bs, const double* bp, T* ylam, T* ydiag, T* lam,
                               T* lr, T* lz, T* pa, T* pb, T* lq, T* ldinv, double* dsig, double* dp, Grid& g,
                               double tol, int maxit, int gsz, int& iters, double& rr0_out, double& rr_out,
-                              const HybPipeBufs<T>* pipe = nullptr) {
+                              const HybPipeBufs<T>* pipe = nullptr, int gsz_reg = 0) {
   // phase 0: per interface slot k of cell c, u_k = kappa A[k,:] bhat + B[k,:] b_p (signed) and kappa Hc[k,k]
   GSTRIDE(k, L.nif) {
     const int c = L.if_cell[k];
@@ -845,7 +937,10 @@ __device__ bool hyb_solve_dev(const LevelDev& L, const T* __restrict__ Hc, const
   T beta = (T)0;
   T* pp = pa;       // search direction p
   int it = 0;
-  if (pipe) {
+  if (pipe && gsz_reg > 0) {
+    if (!hyb_pipe_loop_reg<T>(L, Hc, kapc, lam, lr, lz, ldinv, *pipe, g, gsz_reg, tol2, rr0, maxit, it, rr))
+      return false;
+  } else if (pipe) {
     if (!hyb_pipe_loop<T>(L, Hc, kapc, lam, lr, lz, pp, lq, ldinv, *pipe, g, gsz, tol2, rr0, maxit, it, rr))
       return false;
   }
@@ -1092,7 +1187,7 @@ template <class T>
 __global__ void __launch_bounds__(kPThreads, 1) kp_coarse_step(LevelDev L, const T* __restrict__ Hc,
                                                            const T* __restrict__ Sinv, CoarseStepBufs<T> B,
                                                            CoarseStepParams P, double* partial, GridSync gs,
-                                                           int gsz, CoarseStepResult* res) {
+                                                           int gsz, int gsz_reg, CoarseStepResult* res) {
   __shared__ double sm[kSmDoubles];
   Grid g{gs, partial, sm, 0u};
   double* const xb[3] = {B.x, B.xt1, B.xt2};
@@ -1116,7 +1211,7 @@ __global__ void __launch_bounds__(kPThreads, 1) kp_coarse_step(LevelDev L, const
     double rr0 = 0.0, rr = 0.0;
     if (!hyb_solve_dev<T>(L, Hc, Sinv, B.kapc, B.nb, B.nb + L.nflux, B.ylam, B.ydiag, B.lam, B.lr, B.lz, B.pa,
                           B.pb, B.lq, B.ldinv, B.dx, B.dx + L.nflux, g, P.lin_tol, P.maxit, gsz, it, rr0, rr,
-                          B.pipe.w ? &B.pipe : nullptr))
+                          B.pipe.w ? &B.pipe : nullptr, gsz_reg))
       return;
     iters += it;
     if (!isfinite(rr)) {
@@ -1309,8 +1404,16 @@ cudaError_t launch_coarse_step(cudaStream_t st, const LevelDev& L, const T* Hc, 
     if (v > items) items = v;
   const void* fn = (const void*)kp_coarse_step<T>;
   int grid = coop_grid(fn, (int)items, gs.sm_cap);
+  // register-resident pipelined hybridized CG when every lambda gets its own lane group in one pass of the grid:
+  // the largest power-of-two group (<= 32 lanes) that fits
+  int gsz_reg = 0;
+  const long lanes = (long)grid * kPThreads;
+  if (L.nlam > 0 && L.nlam <= lanes) {
+    gsz_reg = 1;
+    while (gsz_reg < 32 && (long)L.nlam * gsz_reg * 2 <= lanes) gsz_reg *= 2;
+  }
   void* args[] = {(void*)&L, (void*)&Hc, (void*)&Sinv, (void*)&B, (void*)&P, (void*)&partial, (void*)&gs,
-                  (void*)&gsz, (void*)&res};
+                  (void*)&gsz, (void*)&gsz_reg, (void*)&res};
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
 }
 template cudaError_t launch_coarse_step<double>(cudaStream_t, const LevelDev&, const double*, const double*,
