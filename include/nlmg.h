@@ -91,11 +91,12 @@ typedef struct {
                                 The grid, and with it the reduction order, follows from it: results are bitwise
                                 reproducible for a given max_sms */
   double newton_switch;      /* NLMG_SMOOTH_PICARD_NEWTON: a level-0 smoothing step at p_k is a Newton step (exact
-                                Jacobian, persistent FP64 BiCGStab to lin_tol, clamp, Algorithm 1) once
+                                Jacobian, persistent FP64 BiCGStab to newton_lin_tol, clamp, Algorithm 1) once
                                 ||R(p_k)|| <= newton_switch ||R(p_0)||, a Picard step before (default 1e-3; >= 0).
                                 A Newton step that does not halve the residual returns the rest of the solve to
                                 Picard steps (cleared by the next solve and by nlmg_set_options; consecutive
                                 nlmg_vcycle calls carry it) */
+  double newton_lin_tol;     /* relative tolerance of the BiCGStab solves of the Newton steps (default 1e-2) */
   int32_t reserved[5];
 } nlmg_options;
 
@@ -224,8 +225,8 @@ nlmg_status nlmg_picard_update(nlmg_ctx* ctx, int32_t level, const double* x, co
                                int32_t* iters);
 
 /* The level-0 Newton update (Sec. 3.3.2 in the reduced form): dx solving J(p) dx = -R(p) with the exact Jacobian of
- * the TPFA residual, by the persistent FP64 BiCGStab of the Picard-then-Newton smoother to lin_tol (relative, on the
- * Jacobi-scaled residual). p and dx_out are host arrays of n_cells; *iters (may be NULL) receives the iterations. */
+ * the TPFA residual, by the persistent FP64 BiCGStab of the Picard-then-Newton smoother to newton_lin_tol (relative,
+ * on the Jacobi-scaled residual). p and dx_out are host arrays of n_cells; *iters (may be NULL) receives the iterations. */
 nlmg_status nlmg_newton_update(nlmg_ctx* ctx, const double* p, double* dx_out, int32_t* iters);
 
 /* One FAS cycle from level 0 (Algorithm 2) from p_in; r0 is the reference ||R(p_0)|| for the early exit. */

@@ -128,7 +128,7 @@ struct nlmg_ctx {
   FineState cur, t1, t2;
   bool have_data = false;
   double tol_rel = 1e-8, tol_abs = 1e-10;   // outer tolerances, also used on the coarsest level
-  double lin_tol_eff = 1e-2, coarse_lin_tol_eff = 1e-1;   // inner tolerances of the running solve
+  double lin_tol_eff = 1e-2, coarse_lin_tol_eff = 1e-1, newton_tol_eff = 1e-2;   // inner tolerances of the running solve
   int tightenings = 0;
   double r0_ref = 0.0;             // ||R(p_0)|| of the running solve (the Picard-then-Newton switch)
   bool newton_off = false;         // a Newton smoothing step of the running solve failed to halve the residual
@@ -139,6 +139,7 @@ struct nlmg_ctx {
     sm_cap = opt.max_sms > 0 ? opt.max_sms : auto_sm_cap;
     lin_tol_eff = opt.lin_tol;
     coarse_lin_tol_eff = opt.coarse_lin_tol;
+    newton_tol_eff = opt.newton_lin_tol;
     tightenings = 0;
   }
   // statistics of the running solve
@@ -632,7 +633,7 @@ void newton_linearize(nlmg_ctx* c) {
   launch_jacobi_dinv(c->st, N, c->jdiag, c->diagT, c->jdinv);
 }
 
-// Persistent FP64 BiCGStab on the Jacobi-scaled Newton system J dx = -R (J from newton_linearize) to lin_tol_eff;
+// Persistent FP64 BiCGStab on the Jacobi-scaled Newton system J dx = -R (J from newton_linearize) to newton_tol_eff;
 // dx -> c->cx.
 int fine_bicgstab(nlmg_ctx* c, const double* R) {
   GridSync gs{c->d_bar, &c->d_res->err, c->sm_cap};
@@ -641,7 +642,7 @@ int fine_bicgstab(nlmg_ctx* c, const double* R) {
   launch_scale_jac(c->st, c->F, c->jdiag, c->Joff, c->jdinv, c->Js, c->jdS, c->jsS);
   const int pi = c->prof_begin(3);
   CK(launch_fine_bicgstab(c->st, c->F, c->Js, c->jdS, c->jsS, R, -1.0, c->cx, c->gV, c->d_partial, gs,
-                          c->lin_tol_eff, c->opt.lin_maxit, c->d_res));
+                          c->newton_tol_eff, c->opt.lin_maxit, c->d_res));
   c->prof_end(pi);
   count_launch(1);
   CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(PcgResult), cudaMemcpyDeviceToHost, c->st));
@@ -1113,6 +1114,7 @@ nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double
         (c->lin_tol_eff > 1e-12 || c->coarse_lin_tol_eff > 1e-12)) {
       c->lin_tol_eff = std::max(1e-12, c->lin_tol_eff * 1e-2);
       c->coarse_lin_tol_eff = std::max(1e-12, c->coarse_lin_tol_eff * 1e-2);
+      c->newton_tol_eff = std::max(1e-12, c->newton_tol_eff * 1e-2);
       c->tightenings++;
     }
     best = std::min(best, c->cur.rn);
@@ -1182,6 +1184,7 @@ void nlmg_default_options(nlmg_options* o) {
   o->lin_precision = 0;
   o->setup_threads = 0;
   o->newton_switch = 1e-3;
+  o->newton_lin_tol = 1e-2;
 }
 
 static thread_local std::string g_setup_error;   // message of the calling thread's last failed setup
@@ -1190,7 +1193,7 @@ static thread_local std::string g_setup_error;   // message of the calling threa
 static bool solver_options_ok(const nlmg_options& o) {
   return o.nu_pre >= 0 && o.nu_post >= 0 && o.bt_nmax >= 0 && o.omega > 0 && o.coarsest_steps >= 0 &&
          (o.lin_precision == 0 || o.lin_precision == 1) && o.max_sms >= 0 && o.smoother >= NLMG_SMOOTH_PICARD &&
-         o.smoother <= NLMG_SMOOTH_PICARD_NEWTON && o.newton_switch >= 0.0;
+         o.smoother <= NLMG_SMOOTH_PICARD_NEWTON && o.newton_switch >= 0.0 && o.newton_lin_tol > 0.0;
 }
 
 static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlmg_options* opt,

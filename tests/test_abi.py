@@ -32,7 +32,7 @@ def test_exports_every_declared_symbol(nlmg_lib):
 def test_default_options_are_the_papers(nlmg_lib):
     o = nlmg_lib.default_options()
     assert o.bt_nmax == 4 and abs(o.bt_theta - 0.9) < 1e-15 and o.coarsest_steps == 10
-    assert o.smoother == nlmg_lib.SMOOTH_PICARD and o.newton_switch == 1e-3
+    assert o.smoother == nlmg_lib.SMOOTH_PICARD and o.newton_switch == 1e-3 and o.newton_lin_tol == 1e-2
 
 
 def test_setup_rejects_bad_mesh(nlmg_lib):
@@ -82,7 +82,8 @@ def test_set_options_keeps_the_hierarchy_fixed(nlmg_lib):
     ctx.set_options(smoother="picard_newton", newton_switch=1e-3)
     assert ctx.opts.smoother == nlmg_lib.SMOOTH_PICARD_NEWTON and ctx.opts.newton_switch == 1e-3
     for bad in (dict(n_levels=3), dict(modes=(ctypes.c_int32 * 8)(3, 3, 3, 3, 3, 3, 3, 3)), dict(lin_precision=2),
-                dict(omega=0.0), dict(smoother=3), dict(newton_switch=-1.0), dict(newton_switch=float("nan"))):
+                dict(omega=0.0), dict(smoother=3), dict(newton_switch=-1.0), dict(newton_switch=float("nan")),
+                dict(newton_lin_tol=0.0)):
         with pytest.raises(nlmg_lib.NlmgError):
             ctx.set_options(**bad)
     ctx.close()

@@ -15,7 +15,7 @@ CASES = {
     "cart2d_32": ("cart2d_32", None, {}),
     "vor3d_10": ("voronoi", 10, {}),
 }
-TIGHT = dict(lin_tol=1e-13, lin_maxit=20000)
+TIGHT = dict(lin_tol=1e-13, newton_lin_tol=1e-13, lin_maxit=20000)
 
 
 def _setup(nlmg_lib, key, **upd):
@@ -79,7 +79,7 @@ def test_picard_newton_solve_reaches_newton_solution(nlmg_lib):
     assert _rel(p, pstar) <= 1e-10
     r = tpfa.reduced_residual(pr.mesh, pr.kappa_kind, pr.kappa_a, p, pr.f_cell, pr.g_face)
     assert np.linalg.norm(r) <= 2e-12 * rep["res0"]
-    ctx.set_options(lin_tol=1e-2, coarse_lin_tol=1e-1, lin_maxit=5000)
+    ctx.set_options(lin_tol=1e-2, coarse_lin_tol=1e-1, newton_lin_tol=1e-2, lin_maxit=5000)
     _, rep_n, st = ctx.solve(pr.f_cell, pr.g_face, max_cycles=60)
     assert st == 0 and rep_n["newton_steps"] >= 1
     ctx.set_options(smoother="picard")
