@@ -31,13 +31,10 @@ def workload_name(scale, smoother):
 SAMPLE_SCALE = 16          # side of the bounded CPU sample of the same generator
 
 
-# DRAM bytes (read + write) per launch on the 64^3 workload with the default tolerances, from ncu captures of the
+# DRAM bytes (read + write) per launch on the 64^3 workload with the default options, from ncu captures of the
 # kernels as they are now (averaged over the launches of one solve where they differ): valid for that kernel, that
-# workload and those options only, else the traffic is reported as null.
-FINE_CG_DRAM_BYTES_64 = 23.015680e6 + 91.648e3          # kp_fine_cg_reg<double, 4>
-COARSE_STEP_DRAM_BYTES_64 = 25.4458e6                   # kp_coarse_step<double>, mean over the launches of a solve
-BICGSTAB_DRAM_BYTES_64 = 25.237e6                       # kp_fine_bicgstab
-DRAM_BYTES_64 = {0: FINE_CG_DRAM_BYTES_64, 1: COARSE_STEP_DRAM_BYTES_64, 3: BICGSTAB_DRAM_BYTES_64}
+# workload and those options only, else the traffic is reported as null. Empty until the kernels are captured.
+DRAM_BYTES_64 = {}
 
 KERNELS = {0: ("kp_fine_cg_reg<double, 4> (persistent register-resident pipelined Jacobi-scaled CG of the level-0 "
                "Picard step)", "kp_fine_cg* (level-0 Picard CG)"),

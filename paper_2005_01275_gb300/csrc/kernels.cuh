@@ -41,6 +41,10 @@ struct FineDev {
 __device__ __forceinline__ double kappa_of(double p, int kind, double a) {
   return kind == 0 ? exp(a * p) : 1.0 / (1.0 + p * p);
 }
+// 1 / kappa(p) without a division: exp(-a p), or 1 + p^2.
+__device__ __forceinline__ double inv_kappa_of(double p, int kind, double a) {
+  return kind == 0 ? exp(-a * p) : fma(p, p, 1.0);
+}
 __device__ __forceinline__ double dkappa_of(double p, int kind, double a) {
   if (kind == 0) return a * exp(a * p);
   double t = 1.0 + p * p;

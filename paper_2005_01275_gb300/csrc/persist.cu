@@ -1064,80 +1064,89 @@ __global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* _
 }
 
 // ---- fused coarse Picard step -------------------------------------------------------------------------------
-// r = A^l(x) - b on a coarse level (Prop. 1, eq. structure), in two passes and two grid synchronisations:
-// (1) kappa_c = kappa(w_c . p_c) per cell; with dx given, the point is the trial x = x0 + alpha dx, formed in the
-//     same pass (x written, then used);
-// (2) per flux unknown, r_sigma = sum over its (one or two) owner slots of s_c Mloc_c[u, :] sigma_c + Dloc_c[:, u]^T
-//     p_c, minus b_sigma (one lane per slot, the two lanes of a flux unknown adjacent); per pressure unknown,
-//     r_p = Dloc_c[r, :] sigma_c - b_p; and ||r||^2.
-// nb = -r if given. Inputs written earlier in the launch are read through L2; the caller has put a grid barrier
-// after the last write of x0 (and dx).
-__device__ bool coarse_residual_dev(const LevelDev& L, double* x, const double* x0, const double* dx, double alpha,
-                                    const double* b, double* r, double* nb, double* kapc, int kind, double a,
-                                    Grid& g, double& rn) {
-  double* xs = x;
-  double* xp = x + L.nflux;
-  if (dx) {
-    GSTRIDE(i, L.nflux) xs[i] = fma(alpha, __ldcg(&dx[i]), __ldcg(&x0[i]));
-  }
-  GSTRIDE(c, L.nc) {
-    const int po = L.p_off[c];
-    double pb = 0.0;
-    for (int q = 0; q < L.m[c]; ++q) {
-      double pq;
-      if (dx) {
-        pq = fma(alpha, __ldcg(&dx[L.nflux + po + q]), __ldcg(&x0[L.nflux + po + q]));
-        xp[po + q] = pq;
-      } else {
-        pq = __ldcg(&xp[po + q]);
-      }
-      pb = fma(L.w[po + q], pq, pb);
+// The coarse operator (Prop. 1, eq. structure) is linear in [sigma; p] once kappa is fixed: with kappa_c =
+// kappa((Pi~ p)_c), A(x)_sigma,i = sum over the (one or two) owner slots y of flux unknown i of
+// (M_c sigma_c)_u / kappa_c + (D_c^T p_c)_u and A(x)_p,i = (D_c sigma_c)_i. Algorithm 1 evaluates A at x + s dx for
+// several s; the linear parts of x and of dx (LinParts) are computed once, and each trial is then one pass over the
+// flux and pressure unknowns -- (ms_x + s ms_dx) / kappa(pb_x + s pb_dx) + ds_x + s ds_dx -- and one reduction,
+// instead of a whole operator evaluation with two synchronisations. On this part the FP64 products of an
+// evaluation and its synchronisations are what a coarse step costs, not its bytes.
+
+// Linear parts of v (read through L2: v may have been written earlier in the launch). With shift != 0 the parts
+// `acc` first take acc += shift * out (the previous step's accepted trial; the same lane owns both entries).
+__device__ void lin_parts_pass(const LevelDev& L, const double* v, LinParts out, LinParts acc, double shift) {
+  const double* vs = v;
+  const double* vp = v + L.nflux;
+  GSTRIDE(y, L.nyl) {
+    const int c = L.slot_cell[y];
+    const int lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, mc = L.m[c], po = L.p_off[c];
+    const int u = y - lo;
+    const double* Mu = L.Mloc + L.mat_off[c] + (size_t)u * nl;
+    const double* D = L.Dloc + L.dmat_off[c];
+    double m = 0.0, d = 0.0;
+    for (int k = 0; k < nl; ++k) m = fma(Mu[k], __ldcg(&vs[L.loc[lo + k]]), m);
+    for (int q = 0; q < mc; ++q) d = fma(D[q * nl + u], __ldcg(&vp[po + q]), d);
+    if (shift != 0.0) {
+      acc.ms[y] = fma(shift, out.ms[y], acc.ms[y]);
+      acc.ds[y] = fma(shift, out.ds[y], acc.ds[y]);
     }
-    kapc[c] = kappa_of(pb, kind, a);
-  }
-  if (!grid_barrier(g)) return false;
-  double acc = 0.0;
-  {
-    // one lane per (flux unknown, owner slot) pair, the pair on adjacent lanes of a warp: each lane computes its
-    // slot's product, a shuffle adds the pair (warp-uniform loop so that every lane takes part)
-    const long total = 2L * L.nflux;
-    const int lane = threadIdx.x & 31;
-    const long stride = (long)gridDim.x * blockDim.x;
-    for (long tb = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); tb < total; tb += stride) {
-      const long t = tb + lane;
-      const bool act = t < total;
-      const int i = act ? (int)(t >> 1) : 0;
-      const int y = act ? ((t & 1) ? L.f_y1[i] : L.f_y0[i]) : -1;
-      double v = 0.0;
-      if (y >= 0) {
-        const int c = L.slot_cell[y];
-        const int mc = L.m[c], lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c];
-        const int u = y - lo;
-        const double* Mu = L.Mloc + L.mat_off[c] + (size_t)u * nl;
-        const double* D = L.Dloc + L.dmat_off[c];
-        for (int k = 0; k < nl; ++k) v = fma(Mu[k], __ldcg(&xs[L.loc[lo + k]]), v);
-        v /= __ldcg(&kapc[c]);
-        for (int q = 0; q < mc; ++q) v = fma(D[q * nl + u], __ldcg(&xp[po + q]), v);
-      }
-      const double other = __shfl_xor_sync(0xffffffffu, v, 1);
-      if (act && (t & 1) == 0) {
-        double vv = v + other;
-        if (b) vv -= __ldcg(&b[i]);
-        r[i] = vv;
-        if (nb) nb[i] = -vv;
-        acc = fma(vv, vv, acc);
-      }
-    }
+    out.ms[y] = m;
+    out.ds[y] = d;
   }
   GSTRIDE(i, L.np) {
     const int c = L.p_cell[i];
     const int lo = L.loc_off[c], nl = L.loc_off[c + 1] - lo, po = L.p_off[c];
     const double* Dr = L.Dloc + L.dmat_off[c] + (size_t)(i - po) * nl;
-    double v = 0.0;
-    for (int k = 0; k < nl; ++k) v = fma(Dr[k], __ldcg(&xs[L.loc[lo + k]]), v);
-    if (b) v -= __ldcg(&b[L.nflux + i]);
-    r[L.nflux + i] = v;
-    if (nb) nb[L.nflux + i] = -v;
+    double d = 0.0;
+    for (int k = 0; k < nl; ++k) d = fma(Dr[k], __ldcg(&vs[L.loc[lo + k]]), d);
+    if (shift != 0.0) acc.dr[i] = fma(shift, out.dr[i], acc.dr[i]);
+    out.dr[i] = d;
+  }
+  GSTRIDE(c, L.nc) {
+    const int po = L.p_off[c];
+    double pb = 0.0;
+    for (int q = 0; q < L.m[c]; ++q) pb = fma(L.w[po + q], __ldcg(&vp[po + q]), pb);
+    if (shift != 0.0) acc.pb[c] = fma(shift, out.pb[c], acc.pb[c]);
+    out.pb[c] = pb;
+  }
+}
+
+// A(x + s dx) - b from the linear parts (dir is not read when s == 0), for flux unknown i / pressure unknown i.
+__device__ __forceinline__ double trial_flux_row(const LevelDev& L, const LinParts& bx, const LinParts& dx, double s,
+                                                 const double* b, int kind, double a, int i) {
+  double v = 0.0;
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int y = side == 0 ? L.f_y0[i] : L.f_y1[i];
+    if (y < 0) continue;
+    const int c = L.slot_cell[y];
+    double pb = __ldcg(&bx.pb[c]), m = __ldcg(&bx.ms[y]), d = __ldcg(&bx.ds[y]);
+    if (s != 0.0) {
+      pb = fma(s, __ldcg(&dx.pb[c]), pb);
+      m = fma(s, __ldcg(&dx.ms[y]), m);
+      d = fma(s, __ldcg(&dx.ds[y]), d);
+    }
+    v += fma(m, inv_kappa_of(pb, kind, a), d);
+  }
+  return v - __ldcg(&b[i]);
+}
+__device__ __forceinline__ double trial_p_row(const LevelDev& L, const LinParts& bx, const LinParts& dx, double s,
+                                              const double* b, int i) {
+  double d = __ldcg(&bx.dr[i]);
+  if (s != 0.0) d = fma(s, __ldcg(&dx.dr[i]), d);
+  return d - __ldcg(&b[L.nflux + i]);
+}
+
+// ||A(x + s dx) - b|| (one pass, one reduction).
+__device__ bool trial_norm(const LevelDev& L, const LinParts& bx, const LinParts& dx, double s, const double* b,
+                           int kind, double a, Grid& g, double& rn) {
+  double acc = 0.0;
+  GSTRIDE(i, L.nflux) {
+    const double v = trial_flux_row(L, bx, dx, s, b, kind, a, i);
+    acc = fma(v, v, acc);
+  }
+  GSTRIDE(i, L.np) {
+    const double v = trial_p_row(L, bx, dx, s, b, i);
     acc = fma(v, v, acc);
   }
   double s1[1] = {acc};
@@ -1146,43 +1155,67 @@ __device__ bool coarse_residual_dev(const LevelDev& L, double* x, const double* 
   return true;
 }
 
-// Algorithm 1 on a coarse level along dx from step s0: trial x + s s0 dx, halving s while the half step is no worse
-// than theta times the current trial (at most bt_nmax times) as long as the trial is worse than ||r(x)||; the
-// accepted trial becomes the iterate and rn its residual norm. A trial whose residual norm is not finite counts as
-// +infinity; if the returned trial is not finite, the iterate is kept. The three buffers xb[0..2] rotate: xb[cur]
-// is the iterate, the trials go to the other two, so no copy is needed.
+// Makes x + s dx the iterate: r = A(x) - b, nb = -r and kappa per cell at the new point, x += s dx; returns this
+// thread's share of ||r||^2 (the same sum as the trial's). The linear parts of x are left as they were (the next
+// pass over the step's direction adds s times the old direction's).
 template <class T>
-__device__ bool coarse_backtrack_dev(const LevelDev& L, const CoarseStepBufs<T>& B, const CoarseStepParams& P,
-                                     double* const* xb, int& cur, double s0, double& rn, int& evals, Grid& g) {
-  int t1 = (cur + 1) % 3, t2 = (cur + 2) % 3;
-  double s = 1.0;
-  double r_s = 0.0;
-  if (!coarse_residual_dev(L, xb[t1], xb[cur], B.dx, s * s0, B.b, B.rt, nullptr, B.kapc, P.kind, P.a, g, r_s))
-    return false;
-  ++evals;
-  if (!isfinite(r_s)) r_s = HUGE_VAL;   // a non-finite trial counts as +infinity
+__device__ double accept_pass(const LevelDev& L, const CoarseStepBufs<T>& B, double s, int kind, double a) {
+  double acc = 0.0;
+  GSTRIDE(i, L.nflux) {
+    const double v = trial_flux_row(L, B.base, B.dir, s, B.b, kind, a, i);
+    B.r[i] = v;
+    B.nb[i] = -v;
+    acc = fma(v, v, acc);
+  }
+  GSTRIDE(i, L.np) {
+    const double v = trial_p_row(L, B.base, B.dir, s, B.b, i);
+    B.r[L.nflux + i] = v;
+    B.nb[L.nflux + i] = -v;
+    acc = fma(v, v, acc);
+  }
+  GSTRIDE(c, L.nc) {
+    double pb = __ldcg(&B.base.pb[c]);
+    if (s != 0.0) pb = fma(s, __ldcg(&B.dir.pb[c]), pb);
+    B.kapc[c] = kappa_of(pb, kind, a);
+  }
+  if (s != 0.0) {
+    const int nx = L.nflux + L.np;
+    GSTRIDE(i, nx) B.x[i] = fma(s, __ldcg(&B.dx[i]), B.x[i]);
+  }
+  return acc;
+}
+
+// Algorithm 1 from x (residual norm rn) along s0 dx, with trial norms from the linear parts. Returns the accepted
+// scaling s * s0 in `step` (0: every trial was non-finite, x is kept; a non-finite trial counts as +infinity) and its
+// residual norm in rn.
+__device__ bool backtrack_lin(const LevelDev& L, const LinParts& bx, const LinParts& dx, const CoarseStepParams& P,
+                              const double* b, double s0, double& rn, double& step, int& trials, Grid& g) {
+  double s = 1.0, r_s = 0.0;
+  if (!trial_norm(L, bx, dx, s * s0, b, P.kind, P.a, g, r_s)) return false;
+  ++trials;
+  if (!isfinite(r_s)) r_s = HUGE_VAL;
   int n = 0;
   while (r_s > rn && n < P.bt_nmax) {
     double r_half = 0.0;
-    if (!coarse_residual_dev(L, xb[t2], xb[cur], B.dx, 0.5 * s * s0, B.b, B.rt, nullptr, B.kapc, P.kind, P.a, g,
-                             r_half))
-      return false;
-    ++evals;
+    if (!trial_norm(L, bx, dx, 0.5 * s * s0, b, P.kind, P.a, g, r_half)) return false;
+    ++trials;
     if (!isfinite(r_half)) r_half = HUGE_VAL;
     if (r_half > P.bt_theta * r_s) break;
     s *= 0.5;
     ++n;
     r_s = r_half;
-    const int t = t1;
-    t1 = t2;
-    t2 = t;
   }
-  if (r_s == HUGE_VAL) return true;   // no finite trial: the iterate is kept
-  cur = t1;
+  if (r_s == HUGE_VAL) {
+    step = 0.0;
+    return true;
+  }
+  step = s * s0;
   rn = r_s;
   return true;
 }
 
+// One launch. On entry x (and, with backtrack_first, the correction in dx and ||A(x) - b|| in rn_in); on exit x, r,
+// nb = -r and kappa per cell at the final x.
 template <class T>
 __global__ void __launch_bounds__(kPThreads, 1) kp_coarse_step(LevelDev L, const T* __restrict__ Hc,
                                                            const T* __restrict__ Sinv, CoarseStepBufs<T> B,
@@ -1190,22 +1223,33 @@ __global__ void __launch_bounds__(kPThreads, 1) kp_coarse_step(LevelDev L, const
                                                            int gsz, int gsz_reg, CoarseStepResult* res) {
   __shared__ double sm[kSmDoubles];
   Grid g{gs, partial, sm, 0u};
-  double* const xb[3] = {B.x, B.xt1, B.xt2};
-  int cur = 0;
-  int iters = 0, steps = 0, evals = 0, bad = 0;
+  int iters = 0, steps = 0, evals = 0, trials = 0, bad = 0;
   double rn = P.rn_in;
+  double pending = 0.0;   // accepted step not yet added to the linear parts of x
+  // linear parts of x (and of the given correction)
+  lin_parts_pass(L, B.x, B.base, B.base, 0.0);
+  ++evals;
   if (P.backtrack_first) {
-    if (!coarse_backtrack_dev<T>(L, B, P, xb, cur, 1.0, rn, evals, g)) return;
-  }
-  double r0 = 0.0;
-  for (int k = 0; k < P.nsteps; ++k) {
-    if (!coarse_residual_dev(L, xb[cur], nullptr, nullptr, 0.0, B.b, B.r, B.nb, B.kapc, P.kind, P.a, g, rn)) return;
+    lin_parts_pass(L, B.dx, B.dir, B.dir, 0.0);
     ++evals;
-    if (!isfinite(rn)) {
-      bad = 1;
-      break;
-    }
-    if (k == 0) r0 = rn;
+  }
+  if (!grid_barrier(g)) return;
+  double step = 0.0;
+  if (P.backtrack_first) {
+    if (!backtrack_lin(L, B.base, B.dir, P, B.b, 1.0, rn, step, trials, g)) return;
+  }
+  const double acc = accept_pass<T>(L, B, step, P.kind, P.a);   // r, nb, kappa at the (new) x
+  pending = step;
+  if (!P.backtrack_first) {
+    double s1[1] = {acc};
+    if (!grid_sum<1>(g, s1)) return;
+    rn = sqrt(s1[0]);
+    if (!isfinite(rn)) bad = 1;
+  } else if (!grid_barrier(g)) {
+    return;
+  }
+  const double r0 = rn;
+  for (int k = 0; k < P.nsteps && !bad; ++k) {
     if (P.coarsest && (rn <= P.tol_rel * r0 || rn <= P.tol_abs)) break;
     int it = 0;
     double rr0 = 0.0, rr = 0.0;
@@ -1219,31 +1263,23 @@ __global__ void __launch_bounds__(kPThreads, 1) kp_coarse_step(LevelDev L, const
       break;
     }
     if (!grid_barrier(g)) return;   // dx complete
+    // linear parts of dx (after folding the previous accepted step into those of x), and the clamp on Pi~ dp
+    lin_parts_pass(L, B.dx, B.dir, B.base, pending);
+    ++evals;
     double s0 = 1.0;
     if (P.dp_clamp > 0.0) {
       double m = 0.0;
-      GSTRIDE(c, L.nc) {
-        const int po = L.p_off[c];
-        double v = 0.0;
-        for (int q = 0; q < L.m[c]; ++q) v = fma(L.w[po + q], __ldcg(&B.dx[L.nflux + po + q]), v);
-        m = fmax(m, fabs(v));
-      }
+      GSTRIDE(c, L.nc) m = fmax(m, fabs(B.dir.pb[c]));   // written by this thread just above
       if (!grid_max(g, m)) return;
       if (m > P.dp_clamp) s0 = P.dp_clamp / m;
-    }
-    if (!coarse_backtrack_dev<T>(L, B, P, xb, cur, s0, rn, evals, g)) return;
-    ++steps;
-  }
-  if (P.final_residual) {
-    if (!coarse_residual_dev(L, xb[cur], nullptr, nullptr, 0.0, B.b, B.r, nullptr, B.kapc, P.kind, P.a, g, rn))
+    } else if (!grid_barrier(g)) {
       return;
-    ++evals;
-  }
-  if (cur != 0) {
-    // the iterate ends in a trial buffer: copy it to x (every block has passed the last reduction, after which
-    // nothing reads it)
-    const int nx = L.nflux + L.np;
-    GSTRIDE(i, nx) B.x[i] = __ldcg(&xb[cur][i]);
+    }
+    if (!backtrack_lin(L, B.base, B.dir, P, B.b, s0, rn, step, trials, g)) return;
+    (void)accept_pass<T>(L, B, step, P.kind, P.a);
+    pending = step;
+    if (!grid_barrier(g)) return;   // r, nb, kappa and x complete
+    ++steps;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     res->rn = rn;
@@ -1251,6 +1287,7 @@ __global__ void __launch_bounds__(kPThreads, 1) kp_coarse_step(LevelDev L, const
     res->steps = steps;
     res->res_evals = evals;
     res->bad = bad;
+    res->trials = trials;
   }
 }
 

@@ -58,11 +58,19 @@ struct HybPipeBufs {
   T *w = nullptr, *z = nullptr, *s = nullptr, *ma = nullptr, *mb = nullptr;
 };
 
+// The linear parts of the coarse operator at a vector v = [sigma; p] with kappa left out: per local flux slot y of
+// cell c (local index u) ms[y] = (M_c sigma_c)_u and ds[y] = (D_c^T p_c)_u (nyl each), per pressure unknown
+// dr[i] = (D_c sigma_c)_i (np), per cell pb[c] = (Pi~ p)_c (nc).
+struct LinParts {
+  double *ms, *ds, *dr, *pb;
+};
+
 // Device buffers of one coarse level used by the fused Picard step (all of length nflux + np unless noted).
 template <class T>
 struct CoarseStepBufs {
-  double *x, *b, *r, *nb, *dx, *xt1, *xt2, *rt;   // iterate, rhs, residual, -residual, step, trials, trial residual
+  double *x, *b, *r, *nb, *dx;                    // iterate, rhs, residual, -residual, step
   double* kapc;                                   // kappa per cell (nc)
+  LinParts base, dir;                             // linear parts at x and along dx (Algorithm 1's trials)
   T *ylam, *ydiag, *lam, *lr, *lz, *pa, *pb, *lq, *ldinv;   // hybridized CG (nif / nlam)
   HybPipeBufs<T> pipe;   // set: pipelined hybridized CG (one grid synchronisation per iteration)
 };
@@ -78,7 +86,6 @@ struct CoarseStepParams {
   int nsteps;            // Picard steps after that
   int coarsest;          // 1: stop the steps once ||r|| <= tol_rel ||r(x_entry)|| or ||r|| <= tol_abs
   double tol_rel, tol_abs;
-  int final_residual;    // 1: r = A(x) - b at the final x
   double lin_tol;
   int maxit;
 };
@@ -87,12 +94,14 @@ struct CoarseStepResult {
   double rn;        // ||A(x) - b|| at the final x
   int iters;        // hybridized CG iterations
   int steps;        // Picard steps taken
-  int res_evals;    // coarse operator evaluations
+  int res_evals;    // evaluations of the operator's linear parts (one per Picard step and one on entry)
   int bad;          // 0, or where a non-finite value appeared: 1 residual, 2 hybridized CG
+  int trials;       // residual norms of Algorithm 1's trial points (from the linear parts)
 };
 
-// One launch: [Algorithm 1 along a given correction], up to nsteps coarse Picard steps (residual, frozen-kappa
-// hybridized solve, clamp on Pi~ dp, Algorithm 1), [final residual]; every decision is taken on the device.
+// One launch: [Algorithm 1 along a given correction], up to nsteps coarse Picard steps (frozen-kappa hybridized
+// solve, clamp on Pi~ dp, Algorithm 1), leaving the residual r = A(x) - b (and -r, kappa per cell) at the final x;
+// every decision is taken on the device.
 template <class T>
 cudaError_t launch_coarse_step(cudaStream_t st, const LevelDev& L, const T* Hc, const T* Sinv,
                                const CoarseStepBufs<T>& B, const CoarseStepParams& P, double* partial, GridSync gs,

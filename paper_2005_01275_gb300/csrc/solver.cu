@@ -41,11 +41,12 @@ struct Error : std::runtime_error {
 
 // Per coarse level work buffers.
 struct CoarseBuf {
-  double *x = nullptr, *b = nullptr, *r = nullptr, *dx = nullptr, *nb = nullptr, *xt1 = nullptr, *xt2 = nullptr;
-  double *xc = nullptr, *yl = nullptr, *kapc = nullptr, *ptmp = nullptr, *rt = nullptr;
+  double *x = nullptr, *b = nullptr, *r = nullptr, *dx = nullptr, *nb = nullptr, *xt2 = nullptr;
+  double *xc = nullptr, *yl = nullptr, *kapc = nullptr, *ptmp = nullptr;
   double *ylam = nullptr, *ydiag = nullptr, *lam = nullptr, *lr = nullptr, *lz = nullptr, *lpa = nullptr, *lpb = nullptr,
          *lq = nullptr, *ldinv = nullptr, *xi = nullptr;
   double *hw = nullptr, *hz = nullptr, *hs = nullptr, *hma = nullptr, *hmb = nullptr;   // pipelined hybridized CG
+  LinParts base{}, dir{};   // linear parts of the operator at x and along dx (fused coarse step)
   float *f_ylam = nullptr, *f_ydiag = nullptr, *f_lam = nullptr, *f_lr = nullptr, *f_lz = nullptr,
         *f_lpa = nullptr, *f_lpb = nullptr, *f_lq = nullptr, *f_ldinv = nullptr;
   double rn = 0.0;  // ||A(x) - b|| at the current x (valid after coarse_res)
@@ -84,6 +85,8 @@ struct Shared {
   // algorithmic flops (FMA = 2) per level: one hybridized CG iteration, the fixed work of one hybridized solve
   // (right-hand side per interface slot, local recovery), one coarse operator evaluation
   double hyb_flops_per_iter[8] = {0}, hyb_flops_per_solve[8] = {0}, coarse_res_flops[8] = {0};
+  // one trial evaluation from the linear parts (also the pass that accepts a trial): bytes and flops
+  double coarse_trial_bytes[8] = {0}, coarse_trial_flops[8] = {0};
   ~Shared() {
     for (void* p : allocs) cudaFree(p);
   }
@@ -411,6 +414,11 @@ void upload_level(nlmg_ctx* c, int l) {
   c->sh->hyb_flops_per_iter[l] = 2.0 * (double)Hc.size() + 2.0 * D.nif + 18.0 * nlam;
   c->sh->hyb_flops_per_solve[l] = per_solve;
   c->sh->coarse_res_flops[l] = 2.0 * (double)L.Mloc.size() + 4.0 * (double)L.Dloc.size();
+  // a trial: per flux unknown its b and slot ids, per owner slot its cell and the six parts read (ms, ds, pb of x and
+  // of dx), per pressure unknown b and two parts; about 20 flops per owner slot (three FMAs and 1/kappa), 4 per
+  // pressure unknown, 2 per unknown for the norm
+  c->sh->coarse_trial_bytes[l] = 16.0 * D.nflux + (double)D.nyl * (4.0 + 48.0) + 24.0 * D.np;
+  c->sh->coarse_trial_flops[l] = 20.0 * (double)D.nyl + 6.0 * D.np + 2.0 * D.nflux;
 }
 
 // Work buffers of coarse level l (per context).
@@ -424,13 +432,11 @@ void alloc_level(nlmg_ctx* c, int l) {
   B.r = c->dalloc<double>(nx);
   B.dx = c->dalloc<double>(nx);
   B.nb = c->dalloc<double>(nx);
-  B.xt1 = c->dalloc<double>(nx);
   B.xt2 = c->dalloc<double>(nx);
   B.xc = c->dalloc<double>(nx);
   B.yl = c->dalloc<double>(D.nyl);
   B.kapc = c->dalloc<double>(D.nc);
   B.ptmp = c->dalloc<double>(nx);
-  B.rt = c->dalloc<double>(nx);
   B.ylam = c->dalloc<double>(D.nif);
   B.ydiag = c->dalloc<double>(D.nif);
   B.f_ylam = c->dalloc<float>(D.nif);
@@ -445,6 +451,12 @@ void alloc_level(nlmg_ctx* c, int l) {
   B.ldinv = c->dalloc<double>(nlam);
   B.xi = c->dalloc<double>(nlam);
   for (double** pp : {&B.hw, &B.hz, &B.hs, &B.hma, &B.hmb}) *pp = c->dalloc<double>(nlam);
+  for (LinParts* lp : {&B.base, &B.dir}) {
+    lp->ms = c->dalloc<double>(D.nyl);
+    lp->ds = c->dalloc<double>(D.nyl);
+    lp->dr = c->dalloc<double>(D.np);
+    lp->pb = c->dalloc<double>(D.nc);
+  }
 }
 
 void upload_transfer(nlmg_ctx* c, int l) {
@@ -896,7 +908,9 @@ void make_coarse_problem(nlmg_ctx* c, int l) {
 
 // One launch of the fused coarse Picard step on level l (see launch_coarse_step): optional Algorithm 1 along B.dx
 // from s = 1, then up to nsteps Picard steps, then optionally the residual at the final x. B.rn is updated.
-void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coarsest, bool final_residual) {
+// One launch of the fused coarse step on level l: [Algorithm 1 along B.dx,] nsteps Picard steps; leaves x, r = A(x) - b,
+// -r and kappa per cell at the final x, and ||r|| in B.rn.
+void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coarsest) {
   const LevelDev& L = c->LD[l];
   CoarseBuf& B = c->CB[l];
   CoarseStepParams P{};
@@ -911,7 +925,6 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
   P.coarsest = coarsest ? 1 : 0;
   P.tol_rel = c->opt.coarsest_tol > 0.0 ? c->opt.coarsest_tol : c->tol_rel;
   P.tol_abs = c->tol_abs;
-  P.final_residual = final_residual ? 1 : 0;
   P.maxit = c->opt.lin_maxit;
   GridSync gs{c->d_bar, &c->d_res->err, c->sm_cap};
   CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->st));
@@ -922,14 +935,14 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
   int pi = c->prof_begin(kid);
   if (c->opt.lin_precision == 1) {
     P.lin_tol = std::max(c->coarse_lin_tol_eff, 1e-6);
-    CoarseStepBufs<float> Bf{B.x, B.b, B.r, B.nb, B.dx, B.xt1, B.xt2, B.rt, B.kapc, B.f_ylam, B.f_ydiag,
+    CoarseStepBufs<float> Bf{B.x, B.b, B.r, B.nb, B.dx, B.kapc, B.base, B.dir, B.f_ylam, B.f_ydiag,
                              B.f_lam, B.f_lr, B.f_lz, B.f_lpa, B.f_lpb, B.f_lq, B.f_ldinv, HybPipeBufs<float>{}};
     CK(launch_coarse_step<float>(c->st, L, L.Hc32, L.Sinv32, Bf, P, c->d_partial, gs, dres));
   } else {
     P.lin_tol = c->coarse_lin_tol_eff;
     // pipelined hybridized CG at loose tolerances; the two-synchronisation CG when a tight solve is asked for
     const bool pipe = c->coarse_lin_tol_eff >= 1e-6;
-    CoarseStepBufs<double> Bd{B.x, B.b, B.r, B.nb, B.dx, B.xt1, B.xt2, B.rt, B.kapc, B.ylam, B.ydiag,
+    CoarseStepBufs<double> Bd{B.x, B.b, B.r, B.nb, B.dx, B.kapc, B.base, B.dir, B.ylam, B.ydiag,
                               B.lam, B.lr, B.lz, B.lpa, B.lpb, B.lq, B.ldinv,
                               pipe ? HybPipeBufs<double>{B.hw, B.hz, B.hs, B.hma, B.hmb} : HybPipeBufs<double>{}};
     CK(launch_coarse_step<double>(c->st, L, L.Hc, L.Sinv, Bd, P, c->d_partial, gs, dres));
@@ -948,10 +961,12 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
   B.rn = R.rn;
   if (pi >= 0) {
     c->prof.bytes[kid] += (double)R.iters * c->sh->hyb_bytes_per_iter[l] * (c->opt.lin_precision == 1 ? 0.5 : 1.0) +
-                          (double)R.res_evals * c->sh->coarse_res_bytes[l];
+                          (double)R.res_evals * c->sh->coarse_res_bytes[l] +
+                          (double)(R.trials + R.steps + 1) * c->sh->coarse_trial_bytes[l];
     c->prof.flops[kid] += (double)R.iters * c->sh->hyb_flops_per_iter[l] +
-                        (double)R.steps * c->sh->hyb_flops_per_solve[l] +
-                        (double)R.res_evals * c->sh->coarse_res_flops[l];
+                          (double)R.steps * c->sh->hyb_flops_per_solve[l] +
+                          (double)R.res_evals * c->sh->coarse_res_flops[l] +
+                          (double)(R.trials + R.steps + 1) * c->sh->coarse_trial_flops[l];
   }
   c->lin_iters += R.iters;
   c->lin_iters_level[l] += R.iters;
@@ -962,10 +977,10 @@ void coarse_cycle(nlmg_ctx* c, int l) {
   CoarseBuf& B = c->CB[l];
   const LevelDev& L = c->LD[l];
   if (l == c->nlev() - 1) {
-    coarse_step(c, l, false, o.coarsest_steps, true, false);
+    coarse_step(c, l, false, o.coarsest_steps, true);
     return;
   }
-  coarse_step(c, l, false, 1, false, true);   // pre-smoothing, then r at the smoothed x for the restriction
+  coarse_step(c, l, false, 1, false);   // pre-smoothing; leaves r at the smoothed x for the restriction
   make_coarse_problem(c, l);
   coarse_cycle(c, l + 1);
   const LevelDev& C = c->LD[l + 1];
@@ -974,7 +989,7 @@ void coarse_cycle(nlmg_ctx* c, int l) {
   launch_sub(c->st, C.nflux + C.np, Bc.x, Bc.xc, Bc.ptmp);
   launch_csr(c->st, T.ps_n, T.ps_off, T.ps_col, T.ps_val, Bc.ptmp, B.dx, 1.0, 0.0);
   launch_prolong_p(c->st, T, Bc.ptmp + C.nflux, B.dx + L.nflux);
-  coarse_step(c, l, true, 1, false, false);   // Algorithm 1 along the correction, then post-smoothing
+  coarse_step(c, l, true, 1, false);   // Algorithm 1 along the correction, then post-smoothing
 }
 
 // One FAS cycle from level 0 (Algorithm 2). Returns true if it stopped after pre-smoothing.
@@ -1216,11 +1231,11 @@ static void init_work(nlmg_ctx* c) {
   c->d_cnt = c->dalloc<unsigned>(16);
   CK(cudaMemsetAsync(c->d_cnt, 0, 16 * sizeof(unsigned), c->st));
   c->d_sc = c->dalloc<double>(64);
-  static_assert(sizeof(CoarseStepResult) <= sizeof(PcgResult), "result slots");
-  c->d_res = c->dalloc<PcgResult>(2);   // the CG result, then the coarse-step result
+  static_assert(sizeof(CoarseStepResult) <= 2 * sizeof(PcgResult), "result slots");
+  c->d_res = c->dalloc<PcgResult>(3);   // the CG result, then the coarse-step result (two slots)
   c->d_bar = c->dalloc<unsigned>(64);   // count and generation on separate 128-byte lines
   CK(cudaMemsetAsync(c->d_bar, 0, 64 * sizeof(unsigned), c->st));
-  CK(cudaMallocHost(&c->h_res, 2 * sizeof(PcgResult)));
+  CK(cudaMallocHost(&c->h_res, 3 * sizeof(PcgResult)));
   CK(cudaMemsetAsync(c->d_sc, 0, 64 * sizeof(double), c->st));
   c->reset_inner_tols();
   alloc_fine(c);
