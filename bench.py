@@ -33,8 +33,10 @@ SAMPLE_SCALE = 16          # side of the bounded CPU sample of the same generato
 
 # DRAM bytes (read + write) per launch on the 64^3 workload with the default options, from ncu captures of the
 # kernels as they are now (averaged over the launches of one solve where they differ): valid for that kernel, that
-# workload and those options only, else the traffic is reported as null. Empty until the kernels are captured.
-DRAM_BYTES_64 = {}
+# workload and those options only, else the traffic is reported as null.
+DRAM_BYTES_64 = {0: 23.102e6,     # kp_fine_cg_reg<double, 4>, mean of the 8 launches of a solve
+                 1: 25.362e6,     # kp_coarse_step<double>, mean of the 15 launches (10 on level 1, 5 coarsest solves)
+                 3: 25.216e6}     # kp_fine_bicgstab, mean of the 3 launches
 
 KERNELS = {0: ("kp_fine_cg_reg<double, 4> (persistent register-resident pipelined Jacobi-scaled CG of the level-0 "
                "Picard step)", "kp_fine_cg* (level-0 Picard CG)"),
