@@ -56,6 +56,25 @@ def backtracking(res_norm, x, dx, r_x, nmax, theta):
     return x + s * dx, r_s, s, n
 
 
+def level_params(H, mesh, kind, a):
+    """The nonlinearity's parameter on every level: `a` itself, except for the Richards kind, whose cell heights are
+    carried to the coarse levels as volume-weighted aggregate means (the averaging of Pi~ p, eq. pwc_projector)."""
+    L = len(H.levels)
+    if kind != tpfa.KAPPA_RICHARDS:
+        return [a] * L
+    out = [a]
+    z = np.asarray(a.z, dtype=np.float64)
+    vol = np.asarray(mesh.cell_volume, dtype=np.float64)
+    for l in range(L - 1):
+        agg = H.transfers[l].agg_of
+        na = int(agg.max()) + 1
+        vz = np.bincount(agg, weights=vol * z, minlength=na)
+        vol = np.bincount(agg, weights=vol, minlength=na)
+        z = vz / vol
+        out.append(tpfa.RichardsParams(a.alpha, a.beta, z))
+    return out
+
+
 @dataclass
 class Stats:
     cycles: int = 0
@@ -73,6 +92,7 @@ class FAS:
         self.f, self.g, self.o = f_cell, g_face, opts
         self.dofs = tpfa.flux_dofs(mesh)
         self.stats = Stats()
+        self.a_lev = level_params(H, mesh, kind, a)
         self.r0_ref = 0.0         # ||R(p_0)|| of the current solve (set by vcycle; 0: no Newton step)
         self.newton_off = False   # set once a Newton step reduced the residual by less than NEWTON_KEEP
 
@@ -146,13 +166,13 @@ class FAS:
     def res(self, l, x, b):
         lev = self.H.levels[l]
         s, p = self.split(l, x)
-        return coarse.operator(lev, self.kind, self.a, s, p) - b
+        return coarse.operator(lev, self.kind, self.a_lev[l], s, p) - b
 
     def picard_smooth(self, l, x, b, r_x=None):
         lev = self.H.levels[l]
         o = self.o
         s, p = self.split(l, x)
-        sP, pP = coarse.picard_solve(lev, self.kind, self.a, s, p, b)
+        sP, pP = coarse.picard_solve(lev, self.kind, self.a_lev[l], s, p, b)
         dx = np.concatenate([sP, pP]) - x
         if o["dp_clamp"] > 0:
             mx = np.max(np.abs(coarse.pbar(lev, dx[lev.n_flux:])))
@@ -184,7 +204,7 @@ class FAS:
         r = self.res(l, x, b)
         rs, rp = r[:lev.n_flux], r[lev.n_flux:]
         xc = np.concatenate([tr.Qsigma @ s, tr.Qp @ p])
-        bc = coarse.operator(levc, self.kind, self.a, xc[:levc.n_flux], xc[levc.n_flux:]) \
+        bc = coarse.operator(levc, self.kind, self.a_lev[l + 1], xc[:levc.n_flux], xc[levc.n_flux:]) \
             - np.concatenate([tr.Psigma.T @ rs, tr.Pp.T @ rp])
         yc = self.cycle_coarse(l + 1, xc, bc)
         e = yc - xc
@@ -209,7 +229,7 @@ class FAS:
         Rp = self.R(p)
         xc = np.concatenate([tr.Qsigma @ self.sigma0(p), tr.Qp @ p])
         # mixed fine residual is [0; -R(p)]; R r^0 = [0; P_p^T (-R(p))]
-        bc = coarse.operator(levc, self.kind, self.a, xc[:levc.n_flux], xc[levc.n_flux:]) \
+        bc = coarse.operator(levc, self.kind, self.a_lev[1], xc[:levc.n_flux], xc[levc.n_flux:]) \
             - np.concatenate([np.zeros(levc.n_flux), tr.Pp.T @ (-Rp)])
         yc = self.cycle_coarse(1, xc, bc)
         dp = tr.Pp @ (yc - xc)[levc.n_flux:]
@@ -231,14 +251,15 @@ class FAS:
         tr, levc = H.transfers[0], H.levels[1]
         Rp = self.R(p)
         xs[1] = np.concatenate([tr.Qsigma @ self.sigma0(p), tr.Qp @ p])
-        bs[1] = coarse.operator(levc, self.kind, self.a, xs[1][:levc.n_flux], xs[1][levc.n_flux:]) \
+        bs[1] = coarse.operator(levc, self.kind, self.a_lev[1], xs[1][:levc.n_flux], xs[1][levc.n_flux:]) \
             - np.concatenate([np.zeros(levc.n_flux), tr.Pp.T @ (-Rp)])
         for l in range(1, L - 1):
             lev, tr, levc = H.levels[l], H.transfers[l], H.levels[l + 1]
             s, q = self.split(l, xs[l])
             r = self.res(l, xs[l], bs[l])
             xs[l + 1] = np.concatenate([tr.Qsigma @ s, tr.Qp @ q])
-            bs[l + 1] = coarse.operator(levc, self.kind, self.a, xs[l + 1][:levc.n_flux], xs[l + 1][levc.n_flux:]) \
+            bs[l + 1] = coarse.operator(levc, self.kind, self.a_lev[l + 1], xs[l + 1][:levc.n_flux],
+                                        xs[l + 1][levc.n_flux:]) \
                 - np.concatenate([tr.Psigma.T @ r[:lev.n_flux], tr.Pp.T @ r[lev.n_flux:]])
         for l in range(1, L):
             x0s[l] = xs[l].copy()

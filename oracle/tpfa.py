@@ -5,6 +5,9 @@ Follows Sec. 2.1 of the paper:
     (the printed comma "(g_D, - p_K)" is read as a minus sign), Neumann flux sigma = -|eps| g_N;
   * eq. half-transmissibility: Ups_i,eps = kappa(p_i) * Ups_bar_i,eps, Ups_KL the harmonic mean of the two halves;
   * eq. permeability_pressure_relationship: kappa(p) = exp(a p); the second kind (1 + p^2)^-1 is a workload's;
+    the third is the static Richards' equation of Sec. 4.3 (Example 3): with p = psi + z, K(p) = K_hat(p - z) and
+    eq. permeability_function_richards K_hat(psi) = K_0 alpha / (alpha + |psi|^beta), so kappa_K(p) = alpha /
+    (alpha + |p - z_K|^beta) with K_0 in the transmissibilities and z_K the height of cell K (RichardsParams);
   * eq. FV_matrix and its definitions: the mixed matrices M(p) (diagonal), D, and the vectors g, [f];
   * Remark after eq. FV_matrix: the equivalent reduced cell-centred residual (eliminating sigma gives
     D M^-1 D^T p + D M^-1 g = -[f] for the mixed system as printed; the remark's sign on g is read from the mixed
@@ -14,18 +17,33 @@ which equals minus the pressure row of the mixed residual with sigma eliminated.
 """
 from __future__ import annotations
 
+from dataclasses import dataclass
+
 import numpy as np
 import scipy.sparse as sp
 
-KAPPA_EXP, KAPPA_INV1P2 = 0, 1
+KAPPA_EXP, KAPPA_INV1P2, KAPPA_RICHARDS = 0, 1, 2
 BC_INTERIOR, BC_DIRICHLET, BC_NEUMANN = 0, 1, 2
 
 
+@dataclass
+class RichardsParams:
+    """Parameters of the Richards nonlinearity on one level: alpha, beta of eq. permeability_function_richards and
+    the height z of every cell of that level (coarse levels: the volume-weighted aggregate mean, like Pi~ p)."""
+    alpha: float
+    beta: float
+    z: np.ndarray
+
+
 def kappa(p, kind, a):
-    """kappa(p) = exp(a p) (eq. permeability_pressure_relationship) or (1 + p^2)^-1."""
+    """kappa(p) = exp(a p) (eq. permeability_pressure_relationship), (1 + p^2)^-1, or, for the Richards kind,
+    alpha / (alpha + |p - z|^beta) per cell (a: RichardsParams)."""
     p = np.asarray(p, dtype=np.float64)
     if kind == KAPPA_EXP:
         return np.exp(a * p)
+    if kind == KAPPA_RICHARDS:
+        psi = np.abs(p - a.z)
+        return a.alpha / (a.alpha + psi ** a.beta)
     return 1.0 / (1.0 + p * p)
 
 
@@ -34,6 +52,11 @@ def dkappa(p, kind, a):
     p = np.asarray(p, dtype=np.float64)
     if kind == KAPPA_EXP:
         return a * np.exp(a * p)
+    if kind == KAPPA_RICHARDS:
+        psi = p - a.z
+        apsi = np.abs(psi)
+        den = a.alpha + apsi ** a.beta
+        return -a.alpha * a.beta * np.sign(psi) * apsi ** (a.beta - 1.0) / (den * den)
     return -2.0 * p / (1.0 + p * p) ** 2
 
 

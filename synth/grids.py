@@ -13,7 +13,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 BC_INTERIOR, BC_DIRICHLET, BC_NEUMANN = 0, 1, 2
-KAPPA_EXP, KAPPA_INV1P2 = 0, 1
+KAPPA_EXP, KAPPA_INV1P2, KAPPA_RICHARDS = 0, 1, 2
 
 
 @dataclass
@@ -37,14 +37,17 @@ def _lin(shape):
     return np.arange(int(np.prod(shape)), dtype=np.int64).reshape(shape[::-1]).T  # index = i + nx*(j + ny*k)
 
 
-def cartesian_mesh(shape, K, dirichlet_x=True):
-    """Unit square/cube split into shape cells; K is [N] in lexicographic order (x fastest).
+def cartesian_mesh(shape, K, dirichlet_x=True, lengths=None, dirichlet_axes=None):
+    """Unit square/cube (or a box of the given side lengths) split into shape cells; K is [N] in lexicographic order
+    (x fastest).
 
-    Boundary faces on x = 0 and x = 1 are Dirichlet, all others Neumann (no-flow unless data says otherwise).
+    Boundary faces on x = 0 and x = 1 are Dirichlet, all others Neumann (no-flow unless data says otherwise);
+    dirichlet_axes, if given, lists the axes whose two boundary sides are Dirichlet instead.
     """
     shape = tuple(int(s) for s in shape)
     d = len(shape)
-    h = np.array([1.0 / s for s in shape])
+    lengths = [1.0] * d if lengths is None else [float(v) for v in lengths]
+    h = np.array([lengths[i] / s for i, s in enumerate(shape)])
     idx = _lin(shape)
     N = idx.size
     vol = np.full(N, float(np.prod(h)))
@@ -68,7 +71,8 @@ def cartesian_mesh(shape, K, dirichlet_x=True):
             cells = np.sort(np.take(idx, side, axis=ax).reshape(-1))
             fc.append(np.stack([cells, np.full(cells.size, -1)], 1))
             ht.append(np.stack([a_face * K[cells] / dist, np.zeros(cells.size)], 1))
-            kind = BC_DIRICHLET if (ax == 0 and dirichlet_x) else BC_NEUMANN
+            dir_here = (ax in dirichlet_axes) if dirichlet_axes is not None else (ax == 0 and dirichlet_x)
+            kind = BC_DIRICHLET if dir_here else BC_NEUMANN
             bc.append(np.full(cells.size, kind, np.uint8))
             area.append(np.full(cells.size, a_face))
     return Mesh(n_cells=N, cell_volume=vol,
@@ -218,6 +222,8 @@ class Problem:
     g_face: np.ndarray               # [F] Dirichlet value or Neumann flux density
     opts: dict = field(default_factory=dict)
     name: str = ""
+    kappa_b: float = 0.0                    # second parameter (beta of the Richards kind)
+    cell_shift: np.ndarray | None = None    # [N] cell heights z of the Richards kind (kappa depends on p - z)
 
 
 def default_options(**kw):
@@ -303,3 +309,35 @@ def multi_rhs_rows(mesh, n_rhs, seed):
 
 
 CONFIGS = ("cart2d_32", "chan3d_64")
+
+
+# alpha, beta and k0 [cm/day] of the two media of the Richards example (Sec. 4.3, Table richard-parameters)
+RICHARDS_MEDIA = {"loam": (1.246e2, 1.77, 1.067e0), "sand": (1.175e6, 4.74, 8.160e2)}
+
+
+def richards_problem(medium="loam", refine=0):
+    """Static Richards' equation (Sec. 4.3, Example 3) on (0, 4000) x (0, 1000) (lengths in cm, the units of the
+    media's parameters), 160 x 40 cells refined `refine` times by 2 in each direction; K_0 = k0 of the medium,
+    kappa_K(p) = alpha / (alpha + |p - z_K|^beta) with p = psi + z and z_K the cell centre's height; f = 0.
+    The paper gives the boundary conditions only in a figure; assumed here: no flow through the sides, the water
+    table at the bottom (psi = 0, p = 0 on z = 0), and on the top (z = 1000) a ponded strip psi = 0 (p = 1000) on
+    x < 1000 and a dry surface psi = -500 (p = 500) elsewhere. FAS options: aggregates of 36 cells on every level
+    (the example's coarsening factor), 3 levels on the 160 x 40 mesh and 4 on refined ones, 4 spectral modes, at most
+    4 halvings in Algorithm 1 for loam and 10 for sand (as in the example), no pressure-change clamp."""
+    alpha, beta, k0 = RICHARDS_MEDIA[medium]
+    nx, nz = 160 * 2 ** refine, 40 * 2 ** refine
+    Lx, Lz = 4000.0, 1000.0
+    mesh = cartesian_mesh((nx, nz), np.full(nx * nz, k0), lengths=(Lx, Lz), dirichlet_axes=(1,))
+    hx, hz = Lx / nx, Lz / nz
+    z_cell = (np.arange(nx * nz) // nx + 0.5) * hz
+    g = np.zeros(mesh.n_faces)
+    dirf = np.where(mesh.face_bc == BC_DIRICHLET)[0]
+    K = mesh.face_cells[dirf, 0]
+    top = K // nx == nz - 1
+    x_c = (K % nx + 0.5) * hx
+    g[dirf] = np.where(top, np.where(x_c < 1000.0, Lz, Lz - 500.0), 0.0)
+    levels = 3 if refine == 0 else 4
+    opts = default_options(n_levels=levels, agg_size=[36] * 7, modes=[4] * 7,
+                           bt_nmax=4 if medium == "loam" else 10)
+    return Problem(mesh, KAPPA_RICHARDS, alpha, np.zeros(mesh.n_cells), g, opts, "richards_" + medium,
+                   kappa_b=beta, cell_shift=z_cell)

@@ -39,9 +39,11 @@ def test_reduced_equals_mixed_with_sigma_eliminated():
     assert np.allclose(r, -r_mixed, rtol=1e-12, atol=1e-12)
 
 
-@pytest.mark.parametrize("kind,a", [(KAPPA_EXP, 2.0), (KAPPA_INV1P2, 0.0)])
+@pytest.mark.parametrize("kind,a", [(KAPPA_EXP, 2.0), (KAPPA_INV1P2, 0.0), (tpfa.KAPPA_RICHARDS, None)])
 def test_jacobian_matches_central_differences(kind, a):
     mesh = cartesian_mesh((5, 4, 3), lognormal_field((5, 4, 3), 1.0, 2.0, seed=4))
+    if kind == tpfa.KAPPA_RICHARDS:      # loam parameters, heights of the cell centres in [0, 1] scaled to 0.3
+        a = tpfa.RichardsParams(1.246e2, 1.77, 0.3 * ((np.arange(mesh.n_cells) // 20) + 0.5) / 3.0)
     rng = np.random.default_rng(1)
     p = rng.uniform(-0.5, 1.0, mesh.n_cells)
     g = _dirichlet(mesh, 1.0, 0.0)
@@ -144,3 +146,16 @@ def test_frozen_matrix_is_m_matrix_and_reproduces_residual():
     np.add.at(rhs, m.face_cells[d, 0], kp[m.face_cells[d, 0]] * m.half_trans[d, 0] * pr.g_face[d])
     assert np.allclose(A @ p - rhs, tpfa.reduced_residual(m, pr.kappa_kind, pr.kappa_a, p, pr.f_cell, pr.g_face),
                        rtol=1e-12, atol=1e-10)
+
+
+def test_richards_hydrostatic_state_is_exact():
+    """Static Richards' equation (Sec. 4.3) with p = psi + z: a constant p carries no flux whatever kappa(p - z) is,
+    so with p = c on every Dirichlet face and no source the residual of p = c vanishes; a tilted p does not."""
+    from synth.grids import richards_problem
+    pr = richards_problem("sand", 0)
+    a = tpfa.RichardsParams(pr.kappa_a, pr.kappa_b, pr.cell_shift)
+    g = np.where(pr.mesh.face_bc == 1, 250.0, 0.0)
+    r = tpfa.reduced_residual(pr.mesh, pr.kappa_kind, a, np.full(pr.mesh.n_cells, 250.0), pr.f_cell, g)
+    assert np.max(np.abs(r)) == 0.0
+    r2 = tpfa.reduced_residual(pr.mesh, pr.kappa_kind, a, 250.0 + 1e-3 * pr.cell_shift, pr.f_cell, g)
+    assert np.max(np.abs(r2)) > 0.0
