@@ -83,8 +83,9 @@ typedef struct {
   double lin_tol;            /* relative tolerance of the level-0 CG solves inside Picard steps (default 1e-2) */
   int32_t lin_maxit;         /* iteration cap of the CG solves */
   double coarse_lin_tol;     /* relative tolerance of the coarse-level (hybridized) CG solves (default 1e-1) */
-  int32_t lin_precision;     /* 0: CG in FP64; 1: CG vectors and matrices in FP32 (tolerances floored at 1e-6),
-                                inside the FP64 nonlinear iteration */
+  int32_t lin_precision;     /* 0: level-0 CG in FP64; 1: level-0 CG vectors and matrix in FP32 (tolerance floored
+                                at 1e-6), inside the FP64 nonlinear iteration; the coarse levels' hybridized CG and
+                                the Newton steps' BiCGStab stay FP64 */
   int32_t setup_threads;     /* host threads for the setup (0 = all) */
   int32_t max_sms;           /* SMs the persistent solver kernels of a context may use (0 = all): contexts that
                                 solve concurrently (nlmg_solve_many, the request loop) can then run side by side.

@@ -69,7 +69,6 @@ struct LevelDev {
   int* if_cell = nullptr;                          // per interface slot: its cell
   int* slot_cell = nullptr;                        // per local flux slot: its cell
   int* p_cell = nullptr;                           // per pressure unknown: its cell
-  float *Hc32 = nullptr, *Sinv32 = nullptr;        // FP32 copies for the mixed-precision solves
 };
 
 // Transfer between level l and l+1

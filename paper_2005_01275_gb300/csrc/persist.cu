@@ -778,6 +778,142 @@ __global__ void __launch_bounds__(kPThreads) kp_fine_cg2_reg(FineDev F, const T*
   }
 }
 
+// FP32 pipelined CG with residual replacement. The recurrences of the pipelined CG (kp_fine_cg_reg) run in FP32
+// here, vectors and scaled matrix alike, a thread's cells in registers; in FP32 they drift away from the true
+// residual on the six-decade channelized field (the iteration count grew fivefold), so every `replace` iterations
+// the residual and the auxiliary vectors are recomputed from their definitions -- r = b - A y, s = A p, then
+// w = A r and z = A s (residual replacement, Cools and Vanroose) -- which costs four matrix products and two extra
+// synchronisations and keeps the iteration on the track of the FP64 one. Per-thread partial sums in FP32, block and
+// grid sums in FP64; the stopping test and the step lengths are those of kp_fine_cg_reg.
+template <int R>
+__global__ void __launch_bounds__(kPThreads) kp_fine_cg_rr32(FineDev F, const float* __restrict__ Ts,
+                                                             const double* __restrict__ sdiag,
+                                                             const double* __restrict__ b, double bscale,
+                                                             double* __restrict__ dx, float* wa, float* wb,
+                                                             float* ypub, float* ppub, float* rpub, float* spub,
+                                                             double* partial, GridSync gs, double tol, int maxit,
+                                                             int replace, PcgResult* res) {
+  __shared__ double sm[kSmDoubles];
+  Grid g{gs, partial, sm, 0u};
+  const int stride = gridDim.x * blockDim.x;
+  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+  float y[R], r[R], p[R], sv[R], z[R], w[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int K = k0 + u * stride;
+    y[u] = p[u] = sv[u] = z[u] = w[u] = r[u] = 0.0f;
+    if (K < F.N) {
+      r[u] = (float)(sdiag[K] * bscale * b[K]);
+      wa[K] = r[u];   // the first product is A r
+    }
+  }
+  if (!grid_barrier(g)) return;
+  float t0 = 0.0f, t1 = 0.0f;
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int K = k0 + u * stride;
+    if (K < F.N) {
+      w[u] = sell_apply<float>(F, Ts, wa, K);
+      wb[K] = w[u];
+      t0 = fmaf(r[u], r[u], t0);
+      t1 = fmaf(w[u], r[u], t1);
+    }
+  }
+  double a4[4] = {(double)t0, (double)t1, 0.0, 0.0};
+  if (!grid_sum_x<2, 2>(g, a4, [&](double* o) {
+        o[2] = 0.0;
+        o[3] = o[1] != 0.0 ? o[0] / o[1] : 0.0;
+      }))
+    return;
+  double gamma = a4[0], beta = a4[2], alpha = a4[3];
+  const double rr0 = gamma;
+  const double tol2 = tol * tol * rr0;
+  float* wc = wb;   // published w of the current iteration
+  float* wn = wa;   // next w
+  int it = 0;
+  while (rr0 > 0.0 && gamma > tol2 && it < maxit) {
+    if (!(alpha != 0.0)) break;
+    const float af = (float)alpha, bf = (float)beta;
+    float n0 = 0.0f, n1 = 0.0f;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const int K = k0 + u * stride;
+      if (K < F.N) {
+        const float nK = sell_apply<float>(F, Ts, wc, K);
+        z[u] = nK + bf * z[u];
+        sv[u] = w[u] + bf * sv[u];
+        p[u] = r[u] + bf * p[u];
+        y[u] += af * p[u];
+        r[u] = r[u] - af * sv[u];
+        w[u] = w[u] - af * z[u];
+        wn[K] = w[u];
+        n0 = fmaf(r[u], r[u], n0);
+        n1 = fmaf(w[u], r[u], n1);
+      }
+    }
+    if (replace > 0 && (it + 1) % replace == 0) {
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        const int K = k0 + u * stride;
+        if (K < F.N) {
+          ypub[K] = y[u];
+          ppub[K] = p[u];
+        }
+      }
+      if (!grid_barrier(g)) return;
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        const int K = k0 + u * stride;
+        if (K < F.N) {
+          r[u] = (float)(sdiag[K] * bscale * b[K]) - sell_apply<float>(F, Ts, ypub, K);
+          sv[u] = sell_apply<float>(F, Ts, ppub, K);
+          rpub[K] = r[u];
+          spub[K] = sv[u];
+        }
+      }
+      if (!grid_barrier(g)) return;
+      n0 = n1 = 0.0f;
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        const int K = k0 + u * stride;
+        if (K < F.N) {
+          w[u] = sell_apply<float>(F, Ts, rpub, K);
+          z[u] = sell_apply<float>(F, Ts, spub, K);
+          wn[K] = w[u];
+          n0 = fmaf(r[u], r[u], n0);
+          n1 = fmaf(w[u], r[u], n1);
+        }
+      }
+    }
+    double n4[4] = {(double)n0, (double)n1, 0.0, 0.0};
+    if (!grid_sum_x<2, 2>(g, n4, [&](double* o) {
+          const double g = o[0], d = o[1];
+          const double bn = gamma != 0.0 ? g / gamma : 0.0;
+          const double den = d - bn * g / alpha;
+          o[2] = bn;
+          o[3] = den != 0.0 ? g / den : 0.0;
+        }))
+      return;
+    gamma = n4[0];
+    beta = n4[2];
+    alpha = n4[3];
+    float* t = wc;
+    wc = wn;
+    wn = t;
+    ++it;
+  }
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int K = k0 + u * stride;
+    if (K < F.N) dx[K] = sdiag[K] * (double)y[u];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    res->iters = it;
+    res->rr0 = rr0;
+    res->rr = gamma;
+  }
+}
+
 // ---- fine level: Newton update J dx = bscale * b with the exact Jacobian ---------------------------------------
 // Row K of the scaled Jacobian applied to v: jd_K v_K + sum_e Js_e v_L(e) (SELL-32 layout; padding entries are 0).
 __device__ __forceinline__ double jac_row(const FineDev& F, const double* __restrict__ Js, double jdK, const double* v,
@@ -1334,6 +1470,27 @@ cudaError_t launch_fine_cg_pipe(cudaStream_t st, const FineDev& F, const T* Ts, 
                   (void*)&tol, (void*)&maxit, (void*)&res};
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
 }
+// FP32 pipelined CG with residual replacement if every thread holds at most 8 cells on the grid the launch gets;
+// returns cudaErrorNotSupported (nothing launched) otherwise.
+cudaError_t launch_fine_cg_rr32(cudaStream_t st, const FineDev& F, const float* Ts, const double* sdiag,
+                                const double* b, double bscale, double* dx, float* wa, float* wb, float* ypub,
+                                float* ppub, float* rpub, float* spub, double* partial, GridSync gs, double tol,
+                                int maxit, int replace, PcgResult* res) {
+  const void* fns[4] = {(const void*)kp_fine_cg_rr32<1>, (const void*)kp_fine_cg_rr32<2>,
+                        (const void*)kp_fine_cg_rr32<4>, (const void*)kp_fine_cg_rr32<8>};
+  const int Rs[4] = {1, 2, 4, 8};
+  for (int i = 0; i < 4; ++i) {
+    const int grid = coop_grid(fns[i], F.N, gs.sm_cap);
+    const long cap = (long)grid * kPThreads * Rs[i];
+    if (cap < F.N) continue;
+    void* args[] = {(void*)&F, (void*)&Ts, (void*)&sdiag, (void*)&b, (void*)&bscale, (void*)&dx, (void*)&wa,
+                    (void*)&wb, (void*)&ypub, (void*)&ppub, (void*)&rpub, (void*)&spub, (void*)&partial,
+                    (void*)&gs, (void*)&tol, (void*)&maxit, (void*)&replace, (void*)&res};
+    return cudaLaunchCooperativeKernel(fns[i], dim3(grid), dim3(kPThreads), args, 0, st);
+  }
+  return cudaErrorNotSupported;
+}
+
 cudaError_t launch_fine_bicgstab(cudaStream_t st, const FineDev& F, const double* Js, const double* jd,
                                  const double* sS, const double* b, double bscale, double* dx, double* work,
                                  double* partial, GridSync gs, double tol, int maxit, PcgResult* res) {
@@ -1425,10 +1582,6 @@ template cudaError_t launch_hyb_solve<double>(cudaStream_t, const LevelDev&, con
                                               const double*, const double*, const double*, double*, double*,
                                               double*, double*, double*, double*, double*, double*, double*,
                                               double*, double*, double*, GridSync, double, int, PcgResult*);
-template cudaError_t launch_hyb_solve<float>(cudaStream_t, const LevelDev&, const float*, const float*,
-                                             const double*, const double*, const double*, float*, float*, float*,
-                                             float*, float*, float*, float*, float*, float*, double*, double*,
-                                             double*, GridSync, double, int, PcgResult*);
 
 template <class T>
 cudaError_t launch_coarse_step(cudaStream_t st, const LevelDev& L, const T* Hc, const T* Sinv,
@@ -1456,8 +1609,5 @@ cudaError_t launch_coarse_step(cudaStream_t st, const LevelDev& L, const T* Hc, 
 template cudaError_t launch_coarse_step<double>(cudaStream_t, const LevelDev&, const double*, const double*,
                                                 const CoarseStepBufs<double>&, const CoarseStepParams&, double*,
                                                 GridSync, CoarseStepResult*);
-template cudaError_t launch_coarse_step<float>(cudaStream_t, const LevelDev&, const float*, const float*,
-                                               const CoarseStepBufs<float>&, const CoarseStepParams&, double*,
-                                               GridSync, CoarseStepResult*);
 
 }  // namespace nlmg

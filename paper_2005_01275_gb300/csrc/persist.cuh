@@ -46,6 +46,13 @@ cudaError_t launch_fine_cg2_reg(cudaStream_t st, const FineDev& F, const T* Ts, 
                                 double bscale, double* dx, T* rpub, double* partial, GridSync gs, double tol,
                                 int maxit, PcgResult* res);
 
+// Register-resident FP32 pipelined CG with residual replacement every `replace` iterations (0: never). Returns
+// cudaErrorNotSupported without launching when a thread would have to hold more than 8 cells.
+cudaError_t launch_fine_cg_rr32(cudaStream_t st, const FineDev& F, const float* Ts, const double* sdiag,
+                                const double* b, double bscale, double* dx, float* wa, float* wb, float* ypub,
+                                float* ppub, float* rpub, float* spub, double* partial, GridSync gs, double tol,
+                                int maxit, int replace, PcgResult* res);
+
 // Persistent FP64 BiCGStab for the level-0 Newton system J dx = bscale b on the scaled Jacobian (Js off the
 // diagonal in the SELL layout, jd on it, sS = S per cell); work holds 7 n_cells doubles.
 cudaError_t launch_fine_bicgstab(cudaStream_t st, const FineDev& F, const double* Js, const double* jd,

@@ -47,8 +47,6 @@ struct CoarseBuf {
          *lq = nullptr, *ldinv = nullptr, *xi = nullptr;
   double *hw = nullptr, *hz = nullptr, *hs = nullptr, *hma = nullptr, *hmb = nullptr;   // pipelined hybridized CG
   LinParts base{}, dir{};   // linear parts of the operator at x and along dx (fused coarse step)
-  float *f_ylam = nullptr, *f_ydiag = nullptr, *f_lam = nullptr, *f_lr = nullptr, *f_lz = nullptr,
-        *f_lpa = nullptr, *f_lpb = nullptr, *f_lq = nullptr, *f_ldinv = nullptr;
   double rn = 0.0;  // ||A(x) - b|| at the current x (valid after coarse_res)
 };
 
@@ -127,7 +125,7 @@ struct nlmg_ctx {
   // Newton smoothing steps: the scaled Jacobian of the BiCGStab (off-diagonal, diagonal, S); its 7 work vectors
   // are the first 7 of the GMRES basis
   double *Js = nullptr, *jdS = nullptr, *jsS = nullptr;
-  float *Ts32 = nullptr, *fy = nullptr, *fr = nullptr, *fpa = nullptr, *fpb = nullptr, *fq = nullptr;
+  float *Ts32 = nullptr, *fy = nullptr, *fr = nullptr, *fpa = nullptr, *fpb = nullptr, *fq = nullptr, *fs = nullptr;
   FineState cur, t1, t2;
   bool have_data = false;
   double tol_rel = 1e-8, tol_abs = 1e-10;   // outer tolerances, also used on the coarsest level
@@ -381,8 +379,6 @@ void upload_level(nlmg_ctx* c, int l) {
   D.if_sign = c->upload(if_sign);
   D.hc_off = c->upload(hc_off);
   D.Hc = c->upload(Hc);
-  D.Hc32 = c->upload(std::vector<float>(Hc.begin(), Hc.end()));
-  D.Sinv32 = c->upload(std::vector<float>(Sinv.begin(), Sinv.end()));
   D.lam_y0 = c->upload(ly0);
   D.lam_y1 = c->upload(ly1);
   std::vector<int> ifc(if_slot.size()), slc(L.loc.size()), pc(L.n_p());
@@ -439,9 +435,6 @@ void alloc_level(nlmg_ctx* c, int l) {
   B.ptmp = c->dalloc<double>(nx);
   B.ylam = c->dalloc<double>(D.nif);
   B.ydiag = c->dalloc<double>(D.nif);
-  B.f_ylam = c->dalloc<float>(D.nif);
-  B.f_ydiag = c->dalloc<float>(D.nif);
-  for (float** pp : {&B.f_lam, &B.f_lr, &B.f_lz, &B.f_lpa, &B.f_lpb, &B.f_lq, &B.f_ldinv}) *pp = c->dalloc<float>(nlam);
   B.lam = c->dalloc<double>(nlam);
   B.lr = c->dalloc<double>(nlam);
   B.lz = c->dalloc<double>(nlam);
@@ -547,24 +540,33 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
   launch_sdiag(c->st, c->F.N, c->diagT, c->sdiag);
   const bool fp32 = c->opt.lin_precision == 1;
   // FP64 at loose tolerances: pipelined CG (one grid barrier per iteration), register-resident when every thread
-  // holds at most 4 cells. Tight tolerances, and FP32: the two-barrier CG, whose updated residual tracks the true
-  // one more closely (the pipelined recurrences with an FP32 matrix product drift: measured 10,768 instead of 3,466
-  // fine iterations on the 64^3 workload, whether the recurrences run in FP32 or in FP64).
+  // holds at most 4 cells. FP32: the pipelined CG with residual replacement every kReplace iterations (without it
+  // the FP32 recurrences drift: measured 10,768 instead of 3,466 fine iterations on the 64^3 workload), registers
+  // for at most 8 cells per thread; else the two-barrier CG. Tight FP64 tolerances: the two-barrier CG, whose
+  // updated residual tracks the true one more closely.
+  constexpr int kReplace = 50;
   const bool pipe = !fp32 && c->lin_tol_eff >= 1e-6;
-  int kind = 0;   // 0 two-barrier, 1 pipelined in memory, 2 pipelined in registers, 3 two-barrier in registers
+  int kind = 0;   // 0 two-barrier, 1 pipelined in memory, 2 pipelined in registers, 3 two-barrier in registers,
+                  // 4 FP32 pipelined with residual replacement
   int pi;
   if (fp32) {
     launch_scale_sell<float>(c->st, c->F, c->Tval, c->sdiag, c->Ts32);
     pi = c->prof_begin(0);
-    const cudaError_t e = launch_fine_cg2_reg<float>(c->st, c->F, c->Ts32, c->sdiag, R, -1.0, c->cx, c->fr,
-                                                     c->d_partial, gs, std::max(c->lin_tol_eff, 1e-6),
-                                                     c->opt.lin_maxit, c->d_res);
-    if (e == cudaSuccess) {
+    cudaError_t e = launch_fine_cg_rr32(c->st, c->F, c->Ts32, c->sdiag, R, -1.0, c->cx, c->fpa, c->fpb, c->fy,
+                                        c->fq, c->fr, c->fs, c->d_partial, gs, std::max(c->lin_tol_eff, 1e-6),
+                                        c->opt.lin_maxit, kReplace, c->d_res);
+    kind = 4;
+    if (e == cudaErrorNotSupported) {
+      e = launch_fine_cg2_reg<float>(c->st, c->F, c->Ts32, c->sdiag, R, -1.0, c->cx, c->fr, c->d_partial, gs,
+                                     std::max(c->lin_tol_eff, 1e-6), c->opt.lin_maxit, c->d_res);
       kind = 3;
-    } else {
-      if (e != cudaErrorNotSupported) CK(e);
+    }
+    if (e == cudaErrorNotSupported) {
+      kind = 0;
       CK(launch_fine_cg<float>(c->st, c->F, c->Ts32, c->sdiag, R, -1.0, c->cx, c->fy, c->fr, c->fpa, c->fpb, c->fq,
                                c->d_partial, gs, std::max(c->lin_tol_eff, 1e-6), c->opt.lin_maxit, c->d_res));
+    } else {
+      CK(e);
     }
   } else {
     launch_scale_sell<double>(c->st, c->F, c->Tval, c->sdiag, c->Ts64);
@@ -606,7 +608,7 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
     const double N = c->F.N, nnz = (double)c->sh->nnz_real, v = fp32 ? 4.0 : 8.0;
     const double nvec = kind >= 2 ? 2.0 : kind == 1 ? 12.0 : 11.0;
     const double per_it_b = (4.0 + v) * nnz + nvec * v * N;
-    const bool pipelined = kind == 1 || kind == 2;
+    const bool pipelined = kind == 1 || kind == 2 || kind == 4;
     const double per_it_f = pipelined ? 2.0 * nnz + 18.0 * N : 2.0 * nnz + 12.0 * N;   // an FMA counts 2
     c->prof.bytes[0] += (8.0 + 8.0) * N + 2.0 * v * N + 8.0 * N + v * N + 8.0 * N + (pipelined ? per_it_b : 0.0) +
                         it * per_it_b;
@@ -860,12 +862,7 @@ int coarse_linear(nlmg_ctx* c, int l) {
   CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->st));
   CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
   int pi = c->prof_begin(1);
-  if (c->opt.lin_precision == 1)
-    CK(launch_hyb_solve<float>(c->st, L, L.Hc32, L.Sinv32, B.kapc, bs, bp, B.f_ylam, B.f_ydiag, B.f_lam, B.f_lr,
-                               B.f_lz, B.f_lpa, B.f_lpb, B.f_lq, B.f_ldinv, B.dx, B.dx + L.nflux, c->d_partial, gs,
-                               std::max(c->coarse_lin_tol_eff, 1e-6), c->opt.lin_maxit, c->d_res));
-  else
-    CK(launch_hyb_solve<double>(c->st, L, L.Hc, L.Sinv, B.kapc, bs, bp, B.ylam, B.ydiag, B.lam, B.lr, B.lz, B.lpa,
+  CK(launch_hyb_solve<double>(c->st, L, L.Hc, L.Sinv, B.kapc, bs, bp, B.ylam, B.ydiag, B.lam, B.lr, B.lz, B.lpa,
                                 B.lpb, B.lq, B.ldinv, B.dx, B.dx + L.nflux, c->d_partial, gs, c->coarse_lin_tol_eff,
                                 c->opt.lin_maxit, c->d_res));
   c->prof_end(pi);
@@ -874,7 +871,7 @@ int coarse_linear(nlmg_ctx* c, int l) {
   CK(cudaStreamSynchronize(c->st));
   if (c->h_res->err) throw Error(NLMG_ETIMEOUT, "grid barrier wait gave up in the coarse CG kernel");
   const int it = c->h_res->iters;
-  if (pi >= 0) c->prof.bytes[1] += (double)it * c->sh->hyb_bytes_per_iter[l] * (c->opt.lin_precision == 1 ? 0.5 : 1.0);
+  if (pi >= 0) c->prof.bytes[1] += (double)it * c->sh->hyb_bytes_per_iter[l];
   c->lin_iters += it;
   c->lin_iters_level[l] += it;
   return it;
@@ -933,20 +930,14 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
   CK(cudaMemsetAsync(dres, 0, sizeof(CoarseStepResult), c->st));
   const int kid = coarsest ? 4 : 1;   // profile id: the coarsest solve apart from the other coarse steps
   int pi = c->prof_begin(kid);
-  if (c->opt.lin_precision == 1) {
-    P.lin_tol = std::max(c->coarse_lin_tol_eff, 1e-6);
-    CoarseStepBufs<float> Bf{B.x, B.b, B.r, B.nb, B.dx, B.kapc, B.base, B.dir, B.f_ylam, B.f_ydiag,
-                             B.f_lam, B.f_lr, B.f_lz, B.f_lpa, B.f_lpb, B.f_lq, B.f_ldinv, HybPipeBufs<float>{}};
-    CK(launch_coarse_step<float>(c->st, L, L.Hc32, L.Sinv32, Bf, P, c->d_partial, gs, dres));
-  } else {
-    P.lin_tol = c->coarse_lin_tol_eff;
-    // pipelined hybridized CG at loose tolerances; the two-synchronisation CG when a tight solve is asked for
-    const bool pipe = c->coarse_lin_tol_eff >= 1e-6;
-    CoarseStepBufs<double> Bd{B.x, B.b, B.r, B.nb, B.dx, B.kapc, B.base, B.dir, B.ylam, B.ydiag,
-                              B.lam, B.lr, B.lz, B.lpa, B.lpb, B.lq, B.ldinv,
-                              pipe ? HybPipeBufs<double>{B.hw, B.hz, B.hs, B.hma, B.hmb} : HybPipeBufs<double>{}};
-    CK(launch_coarse_step<double>(c->st, L, L.Hc, L.Sinv, Bd, P, c->d_partial, gs, dres));
-  }
+  // FP64 whatever lin_precision is: the coarse levels are latency bound, FP32 would save nothing there. Pipelined
+  // hybridized CG at loose tolerances; the two-synchronisation CG when a tight solve is asked for.
+  P.lin_tol = c->coarse_lin_tol_eff;
+  const bool pipe = c->coarse_lin_tol_eff >= 1e-6;
+  CoarseStepBufs<double> Bd{B.x, B.b, B.r, B.nb, B.dx, B.kapc, B.base, B.dir, B.ylam, B.ydiag,
+                            B.lam, B.lr, B.lz, B.lpa, B.lpb, B.lq, B.ldinv,
+                            pipe ? HybPipeBufs<double>{B.hw, B.hz, B.hs, B.hma, B.hmb} : HybPipeBufs<double>{}};
+  CK(launch_coarse_step<double>(c->st, L, L.Hc, L.Sinv, Bd, P, c->d_partial, gs, dres));
   c->prof_end(pi);
   count_launch(1);
   CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(PcgResult) + sizeof(CoarseStepResult), cudaMemcpyDeviceToHost,
@@ -960,7 +951,7 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
                                     std::to_string(l));
   B.rn = R.rn;
   if (pi >= 0) {
-    c->prof.bytes[kid] += (double)R.iters * c->sh->hyb_bytes_per_iter[l] * (c->opt.lin_precision == 1 ? 0.5 : 1.0) +
+    c->prof.bytes[kid] += (double)R.iters * c->sh->hyb_bytes_per_iter[l] +
                           (double)R.res_evals * c->sh->coarse_res_bytes[l] +
                           (double)(R.trials + R.steps + 1) * c->sh->coarse_trial_bytes[l];
     c->prof.flops[kid] += (double)R.iters * c->sh->hyb_flops_per_iter[l] +
@@ -1033,7 +1024,7 @@ void alloc_fine(nlmg_ctx* c) {
   c->dv2 = c->dalloc<double>(N);
   c->Ts64 = c->dalloc<double>(c->F.nnz);
   c->Ts32 = c->dalloc<float>(c->F.nnz);
-  for (float** pp : {&c->fy, &c->fr, &c->fpa, &c->fpb, &c->fq}) *pp = c->dalloc<float>(N);
+  for (float** pp : {&c->fy, &c->fr, &c->fpa, &c->fpb, &c->fq, &c->fs}) *pp = c->dalloc<float>(N);
   for (FineState* s : {&c->cur, &c->t1, &c->t2}) {
     s->p = c->dalloc<double>(N);
     s->kap = c->dalloc<double>(N);
