@@ -98,6 +98,7 @@ typedef struct {
                                 Picard steps (cleared by the next solve and by nlmg_set_options; consecutive
                                 nlmg_vcycle calls carry it) */
   double newton_lin_tol;     /* relative tolerance of the BiCGStab solves of the Newton steps (default 1e-2) */
+  double coarsest_lin_tol;   /* the same on the coarsest level (default 2e-1; <= 0: coarse_lin_tol) */
   int32_t reserved[5];
 } nlmg_options;
 

@@ -129,7 +129,8 @@ struct nlmg_ctx {
   FineState cur, t1, t2;
   bool have_data = false;
   double tol_rel = 1e-8, tol_abs = 1e-10;   // outer tolerances, also used on the coarsest level
-  double lin_tol_eff = 1e-2, coarse_lin_tol_eff = 1e-1, newton_tol_eff = 1e-2;   // inner tolerances of the running solve
+  double lin_tol_eff = 1e-2, coarse_lin_tol_eff = 1e-1, coarsest_lin_tol_eff = 2e-1, newton_tol_eff = 1e-2;   // inner
+  // tolerances of the running solve
   int tightenings = 0;
   double r0_ref = 0.0;             // ||R(p_0)|| of the running solve (the Picard-then-Newton switch)
   bool newton_off = false;         // a Newton smoothing step of the running solve failed to halve the residual
@@ -140,6 +141,7 @@ struct nlmg_ctx {
     sm_cap = opt.max_sms > 0 ? opt.max_sms : auto_sm_cap;
     lin_tol_eff = opt.lin_tol;
     coarse_lin_tol_eff = opt.coarse_lin_tol;
+    coarsest_lin_tol_eff = opt.coarsest_lin_tol > 0.0 ? opt.coarsest_lin_tol : opt.coarse_lin_tol;
     newton_tol_eff = opt.newton_lin_tol;
     tightenings = 0;
   }
@@ -932,8 +934,8 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
   int pi = c->prof_begin(kid);
   // FP64 whatever lin_precision is: the coarse levels are latency bound, FP32 would save nothing there. Pipelined
   // hybridized CG at loose tolerances; the two-synchronisation CG when a tight solve is asked for.
-  P.lin_tol = c->coarse_lin_tol_eff;
-  const bool pipe = c->coarse_lin_tol_eff >= 1e-6;
+  P.lin_tol = coarsest ? c->coarsest_lin_tol_eff : c->coarse_lin_tol_eff;
+  const bool pipe = P.lin_tol >= 1e-6;
   CoarseStepBufs<double> Bd{B.x, B.b, B.r, B.nb, B.dx, B.kapc, B.base, B.dir, B.ylam, B.ydiag,
                             B.lam, B.lr, B.lz, B.lpa, B.lpb, B.lq, B.ldinv,
                             pipe ? HybPipeBufs<double>{B.hw, B.hz, B.hs, B.hma, B.hmb} : HybPipeBufs<double>{}};
@@ -1120,6 +1122,7 @@ nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double
         (c->lin_tol_eff > 1e-12 || c->coarse_lin_tol_eff > 1e-12)) {
       c->lin_tol_eff = std::max(1e-12, c->lin_tol_eff * 1e-2);
       c->coarse_lin_tol_eff = std::max(1e-12, c->coarse_lin_tol_eff * 1e-2);
+      c->coarsest_lin_tol_eff = std::max(1e-12, c->coarsest_lin_tol_eff * 1e-2);
       c->newton_tol_eff = std::max(1e-12, c->newton_tol_eff * 1e-2);
       c->tightenings++;
     }
@@ -1187,6 +1190,7 @@ void nlmg_default_options(nlmg_options* o) {
   o->lin_tol = 1e-2;          // inner solves of the Picard smoothing steps: loose, the outer iteration corrects them
   o->lin_maxit = 5000;
   o->coarse_lin_tol = 1e-1;
+  o->coarsest_lin_tol = 2e-1;
   o->lin_precision = 0;
   o->setup_threads = 0;
   o->newton_switch = 1e-3;

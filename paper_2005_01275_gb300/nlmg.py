@@ -40,7 +40,7 @@ class Options(C.Structure):
                 ("lin_maxit", C.c_int32),
                 ("coarse_lin_tol", C.c_double), ("lin_precision", C.c_int32),
                 ("setup_threads", C.c_int32), ("max_sms", C.c_int32), ("newton_switch", C.c_double),
-                ("newton_lin_tol", C.c_double), ("reserved", C.c_int32 * 5)]
+                ("newton_lin_tol", C.c_double), ("coarsest_lin_tol", C.c_double), ("reserved", C.c_int32 * 5)]
 
 
 class Report(C.Structure):
@@ -167,11 +167,13 @@ def options_from_dict(d):
     """Options from the dictionary used by the synthetic problem configurations."""
     keep = {k: d[k] for k in ("n_levels", "agg_size", "modes", "nu_pre", "nu_post", "omega", "bt_nmax", "bt_theta",
                               "dp_clamp", "coarsest_steps", "coarsest_tol", "lin_tol", "lin_maxit", "coarse_lin_tol",
-                              "lin_precision", "max_sms", "newton_switch", "newton_lin_tol") if k in d}
+                              "lin_precision", "max_sms", "newton_switch", "newton_lin_tol", "coarsest_lin_tol") if k in d}
     if "lin_tol" in d and "coarse_lin_tol" not in d:
         keep["coarse_lin_tol"] = d["lin_tol"]       # one tolerance given: use it on every level
     if "lin_tol" in d and "newton_lin_tol" not in d:
         keep["newton_lin_tol"] = d["lin_tol"]       # ... and for the Newton steps
+    if "coarsest_lin_tol" not in d and ("coarse_lin_tol" in keep):
+        keep["coarsest_lin_tol"] = keep["coarse_lin_tol"]   # ... and on the coarsest level
     if "smoother" in d:
         keep["smoother"] = _SMOOTHERS[d["smoother"]]
     return default_options(**keep)

@@ -33,6 +33,7 @@ def test_default_options_are_the_papers(nlmg_lib):
     o = nlmg_lib.default_options()
     assert o.bt_nmax == 4 and abs(o.bt_theta - 0.9) < 1e-15 and o.coarsest_steps == 10
     assert o.smoother == nlmg_lib.SMOOTH_PICARD and o.newton_switch == 1e-3 and o.newton_lin_tol == 1e-2
+    assert o.coarse_lin_tol == 1e-1 and o.coarsest_lin_tol == 2e-1
 
 
 def test_setup_rejects_bad_mesh(nlmg_lib):

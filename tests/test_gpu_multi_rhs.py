@@ -112,7 +112,7 @@ def test_loose_inner_tolerances_do_not_stall(nlmg_lib):
     the solver divides them by 100 after a stalled cycle and then converges like the exact-inner-solve oracle."""
     pr = _problem()
     F, G = _rows(pr, 1, seed=50)
-    ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.opts)
+    ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, dict(pr.opts, lin_tol=1e-2, coarse_lin_tol=1e-1))
     p, rep, st = ctx.solve(F[0], G[0], max_cycles=60)
     assert st == 0, rep
     assert rep["tol_tightened"] >= 1

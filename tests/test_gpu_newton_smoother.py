@@ -79,7 +79,7 @@ def test_picard_newton_solve_reaches_newton_solution(nlmg_lib):
     assert _rel(p, pstar) <= 1e-10
     r = tpfa.reduced_residual(pr.mesh, pr.kappa_kind, pr.kappa_a, p, pr.f_cell, pr.g_face)
     assert np.linalg.norm(r) <= 2e-12 * rep["res0"]
-    ctx.set_options(lin_tol=1e-2, coarse_lin_tol=1e-1, newton_lin_tol=1e-2, lin_maxit=5000)
+    ctx.set_options(lin_tol=1e-2, coarse_lin_tol=1e-1, coarsest_lin_tol=2e-1, newton_lin_tol=1e-2, lin_maxit=5000)
     _, rep_n, st = ctx.solve(pr.f_cell, pr.g_face, max_cycles=60)
     assert st == 0 and rep_n["newton_steps"] >= 1
     ctx.set_options(smoother="picard")
