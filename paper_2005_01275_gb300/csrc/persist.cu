@@ -700,84 +700,6 @@ __device__ bool hyb_pipe_loop_reg(const LevelDev& L, const T* __restrict__ Hc, c
   return true;
 }
 
-// Register-resident two-barrier CG (the CG of kp_fine_cg, bitwise on the same grid): a thread keeps r, p, q = A p
-// and y of its at most R cells in registers for the whole solve and publishes only r, which the neighbours gather
-// for the product A r. Used for the FP32 solves, where the pipelined forms drift.
-template <class T, int R>
-__global__ void __launch_bounds__(kPThreads) kp_fine_cg2_reg(FineDev F, const T* __restrict__ Ts,
-                                                             const double* __restrict__ sdiag,
-                                                             const double* __restrict__ b, double bscale,
-                                                             double* __restrict__ dx, T* rpub, double* partial,
-                                                             GridSync gs, double tol, int maxit, PcgResult* res) {
-  __shared__ double sm[kSmDoubles];
-  Grid g{gs, partial, sm, 0u};
-  const int stride = gridDim.x * blockDim.x;
-  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
-  T y[R], r[R], p[R], q[R];
-  T t1 = (T)0;
-#pragma unroll
-  for (int u = 0; u < R; ++u) {
-    const int K = k0 + u * stride;
-    y[u] = p[u] = q[u] = r[u] = (T)0;
-    if (K < F.N) {
-      r[u] = (T)(sdiag[K] * bscale * b[K]);
-      rpub[K] = r[u];
-      t1 = fma(r[u], r[u], t1);
-    }
-  }
-  double a1[1] = {(double)t1};
-  if (!grid_sum<1>(g, a1)) return;
-  const double rr0 = a1[0];
-  double rr = rr0;
-  const double tol2 = tol * tol * rr0;
-  T beta = (T)0;
-  int it = 0;
-  while (rr0 > 0.0 && rr > tol2 && it < maxit) {
-    T tpq = (T)0;
-#pragma unroll
-    for (int u = 0; u < R; ++u) {
-      const int K = k0 + u * stride;
-      if (K < F.N) {
-        const T acc = sell_apply<T>(F, Ts, rpub, K);
-        p[u] = it == 0 ? r[u] : r[u] + beta * p[u];
-        q[u] = it == 0 ? acc : acc + beta * q[u];
-        tpq = fma(p[u], q[u], tpq);
-      }
-    }
-    double pq[2] = {(double)tpq, 0.0};
-    if (!grid_sum_x<1, 1>(g, pq, [&](double* o) { o[1] = o[0] != 0.0 ? rr / o[0] : 0.0; })) return;
-    const double alpha_d = pq[1];
-    const T alpha = (T)alpha_d;
-    T trn = (T)0;
-#pragma unroll
-    for (int u = 0; u < R; ++u) {
-      const int K = k0 + u * stride;
-      if (K < F.N) {
-        y[u] = alpha * p[u] + y[u];
-        r[u] = r[u] - alpha * q[u];
-        rpub[K] = r[u];
-        trn = fma(r[u], r[u], trn);
-      }
-    }
-    double rn[2] = {(double)trn, 0.0};
-    if (!grid_sum_x<1, 1>(g, rn, [&](double* o) { o[1] = rr != 0.0 ? o[0] / rr : 0.0; })) return;
-    beta = (T)rn[1];
-    rr = rn[0];
-    ++it;
-    if (!(alpha_d != 0.0)) break;
-  }
-#pragma unroll
-  for (int u = 0; u < R; ++u) {
-    const int K = k0 + u * stride;
-    if (K < F.N) dx[K] = sdiag[K] * (double)y[u];
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    res->iters = it;
-    res->rr0 = rr0;
-    res->rr = rr;
-  }
-}
-
 // FP32 pipelined CG with residual replacement. The recurrences of the pipelined CG (kp_fine_cg_reg) run in FP32
 // here, vectors and scaled matrix alike, a thread's cells in registers; in FP32 they drift away from the true
 // residual on the six-decade channelized field (the iteration count grew fivefold), so every `replace` iterations
@@ -1526,28 +1448,6 @@ cudaError_t launch_fine_cg_reg(cudaStream_t st, const FineDev& F, const TM* Ts, 
 template cudaError_t launch_fine_cg_reg<double>(cudaStream_t, const FineDev&, const double*, const double*,
                                                 const double*, double, double*, double*, double*, double*, GridSync,
                                                 double, int, PcgResult*);
-// Register-resident two-barrier CG if every thread holds at most 8 cells on the grid the launch gets; returns
-// cudaErrorNotSupported (nothing launched) otherwise.
-template <class T>
-cudaError_t launch_fine_cg2_reg(cudaStream_t st, const FineDev& F, const T* Ts, const double* sdiag, const double* b,
-                                double bscale, double* dx, T* rpub, double* partial, GridSync gs, double tol,
-                                int maxit, PcgResult* res) {
-  const void* fns[4] = {(const void*)kp_fine_cg2_reg<T, 1>, (const void*)kp_fine_cg2_reg<T, 2>,
-                        (const void*)kp_fine_cg2_reg<T, 4>, (const void*)kp_fine_cg2_reg<T, 8>};
-  const int Rs[4] = {1, 2, 4, 8};
-  for (int i = 0; i < 4; ++i) {
-    const int grid = coop_grid(fns[i], F.N, gs.sm_cap);
-    const long cap = (long)grid * kPThreads * Rs[i];
-    if (cap < F.N) continue;
-    void* args[] = {(void*)&F, (void*)&Ts, (void*)&sdiag, (void*)&b, (void*)&bscale, (void*)&dx, (void*)&rpub,
-                    (void*)&partial, (void*)&gs, (void*)&tol, (void*)&maxit, (void*)&res};
-    return cudaLaunchCooperativeKernel(fns[i], dim3(grid), dim3(kPThreads), args, 0, st);
-  }
-  return cudaErrorNotSupported;
-}
-template cudaError_t launch_fine_cg2_reg<float>(cudaStream_t, const FineDev&, const float*, const double*,
-                                                const double*, double, double*, float*, double*, GridSync, double,
-                                                int, PcgResult*);
 template cudaError_t launch_fine_cg_pipe<double>(cudaStream_t, const FineDev&, const double*, const double*,
                                                  const double*, double, double*, double*, double*, double*, double*,
                                                  double*, double*, double*, double*, GridSync, double, int,

@@ -39,13 +39,6 @@ cudaError_t launch_fine_cg_reg(cudaStream_t st, const FineDev& F, const TM* Ts, 
                                double bscale, double* dx, TM* wa, TM* wb, double* partial, GridSync gs, double tol,
                                int maxit, PcgResult* res);
 
-// Register-resident two-barrier CG (T = float: the FP32 solves). Returns cudaErrorNotSupported without launching
-// when a thread would have to hold more than 8 cells.
-template <class T>
-cudaError_t launch_fine_cg2_reg(cudaStream_t st, const FineDev& F, const T* Ts, const double* sdiag, const double* b,
-                                double bscale, double* dx, T* rpub, double* partial, GridSync gs, double tol,
-                                int maxit, PcgResult* res);
-
 // Register-resident FP32 pipelined CG with residual replacement every `replace` iterations (0: never). Returns
 // cudaErrorNotSupported without launching when a thread would have to hold more than 8 cells.
 cudaError_t launch_fine_cg_rr32(cudaStream_t st, const FineDev& F, const float* Ts, const double* sdiag,

@@ -544,12 +544,12 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
   // FP64 at loose tolerances: pipelined CG (one grid barrier per iteration), register-resident when every thread
   // holds at most 4 cells. FP32: the pipelined CG with residual replacement every kReplace iterations (without it
   // the FP32 recurrences drift: measured 10,768 instead of 3,466 fine iterations on the 64^3 workload), registers
-  // for at most 8 cells per thread; else the two-barrier CG. Tight FP64 tolerances: the two-barrier CG, whose
+  // for at most 8 cells per thread; else the two-barrier CG in memory. Tight FP64 tolerances: the two-barrier CG, whose
   // updated residual tracks the true one more closely.
   constexpr int kReplace = 50;
   const bool pipe = !fp32 && c->lin_tol_eff >= 1e-6;
-  int kind = 0;   // 0 two-barrier, 1 pipelined in memory, 2 pipelined in registers, 3 two-barrier in registers,
-                  // 4 FP32 pipelined with residual replacement
+  int kind = 0;   // 0 two-barrier, 1 pipelined in memory, 2 pipelined in registers, 4 FP32 pipelined with
+                  // residual replacement
   int pi;
   if (fp32) {
     launch_scale_sell<float>(c->st, c->F, c->Tval, c->sdiag, c->Ts32);
@@ -558,11 +558,6 @@ int fine_pcg(nlmg_ctx* c, const double* R) {
                                         c->fq, c->fr, c->fs, c->d_partial, gs, std::max(c->lin_tol_eff, 1e-6),
                                         c->opt.lin_maxit, kReplace, c->d_res);
     kind = 4;
-    if (e == cudaErrorNotSupported) {
-      e = launch_fine_cg2_reg<float>(c->st, c->F, c->Ts32, c->sdiag, R, -1.0, c->cx, c->fr, c->d_partial, gs,
-                                     std::max(c->lin_tol_eff, 1e-6), c->opt.lin_maxit, c->d_res);
-      kind = 3;
-    }
     if (e == cudaErrorNotSupported) {
       kind = 0;
       CK(launch_fine_cg<float>(c->st, c->F, c->Ts32, c->sdiag, R, -1.0, c->cx, c->fy, c->fr, c->fpa, c->fpb, c->fq,
