@@ -370,13 +370,28 @@ __global__ void k_prolong_p(TransferDev T, const double* __restrict__ e, double*
   }
 }
 
+// y = alpha A x + beta y for a CSR matrix (the sparse transfers): kCsrLanes adjacent lanes per row, each taking every
+// kCsrLanes-th entry, then a fixed shuffle tree (the rows are short and the level is small, so spreading a row
+// over lanes hides the gather latency that a thread per row would serialise). Warp-uniform loop: every lane takes
+// part in the shuffles.
+constexpr int kCsrLanes = 4;
 __global__ void k_csr(int nrows, const int* __restrict__ off, const int* __restrict__ col,
                       const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y,
                       double alpha, double beta) {
-  GRID_STRIDE(r, nrows) {
+  const long total = (long)nrows * kCsrLanes;
+  const int lane = threadIdx.x & 31;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long tb = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); tb < total; tb += stride) {
+    const long t = tb + lane;
+    const bool act = t < total;
+    const int r = act ? (int)(t / kCsrLanes) : 0;
+    const int g = (int)(t & (kCsrLanes - 1));
     double v = 0.0;
-    for (int k = off[r]; k < off[r + 1]; ++k) v = fma(val[k], x[col[k]], v);
-    y[r] = beta == 0.0 ? alpha * v : fma(beta, y[r], alpha * v);
+    if (act)
+      for (int k = off[r] + g; k < off[r + 1]; k += kCsrLanes) v = fma(val[k], x[col[k]], v);
+#pragma unroll
+    for (int o = kCsrLanes >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (act && g == 0) y[r] = beta == 0.0 ? alpha * v : fma(beta, y[r], alpha * v);
   }
 }
 
@@ -516,7 +531,7 @@ void launch_prolong_p(cudaStream_t st, const TransferDev& T, const double* e, do
 void launch_csr(cudaStream_t st, int nrows, const int* off, const int* col, const double* val, const double* x,
                 double* y, double alpha, double beta) {
   COUNT(1);
-  k_csr<<<grid_for(nrows), kThreads, 0, st>>>(nrows, off, col, val, x, y, alpha, beta);
+  k_csr<<<grid_for((long)nrows * kCsrLanes), kThreads, 0, st>>>(nrows, off, col, val, x, y, alpha, beta);
 }
 void launch_coarse_cell(cudaStream_t st, const LevelDev& L, const double* sig, const double* p, const double* bp,
                         double* yl, double* rp, double* kapc, int kind, double a, Reduce red) {
