@@ -263,6 +263,25 @@ def run_serving(nlmg, n, smoother):
                     "smoother: " + smoother}
 
 
+def run_baselines(nlmg, pr, ctx):
+    """The single-level solvers the paper compares FAS with (Sec. 2.2), on the same problem and GPU: Picard steps
+    (frozen-coefficient CG to lin_tol, clamp, Algorithm 1) and Newton steps (exact Jacobian, GMRES(30), clamp,
+    Algorithm 1), each from p = 0 to relative residual 1e-8 or its iteration cap; one timed solve each."""
+    out = {}
+    for name, kw, cap in (("picard", dict(picard_only=True), 400), ("newton", dict(newton=True), 60)):
+        try:
+            _, rep, st = ctx.solve(pr.f_cell, pr.g_face, max_cycles=cap, allow_noconv=True, **kw)
+            out[name] = {"status": nlmg.STATUS_NAMES.get(int(st), str(st)), "iterations": rep["cycles"],
+                         "ms": rep["solve_ms"], "solves_per_s": 1e3 / rep["solve_ms"] if rep["solve_ms"] else None,
+                         "rel_residual": rep["res"] / rep["res0"] if rep["res0"] else None,
+                         "lin_iters": rep["lin_iters"], "cap": cap}
+        except nlmg.NlmgError as e:
+            out[name] = {"status": "error", "what": str(e)[:160], "cap": cap}
+    out["what"] = ("single-level solvers from p = 0 on the same workload and GPU (the FAS line is the bench value); "
+                   "a Newton iteration from p = 0 is outside its region of fast convergence on this channelized case")
+    return out
+
+
 def run_multi_rhs(nlmg, pr, ctx, n_rhs, n_streams):
     """n_rhs right-hand sides on the bench mesh and its hierarchy: one plain FP64 context solving them one after the
     other, against nlmg_solve_many on n_streams contexts of the same hierarchy, in FP64 and with the FP32 inner CG,
@@ -516,6 +535,7 @@ def run_gpu(args, rank, world, local_rank):
                  "what": "same FP64 FAS (residuals, transfers, coarse operators, convergence test in FP64); the CG "
                          "solves inside the Picard steps in FP32 (tolerances floored at 1e-6); the Newton steps' "
                          "BiCGStab stays FP64"}
+    baselines = run_baselines(nlmg, pr, ctx) if (args.baselines and world == 1) else None
     multi = run_multi_rhs(nlmg, pr, ctx, args.multi_rhs, args.streams) if (args.multi_rhs > 0 and world == 1) \
         else None
     serving = run_serving(nlmg, args.serving, args.smoother) if (args.serving > 0 and world == 1) else None
@@ -538,6 +558,7 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": roof,
         "newton_steps_per_solve": sum(r["newton_steps"] for r in reps) / len(reps),
         "picard_smoother": picard,
+        "single_level_baselines": baselines,
         "mixed": mixed,
         "multi_rhs": multi,
         "serving": serving,
@@ -570,6 +591,8 @@ def main():
     ap.add_argument("--streams", type=int, default=8, help="contexts (streams) of the multi-RHS solve")
     ap.add_argument("--smoother", default="picard_newton", choices=["picard", "picard_newton"],
                     help="level-0 smoother (Picard-then-Newton by default)")
+    ap.add_argument("--no-baselines", dest="baselines", action="store_false",
+                    help="skip the single-level Picard and Newton solves")
     ap.add_argument("--no-compare-picard", dest="compare_picard", action="store_false",
                     help="skip the timed loop with Picard steps throughout")
     ap.add_argument("--voronoi", type=int, default=0,

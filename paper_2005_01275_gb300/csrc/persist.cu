@@ -1,7 +1,8 @@
-// Persistent (cooperative) conjugate-gradient kernels: one launch runs a whole Picard linear solve, with
-// device-side scalars and convergence test, so the CG iterations pay neither launch gaps nor host round trips.
+// Persistent (cooperative) kernels: one launch runs a whole level-0 linear solve (the Picard step's CG, the Newton
+// step's BiCGStab) or whole coarse Picard steps (hybridized CG, clamp, Algorithm 1), with device-side scalars,
+// decisions and convergence tests, so the iterations pay neither launch gaps nor host round trips.
 //
-// Grid-wide synchronisation uses a counter/generation barrier whose wait is bounded: after ~2 s of spinning the
+// Grid-wide synchronisation uses a counter barrier whose wait is bounded: after ~2 s of spinning the
 // kernel records an error flag and every block leaves. The launch goes through cudaLaunchCooperativeKernel with at
 // most the co-resident number of blocks, so in a correct run every wait ends.
 //
