@@ -268,7 +268,7 @@ def run_baselines(nlmg, pr, ctx):
     (frozen-coefficient CG to lin_tol, clamp, Algorithm 1) and Newton steps (exact Jacobian, GMRES(30), clamp,
     Algorithm 1), each from p = 0 to relative residual 1e-8 or its iteration cap; one timed solve each."""
     out = {}
-    for name, kw, cap in (("picard", dict(picard_only=True), 400), ("newton", dict(newton=True), 60)):
+    for name, kw, cap in (("picard", dict(picard_only=True), 400), ("newton", dict(newton=True), 15)):
         try:
             _, rep, st = ctx.solve(pr.f_cell, pr.g_face, max_cycles=cap, allow_noconv=True, **kw)
             out[name] = {"status": nlmg.STATUS_NAMES.get(int(st), str(st)), "iterations": rep["cycles"],
@@ -488,6 +488,23 @@ def run_gpu(args, rank, world, local_rank):
                   "ms_per_step": pms / args.steps, "cycles_per_solve": sum(r["cycles"] for r in preps) / len(preps),
                   "lin_iters_level": preps[-1]["lin_iters_level"][:3],
                   "what": "the same solves with Picard steps on level 0 throughout (Sec. 3.3.1 smoother)"}
+    one_coarsest = None
+    if args.compare_picard:
+        # the same timed loop with one Picard step on the coarsest level instead of up to 10
+        ctx.set_options(coarsest_steps=1)
+        solve_dev()
+        creps = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            creps.append(solve_dev())
+        ctx.set_options(coarsest_steps=pr.opts.get("coarsest_steps", 10))
+        cms = max_over_ranks(sum(r["solve_ms"] for r in creps), dist, dev)
+        one_coarsest = {"value": replica_throughput(world, args.steps, cms), "unit": "solves/s",
+                        "ms_per_step": cms / args.steps,
+                        "cycles_per_solve": sum(r["cycles"] for r in creps) / len(creps),
+                        "what": "the same solves with one Picard step on the coarsest level (coarsest_steps = 1) "
+                                "instead of the paper's up to 10"}
     # end to end through the host-pointer C-ABI call: H2D of f and g from pinned memory, D2H of p
     f_h = torch.from_numpy(pr.f_cell).pin_memory()
     g_h = torch.from_numpy(pr.g_face).pin_memory()
@@ -558,6 +575,7 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": roof,
         "newton_steps_per_solve": sum(r["newton_steps"] for r in reps) / len(reps),
         "picard_smoother": picard,
+        "one_coarsest_step": one_coarsest,
         "single_level_baselines": baselines,
         "mixed": mixed,
         "multi_rhs": multi,
