@@ -167,7 +167,8 @@ def options_from_dict(d):
     """Options from the dictionary used by the synthetic problem configurations."""
     keep = {k: d[k] for k in ("n_levels", "agg_size", "modes", "nu_pre", "nu_post", "omega", "bt_nmax", "bt_theta",
                               "dp_clamp", "coarsest_steps", "coarsest_tol", "lin_tol", "lin_maxit", "coarse_lin_tol",
-                              "lin_precision", "max_sms", "newton_switch", "newton_lin_tol", "coarsest_lin_tol") if k in d}
+                              "lin_precision", "max_sms", "newton_switch", "newton_lin_tol", "coarsest_lin_tol",
+                              "setup_threads") if k in d}
     if "lin_tol" in d and "coarse_lin_tol" not in d:
         keep["coarse_lin_tol"] = d["lin_tol"]       # one tolerance given: use it on every level
     if "lin_tol" in d and "newton_lin_tol" not in d:
