@@ -1,6 +1,6 @@
 """Multilevel spectral coarsening in FP64 (oracle; test only).
 
-Builds, level by level, the objects of App. A of the paper with m_f = 1 flux unknown per coarse interface:
+Builds, level by level, the objects of App. A of the paper with m_f >= 1 flux unknowns per coarse interface:
   * Level: the mixed operator data of one level, stored cell by cell as in Prop. 1 / eq. assemble: for every cell
     c its static local flux matrix Mloc[c] (so that M(Pi~ p) = sum_c W_c^T Mloc[c] W_c / kappa(pbar_c)), its local
     divergence block Dloc[c] (so that D = sum_c rows_c Dloc[c] W_c) and its Pi~ weights w[c] (pbar_c = w[c].p_c).
@@ -23,6 +23,15 @@ Readings where the paper is silent:
   * Q_sigma (whose construction the paper defers): an interface (or boundary) coefficient is the total flux
     leaving the aggregate through that interface divided by the same total for its basis function; the bubble
     coefficients of A are P_NPV,A^T (D sigma)|_A. This gives Q_sigma P_sigma = I and D^{l+1} Q_sigma = Q_p D^l.
+  * m_f > 1 (App. A.2, eq. definition-traces): the traces at F_{K,L} are (M_N^-1 D_N^T q_i)|_F on N = N(A_K) for every
+    column q_i of P_{A_K} (extended by zero from A_K to N(A_K)), and the same from A_L. Each is scaled to unit 2-norm
+    and projected by Pi_F = I - sigma^PV t^T / (t . sigma^PV), t the outflow functional of A_K through F, so that
+    sigma^PV stays the only carrier of the net flux through F; the left singular vectors of the projected set with
+    singular value > 1e-8 are kept (at most m_f - 1 and |F| - 1), each signed so that its first entry within 1e-6 of
+    the largest magnitude is positive. Each is extended
+    into A_K and A_L like sigma^PV (its net flux, hence its coarse divergence, is zero) and is numbered after the
+    bubbles, interface by interface; its Q_sigma row is u^T Pi_F (u orthonormal), which keeps Q_sigma P_sigma = I and the commuting
+    relation. Coarse boundary unknowns keep one trace.
 Local Neumann problems are solved densely with the pressure null vector 1^l fixed by a bordering constraint.
 """
 from __future__ import annotations
@@ -37,6 +46,7 @@ from .tpfa import BC_INTERIOR, BC_DIRICHLET, flux_dofs
 
 KIND_IFACE, KIND_BDRY, KIND_BUBBLE = 0, 1, 2
 SVD_DROP = 1e-10
+TRACE_DROP = 1e-8
 
 
 @dataclass
@@ -184,9 +194,18 @@ def _sign_fix(u):
     return u if u[i] > 0 else -u
 
 
-def coarsen(lev, target, modes, fine_vol, P0_prev, fine_agg_prev):
+def _sign_fix_tie(u):
+    """Sign of a kept trace: its first entry within 1e-6 (relative) of the largest magnitude is made positive, so
+    that entries equal in exact arithmetic (mirror-symmetric interfaces) do not let rounding pick the sign."""
+    a = np.abs(u)
+    i = int(np.argmax(a >= (1.0 - 1e-6) * a.max()))
+    return u if u[i] > 0 else -u
+
+
+def coarsen(lev, target, modes, fine_vol, P0_prev, fine_agg_prev, flux_modes=1):
     """One coarsening step l -> l+1. Returns (coarse Level, Transfer, composed P to level 0, fine->coarse map).
 
+    flux_modes: m_f, flux unknowns per coarse interface at most (1: sigma^PV alone).
     fine_vol: level-0 cell volumes; P0_prev: (P_p)^0_l (sparse, n_fine x n_p(l)); fine_agg_prev: level-0 cell ->
     level-l cell map.
     """
@@ -211,6 +230,7 @@ def coarsen(lev, target, modes, fine_vol, P0_prev, fine_agg_prev):
     # --- local eigenproblems on extended aggregates -> P_A = [q_PV, P_NPV] ------------------------------------
     PA = []
     eig_gap = []
+    trace_src = []       # m_f > 1: (sN, M_N^-1 D_N^T [P_A extended by zero]) per aggregate, eq. definition-traces
     for a in range(n_agg):
         cA = cells_of[a]
         ext = set(cA.tolist())
@@ -240,6 +260,10 @@ def coarsen(lev, target, modes, fine_vol, P0_prev, fine_agg_prev):
                 for j in range(k):
                     cols.append(_sign_fix(U[:, j]))
         PA.append(np.stack(cols, 1))
+        if flux_modes > 1:
+            Qt = np.zeros((pN.size, PA[-1].shape[1]))
+            Qt[pos] = PA[-1]
+            trace_src.append((sN, np.linalg.solve(MN, DN.T @ Qt) if sN.size else np.zeros((0, Qt.shape[1]))))
     mc = np.array([P.shape[1] for P in PA], dtype=np.int64)
     coff = np.concatenate([[0], np.cumsum(mc)])
     rows, cols_, vals = [], [], []
@@ -281,10 +305,31 @@ def coarsen(lev, target, modes, fine_vol, P0_prev, fine_agg_prev):
         rp = c_a * q - DaF
         return _neumann_solve(Msub(ia, ia), Dsub(pa, ia), lev.ones[pa], rs, rp), c_a
 
+    def extra_traces(a, b, Fd, sF, tvec):
+        """m_f > 1: orthonormal traces on F beside sigma^PV, and the projection Pi_F (docstring of the module)."""
+        cols = []
+        for c in (a, b):
+            sN, T = trace_src[c]
+            pos = np.searchsorted(sN, Fd)
+            assert np.all(sN[pos] == Fd)
+            for i in range(T.shape[1]):
+                v = T[pos, i]
+                nv = np.linalg.norm(v)
+                if nv > 0:
+                    cols.append(v / nv)
+        Pi = np.eye(Fd.size) - np.outer(sF, tvec) / (tvec @ sF)
+        if not cols or Fd.size < 2:
+            return [], Pi, np.zeros(0)
+        U, S, _ = np.linalg.svd(Pi @ np.stack(cols, 1), full_matrices=False)
+        k = min(int(np.sum(S > TRACE_DROP)), flux_modes - 1, Fd.size - 1)
+        return [_sign_fix_tie(U[:, j]) for j in range(k)], Pi, S
+
     psi_cols = []        # (support ids, values)
     qrows = []           # (ids, coefficients)
     coarse_kind, coarse_owner = [], []
     sigma_pv = {}
+    trace_sv = {}        # m_f > 1: singular values of the projected trace set per interface
+    pending = []         # m_f > 1: the kept traces, numbered after the bubbles (interface by interface)
     for (a, b) in pairs:
         Fd = np.array(sorted(iface_pairs[(a, b)]), dtype=np.int64)
         U = np.concatenate([cells_of[a], cells_of[b]])
@@ -305,6 +350,13 @@ def coarsen(lev, target, modes, fine_vol, P0_prev, fine_agg_prev):
         qrows.append((Fd, tvec / (tvec @ sF)))
         coarse_kind.append(KIND_IFACE)
         coarse_owner.append((a, b))
+        if flux_modes > 1:
+            extras, Pi, sv = extra_traces(a, b, Fd, sF, tvec)
+            trace_sv[(a, b)] = sv
+            for u in extras:
+                ea, _ = extend(a, Fd, u)
+                eb, _ = extend(b, Fd, u)
+                pending.append(((ids, np.concatenate([ea, u, eb])), (Fd, Pi.T @ u), (a, b)))
     for a in bdry_aggs:
         Bd = np.array(sorted(bdry_of[a]), dtype=np.int64)
         ia, pa = int_of[a], pd_of[a]
@@ -330,6 +382,11 @@ def coarsen(lev, target, modes, fine_vol, P0_prev, fine_agg_prev):
             qrows.append((nz, row[nz]))
             coarse_kind.append(KIND_BUBBLE)
             coarse_owner.append((a, -1))
+    for col, qr, ab in pending:
+        psi_cols.append(col)
+        qrows.append(qr)
+        coarse_kind.append(KIND_IFACE)
+        coarse_owner.append(ab)
     ncf = len(psi_cols)
     rows, cols_, vals = [], [], []
     for J, (ids, v) in enumerate(psi_cols):
@@ -376,7 +433,8 @@ def coarsen(lev, target, modes, fine_vol, P0_prev, fine_agg_prev):
     coarse = Level(n_cells=n_agg, m=mc, n_flux=ncf, flux_kind=coarse_kind, flux_owner=coarse_owner, loc=loc_c,
                    Mloc=Mloc_c, Dloc=Dloc_c, w=w_c, vol=vol_c, ones=ones_c)
     tr = Transfer(agg_of=agg_of, Pp=Pp, Psigma=Psig, Qsigma=Qsig,
-                  extra=dict(PA=PA, sigma_pv=sigma_pv, pairs=pairs, eig_gap=np.array(eig_gap), Dc=Dc))
+                  extra=dict(PA=PA, sigma_pv=sigma_pv, pairs=pairs, eig_gap=np.array(eig_gap), Dc=Dc,
+                             trace_sv=trace_sv))
     return coarse, tr, P0, fine_agg
 
 
@@ -387,13 +445,16 @@ class Hierarchy:
 
 
 def build(mesh, opts):
-    """Levels 0..n_levels-1 with aggregate targets opts['agg_size'][l] and modes opts['modes'][l]."""
+    """Levels 0..n_levels-1 with aggregate targets opts['agg_size'][l], modes opts['modes'][l] and flux unknowns per
+    coarse interface opts['flux_modes'][l] (default 1)."""
     lev = level0(mesh)
     levels, transfers = [lev], []
     P0 = sp.identity(mesh.n_cells, format="csr")
     fagg = np.arange(mesh.n_cells)
+    mf = opts.get("flux_modes", [1] * 8)
     for l in range(opts["n_levels"] - 1):
-        lev, tr, P0, fagg = coarsen(lev, opts["agg_size"][l], opts["modes"][l], mesh.cell_volume, P0, fagg)
+        lev, tr, P0, fagg = coarsen(lev, opts["agg_size"][l], opts["modes"][l], mesh.cell_volume, P0, fagg,
+                                    flux_modes=int(mf[l]))
         levels.append(lev)
         transfers.append(tr)
     return Hierarchy(levels, transfers)

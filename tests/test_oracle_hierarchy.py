@@ -68,11 +68,19 @@ def hier3d():
     return pr, hierarchy.build(pr.mesh, opts)
 
 
+@pytest.fixture(scope="module")
+def hier3d_mf():
+    """m_f = 3 flux unknowns per coarse interface at most (App. A.2), three levels."""
+    pr = problem_config("chan3d_64", scale=8)
+    opts = dict(pr.opts, agg_size=[16, 4, 4], modes=[3, 3, 3], flux_modes=[3, 3, 3])
+    return pr, hierarchy.build(pr.mesh, opts)
+
+
 def _levels(request):
     return request.getfixturevalue(request.param)
 
 
-@pytest.fixture(params=["hier2d", "hier3d"])
+@pytest.fixture(params=["hier2d", "hier3d", "hier3d_mf"])
 def H(request):
     return _levels(request)
 
@@ -219,3 +227,81 @@ def test_level0_mixed_operator_matches_fv_matrix():
     M1 = hierarchy.assemble_M(lev, 1.0 / tpfa.kappa(p, pr.kappa_kind, pr.kappa_a))
     assert np.allclose(M1.toarray(), M0.toarray(), rtol=1e-14)
     assert np.array_equal(hierarchy.assemble_D(lev).toarray(), D0.toarray())
+
+
+def test_flux_modes_add_divergence_free_traces(hier3d, hier3d_mf):
+    """m_f > 1 keeps the m_f = 1 space as its leading columns (sigma^PV, boundary traces, bubbles are unchanged) and
+    adds interface unknowns whose coarse divergence vanishes: they carry no net flux through their interface, so
+    D^{l+1} of the m_f = 1 space is unchanged too."""
+    _, H1 = hier3d
+    _, H3 = hier3d_mf
+    for l, (t1, t3) in enumerate(zip(H1.transfers, H3.transfers)):
+        L3 = H3.levels[l + 1]
+        n0 = int(np.sum(L3.flux_kind != hierarchy.KIND_IFACE)) + len(t3.extra["pairs"])   # m_f = 1 unknowns
+        assert t3.Psigma.shape[1] > n0
+        if l == 0:   # same fine level: the m_f = 1 space is the leading block
+            P1, P3 = t1.Psigma.toarray(), t3.Psigma.toarray()
+            assert t1.Psigma.shape[1] == n0
+            assert np.allclose(P3[:, :n0], P1, rtol=0, atol=1e-12 * np.abs(P1).max())
+            assert np.allclose(t3.Qsigma.toarray()[:n0], t1.Qsigma.toarray(), rtol=0, atol=1e-12)
+        assert np.all(L3.flux_kind[n0:] == hierarchy.KIND_IFACE)
+        own = L3.flux_owner[n0:]
+        assert np.all(own[:, 0] >= 0) and np.all(own[:, 1] >= 0)
+        Dc = hierarchy.assemble_D(L3).toarray()
+        assert np.abs(Dc[:, n0:]).max() <= 1e-10 * np.abs(Dc[:, :n0]).max()
+        # at most m_f unknowns per coarse interface
+        pairs, counts = np.unique(np.sort(L3.flux_owner[L3.flux_kind == hierarchy.KIND_IFACE], 1), axis=0,
+                                  return_counts=True)
+        assert counts.max() <= 3 and counts.max() >= 2
+
+
+def test_flux_modes_reproduce_the_local_traces():
+    """eq. definition-traces: with m_f = 1 + (number of traces), so that no trace is cut by m_f, every trace
+    (M_N^-1 D_N^T q_i)|_F of both aggregates' pressure modes, computed here by a sparse direct solve on N(A), lies in
+    the span of the coarse flux unknowns of F restricted to F (checked where that span is not all of F)."""
+    import scipy.sparse.linalg as spla
+    pr = problem_config("chan3d_64", scale=8)
+    modes = 3
+    opts = dict(pr.opts, agg_size=[16, 4], modes=[modes, 2], flux_modes=[1 + 2 * modes, 1], n_levels=2)
+    Hh = hierarchy.build(pr.mesh, opts)
+    lev, tr = Hh.levels[0], Hh.transfers[0]
+    M = hierarchy.assemble_M(lev).tocsc()
+    D = hierarchy.assemble_D(lev).tocsr()
+    own = lev.flux_owner
+    ifc = np.where(lev.flux_kind == hierarchy.KIND_IFACE)[0]
+    nbrs = [set() for _ in range(lev.n_cells)]
+    for j in ifc:
+        nbrs[own[j, 0]].add(int(own[j, 1]))
+        nbrs[own[j, 1]].add(int(own[j, 0]))
+    agg = tr.agg_of
+    Ps = tr.Psigma.tocsc()
+    L1 = Hh.levels[1]
+    checked = 0
+    for (a, b) in tr.extra["pairs"]:
+        F = np.array(sorted(j for j in ifc if {agg[own[j, 0]], agg[own[j, 1]]} == {a, b}))
+        cols = [J for J in range(L1.n_flux) if L1.flux_kind[J] == hierarchy.KIND_IFACE
+                and sorted(L1.flux_owner[J]) == [a, b]]
+        assert len(cols) <= min(F.size, 1 + 2 * modes)
+        if len(cols) == F.size:
+            continue                                  # the span is all of F: nothing to check
+        B = Ps[:, cols].toarray()[F]
+        for c in (a, b):
+            cells = np.where(agg == c)[0]
+            N = set(cells.tolist())
+            for x in cells:
+                N |= nbrs[x]
+            inN = np.zeros(lev.n_cells, bool)
+            inN[list(N)] = True
+            sN = np.array([j for j in ifc if inN[own[j, 0]] and inN[own[j, 1]]])
+            PA = tr.extra["PA"][c]
+            for i in range(PA.shape[1]):
+                q = np.zeros(lev.n_cells)
+                q[cells] = PA[:, i]
+                v = spla.spsolve(M[sN][:, sN].tocsc(), D[:, sN].T @ q)
+                v = v[np.searchsorted(sN, F)]
+                if np.linalg.norm(v) == 0:
+                    continue
+                coef, *_ = np.linalg.lstsq(B, v, rcond=None)
+                assert np.linalg.norm(B @ coef - v) <= 1e-7 * np.linalg.norm(v)
+                checked += 1
+    assert checked > 50
