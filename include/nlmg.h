@@ -99,6 +99,11 @@ typedef struct {
                                 nlmg_vcycle calls carry it) */
   double newton_lin_tol;     /* relative tolerance of the BiCGStab solves of the Newton steps (default 1e-2) */
   double coarsest_lin_tol;   /* the same on the coarsest level (default 2e-1; <= 0: coarse_lin_tol) */
+  int32_t flux_modes[8];     /* m_f of step l -> l+1: flux unknowns per coarse interface at most (1..8, default 1).
+                                1 keeps sigma^PV alone; above 1 the traces of eq. definition-traces from both
+                                aggregates' pressure modes are projected off the net flux, and the leading left
+                                singular vectors (value > 1e-8 on unit-norm traces) are added beside sigma^PV, each
+                                extended into both aggregates (App. A.2). A hierarchy option, fixed at setup */
   int32_t reserved[5];
 } nlmg_options;
 

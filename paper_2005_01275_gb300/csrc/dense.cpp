@@ -301,16 +301,41 @@ bool invert(int n, const double* A, double* Ainv) {
   return true;
 }
 
+// Left-looking Cholesky, L in the lower triangle. Every entry is one dot product summed in k order; eight rows of a
+// column are summed side by side (independent chains, each in the same order as alone), which hides the add latency
+// without changing a single rounding.
 bool chol_factor(int n, double* A) {
   for (int j = 0; j < n; ++j) {
-    double s = A[(size_t)j * n + j];
-    for (int k = 0; k < j; ++k) s -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
+    const double* Aj = A + (size_t)j * n;
+    double s = Aj[j];
+    for (int k = 0; k < j; ++k) s -= Aj[k] * Aj[k];
     if (!(s > 0.0)) return false;
     double ljj = std::sqrt(s);
     A[(size_t)j * n + j] = ljj;
-    for (int i = j + 1; i < n; ++i) {
+    int i = j + 1;
+    for (; i + 8 <= n; i += 8) {
+      double* R[8];
+      double t[8];
+      for (int u = 0; u < 8; ++u) {
+        R[u] = A + (size_t)(i + u) * n;
+        t[u] = R[u][j];
+      }
+      for (int k = 0; k < j; ++k) {
+        const double a = Aj[k];
+        t[0] -= R[0][k] * a;
+        t[1] -= R[1][k] * a;
+        t[2] -= R[2][k] * a;
+        t[3] -= R[3][k] * a;
+        t[4] -= R[4][k] * a;
+        t[5] -= R[5][k] * a;
+        t[6] -= R[6][k] * a;
+        t[7] -= R[7][k] * a;
+      }
+      for (int u = 0; u < 8; ++u) R[u][j] = t[u] / ljj;
+    }
+    for (; i < n; ++i) {
       double t = A[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) t -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+      for (int k = 0; k < j; ++k) t -= A[(size_t)i * n + k] * Aj[k];
       A[(size_t)i * n + j] = t / ljj;
     }
   }

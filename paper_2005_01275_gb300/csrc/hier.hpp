@@ -68,6 +68,7 @@ struct Options {
   int n_levels = 2;
   int agg_size[8] = {16, 8, 8, 8, 8, 8, 8, 8};
   int modes[8] = {2, 2, 2, 2, 2, 2, 2, 2};
+  int flux_modes[8] = {1, 1, 1, 1, 1, 1, 1, 1};   // m_f: flux unknowns per coarse interface at most
   int threads = 0;
 };
 

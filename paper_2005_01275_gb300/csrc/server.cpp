@@ -113,6 +113,7 @@ uint64_t hierarchy_key(const Request& r) {
   for (int l = 0; l + 1 < nl; ++l) {
     f.add(&r.opt.agg_size[l], sizeof(int32_t));
     f.add(&r.opt.modes[l], sizeof(int32_t));
+    f.add(&r.opt.flux_modes[l], sizeof(int32_t));
   }
   return f.h;
 }
@@ -121,7 +122,9 @@ bool same_hierarchy(const Request& a, const Request& b) {
   if (a.key != b.key || a.n_cells != b.n_cells || a.n_faces != b.n_faces || a.opt.n_levels != b.opt.n_levels)
     return false;
   for (int l = 0; l + 1 < a.opt.n_levels; ++l)
-    if (a.opt.agg_size[l] != b.opt.agg_size[l] || a.opt.modes[l] != b.opt.modes[l]) return false;
+    if (a.opt.agg_size[l] != b.opt.agg_size[l] || a.opt.modes[l] != b.opt.modes[l] ||
+        a.opt.flux_modes[l] != b.opt.flux_modes[l])
+      return false;
   return a.vol == b.vol && a.fc == b.fc && a.ht == b.ht && a.bc == b.bc && a.area == b.area;
 }
 

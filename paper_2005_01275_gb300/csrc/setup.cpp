@@ -32,6 +32,8 @@ namespace nlmg {
 
 namespace {
 
+constexpr double kTraceDrop = 1e-8;   // m_f > 1: singular values kept of the projected unit-norm traces
+
 void parallel_for(int n, int threads, const std::function<void(int, int, int)>& body) {
   // body(begin, end, worker) over contiguous chunks claimed dynamically; results must not depend on the order
   if (threads <= 1 || n < 2) {
@@ -55,6 +57,8 @@ void parallel_for(int n, int threads, const std::function<void(int, int, int)>& 
 // Per-thread scratch: stamped membership and position maps so that sets can be built without clearing.
 struct Scratch {
   std::vector<int> cell_stamp, flux_stamp, flux_pos;
+  std::vector<int> trow, tcol;   // D's entries in assembly order (row, flux column, value)
+  std::vector<double> tval;
   int token = 0;
   void init(int nc, int nf) {
     cell_stamp.assign(nc, 0);
@@ -69,7 +73,20 @@ struct Scratch {
 struct LocalProblem {
   std::vector<int> cells, U, prow;   // prow[k] = first local pressure row of cells[k]
   int np = 0;
-  std::vector<double> M, D, ones;    // M: |U| x |U|, D: np x |U|
+  bool mdiag = false;                // M is diagonal (level 0: TPFA): only Md and the sparse D are stored
+  std::vector<double> M, Md, D, ones;   // M: |U| x |U| (when not diagonal), Md: its diagonal, D: np x |U| (dense,
+                                        // when M is not diagonal)
+  std::vector<int> dc_off, dc_row;      // when M is diagonal: the nonzeros of D by flux column, rows ascending
+  std::vector<double> dc_val;
+};
+
+// X = M^-1 D^T (|U| x np): dense, or by rows of its nonzeros (columns ascending) when M is diagonal.
+struct LocalX {
+  bool sparse = false;
+  std::vector<double> dense;
+  std::vector<double> mfac;   // Cholesky factor of M (dense case; kept for solves with a flux right-hand side)
+  std::vector<int> off, col;
+  std::vector<double> val;
 };
 
 void assemble_local(const Level& L, const std::vector<int>& cells, const std::vector<int>& U, Scratch& sc,
@@ -88,9 +105,17 @@ void assemble_local(const Level& L, const std::vector<int>& cells, const std::ve
     lp.prow[k] = lp.np;
     lp.np += L.m[cells[k]];
   }
-  lp.M.assign((size_t)ns * ns, 0.0);
-  lp.D.assign((size_t)lp.np * ns, 0.0);
+  // M is assembled densely only when some off-diagonal entry is nonzero (coarse levels); the TPFA level keeps its
+  // diagonal alone, which saves the |U|^2 storage and scans that dominated the setup (same sums, same order)
+  lp.Md.assign(ns, 0.0);
   lp.ones.assign(lp.np, 0.0);
+  std::vector<int>& trow = sc.trow;
+  std::vector<int>& tcol = sc.tcol;
+  std::vector<double>& tval = sc.tval;
+  trow.clear();
+  tcol.clear();
+  tval.clear();
+  bool diag = true;
   for (size_t k = 0; k < cells.size(); ++k) {
     int c = cells[k];
     int nl = L.nloc(c), mc = L.m[c];
@@ -103,9 +128,79 @@ void assemble_local(const Level& L, const std::vector<int>& cells, const std::ve
       int ps = sc.flux_pos[lc[s]];
       for (int t = 0; t < nl; ++t) {
         if (sc.flux_stamp[lc[t]] != tok) continue;
+        const int pt = sc.flux_pos[lc[t]];
+        const double v = Mc[(size_t)s * nl + t];
+        if (pt == ps)
+          lp.Md[ps] += v;
+        else if (v != 0.0)
+          diag = false;
+      }
+      for (int r = 0; r < mc; ++r) {
+        trow.push_back(lp.prow[k] + r);
+        tcol.push_back(ps);
+        tval.push_back(Dc[(size_t)r * nl + s]);
+      }
+    }
+  }
+  lp.mdiag = diag;
+  lp.M.clear();
+  lp.D.clear();
+  lp.dc_off.clear();
+  lp.dc_row.clear();
+  lp.dc_val.clear();
+  const size_t nt = trow.size();
+  if (diag) {
+    // D by flux column: a stable counting sort keeps each column's rows in generation order, which ascends (cells in
+    // order, then their pressure rows); an entry met twice is summed in that order, as the dense assembly would
+    lp.dc_off.assign(ns + 1, 0);
+    for (size_t t = 0; t < nt; ++t) ++lp.dc_off[tcol[t] + 1];
+    for (int i = 0; i < ns; ++i) lp.dc_off[i + 1] += lp.dc_off[i];
+    std::vector<int> fill(lp.dc_off.begin(), lp.dc_off.end() - 1);
+    lp.dc_row.assign(nt, 0);
+    lp.dc_val.assign(nt, 0.0);
+    for (size_t t = 0; t < nt; ++t) {
+      const int at = fill[tcol[t]]++;
+      lp.dc_row[at] = trow[t];
+      lp.dc_val[at] = tval[t];
+    }
+    int w = 0;
+    for (int i = 0; i < ns; ++i) {
+      const int b = lp.dc_off[i], e = lp.dc_off[i + 1];
+      lp.dc_off[i] = w;
+      const int w0 = w;
+      for (int t = b; t < e; ++t) {
+        int hit = -1;
+        for (int u = w0; u < w; ++u)
+          if (lp.dc_row[u] == lp.dc_row[t]) hit = u;
+        if (hit >= 0) {
+          lp.dc_val[hit] += lp.dc_val[t];
+        } else {
+          lp.dc_row[w] = lp.dc_row[t];
+          lp.dc_val[w] = lp.dc_val[t];
+          ++w;
+        }
+      }
+    }
+    lp.dc_off[ns] = w;
+    lp.dc_row.resize(w);
+    lp.dc_val.resize(w);
+    return;
+  }
+  lp.D.assign((size_t)lp.np * ns, 0.0);
+  for (size_t t = 0; t < nt; ++t) lp.D[(size_t)trow[t] * ns + tcol[t]] += tval[t];
+  lp.M.assign((size_t)ns * ns, 0.0);
+  for (size_t k = 0; k < cells.size(); ++k) {
+    int c = cells[k];
+    int nl = L.nloc(c);
+    const int* lc = &L.loc[L.loc_off[c]];
+    const double* Mc = &L.Mloc[L.mat_off[c]];
+    for (int s = 0; s < nl; ++s) {
+      if (sc.flux_stamp[lc[s]] != tok) continue;
+      int ps = sc.flux_pos[lc[s]];
+      for (int t = 0; t < nl; ++t) {
+        if (sc.flux_stamp[lc[t]] != tok) continue;
         lp.M[(size_t)ps * ns + sc.flux_pos[lc[t]]] += Mc[(size_t)s * nl + t];
       }
-      for (int r = 0; r < mc; ++r) lp.D[(size_t)(lp.prow[k] + r) * ns + ps] += Dc[(size_t)r * nl + s];
     }
   }
 }
@@ -129,22 +224,44 @@ std::vector<int> internal_flux(const Level& L, const std::vector<int>& cells, Sc
   return U;
 }
 
-// Schur complement S = D M^-1 D^T and X = M^-1 D^T (|U| x np); returns false if M is not SPD.
-bool schur(const LocalProblem& lp, std::vector<double>& S, std::vector<double>& X) {
+// Schur complement S = D M^-1 D^T and X = M^-1 D^T (|U| x np); returns false if M is not SPD. With a diagonal M both
+// follow from D's nonzeros alone: every entry of S gathers the same products in the same order (flux columns
+// ascending) as the dense form, whose other terms are zeros, so the result is the same to the bit.
+bool schur(const LocalProblem& lp, std::vector<double>& S, LocalX& XL) {
   const int ns = (int)lp.U.size(), np = lp.np;
+  XL.sparse = lp.mdiag;
+  XL.dense.clear();
+  XL.off.clear();
+  XL.col.clear();
+  XL.val.clear();
+  if (lp.mdiag) {
+    for (int i = 0; i < ns; ++i)
+      if (!(lp.Md[i] > 0)) return false;
+    XL.off = lp.dc_off;
+    XL.col = lp.dc_row;
+    XL.val.resize(lp.dc_val.size());
+    for (int i = 0; i < ns; ++i)
+      for (int t = lp.dc_off[i]; t < lp.dc_off[i + 1]; ++t) XL.val[t] = lp.dc_val[t] / lp.Md[i];
+    S.assign((size_t)np * np, 0.0);
+    for (int i = 0; i < ns; ++i)
+      for (int t = lp.dc_off[i]; t < lp.dc_off[i + 1]; ++t) {
+        const double d = lp.dc_val[t];
+        if (d == 0.0) continue;
+        double* Sr = &S[(size_t)lp.dc_row[t] * np];
+        for (int u = lp.dc_off[i]; u < lp.dc_off[i + 1]; ++u) Sr[lp.dc_row[u]] += d * XL.val[u];
+      }
+    for (int r = 0; r < np; ++r)
+      for (int q = r + 1; q < np; ++q) {
+        double a = 0.5 * (S[(size_t)r * np + q] + S[(size_t)q * np + r]);
+        S[(size_t)r * np + q] = S[(size_t)q * np + r] = a;
+      }
+    return true;
+  }
+  std::vector<double>& X = XL.dense;
   X.assign((size_t)ns * np, 0.0);
-  bool diag = true;
-  for (int i = 0; i < ns && diag; ++i)
-    for (int j = 0; j < ns; ++j)
-      if (i != j && lp.M[(size_t)i * ns + j] != 0.0) { diag = false; break; }
-  if (diag) {
-    for (int i = 0; i < ns; ++i) {
-      double mi = lp.M[(size_t)i * ns + i];
-      if (!(mi > 0)) return false;
-      for (int r = 0; r < np; ++r) X[(size_t)i * np + r] = lp.D[(size_t)r * ns + i] / mi;
-    }
-  } else {
-    std::vector<double> Lc(lp.M);
+  {
+    std::vector<double>& Lc = XL.mfac;
+    Lc = lp.M;
     if (!chol_factor(ns, Lc.data())) return false;
     for (int r = 0; r < np; ++r)
       for (int i = 0; i < ns; ++i) X[(size_t)i * np + r] = lp.D[(size_t)r * ns + i];
@@ -178,7 +295,8 @@ bool schur(const LocalProblem& lp, std::vector<double>& S, std::vector<double>& 
 // rounding.
 struct LocalSolver {
   const LocalProblem* lp = nullptr;
-  std::vector<double> X, U;   // X = M^-1 D^T ; U = upper Cholesky factor of the (reduced) S
+  LocalX X;                   // M^-1 D^T
+  std::vector<double> U;      // upper Cholesky factor of the (reduced) S
   std::vector<double> S;      // the full S (Neumann problems, for the refinement step)
   int pin = -1;               // pressure unknown fixed to 0, or -1
   int nk = 0;
@@ -218,6 +336,22 @@ struct LocalSolver {
     for (int r = 0, rr = 0; r < np; ++r)
       if (r != pin) pv[r] = b[rr++];
   }
+  // [M D^T; D 0][sigma; p] = [rs; rp]: y = M^-1 rs, S p = D y - rp, sigma = y - X p
+  void solve_rhs(const std::vector<double>& rs, const std::vector<double>& rp, std::vector<double>& sigma) const {
+    const int np = lp->np, ns = (int)lp->U.size();
+    std::vector<double> y(rs), rq(rp);
+    if (X.sparse) {
+      for (int i = 0; i < ns; ++i) y[i] /= lp->Md[i];
+      for (int i = 0; i < ns; ++i)
+        for (int t = lp->dc_off[i]; t < lp->dc_off[i + 1]; ++t) rq[lp->dc_row[t]] -= lp->dc_val[t] * y[i];
+    } else {
+      chol_solve(ns, X.mfac.data(), y.data());
+      for (int r = 0; r < np; ++r)
+        for (int i = 0; i < ns; ++i) rq[r] -= lp->D[(size_t)r * ns + i] * y[i];
+    }
+    solve_p_rhs(rq, sigma);
+    for (int i = 0; i < ns; ++i) sigma[i] += y[i];
+  }
   // S p = -rp ; sigma = -X p
   void solve_p_rhs(const std::vector<double>& rp, std::vector<double>& sigma) const {
     const int np = lp->np, ns = (int)lp->U.size();
@@ -243,8 +377,12 @@ struct LocalSolver {
     sigma.assign(ns, 0.0);
     for (int i = 0; i < ns; ++i) {
       double s = 0.0;
-      const double* Xi = &X[(size_t)i * np];
-      for (int r = 0; r < np; ++r) s += Xi[r] * pv[r];
+      if (X.sparse) {
+        for (int t = X.off[i]; t < X.off[i + 1]; ++t) s += X.val[t] * pv[X.col[t]];
+      } else {
+        const double* Xi = &X.dense[(size_t)i * np];
+        for (int r = 0; r < np; ++r) s += Xi[r] * pv[r];
+      }
       sigma[i] = -s;
     }
   }
@@ -357,8 +495,8 @@ Level make_level0(const FineMesh& fm) {
 }
 
 // One coarsening step.
-static bool coarsen(const Level& L, int target, int modes, int threads, bool use_gpu_eig, const EigBatchFn& eig_fn,
-                    Level& C, Transfer& T, std::string& err) {
+static bool coarsen(const Level& L, int target, int modes, int flux_modes, int threads, bool use_gpu_eig,
+                    const EigBatchFn& eig_fn, Level& C, Transfer& T, std::string& err) {
   const int n = L.n_cells;
   // ---- cell graph ----------------------------------------------------------------------------------------------
   std::vector<std::vector<int>> nbv(n);
@@ -402,6 +540,10 @@ static bool coarsen(const Level& L, int target, int modes, int threads, bool use
   std::vector<std::vector<double>> Smat(na);
   std::vector<std::vector<int>> rows_in_N(na);
   std::vector<int> nS(na, 0), kS(na, 1);
+  // m_f > 1: the rows of X_N = M_N^-1 D_N^T at the flux unknowns leaving A (one owner in A), restricted to A's
+  // pressure rows, so that the traces of eq. definition-traces follow once P_A is known (CSR over A's rows)
+  std::vector<std::vector<int>> xb_ids(na), xb_off(na), xb_col(na);
+  std::vector<std::vector<double>> xb_val(na);
   parallel_for(na, threads, [&](int b, int e, int w) {
     Scratch& sc = scr[w];
     for (int a = b; a < e; ++a) {
@@ -412,7 +554,7 @@ static bool coarsen(const Level& L, int target, int modes, int threads, bool use
       std::vector<int> UN = internal_flux(L, cN, sc);
       LocalProblem lp;
       assemble_local(L, cN, UN, sc, lp);
-      std::vector<double> X;
+      LocalX X;
       if (!schur(lp, Smat[a], X)) { fail = true; continue; }
       nS[a] = lp.np;
       kS[a] = std::min(modes, np_of(a));
@@ -421,6 +563,27 @@ static bool coarsen(const Level& L, int target, int modes, int threads, bool use
         if (j < cA.size() && cN[k] == cA[j]) {
           for (int r = 0; r < L.m[cN[k]]; ++r) rows.push_back(lp.prow[k] + r);
           ++j;
+        }
+      }
+      if (flux_modes > 1) {
+        std::vector<int> tmap(lp.np, -1);
+        for (size_t t = 0; t < rows.size(); ++t) tmap[rows[t]] = (int)t;
+        auto inA = [&](int c) { return c >= 0 && std::binary_search(cA.begin(), cA.end(), c); };
+        xb_off[a].push_back(0);
+        for (size_t k = 0; k < UN.size(); ++k) {
+          const int f = UN[k];
+          if (L.fkind[f] != KIND_IFACE || inA(L.fown0[f]) == inA(L.fown1[f])) continue;
+          xb_ids[a].push_back(f);
+          if (X.sparse) {
+            for (int t = X.off[k]; t < X.off[k + 1]; ++t)
+              if (tmap[X.col[t]] >= 0) { xb_col[a].push_back(tmap[X.col[t]]); xb_val[a].push_back(X.val[t]); }
+          } else {
+            for (size_t t = 0; t < rows.size(); ++t) {
+              const double v = X.dense[k * lp.np + rows[t]];
+              if (v != 0.0) { xb_col[a].push_back((int)t); xb_val[a].push_back(v); }
+            }
+          }
+          xb_off[a].push_back((int)xb_col[a].size());
         }
       }
     }
@@ -565,9 +728,12 @@ static bool coarsen(const Level& L, int target, int modes, int threads, bool use
   const int nF = (int)plist.size(), nB = (int)bagg.size();
   std::vector<int> bub_off(na + 1, 0);
   for (int a = 0; a < na; ++a) bub_off[a + 1] = bub_off[a] + (ma[a] - 1);
-  const int nC = nF + nB + bub_off[na];
+  const int nC0 = nF + nB + bub_off[na];   // sigma^PV per interface, boundary unknowns, bubbles; m_f > 1 traces follow
+  int nC = nC0;
   // basis functions as sparse columns (level-l flux id, value) and Q_sigma rows
   std::vector<std::vector<std::pair<int, double>>> psi(nC), qrow(nC);
+  // m_f > 1: per interface the orthonormal traces kept beside sigma^PV and their Q_sigma rows (both on Fd)
+  std::vector<std::vector<std::vector<double>>> extraU(nF), extraQ(nF);
   // outflow functional of aggregate a over a set of flux ids: t_i = -(1_a^T D)_i
   auto outflow_coef = [&](int a, const std::vector<int>& ids, Scratch& sc) {
     int tok = sc.next();
@@ -598,6 +764,82 @@ static bool coarsen(const Level& L, int target, int modes, int threads, bool use
     for (size_t k = 0; k < Fd.size(); ++k) qrow[J].push_back({Fd[k], t[k] / tot});
     return tot != 0.0;
   };
+  // m_f > 1 (eq. definition-traces, then an SVD): the traces (M_N^-1 D_N^T q_i)|_F from both aggregates' pressure
+  // modes, each scaled to unit norm and projected by Pi_F = I - sigma^PV t^T / (t . sigma^PV) (t: outflow of a
+  // through F), so that sigma^PV alone carries the net flux; the left singular vectors with value > 1e-8 are kept,
+  // m_f - 1 and |F| - 1 at most, each with its first entry within 1e-6 of the largest magnitude positive; Q_sigma
+  // row of a kept u: Pi_F^T u.
+  auto interface_traces = [&](int J, int a, int bb, const std::vector<int>& U, const std::vector<double>& sig,
+                              Scratch& sc) {
+    const std::vector<int>& Fd = Fdofs[J];
+    const int nf = (int)Fd.size();
+    std::vector<double> t = outflow_coef(a, Fd, sc), sF(nf);
+    double ts = 0.0;
+    for (int k = 0; k < nf; ++k) {
+      sF[k] = sig[std::lower_bound(U.begin(), U.end(), Fd[k]) - U.begin()];
+      ts += t[k] * sF[k];
+    }
+    std::vector<std::vector<double>> tr;
+    for (int side = 0; side < 2; ++side) {
+      const int c = side ? bb : a;
+      const std::vector<int>& ids = xb_ids[c];
+      std::vector<int> rowk(nf);
+      for (int k = 0; k < nf; ++k) {
+        auto it = std::lower_bound(ids.begin(), ids.end(), Fd[k]);
+        if (it == ids.end() || *it != Fd[k]) return false;
+        rowk[k] = (int)(it - ids.begin());
+      }
+      for (int i = 0; i < ma[c]; ++i) {
+        std::vector<double> v(nf, 0.0);
+        double nv = 0.0;
+        for (int k = 0; k < nf; ++k) {
+          double acc = 0.0;
+          for (int q = xb_off[c][rowk[k]]; q < xb_off[c][rowk[k] + 1]; ++q)
+            acc += xb_val[c][q] * PA[c][(size_t)xb_col[c][q] * ma[c] + i];
+          v[k] = acc;
+          nv += acc * acc;
+        }
+        nv = std::sqrt(nv);
+        if (nv > 0.0) {
+          for (auto& x : v) x /= nv;
+          tr.push_back(v);
+        }
+      }
+    }
+    if (tr.empty() || nf < 2) return true;
+    const int m = (int)tr.size();
+    std::vector<double> V((size_t)nf * m), Uu, sv;
+    for (int j = 0; j < m; ++j) {
+      double d = 0.0;
+      for (int k = 0; k < nf; ++k) d += t[k] * tr[j][k];
+      d /= ts;
+      for (int k = 0; k < nf; ++k) V[(size_t)k * m + j] = tr[j][k] - sF[k] * d;
+    }
+    jacobi_svd(nf, m, V, Uu, sv);
+    int keep = 0;
+    for (int j = 0; j < m; ++j)
+      if (sv[j] > kTraceDrop) keep++;
+    keep = std::min(keep, std::min(flux_modes - 1, nf - 1));
+    for (int j = 0; j < keep; ++j) {
+      std::vector<double> u(nf);
+      double umax = 0.0;
+      for (int k = 0; k < nf; ++k) {
+        u[k] = Uu[(size_t)k * m + j];
+        umax = std::max(umax, std::fabs(u[k]));
+      }
+      int imax = 0;   // first entry within 1e-6 of the largest magnitude: mirror-symmetric ties do not pick the sign
+      while (imax + 1 < nf && !(std::fabs(u[imax]) >= (1.0 - 1e-6) * umax)) ++imax;
+      if (u[imax] < 0)
+        for (auto& x : u) x = -x;
+      double su = 0.0;
+      for (int k = 0; k < nf; ++k) su += sF[k] * u[k];
+      std::vector<double> qv(nf);
+      for (int k = 0; k < nf; ++k) qv[k] = u[k] - t[k] * (su / ts);
+      extraU[J].push_back(u);
+      extraQ[J].push_back(qv);
+    }
+    return true;
+  };
   parallel_for(nF, threads, [&](int b, int e, int w) {
     Scratch& sc = scr[w];
     for (int J = b; J < e; ++J) {
@@ -625,6 +867,7 @@ static bool coarsen(const Level& L, int target, int modes, int threads, bool use
       std::vector<double> sig;
       ls.solve_p_rhs(rp, sig);
       if (!finish_trace(J, a, U, sig, Fdofs[J], sc)) fail = true;
+      if (flux_modes > 1 && !interface_traces(J, a, bb, U, sig, sc)) fail = true;
     }
   });
   parallel_for(nB, threads, [&](int b, int e, int w) {
@@ -688,6 +931,83 @@ static bool coarsen(const Level& L, int target, int modes, int threads, bool use
     }
   });
   if (fail) { err = "singular local problem while building the coarse flux space"; return false; }
+  // m_f > 1: extend every kept trace u into both aggregates by the Neumann problem of App. A.2 (flux data
+  // -M_{iF} u, pressure data c q - D_{AF} u with c = q . D_{AF} u), numbered after the bubbles, interface by interface
+  std::vector<int> e_off(nF + 1, 0);
+  for (int F = 0; F < nF; ++F) e_off[F + 1] = e_off[F] + (int)extraU[F].size();
+  const int nE = e_off[nF];
+  if (nE > 0) {
+    std::vector<std::vector<int>> pairs_of(na);
+    for (int F = 0; F < nF; ++F)
+      if (!extraU[F].empty()) {
+        pairs_of[plist[F].first].push_back(F);
+        pairs_of[plist[F].second].push_back(F);
+      }
+    std::vector<std::vector<std::pair<int, double>>> extp((size_t)2 * nE);   // (trace, side) -> interior part
+    parallel_for(na, threads, [&](int b, int e, int w) {
+      Scratch& sc = scr[w];
+      for (int a = b; a < e; ++a) {
+        if (pairs_of[a].empty()) continue;
+        std::vector<int> cA = cells_of(a);
+        std::vector<int> U = internal_flux(L, cA, sc);
+        if (U.empty()) continue;
+        LocalProblem lp;
+        assemble_local(L, cA, U, sc, lp);
+        LocalSolver ls;
+        if (!ls.init(lp, true)) { fail = true; continue; }
+        double qn = 0.0;
+        for (double x : lp.ones) qn += x * x;
+        qn = std::sqrt(qn);
+        for (int F : pairs_of[a]) {
+          const int side = plist[F].first == a ? 0 : 1;
+          const std::vector<int>& Fd = Fdofs[F];
+          const int tok = sc.next();
+          for (size_t k = 0; k < Fd.size(); ++k) {
+            sc.flux_stamp[Fd[k]] = tok;
+            sc.flux_pos[Fd[k]] = (int)k;
+          }
+          for (size_t j = 0; j < extraU[F].size(); ++j) {
+            const std::vector<double>& u = extraU[F][j];
+            std::vector<double> rs(U.size(), 0.0), dfu(lp.np, 0.0), rp(lp.np), sig;
+            for (size_t kc = 0; kc < cA.size(); ++kc) {
+              const int c = cA[kc], nl = L.nloc(c);
+              const int* lc = &L.loc[L.loc_off[c]];
+              const double* Mc = &L.Mloc[L.mat_off[c]];
+              const double* Dc = &L.Dloc[L.dmat_off[c]];
+              for (int tt = 0; tt < nl; ++tt) {
+                if (sc.flux_stamp[lc[tt]] != tok) continue;
+                const double ut = u[sc.flux_pos[lc[tt]]];
+                for (int r = 0; r < L.m[c]; ++r) dfu[lp.prow[kc] + r] += Dc[(size_t)r * nl + tt] * ut;
+                for (int ss = 0; ss < nl; ++ss) {
+                  auto it = std::lower_bound(U.begin(), U.end(), lc[ss]);
+                  if (it != U.end() && *it == lc[ss]) rs[it - U.begin()] -= Mc[(size_t)ss * nl + tt] * ut;
+                }
+              }
+            }
+            double cq = 0.0;
+            for (int r = 0; r < lp.np; ++r) cq += lp.ones[r] / qn * dfu[r];
+            for (int r = 0; r < lp.np; ++r) rp[r] = cq * lp.ones[r] / qn - dfu[r];
+            ls.solve_rhs(rs, rp, sig);
+            auto& dst = extp[(size_t)2 * (e_off[F] + j) + side];
+            for (size_t k = 0; k < U.size(); ++k) dst.push_back({U[k], sig[k]});
+          }
+        }
+      }
+    });
+    if (fail) { err = "singular local problem while extending the interface traces"; return false; }
+    nC = nC0 + nE;
+    psi.resize(nC);
+    qrow.resize(nC);
+    for (int F = 0; F < nF; ++F)
+      for (size_t j = 0; j < extraU[F].size(); ++j) {
+        const int i = e_off[F] + (int)j, J = nC0 + i;
+        const std::vector<int>& Fd = Fdofs[F];
+        psi[J] = extp[(size_t)2 * i];
+        for (size_t k = 0; k < Fd.size(); ++k) psi[J].push_back({Fd[k], extraU[F][j][k]});
+        psi[J].insert(psi[J].end(), extp[(size_t)2 * i + 1].begin(), extp[(size_t)2 * i + 1].end());
+        for (size_t k = 0; k < Fd.size(); ++k) qrow[J].push_back({Fd[k], extraQ[F][j][k]});
+      }
+  }
   // ---- coarse level description ---------------------------------------------------------------------------------
   C.n_flux = nC;
   C.fkind.assign(nC, KIND_BUBBLE);
@@ -697,6 +1017,12 @@ static bool coarsen(const Level& L, int target, int modes, int threads, bool use
   for (int k = 0; k < nB; ++k) { C.fkind[nF + k] = KIND_BDRY; C.fown0[nF + k] = bagg[k]; }
   for (int a = 0; a < na; ++a)
     for (int j = 1; j < ma[a]; ++j) C.fown0[nF + nB + bub_off[a] + j - 1] = a;
+  for (int F = 0; F < nF; ++F)
+    for (int i = e_off[F]; i < e_off[F + 1]; ++i) {
+      C.fkind[nC0 + i] = KIND_IFACE;
+      C.fown0[nC0 + i] = plist[F].first;
+      C.fown1[nC0 + i] = plist[F].second;
+    }
   std::vector<std::vector<int>> locs(na);
   for (int J = 0; J < nC; ++J) {
     locs[C.fown0[J]].push_back(J);
@@ -858,7 +1184,8 @@ bool build_hierarchy(const FineMesh& fm, const Options& opt, Hierarchy& H, std::
   for (int l = 0; l + 1 < opt.n_levels; ++l) {
     Level C;
     Transfer T;
-    if (!coarsen(H.levels.back(), opt.agg_size[l], opt.modes[l], threads, opt.gpu_eig, opt.eig_fn, C, T, err))
+    if (!coarsen(H.levels.back(), opt.agg_size[l], opt.modes[l], opt.flux_modes[l], threads, opt.gpu_eig,
+                 opt.eig_fn, C, T, err))
       return false;
     H.levels.push_back(std::move(C));
     H.transfers.push_back(std::move(T));

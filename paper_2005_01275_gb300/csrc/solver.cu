@@ -1173,6 +1173,7 @@ void nlmg_default_options(nlmg_options* o) {
   for (int l = 0; l < 8; ++l) {
     o->agg_size[l] = l == 0 ? 64 : 8;
     o->modes[l] = 4;
+    o->flux_modes[l] = 1;
   }
   o->smoother = NLMG_SMOOTH_PICARD;
   o->nu_pre = o->nu_post = 2;
@@ -1278,8 +1279,11 @@ static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, co
     for (int l = 0; l < 8; ++l) {
       ho.agg_size[l] = opt->agg_size[l];
       ho.modes[l] = opt->modes[l];
+      ho.flux_modes[l] = opt->flux_modes[l];
       if (l + 1 < opt->n_levels && (opt->agg_size[l] < 2 || opt->modes[l] < 1 || opt->modes[l] > kMaxM))
         throw Error(NLMG_EINVAL, "agg_size >= 2 and 1 <= modes <= 8 per level");
+      if (l + 1 < opt->n_levels && (opt->flux_modes[l] < 1 || opt->flux_modes[l] > 8))
+        throw Error(NLMG_EINVAL, "1 <= flux_modes <= 8 per level");
     }
     ho.threads = opt->setup_threads;
     if (device) {
@@ -1388,8 +1392,9 @@ nlmg_status nlmg_set_options(nlmg_ctx* c, const nlmg_options* opt) {
     if (!opt) throw Error(NLMG_EINVAL, "null options");
     if (opt->n_levels != c->opt.n_levels) throw Error(NLMG_EINVAL, "n_levels is fixed at setup");
     for (int l = 0; l + 1 < c->opt.n_levels; ++l)
-      if (opt->agg_size[l] != c->opt.agg_size[l] || opt->modes[l] != c->opt.modes[l])
-        throw Error(NLMG_EINVAL, "agg_size and modes are fixed at setup");
+      if (opt->agg_size[l] != c->opt.agg_size[l] || opt->modes[l] != c->opt.modes[l] ||
+          opt->flux_modes[l] != c->opt.flux_modes[l])
+        throw Error(NLMG_EINVAL, "agg_size, modes and flux_modes are fixed at setup");
     if (!solver_options_ok(*opt)) throw Error(NLMG_EINVAL, "bad solver option");
     const int threads = c->opt.setup_threads;
     c->opt = *opt;

@@ -49,7 +49,10 @@ def test_setup_rejects_bad_mesh(nlmg_lib):
 CASES = [("cart2d_32", None, {}), ("cart2d_32", 13, dict(agg_size=[9, 4], modes=[3, 2])),
          ("chan3d_64", 8, dict(agg_size=[16, 4, 4], modes=[3, 3, 3])),
          ("chan3d_64", 12, dict(n_levels=3, agg_size=[27, 6, 4], modes=[4, 3, 3])),
-         ("voronoi", 9, {})]
+         ("voronoi", 9, {}),
+         ("cart2d_32", 13, dict(agg_size=[9, 4], modes=[3, 2], flux_modes=[3, 3])),
+         ("chan3d_64", 12, dict(n_levels=3, agg_size=[27, 6, 4], modes=[4, 3, 3], flux_modes=[3, 2, 2])),
+         ("voronoi", 9, dict(flux_modes=[2, 2]))]
 
 
 @pytest.mark.parametrize("name,scale,upd", CASES)

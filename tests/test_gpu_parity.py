@@ -14,6 +14,8 @@ CASES = {
     "chan3d_16": ("chan3d_64", 16, dict(n_levels=3, agg_size=[64, 8, 8], modes=[4, 4, 4])),
     "chan3d_11": ("chan3d_64", 11, dict(n_levels=3, agg_size=[27, 6, 4], modes=[4, 3, 3])),
     "vor3d_10": ("voronoi", 10, {}),     # unstructured: clipped Voronoi cells, 5-21 neighbours, kappa = 1/(1+p^2)
+    # m_f = 3 flux unknowns per coarse interface (App. A.2): up to 51 local flux unknowns per coarse cell
+    "chan3d_16_mf3": ("chan3d_64", 16, dict(n_levels=3, agg_size=[64, 8, 8], modes=[4, 4, 4], flux_modes=[3, 3, 3])),
 }
 TIGHT = dict(lin_tol=1e-13, lin_maxit=20000)
 
@@ -148,6 +150,19 @@ def test_solve_matches_newton_solution(case):
 def test_fas_cycle_counts_follow_oracle(nlmg_lib):
     """At the default tolerances (rel 1e-8) both FAS implementations take the same number of cycles."""
     pr, H, ctx = _setup(nlmg_lib, "chan3d_16", **TIGHT)
+    S = fas.FAS(H, pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, pr.opts)
+    S.solve()
+    p, rep, st = ctx.solve(pr.f_cell, pr.g_face)
+    assert st == 0
+    assert rep["cycles"] == S.stats.cycles and rep["early_exit"] == S.stats.early_exit
+    h = np.array(rep["history"])
+    ho = np.array(S.stats.history)
+    assert np.allclose(h, ho, rtol=1e-6, atol=1e-9 * ho[0])
+
+
+def test_flux_modes_cycle_counts_follow_oracle(nlmg_lib):
+    """m_f = 3: both FAS implementations take the same cycles (fewer than with m_f = 1 on this case: 9 against 13)."""
+    pr, H, ctx = _setup(nlmg_lib, "chan3d_16_mf3", **TIGHT)
     S = fas.FAS(H, pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, pr.opts)
     S.solve()
     p, rep, st = ctx.solve(pr.f_cell, pr.g_face)
