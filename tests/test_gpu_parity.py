@@ -75,6 +75,9 @@ def test_level_operator(case):
 def test_transfers(case, nlmg_lib):
     pr, H, ctx = case
     rng = np.random.default_rng(13)
+    # the library's hierarchy is compared here through the oracle's: with m_f > 1 its interface traces come from an
+    # SVD (App. A.2) taken by two different algorithms, which agree to 1e-9 relative (host hierarchy parity)
+    tol = 1e-9 if max(pr.opts.get("flux_modes", [1])) > 1 else 1e-10
     for l, tr in enumerate(H.transfers):
         levc = H.levels[l + 1]
         if l == 0:
@@ -98,7 +101,7 @@ def test_transfers(case, nlmg_lib):
             ref_e = np.concatenate([tr.Psigma @ e[:levc.n_flux], tr.Pp @ e[levc.n_flux:]])
         got_e = ctx.transfer(l, nlmg_lib.PROLONG, e)
         for g_, r_ in ((got, ref), (got_r, ref_r), (got_e, ref_e)):
-            assert np.abs(g_ - r_).max() <= 1e-10 * max(1.0, np.abs(r_).max())
+            assert np.abs(g_ - r_).max() <= tol * max(1.0, np.abs(r_).max())
 
 
 def test_picard_updates(case):
