@@ -87,7 +87,21 @@ def test_set_options_keeps_the_hierarchy_fixed(nlmg_lib):
     assert ctx.opts.smoother == nlmg_lib.SMOOTH_PICARD_NEWTON and ctx.opts.newton_switch == 1e-3
     for bad in (dict(n_levels=3), dict(modes=(ctypes.c_int32 * 8)(3, 3, 3, 3, 3, 3, 3, 3)), dict(lin_precision=2),
                 dict(omega=0.0), dict(smoother=3), dict(newton_switch=-1.0), dict(newton_switch=float("nan")),
-                dict(newton_lin_tol=0.0)):
+                dict(newton_lin_tol=0.0), dict(flux_modes=(ctypes.c_int32 * 8)(2, 1, 1, 1, 1, 1, 1, 1))):
         with pytest.raises(nlmg_lib.NlmgError):
             ctx.set_options(**bad)
     ctx.close()
+
+
+def test_flux_modes_option_range(nlmg_lib):
+    """m_f is a hierarchy option: 1..8 per coarsening step, checked at setup."""
+    pr = problem_config("cart2d_32", scale=8)
+    for bad in (0, 9):
+        with pytest.raises(nlmg_lib.NlmgError):
+            nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, dict(pr.opts, flux_modes=[bad] * 8), device=False)
+    c1 = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.opts, device=False)
+    c2 = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, dict(pr.opts, flux_modes=[2] * 8), device=False)
+    assert c2.opts.flux_modes[0] == 2 and c1.opts.flux_modes[0] == 1
+    assert c2.level_info(1)["n_flux"] > c1.level_info(1)["n_flux"]
+    c1.close()
+    c2.close()
