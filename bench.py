@@ -434,6 +434,8 @@ def run_gpu(args, rank, world, local_rank):
         pr.opts["lin_tol"] = args.lin_tol
     if args.coarse_lin_tol is not None:
         pr.opts["coarse_lin_tol"] = args.coarse_lin_tol
+    if args.flux_modes != 1:
+        pr.opts["flux_modes"] = [args.flux_modes] * 8
     t0 = time.perf_counter()
     ctx = nlmg.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.opts)
     setup_s = time.perf_counter() - t0
@@ -565,7 +567,7 @@ def run_gpu(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(args.scale, args.smoother), "cells": N, "smoother": args.smoother, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "256 MiB buffer written between steps, outside each step's CUDA-event pair",
-                   "setup_s": round(setup_s, 3), "lin_tol": ctx.opts.lin_tol,
+                   "setup_s": round(setup_s, 3), "lin_tol": ctx.opts.lin_tol, "flux_modes": args.flux_modes,
                    "coarse_lin_tol": ctx.opts.coarse_lin_tol},
         "vcycle_dof_per_s": N * cycles * world / (ms_step / 1e3),
         "cycles_per_solve": cycles,
@@ -613,6 +615,8 @@ def main():
                     help="skip the single-level Picard and Newton solves")
     ap.add_argument("--no-compare-picard", dest="compare_picard", action="store_false",
                     help="skip the timed loop with Picard steps throughout")
+    ap.add_argument("--flux-modes", type=int, default=1,
+                    help="m_f, flux unknowns per coarse interface at most, on every coarsening step (default 1)")
     ap.add_argument("--voronoi", type=int, default=0,
                     help="lattice side of the unstructured Voronoi section (100 = 1M cells; 0 = skip)")
     args = ap.parse_args()
