@@ -104,7 +104,14 @@ typedef struct {
                                 aggregates' pressure modes are projected off the net flux, and the leading left
                                 singular vectors (value > 1e-8 on unit-norm traces) are added beside sigma^PV, each
                                 extended into both aggregates (App. A.2). A hierarchy option, fixed at setup */
-  int32_t reserved[5];
+  int32_t cascadic;          /* 1: nlmg_solve starts its FAS cycles from the nonlinear cascadic iterate (Sec. 4.2):
+                                the coarse problems of Algorithm 2 are formed top-down at the initial iterate without
+                                smoothing; then, from the coarsest level up, each is solved by up to coarsest_steps
+                                Picard steps (stopping like the coarsest solve) from the point its finer level
+                                projected, and its correction is carried to the finer level with Algorithm 1; the
+                                level-0 correction too. The report's history then holds the residual after it as its
+                                second entry (not counted as a cycle). 0 (default): plain FAS cycles */
+  int32_t reserved[4];
 } nlmg_options;
 
 typedef struct {

@@ -998,6 +998,39 @@ bool vcycle(nlmg_ctx* c, double r0, double tol_rel, double tol_abs) {
   return false;
 }
 
+// Nonlinear cascadic start (Sec. 4.2): the FAS coarse problems of Algorithm 2 formed top-down at the current
+// level-0 iterate with no smoothing, then solved from the coarsest level up, each by up to coarsest_steps Picard
+// steps that stop like the coarsest solve, from the point its finer level projected; each level's correction
+// y - Qx is carried to the finer level with Algorithm 1, the level-0 one too. Leaves cur (p, R, ||R||).
+void cascade(nlmg_ctx* c) {
+  const int nl = c->nlev();
+  if (nl < 2) return;
+  const nlmg_options& o = c->opt;
+  make_coarse_problem(c, 0);
+  for (int l = 1; l + 1 < nl; ++l) {
+    CoarseBuf& B = c->CB[l];
+    B.rn = coarse_res(c, l, B.x, B.b, B.r);   // r = A(x) - b at the projected x, restricted below
+    make_coarse_problem(c, l);
+  }
+  coarse_step(c, nl - 1, false, o.coarsest_steps, true);
+  for (int l = nl - 2; l >= 1; --l) {
+    const LevelDev& L = c->LD[l];
+    const LevelDev& C = c->LD[l + 1];
+    CoarseBuf& B = c->CB[l];
+    CoarseBuf& Bc = c->CB[l + 1];
+    const TransferDev& T = c->TD[l];
+    launch_sub(c->st, C.nflux + C.np, Bc.x, Bc.xc, Bc.ptmp);
+    launch_csr(c->st, T.ps_n, T.ps_off, T.ps_col, T.ps_val, Bc.ptmp, B.dx, 1.0, 0.0);
+    launch_prolong_p(c->st, T, Bc.ptmp + C.nflux, B.dx + L.nflux);
+    coarse_step(c, l, true, o.coarsest_steps, true);   // Algorithm 1 along the correction, then the level solve
+  }
+  const LevelDev& C = c->LD[1];
+  CoarseBuf& Bc = c->CB[1];
+  launch_sub(c->st, C.nflux + C.np, Bc.x, Bc.xc, Bc.ptmp);
+  launch_prolong_p(c->st, c->TD[0], Bc.ptmp + C.nflux, c->fdp);
+  backtrack0(c, c->fdp, 1.0);
+}
+
 void alloc_fine(nlmg_ctx* c) {
   const int N = c->F.N;
   c->f = c->dalloc<double>(N);
@@ -1095,6 +1128,10 @@ nlmg_status solve_core(nlmg_ctx* c, const double* x0_dev, double tol_rel, double
   nlmg_status st = NLMG_OK;
   const int saved_smoother = c->opt.smoother;
   if (picard_only) c->opt.smoother = NLMG_SMOOTH_PICARD;
+  if (mode == 0 && c->opt.cascadic && c->nlev() > 1 && !(r0 <= tol_abs) && std::isfinite(r0)) {
+    cascade(c);
+    R.history[R.history_len++] = c->cur.rn;
+  }
   double best = r0;
   while (true) {
     double rn = c->cur.rn;
@@ -1199,7 +1236,8 @@ static thread_local std::string g_setup_error;   // message of the calling threa
 static bool solver_options_ok(const nlmg_options& o) {
   return o.nu_pre >= 0 && o.nu_post >= 0 && o.bt_nmax >= 0 && o.omega > 0 && o.coarsest_steps >= 0 &&
          (o.lin_precision == 0 || o.lin_precision == 1) && o.max_sms >= 0 && o.smoother >= NLMG_SMOOTH_PICARD &&
-         o.smoother <= NLMG_SMOOTH_PICARD_NEWTON && o.newton_switch >= 0.0 && o.newton_lin_tol > 0.0;
+         o.smoother <= NLMG_SMOOTH_PICARD_NEWTON && o.newton_switch >= 0.0 && o.newton_lin_tol > 0.0 &&
+         (o.cascadic == 0 || o.cascadic == 1);
 }
 
 static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlmg_options* opt,

@@ -176,6 +176,21 @@ def test_flux_modes_cycle_counts_follow_oracle(nlmg_lib):
     assert np.allclose(h, ho, rtol=1e-6, atol=1e-9 * ho[0])
 
 
+@pytest.mark.parametrize("key", ["cart2d_13", "chan3d_11"])
+def test_cascadic_start_matches_oracle(nlmg_lib, key):
+    """Nonlinear cascadic start (Sec. 4.2) then FAS cycles: the same iterate after the cascade (second history entry)
+    and the same cycles as the oracle's FAS.cascade."""
+    pr, H, ctx = _setup(nlmg_lib, key, cascadic=1, **TIGHT)
+    S = fas.FAS(H, pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, pr.opts)
+    S.solve(cascadic=True)
+    p, rep, st = ctx.solve(pr.f_cell, pr.g_face)
+    assert st == 0
+    h = np.array(rep["history"])
+    ho = np.array(S.stats.history)
+    assert h.size == ho.size and rep["cycles"] == S.stats.cycles
+    assert np.allclose(h, ho, rtol=1e-6, atol=1e-9 * ho[0])
+
+
 def test_jacobi_smoother_cycle_matches_oracle(nlmg_lib):
     pr, H, ctx = _setup(nlmg_lib, "cart2d_32", smoother="jacobi", **TIGHT)
     S = fas.FAS(H, pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, pr.opts)
