@@ -8,7 +8,7 @@ namespace nlmg {
 
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 4096;
-constexpr int kMaxLoc = 64;      // max local flux unknowns of a coarse cell
+constexpr int kMaxLoc = 128;     // max local flux unknowns of a coarse cell
 constexpr int kMaxM = 8;         // max pressure unknowns of a coarse cell
 
 // device scalar slots

@@ -309,7 +309,7 @@ void upload_level(nlmg_ctx* c, int l) {
   D.np = L.n_p();
   D.nyl = (int)L.loc.size();
   for (int cc = 0; cc < L.n_cells; ++cc) {
-    if (L.nloc(cc) > kMaxLoc) throw Error(NLMG_EUNSUPPORTED, "a coarse cell has more than 64 flux unknowns");
+    if (L.nloc(cc) > kMaxLoc) throw Error(NLMG_EUNSUPPORTED, "a coarse cell has more than 128 flux unknowns");
     if (L.m[cc] > kMaxM) throw Error(NLMG_EUNSUPPORTED, "more than 8 modes per aggregate");
   }
   D.m = c->upload(L.m);

@@ -176,6 +176,23 @@ def test_flux_modes_cycle_counts_follow_oracle(nlmg_lib):
     assert np.allclose(h, ho, rtol=1e-6, atol=1e-9 * ho[0])
 
 
+def test_more_than_64_local_flux_unknowns(nlmg_lib):
+    """m_f = 4 on 64-cell aggregates gives coarse cells with up to 66 local flux unknowns: the GPU solve follows the
+    oracle's cycles and residual history."""
+    pr = problem_config("chan3d_64", scale=16)
+    opts = dict(pr.opts, n_levels=3, agg_size=[64, 8, 8], modes=[4, 4, 4], flux_modes=[4, 4, 4], **TIGHT)
+    H = hierarchy.build(pr.mesh, opts)
+    assert max(len(x) for x in H.levels[1].loc) > 64
+    ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, opts)
+    S = fas.FAS(H, pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, opts)
+    po = S.solve()
+    p, rep, st = ctx.solve(pr.f_cell, pr.g_face)
+    assert st == 0 and rep["cycles"] == S.stats.cycles
+    ho = np.array(S.stats.history)
+    assert np.allclose(np.array(rep["history"]), ho, rtol=1e-6, atol=1e-9 * ho[0])
+    assert _rel(p, po) <= 1e-6
+
+
 @pytest.mark.parametrize("key", ["cart2d_13", "chan3d_11"])
 def test_cascadic_start_matches_oracle(nlmg_lib, key):
     """Nonlinear cascadic start (Sec. 4.2) then FAS cycles: the same iterate after the cascade (second history entry)
