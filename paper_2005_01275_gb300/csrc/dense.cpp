@@ -355,30 +355,72 @@ void chol_solve(int n, const double* L, double* b) {
   }
 }
 
-// L L^T X = B for nr right-hand sides stored row-major (n x nr), in place; same operation order per column as
-// chol_solve, with contiguous inner loops over the right-hand sides.
+// L L^T X = B for nr right-hand sides stored row-major (n x nr), in place; same operation order per entry as
+// chol_solve (subtractions in k order, then the division). The right-hand sides are taken eight at a time with their
+// running values in registers, so that a block of X stays in L1 and no entry is stored before it is final; the back
+// substitution reads L^T by rows.
 void chol_solve_multi(int n, const double* L, int nr, double* X) {
-  for (int i = 0; i < n; ++i) {
-    double* Xi = X + (size_t)i * nr;
-    for (int k = 0; k < i; ++k) {
-      const double l = L[(size_t)i * n + k];
-      if (l == 0.0) continue;
-      const double* Xk = X + (size_t)k * nr;
-      for (int r = 0; r < nr; ++r) Xi[r] -= l * Xk[r];
+  constexpr int W = 8;
+  std::vector<double> Lt((size_t)n * n, 0.0);
+  for (int k = 0; k < n; ++k)
+    for (int i = 0; i < k; ++i) Lt[(size_t)i * n + k] = L[(size_t)k * n + i];
+  for (int r0 = 0; r0 < nr; r0 += W) {
+    const int w = std::min(W, nr - r0);
+    if (w == W) {
+      for (int i = 0; i < n; ++i) {
+        double* Xi = X + (size_t)i * nr + r0;
+        double a[W];
+        for (int u = 0; u < W; ++u) a[u] = Xi[u];
+        const double* Li = L + (size_t)i * n;
+        for (int k = 0; k < i; ++k) {
+          const double l = Li[k];
+          if (l == 0.0) continue;
+          const double* Xk = X + (size_t)k * nr + r0;
+          for (int u = 0; u < W; ++u) a[u] -= l * Xk[u];
+        }
+        const double d = Li[i];
+        for (int u = 0; u < W; ++u) Xi[u] = a[u] / d;
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        double* Xi = X + (size_t)i * nr + r0;
+        double a[W];
+        for (int u = 0; u < W; ++u) a[u] = Xi[u];
+        const double* Ui = Lt.data() + (size_t)i * n;
+        for (int k = i + 1; k < n; ++k) {
+          const double l = Ui[k];
+          if (l == 0.0) continue;
+          const double* Xk = X + (size_t)k * nr + r0;
+          for (int u = 0; u < W; ++u) a[u] -= l * Xk[u];
+        }
+        const double d = L[(size_t)i * n + i];
+        for (int u = 0; u < W; ++u) Xi[u] = a[u] / d;
+      }
+    } else {
+      for (int i = 0; i < n; ++i) {
+        double* Xi = X + (size_t)i * nr + r0;
+        const double* Li = L + (size_t)i * n;
+        for (int k = 0; k < i; ++k) {
+          const double l = Li[k];
+          if (l == 0.0) continue;
+          const double* Xk = X + (size_t)k * nr + r0;
+          for (int u = 0; u < w; ++u) Xi[u] -= l * Xk[u];
+        }
+        const double d = Li[i];
+        for (int u = 0; u < w; ++u) Xi[u] /= d;
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        double* Xi = X + (size_t)i * nr + r0;
+        const double* Ui = Lt.data() + (size_t)i * n;
+        for (int k = i + 1; k < n; ++k) {
+          const double l = Ui[k];
+          if (l == 0.0) continue;
+          const double* Xk = X + (size_t)k * nr + r0;
+          for (int u = 0; u < w; ++u) Xi[u] -= l * Xk[u];
+        }
+        const double d = L[(size_t)i * n + i];
+        for (int u = 0; u < w; ++u) Xi[u] /= d;
+      }
     }
-    const double d = L[(size_t)i * n + i];
-    for (int r = 0; r < nr; ++r) Xi[r] /= d;
-  }
-  for (int i = n - 1; i >= 0; --i) {
-    double* Xi = X + (size_t)i * nr;
-    for (int k = i + 1; k < n; ++k) {
-      const double l = L[(size_t)k * n + i];
-      if (l == 0.0) continue;
-      const double* Xk = X + (size_t)k * nr;
-      for (int r = 0; r < nr; ++r) Xi[r] -= l * Xk[r];
-    }
-    const double d = L[(size_t)i * n + i];
-    for (int r = 0; r < nr; ++r) Xi[r] /= d;
   }
 }
 
