@@ -436,6 +436,8 @@ def run_gpu(args, rank, world, local_rank):
         pr.opts["coarse_lin_tol"] = args.coarse_lin_tol
     if args.flux_modes != 1:
         pr.opts["flux_modes"] = [args.flux_modes] * 8
+    if args.cascadic:
+        pr.opts["cascadic"] = 1
     t0 = time.perf_counter()
     ctx = nlmg.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.opts)
     setup_s = time.perf_counter() - t0
@@ -567,7 +569,7 @@ def run_gpu(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(args.scale, args.smoother), "cells": N, "smoother": args.smoother, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "256 MiB buffer written between steps, outside each step's CUDA-event pair",
-                   "setup_s": round(setup_s, 3), "lin_tol": ctx.opts.lin_tol, "flux_modes": args.flux_modes,
+                   "setup_s": round(setup_s, 3), "lin_tol": ctx.opts.lin_tol, "flux_modes": args.flux_modes, "cascadic": int(args.cascadic),
                    "coarse_lin_tol": ctx.opts.coarse_lin_tol},
         "vcycle_dof_per_s": N * cycles * world / (ms_step / 1e3),
         "cycles_per_solve": cycles,
@@ -617,6 +619,8 @@ def main():
                     help="skip the timed loop with Picard steps throughout")
     ap.add_argument("--flux-modes", type=int, default=1,
                     help="m_f, flux unknowns per coarse interface at most, on every coarsening step (default 1)")
+    ap.add_argument("--cascadic", action="store_true",
+                    help="start every solve from the nonlinear cascadic iterate (Sec. 4.2)")
     ap.add_argument("--voronoi", type=int, default=0,
                     help="lattice side of the unstructured Voronoi section (100 = 1M cells; 0 = skip)")
     args = ap.parse_args()
