@@ -240,7 +240,8 @@ class FAS:
     def cascade(self, p):
         """Nonlinear cascadic start (Sec. 4.2, Example 2): the FAS coarse problems of Algorithm 2 are formed top-down
         at the current iterate; then, from the coarsest level up, each is solved nonlinearly by Picard smoothing steps
-        (at most `coarsest_steps`, stopping at the relative tolerance of the solve) from the point its finer level
+        (at most `coarsest_steps`, stopping like the coarsest solve of a cycle: `coarsest_tol`, else the relative
+        tolerance of the solve) from the point its finer level
         projected, and its correction is carried to the finer level with Algorithm 1. Returns the new level-0
         iterate."""
         o, H = self.o, self.H
@@ -264,11 +265,13 @@ class FAS:
         for l in range(1, L):
             x0s[l] = xs[l].copy()
 
+        rel = o.get("coarsest_tol", 0.0) or o["tol_rel"]   # each level stops like the coarsest solve of a cycle
+
         def solve_level(l, x, b):
             r = float(np.linalg.norm(self.res(l, x, b)))
             r_in = r
             for _ in range(o["coarsest_steps"]):
-                if r <= o["tol_rel"] * r_in or r <= o["tol_abs"]:
+                if r <= rel * r_in or r <= o["tol_abs"]:
                     break
                 x, r = self.picard_smooth(l, x, b, r)
             return x
