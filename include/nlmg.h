@@ -140,7 +140,8 @@ void nlmg_default_options(nlmg_options* opt);
 
 /* Builds the hierarchy (host C++: aggregation, spectral bases, coarse flux space, static local matrices;
  * App. A-C) and uploads it and the mesh to the current CUDA device. *out receives a new context, to be released
- * with nlmg_destroy. Errors: NLMG_EINVAL (bad mesh/options), NLMG_ENOMEM, NLMG_ECUDA. */
+ * with nlmg_destroy. Errors: NLMG_EINVAL (bad mesh/options), NLMG_ENOMEM, NLMG_ECUDA, NLMG_EUNSUPPORTED (a coarse
+ * cell with more than 128 local flux unknowns or more than 8 pressure modes). */
 nlmg_status nlmg_setup(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlmg_options* opt, nlmg_ctx** out);
 
 /* Host-only variant of nlmg_setup: builds the same hierarchy without touching any CUDA device. The context then
