@@ -200,3 +200,32 @@ def test_failed_newton_step_returns_to_picard():
     assert np.linalg.norm(p - pstar) <= 1e-10 * np.linalg.norm(pstar)
     S.solve()                       # a new solve clears the latch
     assert S.stats.newton_steps == 2
+
+
+def test_cascade_on_a_linear_problem_is_a_galerkin_coarse_correction():
+    """kappa = 1 (linear): with two levels the cascade solves the coarse FAS problem exactly (its Picard steps are
+    exact linear solves), so it moves p by s P_p e_p, e = (P^T A P)^-1 [0; P_p^T R(p)], with A the mixed matrix of
+    eq. FV_matrix and s the step Algorithm 1 takes. Built here from tpfa's matrices and residual, not the oracle's
+    coarse operators: a wrong sign or a transposed transfer in the cascade's right-hand side moves p elsewhere."""
+    import scipy.sparse as sp
+    from oracle import tpfa
+    pr = problem_config("cart2d_32", scale=13)
+    opts = dict(pr.opts, n_levels=2, agg_size=[9, 4], modes=[3, 2], dp_clamp=0.0)
+    H = hierarchy.build(pr.mesh, opts)
+    kind, a = tpfa.KAPPA_EXP, 0.0
+    assert np.all(tpfa.kappa(np.linspace(-3, 3, 7), kind, a) == 1.0)
+    S = fas.FAS(H, pr.mesh, kind, a, pr.f_cell, pr.g_face, opts)
+    p0 = np.random.default_rng(5).uniform(0.0, 1.0, pr.mesh.n_cells)
+    p1 = S.cascade(p0.copy())
+    M, D, _, _, _ = tpfa.mixed_matrices(pr.mesh, kind, a, p0, pr.f_cell, pr.g_face)
+    A0 = sp.bmat([[M, D.T], [D, None]]).tocsr()
+    tr = H.transfers[0]
+    P = sp.block_diag([tr.Psigma, tr.Pp]).tocsr()
+    A1 = (P.T @ A0 @ P).toarray()
+    R = tpfa.reduced_residual(pr.mesh, kind, a, p0, pr.f_cell, pr.g_face)
+    nf1 = H.levels[1].n_flux
+    e = np.linalg.solve(A1, np.concatenate([np.zeros(nf1), tr.Pp.T @ R]))
+    dp = tr.Pp @ e[nf1:]
+    assert np.linalg.norm(dp) > 0
+    err = min(np.linalg.norm(p1 - (p0 + s * dp)) for s in (1.0, 0.5, 0.25, 0.125, 0.0625))
+    assert err <= 1e-9 * np.linalg.norm(dp)
