@@ -11,8 +11,11 @@ Modules:
   aggregation- deterministic greedy graph aggregation (stands in for METIS, Sec. 3.1 / App. A.1)
   hierarchy  - spectral pressure bases, coarse flux space, Q, D, static local M, Pi~ weights (App. A, B)
   coarse     - level operators A^l(x) (eq. structure, Prop. 1) and the Picard step (eq. picardian_system)
-  fas        - Algorithm 1 (backtracking), the fine nonlinear Jacobi smoother, Algorithm 2 (FAS V-cycle)
-  baselines  - single-level Picard and Newton (Sec. 2.2)
+  fas        - Algorithm 1 (backtracking), the level-0 smoothers (Picard, Picard-then-Newton, nonlinear Jacobi),
+               Algorithm 2 (FAS V-cycle) and the nonlinear cascadic start (Sec. 4.2)
+The single-level Picard and Newton iterations of Sec. 2.2 have no module of their own: newton.solve is that
+iteration (Picard steps, then Newton steps, each solved exactly) run to its limit p*, the value the library's
+single-level baselines are compared with.
 
 Every function whose result is not pinned by a test to something other than itself says "parity unpinned".
 """
