@@ -310,19 +310,22 @@ nlmg_status nlmg_profile_read(nlmg_ctx* ctx, int32_t kernel, int64_t* launches, 
 
 /* ---- allocation-free call ------------------------------------------------------------------------------- */
 /* R(p) into r_dev[n_cells] and ||R(p)||_2^2 into *norm2_dev, for callers that cannot allocate device memory when
- * they call: code running under a fixed device-memory budget or a caching allocator they do not control, or code
- * issuing work between a stream-capture begin and end (a captured cudaMalloc is an error there). It allocates
- * nothing: the per-cell kappa values and the reduction partial sums live in one fixed device array of this library
- * (about 8.1 MiB, held on every device that loads the library until the process exits), and p_dev, r_dev,
- * norm2_dev are caller-owned device pointers. It computes exactly what nlmg_fine_residual computes, with the same
- * kernels, on the context's mesh and the data of the last nlmg_set_data (which must have completed).
- * The paper has no counterpart: this is a library-interface addition.
+ * they call: an application whose caching allocator already holds the device memory it may use (a cudaMalloc
+ * there fails or forces the pool to give memory back), code under a fixed device-memory budget, and loops that must
+ * not stall other streams (cudaFree, and often cudaMalloc, synchronize the device). It allocates nothing: the
+ * per-cell kappa values and the reduction partial sums live in one fixed device array of this library (about
+ * 8.1 MiB, held on every device that loads the library until the process exits), and p_dev, r_dev, norm2_dev are
+ * caller-owned device pointers. It computes exactly what nlmg_fine_residual computes, with the same kernels, on the
+ * context's mesh and the context's current problem data: those of the last nlmg_set_data, or of the last solve
+ * call that took data (nlmg_solve, nlmg_solve_device, nlmg_solve_picard, nlmg_solve_newton), which must have
+ * completed. The paper has no counterpart: this is a library-interface addition.
  *   - stream: a cudaStream_t given as void* (NULL = legacy default stream); the work is only enqueued there.
  *   - meshes of more than 1,048,576 cells are rejected with NLMG_EINVAL.
- *   - the first call on a device resolves the array's device address and clears it (a synchronous memset), so make
- *     that first call before any stream capture.
- *   - every call reuses the same array, which keeps the last call's contents; calls that overlap on the GPU (on
- *     different streams, or from different contexts on the same device) race on it and must be serialized. */
+ *   - the first call on a device resolves the array's device address (cudaGetSymbolAddress, checked), so make that
+ *     first call before any stream capture.
+ *   - every call reuses the same array, which keeps the last call's contents (the reduction's arrival counter is
+ *     zeroed on the given stream by every call); calls that overlap on the GPU (on different streams, or from
+ *     different contexts on the same device) race on it and must be serialized. */
 nlmg_status nlmg_fine_residual_noalloc(nlmg_ctx* ctx, const double* p_dev, double* r_dev, double* norm2_dev,
                                        void* stream);
 

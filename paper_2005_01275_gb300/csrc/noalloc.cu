@@ -31,7 +31,9 @@ NoallocScratch* g_addr[kMaxDevices] = {nullptr};
 
 }  // namespace
 
-// Device address of the scratch array on the current device; resolved (and the array cleared) once per device.
+// Device address of the scratch array on the current device, resolved once per device. Nothing in the array needs
+// clearing here: kappa and the partial sums are written before they are read, and the arrival counter is zeroed on
+// the caller's stream before every launch (and left at zero by the reduction's last block).
 bool noalloc_scratch_address(void** out, std::string& err) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -45,16 +47,6 @@ bool noalloc_scratch_address(void** out, std::string& err) {
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
       err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-      return false;
-    }
-    e = cudaMemset(p, 0, sizeof(NoallocScratch));
-    if (e != cudaSuccess) {
-      err = std::string("cudaMemset: ") + cudaGetErrorString(e);
-      return false;
-    }
-    e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) {
-      err = std::string("cudaDeviceSynchronize: ") + cudaGetErrorString(e);
       return false;
     }
     g_addr[dev] = (NoallocScratch*)p;

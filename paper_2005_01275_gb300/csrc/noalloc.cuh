@@ -11,8 +11,9 @@ namespace nlmg {
 // Largest fine mesh nlmg_fine_residual_noalloc accepts: its per-cell scratch is a fixed device array.
 constexpr int kNoallocMaxCells = 1 << 20;
 
-// Resolves (once per device, with that device current) the device address of the file-scope scratch array and
-// clears it. Not capturable: call it, or the entry point's first call on a device, before any stream capture.
+// Resolves (once per device, with that device current) the device address of the file-scope scratch array with
+// cudaGetSymbolAddress. The entry point's first call on a device does this, so that first call belongs before any
+// stream capture.
 bool noalloc_scratch_address(void** out, std::string& err);
 
 // Enqueues kappa + residual + ||R||^2 on stream st using the scratch array; allocates nothing.

@@ -315,6 +315,9 @@ nlmg_status nlmg_server_poll(nlmg_server* s, uint64_t ticket, int32_t wait_ms, d
       if (wait_ms <= 0) return NLMG_ETIMEOUT;
       if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return r->done; }))
         return NLMG_ETIMEOUT;
+      // the wait released the lock: another poll of the same ticket may have released it meanwhile
+      it = s->all.find(ticket);
+      if (it == s->all.end() || it->second != r) return NLMG_EINVAL;
     }
     s->all.erase(it);
   }

@@ -1,5 +1,6 @@
-"""The allocation-free residual entry point, for callers that cannot allocate device memory when they call (a fixed
-device-memory budget, or work issued inside a stream capture). It must return what nlmg_fine_residual returns.
+"""The allocation-free residual entry point, for callers that cannot allocate device memory when they call (their
+caching allocator already holds the memory they may use, a fixed device-memory budget, or loops that must not stall
+other streams with cudaMalloc/cudaFree). It must return what nlmg_fine_residual returns.
 
 This file is collected last on purpose: a failure here leaves every other test already run.
 """
