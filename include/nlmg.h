@@ -235,7 +235,11 @@ enum { NLMG_PROJECT = 0, NLMG_RESTRICT = 1, NLMG_PROLONG = 2 };
 nlmg_status nlmg_transfer(nlmg_ctx* ctx, int32_t level, int32_t op, const double* in, double* out);
 
 /* The Picard update on level l: dx solving the frozen-coefficient system of eq. picardian_system,
- * A_frozen(x) dx = b - A(x) (level 0: A(kappa(p)) dp = -R(p), b ignored), by PCG to lin_tol. */
+ * A_frozen(x) dx = b - A(x) (level 0: A(kappa(p)) dp = -R(p), b ignored), with the kernels the solves run: level 0 by
+ * the persistent Jacobi-preconditioned CG to lin_tol (the variant follows from lin_tol, lin_precision and max_sms as
+ * in a solve); level l >= 1 by one launch of the fused coarse step, whose hybridized CG (Sec. 3.4) runs to
+ * coarse_lin_tol (coarsest_lin_tol on the coarsest level). Every Krylov solve stops after at most lin_maxit
+ * iterations; *iters (may be NULL) receives the iterations taken. */
 nlmg_status nlmg_picard_update(nlmg_ctx* ctx, int32_t level, const double* x, const double* b, double* dx_out,
                                int32_t* iters);
 
@@ -281,6 +285,10 @@ typedef struct {
   int32_t hierarchy_reused;                          /* 1 if the request ran on a kept hierarchy */
 } nlmg_request_times;
 void nlmg_server_default_options(nlmg_server_options* opt);
+/* The device memory the request loop reserves for a request on this mesh before admitting it (the estimate its
+ * admission compares with mem_budget_bytes): a fixed 1 MiB plus 900 bytes per cell and 120 per face. It is meant to
+ * cover the shared and own device bytes a context holds after a solve (nlmg_device_bytes). Errors: NLMG_EINVAL. */
+nlmg_status nlmg_server_request_bytes(const nlmg_mesh* mesh, size_t* bytes);
 /* Uses the calling thread's current CUDA device. */
 nlmg_status nlmg_server_create(const nlmg_server_options* opt, nlmg_server** out);
 /* Returns NLMG_ENOMEM if the request alone exceeds the memory budget. *ticket identifies the request. */
@@ -297,7 +305,7 @@ void nlmg_server_destroy(nlmg_server* srv);
 /* ---- measurement ----------------------------------------------------------------------------------------- */
 /* Enables (1) or disables (0) CUDA-event timing of the hot kernels on the context stream and clears the counters.
  * Kernel ids: 0 = persistent fine CG solve (kp_fine_cg*), 1 = persistent coarse Picard step (kp_coarse_step:
- * coarse operator evaluations, hybridized CG, clamp and Algorithm 1 in one launch; kp_hyb_solve for the step calls)
+ * coarse operator evaluations, hybridized CG, clamp and Algorithm 1 in one launch; also for nlmg_picard_update)
  * on the levels between the finest and the coarsest, 2 = fine TPFA residual (k_residual), 3 = persistent fine
  * BiCGStab of the Newton smoothing steps (kp_fine_bicgstab), 4 = kp_coarse_step on the coarsest level (the whole
  * coarsest solve in one launch). */
@@ -328,6 +336,22 @@ nlmg_status nlmg_profile_read(nlmg_ctx* ctx, int32_t kernel, int64_t* launches, 
  *     different contexts on the same device) race on it and must be serialized. */
 nlmg_status nlmg_fine_residual_noalloc(nlmg_ctx* ctx, const double* p_dev, double* r_dev, double* norm2_dev,
                                        void* stream);
+
+/* Device memory held by ctx: *shared_bytes by the hierarchy and mesh copies it shares with its instances,
+ * *own_bytes by its own work buffers (the level-0 Newton and GMRES buffers are allocated by the first call that needs
+ * them). Either pointer may be NULL. Not a step of the paper's method. */
+nlmg_status nlmg_device_bytes(const nlmg_ctx* ctx, size_t* shared_bytes, size_t* own_bytes);
+
+/* Failure detection, without a GPU fault (not a step of the paper's method). Every grid-wide wait of the persistent
+ * kernels is bounded: a block that has polled the barrier spin_limit times (about 2 s in the solver kernels) records
+ * an error and every block leaves, so a solve returns NLMG_ETIMEOUT instead of hanging. This call runs that barrier
+ * alone on the context's stream, in a cooperative launch of min(blocks, co-resident) blocks of which block
+ * absent_block (< 0: none) leaves without arriving, with the given spin limit (1024 .. 2^26 polls of ~32 ns sleeps).
+ * Returns NLMG_ETIMEOUT when a wait gave up (the expected outcome with an absent block), NLMG_OK when every block
+ * passed; *passed (may be NULL) receives the number of blocks whose wait completed. The context stays usable.
+ * Errors: NLMG_EINVAL (bad arguments, host-only context), NLMG_ECUDA. */
+nlmg_status nlmg_check_grid_barrier(nlmg_ctx* ctx, int32_t blocks, int32_t absent_block, int64_t spin_limit,
+                                    int32_t* passed);
 
 /* FP64 fused multiply-add throughput of the current device in GFLOP/s (an FMA counts 2), measured with a synthetic
  * kernel of independent FMA chains; the denominator of the FP64-arithmetic roofline. */

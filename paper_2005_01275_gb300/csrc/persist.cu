@@ -53,7 +53,7 @@ struct Grid {
 // to 0 (barriers follow one another without a reset). Thread 0 arrives with an acquire-release atomic after
 // __syncthreads (its release covers the block's earlier writes) and polls the counter with acquire loads until the
 // top bit differs from the value it added to. Returns false (and sets *err) if the wait gave up after ~2 s.
-__device__ __forceinline__ bool grid_barrier(Grid& g) {
+__device__ __forceinline__ bool grid_barrier(Grid& g, unsigned long long spin_limit = kSpinLimit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -63,7 +63,7 @@ __device__ __forceinline__ bool grid_barrier(Grid& g) {
     unsigned long long spins = 0;
     while (((ld_acquire_gpu(g.gs.count) ^ old) & 0x80000000u) == 0u) {
       __nanosleep(32);
-      if ((++spins & 1023u) == 0 && (spins > kSpinLimit || *((volatile int*)g.gs.err) != 0)) {
+      if ((++spins & 1023u) == 0 && (spins > spin_limit || *((volatile int*)g.gs.err) != 0)) {
         atomicExch(g.gs.err, 1);
         ok = 0;
         break;
@@ -1101,26 +1101,6 @@ __device__ bool hyb_solve_dev(const LevelDev& L, const T* __restrict__ Hc, const
   return true;
 }
 
-template <class T>
-__global__ void __launch_bounds__(kPThreads) kp_hyb_solve(LevelDev L, const T* __restrict__ Hc,
-                                                         const T* __restrict__ Sinv, const double* kapc,
-                                                         const double* bs, const double* bp, T* ylam, T* ydiag,
-                                                         T* lam, T* lr, T* lz, T* pa, T* pb, T* lq, T* ldinv,
-                                                         double* dsig, double* dp, double* partial, GridSync gs,
-                                                         double tol, int maxit, int gsz, PcgResult* res) {
-  __shared__ double sm[kSmDoubles];
-  Grid g{gs, partial, sm, 0u};
-  int it = 0;
-  double rr0 = 0.0, rr = 0.0;
-  if (!hyb_solve_dev<T>(L, Hc, Sinv, kapc, bs, bp, ylam, ydiag, lam, lr, lz, pa, pb, lq, ldinv, dsig, dp, g, tol,
-                        maxit, gsz, it, rr0, rr))
-    return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    res->iters = it;
-    res->rr0 = rr0;
-    res->rr = rr;
-  }
-}
 
 // ---- fused coarse Picard step -------------------------------------------------------------------------------
 // The coarse operator (Prop. 1, eq. structure) is linear in [sigma; p] once kappa is fixed: with kappa_c =
@@ -1460,29 +1440,6 @@ template cudaError_t launch_fine_cg<float>(cudaStream_t, const FineDev&, const f
                                            double, double*, float*, float*, float*, float*, float*, double*,
                                            GridSync, double, int, PcgResult*);
 
-template <class T>
-cudaError_t launch_hyb_solve(cudaStream_t st, const LevelDev& L, const T* Hc, const T* Sinv, const double* kapc,
-                             const double* bs, const double* bp, T* ylam, T* ydiag, T* lam, T* lr, T* lz, T* pa,
-                             T* pb, T* lq, T* ldinv, double* dsig, double* dp, double* partial, GridSync gs,
-                             double tol, int maxit, PcgResult* res) {
-  // lanes per lambda in the H product: enough that the level spreads over ~64k threads
-  int gsz = 1;
-  while (gsz < 32 && (long)L.nlam * gsz < 65536) gsz *= 2;
-  long items = (long)L.nlam * gsz;
-  if (L.nif > items) items = L.nif;
-  if (L.nyl > items) items = L.nyl;
-  const void* fn = (const void*)kp_hyb_solve<T>;
-  int grid = coop_grid(fn, (int)items, gs.sm_cap);
-  void* args[] = {(void*)&L, (void*)&Hc, (void*)&Sinv, (void*)&kapc, (void*)&bs, (void*)&bp, (void*)&ylam,
-                  (void*)&ydiag, (void*)&lam, (void*)&lr, (void*)&lz, (void*)&pa, (void*)&pb, (void*)&lq,
-                  (void*)&ldinv, (void*)&dsig, (void*)&dp, (void*)&partial, (void*)&gs, (void*)&tol, (void*)&maxit,
-                  (void*)&gsz, (void*)&res};
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
-}
-template cudaError_t launch_hyb_solve<double>(cudaStream_t, const LevelDev&, const double*, const double*,
-                                              const double*, const double*, const double*, double*, double*,
-                                              double*, double*, double*, double*, double*, double*, double*,
-                                              double*, double*, double*, GridSync, double, int, PcgResult*);
 
 template <class T>
 cudaError_t launch_coarse_step(cudaStream_t st, const LevelDev& L, const T* Hc, const T* Sinv,
@@ -1510,5 +1467,26 @@ cudaError_t launch_coarse_step(cudaStream_t st, const LevelDev& L, const T* Hc, 
 template cudaError_t launch_coarse_step<double>(cudaStream_t, const LevelDev&, const double*, const double*,
                                                 const CoarseStepBufs<double>&, const CoarseStepParams&, double*,
                                                 GridSync, CoarseStepResult*);
+
+// ---- failure detection: the bounded grid barrier on its own ---------------------------------------------------
+// Every block except `absent` waits at one grid barrier whose spin limit is `spin_limit` (1024-spin granularity);
+// the absent block returns without arriving, so the others give up once the limit is spent, set *gs.err and leave.
+// With absent < 0 every block arrives and the barrier completes. *passed counts the blocks whose wait completed.
+__global__ void __launch_bounds__(kPThreads) kp_barrier_probe(GridSync gs, double* partial, int absent,
+                                                              unsigned long long spin_limit, int* passed) {
+  __shared__ double sm[kSmDoubles];
+  Grid g{gs, partial, sm, 0u};
+  if ((int)blockIdx.x == absent) return;
+  const bool ok = grid_barrier(g, spin_limit);
+  if (ok && threadIdx.x == 0) atomicAdd(passed, 1);
+}
+
+cudaError_t launch_barrier_probe(cudaStream_t st, GridSync gs, double* partial, int blocks, int absent,
+                                 unsigned long long spin_limit, int* passed) {
+  const void* fn = (const void*)kp_barrier_probe;
+  const int grid = coop_grid(fn, blocks * kPThreads, gs.sm_cap);
+  void* args[] = {(void*)&gs, (void*)&partial, (void*)&absent, (void*)&spin_limit, (void*)&passed};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
+}
 
 }  // namespace nlmg

@@ -107,10 +107,11 @@ cudaError_t launch_coarse_step(cudaStream_t st, const LevelDev& L, const T* Hc, 
                                const CoarseStepBufs<T>& B, const CoarseStepParams& P, double* partial, GridSync gs,
                                CoarseStepResult* res);
 
-template <class T>
-cudaError_t launch_hyb_solve(cudaStream_t st, const LevelDev& L, const T* Hc, const T* Sinv, const double* kapc,
-                             const double* bs, const double* bp, T* ylam, T* ydiag, T* lam, T* lr, T* lz, T* pa,
-                             T* pb, T* lq, T* ldinv, double* dsig, double* dp, double* partial, GridSync gs,
-                             double tol, int maxit, PcgResult* res);
+
+// Failure-detection check: a cooperative launch of min(blocks, co-resident) blocks in which every block but `absent`
+// (absent < 0: none) waits at one bounded grid barrier (spin_limit polls); *passed (zeroed by the caller) counts the
+// blocks whose wait completed, and *gs.err is set when a wait gave up.
+cudaError_t launch_barrier_probe(cudaStream_t st, GridSync gs, double* partial, int blocks, int absent,
+                                 unsigned long long spin_limit, int* passed);
 
 }  // namespace nlmg

@@ -81,10 +81,8 @@ struct nlmg_server {
 namespace {
 
 // Conservative device-memory estimate of one context (fine level, CG work vectors, coarse levels, transfers).
-size_t estimate_bytes(const Request& r) {
-  const size_t N = (size_t)r.n_cells, F = (size_t)r.n_faces;
-  return 64 * 1024 * 1024 / 64 + N * 900 + F * 120;
-}
+size_t estimate_cells_faces(size_t N, size_t F) { return 64 * 1024 * 1024 / 64 + N * 900 + F * 120; }
+size_t estimate_bytes(const Request& r) { return estimate_cells_faces((size_t)r.n_cells, (size_t)r.n_faces); }
 
 // FNV-1a over the bytes that determine a hierarchy.
 struct Fnv {
@@ -240,6 +238,12 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 }  // namespace
 
 extern "C" {
+
+nlmg_status nlmg_server_request_bytes(const nlmg_mesh* mesh, size_t* bytes) {
+  if (!mesh || !bytes || mesh->n_cells < 1 || mesh->n_faces < 0) return NLMG_EINVAL;
+  *bytes = estimate_cells_faces((size_t)mesh->n_cells, (size_t)mesh->n_faces);
+  return NLMG_OK;
+}
 
 void nlmg_server_default_options(nlmg_server_options* o) {
   if (!o) return;

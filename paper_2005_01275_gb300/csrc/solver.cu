@@ -74,6 +74,7 @@ struct Shared {
   FineMesh fm;
   Hierarchy H;
   std::vector<void*> allocs;
+  size_t bytes = 0;   // device bytes of allocs
   FineDev F;
   std::vector<LevelDev> LD;
   std::vector<TransferDev> TD;
@@ -102,6 +103,7 @@ struct nlmg_ctx {
   Hierarchy& H() { return sh->H; }
   cudaStream_t st = nullptr;
   std::vector<void*> allocs;   // this context's work buffers
+  size_t own_bytes = 0;        // device bytes of allocs
   FineDev F;                   // copies of the shared descriptors (device pointers into sh)
   std::vector<LevelDev> LD;
   std::vector<TransferDev> TD;
@@ -181,6 +183,7 @@ struct nlmg_ctx {
     if (n == 0) n = 1;
     CK(cudaMalloc(&p, n * sizeof(T)));
     allocs.push_back(p);
+    own_bytes += n * sizeof(T);
     return (T*)p;
   }
   // read-only data of the hierarchy: owned by the shared part
@@ -189,6 +192,7 @@ struct nlmg_ctx {
     void* p = nullptr;
     CK(cudaMalloc(&p, std::max<size_t>(v.size(), 1) * sizeof(T)));
     sh->allocs.push_back(p);
+    sh->bytes += std::max<size_t>(v.size(), 1) * sizeof(T);
     if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
     return (T*)p;
@@ -844,34 +848,6 @@ double coarse_res(nlmg_ctx* c, int l, const double* x, const double* b, double* 
   double v0, v1;
   c->read_sc2(S_NORM2, v0, v1);
   return std::sqrt(v0 + v1);
-}
-
-// Solve the frozen-coefficient saddle A_frozen(x) dx = -r (r, kapc current) by hybridization + persistent CG
-// -> B.dx. Returns iterations.
-int coarse_linear(nlmg_ctx* c, int l) {
-  const LevelDev& L = c->LD[l];
-  CoarseBuf& B = c->CB[l];
-  const int nx = L.nflux + L.np;
-  launch_axpy(c->st, nx, B.r, -2.0, B.r, B.nb);   // nb = -r
-  const double* bs = B.nb;
-  const double* bp = B.nb + L.nflux;
-  GridSync gs{c->d_bar, &c->d_res->err, c->sm_cap};
-  CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->st));
-  CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
-  int pi = c->prof_begin(1);
-  CK(launch_hyb_solve<double>(c->st, L, L.Hc, L.Sinv, B.kapc, bs, bp, B.ylam, B.ydiag, B.lam, B.lr, B.lz, B.lpa,
-                                B.lpb, B.lq, B.ldinv, B.dx, B.dx + L.nflux, c->d_partial, gs, c->coarse_lin_tol_eff,
-                                c->opt.lin_maxit, c->d_res));
-  c->prof_end(pi);
-  count_launch(1);
-  CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(PcgResult), cudaMemcpyDeviceToHost, c->st));
-  CK(cudaStreamSynchronize(c->st));
-  if (c->h_res->err) throw Error(NLMG_ETIMEOUT, "grid barrier wait gave up in the coarse CG kernel");
-  const int it = c->h_res->iters;
-  if (pi >= 0) c->prof.bytes[1] += (double)it * c->sh->hyb_bytes_per_iter[l];
-  c->lin_iters += it;
-  c->lin_iters_level[l] += it;
-  return it;
 }
 
 // x_{l+1} = Q x_l, b_{l+1} = A_{l+1}(x_{l+1}) - P^T r_l (r_l = [r_sigma; r_p] of level l >= 1 in CB[l].r)
@@ -1693,8 +1669,11 @@ nlmg_status nlmg_picard_update(nlmg_ctx* c, int32_t level, const double* x, cons
       size_t nx = (size_t)L.nflux + L.np;
       CK(cudaMemcpyAsync(B.x, x, nx * sizeof(double), cudaMemcpyHostToDevice, c->st));
       CK(cudaMemcpyAsync(B.b, b, nx * sizeof(double), cudaMemcpyHostToDevice, c->st));
-      coarse_res(c, level, B.x, B.b, B.r);
-      it = coarse_linear(c, level);
+      // the fused coarse step the cycles run (one Picard step): its hybridized solve leaves the update in B.dx
+      // (the clamp and Algorithm 1 after it only move x)
+      const long long before = c->lin_iters_level[level];
+      coarse_step(c, level, false, 1, level == c->nlev() - 1);
+      it = (int)(c->lin_iters_level[level] - before);
       CK(cudaMemcpyAsync(dx_out, B.dx, nx * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     }
     CK(cudaStreamSynchronize(c->st));
@@ -1843,6 +1822,37 @@ nlmg_status nlmg_fine_residual_noalloc(nlmg_ctx* c, const double* p_dev, double*
     if (!noalloc_residual((cudaStream_t)stream, scratch, c->F, p_dev, c->g, c->rhs, r_dev, norm2_dev, c->kind, c->a,
                           err))
       throw Error(NLMG_ECUDA, err);
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_device_bytes(const nlmg_ctx* c, size_t* shared_bytes, size_t* own_bytes) {
+  if (!c) return NLMG_EINVAL;
+  if (shared_bytes) *shared_bytes = c->sh->bytes;
+  if (own_bytes) *own_bytes = c->own_bytes;
+  return NLMG_OK;
+}
+
+nlmg_status nlmg_check_grid_barrier(nlmg_ctx* c, int32_t blocks, int32_t absent_block, int64_t spin_limit,
+                                    int32_t* passed) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_device(c);
+    if (blocks < 1 || absent_block >= blocks || spin_limit < 1024 || spin_limit > (int64_t)1 << 26)
+      throw Error(NLMG_EINVAL, "nlmg_check_grid_barrier: blocks >= 1, absent_block < blocks and a spin limit in "
+                               "[1024, 2^26] are required");
+    GridSync gs{c->d_bar, &c->d_res->err, c->sm_cap};
+    CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->st));
+    CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
+    CK(launch_barrier_probe(c->st, gs, c->d_partial, blocks, absent_block, (unsigned long long)spin_limit,
+                            &c->d_res->iters));
+    count_launch(1);
+    CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(PcgResult), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (passed) *passed = c->h_res->iters;
+    if (c->h_res->err) {
+      c->err = "grid barrier wait gave up";
+      return NLMG_ETIMEOUT;
+    }
     return NLMG_OK;
   });
 }

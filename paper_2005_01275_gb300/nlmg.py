@@ -114,6 +114,9 @@ SIGNATURES = {
     "nlmg_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), _D, _D, _D]),
     "nlmg_fine_residual_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "nlmg_measure_fp64": (C.c_int, [_D]),
+    "nlmg_device_bytes": (C.c_int, [_P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "nlmg_check_grid_barrier": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int64, _I]),
+    "nlmg_server_request_bytes": (C.c_int, [C.POINTER(Mesh), C.POINTER(C.c_size_t)]),
     "nlmg_last_error": (C.c_char_p, [_P]),
     "nlmg_destroy": (None, [_P]),
 }
@@ -394,6 +397,18 @@ class Context:
     def last_error(self):
         return lib().nlmg_last_error(self.h).decode()
 
+    def device_bytes(self):
+        """(shared, own) device bytes held by this context."""
+        a, b = C.c_size_t(0), C.c_size_t(0)
+        self._check(lib().nlmg_device_bytes(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def check_grid_barrier(self, blocks, absent_block, spin_limit):
+        """Runs the bounded grid barrier alone (one block may stay away); returns (status, blocks that passed)."""
+        n = C.c_int32(0)
+        st = lib().nlmg_check_grid_barrier(self.h, int(blocks), int(absent_block), int(spin_limit), C.byref(n))
+        return st, n.value
+
     def solve_device(self, f_ptr, g_ptr, x0_ptr, p_ptr, tol_rel=1e-8, tol_abs=1e-10, max_cycles=50):
         """Device-resident solve on raw device pointers (ints), e.g. torch tensor.data_ptr()."""
         rep = Report()
@@ -459,6 +474,20 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def request_bytes(mesh):
+    """Device bytes the request loop reserves for a request on this mesh before admitting it."""
+    fc = np.ascontiguousarray(mesh.face_cells, dtype=np.int32)
+    vol, ht, area = _f64(mesh.cell_volume), _f64(mesh.half_trans), _f64(mesh.face_area)
+    bc = np.ascontiguousarray(mesh.face_bc, dtype=np.uint8)
+    m = Mesh(mesh.n_cells, _dp(vol), int(fc.shape[0]), fc.ctypes.data_as(_I), _dp(ht),
+             bc.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(area))
+    v = C.c_size_t(0)
+    st = lib().nlmg_server_request_bytes(C.byref(m), C.byref(v))
+    if st != OK:
+        raise NlmgError(st, "request_bytes failed")
+    return v.value
 
 
 def measure_fp64_gflops():

@@ -291,12 +291,14 @@ def test_single_level_newton_baseline(nlmg_lib):
 
 
 def test_full_size_bench_configuration(nlmg_lib):
-    """The benchmarked 64^3 workload in its benchmarked configuration (library defaults): the returned iterate meets
-    the relative tolerance when its residual is recomputed by the oracle, and sampled residual rows agree."""
+    """The benchmarked 64^3 workload in its benchmarked configuration (Picard-then-Newton level-0 smoothing, the
+    library's inner tolerances): the returned iterate meets the relative tolerance when its residual is recomputed by
+    the oracle, and sampled residual rows agree."""
     pr = problem_config("chan3d_64")
-    ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.opts)
+    ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, dict(pr.opts, smoother="picard_newton"))
     p, rep, st = ctx.solve(pr.f_cell, pr.g_face)
     assert st == 0, rep
+    assert rep["newton_steps"] > 0
     r = tpfa.reduced_residual(pr.mesh, pr.kappa_kind, pr.kappa_a, p, pr.f_cell, pr.g_face)
     r0 = tpfa.reduced_residual(pr.mesh, pr.kappa_kind, pr.kappa_a, np.zeros(pr.mesh.n_cells), pr.f_cell, pr.g_face)
     assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(r0) * 1.0001
@@ -305,3 +307,18 @@ def test_full_size_bench_configuration(nlmg_lib):
     rows = np.random.default_rng(5).choice(pr.mesh.n_cells, 4096, replace=False)
     sig = tpfa.face_fluxes(pr.mesh, pr.kappa_kind, pr.kappa_a, p, pr.g_face)
     assert np.abs(rg[rows] - r[rows]).max() <= 1e-13 * np.abs(sig).max()
+
+
+def test_bench_options_reach_the_newton_solution(nlmg_lib):
+    """The benchmark's solver options (Picard-then-Newton smoothing, loose inner tolerances) on the 32^3 instance of
+    the same generator and hierarchy shape, run to relative residual 1e-12: the solution is p* within 1e-10; at the
+    benchmark's 1e-8 the error against p* is reported by the bench and bounded here by 1e-6."""
+    pr = problem_config("chan3d_64", scale=32)
+    ctx = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, dict(pr.opts, smoother="picard_newton"))
+    pstar, _ = newton.solve(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, dp_clamp=pr.opts["dp_clamp"])
+    p, rep, st = ctx.solve(pr.f_cell, pr.g_face, tol_rel=1e-12, tol_abs=1e-300, max_cycles=60)
+    assert st == 0, rep
+    assert _rel(p, pstar) <= 1e-10
+    p8, rep8, st8 = ctx.solve(pr.f_cell, pr.g_face)
+    assert st8 == 0 and rep8["newton_steps"] > 0
+    assert _rel(p8, pstar) <= 1e-6
