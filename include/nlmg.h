@@ -286,7 +286,7 @@ typedef struct {
 } nlmg_request_times;
 void nlmg_server_default_options(nlmg_server_options* opt);
 /* The device memory the request loop reserves for a request on this mesh before admitting it (the estimate its
- * admission compares with mem_budget_bytes): a fixed 1 MiB plus 900 bytes per cell and 120 per face. It is meant to
+ * admission compares with mem_budget_bytes): a fixed 4 MiB plus 2,000 bytes per cell and 200 per face. It is meant to
  * cover the shared and own device bytes a context holds after a solve (nlmg_device_bytes). Errors: NLMG_EINVAL. */
 nlmg_status nlmg_server_request_bytes(const nlmg_mesh* mesh, size_t* bytes);
 /* Uses the calling thread's current CUDA device. */

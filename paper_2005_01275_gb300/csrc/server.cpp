@@ -80,8 +80,9 @@ struct nlmg_server {
 
 namespace {
 
-// Conservative device-memory estimate of one context (fine level, CG work vectors, coarse levels, transfers).
-size_t estimate_cells_faces(size_t N, size_t F) { return 64 * 1024 * 1024 / 64 + N * 900 + F * 120; }
+// Conservative device-memory estimate of one context (fine level, Krylov work vectors including the Newton and
+// GMRES buffers, coarse levels, transfers); checked against the bytes contexts really hold by the GPU tests.
+size_t estimate_cells_faces(size_t N, size_t F) { return ((size_t)4 << 20) + N * 2000 + F * 200; }
 size_t estimate_bytes(const Request& r) { return estimate_cells_faces((size_t)r.n_cells, (size_t)r.n_faces); }
 
 // FNV-1a over the bytes that determine a hierarchy.

@@ -91,3 +91,4 @@ def test_admission_estimate_covers_a_contexts_device_memory(nlmg_lib, shape):
     est = nlmg_lib.request_bytes(mesh)
     assert shared > 0 and own > 0
     assert shared + own <= est, (shared, own, est)
+    assert est <= 4 * (shared + own), (shared, own, est)      # and not so loose that it starves the loop
