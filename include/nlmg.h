@@ -111,7 +111,15 @@ typedef struct {
                                 projected, and its correction is carried to the finer level with Algorithm 1; the
                                 level-0 correction too. The report's history then holds the residual after it as its
                                 second entry (not counted as a cycle). 0 (default): plain FAS cycles */
-  int32_t reserved[4];
+  int32_t lin_precond;       /* preconditioner of the level-0 Krylov solves (the Picard steps' CG and the Newton
+                                steps' BiCGStab; Sec. 3.4 uses AMG there): 0 (default) Jacobi, in the persistent
+                                kernels; 1 one V-cycle of a linear multigrid on the hierarchy's pressure spaces
+                                (Galerkin operators P^T A P, Chebyshev smoothing, dense coarsest solve; FP32 inside
+                                the FP64 Krylov iteration, run as CUDA graphs with a device-side loop). A hierarchy
+                                option when set at setup: the setup then coarsens beyond n_levels, for the
+                                preconditioner only, until the coarsest level has at most 128 pressure unknowns (the
+                                FAS cycles still use n_levels levels); a context set up with 0 cannot switch to 1 */
+  int32_t reserved[3];
 } nlmg_options;
 
 typedef struct {
@@ -243,6 +251,13 @@ nlmg_status nlmg_transfer(nlmg_ctx* ctx, int32_t level, int32_t op, const double
 nlmg_status nlmg_picard_update(nlmg_ctx* ctx, int32_t level, const double* x, const double* b, double* dx_out,
                                int32_t* iters);
 
+/* One application z = B r of the multigrid preconditioner of the level-0 Krylov solves (lin_precond = 1; the
+ * paper's Sec. 3.4 preconditions them with AMG) for the frozen TPFA matrix A(kappa(p)): one V-cycle on the
+ * hierarchy's pressure spaces with Galerkin operators A_{l+1} = P_l^T A_l P_l, Chebyshev smoothing preconditioned by
+ * the (block) diagonal and a dense coarsest solve, in FP32. p, r, z_out are host arrays of n_cells. Errors:
+ * NLMG_EINVAL (context not set up with lin_precond = 1, no data). */
+nlmg_status nlmg_precond_apply(nlmg_ctx* ctx, const double* p, const double* r, double* z_out);
+
 /* The level-0 Newton update (Sec. 3.3.2 in the reduced form): dx solving J(p) dx = -R(p) with the exact Jacobian of
  * the TPFA residual, by the persistent FP64 BiCGStab of the Picard-then-Newton smoother to newton_lin_tol (relative,
  * on the Jacobi-scaled residual). p and dx_out are host arrays of n_cells; *iters (may be NULL) receives the iterations. */
@@ -308,7 +323,8 @@ void nlmg_server_destroy(nlmg_server* srv);
  * coarse operator evaluations, hybridized CG, clamp and Algorithm 1 in one launch; also for nlmg_picard_update)
  * on the levels between the finest and the coarsest, 2 = fine TPFA residual (k_residual), 3 = persistent fine
  * BiCGStab of the Newton smoothing steps (kp_fine_bicgstab), 4 = kp_coarse_step on the coarsest level (the whole
- * coarsest solve in one launch). */
+ * coarsest solve in one launch), 5 = a level-0 CG solve preconditioned by the multigrid V-cycle (lin_precond = 1:
+ * its setup and its graph launches), 6 = the same for a Newton step's BiCGStab. */
 nlmg_status nlmg_profile(nlmg_ctx* ctx, int32_t enable);
 /* Launch count, summed event time, algorithmic bytes per launch (each streamed array counted once; the gathered
  * neighbour values counted once) and arithmetic per launch (FMA = 2 flops; every kernel but 2) of a profiled kernel

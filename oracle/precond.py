@@ -10,7 +10,11 @@ by one linear V-cycle on the pressure spaces of the spectral hierarchy itself (t
     coarse cell; the Chebyshev interval is [lam / alpha, lam], lam = max_i sum_j |(D_l^-1 A_l)_ij|, a Gershgorin
     bound of the largest eigenvalue of D_l^-1 A_l (whose eigenvalues are real and positive);
   * V-cycle on level l: x = smooth(b); x += P_l Vcycle_{l+1}(P_l^T (b - A_l x)); x = smooth continued from x; the
-    coarsest level is solved exactly. Pre- and post-smoothing are the same polynomial, so the cycle is a symmetric
+    coarsest level is solved exactly;
+  * levels: the hierarchy the FAS cycles use, coarsened further for the preconditioner alone when its coarsest level
+    is large (extended_options: up to four more steps, aggregates of agg_size[l] cells (8 unless given), the last
+    FAS step's modes, one flux unknown per interface), cut at the first level whose cell count times its largest
+    mode count is at most MAX_COARSE (levels_for). Pre- and post-smoothing are the same polynomial, so the cycle is a symmetric
     positive definite operator B ~ A_0^-1 (the smoother converges in the energy norm: the interval covers the
     spectrum's top).
 Chebyshev iteration (the three-term recurrence for the shifted and scaled Chebyshev polynomials on [lmin, lmax]):
@@ -26,7 +30,9 @@ import numpy as np
 import scipy.sparse as sp
 
 ALPHA = 4.0       # Chebyshev interval [lam / ALPHA, lam]
-DEGREE = 2        # smoothing steps before and after the coarse correction
+DEGREES = (2, 2)  # smoothing steps before and after the coarse correction: level 0, levels >= 1
+MAX_COARSE = 128  # the coarsest level the V-cycle solves directly has at most this many pressure unknowns (padded
+                  # to the largest mode count of the level)
 
 
 @dataclass
@@ -51,6 +57,33 @@ def _block_diag_inverse(A, blocks):
     return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
 
 
+def extended_options(opts):
+    """Hierarchy options with the preconditioner's extra coarsening steps (module docstring)."""
+    o = dict(opts)
+    nl = int(opts["n_levels"])
+    total = min(8, nl + 4)
+    agg = list(opts["agg_size"]) + [8] * 8
+    modes = list(opts["modes"]) + [2] * 8
+    mf = list(opts.get("flux_modes", [1] * 8)) + [1] * 8
+    mlast = modes[nl - 2] if nl >= 2 else modes[0]
+    for l in range(max(nl - 1, 0), 8):
+        agg[l] = agg[l] if agg[l] >= 2 else 8
+        modes[l] = max(1, min(8, mlast))
+        mf[l] = 1
+    o.update(n_levels=total, agg_size=agg[:8], modes=modes[:8], flux_modes=mf[:8])
+    return o
+
+
+def levels_for(H):
+    """The number of levels of H the V-cycle uses: the first level whose cells times largest mode count is at most
+    MAX_COARSE ends it (0 if none)."""
+    for L in range(2, len(H.levels) + 1):
+        lev = H.levels[L - 1]
+        if lev.n_cells * int(np.max(lev.m)) <= MAX_COARSE:
+            return L
+    return 0
+
+
 def build(A0, H, n_levels=None):
     """The V-cycle's levels on the hierarchy H (oracle.hierarchy.Hierarchy) for the fine matrix A0; n_levels caps the
     number of levels (default: all of H)."""
@@ -72,7 +105,7 @@ def build(A0, H, n_levels=None):
     return levels
 
 
-def chebyshev(lv, b, x, degree=DEGREE, alpha=ALPHA):
+def chebyshev(lv, b, x, degree, alpha=ALPHA):
     """`degree` Chebyshev steps for lv.A x = b from x, preconditioned by lv.Dinv (module docstring)."""
     lmax = lv.lam
     lmin = lmax / alpha
@@ -91,15 +124,16 @@ def chebyshev(lv, b, x, degree=DEGREE, alpha=ALPHA):
     return x
 
 
-def vcycle(levels, H, b, l=0, degree=DEGREE, alpha=ALPHA):
+def vcycle(levels, H, b, l=0, degrees=DEGREES, alpha=ALPHA):
     """B b: one V-cycle from level l for A_l x = b (module docstring)."""
     lv = levels[l]
     if l == len(levels) - 1:
         return np.linalg.solve(lv.A.toarray(), b)
-    x = chebyshev(lv, b, np.zeros(b.size), degree, alpha)
+    deg = degrees[0] if l == 0 else degrees[1]
+    x = chebyshev(lv, b, np.zeros(b.size), deg, alpha)
     P = H.transfers[l].Pp
-    x = x + P @ vcycle(levels, H, P.T @ (b - lv.A @ x), l + 1, degree, alpha)
-    return chebyshev(lv, b, x, degree, alpha)
+    x = x + P @ vcycle(levels, H, P.T @ (b - lv.A @ x), l + 1, degrees, alpha)
+    return chebyshev(lv, b, x, deg, alpha)
 
 
 def pcg(A, b, apply_B, k, tol=0.0, w=None):

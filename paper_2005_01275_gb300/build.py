@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libnlmg.so")
-SOURCES = ["dense.cpp", "setup.cpp", "kernels.cu", "persist.cu", "eig.cu", "noalloc.cu", "solver.cu", "server.cpp"]
+SOURCES = ["dense.cpp", "setup.cpp", "kernels.cu", "persist.cu", "eig.cu", "mg.cu", "noalloc.cu", "solver.cu",
+           "server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
 

@@ -1,0 +1,1168 @@
+// Linear multigrid preconditioner for the level-0 Krylov solves (see mg.cuh), and the preconditioned CG / BiCGStab
+// that use it, each captured once per context as CUDA graphs with a device-side conditional while loop.
+//
+// Every reduction is deterministic: per-block partial sums in a fixed tree, then the grid's last block adds the
+// partials in block order (the arrival counter is reset by that block, so graphs replay). Maxima are exact.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "mg.cuh"
+
+namespace nlmg {
+
+namespace {
+
+constexpr int kT = 256;               // threads per block of the preconditioner kernels
+constexpr int kMaxRedBlocks = 1024;   // grid cap of the reduction kernels (partials summed by one block)
+constexpr int kG = 8;                 // lanes per cell in the block kernels (block size <= kMaxM = 8)
+
+inline int blocks_for(long n, int cap = 1 << 20) {
+  long b = (n + kT - 1) / kT;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// reductions
+
+// Sums NV values over the grid: block tree sums to part[block][k]; the last block to arrive adds the partials in block
+// order (thread t takes partials t, t + blockDim, ...; then a fixed tree) and returns true in every one of its
+// threads with the sums in out (shared). The counter is left at zero.
+template <int NV>
+__device__ bool reduce_last(double (&v)[NV], double* part, unsigned* cnt, double* out) {
+  __shared__ double sh[NV][kT / 32];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double a = v[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (lane == 0) sh[k][warp] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double a = 0.0;
+      for (int w = 0; w < kT / 32; ++w) a += sh[k][w];
+      part[(size_t)blockIdx.x * NV + k] = a;
+    }
+    __threadfence();
+    last = atomicAdd(cnt, 1u) == gridDim.x - 1 ? 1 : 0;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double a = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kT) a += __ldcg(&part[(size_t)b * NV + k]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (lane == 0) sh[k][warp] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double a = 0.0;
+      for (int w = 0; w < kT / 32; ++w) a += sh[k][w];
+      out[k] = a;
+    }
+    *cnt = 0u;
+  }
+  __syncthreads();
+  return true;
+}
+
+__device__ __forceinline__ void atomic_max_pos(float* addr, float v) {
+  // non-negative floats order like their bit patterns
+  atomicMax((unsigned*)addr, __float_as_uint(v));
+}
+
+// Chebyshev coefficients of step k on [lam / alpha, lam] (see oracle/precond.py): k = 0 -> (0, 1 / theta);
+// k >= 1 -> (rho_k rho_{k-1}, 2 rho_k / delta).
+__device__ __forceinline__ void cheb_coef(float lam, int k, float& c1, float& c2) {
+  const double lmax = lam, lmin = lam / kMgAlpha;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  if (k == 0) {
+    c1 = 0.0f;
+    c2 = (float)(1.0 / theta);
+    return;
+  }
+  double rho = 1.0 / sigma, rho_prev = rho;
+  for (int i = 1; i <= k; ++i) {
+    rho_prev = rho;
+    rho = 1.0 / (2.0 * sigma - rho);
+  }
+  c1 = (float)(rho * rho_prev);
+  c2 = (float)(2.0 * rho / delta);
+}
+
+__device__ __forceinline__ bool stop(const int* done) { return done && *((volatile const int*)done) != 0; }
+
+// ---------------------------------------------------------------------------------------------------------------
+// setup kernels (once per frozen matrix)
+
+// FP32 copy of the level-0 matrix (off-diagonal entries -T in the SELL layout, diagonal, its inverse) and the
+// Gershgorin bound max_K (A_KK + sum_L T_KL) / A_KK of D^-1 A.
+__global__ void k_fine_vals(FineDev F, const double* __restrict__ Tval, const double* __restrict__ diagT,
+                            float* __restrict__ a0off, float* __restrict__ a0diag, float* __restrict__ a0dinv,
+                            float* lam) {
+  float g = 0.0f;
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < F.N; K += gridDim.x * blockDim.x) {
+    const int w = F.sell_w[K >> 5];
+    int e = F.sell_off[K >> 5] + (K & 31);
+    double s = 0.0;
+    for (int j = 0; j < w; ++j, e += 32) {
+      const double t = Tval[e];
+      a0off[e] = (float)(-t);
+      s += t;
+    }
+    const double dg = diagT[K];
+    a0diag[K] = (float)dg;
+    a0dinv[K] = (float)(1.0 / dg);
+    g = fmaxf(g, (float)((dg + s) / dg));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) g = fmaxf(g, __shfl_down_sync(0xffffffffu, g, off));
+  if ((threadIdx.x & 31) == 0) atomic_max_pos(&lam[0], g);
+}
+
+// Level-1 Galerkin blocks from the fine faces, one warp per block, lane t owning entries t and t + 32 of the
+// mb x mb block. Contributions (K, L, e, type): 0 interior face inside the aggregate, T (P_K - P_L)(P_K - P_L)^T;
+// 1 face to another aggregate seen from this one's cell K, T P_K P_K^T; 2 the off-diagonal part, -T P_K P_L^T;
+// 3 Dirichlet face (L = its entry in the Dirichlet list), h P_K P_K^T with h = kappa_K Ups_K. Padded modes get a unit
+// diagonal.
+__global__ void k_asm1(int nblk, int mb, const int* __restrict__ off, const int4* __restrict__ list,
+                       const float* __restrict__ P0, const double* __restrict__ Tval, const double* __restrict__ kap,
+                       const double* __restrict__ dir_ups, const int* __restrict__ rowptr, const int* __restrict__ dpos,
+                       const int* __restrict__ mcnt, float* __restrict__ aval) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int mm = mb * mb;
+  for (int b = warp; b < nblk; b += nw) {
+    float acc[2] = {0.0f, 0.0f};
+    int uu[2], vv[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int idx = lane + 32 * h;
+      uu[h] = idx / mb;
+      vv[h] = idx % mb;
+    }
+    for (int c = off[b]; c < off[b + 1]; ++c) {
+      const int4 t = list[c];
+      const float* PK = P0 + (size_t)t.x * mb;
+      if (t.w == 3) {
+        const float h = (float)(kap[t.x] * dir_ups[t.y]);
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+          if (lane + 32 * q < mm) acc[q] = fmaf(h * PK[uu[q]], PK[vv[q]], acc[q]);
+        continue;
+      }
+      const float T = (float)Tval[t.z];
+      const float* PL = P0 + (size_t)t.y * mb;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (lane + 32 * q >= mm) continue;
+        const int u = uu[q], v = vv[q];
+        if (t.w == 0) {
+          acc[q] = fmaf(T * (PK[u] - PL[u]), PK[v] - PL[v], acc[q]);
+        } else if (t.w == 1) {
+          acc[q] = fmaf(T * PK[u], PK[v], acc[q]);
+        } else {
+          acc[q] = fmaf(-T * PK[u], PL[v], acc[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int idx = lane + 32 * q;
+      if (idx >= mm) continue;
+      aval[(size_t)b * mm + idx] = acc[q];
+    }
+    (void)rowptr;
+    (void)dpos;
+    (void)mcnt;
+  }
+}
+
+// Unit diagonal on the padded modes of every diagonal block of level l (cells with fewer modes than mb).
+__global__ void k_pad_diag(int nc, int mb, const int* __restrict__ dpos, const int* __restrict__ mcnt,
+                           float* __restrict__ aval) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+    float* B = aval + (size_t)dpos[c] * mb * mb;
+    for (int u = mcnt[c]; u < mb; ++u) {
+      for (int v = 0; v < mb; ++v) B[u * mb + v] = B[v * mb + u] = 0.0f;
+      B[u * mb + u] = 1.0f;
+    }
+  }
+}
+
+// Level-l Galerkin blocks (l >= 2) from the level-(l-1) blocks: block (A, B) = sum over (c, d) with agg(c) = A,
+// agg(d) = B of P_c^T A_cd P_d, P_c the mbf x mb transfer block of level-(l-1) cell c. One warp per block.
+__global__ void k_asml(int nblk, int mb, int mbf, const int* __restrict__ off, const int4* __restrict__ list,
+                       const float* __restrict__ Pf, const float* __restrict__ afine, float* __restrict__ aval) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int mm = mb * mb, mmf = mbf * mbf;
+  for (int b = warp; b < nblk; b += nw) {
+    float acc[2] = {0.0f, 0.0f};
+    for (int c = off[b]; c < off[b + 1]; ++c) {
+      const int4 t = list[c];   // (source block, c, d, -)
+      const float* As = afine + (size_t)t.x * mmf;
+      const float* Pc = Pf + (size_t)t.y * mbf * mb;
+      const float* Pd = Pf + (size_t)t.z * mbf * mb;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int idx = lane + 32 * q;
+        if (idx >= mm) continue;
+        const int u = idx / mb, v = idx % mb;
+        float s = 0.0f;
+        for (int i = 0; i < mbf; ++i) {
+          float r = 0.0f;
+          for (int j = 0; j < mbf; ++j) r = fmaf(As[i * mbf + j], Pd[j * mb + v], r);
+          s = fmaf(Pc[i * mb + u], r, s);
+        }
+        acc[q] += s;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int idx = lane + 32 * q;
+      if (idx < mm) aval[(size_t)b * mm + idx] = acc[q];
+    }
+  }
+}
+
+// Inverse of each diagonal block of level l (Gauss-Jordan in FP64, no pivoting: the blocks are symmetric positive
+// definite) and the Gershgorin bound max over rows of sum |D^-1 A| (one thread per cell).
+__global__ void k_block_inv(int nc, int mb, const int* __restrict__ rowptr, const int* __restrict__ col,
+                            const int* __restrict__ dpos, const float* __restrict__ aval, float* __restrict__ dinv,
+                            float* lam) {
+  float g = 0.0f;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+    double A[kMaxM * kMaxM];
+    const float* B = aval + (size_t)dpos[c] * mb * mb;
+    for (int i = 0; i < mb * mb; ++i) A[i] = B[i];
+    for (int k = 0; k < mb; ++k) {
+      const double dk = 1.0 / A[k * mb + k];
+      A[k * mb + k] = 1.0;
+      for (int j = 0; j < mb; ++j) A[k * mb + j] *= dk;
+      for (int i = 0; i < mb; ++i) {
+        if (i == k) continue;
+        const double f = A[i * mb + k];
+        A[i * mb + k] = 0.0;
+        for (int j = 0; j < mb; ++j) A[i * mb + j] -= f * A[k * mb + j];
+      }
+    }
+    float* Dc = dinv + (size_t)c * mb * mb;
+    for (int i = 0; i < mb * mb; ++i) Dc[i] = (float)A[i];
+    for (int u = 0; u < mb; ++u) {
+      double s = 0.0;
+      for (int q = rowptr[c]; q < rowptr[c + 1]; ++q) {
+        const float* Bq = aval + (size_t)q * mb * mb;
+        for (int v = 0; v < mb; ++v) {
+          double t = 0.0;
+          for (int w = 0; w < mb; ++w) t += A[u * mb + w] * Bq[w * mb + v];
+          s += fabs(t);
+        }
+      }
+      g = fmaxf(g, (float)s);
+    }
+    (void)col;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) g = fmaxf(g, __shfl_down_sync(0xffffffffu, g, off));
+  if ((threadIdx.x & 31) == 0) atomic_max_pos(lam, g);
+}
+
+// Dense inverse of the coarsest level (n = nc * mb <= kMgMaxCoarse) in one block: the blocks assembled into an
+// n x n FP64 matrix in shared memory, in-place Gauss-Jordan (symmetric positive definite, no pivoting).
+__global__ void k_coarse_inv(int nc, int mb, const int* __restrict__ rowptr, const int* __restrict__ col,
+                             const float* __restrict__ aval, float* __restrict__ cinv) {
+  extern __shared__ double S[];   // n * n + n
+  const int n = nc * mb;
+  double* colk = S + n * n;
+  __shared__ double piv;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) S[i] = 0.0;
+  __syncthreads();
+  for (int c = 0; c < nc; ++c)
+    for (int q = rowptr[c]; q < rowptr[c + 1]; ++q) {
+      const int d = col[q];
+      for (int idx = threadIdx.x; idx < mb * mb; idx += blockDim.x) {
+        const int u = idx / mb, v = idx % mb;
+        S[(c * mb + u) * n + d * mb + v] = aval[(size_t)q * mb * mb + idx];
+      }
+    }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      piv = 1.0 / S[k * n + k];
+      S[k * n + k] = 1.0;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) S[k * n + j] *= piv;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = i == k ? 0.0 : S[i * n + k];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int i = idx / n, j = idx % n;
+      if (i == k) continue;
+      if (j == k)
+        S[idx] = -colk[i] * S[k * n + k];
+      else
+        S[idx] -= colk[i] * S[k * n + j];
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) cinv[i] = (float)S[i];
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// V-cycle kernels
+
+// One Chebyshev step on level 0: res = b - A x_in, d = c1 d + c2 D^-1 res, x_out = x_in + d (x_in is gathered by the
+// neighbours, so the new iterate goes to the other buffer).
+__global__ void k_cheb0(FineDev F, const float* __restrict__ a0off, const float* __restrict__ a0diag,
+                        const float* __restrict__ a0dinv, const float* __restrict__ b, const float* __restrict__ xin,
+                        float* __restrict__ xout, float* __restrict__ d, const float* __restrict__ lam, int k,
+                        const int* done) {
+  if (stop(done)) return;
+  float c1, c2;
+  cheb_coef(lam[0], k, c1, c2);
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < F.N; K += gridDim.x * blockDim.x) {
+    const int w = F.sell_w[K >> 5];
+    int e = F.sell_off[K >> 5] + (K & 31);
+    const float xk = xin[K];
+    float ax = a0diag[K] * xk;
+    for (int j = 0; j < w; ++j, e += 32) ax = fmaf(a0off[e], xin[F.nbr[e]], ax);
+    const float res = b[K] - ax;
+    const float dn = (k == 0 ? 0.0f : c1 * d[K]) + c2 * a0dinv[K] * res;
+    d[K] = dn;
+    xout[K] = xk + dn;
+  }
+}
+
+// Level-0 residual and its restriction to level 1, one warp per level-1 cell A: b1_A = P_A^T (b - A x) over the fine
+// cells of A. If `first` is set, the first Chebyshev step of level 1 follows (x1 = D1^-1 b1 / theta, d1 = x1).
+__global__ void k_rr0(FineDev F, const float* __restrict__ a0off, const float* __restrict__ a0diag,
+                      const float* __restrict__ b, const float* __restrict__ x, const float* __restrict__ P0,
+                      const int* __restrict__ ch_off, const int* __restrict__ ch, int nc1, int mb,
+                      float* __restrict__ b1, const float* __restrict__ dinv1, float* __restrict__ x1,
+                      float* __restrict__ d1, const float* __restrict__ lam, int first, const int* done) {
+  if (stop(done)) return;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  float c1 = 0.0f, c2 = 0.0f;
+  if (first) cheb_coef(lam[1], 0, c1, c2);
+  for (int A = warp; A < nc1; A += nw) {
+    float acc[kMaxM];
+#pragma unroll
+    for (int j = 0; j < kMaxM; ++j) acc[j] = 0.0f;
+    for (int t = ch_off[A] + lane; t < ch_off[A + 1]; t += 32) {
+      const int K = ch[t];
+      const int w = F.sell_w[K >> 5];
+      int e = F.sell_off[K >> 5] + (K & 31);
+      float ax = a0diag[K] * x[K];
+      for (int j = 0; j < w; ++j, e += 32) ax = fmaf(a0off[e], x[F.nbr[e]], ax);
+      const float res = b[K] - ax;
+      const float* PK = P0 + (size_t)K * mb;
+#pragma unroll
+      for (int j = 0; j < kMaxM; ++j)
+        if (j < mb) acc[j] = fmaf(PK[j], res, acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxM; ++j) {
+      if (j >= mb) break;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], off);
+    }
+    if (lane < mb) {
+      float bj = 0.0f;
+#pragma unroll
+      for (int j = 0; j < kMaxM; ++j)
+        if (j == lane) bj = acc[j];
+      b1[(size_t)A * mb + lane] = bj;
+      if (first) {
+        const float* Dc = dinv1 + (size_t)A * mb * mb + lane * mb;
+        float s = 0.0f;
+#pragma unroll
+        for (int v = 0; v < kMaxM; ++v)
+          if (v < mb) s = fmaf(Dc[v], acc[v], s);
+        const float dn = c2 * s;
+        d1[(size_t)A * mb + lane] = dn;
+        x1[(size_t)A * mb + lane] = dn;
+      }
+    }
+  }
+}
+
+// (b - A x)_u for cell c on a block level: lane u of the group (u < mb).
+__device__ __forceinline__ float block_res(int c, int u, int mb, const int* __restrict__ rowptr,
+                                           const int* __restrict__ col, const float* __restrict__ aval,
+                                           const float* __restrict__ b, const float* __restrict__ x) {
+  float ax = 0.0f;
+  for (int q = rowptr[c]; q < rowptr[c + 1]; ++q) {
+    const float* Bq = aval + (size_t)q * mb * mb + u * mb;
+    const float* xd = x + (size_t)col[q] * mb;
+    for (int v = 0; v < mb; ++v) ax = fmaf(Bq[v], xd[v], ax);
+  }
+  return b[(size_t)c * mb + u] - ax;
+}
+
+// One Chebyshev step on block level l: groups of kG lanes per cell, lane u < mb owning component u.
+__global__ void k_chebl(int nc, int mb, const int* __restrict__ rowptr, const int* __restrict__ col,
+                        const float* __restrict__ aval, const float* __restrict__ dinv, const float* __restrict__ b,
+                        const float* __restrict__ xin, float* __restrict__ xout, float* __restrict__ d,
+                        const float* __restrict__ lam, int l, int k, const int* done) {
+  if (stop(done)) return;
+  float c1, c2;
+  cheb_coef(lam[l], k, c1, c2);
+  const int lane = threadIdx.x & 31, u = lane & (kG - 1);
+  const long total = (long)nc * kG;
+  for (long tb = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); tb < total; tb += (long)gridDim.x * blockDim.x) {
+    const long t = tb + lane;
+    const int c = (int)(t / kG);
+    const bool act = t < total && u < mb;
+    const float res = act ? block_res(c, u, mb, rowptr, col, aval, b, xin) : 0.0f;
+    float s = 0.0f;
+    for (int v = 0; v < mb; ++v) {
+      const float rv = __shfl_sync(0xffffffffu, res, (lane & ~(kG - 1)) + v);
+      if (act) s = fmaf(dinv[(size_t)c * mb * mb + u * mb + v], rv, s);
+    }
+    if (act) {
+      const size_t i = (size_t)c * mb + u;
+      const float dn = (k == 0 ? 0.0f : c1 * d[i]) + c2 * s;
+      d[i] = dn;
+      xout[i] = xin[i] + dn;
+    }
+  }
+}
+
+// Level-l residual restricted to level l+1, one warp per level-(l+1) cell A, four groups of kG lanes taking its
+// children in turn; `first` adds the first Chebyshev step of level l+1.
+__global__ void k_rrl(int mbf, const int* __restrict__ rowptr, const int* __restrict__ col,
+                      const float* __restrict__ aval, const float* __restrict__ b, const float* __restrict__ x,
+                      const float* __restrict__ Pl, const int* __restrict__ ch_off, const int* __restrict__ ch,
+                      int ncc, int mb, float* __restrict__ bc, const float* __restrict__ dinvc, float* __restrict__ xc,
+                      float* __restrict__ dc, const float* __restrict__ lam, int lc, int first, const int* done) {
+  if (stop(done)) return;
+  const int lane = threadIdx.x & 31, grp = lane / kG, u = lane & (kG - 1);
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  float c1 = 0.0f, c2 = 0.0f;
+  if (first) cheb_coef(lam[lc], 0, c1, c2);
+  for (int A = warp; A < ncc; A += nw) {
+    float acc[kMaxM];
+#pragma unroll
+    for (int j = 0; j < kMaxM; ++j) acc[j] = 0.0f;
+    for (int t = ch_off[A] + grp; t < ch_off[A + 1]; t += 32 / kG) {
+      if (u >= mbf) continue;
+      const int c = ch[t];
+      const float res = block_res(c, u, mbf, rowptr, col, aval, b, x);
+      const float* Pr = Pl + ((size_t)c * mbf + u) * mb;
+#pragma unroll
+      for (int j = 0; j < kMaxM; ++j)
+        if (j < mb) acc[j] = fmaf(Pr[j], res, acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxM; ++j) {
+      if (j >= mb) break;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], off);
+    }
+    if (lane < mb) {
+      float bj = 0.0f;
+#pragma unroll
+      for (int j = 0; j < kMaxM; ++j)
+        if (j == lane) bj = acc[j];
+      bc[(size_t)A * mb + lane] = bj;
+      if (first) {
+        const float* Dc = dinvc + (size_t)A * mb * mb + lane * mb;
+        float s = 0.0f;
+#pragma unroll
+        for (int v = 0; v < kMaxM; ++v)
+          if (v < mb) s = fmaf(Dc[v], acc[v], s);
+        const float dn = c2 * s;
+        dc[(size_t)A * mb + lane] = dn;
+        xc[(size_t)A * mb + lane] = dn;
+      }
+    }
+  }
+}
+
+// Coarsest level: x = C^-1 b with the dense inverse.
+__global__ void k_coarse_solve(int n, const float* __restrict__ cinv, const float* __restrict__ b,
+                               float* __restrict__ x, const int* done) {
+  if (stop(done)) return;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float s = 0.0f;
+    for (int j = 0; j < n; ++j) s = fmaf(cinv[(size_t)i * n + j], b[j], s);
+    x[i] = s;
+  }
+}
+
+// x_0 += P e on level 0 (per fine cell) and on a block level (per cell and component).
+__global__ void k_pro0(int N, int mb, const float* __restrict__ P0, const int* __restrict__ agg,
+                       const float* __restrict__ e, float* __restrict__ x, const int* done) {
+  if (stop(done)) return;
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
+    const float* PK = P0 + (size_t)K * mb;
+    const float* ea = e + (size_t)agg[K] * mb;
+    float s = x[K];
+    for (int j = 0; j < mb; ++j) s = fmaf(PK[j], ea[j], s);
+    x[K] = s;
+  }
+}
+__global__ void k_prol(int nc, int mbf, int mb, const float* __restrict__ Pl, const int* __restrict__ agg,
+                       const float* __restrict__ e, float* __restrict__ x, const int* done) {
+  if (stop(done)) return;
+  const long total = (long)nc * mbf;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / mbf);
+    const float* Pr = Pl + (size_t)i * mb;
+    const float* ea = e + (size_t)agg[c] * mb;
+    float s = x[i];
+    for (int j = 0; j < mb; ++j) s = fmaf(Pr[j], ea[j], s);
+    x[i] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// Krylov kernels (FP64 outer iteration)
+
+// A v with the frozen FP64 matrix (diagT, Tval) at cell K, v of type T.
+template <class T>
+__device__ __forceinline__ double amul(const FineDev& F, const double* __restrict__ Tval,
+                                       const double* __restrict__ diagT, const T* __restrict__ v, int K) {
+  const int w = F.sell_w[K >> 5];
+  int e = F.sell_off[K >> 5] + (K & 31);
+  double s = diagT[K] * (double)v[K];
+  for (int j = 0; j < w; ++j, e += 32) s = fma(-Tval[e], (double)v[F.nbr[e]], s);
+  return s;
+}
+
+// Fused first pre-smoothing step of level 0 for the FP32 right-hand side r32: x0 = D^-1 r32 / theta, d0 = x0.
+__device__ __forceinline__ void first_step0(int K, float r32, const float* __restrict__ a0dinv, float c2,
+                                            float* __restrict__ x0, float* __restrict__ d0) {
+  const float dn = c2 * a0dinv[K] * r32;
+  x0[K] = dn;
+  d0[K] = dn;
+}
+
+// PCG start: x = 0, r = bscale b, r32 = r, first smoothing step, rr0 = ||S r||^2 (S = diag(A)^-1/2).
+__global__ void k_pcg_init(int N, const double* __restrict__ b, double bscale, const double* __restrict__ diagT,
+                           double* __restrict__ x, double* __restrict__ r, float* __restrict__ r32,
+                           const float* __restrict__ a0dinv, float* __restrict__ x0, float* __restrict__ d0,
+                           const float* __restrict__ lam, double* part, MgScal* sc) {
+  float c1, c2;
+  cheb_coef(lam[0], 0, c1, c2);
+  double v[1] = {0.0};
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
+    const double ri = bscale * b[K];
+    x[K] = 0.0;
+    r[K] = ri;
+    r32[K] = (float)ri;
+    first_step0(K, (float)ri, a0dinv, c2, x0, d0);
+    v[0] = fma(ri * ri, 1.0 / diagT[K], v[0]);
+  }
+  __shared__ double out[1];
+  if (reduce_last<1>(v, part, &sc->cnt[0], out) && threadIdx.x == 0) {
+    sc->rr0 = out[0];
+    sc->rr = out[0];
+    sc->it = 0;
+    sc->done = !(out[0] > 0.0) ? 1 : 0;
+    sc->bad = isfinite(out[0]) ? 0 : 1;
+    sc->rz = 0.0;
+  }
+}
+
+// Flexible CG step length: rz_new = (r, z), beta = (r, z - z_old) / rz (0 on the first step), which equals the plain
+// rz_new / rz for a fixed linear preconditioner and tolerates the FP32 rounding of the V-cycle.
+__global__ void k_pcg_beta(int N, const double* __restrict__ r, const float* __restrict__ z,
+                           const float* __restrict__ zold, double* part, MgScal* sc) {
+  if (stop(&sc->done)) return;
+  const bool first = sc->it == 0;
+  double v[2] = {0.0, 0.0};
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
+    v[0] = fma(r[K], (double)z[K], v[0]);
+    if (!first) v[1] = fma(r[K], (double)zold[K], v[1]);
+  }
+  __shared__ double out[2];
+  if (reduce_last<2>(v, part, &sc->cnt[1], out) && threadIdx.x == 0) {
+    sc->beta = first ? 0.0 : (out[0] - out[1]) / sc->rz;
+    sc->rz = out[0];
+  }
+}
+
+// p = z + beta p, q = A z + beta q (= A p), alpha = rz / (p, q); z is kept as z_old for the next beta.
+__global__ void k_pcg_pq(FineDev F, const double* __restrict__ Tval, const double* __restrict__ diagT,
+                         const float* __restrict__ z, float* __restrict__ zold, double* __restrict__ p,
+                         double* __restrict__ q, double* part, MgScal* sc) {
+  if (stop(&sc->done)) return;
+  const double beta = sc->beta;
+  const bool first = sc->it == 0;
+  double v[1] = {0.0};
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < F.N; K += gridDim.x * blockDim.x) {
+    const double az = amul<float>(F, Tval, diagT, z, K);
+    const double pk = first ? (double)z[K] : fma(beta, p[K], (double)z[K]);
+    const double qk = first ? az : fma(beta, q[K], az);
+    p[K] = pk;
+    q[K] = qk;
+    zold[K] = z[K];
+    v[0] = fma(pk, qk, v[0]);
+  }
+  __shared__ double out[1];
+  if (reduce_last<1>(v, part, &sc->cnt[2], out) && threadIdx.x == 0) sc->alpha = sc->rz / out[0];
+}
+
+// x += alpha p, r -= alpha q, r32 = r with the first smoothing step of the next V-cycle; ||S r||^2 decides: the
+// iteration stops (conditional value 0) at ||S r||^2 <= tol^2 ||S r_0||^2, at maxit, or on a non-finite value.
+__global__ void k_pcg_update(int N, const double* __restrict__ p, const double* __restrict__ q,
+                             const double* __restrict__ diagT, double* __restrict__ x, double* __restrict__ r,
+                             float* __restrict__ r32, const float* __restrict__ a0dinv, float* __restrict__ x0,
+                             float* __restrict__ d0, const float* __restrict__ lam, double* part, MgScal* sc,
+                             cudaGraphConditionalHandle h) {
+  if (stop(&sc->done)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0);
+    return;
+  }
+  const double alpha = sc->alpha;
+  float c1, c2;
+  cheb_coef(lam[0], 0, c1, c2);
+  double v[1] = {0.0};
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
+    x[K] = fma(alpha, p[K], x[K]);
+    const double ri = fma(-alpha, q[K], r[K]);
+    r[K] = ri;
+    r32[K] = (float)ri;
+    first_step0(K, (float)ri, a0dinv, c2, x0, d0);
+    v[0] = fma(ri * ri, 1.0 / diagT[K], v[0]);
+  }
+  __shared__ double out[1];
+  if (reduce_last<1>(v, part, &sc->cnt[3], out) && threadIdx.x == 0) {
+    sc->rr = out[0];
+    sc->it += 1;
+    const bool fin = isfinite(out[0]) && isfinite(alpha);
+    if (!fin) sc->bad = 1;
+    const int d = (!fin || out[0] <= sc->tol2 * sc->rr0 || sc->it >= sc->maxit) ? 1 : 0;
+    sc->done = d;
+    cudaGraphSetConditional(h, d ? 0 : 1);
+  }
+}
+
+// ---- BiCGStab (right-preconditioned) for J dx = bscale b with the Newton Jacobian (jd diagonal, Joff SELL) ------
+template <class T>
+__device__ __forceinline__ double jmul(const FineDev& F, const double* __restrict__ Joff,
+                                       const double* __restrict__ jd, const T* __restrict__ v, int K) {
+  const int w = F.sell_w[K >> 5];
+  int e = F.sell_off[K >> 5] + (K & 31);
+  double s = jd[K] * (double)v[K];
+  for (int j = 0; j < w; ++j, e += 32) s = fma(Joff[e], (double)v[F.nbr[e]], s);
+  return s;
+}
+
+// start: x = 0, r = rh = p = bscale b, rho = (rh, r), rr0 = ||W r||^2 (W the Jacobi weights' square roots);
+// r32 = p for the first V-cycle (p^ = B p).
+__global__ void k_bicg_init(int N, const double* __restrict__ b, double bscale, const double* __restrict__ wgt,
+                            double* __restrict__ x, double* __restrict__ r, double* __restrict__ rh,
+                            double* __restrict__ p, float* __restrict__ r32, const float* __restrict__ a0dinv,
+                            float* __restrict__ x0, float* __restrict__ d0, const float* __restrict__ lam,
+                            double* part, MgScal* sc) {
+  float c1, c2;
+  cheb_coef(lam[0], 0, c1, c2);
+  double v[2] = {0.0, 0.0};
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
+    const double ri = bscale * b[K];
+    x[K] = 0.0;
+    r[K] = ri;
+    rh[K] = ri;
+    p[K] = ri;
+    r32[K] = (float)ri;
+    first_step0(K, (float)ri, a0dinv, c2, x0, d0);
+    v[0] = fma(ri, ri, v[0]);
+    v[1] = fma(ri * ri, wgt[K], v[1]);
+  }
+  __shared__ double out[2];
+  if (reduce_last<2>(v, part, &sc->cnt[0], out) && threadIdx.x == 0) {
+    sc->rho = out[0];
+    sc->rr0 = out[1];
+    sc->rr = out[1];
+    sc->it = 0;
+    sc->done = !(out[1] > 0.0) ? 1 : 0;
+    sc->bad = isfinite(out[1]) ? 0 : 1;
+  }
+}
+
+// v = J p^ (p^ = B p from the V-cycle, kept in FP64 in pp); alpha = rho / (rh, v); s = r - alpha v, r32 = s with the
+// first smoothing step of the next V-cycle (s^ = B s).
+__global__ void k_bicg_v(FineDev F, const double* __restrict__ Joff, const double* __restrict__ jd,
+                         const float* __restrict__ zp, double* __restrict__ pp, double* __restrict__ v,
+                         const double* __restrict__ rh, double* part, MgScal* sc) {
+  if (stop(&sc->done)) return;
+  double a[1] = {0.0};
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < F.N; K += gridDim.x * blockDim.x) {
+    pp[K] = (double)zp[K];
+    const double vk = jmul<float>(F, Joff, jd, zp, K);
+    v[K] = vk;
+    a[0] = fma(rh[K], vk, a[0]);
+  }
+  __shared__ double out[1];
+  if (reduce_last<1>(a, part, &sc->cnt[1], out) && threadIdx.x == 0) sc->alpha = sc->rho / out[0];
+}
+__global__ void k_bicg_s(int N, const double* __restrict__ r, const double* __restrict__ v, double* __restrict__ s,
+                         float* __restrict__ r32, const float* __restrict__ a0dinv, float* __restrict__ x0,
+                         float* __restrict__ d0, const float* __restrict__ lam, MgScal* sc) {
+  if (stop(&sc->done)) return;
+  const double alpha = sc->alpha;
+  float c1, c2;
+  cheb_coef(lam[0], 0, c1, c2);
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
+    const double sk = fma(-alpha, v[K], r[K]);
+    s[K] = sk;
+    r32[K] = (float)sk;
+    first_step0(K, (float)sk, a0dinv, c2, x0, d0);
+  }
+}
+// t = J s^ (s^ = B s from the V-cycle), omega = (t, s) / (t, t).
+__global__ void k_bicg_t(FineDev F, const double* __restrict__ Joff, const double* __restrict__ jd,
+                         const float* __restrict__ zs, const double* __restrict__ s, double* __restrict__ t,
+                         double* part, MgScal* sc) {
+  if (stop(&sc->done)) return;
+  double a[2] = {0.0, 0.0};
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < F.N; K += gridDim.x * blockDim.x) {
+    const double tk = jmul<float>(F, Joff, jd, zs, K);
+    t[K] = tk;
+    a[0] = fma(tk, s[K], a[0]);
+    a[1] = fma(tk, tk, a[1]);
+  }
+  __shared__ double out[2];
+  if (reduce_last<2>(a, part, &sc->cnt[2], out) && threadIdx.x == 0) sc->omega = out[1] != 0.0 ? out[0] / out[1] : 0.0;
+}
+// x += alpha p^ + omega s^, r = s - omega t, rho_new = (rh, r), ||W r||^2; beta = (rho_new / rho)(alpha / omega).
+__global__ void k_bicg_x(int N, const double* __restrict__ pp, const float* __restrict__ zs,
+                         const double* __restrict__ s, const double* __restrict__ t, const double* __restrict__ rh,
+                         const double* __restrict__ wgt, double* __restrict__ x, double* __restrict__ r, double* part,
+                         MgScal* sc, cudaGraphConditionalHandle h) {
+  if (stop(&sc->done)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0);
+    return;
+  }
+  const double alpha = sc->alpha, omega = sc->omega;
+  double a[2] = {0.0, 0.0};
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
+    x[K] = fma(omega, (double)zs[K], fma(alpha, pp[K], x[K]));
+    const double rk = fma(-omega, t[K], s[K]);
+    r[K] = rk;
+    a[0] = fma(rh[K], rk, a[0]);
+    a[1] = fma(rk * rk, wgt[K], a[1]);
+  }
+  __shared__ double out[2];
+  if (reduce_last<2>(a, part, &sc->cnt[3], out) && threadIdx.x == 0) {
+    sc->rr = out[1];
+    sc->it += 1;
+    const bool fin = isfinite(out[1]) && isfinite(alpha) && isfinite(omega);
+    if (!fin) sc->bad = 1;
+    const bool breakdown = omega == 0.0 || sc->rho == 0.0;
+    sc->beta = breakdown ? 0.0 : (out[0] / sc->rho) * (alpha / omega);
+    sc->rho = out[0];
+    const int d = (!fin || breakdown || out[1] <= sc->tol2 * sc->rr0 || sc->it >= sc->maxit) ? 1 : 0;
+    sc->done = d;
+    cudaGraphSetConditional(h, d ? 0 : 1);
+  }
+}
+// p = r + beta (p - omega v), r32 = p with the first smoothing step of the next V-cycle.
+__global__ void k_bicg_p(int N, const double* __restrict__ r, const double* __restrict__ v, double* __restrict__ p,
+                         float* __restrict__ r32, const float* __restrict__ a0dinv, float* __restrict__ x0,
+                         float* __restrict__ d0, const float* __restrict__ lam, MgScal* sc) {
+  if (stop(&sc->done)) return;
+  const double beta = sc->beta, omega = sc->omega;
+  float c1, c2;
+  cheb_coef(lam[0], 0, c1, c2);
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
+    const double pk = fma(beta, fma(-omega, v[K], p[K]), r[K]);
+    p[K] = pk;
+    r32[K] = (float)pk;
+    first_step0(K, (float)pk, a0dinv, c2, x0, d0);
+  }
+}
+
+// z (FP32) -> out (FP64), and the start of a single application: r32 = b, first smoothing step.
+__global__ void k_apply_in(int N, const double* __restrict__ b, float* __restrict__ r32,
+                           const float* __restrict__ a0dinv, float* __restrict__ x0, float* __restrict__ d0,
+                           const float* __restrict__ lam) {
+  float c1, c2;
+  cheb_coef(lam[0], 0, c1, c2);
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
+    r32[K] = (float)b[K];
+    first_step0(K, (float)b[K], a0dinv, c2, x0, d0);
+  }
+}
+__global__ void k_apply_out(int N, const float* __restrict__ z, double* __restrict__ out) {
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) out[K] = (double)z[K];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------------------------
+// host: static structure
+
+int mg_levels_for(const Hierarchy& H) {
+  for (int L = 2; L <= (int)H.levels.size() && L <= kMgMaxLevels; ++L) {
+    const Level& C = H.levels[L - 1];
+    int mb = 0;
+    for (int c = 0; c < C.n_cells; ++c) mb = std::max(mb, C.m[c]);
+    if ((long)C.n_cells * mb <= kMgMaxCoarse) return L;
+  }
+  return 0;
+}
+
+bool mg_build_host(const FineMesh& fm, const Hierarchy& H, int levels, MgHost& M, std::string& err) {
+  if (levels < 2 || levels > (int)H.levels.size() || levels > kMgMaxLevels) {
+    err = "multigrid preconditioner: bad number of levels";
+    return false;
+  }
+  const int N = fm.n_cells;
+  M.L = levels;
+  M.N = N;
+  M.nc[0] = N;
+  M.mb[0] = 1;
+  for (int l = 1; l < levels; ++l) {
+    const Level& Lv = H.levels[l];
+    M.nc[l] = Lv.n_cells;
+    int mb = 1;
+    for (int c = 0; c < Lv.n_cells; ++c) mb = std::max(mb, Lv.m[c]);
+    if (mb > kMaxM) {
+      err = "multigrid preconditioner: more than 8 modes per cell";
+      return false;
+    }
+    M.mb[l] = mb;
+    M.mcnt[l] = Lv.m;
+  }
+  if ((long)M.nc[levels - 1] * M.mb[levels - 1] > kMgMaxCoarse) {
+    err = "multigrid preconditioner: the coarsest level has more than " + std::to_string(kMgMaxCoarse) +
+          " unknowns";
+    return false;
+  }
+  // fine SELL positions of each interior face from its first cell (the layout of the residual kernel), and the
+  // Dirichlet entry of each Dirichlet face
+  std::vector<int> deg(N, 0), dcount(N, 0), face_pos(fm.n_faces, -1), dir_pos(fm.n_faces, -1);
+  for (int f = 0; f < fm.n_faces; ++f) {
+    if (fm.bc[f] == 0) {
+      face_pos[f] = deg[fm.fk[f]];
+      ++deg[fm.fk[f]];
+      ++deg[fm.fl[f]];
+    } else if (fm.bc[f] == 1) {
+      dir_pos[f] = dcount[fm.fk[f]]++;
+    }
+  }
+  const int nsl = (N + 31) / 32;
+  std::vector<long> soff(nsl + 1, 0);
+  for (int s = 0; s < nsl; ++s) {
+    int w = 0;
+    for (int K = 32 * s; K < std::min(N, 32 * s + 32); ++K) w = std::max(w, deg[K]);
+    soff[s + 1] = soff[s] + 32L * w;
+  }
+  std::vector<int> doff(N + 1, 0);
+  for (int K = 0; K < N; ++K) doff[K + 1] = doff[K] + dcount[K];
+  // transfers (padded) and children
+  for (int l = 0; l + 1 < levels; ++l) {
+    const Transfer& T = H.transfers[l];
+    const Level& Lc = H.levels[l + 1];
+    const int mbf = M.mb[l], mbc = M.mb[l + 1];
+    const int ncf = M.nc[l];
+    M.agg[l] = T.agg_of;
+    M.ch_off[l] = T.agg_off;
+    M.ch[l] = T.agg_cells;
+    M.P[l].assign((size_t)ncf * mbf * mbc, 0.0f);
+    const Level& Lf = H.levels[l];
+    for (int a = 0; a < Lc.n_cells; ++a) {
+      const int ma = Lc.m[a];
+      int t = 0;
+      for (int k = T.agg_off[a]; k < T.agg_off[a + 1]; ++k) {
+        const int c = T.agg_cells[k];
+        const int mc = l == 0 ? 1 : Lf.m[c];
+        for (int u = 0; u < mc; ++u, ++t)
+          for (int j = 0; j < ma; ++j)
+            M.P[l][((size_t)c * mbf + u) * mbc + j] = (float)T.Pblk[T.pblk_off[a] + (size_t)t * ma + j];
+      }
+    }
+  }
+  // level 1: block pattern and contributions from the fine faces
+  {
+    const std::vector<int>& agg = H.transfers[0].agg_of;
+    const int nc = M.nc[1];
+    std::vector<std::map<int, std::vector<int4>>> rows(nc);
+    for (int a = 0; a < nc; ++a) rows[a][a];
+    for (int f = 0; f < fm.n_faces; ++f) {
+      if (fm.bc[f] == 0) {
+        const int K = fm.fk[f], Lc = fm.fl[f];
+        const int e = (int)(soff[K >> 5] + 32L * face_pos[f] + (K & 31));
+        const int a = agg[K], b = agg[Lc];
+        if (a == b) {
+          rows[a][a].push_back(make_int4(K, Lc, e, 0));
+        } else {
+          rows[a][a].push_back(make_int4(K, K, e, 1));
+          rows[b][b].push_back(make_int4(Lc, Lc, e, 1));
+          rows[a][b].push_back(make_int4(K, Lc, e, 2));
+          rows[b][a].push_back(make_int4(Lc, K, e, 2));
+        }
+      } else if (fm.bc[f] == 1) {
+        const int K = fm.fk[f];
+        rows[agg[K]][agg[K]].push_back(make_int4(K, doff[K] + dir_pos[f], 0, 3));
+      }
+    }
+    M.rowptr[1].assign(nc + 1, 0);
+    M.dpos[1].assign(nc, 0);
+    M.asm_off[1].push_back(0);
+    for (int a = 0; a < nc; ++a) {
+      for (auto& kv : rows[a]) {
+        if (kv.first == a) M.dpos[1][a] = (int)M.col[1].size();
+        M.col[1].push_back(kv.first);
+        for (const int4& t : kv.second) M.asm_list[1].push_back(t);
+        M.asm_off[1].push_back((int)M.asm_list[1].size());
+      }
+      M.rowptr[1][a + 1] = (int)M.col[1].size();
+    }
+    M.nblk[1] = (int)M.col[1].size();
+  }
+  // levels l >= 2: from the blocks of level l-1
+  for (int l = 2; l < levels; ++l) {
+    const std::vector<int>& agg = H.transfers[l - 1].agg_of;
+    const int nc = M.nc[l], ncf = M.nc[l - 1];
+    std::vector<std::map<int, std::vector<int4>>> rows(nc);
+    for (int a = 0; a < nc; ++a) rows[a][a];
+    for (int c = 0; c < ncf; ++c)
+      for (int q = M.rowptr[l - 1][c]; q < M.rowptr[l - 1][c + 1]; ++q) {
+        const int d = M.col[l - 1][q];
+        rows[agg[c]][agg[d]].push_back(make_int4(q, c, d, 0));
+      }
+    M.rowptr[l].assign(nc + 1, 0);
+    M.dpos[l].assign(nc, 0);
+    M.asm_off[l].push_back(0);
+    for (int a = 0; a < nc; ++a) {
+      for (auto& kv : rows[a]) {
+        if (kv.first == a) M.dpos[l][a] = (int)M.col[l].size();
+        M.col[l].push_back(kv.first);
+        for (const int4& t : kv.second) M.asm_list[l].push_back(t);
+        M.asm_off[l].push_back((int)M.asm_list[l].size());
+      }
+      M.rowptr[l][a + 1] = (int)M.col[l].size();
+    }
+    M.nblk[l] = (int)M.col[l].size();
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// host: enqueueing
+
+void mg_enqueue_setup(cudaStream_t st, const MgDev& M, const FineDev& F, const MgWork& W, const double* Tval,
+                      const double* diagT, const double* kap) {
+  cudaMemsetAsync(W.lam, 0, kMgMaxLevels * sizeof(float), st);
+  k_fine_vals<<<blocks_for(M.N, 4096), kT, 0, st>>>(F, Tval, diagT, W.a0off, W.a0diag, W.a0dinv, W.lam);
+  count_launch(1);
+  k_asm1<<<blocks_for((long)M.nblk[1] * 32, 65535), kT, 0, st>>>(M.nblk[1], M.mb[1], M.asm_off[1], M.asm_list[1],
+                                                                 M.P[0], Tval, kap, F.dir_ups, M.rowptr[1],
+                                                                 M.dpos[1], M.mcnt[1], W.aval[1]);
+  k_pad_diag<<<blocks_for(M.nc[1]), kT, 0, st>>>(M.nc[1], M.mb[1], M.dpos[1], M.mcnt[1], W.aval[1]);
+  count_launch(2);
+  for (int l = 2; l < M.L; ++l) {
+    k_asml<<<blocks_for((long)M.nblk[l] * 32, 65535), kT, 0, st>>>(M.nblk[l], M.mb[l], M.mb[l - 1], M.asm_off[l],
+                                                                   M.asm_list[l], M.P[l - 1], W.aval[l - 1],
+                                                                   W.aval[l]);
+    k_pad_diag<<<blocks_for(M.nc[l]), kT, 0, st>>>(M.nc[l], M.mb[l], M.dpos[l], M.mcnt[l], W.aval[l]);
+    count_launch(2);
+  }
+  for (int l = 1; l + 1 < M.L; ++l) {
+    k_block_inv<<<blocks_for(M.nc[l]), kT, 0, st>>>(M.nc[l], M.mb[l], M.rowptr[l], M.col[l], M.dpos[l], W.aval[l],
+                                                    W.dinv[l], W.lam + l);
+    count_launch(1);
+  }
+  const int C = M.L - 1, n = M.nc[C] * M.mb[C];
+  k_coarse_inv<<<1, 256, (size_t)(n * n + n) * sizeof(double), st>>>(M.nc[C], M.mb[C], M.rowptr[C], M.col[C],
+                                                                      W.aval[C], W.cinv);
+  count_launch(1);
+}
+
+// The V-cycle after the fused first step of level 0 (x[0][0], d[0] set from b[0]); returns the index of the level-0
+// buffer that holds z.
+int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const MgWork& W, const int* flag) {
+  const int L = M.L, C = L - 1;
+  int cur[kMgMaxLevels] = {0};
+  const int g0 = blocks_for(M.N, 4096);
+  // down
+  for (int k = 1; k < kMgDegFine; ++k) {
+    k_cheb0<<<g0, kT, 0, st>>>(F, W.a0off, W.a0diag, W.a0dinv, W.b[0], W.x[0][cur[0]], W.x[0][1 - cur[0]], W.d[0],
+                               W.lam, k, flag);
+    cur[0] ^= 1;
+  }
+  k_rr0<<<blocks_for((long)M.nc[1] * 32, 65535), kT, 0, st>>>(F, W.a0off, W.a0diag, W.b[0], W.x[0][cur[0]], M.P[0],
+                                                              M.ch_off[0], M.ch[0], M.nc[1], M.mb[1], W.b[1],
+                                                              W.dinv[1], W.x[1][0], W.d[1], W.lam, C > 1 ? 1 : 0,
+                                                              flag);
+  for (int l = 1; l < C; ++l) {
+    const int gl = blocks_for((long)M.nc[l] * kG, 65535);
+    for (int k = 1; k < kMgDegCoarse; ++k) {
+      k_chebl<<<gl, kT, 0, st>>>(M.nc[l], M.mb[l], M.rowptr[l], M.col[l], W.aval[l], W.dinv[l], W.b[l],
+                                 W.x[l][cur[l]], W.x[l][1 - cur[l]], W.d[l], W.lam, l, k, flag);
+      cur[l] ^= 1;
+    }
+    k_rrl<<<blocks_for((long)M.nc[l + 1] * 32, 65535), kT, 0, st>>>(
+        M.mb[l], M.rowptr[l], M.col[l], W.aval[l], W.b[l], W.x[l][cur[l]], M.P[l], M.ch_off[l], M.ch[l],
+        M.nc[l + 1], M.mb[l + 1], W.b[l + 1], W.dinv[l + 1], W.x[l + 1][0], W.d[l + 1], W.lam, l + 1,
+        l + 1 < C ? 1 : 0, flag);
+  }
+  k_coarse_solve<<<1, kMgMaxCoarse, 0, st>>>(M.nc[C] * M.mb[C], W.cinv, W.b[C], W.x[C][0], flag);
+  // up
+  for (int l = C - 1; l >= 1; --l) {
+    k_prol<<<blocks_for((long)M.nc[l] * M.mb[l]), kT, 0, st>>>(M.nc[l], M.mb[l], M.mb[l + 1], M.P[l], M.agg[l],
+                                                                W.x[l + 1][cur[l + 1]], W.x[l][cur[l]], flag);
+    const int gl = blocks_for((long)M.nc[l] * kG, 65535);
+    for (int k = 0; k < kMgDegCoarse; ++k) {
+      k_chebl<<<gl, kT, 0, st>>>(M.nc[l], M.mb[l], M.rowptr[l], M.col[l], W.aval[l], W.dinv[l], W.b[l],
+                                 W.x[l][cur[l]], W.x[l][1 - cur[l]], W.d[l], W.lam, l, k, flag);
+      cur[l] ^= 1;
+    }
+  }
+  k_pro0<<<g0, kT, 0, st>>>(M.N, M.mb[1], M.P[0], M.agg[0], W.x[1][cur[1]], W.x[0][cur[0]], flag);
+  for (int k = 0; k < kMgDegFine; ++k) {
+    k_cheb0<<<g0, kT, 0, st>>>(F, W.a0off, W.a0diag, W.a0dinv, W.b[0], W.x[0][cur[0]], W.x[0][1 - cur[0]], W.d[0],
+                               W.lam, k, flag);
+    cur[0] ^= 1;
+  }
+  return cur[0];
+}
+
+int mg_vcycle_kernels(const MgDev& M) {
+  const int C = M.L - 1;
+  return (kMgDegFine - 1) + 1 + (C - 1) * kMgDegCoarse + 1 + (C - 1) * (1 + kMgDegCoarse) + 1 + kMgDegFine;
+}
+
+namespace {
+
+// A graph with one conditional while node whose body is captured from `body(handle)`.
+template <class Body>
+cudaError_t capture_while(cudaStream_t st, Body&& body, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e == cudaSuccess) {
+      cudaGraph_t bg = np.conditional.phGraph_out[0];
+      e = cudaStreamBeginCaptureToGraph(st, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        body(h);
+        cudaError_t e2 = cudaStreamEndCapture(st, &bg);
+        e = e2 != cudaSuccess ? e2 : cudaGetLastError();
+      }
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+template <class Body>
+cudaError_t capture_plain(cudaStream_t st, Body&& body, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  body();
+  e = cudaStreamEndCapture(st, &g);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  return e;
+}
+
+}  // namespace
+
+// Preconditioned CG for A dx = -b (b = W.kb, FP64; dx -> W.kx) as two graphs: out[0] the start (x = 0, r = -b, first
+// V-cycle), out[1] the conditional while loop over the iterations (beta, p and q, x and r with the convergence test,
+// V-cycle). The tolerance and iteration cap are read from W.sc at run time.
+cudaError_t mg_capture_pcg(cudaStream_t st, const MgDev& M, const FineDev& F, MgWork& W, const double* Tval,
+                           const double* diagT, cudaGraphExec_t* out) {
+  const int gr = blocks_for(M.N, kMaxRedBlocks);
+  int zi = 0;
+  cudaError_t e = capture_plain(st, [&]() {
+    k_pcg_init<<<gr, kT, 0, st>>>(M.N, W.kb, -1.0, diagT, W.kx, W.kr, W.b[0], W.a0dinv, W.x[0][0], W.d[0], W.lam,
+                                  W.part, W.sc);
+    zi = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
+  }, &out[0]);
+  if (e != cudaSuccess) return e;
+  const float* z = W.x[0][zi];
+  return capture_while(st, [&](cudaGraphConditionalHandle h) {
+    k_pcg_beta<<<gr, kT, 0, st>>>(M.N, W.kr, z, W.z[0], W.part, W.sc);
+    k_pcg_pq<<<gr, kT, 0, st>>>(F, Tval, diagT, z, W.z[0], W.kp, W.kq, W.part, W.sc);
+    k_pcg_update<<<gr, kT, 0, st>>>(M.N, W.kp, W.kq, diagT, W.kx, W.kr, W.b[0], W.a0dinv, W.x[0][0], W.d[0], W.lam,
+                                    W.part, W.sc, h);
+    const int zj = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
+    (void)zj;
+  }, &out[1]);
+}
+
+// Right-preconditioned BiCGStab for J dx = -b (J: jd diagonal, Joff off-diagonal in the SELL layout; b = W.kb;
+// dx -> W.kx; stopping on ||W r|| with the weights in W.kv's companion wgt = W.ks before the start). out[0] the start
+// (with p^ = B p), out[1] the loop: v = J p^, s, s^ = B s, t = J s^, x and r with the test, p, p^ = B p.
+cudaError_t mg_capture_bicgstab(cudaStream_t st, const MgDev& M, const FineDev& F, MgWork& W, const double* jd,
+                                const double* Joff, const double* wgt, cudaGraphExec_t* out) {
+  const int gr = blocks_for(M.N, kMaxRedBlocks);
+  int zi = 0;
+  cudaError_t e = capture_plain(st, [&]() {
+    k_bicg_init<<<gr, kT, 0, st>>>(M.N, W.kb, -1.0, wgt, W.kx, W.kr, W.krh, W.kp, W.b[0], W.a0dinv, W.x[0][0],
+                                   W.d[0], W.lam, W.part, W.sc);
+    zi = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
+  }, &out[0]);
+  if (e != cudaSuccess) return e;
+  return capture_while(st, [&](cudaGraphConditionalHandle h) {
+    k_bicg_v<<<gr, kT, 0, st>>>(F, Joff, jd, W.x[0][zi], W.kpp, W.kv, W.krh, W.part, W.sc);
+    k_bicg_s<<<gr, kT, 0, st>>>(M.N, W.kr, W.kv, W.ks, W.b[0], W.a0dinv, W.x[0][0], W.d[0], W.lam, W.sc);
+    const int zs = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
+    k_bicg_t<<<gr, kT, 0, st>>>(F, Joff, jd, W.x[0][zs], W.ks, W.kt, W.part, W.sc);
+    k_bicg_x<<<gr, kT, 0, st>>>(M.N, W.kpp, W.x[0][zs], W.ks, W.kt, W.krh, wgt, W.kx, W.kr, W.part, W.sc, h);
+    k_bicg_p<<<gr, kT, 0, st>>>(M.N, W.kr, W.kv, W.kp, W.b[0], W.a0dinv, W.x[0][0], W.d[0], W.lam, W.sc);
+    const int zp = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
+    (void)zp;
+  }, &out[1]);
+}
+
+// One V-cycle z = B b for parity tests: b = W.kb (FP64) -> W.kx (FP64).
+cudaError_t mg_capture_apply(cudaStream_t st, const MgDev& M, const FineDev& F, MgWork& W, cudaGraphExec_t* out) {
+  return capture_plain(st, [&]() {
+    const int g0 = blocks_for(M.N, 4096);
+    k_apply_in<<<g0, kT, 0, st>>>(M.N, W.kb, W.b[0], W.a0dinv, W.x[0][0], W.d[0], W.lam);
+    const int zi = mg_enqueue_vcycle(st, M, F, W, nullptr);
+    k_apply_out<<<g0, kT, 0, st>>>(M.N, W.x[0][zi], W.kx);
+  }, out);
+}
+
+void mg_set_smem_limits() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_coarse_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (kMgMaxCoarse * kMgMaxCoarse + kMgMaxCoarse) * (int)sizeof(double));
+  done = true;
+}
+
+}  // namespace nlmg

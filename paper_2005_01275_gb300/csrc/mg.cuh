@@ -1,0 +1,107 @@
+// Linear multigrid preconditioner for the level-0 Krylov solves (mg.cu).
+//
+// Sec. 3.4 preconditions the fine-level Picard and Newton systems with AMG on the Schur complement, which on the
+// TPFA fine level is the frozen TPFA matrix A itself. Here one V-cycle on the pressure spaces of the spectral
+// hierarchy plays that role: Galerkin operators A_{l+1} = P_l^T A_l P_l (level 1 assembled face by face from the
+// fine transmissibilities, in the difference form that keeps the constant mode exact), Chebyshev smoothing
+// preconditioned by the (block) diagonal, a dense inverse on the coarsest level; FP32 throughout, inside the FP64
+// Krylov iteration. One Krylov solve runs as one CUDA graph whose iterations sit in a device-side conditional
+// while node, so no host round trip separates them.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "hier.hpp"
+#include "kernels.cuh"
+
+namespace nlmg {
+
+constexpr int kMgMaxLevels = 8;
+constexpr int kMgMaxCoarse = 128;   // largest coarsest-level system (unknowns, padded): dense inverse in one block
+constexpr int kMgDegFine = 2;       // Chebyshev steps before and after the coarse correction, level 0
+constexpr int kMgDegCoarse = 2;     // the same on levels 1 .. L-2
+constexpr double kMgAlpha = 4.0;    // Chebyshev interval [lam / alpha, lam]
+
+// Static structure of the preconditioner (host side, built once per hierarchy).
+struct MgHost {
+  int L = 0, N = 0;
+  int nc[kMgMaxLevels] = {0}, mb[kMgMaxLevels] = {0}, nblk[kMgMaxLevels] = {0};
+  std::vector<int> rowptr[kMgMaxLevels], col[kMgMaxLevels], dpos[kMgMaxLevels], mcnt[kMgMaxLevels];
+  std::vector<int> asm_off[kMgMaxLevels];
+  std::vector<int4> asm_list[kMgMaxLevels];
+  std::vector<float> P[kMgMaxLevels];                   // P[l]: transfer l -> l+1, padded
+  std::vector<int> agg[kMgMaxLevels], ch_off[kMgMaxLevels], ch[kMgMaxLevels];
+};
+
+// Device copy of MgHost (pointers owned by the shared part of a context).
+struct MgDev {
+  int L = 0, N = 0;
+  int nc[kMgMaxLevels] = {0}, mb[kMgMaxLevels] = {0}, nblk[kMgMaxLevels] = {0};
+  int *rowptr[kMgMaxLevels] = {nullptr}, *col[kMgMaxLevels] = {nullptr}, *dpos[kMgMaxLevels] = {nullptr},
+      *mcnt[kMgMaxLevels] = {nullptr};
+  int* asm_off[kMgMaxLevels] = {nullptr};
+  int4* asm_list[kMgMaxLevels] = {nullptr};
+  float* P[kMgMaxLevels] = {nullptr};
+  int *agg[kMgMaxLevels] = {nullptr}, *ch_off[kMgMaxLevels] = {nullptr}, *ch[kMgMaxLevels] = {nullptr};
+};
+
+// Device scalars of one Krylov solve (one struct per context).
+struct MgScal {
+  double alpha, beta, omega, rho, rz, rr0, rr, tol2;
+  int it, maxit, done, bad;
+  unsigned cnt[8];   // arrival counters of the reductions (each reset by its last block)
+};
+
+// Per-context work buffers.
+struct MgWork {
+  float *a0off = nullptr, *a0diag = nullptr, *a0dinv = nullptr;
+  float *aval[kMgMaxLevels] = {nullptr}, *dinv[kMgMaxLevels] = {nullptr};
+  float* cinv = nullptr;
+  float* lam = nullptr;                                  // [kMgMaxLevels] Gershgorin bounds
+  float *x[kMgMaxLevels][2] = {{nullptr}}, *b[kMgMaxLevels] = {nullptr}, *d[kMgMaxLevels] = {nullptr};
+  // Krylov vectors (FP64) and the preconditioned vectors (FP32)
+  double *kx = nullptr, *kr = nullptr, *kp = nullptr, *kq = nullptr, *kb = nullptr;
+  double *kv = nullptr, *ks = nullptr, *kt = nullptr, *krh = nullptr, *kpp = nullptr;   // BiCGStab
+  float *z[2] = {nullptr, nullptr};
+  double* part = nullptr;                                // partial sums of the reductions
+  MgScal* sc = nullptr;
+  MgScal* h_sc = nullptr;                                // pinned copy
+  cudaGraphExec_t g_pcg[2] = {nullptr, nullptr}, g_bicg[2] = {nullptr, nullptr}, g_apply = nullptr;
+};
+
+// Builds the preconditioner's structure on the first `levels` levels of H (levels <= H.levels.size()); the coarsest
+// of them must have at most kMgMaxCoarse padded unknowns. Returns false and sets err otherwise.
+bool mg_build_host(const FineMesh& fm, const Hierarchy& H, int levels, MgHost& M, std::string& err);
+
+// Number of levels of H (from level 0) the preconditioner uses: the smallest prefix whose coarsest level has at most
+// kMgMaxCoarse padded unknowns, or 0 if no prefix qualifies.
+int mg_levels_for(const Hierarchy& H);
+
+// Enqueues, on stream st, the per-Picard-step setup: FP32 fine values, Galerkin operators, block-diagonal inverses,
+// Gershgorin bounds and the coarsest inverse, from the frozen matrix (Tval, diagT) and kappa per cell.
+void mg_enqueue_setup(cudaStream_t st, const MgDev& M, const FineDev& F, const MgWork& W, const double* Tval,
+                      const double* diagT, const double* kap);
+
+// Enqueues one V-cycle z = B r on stream st for an FP32 right-hand side already in W.b[0] with the first pre-smoothing
+// step fused by the caller (x[0][0], d[0] hold it); returns the index i of the level-0 buffer W.x[0][i] that holds z;
+// `flag` (may be null) is a device int that makes every kernel return at once when non-zero.
+int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const MgWork& W, const int* flag);
+
+// Kernels in one V-cycle after its fused first step (for the launch counts of graph replays).
+int mg_vcycle_kernels(const MgDev& M);
+
+// The preconditioned Krylov solves as graphs captured once per context (out[0] the start, out[1] a conditional
+// while loop over the iterations; tolerance tol2 and cap maxit read from W.sc at run time), and one V-cycle for the
+// step calls. Right-hand side W.kb (the solve is for -W.kb), solution W.kx.
+cudaError_t mg_capture_pcg(cudaStream_t st, const MgDev& M, const FineDev& F, MgWork& W, const double* Tval,
+                           const double* diagT, cudaGraphExec_t* out);
+cudaError_t mg_capture_bicgstab(cudaStream_t st, const MgDev& M, const FineDev& F, MgWork& W, const double* jd,
+                                const double* Joff, const double* wgt, cudaGraphExec_t* out);
+cudaError_t mg_capture_apply(cudaStream_t st, const MgDev& M, const FineDev& F, MgWork& W, cudaGraphExec_t* out);
+
+// Raises the dynamic shared-memory limit of the coarsest-level inversion (once per process).
+void mg_set_smem_limits();
+
+}  // namespace nlmg

@@ -19,6 +19,7 @@
 #include "hier.hpp"
 #include "kernels.cuh"
 #include "eig.cuh"
+#include "mg.cuh"
 #include "noalloc.cuh"
 #include "persist.cuh"
 
@@ -86,6 +87,9 @@ struct Shared {
   double hyb_flops_per_iter[8] = {0}, hyb_flops_per_solve[8] = {0}, coarse_res_flops[8] = {0};
   // one trial evaluation from the linear parts (also the pass that accepts a trial): bytes and flops
   double coarse_trial_bytes[8] = {0}, coarse_trial_flops[8] = {0};
+  int n_fas = 0;        // levels the FAS cycles use (the hierarchy may hold more for the preconditioner)
+  MgDev MG;             // multigrid preconditioner structure (MG.L = 0: not built)
+  double mg_bytes_setup = 0, mg_bytes_vcycle = 0, mg_bytes_iter = 0;   // algorithmic bytes (see mg_accounting)
   ~Shared() {
     for (void* p : allocs) cudaFree(p);
   }
@@ -209,7 +213,8 @@ struct nlmg_ctx {
     v0 = h_sc[0];
     v1 = h_sc[1];
   }
-  int nlev() const { return (int)sh->H.levels.size(); }
+  int nlev() const { return sh->n_fas; }
+  MgWork mg;               // multigrid preconditioner work buffers and graphs (when sh->MG.L > 0)
 };
 
 namespace {
@@ -501,6 +506,57 @@ void upload_transfer(nlmg_ctx* c, int l) {
   D.qs_val = c->upload(T.Qs.val);
 }
 
+// The multigrid preconditioner's structure on the first `levels` levels (read-only, shared by instances), with the
+// algorithmic bytes of its phases: the per-step setup (fine values read and written, assembly contributions and the
+// coarse blocks written), one V-cycle (level 0: each Chebyshev step and the residual read the SELL values and indices,
+// b, x and write x, d; transfers read P; coarse levels the same with their blocks) and the Krylov vectors of one
+// iteration.
+void upload_mg(nlmg_ctx* c, int levels) {
+  MgHost mh;
+  std::string err;
+  if (!mg_build_host(c->fm(), c->H(), levels, mh, err)) throw Error(NLMG_EUNSUPPORTED, err);
+  MgDev& M = c->sh->MG;
+  M.L = mh.L;
+  M.N = mh.N;
+  for (int l = 0; l < mh.L; ++l) {
+    M.nc[l] = mh.nc[l];
+    M.mb[l] = mh.mb[l];
+    M.nblk[l] = mh.nblk[l];
+    if (l >= 1) {
+      M.rowptr[l] = c->upload(mh.rowptr[l]);
+      M.col[l] = c->upload(mh.col[l]);
+      M.dpos[l] = c->upload(mh.dpos[l]);
+      M.mcnt[l] = c->upload(mh.mcnt[l]);
+      M.asm_off[l] = c->upload(mh.asm_off[l]);
+      M.asm_list[l] = c->upload(mh.asm_list[l]);
+    }
+    if (l + 1 < mh.L) {
+      M.P[l] = c->upload(mh.P[l]);
+      M.agg[l] = c->upload(mh.agg[l]);
+      M.ch_off[l] = c->upload(mh.ch_off[l]);
+      M.ch[l] = c->upload(mh.ch[l]);
+    }
+  }
+  const double N = mh.N, nnz = (double)c->sh->nnz_real;
+  double setup = nnz * (8.0 + 4.0 + 4.0) + N * (8.0 + 12.0);   // Tval, indices read, FP32 values written; diagonals
+  double vc = 0.0;
+  const double fine_step = nnz * 8.0 + N * 20.0;                // SELL values + indices, b, x read, x, d written
+  vc += (2.0 * kMgDegFine) * fine_step + N * 4.0 * mh.mb[1] * 2.0;   // steps, residual; P read twice
+  for (int l = 1; l < mh.L; ++l) {
+    const double mm = (double)mh.mb[l] * mh.mb[l];
+    setup += (double)mh.asm_list[l].size() * 16.0 + mh.nblk[l] * mm * 4.0 * 2.0 + mh.nc[l] * mm * 4.0;
+    if (l + 1 < mh.L) {
+      const double cstep = mh.nblk[l] * (mm * 4.0 + 4.0) + mh.nc[l] * mm * 4.0 + mh.nc[l] * mh.mb[l] * 20.0;
+      vc += (2.0 * kMgDegCoarse) * cstep + mh.P[l].size() * 4.0 * 2.0;
+    } else {
+      vc += (double)mh.nc[l] * mh.mb[l] * mh.nc[l] * mh.mb[l] * 4.0;
+    }
+  }
+  c->sh->mg_bytes_setup = setup;
+  c->sh->mg_bytes_vcycle = vc;
+  c->sh->mg_bytes_iter = nnz * 12.0 + N * (8.0 * 10.0);   // A z (values, indices, z) and the FP64 vector updates
+}
+
 // ---------------------------------------------------------------------------------------------------------------
 // level 0
 
@@ -539,7 +595,11 @@ void backtrack0(nlmg_ctx* c, const double* dp, double s0) {
 // Persistent CG on the frozen fine matrix (Tval, diagT): A dx = -R with symmetric Jacobi scaling; dx -> c->cx.
 // lin_precision 0 runs it in FP64, 1 in FP32 (vectors and matrix; per-thread partial sums in FP32, block and grid
 // sums in FP64).
-int fine_pcg(nlmg_ctx* c, const double* R) {
+int mg_pcg(nlmg_ctx* c, const double* R, const double* kap);
+int mg_bicgstab(nlmg_ctx* c, const double* R, const double* kap);
+
+int fine_pcg(nlmg_ctx* c, const double* R, const double* kap) {
+  if (c->opt.lin_precond == 1) return mg_pcg(c, R, kap);
   GridSync gs{c->d_bar, &c->d_res->err, c->sm_cap};
   CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->st));
   CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
@@ -643,14 +703,16 @@ void newton_linearize(nlmg_ctx* c) {
   alloc_newton(c);
   const int N = c->F.N;
   launch_kappa(c->st, N, c->cur.p, nullptr, 0.0, c->cur.p, c->t2.kap, c->dkap, c->kind, c->a);
-  launch_residual(c->st, c->F, c->cur.p, c->t2.kap, c->dkap, c->g, c->rhs, c->t2.R, nullptr, nullptr, c->diagT,
-                  c->jdiag, c->red(S_NORM2B), c->Joff);
+  launch_residual(c->st, c->F, c->cur.p, c->t2.kap, c->dkap, c->g, c->rhs, c->t2.R,
+                  c->opt.lin_precond == 1 ? c->Tval : nullptr, nullptr, c->diagT, c->jdiag, c->red(S_NORM2B),
+                  c->Joff);
   launch_jacobi_dinv(c->st, N, c->jdiag, c->diagT, c->jdinv);
 }
 
 // Persistent FP64 BiCGStab on the Jacobi-scaled Newton system J dx = -R (J from newton_linearize) to newton_tol_eff;
 // dx -> c->cx.
 int fine_bicgstab(nlmg_ctx* c, const double* R) {
+  if (c->opt.lin_precond == 1) return mg_bicgstab(c, R, c->t2.kap);
   GridSync gs{c->d_bar, &c->d_res->err, c->sm_cap};
   CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->st));
   CK(cudaMemsetAsync(c->d_res, 0, sizeof(PcgResult), c->st));
@@ -807,7 +869,7 @@ void smooth0(nlmg_ctx* c, int nu) {
   } else if (o.smoother == NLMG_SMOOTH_PICARD || o.smoother == NLMG_SMOOTH_PICARD_NEWTON) {
     launch_residual(c->st, c->F, c->cur.p, c->cur.kap, nullptr, c->g, c->rhs, c->t2.R, c->Tval, c->dinv, c->diagT,
                     nullptr, c->red(S_NORM2B));
-    fine_pcg(c, c->cur.R);
+    fine_pcg(c, c->cur.R, c->cur.kap);
     dp = c->cx;
   } else {
     // nu sweeps q <- q - omega R(q) / max(J_qq, d_q / 2) from q = p, then dp = q - p
@@ -1038,6 +1100,108 @@ void alloc_fine(nlmg_ctx* c) {
   }
 }
 
+// Work buffers of the multigrid preconditioner (when the shared part holds one).
+void alloc_mg(nlmg_ctx* c) {
+  const MgDev& M = c->sh->MG;
+  if (M.L == 0) return;
+  MgWork& W = c->mg;
+  const int N = c->F.N;
+  W.a0off = c->dalloc<float>(c->F.nnz);
+  W.a0diag = c->dalloc<float>(N);
+  W.a0dinv = c->dalloc<float>(N);
+  for (int l = 0; l < M.L; ++l) {
+    const size_t n = l == 0 ? (size_t)N : (size_t)M.nc[l] * M.mb[l];
+    W.x[l][0] = c->dalloc<float>(n);
+    W.x[l][1] = c->dalloc<float>(n);
+    W.b[l] = c->dalloc<float>(n);
+    W.d[l] = c->dalloc<float>(n);
+    if (l >= 1) {
+      W.aval[l] = c->dalloc<float>((size_t)M.nblk[l] * M.mb[l] * M.mb[l]);
+      W.dinv[l] = c->dalloc<float>((size_t)M.nc[l] * M.mb[l] * M.mb[l]);
+    }
+  }
+  const int nco = M.nc[M.L - 1] * M.mb[M.L - 1];
+  W.cinv = c->dalloc<float>((size_t)nco * nco);
+  W.lam = c->dalloc<float>(kMgMaxLevels);
+  W.kx = c->cx;
+  W.z[0] = c->dalloc<float>(N);
+  for (double** pp : {&W.kr, &W.kp, &W.kq, &W.kb, &W.kv, &W.ks, &W.kt, &W.krh, &W.kpp}) *pp = c->dalloc<double>(N);
+  W.part = c->dalloc<double>((size_t)2 * 1024);
+  W.sc = c->dalloc<MgScal>(1);
+  CK(cudaMemsetAsync(W.sc, 0, sizeof(MgScal), c->st));
+  CK(cudaMallocHost(&W.h_sc, sizeof(MgScal)));
+  mg_set_smem_limits();
+}
+
+// Reads the scalars of the last multigrid Krylov solve; throws on a non-finite value.
+int mg_finish(nlmg_ctx* c, const char* what) {
+  MgWork& W = c->mg;
+  CK(cudaMemcpyAsync(W.h_sc, W.sc, sizeof(MgScal), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (W.h_sc->bad) throw Error(NLMG_EDIVERGED, std::string("non-finite value in the level-0 ") + what);
+  return W.h_sc->it;
+}
+
+// Tolerance and iteration cap of the next multigrid Krylov solve (read by its graphs on the device).
+void mg_set_limits(nlmg_ctx* c, double tol) {
+  MgWork& W = c->mg;
+  W.h_sc->tol2 = tol * tol;
+  W.h_sc->maxit = c->opt.lin_maxit;
+  CK(cudaMemcpyAsync(&W.sc->tol2, &W.h_sc->tol2, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(&W.sc->maxit, &W.h_sc->maxit, sizeof(int), cudaMemcpyHostToDevice, c->st));
+}
+
+// Level-0 Picard system A(kappa(p)) dx = -R (A from the last residual launch with Tval / diagT; kappa per cell in
+// kap for the Dirichlet terms of the Galerkin operators) by CG preconditioned with one multigrid V-cycle; dx -> c->cx.
+// Stops at ||S r|| <= lin_tol ||S r_0|| (S = diag(A)^-1/2, the test of the Jacobi-preconditioned CG) or lin_maxit.
+int mg_pcg(nlmg_ctx* c, const double* R, const double* kap) {
+  const MgDev& M = c->sh->MG;
+  MgWork& W = c->mg;
+  const int pi = c->prof_begin(5);
+  mg_enqueue_setup(c->st, M, c->F, W, c->Tval, c->diagT, kap);
+  CK(cudaMemcpyAsync(W.kb, R, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  mg_set_limits(c, c->lin_tol_eff);
+  if (!W.g_pcg[0]) CK(mg_capture_pcg(c->st, M, c->F, W, c->Tval, c->diagT, W.g_pcg));
+  CK(cudaGraphLaunch(W.g_pcg[0], c->st));
+  CK(cudaGraphLaunch(W.g_pcg[1], c->st));
+  c->prof_end(pi);
+  const int it = mg_finish(c, "multigrid-preconditioned CG");
+  const int V = mg_vcycle_kernels(M);
+  count_launch(1 + V + (it + 1) * (3 + V));
+  if (pi >= 0) {
+    c->prof.bytes[5] += c->sh->mg_bytes_setup + (double)(it + 1) * (c->sh->mg_bytes_vcycle + c->sh->mg_bytes_iter);
+  }
+  c->lin_iters += it;
+  c->lin_iters_level[0] += it;
+  return it;
+}
+
+// Level-0 Newton system J dx = -R (J from newton_linearize, preconditioner from the Picard matrix at the same point)
+// by right-preconditioned BiCGStab with one V-cycle per preconditioning; stops at ||W r|| <= newton_lin_tol ||W r_0||
+// with W^2 = 1 / max(J_KK, d_K / 2), the test of the Jacobi-scaled BiCGStab; dx -> c->cx.
+int mg_bicgstab(nlmg_ctx* c, const double* R, const double* kap) {
+  const MgDev& M = c->sh->MG;
+  MgWork& W = c->mg;
+  const int pi = c->prof_begin(6);
+  mg_enqueue_setup(c->st, M, c->F, W, c->Tval, c->diagT, kap);
+  CK(cudaMemcpyAsync(W.kb, R, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  mg_set_limits(c, c->newton_tol_eff);
+  if (!W.g_bicg[0]) CK(mg_capture_bicgstab(c->st, M, c->F, W, c->jdiag, c->Joff, c->jdinv, W.g_bicg));
+  CK(cudaGraphLaunch(W.g_bicg[0], c->st));
+  CK(cudaGraphLaunch(W.g_bicg[1], c->st));
+  c->prof_end(pi);
+  const int it = mg_finish(c, "multigrid-preconditioned BiCGStab");
+  const int V = mg_vcycle_kernels(M);
+  count_launch(1 + V + it * (5 + 2 * V));
+  if (pi >= 0) {
+    c->prof.bytes[6] += c->sh->mg_bytes_setup + (double)(2 * it + 1) * c->sh->mg_bytes_vcycle +
+                        (double)it * 2.0 * c->sh->mg_bytes_iter;
+  }
+  c->lin_iters += it;
+  c->lin_iters_level[0] += it;
+  return it;
+}
+
 nlmg_status fail(nlmg_ctx* c, nlmg_status s, const std::string& m) {
   if (c) c->err = m;
   return s;
@@ -1210,7 +1374,7 @@ static thread_local std::string g_setup_error;   // message of the calling threa
 
 // The options a solve reads (those fixed at setup are checked there).
 static bool solver_options_ok(const nlmg_options& o) {
-  return o.nu_pre >= 0 && o.nu_post >= 0 && o.bt_nmax >= 0 && o.omega > 0 && o.coarsest_steps >= 0 &&
+  return (o.lin_precond == 0 || o.lin_precond == 1) && o.nu_pre >= 0 && o.nu_post >= 0 && o.bt_nmax >= 0 && o.omega > 0 && o.coarsest_steps >= 0 &&
          (o.lin_precision == 0 || o.lin_precision == 1) && o.max_sms >= 0 && o.smoother >= NLMG_SMOOTH_PICARD &&
          o.smoother <= NLMG_SMOOTH_PICARD_NEWTON && o.newton_switch >= 0.0 && o.newton_lin_tol > 0.0 &&
          (o.cascadic == 0 || o.cascadic == 1);
@@ -1244,6 +1408,7 @@ static void init_work(nlmg_ctx* c) {
   CK(cudaMemsetAsync(c->d_sc, 0, 64 * sizeof(double), c->st));
   c->reset_inner_tols();
   alloc_fine(c);
+  alloc_mg(c);
   c->CB.resize(c->nlev());
   for (int l = 1; l < c->nlev(); ++l) alloc_level(c, l);
   CK(cudaStreamSynchronize(c->st));
@@ -1304,8 +1469,32 @@ static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, co
       ho.gpu_eig = true;
       ho.eig_fn = batched_smallest_eig;
     }
+    // the multigrid preconditioner wants a coarsest level of at most kMgMaxCoarse pressure unknowns: coarsen further
+    // (aggregates of agg_size[l] cells, the last FAS step's modes, one flux unknown per interface) for it alone
+    if (opt->lin_precond == 1) {
+      const int mlast = opt->n_levels >= 2 ? opt->modes[opt->n_levels - 2] : opt->modes[0];
+      ho.n_levels = std::min(8, opt->n_levels + 4);
+      for (int l = opt->n_levels - 1; l < 8; ++l) {
+        if (l < 0) continue;
+        if (ho.agg_size[l] < 2) ho.agg_size[l] = 8;
+        ho.modes[l] = std::max(1, std::min(kMaxM, mlast));
+        ho.flux_modes[l] = 1;
+      }
+    }
     std::string err;
     if (!build_hierarchy(fm, ho, c->H(), err)) throw Error(NLMG_EINVAL, err);
+    Hierarchy& H = c->H();
+    int mg_levels = 0;
+    if (opt->lin_precond == 1) {
+      mg_levels = mg_levels_for(H);
+      if (mg_levels < 2)
+        throw Error(NLMG_EUNSUPPORTED, "lin_precond = 1: no coarse level of at most " +
+                                           std::to_string(kMgMaxCoarse) + " pressure unknowns within 8 levels");
+      const int keep = std::max(opt->n_levels, mg_levels);
+      H.levels.resize(keep);
+      H.transfers.resize(keep - 1);
+    }
+    c->sh->n_fas = opt->n_levels;
     if (!device) return NLMG_OK;
     CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
     upload_fine(c);
@@ -1313,6 +1502,7 @@ static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, co
     c->TD.resize(std::max(0, c->nlev() - 1));
     for (int l = 1; l < c->nlev(); ++l) upload_level(c, l);
     for (int l = 0; l + 1 < c->nlev(); ++l) upload_transfer(c, l);
+    if (mg_levels >= 2) upload_mg(c, mg_levels);
     c->sh->F = c->F;
     c->sh->LD = c->LD;
     c->sh->TD = c->TD;
@@ -1410,6 +1600,8 @@ nlmg_status nlmg_set_options(nlmg_ctx* c, const nlmg_options* opt) {
           opt->flux_modes[l] != c->opt.flux_modes[l])
         throw Error(NLMG_EINVAL, "agg_size, modes and flux_modes are fixed at setup");
     if (!solver_options_ok(*opt)) throw Error(NLMG_EINVAL, "bad solver option");
+    if (opt->lin_precond == 1 && c->sh->MG.L == 0)
+      throw Error(NLMG_EINVAL, "lin_precond = 1 needs a context set up with lin_precond = 1");
     const int threads = c->opt.setup_threads;
     c->opt = *opt;
     c->opt.setup_threads = threads;
@@ -1661,7 +1853,7 @@ nlmg_status nlmg_picard_update(nlmg_ctx* c, int32_t level, const double* x, cons
       fine_eval(c, c->cpa, nullptr, 0.0, c->t1);
       launch_residual(c->st, c->F, c->t1.p, c->t1.kap, nullptr, c->g, c->rhs, c->t2.R, c->Tval, c->dinv, c->diagT,
                       nullptr, c->red(S_NORM2B));
-      it = fine_pcg(c, c->t1.R);
+      it = fine_pcg(c, c->t1.R, c->t1.kap);
       CK(cudaMemcpyAsync(dx_out, c->cx, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     } else {
       const LevelDev& L = c->LD[level];
@@ -1678,6 +1870,29 @@ nlmg_status nlmg_picard_update(nlmg_ctx* c, int32_t level, const double* x, cons
     }
     CK(cudaStreamSynchronize(c->st));
     if (iters) *iters = it;
+    return NLMG_OK;
+  });
+}
+
+nlmg_status nlmg_precond_apply(nlmg_ctx* c, const double* p, const double* r, double* z_out) {
+  return guarded(c, [&]() -> nlmg_status {
+    need_data(c);
+    if (!p || !r || !z_out) throw Error(NLMG_EINVAL, "null argument");
+    if (c->sh->MG.L == 0) throw Error(NLMG_EINVAL, "the context was not set up with lin_precond = 1");
+    const MgDev& M = c->sh->MG;
+    MgWork& W = c->mg;
+    const size_t N = (size_t)c->F.N;
+    CK(cudaMemcpyAsync(c->cpa, p, N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    fine_eval(c, c->cpa, nullptr, 0.0, c->t1);
+    launch_residual(c->st, c->F, c->t1.p, c->t1.kap, nullptr, c->g, c->rhs, c->t2.R, c->Tval, c->dinv, c->diagT,
+                    nullptr, c->red(S_NORM2B));
+    mg_enqueue_setup(c->st, M, c->F, W, c->Tval, c->diagT, c->t1.kap);
+    CK(cudaMemcpyAsync(W.kb, r, N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    if (!W.g_apply) CK(mg_capture_apply(c->st, M, c->F, W, &W.g_apply));
+    CK(cudaGraphLaunch(W.g_apply, c->st));
+    count_launch(2 + mg_vcycle_kernels(M));
+    CK(cudaMemcpyAsync(z_out, W.kx, N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
     return NLMG_OK;
   });
 }
@@ -1790,7 +2005,7 @@ nlmg_status nlmg_profile_read(nlmg_ctx* c, int32_t kernel, int64_t* launches, do
                               double* bytes_per_launch, double* flops_per_launch) {
   return guarded(c, [&]() -> nlmg_status {
     need_device(c);
-    if (kernel < 0 || kernel > 4) throw Error(NLMG_EINVAL, "kernel id");
+    if (kernel < 0 || kernel > 6) throw Error(NLMG_EINVAL, "kernel id");
     c->prof_flush();
     if (launches) *launches = c->prof.n[kernel];
     if (total_ms) *total_ms = c->prof.ms[kernel];
@@ -1877,6 +2092,9 @@ void nlmg_destroy(nlmg_ctx* c) {
   if (c->h_sc) cudaFreeHost(c->h_sc);
   if (c->h_res) cudaFreeHost(c->h_res);
   if (c->h_gh) cudaFreeHost(c->h_gh);
+  if (c->mg.h_sc) cudaFreeHost(c->mg.h_sc);
+  for (cudaGraphExec_t g : {c->mg.g_pcg[0], c->mg.g_pcg[1], c->mg.g_bicg[0], c->mg.g_bicg[1], c->mg.g_apply})
+    if (g) cudaGraphExecDestroy(g);
   if (c->st) cudaStreamDestroy(c->st);
   delete c;
 }

@@ -41,7 +41,7 @@ class Options(C.Structure):
                 ("coarse_lin_tol", C.c_double), ("lin_precision", C.c_int32),
                 ("setup_threads", C.c_int32), ("max_sms", C.c_int32), ("newton_switch", C.c_double),
                 ("newton_lin_tol", C.c_double), ("coarsest_lin_tol", C.c_double), ("flux_modes", C.c_int32 * 8),
-                ("cascadic", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("cascadic", C.c_int32), ("lin_precond", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class Report(C.Structure):
@@ -100,6 +100,7 @@ SIGNATURES = {
     "nlmg_transfer": (C.c_int, [_P, C.c_int32, C.c_int32, _D, _D]),
     "nlmg_picard_update": (C.c_int, [_P, C.c_int32, _D, _D, _D, _I]),
     "nlmg_newton_update": (C.c_int, [_P, _D, _D, _I]),
+    "nlmg_precond_apply": (C.c_int, [_P, _D, _D, _D]),
     "nlmg_vcycle": (C.c_int, [_P, _D, C.c_double, _D, _D, _I]),
     "nlmg_level_info_get": (C.c_int, [_P, C.c_int32, C.POINTER(LevelInfo)]),
     "nlmg_get_aggregates": (C.c_int, [_P, C.c_int32, _I, _I]),
@@ -172,7 +173,7 @@ def options_from_dict(d):
     keep = {k: d[k] for k in ("n_levels", "agg_size", "modes", "nu_pre", "nu_post", "omega", "bt_nmax", "bt_theta",
                               "dp_clamp", "coarsest_steps", "coarsest_tol", "lin_tol", "lin_maxit", "coarse_lin_tol",
                               "lin_precision", "max_sms", "newton_switch", "newton_lin_tol", "coarsest_lin_tol",
-                              "setup_threads", "flux_modes", "cascadic") if k in d}
+                              "setup_threads", "flux_modes", "cascadic", "lin_precond") if k in d}
     if "lin_tol" in d and "coarse_lin_tol" not in d:
         keep["coarse_lin_tol"] = d["lin_tol"]       # one tolerance given: use it on every level
     if "lin_tol" in d and "newton_lin_tol" not in d:
@@ -347,6 +348,14 @@ class Context:
         it = C.c_int32(0)
         self._check(lib().nlmg_newton_update(self.h, _dp(p), _dp(out), C.byref(it)))
         return out, it.value
+
+    def precond_apply(self, p, r):
+        """z = B r, one V-cycle of the level-0 multigrid preconditioner at the frozen matrix A(kappa(p))."""
+        p = _f64(p, self.n_cells)
+        r = _f64(r, self.n_cells)
+        out = np.zeros_like(p)
+        self._check(lib().nlmg_precond_apply(self.h, _dp(p), _dp(r), _dp(out)))
+        return out
 
     def vcycle(self, p, r0):
         p = _f64(p, self.n_cells)

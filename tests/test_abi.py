@@ -107,3 +107,18 @@ def test_flux_modes_option_range(nlmg_lib):
     assert c2.level_info(1)["n_flux"] > c1.level_info(1)["n_flux"]
     c1.close()
     c2.close()
+
+
+def test_multigrid_preconditioner_option_builds_its_extra_levels(nlmg_lib):
+    """lin_precond = 1 is a hierarchy option: the host setup coarsens beyond n_levels for the preconditioner alone
+    (the exported FAS levels are unchanged) and rejects an unknown value."""
+    pr = problem_config("chan3d_64", scale=12)
+    opts = dict(pr.opts, n_levels=2, agg_size=[27, 8], modes=[4, 4])
+    base = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, opts, device=False)
+    mg = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, dict(opts, lin_precond=1), device=False)
+    for l in range(2):
+        assert base.level_info(l) == mg.level_info(l)
+    with pytest.raises(nlmg_lib.NlmgError):
+        mg.level_info(2)
+    with pytest.raises(nlmg_lib.NlmgError):
+        nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, dict(opts, lin_precond=2), device=False)
