@@ -43,7 +43,11 @@ KERNELS = {0: ("kp_fine_cg_reg<double, 4> (persistent register-resident pipeline
                "Picard step)", "kp_fine_cg* (level-0 Picard CG)"),
            1: ("kp_coarse_step<double> (fused coarse Picard step: coarse operator evaluations, pipelined hybridized "
                "CG, clamp and Algorithm 1 in one persistent launch)",) * 2,
-           3: ("kp_fine_bicgstab (persistent FP64 BiCGStab of the level-0 Newton step)",) * 2}
+           3: ("kp_fine_bicgstab (persistent FP64 BiCGStab of the level-0 Newton step)",) * 2,
+           5: ("level-0 CG preconditioned by the multigrid V-cycle (per-step Galerkin setup, then one CUDA graph "
+               "with a device-side while loop: FP64 CG vectors, FP32 V-cycle kernels)",) * 2,
+           6: ("level-0 BiCGStab of the Newton step preconditioned by the multigrid V-cycle (setup and CUDA "
+               "graphs as for the CG)",) * 2}
 
 
 def roofline(prof, dev_ms, fp64_peak, hbm_peak, hbm_kind, default_case):
@@ -53,14 +57,23 @@ def roofline(prof, dev_ms, fp64_peak, hbm_peak, hbm_kind, default_case):
     beside it."""
     def add(a, b):
         return tuple(x + y for x, y in zip(a, b))
-    kern = {0: prof[0], 1: add(prof[1], prof[4]), 3: prof[3]}
+    kern = {0: prof[0], 1: add(prof[1], prof[4]), 3: prof[3], 5: prof[5], 6: prof[6]}
     kid = max((k for k in kern if kern[k][0]), key=lambda k: kern[k][1])
     n, ms, by, fl = kern[kid]
     avg_ms = ms / n
     gfs = fl / (avg_ms / 1e3) / 1e9
     gbs = by / (avg_ms / 1e3) / 1e9
     traffic = DRAM_BYTES_64.get(kid) if default_case else None
-    out = {"bound": "alu", "kernel": KERNELS[kid][0 if default_case else 1], "achieved": gfs, "peak": fp64_peak,
+    if kid in (5, 6):   # memory-streaming FP32 kernels: the HBM roofline
+        out = {"bound": "hbm", "kernel": KERNELS[kid][0], "achieved": gbs, "peak": hbm_peak, "peak_kind": hbm_kind,
+               "unit": "GB/s", "frac": gbs / hbm_peak, "traffic": None,
+               "traffic_note": "no capture of this kernel in this configuration", "bytes_per_launch": by,
+               "avg_launch_us": avg_ms * 1e3, "launches": n, "share_of_solve": ms / dev_ms if dev_ms else None,
+               "others": {}}
+    else:
+        out = None
+    if out is None:
+      out = {"bound": "alu", "kernel": KERNELS[kid][0 if default_case else 1], "achieved": gfs, "peak": fp64_peak,
            "peak_kind": "measured FP64 FMA throughput (nlmg_measure_fp64, independent FMA chains)",
            "unit": "GFLOP/s", "frac": gfs / fp64_peak, "traffic": traffic,
            "traffic_note": "DRAM read + write bytes per launch from ncu captures of this kernel on this workload" if
@@ -69,8 +82,8 @@ def roofline(prof, dev_ms, fp64_peak, hbm_peak, hbm_kind, default_case):
            "memory_view": {"achieved_GBs": gbs, "peak_GBs": hbm_peak, "peak_kind": hbm_kind, "frac": gbs / hbm_peak},
            "share_of_solve": ms / dev_ms if dev_ms else None, "others": {}}
     names = {0: "level0_cg", 1: "kp_coarse_step_intermediate_levels", 2: "k_residual", 3: "kp_fine_bicgstab",
-             4: "kp_coarse_step_coarsest_solve"}
-    for k in (0, 1, 2, 3, 4):
+             4: "kp_coarse_step_coarsest_solve", 5: "level0_mg_pcg", 6: "level0_mg_bicgstab"}
+    for k in (0, 1, 2, 3, 4, 5, 6):
         if k == kid or not prof[k][0]:
             continue
         n, ms, by, fl = prof[k]
@@ -376,7 +389,7 @@ def run_voronoi(nlmg, n_side, steps, smoother, fp64_peak=None, hbm_peak=None, hb
             p, rep, st = ctx.solve(pr.f_cell, pr.g_face, max_cycles=80)
             ms.append(rep["solve_ms"])
         if key == "fp64":
-            prof = {k: ctx.profile_read(k) for k in (0, 1, 2, 3, 4)}
+            prof = {k: ctx.profile_read(k) for k in (0, 1, 2, 3, 4, 5, 6)}
             ctx.profile(False)
             if fp64_peak:
                 out["roofline"] = roofline(prof, float(np.sum(ms)), fp64_peak, hbm_peak, hbm_kind, False)
@@ -512,7 +525,7 @@ def run_gpu(args, rank, world, local_rank):
             dist.barrier()
         wall = time.perf_counter() - w0
     clocks = clk.summary()
-    prof = {k: ctx.profile_read(k) for k in (0, 1, 2, 3, 4)}
+    prof = {k: ctx.profile_read(k) for k in (0, 1, 2, 3, 4, 5, 6)}
     ctx.profile(False)
     dev_ms = max_over_ranks(sum(r["solve_ms"] for r in reps), dist, dev)
     picard = None

@@ -324,7 +324,8 @@ void nlmg_server_destroy(nlmg_server* srv);
  * on the levels between the finest and the coarsest, 2 = fine TPFA residual (k_residual), 3 = persistent fine
  * BiCGStab of the Newton smoothing steps (kp_fine_bicgstab), 4 = kp_coarse_step on the coarsest level (the whole
  * coarsest solve in one launch), 5 = a level-0 CG solve preconditioned by the multigrid V-cycle (lin_precond = 1:
- * its setup and its graph launches), 6 = the same for a Newton step's BiCGStab. */
+ * its graph launches), 6 = the same for a Newton step's BiCGStab, 7 = the multigrid setup of one such solve (FP32
+ * fine values, Galerkin operators, block inverses, coarsest inverse). */
 nlmg_status nlmg_profile(nlmg_ctx* ctx, int32_t enable);
 /* Launch count, summed event time, algorithmic bytes per launch (each streamed array counted once; the gathered
  * neighbour values counted once) and arithmetic per launch (FMA = 2 flops; every kernel but 2) of a profiled kernel

@@ -20,7 +20,6 @@ namespace {
 
 constexpr int kT = 256;               // threads per block of the preconditioner kernels
 constexpr int kMaxRedBlocks = 1024;   // grid cap of the reduction kernels (partials summed by one block)
-constexpr int kG = 8;                 // lanes per cell in the block kernels (block size <= kMaxM = 8)
 
 inline int blocks_for(long n, int cap = 1 << 20) {
   long b = (n + kT - 1) / kT;
@@ -109,6 +108,20 @@ __device__ __forceinline__ void cheb_coef(float lam, int k, float& c1, float& c2
 
 __device__ __forceinline__ bool stop(const int* done) { return done && *((volatile const int*)done) != 0; }
 
+// Programmatic dependent launch: wait until the preceding kernel of the stream (or graph edge) has finished and its
+// writes are visible, then let the next kernel start its launch (it waits the same way before it reads anything).
+// Without a programmatic predecessor the wait returns at once.
+__device__ __forceinline__ void pdl_start() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
 // ---------------------------------------------------------------------------------------------------------------
 // setup kernels (once per frozen matrix)
 
@@ -117,6 +130,7 @@ __device__ __forceinline__ bool stop(const int* done) { return done && *((volati
 __global__ void k_fine_vals(FineDev F, const double* __restrict__ Tval, const double* __restrict__ diagT,
                             float* __restrict__ a0off, float* __restrict__ a0diag, float* __restrict__ a0dinv,
                             float* lam) {
+  pdl_start();
   float g = 0.0f;
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < F.N; K += gridDim.x * blockDim.x) {
     const int w = F.sell_w[K >> 5];
@@ -137,68 +151,67 @@ __global__ void k_fine_vals(FineDev F, const double* __restrict__ Tval, const do
   if ((threadIdx.x & 31) == 0) atomic_max_pos(&lam[0], g);
 }
 
-// Level-1 Galerkin blocks from the fine faces, one warp per block, lane t owning entries t and t + 32 of the
-// mb x mb block. Contributions (K, L, e, type): 0 interior face inside the aggregate, T (P_K - P_L)(P_K - P_L)^T;
-// 1 face to another aggregate seen from this one's cell K, T P_K P_K^T; 2 the off-diagonal part, -T P_K P_L^T;
-// 3 Dirichlet face (L = its entry in the Dirichlet list), h P_K P_K^T with h = kappa_K Ups_K. Padded modes get a unit
-// diagonal.
-__global__ void k_asm1(int nblk, int mb, const int* __restrict__ off, const int4* __restrict__ list,
+// Level-1 Galerkin blocks from the fine faces, one warp per block: lane t takes contributions t, t + 32, ... of the
+// block's list and accumulates the whole MB x MB block; a fixed shuffle tree then adds the lanes' blocks. The
+// contributions (K, L, e, type): 0 interior face inside the aggregate, T (P_K - P_L)(P_K - P_L)^T; 1 face to another
+// aggregate seen from this one's cell K, T P_K P_K^T; 2 the off-diagonal part, -T P_K P_L^T; 3 Dirichlet face (L = its
+// entry in the Dirichlet list), h P_K P_K^T with h = kappa_K Ups_K.
+template <int MB>
+__global__ void k_asm1(int nblk, const int* __restrict__ off, const int4* __restrict__ list,
                        const float* __restrict__ P0, const double* __restrict__ Tval, const double* __restrict__ kap,
-                       const double* __restrict__ dir_ups, const int* __restrict__ rowptr, const int* __restrict__ dpos,
-                       const int* __restrict__ mcnt, float* __restrict__ aval) {
+                       const double* __restrict__ dir_ups, float* __restrict__ aval) {
+  pdl_start();
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  const int mm = mb * mb;
   for (int b = warp; b < nblk; b += nw) {
-    float acc[2] = {0.0f, 0.0f};
-    int uu[2], vv[2];
+    float acc[MB * MB];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int idx = lane + 32 * h;
-      uu[h] = idx / mb;
-      vv[h] = idx % mb;
-    }
-    for (int c = off[b]; c < off[b + 1]; ++c) {
+    for (int i = 0; i < MB * MB; ++i) acc[i] = 0.0f;
+    for (int c = off[b] + lane; c < off[b + 1]; c += 32) {
       const int4 t = list[c];
-      const float* PK = P0 + (size_t)t.x * mb;
+      float pk[MB], pl[MB];
+#pragma unroll
+      for (int j = 0; j < MB; ++j) pk[j] = P0[(size_t)t.x * MB + j];
+      float w;
       if (t.w == 3) {
-        const float h = (float)(kap[t.x] * dir_ups[t.y]);
+        w = (float)(kap[t.x] * dir_ups[t.y]);
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
-          if (lane + 32 * q < mm) acc[q] = fmaf(h * PK[uu[q]], PK[vv[q]], acc[q]);
-        continue;
-      }
-      const float T = (float)Tval[t.z];
-      const float* PL = P0 + (size_t)t.y * mb;
+        for (int j = 0; j < MB; ++j) pl[j] = pk[j];
+      } else {
+        w = (float)Tval[t.z];
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (lane + 32 * q >= mm) continue;
-        const int u = uu[q], v = vv[q];
+        for (int j = 0; j < MB; ++j) pl[j] = P0[(size_t)t.y * MB + j];
         if (t.w == 0) {
-          acc[q] = fmaf(T * (PK[u] - PL[u]), PK[v] - PL[v], acc[q]);
+#pragma unroll
+          for (int j = 0; j < MB; ++j) {
+            pk[j] -= pl[j];
+            pl[j] = pk[j];
+          }
         } else if (t.w == 1) {
-          acc[q] = fmaf(T * PK[u], PK[v], acc[q]);
+#pragma unroll
+          for (int j = 0; j < MB; ++j) pl[j] = pk[j];
         } else {
-          acc[q] = fmaf(-T * PK[u], PL[v], acc[q]);
+          w = -w;
         }
       }
+#pragma unroll
+      for (int u = 0; u < MB; ++u)
+#pragma unroll
+        for (int v = 0; v < MB; ++v) acc[u * MB + v] = fmaf(w * pk[u], pl[v], acc[u * MB + v]);
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int idx = lane + 32 * q;
-      if (idx >= mm) continue;
-      aval[(size_t)b * mm + idx] = acc[q];
-    }
-    (void)rowptr;
-    (void)dpos;
-    (void)mcnt;
+    for (int i = 0; i < MB * MB; ++i) acc[i] = warp_sum(acc[i]);
+#pragma unroll
+    for (int i = 0; i < MB * MB; ++i)
+      if ((i & 31) == lane) aval[(size_t)b * MB * MB + i] = acc[i];
   }
 }
 
 // Unit diagonal on the padded modes of every diagonal block of level l (cells with fewer modes than mb).
 __global__ void k_pad_diag(int nc, int mb, const int* __restrict__ dpos, const int* __restrict__ mcnt,
                            float* __restrict__ aval) {
+  pdl_start();
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
     float* B = aval + (size_t)dpos[c] * mb * mb;
     for (int u = mcnt[c]; u < mb; ++u) {
@@ -209,78 +222,102 @@ __global__ void k_pad_diag(int nc, int mb, const int* __restrict__ dpos, const i
 }
 
 // Level-l Galerkin blocks (l >= 2) from the level-(l-1) blocks: block (A, B) = sum over (c, d) with agg(c) = A,
-// agg(d) = B of P_c^T A_cd P_d, P_c the mbf x mb transfer block of level-(l-1) cell c. One warp per block.
-__global__ void k_asml(int nblk, int mb, int mbf, const int* __restrict__ off, const int4* __restrict__ list,
+// agg(d) = B of P_c^T A_cd P_d, P_c the mbf x MB transfer block of level-(l-1) cell c. One warp per block, lanes
+// taking the contributions in turn, then a fixed shuffle tree.
+template <int MB>
+__global__ void k_asml(int nblk, int mbf, const int* __restrict__ off, const int4* __restrict__ list,
                        const float* __restrict__ Pf, const float* __restrict__ afine, float* __restrict__ aval) {
+  pdl_start();
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  const int mm = mb * mb, mmf = mbf * mbf;
   for (int b = warp; b < nblk; b += nw) {
-    float acc[2] = {0.0f, 0.0f};
-    for (int c = off[b]; c < off[b + 1]; ++c) {
-      const int4 t = list[c];   // (source block, c, d, -)
-      const float* As = afine + (size_t)t.x * mmf;
-      const float* Pc = Pf + (size_t)t.y * mbf * mb;
-      const float* Pd = Pf + (size_t)t.z * mbf * mb;
+    float acc[MB * MB];
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int idx = lane + 32 * q;
-        if (idx >= mm) continue;
-        const int u = idx / mb, v = idx % mb;
-        float s = 0.0f;
-        for (int i = 0; i < mbf; ++i) {
-          float r = 0.0f;
-          for (int j = 0; j < mbf; ++j) r = fmaf(As[i * mbf + j], Pd[j * mb + v], r);
-          s = fmaf(Pc[i * mb + u], r, s);
+    for (int i = 0; i < MB * MB; ++i) acc[i] = 0.0f;
+    for (int c = off[b] + lane; c < off[b + 1]; c += 32) {
+      const int4 t = list[c];   // (source block, c, d, -)
+      const float* As = afine + (size_t)t.x * mbf * mbf;
+      const float* Pc = Pf + (size_t)t.y * mbf * MB;
+      const float* Pd = Pf + (size_t)t.z * mbf * MB;
+      for (int i = 0; i < mbf; ++i) {
+        float ti[MB];
+#pragma unroll
+        for (int v = 0; v < MB; ++v) ti[v] = 0.0f;
+        for (int j = 0; j < mbf; ++j) {
+          const float a = As[i * mbf + j];
+#pragma unroll
+          for (int v = 0; v < MB; ++v) ti[v] = fmaf(a, Pd[j * MB + v], ti[v]);
         }
-        acc[q] += s;
+#pragma unroll
+        for (int u = 0; u < MB; ++u) {
+          const float pu = Pc[i * MB + u];
+#pragma unroll
+          for (int v = 0; v < MB; ++v) acc[u * MB + v] = fmaf(pu, ti[v], acc[u * MB + v]);
+        }
       }
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int idx = lane + 32 * q;
-      if (idx < mm) aval[(size_t)b * mm + idx] = acc[q];
-    }
+    for (int i = 0; i < MB * MB; ++i) acc[i] = warp_sum(acc[i]);
+#pragma unroll
+    for (int i = 0; i < MB * MB; ++i)
+      if ((i & 31) == lane) aval[(size_t)b * MB * MB + i] = acc[i];
   }
 }
 
-// Inverse of each diagonal block of level l (Gauss-Jordan in FP64, no pivoting: the blocks are symmetric positive
-// definite) and the Gershgorin bound max over rows of sum |D^-1 A| (one thread per cell).
-__global__ void k_block_inv(int nc, int mb, const int* __restrict__ rowptr, const int* __restrict__ col,
-                            const int* __restrict__ dpos, const float* __restrict__ aval, float* __restrict__ dinv,
-                            float* lam) {
+// Inverse of each diagonal block of a block level (Gauss-Jordan in FP64 registers, no pivoting: the blocks are
+// symmetric positive definite) and the Gershgorin bound max over rows of sum |D^-1 A| (one thread per cell).
+template <int MB>
+__global__ void k_block_inv(int nc, const int* __restrict__ rowptr, const int* __restrict__ dpos,
+                            const float* __restrict__ aval, float* __restrict__ dinv, float* lam) {
+  pdl_start();
   float g = 0.0f;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
-    double A[kMaxM * kMaxM];
-    const float* B = aval + (size_t)dpos[c] * mb * mb;
-    for (int i = 0; i < mb * mb; ++i) A[i] = B[i];
-    for (int k = 0; k < mb; ++k) {
-      const double dk = 1.0 / A[k * mb + k];
-      A[k * mb + k] = 1.0;
-      for (int j = 0; j < mb; ++j) A[k * mb + j] *= dk;
-      for (int i = 0; i < mb; ++i) {
+    double A[MB * MB];
+    const float* B = aval + (size_t)dpos[c] * MB * MB;
+#pragma unroll
+    for (int i = 0; i < MB * MB; ++i) A[i] = B[i];
+#pragma unroll
+    for (int k = 0; k < MB; ++k) {
+      const double dk = 1.0 / A[k * MB + k];
+      A[k * MB + k] = 1.0;
+#pragma unroll
+      for (int j = 0; j < MB; ++j) A[k * MB + j] *= dk;
+#pragma unroll
+      for (int i = 0; i < MB; ++i) {
         if (i == k) continue;
-        const double f = A[i * mb + k];
-        A[i * mb + k] = 0.0;
-        for (int j = 0; j < mb; ++j) A[i * mb + j] -= f * A[k * mb + j];
+        const double f = A[i * MB + k];
+        A[i * MB + k] = 0.0;
+#pragma unroll
+        for (int j = 0; j < MB; ++j) A[i * MB + j] -= f * A[k * MB + j];
       }
     }
-    float* Dc = dinv + (size_t)c * mb * mb;
-    for (int i = 0; i < mb * mb; ++i) Dc[i] = (float)A[i];
-    for (int u = 0; u < mb; ++u) {
-      double s = 0.0;
-      for (int q = rowptr[c]; q < rowptr[c + 1]; ++q) {
-        const float* Bq = aval + (size_t)q * mb * mb;
-        for (int v = 0; v < mb; ++v) {
-          double t = 0.0;
-          for (int w = 0; w < mb; ++w) t += A[u * mb + w] * Bq[w * mb + v];
-          s += fabs(t);
+    float Di[MB * MB];
+#pragma unroll
+    for (int i = 0; i < MB * MB; ++i) {
+      Di[i] = (float)A[i];
+      dinv[(size_t)c * MB * MB + i] = Di[i];
+    }
+    float rs[MB];
+#pragma unroll
+    for (int u = 0; u < MB; ++u) rs[u] = 0.0f;
+    for (int q = rowptr[c]; q < rowptr[c + 1]; ++q) {
+      const float* Bq = aval + (size_t)q * MB * MB;
+      float Bl[MB * MB];
+#pragma unroll
+      for (int i = 0; i < MB * MB; ++i) Bl[i] = Bq[i];
+#pragma unroll
+      for (int u = 0; u < MB; ++u)
+#pragma unroll
+        for (int v = 0; v < MB; ++v) {
+          float t = 0.0f;
+#pragma unroll
+          for (int w = 0; w < MB; ++w) t = fmaf(Di[u * MB + w], Bl[w * MB + v], t);
+          rs[u] += fabsf(t);
         }
-      }
-      g = fmaxf(g, (float)s);
     }
-    (void)col;
+#pragma unroll
+    for (int u = 0; u < MB; ++u) g = fmaxf(g, rs[u]);
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) g = fmaxf(g, __shfl_down_sync(0xffffffffu, g, off));
@@ -291,6 +328,7 @@ __global__ void k_block_inv(int nc, int mb, const int* __restrict__ rowptr, cons
 // n x n FP64 matrix in shared memory, in-place Gauss-Jordan (symmetric positive definite, no pivoting).
 __global__ void k_coarse_inv(int nc, int mb, const int* __restrict__ rowptr, const int* __restrict__ col,
                              const float* __restrict__ aval, float* __restrict__ cinv) {
+  pdl_start();
   extern __shared__ double S[];   // n * n + n
   const int n = nc * mb;
   double* colk = S + n * n;
@@ -337,6 +375,7 @@ __global__ void k_cheb0(FineDev F, const float* __restrict__ a0off, const float*
                         const float* __restrict__ a0dinv, const float* __restrict__ b, const float* __restrict__ xin,
                         float* __restrict__ xout, float* __restrict__ d, const float* __restrict__ lam, int k,
                         const int* done) {
+  pdl_start();
   if (stop(done)) return;
   float c1, c2;
   cheb_coef(lam[0], k, c1, c2);
@@ -353,96 +392,52 @@ __global__ void k_cheb0(FineDev F, const float* __restrict__ a0off, const float*
   }
 }
 
-// Level-0 residual and its restriction to level 1, one warp per level-1 cell A: b1_A = P_A^T (b - A x) over the fine
-// cells of A. If `first` is set, the first Chebyshev step of level 1 follows (x1 = D1^-1 b1 / theta, d1 = x1).
-__global__ void k_rr0(FineDev F, const float* __restrict__ a0off, const float* __restrict__ a0diag,
-                      const float* __restrict__ b, const float* __restrict__ x, const float* __restrict__ P0,
-                      const int* __restrict__ ch_off, const int* __restrict__ ch, int nc1, int mb,
-                      float* __restrict__ b1, const float* __restrict__ dinv1, float* __restrict__ x1,
-                      float* __restrict__ d1, const float* __restrict__ lam, int first, const int* done) {
-  if (stop(done)) return;
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  float c1 = 0.0f, c2 = 0.0f;
-  if (first) cheb_coef(lam[1], 0, c1, c2);
-  for (int A = warp; A < nc1; A += nw) {
-    float acc[kMaxM];
-#pragma unroll
-    for (int j = 0; j < kMaxM; ++j) acc[j] = 0.0f;
-    for (int t = ch_off[A] + lane; t < ch_off[A + 1]; t += 32) {
-      const int K = ch[t];
-      const int w = F.sell_w[K >> 5];
-      int e = F.sell_off[K >> 5] + (K & 31);
-      float ax = a0diag[K] * x[K];
-      for (int j = 0; j < w; ++j, e += 32) ax = fmaf(a0off[e], x[F.nbr[e]], ax);
-      const float res = b[K] - ax;
-      const float* PK = P0 + (size_t)K * mb;
-#pragma unroll
-      for (int j = 0; j < kMaxM; ++j)
-        if (j < mb) acc[j] = fmaf(PK[j], res, acc[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < kMaxM; ++j) {
-      if (j >= mb) break;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], off);
-    }
-    if (lane < mb) {
-      float bj = 0.0f;
-#pragma unroll
-      for (int j = 0; j < kMaxM; ++j)
-        if (j == lane) bj = acc[j];
-      b1[(size_t)A * mb + lane] = bj;
-      if (first) {
-        const float* Dc = dinv1 + (size_t)A * mb * mb + lane * mb;
-        float s = 0.0f;
-#pragma unroll
-        for (int v = 0; v < kMaxM; ++v)
-          if (v < mb) s = fmaf(Dc[v], acc[v], s);
-        const float dn = c2 * s;
-        d1[(size_t)A * mb + lane] = dn;
-        x1[(size_t)A * mb + lane] = dn;
-      }
-    }
-  }
-}
 
-// (b - A x)_u for cell c on a block level: lane u of the group (u < mb).
-__device__ __forceinline__ float block_res(int c, int u, int mb, const int* __restrict__ rowptr,
-                                           const int* __restrict__ col, const float* __restrict__ aval,
-                                           const float* __restrict__ b, const float* __restrict__ x) {
+// (A x)_u of block-level cell c, one warp per cell: lane = slot * 8 + u, the four slots take every fourth block of
+// the row; a shuffle tree adds the slots, so every lane with component u < MB holds (A x)_u.
+template <int MB>
+__device__ __forceinline__ float row_ax(int c, int lane, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                        const float* __restrict__ aval, const float* __restrict__ x) {
+  const int slot = lane >> 3, u = lane & 7;
   float ax = 0.0f;
-  for (int q = rowptr[c]; q < rowptr[c + 1]; ++q) {
-    const float* Bq = aval + (size_t)q * mb * mb + u * mb;
-    const float* xd = x + (size_t)col[q] * mb;
-    for (int v = 0; v < mb; ++v) ax = fmaf(Bq[v], xd[v], ax);
+  if (u < MB) {
+    const int q1 = rowptr[c + 1];
+    for (int q = rowptr[c] + slot; q < q1; q += 4) {
+      const float* Bq = aval + (size_t)q * MB * MB + u * MB;
+      const float* xd = x + (size_t)col[q] * MB;
+#pragma unroll
+      for (int v = 0; v < MB; ++v) ax = fmaf(Bq[v], xd[v], ax);
+    }
   }
-  return b[(size_t)c * mb + u] - ax;
+  ax += __shfl_xor_sync(0xffffffffu, ax, 8);
+  ax += __shfl_xor_sync(0xffffffffu, ax, 16);
+  return ax;
 }
 
-// One Chebyshev step on block level l: groups of kG lanes per cell, lane u < mb owning component u.
-__global__ void k_chebl(int nc, int mb, const int* __restrict__ rowptr, const int* __restrict__ col,
+// One Chebyshev step on block level l, one warp per cell (see row_ax).
+template <int MB>
+__global__ void k_chebl(int nc, const int* __restrict__ rowptr, const int* __restrict__ col,
                         const float* __restrict__ aval, const float* __restrict__ dinv, const float* __restrict__ b,
                         const float* __restrict__ xin, float* __restrict__ xout, float* __restrict__ d,
                         const float* __restrict__ lam, int l, int k, const int* done) {
+  pdl_start();
   if (stop(done)) return;
   float c1, c2;
   cheb_coef(lam[l], k, c1, c2);
-  const int lane = threadIdx.x & 31, u = lane & (kG - 1);
-  const long total = (long)nc * kG;
-  for (long tb = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); tb < total; tb += (long)gridDim.x * blockDim.x) {
-    const long t = tb + lane;
-    const int c = (int)(t / kG);
-    const bool act = t < total && u < mb;
-    const float res = act ? block_res(c, u, mb, rowptr, col, aval, b, xin) : 0.0f;
+  const int lane = threadIdx.x & 31, u = lane & 7;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int c = warp; c < nc; c += nw) {
+    const float ax = row_ax<MB>(c, lane, rowptr, col, aval, xin);
+    const float res = u < MB ? b[(size_t)c * MB + u] - ax : 0.0f;
     float s = 0.0f;
-    for (int v = 0; v < mb; ++v) {
-      const float rv = __shfl_sync(0xffffffffu, res, (lane & ~(kG - 1)) + v);
-      if (act) s = fmaf(dinv[(size_t)c * mb * mb + u * mb + v], rv, s);
+#pragma unroll
+    for (int v = 0; v < MB; ++v) {
+      const float rv = __shfl_sync(0xffffffffu, res, v);
+      if (u < MB) s = fmaf(dinv[(size_t)c * MB * MB + u * MB + v], rv, s);
     }
-    if (act) {
-      const size_t i = (size_t)c * mb + u;
+    if (lane < MB) {
+      const size_t i = (size_t)c * MB + u;
       const float dn = (k == 0 ? 0.0f : c1 * d[i]) + c2 * s;
       d[i] = dn;
       xout[i] = xin[i] + dn;
@@ -450,38 +445,55 @@ __global__ void k_chebl(int nc, int mb, const int* __restrict__ rowptr, const in
   }
 }
 
-// Level-l residual restricted to level l+1, one warp per level-(l+1) cell A, four groups of kG lanes taking its
-// children in turn; `first` adds the first Chebyshev step of level l+1.
-__global__ void k_rrl(int mbf, const int* __restrict__ rowptr, const int* __restrict__ col,
-                      const float* __restrict__ aval, const float* __restrict__ b, const float* __restrict__ x,
-                      const float* __restrict__ Pl, const int* __restrict__ ch_off, const int* __restrict__ ch,
-                      int ncc, int mb, float* __restrict__ bc, const float* __restrict__ dinvc, float* __restrict__ xc,
-                      float* __restrict__ dc, const float* __restrict__ lam, int lc, int first, const int* done) {
+// Residual b - A x of a block level, one warp per cell.
+template <int MB>
+__global__ void k_resl(int nc, const int* __restrict__ rowptr, const int* __restrict__ col,
+                       const float* __restrict__ aval, const float* __restrict__ b, const float* __restrict__ x,
+                       float* __restrict__ res, const int* done) {
+  pdl_start();
   if (stop(done)) return;
-  const int lane = threadIdx.x & 31, grp = lane / kG, u = lane & (kG - 1);
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int c = warp; c < nc; c += nw) {
+    const float ax = row_ax<MB>(c, lane, rowptr, col, aval, x);
+    if (lane < MB) res[(size_t)c * MB + lane] = b[(size_t)c * MB + lane] - ax;
+  }
+}
+
+// Restriction of a residual (mbf per cell on level l) to level l+1 (mb per cell), one warp per level-(l+1) cell A:
+// lane = k * 8 + u takes component u of children k, k + 4, ...; a shuffle tree adds the lanes. `first` adds the first
+// Chebyshev step of level l+1 (x = D^-1 b / theta, d = x).
+__global__ void k_restr(int mbf, const float* __restrict__ res, const float* __restrict__ Pl,
+                        const int* __restrict__ ch_off, const int* __restrict__ ch, int ncc, int mb,
+                        float* __restrict__ bc, const float* __restrict__ dinvc, float* __restrict__ xc,
+                        float* __restrict__ dc, const float* __restrict__ lam, int lc, int first, const int* done) {
+  pdl_start();
+  if (stop(done)) return;
+  const int lane = threadIdx.x & 31, grp = lane >> 3, u = lane & 7;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   float c1 = 0.0f, c2 = 0.0f;
   if (first) cheb_coef(lam[lc], 0, c1, c2);
+  // one value per child (level 0): lanes take children one each; else eight lanes per child
+  const int cstep = mbf == 1 ? 32 : 4, c0 = mbf == 1 ? lane : grp, uu = mbf == 1 ? 0 : u;
   for (int A = warp; A < ncc; A += nw) {
     float acc[kMaxM];
 #pragma unroll
     for (int j = 0; j < kMaxM; ++j) acc[j] = 0.0f;
-    for (int t = ch_off[A] + grp; t < ch_off[A + 1]; t += 32 / kG) {
-      if (u >= mbf) continue;
-      const int c = ch[t];
-      const float res = block_res(c, u, mbf, rowptr, col, aval, b, x);
-      const float* Pr = Pl + ((size_t)c * mbf + u) * mb;
+    if (uu < mbf) {
+      for (int t = ch_off[A] + c0; t < ch_off[A + 1]; t += cstep) {
+        const int c = ch[t];
+        const float r = res[(size_t)c * mbf + uu];
+        const float* Pr = Pl + ((size_t)c * mbf + uu) * mb;
 #pragma unroll
-      for (int j = 0; j < kMaxM; ++j)
-        if (j < mb) acc[j] = fmaf(Pr[j], res, acc[j]);
+        for (int j = 0; j < kMaxM; ++j)
+          if (j < mb) acc[j] = fmaf(Pr[j], r, acc[j]);
+      }
     }
 #pragma unroll
-    for (int j = 0; j < kMaxM; ++j) {
-      if (j >= mb) break;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], off);
-    }
+    for (int j = 0; j < kMaxM; ++j)
+      if (j < mb) acc[j] = warp_sum(acc[j]);
     if (lane < mb) {
       float bj = 0.0f;
 #pragma unroll
@@ -502,9 +514,25 @@ __global__ void k_rrl(int mbf, const int* __restrict__ rowptr, const int* __rest
   }
 }
 
+// Level-0 residual b - A x (FP32), one thread per cell.
+__global__ void k_res0(FineDev F, const float* __restrict__ a0off, const float* __restrict__ a0diag,
+                       const float* __restrict__ b, const float* __restrict__ x, float* __restrict__ res,
+                       const int* done) {
+  pdl_start();
+  if (stop(done)) return;
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < F.N; K += gridDim.x * blockDim.x) {
+    const int w = F.sell_w[K >> 5];
+    int e = F.sell_off[K >> 5] + (K & 31);
+    float ax = a0diag[K] * x[K];
+    for (int j = 0; j < w; ++j, e += 32) ax = fmaf(a0off[e], x[F.nbr[e]], ax);
+    res[K] = b[K] - ax;
+  }
+}
+
 // Coarsest level: x = C^-1 b with the dense inverse.
 __global__ void k_coarse_solve(int n, const float* __restrict__ cinv, const float* __restrict__ b,
                                float* __restrict__ x, const int* done) {
+  pdl_start();
   if (stop(done)) return;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     float s = 0.0f;
@@ -516,6 +544,7 @@ __global__ void k_coarse_solve(int n, const float* __restrict__ cinv, const floa
 // x_0 += P e on level 0 (per fine cell) and on a block level (per cell and component).
 __global__ void k_pro0(int N, int mb, const float* __restrict__ P0, const int* __restrict__ agg,
                        const float* __restrict__ e, float* __restrict__ x, const int* done) {
+  pdl_start();
   if (stop(done)) return;
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
     const float* PK = P0 + (size_t)K * mb;
@@ -527,6 +556,7 @@ __global__ void k_pro0(int N, int mb, const float* __restrict__ P0, const int* _
 }
 __global__ void k_prol(int nc, int mbf, int mb, const float* __restrict__ Pl, const int* __restrict__ agg,
                        const float* __restrict__ e, float* __restrict__ x, const int* done) {
+  pdl_start();
   if (stop(done)) return;
   const long total = (long)nc * mbf;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
@@ -566,6 +596,7 @@ __global__ void k_pcg_init(int N, const double* __restrict__ b, double bscale, c
                            double* __restrict__ x, double* __restrict__ r, float* __restrict__ r32,
                            const float* __restrict__ a0dinv, float* __restrict__ x0, float* __restrict__ d0,
                            const float* __restrict__ lam, double* part, MgScal* sc) {
+  pdl_start();
   float c1, c2;
   cheb_coef(lam[0], 0, c1, c2);
   double v[1] = {0.0};
@@ -592,6 +623,7 @@ __global__ void k_pcg_init(int N, const double* __restrict__ b, double bscale, c
 // rz_new / rz for a fixed linear preconditioner and tolerates the FP32 rounding of the V-cycle.
 __global__ void k_pcg_beta(int N, const double* __restrict__ r, const float* __restrict__ z,
                            const float* __restrict__ zold, double* part, MgScal* sc) {
+  pdl_start();
   if (stop(&sc->done)) return;
   const bool first = sc->it == 0;
   double v[2] = {0.0, 0.0};
@@ -610,6 +642,7 @@ __global__ void k_pcg_beta(int N, const double* __restrict__ r, const float* __r
 __global__ void k_pcg_pq(FineDev F, const double* __restrict__ Tval, const double* __restrict__ diagT,
                          const float* __restrict__ z, float* __restrict__ zold, double* __restrict__ p,
                          double* __restrict__ q, double* part, MgScal* sc) {
+  pdl_start();
   if (stop(&sc->done)) return;
   const double beta = sc->beta;
   const bool first = sc->it == 0;
@@ -634,6 +667,7 @@ __global__ void k_pcg_update(int N, const double* __restrict__ p, const double* 
                              float* __restrict__ r32, const float* __restrict__ a0dinv, float* __restrict__ x0,
                              float* __restrict__ d0, const float* __restrict__ lam, double* part, MgScal* sc,
                              cudaGraphConditionalHandle h) {
+  pdl_start();
   if (stop(&sc->done)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0);
     return;
@@ -680,6 +714,7 @@ __global__ void k_bicg_init(int N, const double* __restrict__ b, double bscale, 
                             double* __restrict__ p, float* __restrict__ r32, const float* __restrict__ a0dinv,
                             float* __restrict__ x0, float* __restrict__ d0, const float* __restrict__ lam,
                             double* part, MgScal* sc) {
+  pdl_start();
   float c1, c2;
   cheb_coef(lam[0], 0, c1, c2);
   double v[2] = {0.0, 0.0};
@@ -710,6 +745,7 @@ __global__ void k_bicg_init(int N, const double* __restrict__ b, double bscale, 
 __global__ void k_bicg_v(FineDev F, const double* __restrict__ Joff, const double* __restrict__ jd,
                          const float* __restrict__ zp, double* __restrict__ pp, double* __restrict__ v,
                          const double* __restrict__ rh, double* part, MgScal* sc) {
+  pdl_start();
   if (stop(&sc->done)) return;
   double a[1] = {0.0};
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < F.N; K += gridDim.x * blockDim.x) {
@@ -724,6 +760,7 @@ __global__ void k_bicg_v(FineDev F, const double* __restrict__ Joff, const doubl
 __global__ void k_bicg_s(int N, const double* __restrict__ r, const double* __restrict__ v, double* __restrict__ s,
                          float* __restrict__ r32, const float* __restrict__ a0dinv, float* __restrict__ x0,
                          float* __restrict__ d0, const float* __restrict__ lam, MgScal* sc) {
+  pdl_start();
   if (stop(&sc->done)) return;
   const double alpha = sc->alpha;
   float c1, c2;
@@ -739,6 +776,7 @@ __global__ void k_bicg_s(int N, const double* __restrict__ r, const double* __re
 __global__ void k_bicg_t(FineDev F, const double* __restrict__ Joff, const double* __restrict__ jd,
                          const float* __restrict__ zs, const double* __restrict__ s, double* __restrict__ t,
                          double* part, MgScal* sc) {
+  pdl_start();
   if (stop(&sc->done)) return;
   double a[2] = {0.0, 0.0};
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < F.N; K += gridDim.x * blockDim.x) {
@@ -755,6 +793,7 @@ __global__ void k_bicg_x(int N, const double* __restrict__ pp, const float* __re
                          const double* __restrict__ s, const double* __restrict__ t, const double* __restrict__ rh,
                          const double* __restrict__ wgt, double* __restrict__ x, double* __restrict__ r, double* part,
                          MgScal* sc, cudaGraphConditionalHandle h) {
+  pdl_start();
   if (stop(&sc->done)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0);
     return;
@@ -786,6 +825,7 @@ __global__ void k_bicg_x(int N, const double* __restrict__ pp, const float* __re
 __global__ void k_bicg_p(int N, const double* __restrict__ r, const double* __restrict__ v, double* __restrict__ p,
                          float* __restrict__ r32, const float* __restrict__ a0dinv, float* __restrict__ x0,
                          float* __restrict__ d0, const float* __restrict__ lam, MgScal* sc) {
+  pdl_start();
   if (stop(&sc->done)) return;
   const double beta = sc->beta, omega = sc->omega;
   float c1, c2;
@@ -802,6 +842,7 @@ __global__ void k_bicg_p(int N, const double* __restrict__ r, const double* __re
 __global__ void k_apply_in(int N, const double* __restrict__ b, float* __restrict__ r32,
                            const float* __restrict__ a0dinv, float* __restrict__ x0, float* __restrict__ d0,
                            const float* __restrict__ lam) {
+  pdl_start();
   float c1, c2;
   cheb_coef(lam[0], 0, c1, c2);
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
@@ -810,6 +851,7 @@ __global__ void k_apply_in(int N, const double* __restrict__ b, float* __restric
   }
 }
 __global__ void k_apply_out(int N, const float* __restrict__ z, double* __restrict__ out) {
+  pdl_start();
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) out[K] = (double)z[K];
 }
 
@@ -968,32 +1010,69 @@ bool mg_build_host(const FineMesh& fm, const Hierarchy& H, int levels, MgHost& M
 // ---------------------------------------------------------------------------------------------------------------
 // host: enqueueing
 
+namespace {
+
+// Launches with programmatic stream serialization (each kernel starts its launch while its predecessor finishes;
+// pdl_start() in every kernel orders the memory accesses). Launch errors surface through cudaGetLastError().
+template <class... KArgs, class... Args>
+void launchk(cudaStream_t st, int grid, int block, size_t smem, void (*k)(KArgs...), Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, (KArgs)args...);
+}
+
+#define MG_MB_SWITCH(mb, CALL)                                                     \
+  switch (mb) {                                                                    \
+    case 1: { constexpr int MB = 1; CALL; } break;                                 \
+    case 2: { constexpr int MB = 2; CALL; } break;                                 \
+    case 3: { constexpr int MB = 3; CALL; } break;                                 \
+    case 4: { constexpr int MB = 4; CALL; } break;                                 \
+    case 5: { constexpr int MB = 5; CALL; } break;                                 \
+    case 6: { constexpr int MB = 6; CALL; } break;                                 \
+    case 7: { constexpr int MB = 7; CALL; } break;                                 \
+    default: { constexpr int MB = 8; CALL; } break;                                \
+  }
+
+inline int warps_grid(long warps) { return blocks_for(warps * 32, 65535); }
+
+}  // namespace
+
 void mg_enqueue_setup(cudaStream_t st, const MgDev& M, const FineDev& F, const MgWork& W, const double* Tval,
                       const double* diagT, const double* kap) {
   cudaMemsetAsync(W.lam, 0, kMgMaxLevels * sizeof(float), st);
-  k_fine_vals<<<blocks_for(M.N, 4096), kT, 0, st>>>(F, Tval, diagT, W.a0off, W.a0diag, W.a0dinv, W.lam);
-  count_launch(1);
-  k_asm1<<<blocks_for((long)M.nblk[1] * 32, 65535), kT, 0, st>>>(M.nblk[1], M.mb[1], M.asm_off[1], M.asm_list[1],
-                                                                 M.P[0], Tval, kap, F.dir_ups, M.rowptr[1],
-                                                                 M.dpos[1], M.mcnt[1], W.aval[1]);
-  k_pad_diag<<<blocks_for(M.nc[1]), kT, 0, st>>>(M.nc[1], M.mb[1], M.dpos[1], M.mcnt[1], W.aval[1]);
-  count_launch(2);
+  launchk(st, blocks_for(M.N, 4096), kT, 0, k_fine_vals, F, Tval, diagT, W.a0off, W.a0diag, W.a0dinv, W.lam);
+  MG_MB_SWITCH(M.mb[1], launchk(st, warps_grid(M.nblk[1]), kT, 0, k_asm1<MB>, M.nblk[1], (const int*)M.asm_off[1],
+                                (const int4*)M.asm_list[1], (const float*)M.P[0], Tval, kap,
+                                (const double*)F.dir_ups, W.aval[1]));
+  launchk(st, blocks_for(M.nc[1]), kT, 0, k_pad_diag, M.nc[1], M.mb[1], (const int*)M.dpos[1],
+          (const int*)M.mcnt[1], W.aval[1]);
+  int n = 3;
   for (int l = 2; l < M.L; ++l) {
-    k_asml<<<blocks_for((long)M.nblk[l] * 32, 65535), kT, 0, st>>>(M.nblk[l], M.mb[l], M.mb[l - 1], M.asm_off[l],
-                                                                   M.asm_list[l], M.P[l - 1], W.aval[l - 1],
-                                                                   W.aval[l]);
-    k_pad_diag<<<blocks_for(M.nc[l]), kT, 0, st>>>(M.nc[l], M.mb[l], M.dpos[l], M.mcnt[l], W.aval[l]);
-    count_launch(2);
+    MG_MB_SWITCH(M.mb[l], launchk(st, warps_grid(M.nblk[l]), kT, 0, k_asml<MB>, M.nblk[l], M.mb[l - 1],
+                                  (const int*)M.asm_off[l], (const int4*)M.asm_list[l], (const float*)M.P[l - 1],
+                                  (const float*)W.aval[l - 1], W.aval[l]));
+    launchk(st, blocks_for(M.nc[l]), kT, 0, k_pad_diag, M.nc[l], M.mb[l], (const int*)M.dpos[l],
+            (const int*)M.mcnt[l], W.aval[l]);
+    n += 2;
   }
   for (int l = 1; l + 1 < M.L; ++l) {
-    k_block_inv<<<blocks_for(M.nc[l]), kT, 0, st>>>(M.nc[l], M.mb[l], M.rowptr[l], M.col[l], M.dpos[l], W.aval[l],
-                                                    W.dinv[l], W.lam + l);
-    count_launch(1);
+    MG_MB_SWITCH(M.mb[l], launchk(st, blocks_for(M.nc[l]), 128, 0, k_block_inv<MB>, M.nc[l],
+                                  (const int*)M.rowptr[l], (const int*)M.dpos[l], (const float*)W.aval[l], W.dinv[l],
+                                  W.lam + l));
+    ++n;
   }
-  const int C = M.L - 1, n = M.nc[C] * M.mb[C];
-  k_coarse_inv<<<1, 256, (size_t)(n * n + n) * sizeof(double), st>>>(M.nc[C], M.mb[C], M.rowptr[C], M.col[C],
-                                                                      W.aval[C], W.cinv);
-  count_launch(1);
+  const int C = M.L - 1, nco = M.nc[C] * M.mb[C];
+  launchk(st, 1, 512, (size_t)(nco * nco + nco) * sizeof(double), k_coarse_inv, M.nc[C], M.mb[C],
+          (const int*)M.rowptr[C], (const int*)M.col[C], (const float*)W.aval[C], W.cinv);
+  count_launch(n + 1);
 }
 
 // The V-cycle after the fused first step of level 0 (x[0][0], d[0] set from b[0]); returns the index of the level-0
@@ -1002,44 +1081,56 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
   const int L = M.L, C = L - 1;
   int cur[kMgMaxLevels] = {0};
   const int g0 = blocks_for(M.N, 4096);
-  // down
+  // down: level-0 smoothing, residual into d[0] (dead until the post-smoothing rewrites it), restriction
   for (int k = 1; k < kMgDegFine; ++k) {
-    k_cheb0<<<g0, kT, 0, st>>>(F, W.a0off, W.a0diag, W.a0dinv, W.b[0], W.x[0][cur[0]], W.x[0][1 - cur[0]], W.d[0],
-                               W.lam, k, flag);
+    launchk(st, g0, kT, 0, k_cheb0, F, (const float*)W.a0off, (const float*)W.a0diag, (const float*)W.a0dinv,
+            (const float*)W.b[0], (const float*)W.x[0][cur[0]], W.x[0][1 - cur[0]], W.d[0], (const float*)W.lam, k,
+            flag);
     cur[0] ^= 1;
   }
-  k_rr0<<<blocks_for((long)M.nc[1] * 32, 65535), kT, 0, st>>>(F, W.a0off, W.a0diag, W.b[0], W.x[0][cur[0]], M.P[0],
-                                                              M.ch_off[0], M.ch[0], M.nc[1], M.mb[1], W.b[1],
-                                                              W.dinv[1], W.x[1][0], W.d[1], W.lam, C > 1 ? 1 : 0,
-                                                              flag);
+  launchk(st, g0, kT, 0, k_res0, F, (const float*)W.a0off, (const float*)W.a0diag, (const float*)W.b[0],
+          (const float*)W.x[0][cur[0]], W.d[0], flag);
+  launchk(st, warps_grid(M.nc[1]), kT, 0, k_restr, 1, (const float*)W.d[0], (const float*)M.P[0],
+          (const int*)M.ch_off[0], (const int*)M.ch[0], M.nc[1], M.mb[1], W.b[1], (const float*)W.dinv[1],
+          W.x[1][0], W.d[1], (const float*)W.lam, 1, C > 1 ? 1 : 0, flag);
   for (int l = 1; l < C; ++l) {
-    const int gl = blocks_for((long)M.nc[l] * kG, 65535);
+    const int gl = warps_grid(M.nc[l]);
     for (int k = 1; k < kMgDegCoarse; ++k) {
-      k_chebl<<<gl, kT, 0, st>>>(M.nc[l], M.mb[l], M.rowptr[l], M.col[l], W.aval[l], W.dinv[l], W.b[l],
-                                 W.x[l][cur[l]], W.x[l][1 - cur[l]], W.d[l], W.lam, l, k, flag);
+      MG_MB_SWITCH(M.mb[l], launchk(st, gl, kT, 0, k_chebl<MB>, M.nc[l], (const int*)M.rowptr[l],
+                                    (const int*)M.col[l], (const float*)W.aval[l], (const float*)W.dinv[l],
+                                    (const float*)W.b[l], (const float*)W.x[l][cur[l]], W.x[l][1 - cur[l]], W.d[l],
+                                    (const float*)W.lam, l, k, flag));
       cur[l] ^= 1;
     }
-    k_rrl<<<blocks_for((long)M.nc[l + 1] * 32, 65535), kT, 0, st>>>(
-        M.mb[l], M.rowptr[l], M.col[l], W.aval[l], W.b[l], W.x[l][cur[l]], M.P[l], M.ch_off[l], M.ch[l],
-        M.nc[l + 1], M.mb[l + 1], W.b[l + 1], W.dinv[l + 1], W.x[l + 1][0], W.d[l + 1], W.lam, l + 1,
-        l + 1 < C ? 1 : 0, flag);
+    MG_MB_SWITCH(M.mb[l], launchk(st, gl, kT, 0, k_resl<MB>, M.nc[l], (const int*)M.rowptr[l],
+                                  (const int*)M.col[l], (const float*)W.aval[l], (const float*)W.b[l],
+                                  (const float*)W.x[l][cur[l]], W.d[l], flag));
+    launchk(st, warps_grid(M.nc[l + 1]), kT, 0, k_restr, M.mb[l], (const float*)W.d[l], (const float*)M.P[l],
+            (const int*)M.ch_off[l], (const int*)M.ch[l], M.nc[l + 1], M.mb[l + 1], W.b[l + 1],
+            (const float*)W.dinv[l + 1], W.x[l + 1][0], W.d[l + 1], (const float*)W.lam, l + 1, l + 1 < C ? 1 : 0,
+            flag);
   }
-  k_coarse_solve<<<1, kMgMaxCoarse, 0, st>>>(M.nc[C] * M.mb[C], W.cinv, W.b[C], W.x[C][0], flag);
+  launchk(st, 1, kMgMaxCoarse, 0, k_coarse_solve, M.nc[C] * M.mb[C], (const float*)W.cinv, (const float*)W.b[C],
+          W.x[C][0], flag);
   // up
   for (int l = C - 1; l >= 1; --l) {
-    k_prol<<<blocks_for((long)M.nc[l] * M.mb[l]), kT, 0, st>>>(M.nc[l], M.mb[l], M.mb[l + 1], M.P[l], M.agg[l],
-                                                                W.x[l + 1][cur[l + 1]], W.x[l][cur[l]], flag);
-    const int gl = blocks_for((long)M.nc[l] * kG, 65535);
+    launchk(st, blocks_for((long)M.nc[l] * M.mb[l]), kT, 0, k_prol, M.nc[l], M.mb[l], M.mb[l + 1],
+            (const float*)M.P[l], (const int*)M.agg[l], (const float*)W.x[l + 1][cur[l + 1]], W.x[l][cur[l]], flag);
+    const int gl = warps_grid(M.nc[l]);
     for (int k = 0; k < kMgDegCoarse; ++k) {
-      k_chebl<<<gl, kT, 0, st>>>(M.nc[l], M.mb[l], M.rowptr[l], M.col[l], W.aval[l], W.dinv[l], W.b[l],
-                                 W.x[l][cur[l]], W.x[l][1 - cur[l]], W.d[l], W.lam, l, k, flag);
+      MG_MB_SWITCH(M.mb[l], launchk(st, gl, kT, 0, k_chebl<MB>, M.nc[l], (const int*)M.rowptr[l],
+                                    (const int*)M.col[l], (const float*)W.aval[l], (const float*)W.dinv[l],
+                                    (const float*)W.b[l], (const float*)W.x[l][cur[l]], W.x[l][1 - cur[l]], W.d[l],
+                                    (const float*)W.lam, l, k, flag));
       cur[l] ^= 1;
     }
   }
-  k_pro0<<<g0, kT, 0, st>>>(M.N, M.mb[1], M.P[0], M.agg[0], W.x[1][cur[1]], W.x[0][cur[0]], flag);
+  launchk(st, g0, kT, 0, k_pro0, M.N, M.mb[1], (const float*)M.P[0], (const int*)M.agg[0],
+          (const float*)W.x[1][cur[1]], W.x[0][cur[0]], flag);
   for (int k = 0; k < kMgDegFine; ++k) {
-    k_cheb0<<<g0, kT, 0, st>>>(F, W.a0off, W.a0diag, W.a0dinv, W.b[0], W.x[0][cur[0]], W.x[0][1 - cur[0]], W.d[0],
-                               W.lam, k, flag);
+    launchk(st, g0, kT, 0, k_cheb0, F, (const float*)W.a0off, (const float*)W.a0diag, (const float*)W.a0dinv,
+            (const float*)W.b[0], (const float*)W.x[0][cur[0]], W.x[0][1 - cur[0]], W.d[0], (const float*)W.lam, k,
+            flag);
     cur[0] ^= 1;
   }
   return cur[0];
@@ -1047,7 +1138,7 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
 
 int mg_vcycle_kernels(const MgDev& M) {
   const int C = M.L - 1;
-  return (kMgDegFine - 1) + 1 + (C - 1) * kMgDegCoarse + 1 + (C - 1) * (1 + kMgDegCoarse) + 1 + kMgDegFine;
+  return (kMgDegFine - 1) + 2 + (C - 1) * (kMgDegCoarse + 1) + 1 + (C - 1) * (1 + kMgDegCoarse) + 1 + kMgDegFine;
 }
 
 namespace {
@@ -1106,44 +1197,47 @@ cudaError_t mg_capture_pcg(cudaStream_t st, const MgDev& M, const FineDev& F, Mg
   const int gr = blocks_for(M.N, kMaxRedBlocks);
   int zi = 0;
   cudaError_t e = capture_plain(st, [&]() {
-    k_pcg_init<<<gr, kT, 0, st>>>(M.N, W.kb, -1.0, diagT, W.kx, W.kr, W.b[0], W.a0dinv, W.x[0][0], W.d[0], W.lam,
-                                  W.part, W.sc);
+    launchk(st, gr, kT, 0, k_pcg_init, M.N, (const double*)W.kb, -1.0, diagT, W.kx, W.kr, W.b[0],
+            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.lam, W.part, W.sc);
     zi = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
   }, &out[0]);
   if (e != cudaSuccess) return e;
   const float* z = W.x[0][zi];
   return capture_while(st, [&](cudaGraphConditionalHandle h) {
-    k_pcg_beta<<<gr, kT, 0, st>>>(M.N, W.kr, z, W.z[0], W.part, W.sc);
-    k_pcg_pq<<<gr, kT, 0, st>>>(F, Tval, diagT, z, W.z[0], W.kp, W.kq, W.part, W.sc);
-    k_pcg_update<<<gr, kT, 0, st>>>(M.N, W.kp, W.kq, diagT, W.kx, W.kr, W.b[0], W.a0dinv, W.x[0][0], W.d[0], W.lam,
-                                    W.part, W.sc, h);
-    const int zj = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
-    (void)zj;
+    launchk(st, gr, kT, 0, k_pcg_beta, M.N, (const double*)W.kr, z, (const float*)W.z[0], W.part, W.sc);
+    launchk(st, gr, kT, 0, k_pcg_pq, F, Tval, diagT, z, W.z[0], W.kp, W.kq, W.part, W.sc);
+    launchk(st, gr, kT, 0, k_pcg_update, M.N, (const double*)W.kp, (const double*)W.kq, diagT, W.kx, W.kr, W.b[0],
+            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.lam, W.part, W.sc, h);
+    mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
   }, &out[1]);
 }
 
 // Right-preconditioned BiCGStab for J dx = -b (J: jd diagonal, Joff off-diagonal in the SELL layout; b = W.kb;
-// dx -> W.kx; stopping on ||W r|| with the weights in W.kv's companion wgt = W.ks before the start). out[0] the start
-// (with p^ = B p), out[1] the loop: v = J p^, s, s^ = B s, t = J s^, x and r with the test, p, p^ = B p.
+// dx -> W.kx; stopping on ||W r|| with W^2 = wgt). out[0] the start (with p^ = B p), out[1] the loop: v = J p^, s,
+// s^ = B s, t = J s^, x and r with the test, p, p^ = B p.
 cudaError_t mg_capture_bicgstab(cudaStream_t st, const MgDev& M, const FineDev& F, MgWork& W, const double* jd,
                                 const double* Joff, const double* wgt, cudaGraphExec_t* out) {
   const int gr = blocks_for(M.N, kMaxRedBlocks);
   int zi = 0;
   cudaError_t e = capture_plain(st, [&]() {
-    k_bicg_init<<<gr, kT, 0, st>>>(M.N, W.kb, -1.0, wgt, W.kx, W.kr, W.krh, W.kp, W.b[0], W.a0dinv, W.x[0][0],
-                                   W.d[0], W.lam, W.part, W.sc);
+    launchk(st, gr, kT, 0, k_bicg_init, M.N, (const double*)W.kb, -1.0, wgt, W.kx, W.kr, W.krh, W.kp, W.b[0],
+            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.lam, W.part, W.sc);
     zi = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
   }, &out[0]);
   if (e != cudaSuccess) return e;
   return capture_while(st, [&](cudaGraphConditionalHandle h) {
-    k_bicg_v<<<gr, kT, 0, st>>>(F, Joff, jd, W.x[0][zi], W.kpp, W.kv, W.krh, W.part, W.sc);
-    k_bicg_s<<<gr, kT, 0, st>>>(M.N, W.kr, W.kv, W.ks, W.b[0], W.a0dinv, W.x[0][0], W.d[0], W.lam, W.sc);
+    launchk(st, gr, kT, 0, k_bicg_v, F, Joff, jd, (const float*)W.x[0][zi], W.kpp, W.kv, (const double*)W.krh,
+            W.part, W.sc);
+    launchk(st, gr, kT, 0, k_bicg_s, M.N, (const double*)W.kr, (const double*)W.kv, W.ks, W.b[0],
+            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.lam, W.sc);
     const int zs = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
-    k_bicg_t<<<gr, kT, 0, st>>>(F, Joff, jd, W.x[0][zs], W.ks, W.kt, W.part, W.sc);
-    k_bicg_x<<<gr, kT, 0, st>>>(M.N, W.kpp, W.x[0][zs], W.ks, W.kt, W.krh, wgt, W.kx, W.kr, W.part, W.sc, h);
-    k_bicg_p<<<gr, kT, 0, st>>>(M.N, W.kr, W.kv, W.kp, W.b[0], W.a0dinv, W.x[0][0], W.d[0], W.lam, W.sc);
-    const int zp = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
-    (void)zp;
+    launchk(st, gr, kT, 0, k_bicg_t, F, Joff, jd, (const float*)W.x[0][zs], (const double*)W.ks, W.kt, W.part,
+            W.sc);
+    launchk(st, gr, kT, 0, k_bicg_x, M.N, (const double*)W.kpp, (const float*)W.x[0][zs], (const double*)W.ks,
+            (const double*)W.kt, (const double*)W.krh, wgt, W.kx, W.kr, W.part, W.sc, h);
+    launchk(st, gr, kT, 0, k_bicg_p, M.N, (const double*)W.kr, (const double*)W.kv, W.kp, W.b[0],
+            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.lam, W.sc);
+    mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
   }, &out[1]);
 }
 
@@ -1151,9 +1245,10 @@ cudaError_t mg_capture_bicgstab(cudaStream_t st, const MgDev& M, const FineDev& 
 cudaError_t mg_capture_apply(cudaStream_t st, const MgDev& M, const FineDev& F, MgWork& W, cudaGraphExec_t* out) {
   return capture_plain(st, [&]() {
     const int g0 = blocks_for(M.N, 4096);
-    k_apply_in<<<g0, kT, 0, st>>>(M.N, W.kb, W.b[0], W.a0dinv, W.x[0][0], W.d[0], W.lam);
+    launchk(st, g0, kT, 0, k_apply_in, M.N, (const double*)W.kb, W.b[0], (const float*)W.a0dinv, W.x[0][0], W.d[0],
+            (const float*)W.lam);
     const int zi = mg_enqueue_vcycle(st, M, F, W, nullptr);
-    k_apply_out<<<g0, kT, 0, st>>>(M.N, W.x[0][zi], W.kx);
+    launchk(st, g0, kT, 0, k_apply_out, M.N, (const float*)W.x[0][zi], W.kx);
   }, out);
 }
 

@@ -1157,8 +1157,10 @@ void mg_set_limits(nlmg_ctx* c, double tol) {
 int mg_pcg(nlmg_ctx* c, const double* R, const double* kap) {
   const MgDev& M = c->sh->MG;
   MgWork& W = c->mg;
-  const int pi = c->prof_begin(5);
+  const int ps = c->prof_begin(7);
   mg_enqueue_setup(c->st, M, c->F, W, c->Tval, c->diagT, kap);
+  c->prof_end(ps);
+  const int pi = c->prof_begin(5);
   CK(cudaMemcpyAsync(W.kb, R, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   mg_set_limits(c, c->lin_tol_eff);
   if (!W.g_pcg[0]) CK(mg_capture_pcg(c->st, M, c->F, W, c->Tval, c->diagT, W.g_pcg));
@@ -1167,9 +1169,10 @@ int mg_pcg(nlmg_ctx* c, const double* R, const double* kap) {
   c->prof_end(pi);
   const int it = mg_finish(c, "multigrid-preconditioned CG");
   const int V = mg_vcycle_kernels(M);
-  count_launch(1 + V + (it + 1) * (3 + V));
+  count_launch(1 + V + std::max(it, 1) * (3 + V));   // the start, then one loop body per iteration
   if (pi >= 0) {
-    c->prof.bytes[5] += c->sh->mg_bytes_setup + (double)(it + 1) * (c->sh->mg_bytes_vcycle + c->sh->mg_bytes_iter);
+    c->prof.bytes[5] += (double)(it + 1) * (c->sh->mg_bytes_vcycle + c->sh->mg_bytes_iter);
+    c->prof.bytes[7] += c->sh->mg_bytes_setup;
   }
   c->lin_iters += it;
   c->lin_iters_level[0] += it;
@@ -1182,8 +1185,10 @@ int mg_pcg(nlmg_ctx* c, const double* R, const double* kap) {
 int mg_bicgstab(nlmg_ctx* c, const double* R, const double* kap) {
   const MgDev& M = c->sh->MG;
   MgWork& W = c->mg;
-  const int pi = c->prof_begin(6);
+  const int ps = c->prof_begin(7);
   mg_enqueue_setup(c->st, M, c->F, W, c->Tval, c->diagT, kap);
+  c->prof_end(ps);
+  const int pi = c->prof_begin(6);
   CK(cudaMemcpyAsync(W.kb, R, (size_t)c->F.N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   mg_set_limits(c, c->newton_tol_eff);
   if (!W.g_bicg[0]) CK(mg_capture_bicgstab(c->st, M, c->F, W, c->jdiag, c->Joff, c->jdinv, W.g_bicg));
@@ -1192,10 +1197,10 @@ int mg_bicgstab(nlmg_ctx* c, const double* R, const double* kap) {
   c->prof_end(pi);
   const int it = mg_finish(c, "multigrid-preconditioned BiCGStab");
   const int V = mg_vcycle_kernels(M);
-  count_launch(1 + V + it * (5 + 2 * V));
+  count_launch(1 + V + std::max(it, 1) * (5 + 2 * V));
   if (pi >= 0) {
-    c->prof.bytes[6] += c->sh->mg_bytes_setup + (double)(2 * it + 1) * c->sh->mg_bytes_vcycle +
-                        (double)it * 2.0 * c->sh->mg_bytes_iter;
+    c->prof.bytes[6] += (double)(2 * it + 1) * c->sh->mg_bytes_vcycle + (double)it * 2.0 * c->sh->mg_bytes_iter;
+    c->prof.bytes[7] += c->sh->mg_bytes_setup;
   }
   c->lin_iters += it;
   c->lin_iters_level[0] += it;
@@ -2005,7 +2010,7 @@ nlmg_status nlmg_profile_read(nlmg_ctx* c, int32_t kernel, int64_t* launches, do
                               double* bytes_per_launch, double* flops_per_launch) {
   return guarded(c, [&]() -> nlmg_status {
     need_device(c);
-    if (kernel < 0 || kernel > 6) throw Error(NLMG_EINVAL, "kernel id");
+    if (kernel < 0 || kernel > 7) throw Error(NLMG_EINVAL, "kernel id");
     c->prof_flush();
     if (launches) *launches = c->prof.n[kernel];
     if (total_ms) *total_ms = c->prof.ms[kernel];

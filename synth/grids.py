@@ -252,6 +252,9 @@ def problem_config(name, scale=None):
       p = 1 left / 0 right, f = 0, aggregates of about 16 cells, 2 modes, 2 levels.
     chan3d_64: 64^3 hexahedra, channelized K over 6 decades, kappa = exp(2 p), aggregates of about 64 then 8
       cells, 4 modes, 3 levels. `scale` replaces 64 by a smaller side for tests.
+    chan3d_256: 256^3 hexahedra (16.8M cells), channelized K over 8 decades (seed 5), kappa = exp(2 p), 5 levels
+      (aggregates of about 64, then 8, 8, 8 cells), 6 modes per aggregate; its right-hand sides come from
+      multi_rhs_rows. `scale` replaces 256 for smaller instances.
     """
     if name == "cart2d_32":
         n = scale or 32
@@ -266,6 +269,14 @@ def problem_config(name, scale=None):
         mesh = cartesian_mesh((n, n, n), K)
         g = _dirichlet_data(mesh, 1.0, 0.0)
         opts = default_options(n_levels=3, agg_size=[64, 8, 8, 8], modes=[4, 4, 4, 4],
+                               dp_clamp=float(np.log(1.5) / 2.0))
+        return Problem(mesh, KAPPA_EXP, 2.0, np.zeros(mesh.n_cells), g, opts, name)
+    if name == "chan3d_256":
+        n = scale or 256
+        K = channelized_field((n, n, n), 8.0, 12, seed=5)
+        mesh = cartesian_mesh((n, n, n), K)
+        g = _dirichlet_data(mesh, 1.0, 0.0)
+        opts = default_options(n_levels=5, agg_size=[64, 8, 8, 8], modes=[6, 6, 6, 6],
                                dp_clamp=float(np.log(1.5) / 2.0))
         return Problem(mesh, KAPPA_EXP, 2.0, np.zeros(mesh.n_cells), g, opts, name)
     raise KeyError(name)

@@ -57,7 +57,9 @@ def test_results_identical_alone_and_in_the_mix(nlmg_lib):
 
 def test_admission_by_memory_and_oversized_request(nlmg_lib):
     reqs = _requests(3, seed=41)
-    srv = nlmg_lib.Server(max_inflight=3, mem_budget_bytes=3 << 20)   # ~one small request at a time
+    # a budget of the largest request's estimate: the requests fit one at a time
+    budget = max(nlmg_lib.request_bytes(r[0]) for r in reqs)
+    srv = nlmg_lib.Server(max_inflight=3, mem_budget_bytes=budget)
     tickets = [srv.submit(mesh, 0, a, opts, f, g) for mesh, a, opts, f, g in reqs]
     res = [srv.poll(t, wait_ms=120000) for t in tickets]
     assert all(r is not None and r[3] == 0 for r in res)
