@@ -198,6 +198,14 @@ nlmg_status nlmg_solve_many(nlmg_ctx* ctx, int32_t n_rhs, const double* f_cell, 
                             const double* x0, double tol_rel, double tol_abs, int32_t max_cycles, int32_t n_streams,
                             double* p_out, nlmg_report* rep, int32_t* status);
 
+/* nlmg_solve_many on device-resident rows: f_dev[n_rhs][n_cells], g_dev[n_rhs][n_faces], x0_dev (NULL = all zero)
+ * and p_dev[n_rhs][n_cells] are device pointers on the context's device, complete before the call (each instance
+ * reads its rows on its own stream); every row is bitwise the nlmg_solve_device result on a context with the same SM
+ * share. rep and status are host arrays as for nlmg_solve_many. */
+nlmg_status nlmg_solve_many_device(nlmg_ctx* ctx, int32_t n_rhs, const double* f_dev, const double* g_dev,
+                                   const double* x0_dev, double tol_rel, double tol_abs, int32_t max_cycles,
+                                   int32_t n_streams, double* p_dev, nlmg_report* rep, int32_t* status);
+
 /* Sets the problem data: f_cell[n_cells] (source density f|_K) and g_face[n_faces] (Dirichlet pressure or Neumann
  * flux density per boundary face, ignored on interior faces). [f]_K = |tau_K| f_K + sum_Neumann |eps| g_N
  * (definitions under eq. FV_matrix). */

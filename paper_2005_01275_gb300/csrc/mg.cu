@@ -18,6 +18,9 @@ namespace nlmg {
 
 namespace {
 
+static_assert(kMgDegFine <= kMgMaxDeg && kMgDegCoarse <= kMgMaxDeg, "Chebyshev coefficient table too small");
+static_assert(kMgMaxLevels * kMgMaxDeg <= 32, "the coefficient table kernel runs one warp");
+
 constexpr int kT = 256;               // threads per block of the preconditioner kernels
 constexpr int kMaxRedBlocks = 1024;   // grid cap of the reduction kernels (partials summed by one block)
 
@@ -104,6 +107,13 @@ __device__ __forceinline__ void cheb_coef(float lam, int k, float& c1, float& c2
   }
   c1 = (float)(rho * rho_prev);
   c2 = (float)(2.0 * rho / delta);
+}
+
+// The coefficients of every level and step, computed once per setup from the Gershgorin bounds (k_cheb_table):
+// tab[(l * kMgMaxDeg + k) * 2 + {0, 1}] = (c1, c2) of cheb_coef.
+__device__ __forceinline__ void cheb_tab(const float* __restrict__ tab, int l, int k, float& c1, float& c2) {
+  c1 = tab[(l * kMgMaxDeg + k) * 2];
+  c2 = tab[(l * kMgMaxDeg + k) * 2 + 1];
 }
 
 __device__ __forceinline__ bool stop(const int* done) { return done && *((volatile const int*)done) != 0; }
@@ -324,6 +334,18 @@ __global__ void k_block_inv(int nc, const int* __restrict__ rowptr, const int* _
   if ((threadIdx.x & 31) == 0) atomic_max_pos(lam, g);
 }
 
+// Chebyshev coefficient table of every level and step from the Gershgorin bounds (one thread per entry).
+__global__ void k_cheb_table(const float* __restrict__ lam, float* __restrict__ tab) {
+  pdl_start();
+  const int t = threadIdx.x;
+  if (t >= kMgMaxLevels * kMgMaxDeg) return;
+  const int l = t / kMgMaxDeg, k = t % kMgMaxDeg;
+  float c1 = 0.0f, c2 = 0.0f;
+  if (lam[l] > 0.0f) cheb_coef(lam[l], k, c1, c2);
+  tab[2 * t] = c1;
+  tab[2 * t + 1] = c2;
+}
+
 // Dense inverse of the coarsest level (n = nc * mb <= kMgMaxCoarse) in one block: the blocks assembled into an
 // n x n FP64 matrix in shared memory, in-place Gauss-Jordan (symmetric positive definite, no pivoting).
 __global__ void k_coarse_inv(int nc, int mb, const int* __restrict__ rowptr, const int* __restrict__ col,
@@ -378,7 +400,7 @@ __global__ void k_cheb0(FineDev F, const float* __restrict__ a0off, const float*
   pdl_start();
   if (stop(done)) return;
   float c1, c2;
-  cheb_coef(lam[0], k, c1, c2);
+  cheb_tab(lam, 0, k, c1, c2);
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < F.N; K += gridDim.x * blockDim.x) {
     const int w = F.sell_w[K >> 5];
     int e = F.sell_off[K >> 5] + (K & 31);
@@ -423,7 +445,7 @@ __global__ void k_chebl(int nc, const int* __restrict__ rowptr, const int* __res
   pdl_start();
   if (stop(done)) return;
   float c1, c2;
-  cheb_coef(lam[l], k, c1, c2);
+  cheb_tab(lam, l, k, c1, c2);
   const int lane = threadIdx.x & 31, u = lane & 7;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -474,7 +496,7 @@ __global__ void k_restr(int mbf, const float* __restrict__ res, const float* __r
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   float c1 = 0.0f, c2 = 0.0f;
-  if (first) cheb_coef(lam[lc], 0, c1, c2);
+  if (first) cheb_tab(lam, lc, 0, c1, c2);
   // one value per child (level 0): lanes take children one each; else eight lanes per child
   const int cstep = mbf == 1 ? 32 : 4, c0 = mbf == 1 ? lane : grp, uu = mbf == 1 ? 0 : u;
   for (int A = warp; A < ncc; A += nw) {
@@ -598,7 +620,7 @@ __global__ void k_pcg_init(int N, const double* __restrict__ b, double bscale, c
                            const float* __restrict__ lam, double* part, MgScal* sc) {
   pdl_start();
   float c1, c2;
-  cheb_coef(lam[0], 0, c1, c2);
+  cheb_tab(lam, 0, 0, c1, c2);
   double v[1] = {0.0};
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
     const double ri = bscale * b[K];
@@ -606,7 +628,7 @@ __global__ void k_pcg_init(int N, const double* __restrict__ b, double bscale, c
     r[K] = ri;
     r32[K] = (float)ri;
     first_step0(K, (float)ri, a0dinv, c2, x0, d0);
-    v[0] = fma(ri * ri, 1.0 / diagT[K], v[0]);
+    v[0] = fma(ri * ri, (double)a0dinv[K], v[0]);   // ||S r||^2 with S^2 = 1 / A_KK
   }
   __shared__ double out[1];
   if (reduce_last<1>(v, part, &sc->cnt[0], out) && threadIdx.x == 0) {
@@ -674,7 +696,7 @@ __global__ void k_pcg_update(int N, const double* __restrict__ p, const double* 
   }
   const double alpha = sc->alpha;
   float c1, c2;
-  cheb_coef(lam[0], 0, c1, c2);
+  cheb_tab(lam, 0, 0, c1, c2);
   double v[1] = {0.0};
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
     x[K] = fma(alpha, p[K], x[K]);
@@ -682,7 +704,7 @@ __global__ void k_pcg_update(int N, const double* __restrict__ p, const double* 
     r[K] = ri;
     r32[K] = (float)ri;
     first_step0(K, (float)ri, a0dinv, c2, x0, d0);
-    v[0] = fma(ri * ri, 1.0 / diagT[K], v[0]);
+    v[0] = fma(ri * ri, (double)a0dinv[K], v[0]);   // ||S r||^2 with S^2 = 1 / A_KK
   }
   __shared__ double out[1];
   if (reduce_last<1>(v, part, &sc->cnt[3], out) && threadIdx.x == 0) {
@@ -716,7 +738,7 @@ __global__ void k_bicg_init(int N, const double* __restrict__ b, double bscale, 
                             double* part, MgScal* sc) {
   pdl_start();
   float c1, c2;
-  cheb_coef(lam[0], 0, c1, c2);
+  cheb_tab(lam, 0, 0, c1, c2);
   double v[2] = {0.0, 0.0};
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
     const double ri = bscale * b[K];
@@ -764,7 +786,7 @@ __global__ void k_bicg_s(int N, const double* __restrict__ r, const double* __re
   if (stop(&sc->done)) return;
   const double alpha = sc->alpha;
   float c1, c2;
-  cheb_coef(lam[0], 0, c1, c2);
+  cheb_tab(lam, 0, 0, c1, c2);
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
     const double sk = fma(-alpha, v[K], r[K]);
     s[K] = sk;
@@ -829,7 +851,7 @@ __global__ void k_bicg_p(int N, const double* __restrict__ r, const double* __re
   if (stop(&sc->done)) return;
   const double beta = sc->beta, omega = sc->omega;
   float c1, c2;
-  cheb_coef(lam[0], 0, c1, c2);
+  cheb_tab(lam, 0, 0, c1, c2);
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
     const double pk = fma(beta, fma(-omega, v[K], p[K]), r[K]);
     p[K] = pk;
@@ -844,7 +866,7 @@ __global__ void k_apply_in(int N, const double* __restrict__ b, float* __restric
                            const float* __restrict__ lam) {
   pdl_start();
   float c1, c2;
-  cheb_coef(lam[0], 0, c1, c2);
+  cheb_tab(lam, 0, 0, c1, c2);
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
     r32[K] = (float)b[K];
     first_step0(K, (float)b[K], a0dinv, c2, x0, d0);
@@ -1069,6 +1091,8 @@ void mg_enqueue_setup(cudaStream_t st, const MgDev& M, const FineDev& F, const M
                                   W.lam + l));
     ++n;
   }
+  launchk(st, 1, 32, 0, k_cheb_table, (const float*)W.lam, W.coef);
+  ++n;
   const int C = M.L - 1, nco = M.nc[C] * M.mb[C];
   launchk(st, 1, 512, (size_t)(nco * nco + nco) * sizeof(double), k_coarse_inv, M.nc[C], M.mb[C],
           (const int*)M.rowptr[C], (const int*)M.col[C], (const float*)W.aval[C], W.cinv);
@@ -1084,7 +1108,7 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
   // down: level-0 smoothing, residual into d[0] (dead until the post-smoothing rewrites it), restriction
   for (int k = 1; k < kMgDegFine; ++k) {
     launchk(st, g0, kT, 0, k_cheb0, F, (const float*)W.a0off, (const float*)W.a0diag, (const float*)W.a0dinv,
-            (const float*)W.b[0], (const float*)W.x[0][cur[0]], W.x[0][1 - cur[0]], W.d[0], (const float*)W.lam, k,
+            (const float*)W.b[0], (const float*)W.x[0][cur[0]], W.x[0][1 - cur[0]], W.d[0], (const float*)W.coef, k,
             flag);
     cur[0] ^= 1;
   }
@@ -1092,14 +1116,14 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
           (const float*)W.x[0][cur[0]], W.d[0], flag);
   launchk(st, warps_grid(M.nc[1]), kT, 0, k_restr, 1, (const float*)W.d[0], (const float*)M.P[0],
           (const int*)M.ch_off[0], (const int*)M.ch[0], M.nc[1], M.mb[1], W.b[1], (const float*)W.dinv[1],
-          W.x[1][0], W.d[1], (const float*)W.lam, 1, C > 1 ? 1 : 0, flag);
+          W.x[1][0], W.d[1], (const float*)W.coef, 1, C > 1 ? 1 : 0, flag);
   for (int l = 1; l < C; ++l) {
     const int gl = warps_grid(M.nc[l]);
     for (int k = 1; k < kMgDegCoarse; ++k) {
       MG_MB_SWITCH(M.mb[l], launchk(st, gl, kT, 0, k_chebl<MB>, M.nc[l], (const int*)M.rowptr[l],
                                     (const int*)M.col[l], (const float*)W.aval[l], (const float*)W.dinv[l],
                                     (const float*)W.b[l], (const float*)W.x[l][cur[l]], W.x[l][1 - cur[l]], W.d[l],
-                                    (const float*)W.lam, l, k, flag));
+                                    (const float*)W.coef, l, k, flag));
       cur[l] ^= 1;
     }
     MG_MB_SWITCH(M.mb[l], launchk(st, gl, kT, 0, k_resl<MB>, M.nc[l], (const int*)M.rowptr[l],
@@ -1107,7 +1131,7 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
                                   (const float*)W.x[l][cur[l]], W.d[l], flag));
     launchk(st, warps_grid(M.nc[l + 1]), kT, 0, k_restr, M.mb[l], (const float*)W.d[l], (const float*)M.P[l],
             (const int*)M.ch_off[l], (const int*)M.ch[l], M.nc[l + 1], M.mb[l + 1], W.b[l + 1],
-            (const float*)W.dinv[l + 1], W.x[l + 1][0], W.d[l + 1], (const float*)W.lam, l + 1, l + 1 < C ? 1 : 0,
+            (const float*)W.dinv[l + 1], W.x[l + 1][0], W.d[l + 1], (const float*)W.coef, l + 1, l + 1 < C ? 1 : 0,
             flag);
   }
   launchk(st, 1, kMgMaxCoarse, 0, k_coarse_solve, M.nc[C] * M.mb[C], (const float*)W.cinv, (const float*)W.b[C],
@@ -1121,7 +1145,7 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
       MG_MB_SWITCH(M.mb[l], launchk(st, gl, kT, 0, k_chebl<MB>, M.nc[l], (const int*)M.rowptr[l],
                                     (const int*)M.col[l], (const float*)W.aval[l], (const float*)W.dinv[l],
                                     (const float*)W.b[l], (const float*)W.x[l][cur[l]], W.x[l][1 - cur[l]], W.d[l],
-                                    (const float*)W.lam, l, k, flag));
+                                    (const float*)W.coef, l, k, flag));
       cur[l] ^= 1;
     }
   }
@@ -1129,7 +1153,7 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
           (const float*)W.x[1][cur[1]], W.x[0][cur[0]], flag);
   for (int k = 0; k < kMgDegFine; ++k) {
     launchk(st, g0, kT, 0, k_cheb0, F, (const float*)W.a0off, (const float*)W.a0diag, (const float*)W.a0dinv,
-            (const float*)W.b[0], (const float*)W.x[0][cur[0]], W.x[0][1 - cur[0]], W.d[0], (const float*)W.lam, k,
+            (const float*)W.b[0], (const float*)W.x[0][cur[0]], W.x[0][1 - cur[0]], W.d[0], (const float*)W.coef, k,
             flag);
     cur[0] ^= 1;
   }
@@ -1198,7 +1222,7 @@ cudaError_t mg_capture_pcg(cudaStream_t st, const MgDev& M, const FineDev& F, Mg
   int zi = 0;
   cudaError_t e = capture_plain(st, [&]() {
     launchk(st, gr, kT, 0, k_pcg_init, M.N, (const double*)W.kb, -1.0, diagT, W.kx, W.kr, W.b[0],
-            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.lam, W.part, W.sc);
+            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.coef, W.part, W.sc);
     zi = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
   }, &out[0]);
   if (e != cudaSuccess) return e;
@@ -1207,7 +1231,7 @@ cudaError_t mg_capture_pcg(cudaStream_t st, const MgDev& M, const FineDev& F, Mg
     launchk(st, gr, kT, 0, k_pcg_beta, M.N, (const double*)W.kr, z, (const float*)W.z[0], W.part, W.sc);
     launchk(st, gr, kT, 0, k_pcg_pq, F, Tval, diagT, z, W.z[0], W.kp, W.kq, W.part, W.sc);
     launchk(st, gr, kT, 0, k_pcg_update, M.N, (const double*)W.kp, (const double*)W.kq, diagT, W.kx, W.kr, W.b[0],
-            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.lam, W.part, W.sc, h);
+            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.coef, W.part, W.sc, h);
     mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
   }, &out[1]);
 }
@@ -1221,7 +1245,7 @@ cudaError_t mg_capture_bicgstab(cudaStream_t st, const MgDev& M, const FineDev& 
   int zi = 0;
   cudaError_t e = capture_plain(st, [&]() {
     launchk(st, gr, kT, 0, k_bicg_init, M.N, (const double*)W.kb, -1.0, wgt, W.kx, W.kr, W.krh, W.kp, W.b[0],
-            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.lam, W.part, W.sc);
+            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.coef, W.part, W.sc);
     zi = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
   }, &out[0]);
   if (e != cudaSuccess) return e;
@@ -1229,14 +1253,14 @@ cudaError_t mg_capture_bicgstab(cudaStream_t st, const MgDev& M, const FineDev& 
     launchk(st, gr, kT, 0, k_bicg_v, F, Joff, jd, (const float*)W.x[0][zi], W.kpp, W.kv, (const double*)W.krh,
             W.part, W.sc);
     launchk(st, gr, kT, 0, k_bicg_s, M.N, (const double*)W.kr, (const double*)W.kv, W.ks, W.b[0],
-            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.lam, W.sc);
+            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.coef, W.sc);
     const int zs = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
     launchk(st, gr, kT, 0, k_bicg_t, F, Joff, jd, (const float*)W.x[0][zs], (const double*)W.ks, W.kt, W.part,
             W.sc);
     launchk(st, gr, kT, 0, k_bicg_x, M.N, (const double*)W.kpp, (const float*)W.x[0][zs], (const double*)W.ks,
             (const double*)W.kt, (const double*)W.krh, wgt, W.kx, W.kr, W.part, W.sc, h);
     launchk(st, gr, kT, 0, k_bicg_p, M.N, (const double*)W.kr, (const double*)W.kv, W.kp, W.b[0],
-            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.lam, W.sc);
+            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.coef, W.sc);
     mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
   }, &out[1]);
 }
@@ -1246,7 +1270,7 @@ cudaError_t mg_capture_apply(cudaStream_t st, const MgDev& M, const FineDev& F, 
   return capture_plain(st, [&]() {
     const int g0 = blocks_for(M.N, 4096);
     launchk(st, g0, kT, 0, k_apply_in, M.N, (const double*)W.kb, W.b[0], (const float*)W.a0dinv, W.x[0][0], W.d[0],
-            (const float*)W.lam);
+            (const float*)W.coef);
     const int zi = mg_enqueue_vcycle(st, M, F, W, nullptr);
     launchk(st, g0, kT, 0, k_apply_out, M.N, (const float*)W.x[0][zi], W.kx);
   }, out);

@@ -23,6 +23,7 @@ constexpr int kMgMaxCoarse = 128;   // largest coarsest-level system (unknowns, 
 constexpr int kMgDegFine = 2;       // Chebyshev steps before and after the coarse correction, level 0
 constexpr int kMgDegCoarse = 2;     // the same on levels 1 .. L-2
 constexpr double kMgAlpha = 4.0;    // Chebyshev interval [lam / alpha, lam]
+constexpr int kMgMaxDeg = 4;        // Chebyshev steps per smoothing at most (coefficient table size)
 
 // Static structure of the preconditioner (host side, built once per hierarchy).
 struct MgHost {
@@ -60,6 +61,7 @@ struct MgWork {
   float *aval[kMgMaxLevels] = {nullptr}, *dinv[kMgMaxLevels] = {nullptr};
   float* cinv = nullptr;
   float* lam = nullptr;                                  // [kMgMaxLevels] Gershgorin bounds
+  float* coef = nullptr;                                 // [kMgMaxLevels][kMgMaxDeg][2] Chebyshev coefficients
   float *x[kMgMaxLevels][2] = {{nullptr}}, *b[kMgMaxLevels] = {nullptr}, *d[kMgMaxLevels] = {nullptr};
   // Krylov vectors (FP64) and the preconditioned vectors (FP32)
   double *kx = nullptr, *kr = nullptr, *kp = nullptr, *kq = nullptr, *kb = nullptr;

@@ -1123,6 +1123,7 @@ void alloc_mg(nlmg_ctx* c) {
   const int nco = M.nc[M.L - 1] * M.mb[M.L - 1];
   W.cinv = c->dalloc<float>((size_t)nco * nco);
   W.lam = c->dalloc<float>(kMgMaxLevels);
+  W.coef = c->dalloc<float>(kMgMaxLevels * kMgMaxDeg * 2);
   W.kx = c->cx;
   W.z[0] = c->dalloc<float>(N);
   for (double** pp : {&W.kr, &W.kp, &W.kq, &W.kb, &W.kv, &W.ks, &W.kt, &W.krh, &W.kpp}) *pp = c->dalloc<double>(N);
@@ -1616,9 +1617,9 @@ nlmg_status nlmg_set_options(nlmg_ctx* c, const nlmg_options* opt) {
   });
 }
 
-nlmg_status nlmg_solve_many(nlmg_ctx* c, int32_t n_rhs, const double* f_cell, const double* g_face,
-                            const double* x0, double tol_rel, double tol_abs, int32_t max_cycles, int32_t n_streams,
-                            double* p_out, nlmg_report* rep, int32_t* status) {
+static nlmg_status solve_many_impl(nlmg_ctx* c, int32_t n_rhs, const double* f_cell, const double* g_face,
+                                   const double* x0, double tol_rel, double tol_abs, int32_t max_cycles,
+                                   int32_t n_streams, double* p_out, nlmg_report* rep, int32_t* status, bool device) {
   return guarded(c, [&]() -> nlmg_status {
     need_device(c);
     if (n_rhs < 0 || (n_rhs > 0 && (!f_cell || !g_face || !p_out))) throw Error(NLMG_EINVAL, "bad argument");
@@ -1662,8 +1663,10 @@ nlmg_status nlmg_solve_many(nlmg_ctx* c, int32_t n_rhs, const double* f_cell, co
       for (;;) {
         const int r = next.fetch_add(1);
         if (r >= n_rhs) break;
-        st[r] = nlmg_solve(w, f_cell + r * N, g_face + r * NF, x0 ? x0 + r * N : nullptr, tol_rel, tol_abs,
-                           max_cycles, p_out + r * N, rep ? rep + r : nullptr);
+        st[r] = device ? nlmg_solve_device(w, f_cell + r * N, g_face + r * NF, x0 ? x0 + r * N : nullptr, tol_rel,
+                                           tol_abs, max_cycles, p_out + r * N, rep ? rep + r : nullptr)
+                       : nlmg_solve(w, f_cell + r * N, g_face + r * NF, x0 ? x0 + r * N : nullptr, tol_rel, tol_abs,
+                                    max_cycles, p_out + r * N, rep ? rep + r : nullptr);
         if (st[r] != NLMG_OK) msg[r] = w->err;
       }
     };
@@ -1683,6 +1686,20 @@ nlmg_status nlmg_solve_many(nlmg_ctx* c, int32_t n_rhs, const double* f_cell, co
     }
     return worst;
   });
+}
+
+nlmg_status nlmg_solve_many(nlmg_ctx* c, int32_t n_rhs, const double* f_cell, const double* g_face,
+                            const double* x0, double tol_rel, double tol_abs, int32_t max_cycles, int32_t n_streams,
+                            double* p_out, nlmg_report* rep, int32_t* status) {
+  return solve_many_impl(c, n_rhs, f_cell, g_face, x0, tol_rel, tol_abs, max_cycles, n_streams, p_out, rep, status,
+                         false);
+}
+
+nlmg_status nlmg_solve_many_device(nlmg_ctx* c, int32_t n_rhs, const double* f_dev, const double* g_dev,
+                                   const double* x0_dev, double tol_rel, double tol_abs, int32_t max_cycles,
+                                   int32_t n_streams, double* p_dev, nlmg_report* rep, int32_t* status) {
+  return solve_many_impl(c, n_rhs, f_dev, g_dev, x0_dev, tol_rel, tol_abs, max_cycles, n_streams, p_dev, rep, status,
+                         true);
 }
 
 nlmg_status nlmg_set_data(nlmg_ctx* c, const double* f_cell, const double* g_face) {

@@ -87,6 +87,8 @@ SIGNATURES = {
     "nlmg_instance": (C.c_int, [_P, C.POINTER(Kappa), C.POINTER(_P)]),
     "nlmg_solve_many": (C.c_int, [_P, C.c_int32, _D, _D, _D, C.c_double, C.c_double, C.c_int32, C.c_int32, _D,
                                   C.POINTER(Report), _I]),
+    "nlmg_solve_many_device": (C.c_int, [_P, C.c_int32, _P, _P, _P, C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                         _P, C.POINTER(Report), _I]),
     "nlmg_set_options": (C.c_int, [_P, C.POINTER(Options)]),
     "nlmg_tune_sm_share": (C.c_int, [_P, C.c_int32, _D, _D, _I, _D]),
     "nlmg_set_data": (C.c_int, [_P, _D, _D]),
@@ -236,6 +238,15 @@ class Context:
         rates = np.zeros(4)
         self._check(lib().nlmg_tune_sm_share(self.h, n, _dp(f), _dp(g), C.byref(best), _dp(rates)))
         return best.value, rates
+
+    def solve_many_device(self, n_rhs, f_ptr, g_ptr, p_ptr, tol_rel=1e-8, tol_abs=1e-10, max_cycles=50, n_streams=0):
+        """nlmg_solve_many on device-resident rows (raw device pointers of [n_rhs][n_cells], [n_rhs][n_faces] and
+        [n_rhs][n_cells] arrays); returns (list of report dicts, status array, overall status)."""
+        reps = (Report * n_rhs)()
+        sts = np.zeros(n_rhs, dtype=np.int32)
+        st = lib().nlmg_solve_many_device(self.h, int(n_rhs), _P(f_ptr), _P(g_ptr), None, tol_rel, tol_abs,
+                                          max_cycles, int(n_streams), _P(p_ptr), reps, sts.ctypes.data_as(_I))
+        return [r.as_dict() for r in reps], sts, st
 
     def solve_many(self, f_rows, g_rows, x0_rows=None, tol_rel=1e-8, tol_abs=1e-10, max_cycles=50, n_streams=0,
                    allow_noconv=False):
