@@ -85,7 +85,9 @@ typedef struct {
   double coarse_lin_tol;     /* relative tolerance of the coarse-level (hybridized) CG solves (default 1e-1) */
   int32_t lin_precision;     /* 0: level-0 CG in FP64; 1: level-0 CG vectors and matrix in FP32 (tolerance floored
                                 at 1e-6), inside the FP64 nonlinear iteration; the coarse levels' hybridized CG and
-                                the Newton steps' BiCGStab stay FP64 */
+                                the Newton steps' BiCGStab stay FP64. With lin_precond = 1 the V-cycle is FP32 and the
+                                Krylov iteration FP64 whatever this is, and 2 stores the V-cycle's transfers P in BF16
+                                (FP32 accumulation; the Galerkin operators use the same rounded P) */
   int32_t setup_threads;     /* host threads for the setup (0 = all) */
   int32_t max_sms;           /* SMs the persistent solver kernels of a context may use (0 = all): contexts that
                                 solve concurrently (nlmg_solve_many, the request loop) can then run side by side.

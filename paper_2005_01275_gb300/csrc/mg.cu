@@ -126,6 +126,9 @@ __device__ __forceinline__ void pdl_start() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+__device__ __forceinline__ float pval(const float* __restrict__ p, size_t i) { return p[i]; }
+__device__ __forceinline__ float pval(const __nv_bfloat16* __restrict__ p, size_t i) { return __bfloat162float(p[i]); }
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -166,9 +169,9 @@ __global__ void k_fine_vals(FineDev F, const double* __restrict__ Tval, const do
 // contributions (K, L, e, type): 0 interior face inside the aggregate, T (P_K - P_L)(P_K - P_L)^T; 1 face to another
 // aggregate seen from this one's cell K, T P_K P_K^T; 2 the off-diagonal part, -T P_K P_L^T; 3 Dirichlet face (L = its
 // entry in the Dirichlet list), h P_K P_K^T with h = kappa_K Ups_K.
-template <int MB>
+template <int MB, class PT>
 __global__ void k_asm1(int nblk, const int* __restrict__ off, const int4* __restrict__ list,
-                       const float* __restrict__ P0, const double* __restrict__ Tval, const double* __restrict__ kap,
+                       const PT* __restrict__ P0, const double* __restrict__ Tval, const double* __restrict__ kap,
                        const double* __restrict__ dir_ups, float* __restrict__ aval) {
   pdl_start();
   const int lane = threadIdx.x & 31;
@@ -182,7 +185,7 @@ __global__ void k_asm1(int nblk, const int* __restrict__ off, const int4* __rest
       const int4 t = list[c];
       float pk[MB], pl[MB];
 #pragma unroll
-      for (int j = 0; j < MB; ++j) pk[j] = P0[(size_t)t.x * MB + j];
+      for (int j = 0; j < MB; ++j) pk[j] = pval(P0, (size_t)t.x * MB + j);
       float w;
       if (t.w == 3) {
         w = (float)(kap[t.x] * dir_ups[t.y]);
@@ -191,7 +194,7 @@ __global__ void k_asm1(int nblk, const int* __restrict__ off, const int4* __rest
       } else {
         w = (float)Tval[t.z];
 #pragma unroll
-        for (int j = 0; j < MB; ++j) pl[j] = P0[(size_t)t.y * MB + j];
+        for (int j = 0; j < MB; ++j) pl[j] = pval(P0, (size_t)t.y * MB + j);
         if (t.w == 0) {
 #pragma unroll
           for (int j = 0; j < MB; ++j) {
@@ -234,9 +237,9 @@ __global__ void k_pad_diag(int nc, int mb, const int* __restrict__ dpos, const i
 // Level-l Galerkin blocks (l >= 2) from the level-(l-1) blocks: block (A, B) = sum over (c, d) with agg(c) = A,
 // agg(d) = B of P_c^T A_cd P_d, P_c the mbf x MB transfer block of level-(l-1) cell c. One warp per block, lanes
 // taking the contributions in turn, then a fixed shuffle tree.
-template <int MB>
+template <int MB, class PT>
 __global__ void k_asml(int nblk, int mbf, const int* __restrict__ off, const int4* __restrict__ list,
-                       const float* __restrict__ Pf, const float* __restrict__ afine, float* __restrict__ aval) {
+                       const PT* __restrict__ Pf, const float* __restrict__ afine, float* __restrict__ aval) {
   pdl_start();
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -248,8 +251,7 @@ __global__ void k_asml(int nblk, int mbf, const int* __restrict__ off, const int
     for (int c = off[b] + lane; c < off[b + 1]; c += 32) {
       const int4 t = list[c];   // (source block, c, d, -)
       const float* As = afine + (size_t)t.x * mbf * mbf;
-      const float* Pc = Pf + (size_t)t.y * mbf * MB;
-      const float* Pd = Pf + (size_t)t.z * mbf * MB;
+      const size_t pc = (size_t)t.y * mbf * MB, pd = (size_t)t.z * mbf * MB;
       for (int i = 0; i < mbf; ++i) {
         float ti[MB];
 #pragma unroll
@@ -257,11 +259,11 @@ __global__ void k_asml(int nblk, int mbf, const int* __restrict__ off, const int
         for (int j = 0; j < mbf; ++j) {
           const float a = As[i * mbf + j];
 #pragma unroll
-          for (int v = 0; v < MB; ++v) ti[v] = fmaf(a, Pd[j * MB + v], ti[v]);
+          for (int v = 0; v < MB; ++v) ti[v] = fmaf(a, pval(Pf, pd + j * MB + v), ti[v]);
         }
 #pragma unroll
         for (int u = 0; u < MB; ++u) {
-          const float pu = Pc[i * MB + u];
+          const float pu = pval(Pf, pc + i * MB + u);
 #pragma unroll
           for (int v = 0; v < MB; ++v) acc[u * MB + v] = fmaf(pu, ti[v], acc[u * MB + v]);
         }
@@ -486,7 +488,8 @@ __global__ void k_resl(int nc, const int* __restrict__ rowptr, const int* __rest
 // Restriction of a residual (mbf per cell on level l) to level l+1 (mb per cell), one warp per level-(l+1) cell A:
 // lane = k * 8 + u takes component u of children k, k + 4, ...; a shuffle tree adds the lanes. `first` adds the first
 // Chebyshev step of level l+1 (x = D^-1 b / theta, d = x).
-__global__ void k_restr(int mbf, const float* __restrict__ res, const float* __restrict__ Pl,
+template <class PT>
+__global__ void k_restr(int mbf, const float* __restrict__ res, const PT* __restrict__ Pl,
                         const int* __restrict__ ch_off, const int* __restrict__ ch, int ncc, int mb,
                         float* __restrict__ bc, const float* __restrict__ dinvc, float* __restrict__ xc,
                         float* __restrict__ dc, const float* __restrict__ lam, int lc, int first, const int* done) {
@@ -507,10 +510,10 @@ __global__ void k_restr(int mbf, const float* __restrict__ res, const float* __r
       for (int t = ch_off[A] + c0; t < ch_off[A + 1]; t += cstep) {
         const int c = ch[t];
         const float r = res[(size_t)c * mbf + uu];
-        const float* Pr = Pl + ((size_t)c * mbf + uu) * mb;
+        const size_t pr = ((size_t)c * mbf + uu) * mb;
 #pragma unroll
         for (int j = 0; j < kMaxM; ++j)
-          if (j < mb) acc[j] = fmaf(Pr[j], r, acc[j]);
+          if (j < mb) acc[j] = fmaf(pval(Pl, pr + j), r, acc[j]);
       }
     }
 #pragma unroll
@@ -564,29 +567,29 @@ __global__ void k_coarse_solve(int n, const float* __restrict__ cinv, const floa
 }
 
 // x_0 += P e on level 0 (per fine cell) and on a block level (per cell and component).
-__global__ void k_pro0(int N, int mb, const float* __restrict__ P0, const int* __restrict__ agg,
+template <class PT>
+__global__ void k_pro0(int N, int mb, const PT* __restrict__ P0, const int* __restrict__ agg,
                        const float* __restrict__ e, float* __restrict__ x, const int* done) {
   pdl_start();
   if (stop(done)) return;
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
-    const float* PK = P0 + (size_t)K * mb;
     const float* ea = e + (size_t)agg[K] * mb;
     float s = x[K];
-    for (int j = 0; j < mb; ++j) s = fmaf(PK[j], ea[j], s);
+    for (int j = 0; j < mb; ++j) s = fmaf(pval(P0, (size_t)K * mb + j), ea[j], s);
     x[K] = s;
   }
 }
-__global__ void k_prol(int nc, int mbf, int mb, const float* __restrict__ Pl, const int* __restrict__ agg,
+template <class PT>
+__global__ void k_prol(int nc, int mbf, int mb, const PT* __restrict__ Pl, const int* __restrict__ agg,
                        const float* __restrict__ e, float* __restrict__ x, const int* done) {
   pdl_start();
   if (stop(done)) return;
   const long total = (long)nc * mbf;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const int c = (int)(i / mbf);
-    const float* Pr = Pl + (size_t)i * mb;
     const float* ea = e + (size_t)agg[c] * mb;
     float s = x[i];
-    for (int j = 0; j < mb; ++j) s = fmaf(Pr[j], ea[j], s);
+    for (int j = 0; j < mb; ++j) s = fmaf(pval(Pl, (size_t)i * mb + j), ea[j], s);
     x[i] = s;
   }
 }
@@ -1071,16 +1074,28 @@ void mg_enqueue_setup(cudaStream_t st, const MgDev& M, const FineDev& F, const M
                       const double* diagT, const double* kap) {
   cudaMemsetAsync(W.lam, 0, kMgMaxLevels * sizeof(float), st);
   launchk(st, blocks_for(M.N, 4096), kT, 0, k_fine_vals, F, Tval, diagT, W.a0off, W.a0diag, W.a0dinv, W.lam);
-  MG_MB_SWITCH(M.mb[1], launchk(st, warps_grid(M.nblk[1]), kT, 0, k_asm1<MB>, M.nblk[1], (const int*)M.asm_off[1],
-                                (const int4*)M.asm_list[1], (const float*)M.P[0], Tval, kap,
-                                (const double*)F.dir_ups, W.aval[1]));
+  if (W.bf16) {
+    MG_MB_SWITCH(M.mb[1], launchk(st, warps_grid(M.nblk[1]), kT, 0, k_asm1<MB, __nv_bfloat16>, M.nblk[1],
+                                  (const int*)M.asm_off[1], (const int4*)M.asm_list[1],
+                                  (const __nv_bfloat16*)M.Pb[0], Tval, kap, (const double*)F.dir_ups, W.aval[1]));
+  } else {
+    MG_MB_SWITCH(M.mb[1], launchk(st, warps_grid(M.nblk[1]), kT, 0, k_asm1<MB, float>, M.nblk[1],
+                                  (const int*)M.asm_off[1], (const int4*)M.asm_list[1], (const float*)M.P[0], Tval,
+                                  kap, (const double*)F.dir_ups, W.aval[1]));
+  }
   launchk(st, blocks_for(M.nc[1]), kT, 0, k_pad_diag, M.nc[1], M.mb[1], (const int*)M.dpos[1],
           (const int*)M.mcnt[1], W.aval[1]);
   int n = 3;
   for (int l = 2; l < M.L; ++l) {
-    MG_MB_SWITCH(M.mb[l], launchk(st, warps_grid(M.nblk[l]), kT, 0, k_asml<MB>, M.nblk[l], M.mb[l - 1],
-                                  (const int*)M.asm_off[l], (const int4*)M.asm_list[l], (const float*)M.P[l - 1],
-                                  (const float*)W.aval[l - 1], W.aval[l]));
+    if (W.bf16) {
+      MG_MB_SWITCH(M.mb[l], launchk(st, warps_grid(M.nblk[l]), kT, 0, k_asml<MB, __nv_bfloat16>, M.nblk[l],
+                                    M.mb[l - 1], (const int*)M.asm_off[l], (const int4*)M.asm_list[l],
+                                    (const __nv_bfloat16*)M.Pb[l - 1], (const float*)W.aval[l - 1], W.aval[l]));
+    } else {
+      MG_MB_SWITCH(M.mb[l], launchk(st, warps_grid(M.nblk[l]), kT, 0, k_asml<MB, float>, M.nblk[l], M.mb[l - 1],
+                                    (const int*)M.asm_off[l], (const int4*)M.asm_list[l], (const float*)M.P[l - 1],
+                                    (const float*)W.aval[l - 1], W.aval[l]));
+    }
     launchk(st, blocks_for(M.nc[l]), kT, 0, k_pad_diag, M.nc[l], M.mb[l], (const int*)M.dpos[l],
             (const int*)M.mcnt[l], W.aval[l]);
     n += 2;
@@ -1114,9 +1129,14 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
   }
   launchk(st, g0, kT, 0, k_res0, F, (const float*)W.a0off, (const float*)W.a0diag, (const float*)W.b[0],
           (const float*)W.x[0][cur[0]], W.d[0], flag);
-  launchk(st, warps_grid(M.nc[1]), kT, 0, k_restr, 1, (const float*)W.d[0], (const float*)M.P[0],
-          (const int*)M.ch_off[0], (const int*)M.ch[0], M.nc[1], M.mb[1], W.b[1], (const float*)W.dinv[1],
-          W.x[1][0], W.d[1], (const float*)W.coef, 1, C > 1 ? 1 : 0, flag);
+  if (W.bf16)
+    launchk(st, warps_grid(M.nc[1]), kT, 0, k_restr<__nv_bfloat16>, 1, (const float*)W.d[0],
+            (const __nv_bfloat16*)M.Pb[0], (const int*)M.ch_off[0], (const int*)M.ch[0], M.nc[1], M.mb[1], W.b[1],
+            (const float*)W.dinv[1], W.x[1][0], W.d[1], (const float*)W.coef, 1, C > 1 ? 1 : 0, flag);
+  else
+    launchk(st, warps_grid(M.nc[1]), kT, 0, k_restr<float>, 1, (const float*)W.d[0], (const float*)M.P[0],
+            (const int*)M.ch_off[0], (const int*)M.ch[0], M.nc[1], M.mb[1], W.b[1], (const float*)W.dinv[1],
+            W.x[1][0], W.d[1], (const float*)W.coef, 1, C > 1 ? 1 : 0, flag);
   for (int l = 1; l < C; ++l) {
     const int gl = warps_grid(M.nc[l]);
     for (int k = 1; k < kMgDegCoarse; ++k) {
@@ -1129,17 +1149,29 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
     MG_MB_SWITCH(M.mb[l], launchk(st, gl, kT, 0, k_resl<MB>, M.nc[l], (const int*)M.rowptr[l],
                                   (const int*)M.col[l], (const float*)W.aval[l], (const float*)W.b[l],
                                   (const float*)W.x[l][cur[l]], W.d[l], flag));
-    launchk(st, warps_grid(M.nc[l + 1]), kT, 0, k_restr, M.mb[l], (const float*)W.d[l], (const float*)M.P[l],
-            (const int*)M.ch_off[l], (const int*)M.ch[l], M.nc[l + 1], M.mb[l + 1], W.b[l + 1],
-            (const float*)W.dinv[l + 1], W.x[l + 1][0], W.d[l + 1], (const float*)W.coef, l + 1, l + 1 < C ? 1 : 0,
-            flag);
+    if (W.bf16)
+      launchk(st, warps_grid(M.nc[l + 1]), kT, 0, k_restr<__nv_bfloat16>, M.mb[l], (const float*)W.d[l],
+              (const __nv_bfloat16*)M.Pb[l], (const int*)M.ch_off[l], (const int*)M.ch[l], M.nc[l + 1],
+              M.mb[l + 1], W.b[l + 1], (const float*)W.dinv[l + 1], W.x[l + 1][0], W.d[l + 1],
+              (const float*)W.coef, l + 1, l + 1 < C ? 1 : 0, flag);
+    else
+      launchk(st, warps_grid(M.nc[l + 1]), kT, 0, k_restr<float>, M.mb[l], (const float*)W.d[l],
+              (const float*)M.P[l], (const int*)M.ch_off[l], (const int*)M.ch[l], M.nc[l + 1], M.mb[l + 1],
+              W.b[l + 1], (const float*)W.dinv[l + 1], W.x[l + 1][0], W.d[l + 1], (const float*)W.coef, l + 1,
+              l + 1 < C ? 1 : 0, flag);
   }
   launchk(st, 1, kMgMaxCoarse, 0, k_coarse_solve, M.nc[C] * M.mb[C], (const float*)W.cinv, (const float*)W.b[C],
           W.x[C][0], flag);
   // up
   for (int l = C - 1; l >= 1; --l) {
-    launchk(st, blocks_for((long)M.nc[l] * M.mb[l]), kT, 0, k_prol, M.nc[l], M.mb[l], M.mb[l + 1],
-            (const float*)M.P[l], (const int*)M.agg[l], (const float*)W.x[l + 1][cur[l + 1]], W.x[l][cur[l]], flag);
+    if (W.bf16)
+      launchk(st, blocks_for((long)M.nc[l] * M.mb[l]), kT, 0, k_prol<__nv_bfloat16>, M.nc[l], M.mb[l],
+              M.mb[l + 1], (const __nv_bfloat16*)M.Pb[l], (const int*)M.agg[l],
+              (const float*)W.x[l + 1][cur[l + 1]], W.x[l][cur[l]], flag);
+    else
+      launchk(st, blocks_for((long)M.nc[l] * M.mb[l]), kT, 0, k_prol<float>, M.nc[l], M.mb[l], M.mb[l + 1],
+              (const float*)M.P[l], (const int*)M.agg[l], (const float*)W.x[l + 1][cur[l + 1]], W.x[l][cur[l]],
+              flag);
     const int gl = warps_grid(M.nc[l]);
     for (int k = 0; k < kMgDegCoarse; ++k) {
       MG_MB_SWITCH(M.mb[l], launchk(st, gl, kT, 0, k_chebl<MB>, M.nc[l], (const int*)M.rowptr[l],
@@ -1149,8 +1181,12 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
       cur[l] ^= 1;
     }
   }
-  launchk(st, g0, kT, 0, k_pro0, M.N, M.mb[1], (const float*)M.P[0], (const int*)M.agg[0],
-          (const float*)W.x[1][cur[1]], W.x[0][cur[0]], flag);
+  if (W.bf16)
+    launchk(st, g0, kT, 0, k_pro0<__nv_bfloat16>, M.N, M.mb[1], (const __nv_bfloat16*)M.Pb[0],
+            (const int*)M.agg[0], (const float*)W.x[1][cur[1]], W.x[0][cur[0]], flag);
+  else
+    launchk(st, g0, kT, 0, k_pro0<float>, M.N, M.mb[1], (const float*)M.P[0], (const int*)M.agg[0],
+            (const float*)W.x[1][cur[1]], W.x[0][cur[0]], flag);
   for (int k = 0; k < kMgDegFine; ++k) {
     launchk(st, g0, kT, 0, k_cheb0, F, (const float*)W.a0off, (const float*)W.a0diag, (const float*)W.a0dinv,
             (const float*)W.b[0], (const float*)W.x[0][cur[0]], W.x[0][1 - cur[0]], W.d[0], (const float*)W.coef, k,

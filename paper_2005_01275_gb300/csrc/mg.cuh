@@ -8,6 +8,7 @@
 // Krylov iteration. One Krylov solve runs as one CUDA graph whose iterations sit in a device-side conditional
 // while node, so no host round trip separates them.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -45,6 +46,7 @@ struct MgDev {
   int* asm_off[kMgMaxLevels] = {nullptr};
   int4* asm_list[kMgMaxLevels] = {nullptr};
   float* P[kMgMaxLevels] = {nullptr};
+  __nv_bfloat16* Pb[kMgMaxLevels] = {nullptr};          // the same transfers rounded to BF16
   int *agg[kMgMaxLevels] = {nullptr}, *ch_off[kMgMaxLevels] = {nullptr}, *ch[kMgMaxLevels] = {nullptr};
 };
 
@@ -71,6 +73,8 @@ struct MgWork {
   MgScal* sc = nullptr;
   MgScal* h_sc = nullptr;                                // pinned copy
   cudaGraphExec_t g_pcg[2] = {nullptr, nullptr}, g_bicg[2] = {nullptr, nullptr}, g_apply = nullptr;
+  int bf16 = 0;            // transfers in BF16 (FP32 accumulation) in the setup and V-cycle enqueued next
+  int graphs_bf16 = -1;    // the transfer type the captured graphs use (-1: none captured)
 };
 
 // Builds the preconditioner's structure on the first `levels` levels of H (levels <= H.levels.size()); the coarsest

@@ -532,6 +532,9 @@ void upload_mg(nlmg_ctx* c, int levels) {
     }
     if (l + 1 < mh.L) {
       M.P[l] = c->upload(mh.P[l]);
+      std::vector<__nv_bfloat16> pb(mh.P[l].size());
+      for (size_t i = 0; i < pb.size(); ++i) pb[i] = __float2bfloat16(mh.P[l][i]);
+      M.Pb[l] = c->upload(pb);
       M.agg[l] = c->upload(mh.agg[l]);
       M.ch_off[l] = c->upload(mh.ch_off[l]);
       M.ch[l] = c->upload(mh.ch[l]);
@@ -1134,6 +1137,21 @@ void alloc_mg(nlmg_ctx* c) {
   mg_set_smem_limits();
 }
 
+// Transfers of the preconditioner in BF16 (lin_precision = 2) or FP32; graphs captured with the other type are
+// dropped and captured again.
+void mg_select_precision(nlmg_ctx* c) {
+  MgWork& W = c->mg;
+  W.bf16 = c->opt.lin_precision == 2 ? 1 : 0;
+  if (W.graphs_bf16 != -1 && W.graphs_bf16 != W.bf16) {
+    for (cudaGraphExec_t* g : {&W.g_pcg[0], &W.g_pcg[1], &W.g_bicg[0], &W.g_bicg[1], &W.g_apply})
+      if (*g) {
+        CK(cudaGraphExecDestroy(*g));
+        *g = nullptr;
+      }
+  }
+  W.graphs_bf16 = W.bf16;
+}
+
 // Reads the scalars of the last multigrid Krylov solve; throws on a non-finite value.
 int mg_finish(nlmg_ctx* c, const char* what) {
   MgWork& W = c->mg;
@@ -1158,6 +1176,7 @@ void mg_set_limits(nlmg_ctx* c, double tol) {
 int mg_pcg(nlmg_ctx* c, const double* R, const double* kap) {
   const MgDev& M = c->sh->MG;
   MgWork& W = c->mg;
+  mg_select_precision(c);
   const int ps = c->prof_begin(7);
   mg_enqueue_setup(c->st, M, c->F, W, c->Tval, c->diagT, kap);
   c->prof_end(ps);
@@ -1186,6 +1205,7 @@ int mg_pcg(nlmg_ctx* c, const double* R, const double* kap) {
 int mg_bicgstab(nlmg_ctx* c, const double* R, const double* kap) {
   const MgDev& M = c->sh->MG;
   MgWork& W = c->mg;
+  mg_select_precision(c);
   const int ps = c->prof_begin(7);
   mg_enqueue_setup(c->st, M, c->F, W, c->Tval, c->diagT, kap);
   c->prof_end(ps);
@@ -1381,7 +1401,7 @@ static thread_local std::string g_setup_error;   // message of the calling threa
 // The options a solve reads (those fixed at setup are checked there).
 static bool solver_options_ok(const nlmg_options& o) {
   return (o.lin_precond == 0 || o.lin_precond == 1) && o.nu_pre >= 0 && o.nu_post >= 0 && o.bt_nmax >= 0 && o.omega > 0 && o.coarsest_steps >= 0 &&
-         (o.lin_precision == 0 || o.lin_precision == 1) && o.max_sms >= 0 && o.smoother >= NLMG_SMOOTH_PICARD &&
+         (o.lin_precision == 0 || o.lin_precision == 1 || o.lin_precision == 2) && o.max_sms >= 0 && o.smoother >= NLMG_SMOOTH_PICARD &&
          o.smoother <= NLMG_SMOOTH_PICARD_NEWTON && o.newton_switch >= 0.0 && o.newton_lin_tol > 0.0 &&
          (o.cascadic == 0 || o.cascadic == 1);
 }
@@ -1908,6 +1928,7 @@ nlmg_status nlmg_precond_apply(nlmg_ctx* c, const double* p, const double* r, do
     fine_eval(c, c->cpa, nullptr, 0.0, c->t1);
     launch_residual(c->st, c->F, c->t1.p, c->t1.kap, nullptr, c->g, c->rhs, c->t2.R, c->Tval, c->dinv, c->diagT,
                     nullptr, c->red(S_NORM2B));
+    mg_select_precision(c);
     mg_enqueue_setup(c->st, M, c->F, W, c->Tval, c->diagT, c->t1.kap);
     CK(cudaMemcpyAsync(W.kb, r, N * sizeof(double), cudaMemcpyHostToDevice, c->st));
     if (!W.g_apply) CK(mg_capture_apply(c->st, M, c->F, W, &W.g_apply));

@@ -116,3 +116,40 @@ def test_bench_workload_shape_with_the_preconditioner(nlmg_lib):
     jac = nlmg_lib.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, dict(pr.opts, smoother="picard_newton"))
     _, rep_j, _ = jac.solve(pr.f_cell, pr.g_face)
     assert rep_mg["lin_iters_level"][0] * 4 <= rep_j["lin_iters_level"][0], (rep_mg, rep_j)
+
+
+def _bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_bf16_transfers(nlmg_lib):
+    """lin_precision = 2: the V-cycle's transfers in BF16. One application equals the oracle's cycle built on the
+    BF16-rounded P (same Galerkin operators), and FAS solves still reach p* to 1e-10 at relative residual 1e-12 (the
+    Krylov iterations and every residual stay FP64)."""
+    from types import SimpleNamespace
+    import scipy.sparse as sp
+    pr, ctx = _case(nlmg_lib, "chan3d_64", 16, n_levels=3, agg_size=[64, 8, 8], modes=[4, 4, 4])
+    ctx.set_options(lin_precision=2)
+    rng = np.random.default_rng(64)
+    p = rng.uniform(0, 1, pr.mesh.n_cells)
+    A = newton.picard_matrix(pr.mesh, pr.kappa_kind, pr.kappa_a, p).tocsr()
+    H = hierarchy.build(pr.mesh, precond.extended_options(pr.opts))
+    L = precond.levels_for(H)
+    tr = [SimpleNamespace(Pp=sp.csr_matrix((_bf16(t.Pp.data), t.Pp.indices, t.Pp.indptr), shape=t.Pp.shape))
+          for t in H.transfers]
+    Hb = SimpleNamespace(levels=H.levels, transfers=tr)
+    lv = precond.build(A, Hb, L)
+    r = rng.uniform(-1, 1, pr.mesh.n_cells)
+    z = ctx.precond_apply(p, r)
+    ref = precond.vcycle(lv, Hb, r)
+    assert np.linalg.norm(z - ref) <= 2e-4 * np.linalg.norm(ref)
+    ref32 = precond.vcycle(precond.build(A, H, L), H, r)
+    assert np.linalg.norm(z - ref32) > 1e-6 * np.linalg.norm(ref32)      # the rounding is really applied
+    pstar, _ = newton.solve(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, dp_clamp=pr.opts["dp_clamp"])
+    pb, rep, st = ctx.solve(pr.f_cell, pr.g_face, tol_rel=1e-12, tol_abs=1e-300, max_cycles=80)
+    assert st == 0, rep
+    assert np.linalg.norm(pb - pstar) <= 1e-10 * np.linalg.norm(pstar)
