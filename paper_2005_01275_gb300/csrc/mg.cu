@@ -10,6 +10,7 @@
 #include <map>
 #include <set>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "mg.cuh"
@@ -23,6 +24,18 @@ static_assert(kMgMaxLevels * kMgMaxDeg <= 32, "the coefficient table kernel runs
 
 constexpr int kT = 256;               // threads per block of the preconditioner kernels
 constexpr int kMaxRedBlocks = 1024;   // grid cap of the reduction kernels (partials summed by one block)
+
+#define MG_MB_SWITCH(mb, CALL)                                                     \
+  switch (mb) {                                                                    \
+    case 1: { constexpr int MB = 1; CALL; } break;                                 \
+    case 2: { constexpr int MB = 2; CALL; } break;                                 \
+    case 3: { constexpr int MB = 3; CALL; } break;                                 \
+    case 4: { constexpr int MB = 4; CALL; } break;                                 \
+    case 5: { constexpr int MB = 5; CALL; } break;                                 \
+    case 6: { constexpr int MB = 6; CALL; } break;                                 \
+    case 7: { constexpr int MB = 7; CALL; } break;                                 \
+    default: { constexpr int MB = 8; CALL; } break;                                \
+  }
 
 inline int blocks_for(long n, int cap = 1 << 20) {
   long b = (n + kT - 1) / kT;
@@ -395,6 +408,24 @@ __global__ void k_coarse_inv(int nc, int mb, const int* __restrict__ rowptr, con
 
 // One Chebyshev step on level 0: res = b - A x_in, d = c1 d + c2 D^-1 res, x_out = x_in + d (x_in is gathered by the
 // neighbours, so the new iterate goes to the other buffer).
+__device__ __forceinline__ float cheb0_cell(const FineDev& F, const float* __restrict__ a0off,
+                                            const float* __restrict__ a0diag, const float* __restrict__ a0dinv,
+                                            const float* __restrict__ b, const float* __restrict__ xin,
+                                            float* __restrict__ xout, float* __restrict__ d, float c1, float c2, int k,
+                                            int K) {
+  const int w = F.sell_w[K >> 5];
+  int e = F.sell_off[K >> 5] + (K & 31);
+  const float xk = xin[K];
+  float ax = a0diag[K] * xk;
+  for (int j = 0; j < w; ++j, e += 32) ax = fmaf(a0off[e], xin[F.nbr[e]], ax);
+  const float res = b[K] - ax;
+  const float dn = (k == 0 ? 0.0f : c1 * d[K]) + c2 * a0dinv[K] * res;
+  d[K] = dn;
+  const float xn = xk + dn;
+  xout[K] = xn;
+  return xn;
+}
+
 __global__ void k_cheb0(FineDev F, const float* __restrict__ a0off, const float* __restrict__ a0diag,
                         const float* __restrict__ a0dinv, const float* __restrict__ b, const float* __restrict__ xin,
                         float* __restrict__ xout, float* __restrict__ d, const float* __restrict__ lam, int k,
@@ -403,34 +434,78 @@ __global__ void k_cheb0(FineDev F, const float* __restrict__ a0off, const float*
   if (stop(done)) return;
   float c1, c2;
   cheb_tab(lam, 0, k, c1, c2);
+  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < F.N; K += gridDim.x * blockDim.x)
+    (void)cheb0_cell(F, a0off, a0diag, a0dinv, b, xin, xout, d, c1, c2, k, K);
+}
+
+// The last Chebyshev step of level 0 (z = xout) fused with the flexible CG step length: rz_new = (r, z),
+// beta = (r, z - z_old) / rz (0 on the first step), which equals the plain rz_new / rz for a fixed linear
+// preconditioner and tolerates the FP32 rounding of the V-cycle. At most kMaxRedBlocks blocks.
+__global__ void k_cheb0_beta(FineDev F, const float* __restrict__ a0off, const float* __restrict__ a0diag,
+                             const float* __restrict__ a0dinv, const float* __restrict__ b,
+                             const float* __restrict__ xin, float* __restrict__ xout, float* __restrict__ d,
+                             const float* __restrict__ lam, int k, const double* __restrict__ r,
+                             const float* __restrict__ zold, double* part, MgScal* sc) {
+  pdl_start();
+  if (stop(&sc->done)) return;
+  float c1, c2;
+  cheb_tab(lam, 0, k, c1, c2);
+  const bool first = sc->it == 0;
+  double v[2] = {0.0, 0.0};
   for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < F.N; K += gridDim.x * blockDim.x) {
-    const int w = F.sell_w[K >> 5];
-    int e = F.sell_off[K >> 5] + (K & 31);
-    const float xk = xin[K];
-    float ax = a0diag[K] * xk;
-    for (int j = 0; j < w; ++j, e += 32) ax = fmaf(a0off[e], xin[F.nbr[e]], ax);
-    const float res = b[K] - ax;
-    const float dn = (k == 0 ? 0.0f : c1 * d[K]) + c2 * a0dinv[K] * res;
-    d[K] = dn;
-    xout[K] = xk + dn;
+    const float z = cheb0_cell(F, a0off, a0diag, a0dinv, b, xin, xout, d, c1, c2, k, K);
+    v[0] = fma(r[K], (double)z, v[0]);
+    if (!first) v[1] = fma(r[K], (double)zold[K], v[1]);
+  }
+  __shared__ double out[2];
+  if (reduce_last<2>(v, part, &sc->cnt[1], out) && threadIdx.x == 0) {
+    sc->beta = first ? 0.0 : (out[0] - out[1]) / sc->rz;
+    sc->rz = out[0];
   }
 }
 
+// Loads of the vectors a V-cycle writes: ordinary loads, or (CG) through L2 with ld.global.cg for data another CTA
+// wrote in the same launch.
+template <bool CG>
+__device__ __forceinline__ float ldv(const float* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
 
 // (A x)_u of block-level cell c, one warp per cell: lane = slot * 8 + u, the four slots take every fourth block of
-// the row; a shuffle tree adds the slots, so every lane with component u < MB holds (A x)_u.
-template <int MB>
+// the row; a shuffle tree adds the slots, so every lane with component u < MB holds (A x)_u. The blocks are taken in
+// batches of RB per slot whose column indices, then matrix and vector entries, are all loaded before the first
+// product: on the small levels few warps are in flight, and a row costs two dependent memory round trips per batch
+// instead of two per block. The products are added in block order either way.
+template <int MB, bool CG>
 __device__ __forceinline__ float row_ax(int c, int lane, const int* __restrict__ rowptr, const int* __restrict__ col,
-                                        const float* __restrict__ aval, const float* __restrict__ x) {
+                                        const float* __restrict__ aval, const float* x) {
+  constexpr int RB = MB >= 8 ? 2 : (MB >= 4 ? 4 : 8);
   const int slot = lane >> 3, u = lane & 7;
   float ax = 0.0f;
   if (u < MB) {
     const int q1 = rowptr[c + 1];
-    for (int q = rowptr[c] + slot; q < q1; q += 4) {
-      const float* Bq = aval + (size_t)q * MB * MB + u * MB;
-      const float* xd = x + (size_t)col[q] * MB;
+    for (int qb = rowptr[c] + slot; qb < q1; qb += 4 * RB) {
+      int cq[RB];
 #pragma unroll
-      for (int v = 0; v < MB; ++v) ax = fmaf(Bq[v], xd[v], ax);
+      for (int j = 0; j < RB; ++j) cq[j] = qb + 4 * j < q1 ? col[qb + 4 * j] : -1;
+      float bv[RB][MB], xv[RB][MB];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        const float* Bq = aval + (size_t)(qb + 4 * j) * MB * MB + u * MB;
+        const float* xd = x + (size_t)(cq[j] < 0 ? 0 : cq[j]) * MB;
+#pragma unroll
+        for (int v = 0; v < MB; ++v) {
+          bv[j][v] = cq[j] >= 0 ? Bq[v] : 0.0f;
+          xv[j][v] = cq[j] >= 0 ? ldv<CG>(xd + v) : 0.0f;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < RB; ++j)
+        if (cq[j] >= 0) {
+#pragma unroll
+          for (int v = 0; v < MB; ++v) ax = fmaf(bv[j][v], xv[j][v], ax);
+        }
     }
   }
   ax += __shfl_xor_sync(0xffffffffu, ax, 8);
@@ -438,22 +513,17 @@ __device__ __forceinline__ float row_ax(int c, int lane, const int* __restrict__
   return ax;
 }
 
-// One Chebyshev step on block level l, one warp per cell (see row_ax).
-template <int MB>
-__global__ void k_chebl(int nc, const int* __restrict__ rowptr, const int* __restrict__ col,
-                        const float* __restrict__ aval, const float* __restrict__ dinv, const float* __restrict__ b,
-                        const float* __restrict__ xin, float* __restrict__ xout, float* __restrict__ d,
-                        const float* __restrict__ lam, int l, int k, const int* done) {
-  pdl_start();
-  if (stop(done)) return;
-  float c1, c2;
-  cheb_tab(lam, l, k, c1, c2);
+// One Chebyshev step on block level l (coefficients c1, c2 of step k): res = b - A x_in, d = c1 d + c2 D^-1 res,
+// x_out = x_in + d; warps w0, w0 + nw, ... take one cell each (see row_ax).
+template <int MB, bool CG>
+__device__ __forceinline__ void chebl_body(int w0, int nw, int nc, const int* __restrict__ rowptr,
+                                           const int* __restrict__ col, const float* __restrict__ aval,
+                                           const float* __restrict__ dinv, const float* b, const float* xin,
+                                           float* xout, float* d, float c1, float c2, int k) {
   const int lane = threadIdx.x & 31, u = lane & 7;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int c = warp; c < nc; c += nw) {
-    const float ax = row_ax<MB>(c, lane, rowptr, col, aval, xin);
-    const float res = u < MB ? b[(size_t)c * MB + u] - ax : 0.0f;
+  for (int c = w0; c < nc; c += nw) {
+    const float ax = row_ax<MB, CG>(c, lane, rowptr, col, aval, xin);
+    const float res = u < MB ? ldv<CG>(b + (size_t)c * MB + u) - ax : 0.0f;
     float s = 0.0f;
 #pragma unroll
     for (int v = 0; v < MB; ++v) {
@@ -462,58 +532,63 @@ __global__ void k_chebl(int nc, const int* __restrict__ rowptr, const int* __res
     }
     if (lane < MB) {
       const size_t i = (size_t)c * MB + u;
-      const float dn = (k == 0 ? 0.0f : c1 * d[i]) + c2 * s;
+      const float dn = (k == 0 ? 0.0f : c1 * ldv<CG>(d + i)) + c2 * s;
       d[i] = dn;
-      xout[i] = xin[i] + dn;
+      xout[i] = ldv<CG>(xin + i) + dn;
     }
   }
 }
 
 // Residual b - A x of a block level, one warp per cell.
-template <int MB>
-__global__ void k_resl(int nc, const int* __restrict__ rowptr, const int* __restrict__ col,
-                       const float* __restrict__ aval, const float* __restrict__ b, const float* __restrict__ x,
-                       float* __restrict__ res, const int* done) {
-  pdl_start();
-  if (stop(done)) return;
+template <int MB, bool CG>
+__device__ __forceinline__ void resl_body(int w0, int nw, int nc, const int* __restrict__ rowptr,
+                                          const int* __restrict__ col, const float* __restrict__ aval, const float* b,
+                                          const float* x, float* res) {
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int c = warp; c < nc; c += nw) {
-    const float ax = row_ax<MB>(c, lane, rowptr, col, aval, x);
-    if (lane < MB) res[(size_t)c * MB + lane] = b[(size_t)c * MB + lane] - ax;
+  for (int c = w0; c < nc; c += nw) {
+    const float ax = row_ax<MB, CG>(c, lane, rowptr, col, aval, x);
+    if (lane < MB) res[(size_t)c * MB + lane] = ldv<CG>(b + (size_t)c * MB + lane) - ax;
   }
 }
 
 // Restriction of a residual (mbf per cell on level l) to level l+1 (mb per cell), one warp per level-(l+1) cell A:
 // lane = k * 8 + u takes component u of children k, k + 4, ...; a shuffle tree adds the lanes. `first` adds the first
-// Chebyshev step of level l+1 (x = D^-1 b / theta, d = x).
-template <class PT>
-__global__ void k_restr(int mbf, const float* __restrict__ res, const PT* __restrict__ Pl,
-                        const int* __restrict__ ch_off, const int* __restrict__ ch, int ncc, int mb,
-                        float* __restrict__ bc, const float* __restrict__ dinvc, float* __restrict__ xc,
-                        float* __restrict__ dc, const float* __restrict__ lam, int lc, int first, const int* done) {
-  pdl_start();
-  if (stop(done)) return;
+// Chebyshev step of level l+1 (x = c2 D^-1 b, d = x).
+template <class PT, bool CG>
+__device__ __forceinline__ void restr_body(int w0, int nw, int mbf, const float* res, const PT* __restrict__ Pl,
+                                           const int* __restrict__ ch_off, const int* __restrict__ ch, int ncc,
+                                           int mb, float* bc, const float* __restrict__ dinvc, float* xc, float* dc,
+                                           float c2, int first) {
   const int lane = threadIdx.x & 31, grp = lane >> 3, u = lane & 7;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  float c1 = 0.0f, c2 = 0.0f;
-  if (first) cheb_tab(lam, lc, 0, c1, c2);
   // one value per child (level 0): lanes take children one each; else eight lanes per child
   const int cstep = mbf == 1 ? 32 : 4, c0 = mbf == 1 ? lane : grp, uu = mbf == 1 ? 0 : u;
-  for (int A = warp; A < ncc; A += nw) {
+  for (int A = w0; A < ncc; A += nw) {
     float acc[kMaxM];
 #pragma unroll
     for (int j = 0; j < kMaxM; ++j) acc[j] = 0.0f;
     if (uu < mbf) {
-      for (int t = ch_off[A] + c0; t < ch_off[A + 1]; t += cstep) {
-        const int c = ch[t];
-        const float r = res[(size_t)c * mbf + uu];
-        const size_t pr = ((size_t)c * mbf + uu) * mb;
+      // children in pairs, both loaded before the products (see row_ax); products in child order
+      const int t1 = ch_off[A + 1];
+      for (int t = ch_off[A] + c0; t < t1; t += 2 * cstep) {
+        const bool two = t + cstep < t1;
+        const int ca = ch[t], cb = two ? ch[t + cstep] : ca;
+        const float ra = ldv<CG>(res + (size_t)ca * mbf + uu), rb = ldv<CG>(res + (size_t)cb * mbf + uu);
+        const size_t pa = ((size_t)ca * mbf + uu) * mb, pb = ((size_t)cb * mbf + uu) * mb;
+        float Pa[kMaxM], Pb[kMaxM];
 #pragma unroll
         for (int j = 0; j < kMaxM; ++j)
-          if (j < mb) acc[j] = fmaf(pval(Pl, pr + j), r, acc[j]);
+          if (j < mb) {
+            Pa[j] = pval(Pl, pa + j);
+            Pb[j] = pval(Pl, pb + j);
+          }
+#pragma unroll
+        for (int j = 0; j < kMaxM; ++j)
+          if (j < mb) acc[j] = fmaf(Pa[j], ra, acc[j]);
+        if (two) {
+#pragma unroll
+          for (int j = 0; j < kMaxM; ++j)
+            if (j < mb) acc[j] = fmaf(Pb[j], rb, acc[j]);
+        }
       }
     }
 #pragma unroll
@@ -539,6 +614,67 @@ __global__ void k_restr(int mbf, const float* __restrict__ res, const PT* __rest
   }
 }
 
+// x += P e on a block level (one thread per cell and component; threads i0, i0 + ni, ...).
+template <class PT, bool CG>
+__device__ __forceinline__ void prol_body(long i0, long ni, int nc, int mbf, int mb, const PT* __restrict__ Pl,
+                                          const int* __restrict__ agg, const float* e, float* x) {
+  const long total = (long)nc * mbf;
+  for (long i = i0; i < total; i += ni) {
+    const int c = (int)(i / mbf);
+    const float* ea = e + (size_t)agg[c] * mb;
+    float s = ldv<CG>(x + i);
+    for (int j = 0; j < mb; ++j) s = fmaf(pval(Pl, (size_t)i * mb + j), ldv<CG>(ea + j), s);
+    x[i] = s;
+  }
+}
+
+// Coarsest level: x = C^-1 b with the dense inverse (threads i0, i0 + ni, ... take one row each).
+template <bool CG>
+__device__ __forceinline__ void coarse_solve_body(int i0, int ni, int n, const float* __restrict__ cinv,
+                                                  const float* b, float* x) {
+  for (int i = i0; i < n; i += ni) {
+    float s = 0.0f;
+    for (int j = 0; j < n; ++j) s = fmaf(cinv[(size_t)i * n + j], ldv<CG>(b + j), s);
+    x[i] = s;
+  }
+}
+
+__device__ __forceinline__ int gwarp() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ int nwarps() { return (gridDim.x * blockDim.x) >> 5; }
+
+template <int MB>
+__global__ void k_chebl(int nc, const int* __restrict__ rowptr, const int* __restrict__ col,
+                        const float* __restrict__ aval, const float* __restrict__ dinv, const float* __restrict__ b,
+                        const float* __restrict__ xin, float* __restrict__ xout, float* __restrict__ d,
+                        const float* __restrict__ lam, int l, int k, const int* done) {
+  pdl_start();
+  if (stop(done)) return;
+  float c1, c2;
+  cheb_tab(lam, l, k, c1, c2);
+  chebl_body<MB, false>(gwarp(), nwarps(), nc, rowptr, col, aval, dinv, b, xin, xout, d, c1, c2, k);
+}
+
+template <int MB>
+__global__ void k_resl(int nc, const int* __restrict__ rowptr, const int* __restrict__ col,
+                       const float* __restrict__ aval, const float* __restrict__ b, const float* __restrict__ x,
+                       float* __restrict__ res, const int* done) {
+  pdl_start();
+  if (stop(done)) return;
+  resl_body<MB, false>(gwarp(), nwarps(), nc, rowptr, col, aval, b, x, res);
+}
+
+template <class PT>
+__global__ void k_restr(int mbf, const float* __restrict__ res, const PT* __restrict__ Pl,
+                        const int* __restrict__ ch_off, const int* __restrict__ ch, int ncc, int mb,
+                        float* __restrict__ bc, const float* __restrict__ dinvc, float* __restrict__ xc,
+                        float* __restrict__ dc, const float* __restrict__ lam, int lc, int first, const int* done) {
+  pdl_start();
+  if (stop(done)) return;
+  float c1 = 0.0f, c2 = 0.0f;
+  if (first) cheb_tab(lam, lc, 0, c1, c2);
+  restr_body<PT, false>(gwarp(), nwarps(), mbf, res, Pl, ch_off, ch, ncc, mb, bc, dinvc, xc, dc, c2, first);
+}
+
 // Level-0 residual b - A x (FP32), one thread per cell.
 __global__ void k_res0(FineDev F, const float* __restrict__ a0off, const float* __restrict__ a0diag,
                        const float* __restrict__ b, const float* __restrict__ x, float* __restrict__ res,
@@ -554,16 +690,11 @@ __global__ void k_res0(FineDev F, const float* __restrict__ a0off, const float* 
   }
 }
 
-// Coarsest level: x = C^-1 b with the dense inverse.
 __global__ void k_coarse_solve(int n, const float* __restrict__ cinv, const float* __restrict__ b,
                                float* __restrict__ x, const int* done) {
   pdl_start();
   if (stop(done)) return;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    float s = 0.0f;
-    for (int j = 0; j < n; ++j) s = fmaf(cinv[(size_t)i * n + j], b[j], s);
-    x[i] = s;
-  }
+  coarse_solve_body<false>(threadIdx.x, blockDim.x, n, cinv, b, x);
 }
 
 // x_0 += P e on level 0 (per fine cell) and on a block level (per cell and component).
@@ -584,14 +715,110 @@ __global__ void k_prol(int nc, int mbf, int mb, const PT* __restrict__ Pl, const
                        const float* __restrict__ e, float* __restrict__ x, const int* done) {
   pdl_start();
   if (stop(done)) return;
-  const long total = (long)nc * mbf;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    const int c = (int)(i / mbf);
-    const float* ea = e + (size_t)agg[c] * mb;
-    float s = x[i];
-    for (int j = 0; j < mb; ++j) s = fmaf(pval(Pl, (size_t)i * mb + j), ea[j], s);
-    x[i] = s;
+  prol_body<PT, false>((long)blockIdx.x * blockDim.x + threadIdx.x, (long)gridDim.x * blockDim.x, nc, mbf, mb, Pl,
+                       agg, e, x);
+}
+
+// The small levels of one V-cycle in one launch of one thread block, out of shared memory: from the restriction of
+// level t-1's residual (W.d[t-1], global) to the prolongation into level t-1 (W.x[t-1][cur_prev], global), the
+// smoothing, residuals and transfers of levels t .. C-1 and the coarsest solve run as phases separated by
+// __syncthreads on copies of their matrices, transfers and vectors held in shared memory, instead of one dependent
+// kernel (a few L2 round trips) per phase. The copy-in is one pass of 16-byte loads, eight in flight per thread, from
+// the table's copy list (every source array is allocated in whole 16-byte units). The phases are the bodies of the
+// per-level kernels with the same work split per cell and the same order of operations, so the result does not depend
+// on which form ran.
+template <class PT>
+__global__ void __launch_bounds__(kTailThreads, 1) k_small(const MgTailTab* __restrict__ Tg, int cur_prev) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ MgTailTab T_;   // the table itself, read by every phase
+  static_assert(sizeof(MgTailTab) % 4 == 0, "table copied in words");
+  pdl_start();
+  for (int i = threadIdx.x; i < (int)(sizeof(MgTailTab) / 4); i += kTailThreads)
+    ((int*)&T_)[i] = __ldg((const int*)Tg + i);
+  __syncthreads();
+  const MgTailTab* T = &T_;
+  constexpr int v = std::is_same_v<PT, float> ? 0 : 1;
+  {
+    const int nch = T->nchunks[v], ncp = T->ncopies[v];
+    for (int i0 = threadIdx.x; i0 < nch; i0 += kTailThreads * 8) {
+      float4 buf[8];
+      unsigned dst[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * kTailThreads;
+        if (i < nch) {
+          int lo = 0, hi = ncp - 1;   // last entry whose first chunk is <= i
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (T->cp[v][mid].c0 <= (unsigned)i) lo = mid;
+            else hi = mid - 1;
+          }
+          const MgTailCopy& e = T->cp[v][lo];
+          buf[u] = __ldg((const float4*)e.src + (i - e.c0));
+          dst[u] = e.dst + 16u * (i - e.c0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (i0 + u * kTailThreads < nch) *(float4*)(sm + dst[u]) = buf[u];
+    }
   }
+  __syncthreads();
+  const MgDev& M = T->M;
+  const int t = T->t, C = M.L - 1;
+  const int w0 = threadIdx.x >> 5, nw = kTailThreads / 32;
+  const int i0 = threadIdx.x, ni = kTailThreads;
+  auto F32 = [&](unsigned off) { return (float*)(sm + off); };
+  auto I32 = [&](unsigned off) { return (const int*)(sm + off); };
+  auto PL = [&](int l) { return (const PT*)(sm + T->o_P[l]); };
+  // buffer of level l's iterate: x[l][0] after the restriction (first step fused), then each Chebyshev step moves
+  // it to the other buffer; the coarsest solve writes x[C][0]
+  constexpr int kDown = (kMgDegCoarse - 1) & 1, kUp = (2 * kMgDegCoarse - 1) & 1;
+  const float* coef = F32(T->o_coef);
+  float c1, c2 = 0.0f;
+  if (t < C) cheb_tab(coef, t, 0, c1, c2);
+  restr_body<PT, false>(w0, nw, M.mb[t - 1], T->d[t - 1], PL(t - 1), I32(T->o_choff[t - 1]), I32(T->o_ch[t - 1]),
+                        M.nc[t], M.mb[t], F32(T->o_b[t]), F32(T->o_dinv[t]), F32(T->o_x[t][0]), F32(T->o_d[t]), c2,
+                        t < C ? 1 : 0);
+  __syncthreads();
+  for (int l = t; l < C; ++l) {
+    const int *rp = I32(T->o_rowptr[l]), *cl = I32(T->o_col[l]);
+    const float *av = F32(T->o_aval[l]), *di = F32(T->o_dinv[l]);
+    float *xb[2] = {F32(T->o_x[l][0]), F32(T->o_x[l][1])}, *bl = F32(T->o_b[l]), *dl = F32(T->o_d[l]);
+    for (int k = 1; k < kMgDegCoarse; ++k) {
+      cheb_tab(coef, l, k, c1, c2);
+      MG_MB_SWITCH(M.mb[l], (chebl_body<MB, false>(w0, nw, M.nc[l], rp, cl, av, di, bl, xb[(k - 1) & 1], xb[k & 1],
+                                                   dl, c1, c2, k)));
+      __syncthreads();
+    }
+    MG_MB_SWITCH(M.mb[l], (resl_body<MB, false>(w0, nw, M.nc[l], rp, cl, av, bl, xb[kDown], dl)));
+    __syncthreads();
+    const int first = l + 1 < C ? 1 : 0;
+    c2 = 0.0f;
+    if (first) cheb_tab(coef, l + 1, 0, c1, c2);
+    restr_body<PT, false>(w0, nw, M.mb[l], dl, PL(l), I32(T->o_choff[l]), I32(T->o_ch[l]), M.nc[l + 1],
+                          M.mb[l + 1], F32(T->o_b[l + 1]), F32(T->o_dinv[l + 1]), F32(T->o_x[l + 1][0]),
+                          F32(T->o_d[l + 1]), c2, first);
+    __syncthreads();
+  }
+  coarse_solve_body<false>(i0, ni, M.nc[C] * M.mb[C], F32(T->o_cinv), F32(T->o_b[C]), F32(T->o_x[C][0]));
+  __syncthreads();
+  for (int l = C - 1; l >= t; --l) {
+    const int *rp = I32(T->o_rowptr[l]), *cl = I32(T->o_col[l]);
+    const float *av = F32(T->o_aval[l]), *di = F32(T->o_dinv[l]);
+    float *xb[2] = {F32(T->o_x[l][0]), F32(T->o_x[l][1])}, *bl = F32(T->o_b[l]), *dl = F32(T->o_d[l]);
+    prol_body<PT, false>(i0, ni, M.nc[l], M.mb[l], M.mb[l + 1], PL(l), I32(T->o_agg[l]),
+                         F32(T->o_x[l + 1][l + 1 == C ? 0 : kUp]), xb[kDown]);
+    __syncthreads();
+    for (int k = 0; k < kMgDegCoarse; ++k) {
+      cheb_tab(coef, l, k, c1, c2);
+      MG_MB_SWITCH(M.mb[l], (chebl_body<MB, false>(w0, nw, M.nc[l], rp, cl, av, di, bl, xb[(kDown + k) & 1],
+                                                   xb[(kDown + k + 1) & 1], dl, c1, c2, k)));
+      __syncthreads();
+    }
+  }
+  prol_body<PT, false>(i0, ni, M.nc[t - 1], M.mb[t - 1], M.mb[t], PL(t - 1), I32(T->o_agg[t - 1]),
+                       F32(T->o_x[t][t == C ? 0 : kUp]), T->x[t - 1][cur_prev]);
 }
 
 // ---------------------------------------------------------------------------------------------------------------
@@ -641,25 +868,6 @@ __global__ void k_pcg_init(int N, const double* __restrict__ b, double bscale, c
     sc->done = !(out[0] > 0.0) ? 1 : 0;
     sc->bad = isfinite(out[0]) ? 0 : 1;
     sc->rz = 0.0;
-  }
-}
-
-// Flexible CG step length: rz_new = (r, z), beta = (r, z - z_old) / rz (0 on the first step), which equals the plain
-// rz_new / rz for a fixed linear preconditioner and tolerates the FP32 rounding of the V-cycle.
-__global__ void k_pcg_beta(int N, const double* __restrict__ r, const float* __restrict__ z,
-                           const float* __restrict__ zold, double* part, MgScal* sc) {
-  pdl_start();
-  if (stop(&sc->done)) return;
-  const bool first = sc->it == 0;
-  double v[2] = {0.0, 0.0};
-  for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < N; K += gridDim.x * blockDim.x) {
-    v[0] = fma(r[K], (double)z[K], v[0]);
-    if (!first) v[1] = fma(r[K], (double)zold[K], v[1]);
-  }
-  __shared__ double out[2];
-  if (reduce_last<2>(v, part, &sc->cnt[1], out) && threadIdx.x == 0) {
-    sc->beta = first ? 0.0 : (out[0] - out[1]) / sc->rz;
-    sc->rz = out[0];
   }
 }
 
@@ -846,12 +1054,13 @@ __global__ void k_bicg_x(int N, const double* __restrict__ pp, const float* __re
     cudaGraphSetConditional(h, d ? 0 : 1);
   }
 }
-// p = r + beta (p - omega v), r32 = p with the first smoothing step of the next V-cycle.
+// p = r + beta (p - omega v), r32 = p with the first smoothing step of the next V-cycle; on the first iteration the
+// start has set p = r and that step already.
 __global__ void k_bicg_p(int N, const double* __restrict__ r, const double* __restrict__ v, double* __restrict__ p,
                          float* __restrict__ r32, const float* __restrict__ a0dinv, float* __restrict__ x0,
                          float* __restrict__ d0, const float* __restrict__ lam, MgScal* sc) {
   pdl_start();
-  if (stop(&sc->done)) return;
+  if (stop(&sc->done) || sc->it == 0) return;
   const double beta = sc->beta, omega = sc->omega;
   float c1, c2;
   cheb_tab(lam, 0, 0, c1, c2);
@@ -1054,18 +1263,6 @@ void launchk(cudaStream_t st, int grid, int block, size_t smem, void (*k)(KArgs.
   cudaLaunchKernelEx(&cfg, k, (KArgs)args...);
 }
 
-#define MG_MB_SWITCH(mb, CALL)                                                     \
-  switch (mb) {                                                                    \
-    case 1: { constexpr int MB = 1; CALL; } break;                                 \
-    case 2: { constexpr int MB = 2; CALL; } break;                                 \
-    case 3: { constexpr int MB = 3; CALL; } break;                                 \
-    case 4: { constexpr int MB = 4; CALL; } break;                                 \
-    case 5: { constexpr int MB = 5; CALL; } break;                                 \
-    case 6: { constexpr int MB = 6; CALL; } break;                                 \
-    case 7: { constexpr int MB = 7; CALL; } break;                                 \
-    default: { constexpr int MB = 8; CALL; } break;                                \
-  }
-
 inline int warps_grid(long warps) { return blocks_for(warps * 32, 65535); }
 
 }  // namespace
@@ -1114,10 +1311,125 @@ void mg_enqueue_setup(cudaStream_t st, const MgDev& M, const FineDev& F, const M
   count_launch(n + 1);
 }
 
+namespace {
+
+// Shared-memory layout of the small levels from t on (byte offsets, every array in whole 16-byte units); returns the
+// total. P slots are sized for FP32 (BF16 transfers use half of theirs).
+size_t small_layout(const MgDev& M, int t, MgTailTab* T) {
+  const int C = M.L - 1;
+  size_t off = 0;
+  auto put = [&](unsigned* o, size_t bytes) {
+    if (o) *o = (unsigned)off;
+    off += (bytes + 15) & ~(size_t)15;
+  };
+  for (int l = t - 1; l < C; ++l) {   // transfers l -> l+1
+    put(T ? &T->o_P[l] : nullptr, (size_t)M.nc[l] * M.mb[l] * M.mb[l + 1] * 4);
+    put(T ? &T->o_choff[l] : nullptr, ((size_t)M.nc[l + 1] + 1) * 4);
+    put(T ? &T->o_ch[l] : nullptr, (size_t)M.nc[l] * 4);
+    put(T ? &T->o_agg[l] : nullptr, (size_t)M.nc[l] * 4);
+  }
+  for (int l = t; l <= C; ++l) {
+    const size_t n = (size_t)M.nc[l] * M.mb[l], mm = (size_t)M.mb[l] * M.mb[l];
+    put(T ? &T->o_b[l] : nullptr, n * 4);
+    put(T ? &T->o_x[l][0] : nullptr, n * 4);
+    if (l == C) break;
+    put(T ? &T->o_rowptr[l] : nullptr, ((size_t)M.nc[l] + 1) * 4);
+    put(T ? &T->o_col[l] : nullptr, (size_t)M.nblk[l] * 4);
+    put(T ? &T->o_aval[l] : nullptr, (size_t)M.nblk[l] * mm * 4);
+    put(T ? &T->o_dinv[l] : nullptr, (size_t)M.nc[l] * mm * 4);
+    put(T ? &T->o_x[l][1] : nullptr, n * 4);
+    put(T ? &T->o_d[l] : nullptr, n * 4);
+  }
+  const size_t nco = (size_t)M.nc[C] * M.mb[C];
+  put(T ? &T->o_cinv : nullptr, nco * nco * 4);
+  put(T ? &T->o_coef : nullptr, kMgMaxLevels * kMgMaxDeg * 2 * 4);
+  return off;
+}
+
+}  // namespace
+
+int mg_tail_level(const MgDev& M) {
+  const int C = M.L - 1;
+  for (int l = 2; l <= C; ++l)
+    if (M.nc[l] <= kTailMaxCells && small_layout(M, l, nullptr) <= kTailSmem) return l;
+  return 0;
+}
+
+void mg_fill_tail(cudaStream_t st, const MgDev& M, MgWork& W) {
+  MgTailTab h;
+  h.M = M;
+  h.t = mg_tail_level(M);
+  for (int l = 0; l < kMgMaxLevels; ++l) {
+    h.d[l] = W.d[l];
+    h.x[l][0] = W.x[l][0];
+    h.x[l][1] = W.x[l][1];
+  }
+  W.tail_smem = 0;
+  if (h.t > 0) {
+    const int t = h.t, C = M.L - 1;
+    W.tail_smem = small_layout(M, t, &h);
+    // copy list: the static structure, the per-setup matrices and transfers (FP32 or BF16 P)
+    for (int v = 0; v < 2; ++v) {
+      unsigned c0 = 0;
+      int n = 0;
+      auto add = [&](const void* src, unsigned dst, size_t bytes) {
+        const unsigned ch = (unsigned)((bytes + 15) / 16);
+        if (ch == 0) return;
+        h.cp[v][n++] = MgTailCopy{src, dst, c0};
+        c0 += ch;
+      };
+      for (int l = t - 1; l < C; ++l) {
+        const size_t np = (size_t)M.nc[l] * M.mb[l] * M.mb[l + 1];
+        if (v == 0) add(M.P[l], h.o_P[l], np * 4);
+        else add(M.Pb[l], h.o_P[l], np * 2);
+        add(M.ch_off[l], h.o_choff[l], ((size_t)M.nc[l + 1] + 1) * 4);
+        add(M.ch[l], h.o_ch[l], (size_t)M.nc[l] * 4);
+        add(M.agg[l], h.o_agg[l], (size_t)M.nc[l] * 4);
+      }
+      for (int l = t; l < C; ++l) {
+        const size_t mm = (size_t)M.mb[l] * M.mb[l];
+        add(M.rowptr[l], h.o_rowptr[l], ((size_t)M.nc[l] + 1) * 4);
+        add(M.col[l], h.o_col[l], (size_t)M.nblk[l] * 4);
+        add(W.aval[l], h.o_aval[l], (size_t)M.nblk[l] * mm * 4);
+        add(W.dinv[l], h.o_dinv[l], (size_t)M.nc[l] * mm * 4);
+      }
+      const size_t nco = (size_t)M.nc[C] * M.mb[C];
+      add(W.cinv, h.o_cinv, nco * nco * 4);
+      add(W.coef, h.o_coef, kMgMaxLevels * kMgMaxDeg * 2 * 4);
+      h.ncopies[v] = n;
+      h.nchunks[v] = (int)c0;
+    }
+  }
+  // pageable source: the call returns once the table is staged, so h may go out of scope
+  cudaMemcpyAsync(W.tail, &h, sizeof(MgTailTab), cudaMemcpyHostToDevice, st);
+}
+
+namespace {
+
+template <class PT>
+void launch_small(cudaStream_t st, const MgWork& W, int cur_prev) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1);
+  cfg.blockDim = dim3(kTailThreads);
+  cfg.dynamicSmemBytes = W.tail_smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_small<PT>, (const MgTailTab*)W.tail, cur_prev);
+}
+
+}  // namespace
+
 // The V-cycle after the fused first step of level 0 (x[0][0], d[0] set from b[0]); returns the index of the level-0
-// buffer that holds z.
-int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const MgWork& W, const int* flag) {
+// buffer that holds z. Levels from mg_tail_level on run in one launch of k_small.
+int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const MgWork& W, const int* flag,
+                      bool cg_beta) {
   const int L = M.L, C = L - 1;
+  const int tl = mg_tail_level(M);
+  const int top = tl > 0 ? tl - 1 : C;   // levels 1 .. top-1 restrict with their own kernels
   int cur[kMgMaxLevels] = {0};
   const int g0 = blocks_for(M.N, 4096);
   // down: level-0 smoothing, residual into d[0] (dead until the post-smoothing rewrites it), restriction
@@ -1137,7 +1449,7 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
     launchk(st, warps_grid(M.nc[1]), kT, 0, k_restr<float>, 1, (const float*)W.d[0], (const float*)M.P[0],
             (const int*)M.ch_off[0], (const int*)M.ch[0], M.nc[1], M.mb[1], W.b[1], (const float*)W.dinv[1],
             W.x[1][0], W.d[1], (const float*)W.coef, 1, C > 1 ? 1 : 0, flag);
-  for (int l = 1; l < C; ++l) {
+  for (int l = 1; l < C && l <= top; ++l) {
     const int gl = warps_grid(M.nc[l]);
     for (int k = 1; k < kMgDegCoarse; ++k) {
       MG_MB_SWITCH(M.mb[l], launchk(st, gl, kT, 0, k_chebl<MB>, M.nc[l], (const int*)M.rowptr[l],
@@ -1149,6 +1461,7 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
     MG_MB_SWITCH(M.mb[l], launchk(st, gl, kT, 0, k_resl<MB>, M.nc[l], (const int*)M.rowptr[l],
                                   (const int*)M.col[l], (const float*)W.aval[l], (const float*)W.b[l],
                                   (const float*)W.x[l][cur[l]], W.d[l], flag));
+    if (l == top) break;   // the tail restricts from here
     if (W.bf16)
       launchk(st, warps_grid(M.nc[l + 1]), kT, 0, k_restr<__nv_bfloat16>, M.mb[l], (const float*)W.d[l],
               (const __nv_bfloat16*)M.Pb[l], (const int*)M.ch_off[l], (const int*)M.ch[l], M.nc[l + 1],
@@ -1160,18 +1473,27 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
               W.b[l + 1], (const float*)W.dinv[l + 1], W.x[l + 1][0], W.d[l + 1], (const float*)W.coef, l + 1,
               l + 1 < C ? 1 : 0, flag);
   }
-  launchk(st, 1, kMgMaxCoarse, 0, k_coarse_solve, M.nc[C] * M.mb[C], (const float*)W.cinv, (const float*)W.b[C],
-          W.x[C][0], flag);
-  // up
-  for (int l = C - 1; l >= 1; --l) {
+  if (tl > 0) {
     if (W.bf16)
-      launchk(st, blocks_for((long)M.nc[l] * M.mb[l]), kT, 0, k_prol<__nv_bfloat16>, M.nc[l], M.mb[l],
-              M.mb[l + 1], (const __nv_bfloat16*)M.Pb[l], (const int*)M.agg[l],
-              (const float*)W.x[l + 1][cur[l + 1]], W.x[l][cur[l]], flag);
+      launch_small<__nv_bfloat16>(st, W, cur[tl - 1]);
     else
-      launchk(st, blocks_for((long)M.nc[l] * M.mb[l]), kT, 0, k_prol<float>, M.nc[l], M.mb[l], M.mb[l + 1],
-              (const float*)M.P[l], (const int*)M.agg[l], (const float*)W.x[l + 1][cur[l + 1]], W.x[l][cur[l]],
-              flag);
+      launch_small<float>(st, W, cur[tl - 1]);
+  } else {
+    launchk(st, 1, kMgMaxCoarse, 0, k_coarse_solve, M.nc[C] * M.mb[C], (const float*)W.cinv, (const float*)W.b[C],
+            W.x[C][0], flag);
+  }
+  // up
+  for (int l = std::min(top, C - 1); l >= 1; --l) {
+    if (l != top || tl == 0) {
+      if (W.bf16)
+        launchk(st, blocks_for((long)M.nc[l] * M.mb[l]), kT, 0, k_prol<__nv_bfloat16>, M.nc[l], M.mb[l],
+                M.mb[l + 1], (const __nv_bfloat16*)M.Pb[l], (const int*)M.agg[l],
+                (const float*)W.x[l + 1][cur[l + 1]], W.x[l][cur[l]], flag);
+      else
+        launchk(st, blocks_for((long)M.nc[l] * M.mb[l]), kT, 0, k_prol<float>, M.nc[l], M.mb[l], M.mb[l + 1],
+                (const float*)M.P[l], (const int*)M.agg[l], (const float*)W.x[l + 1][cur[l + 1]], W.x[l][cur[l]],
+                flag);
+    }
     const int gl = warps_grid(M.nc[l]);
     for (int k = 0; k < kMgDegCoarse; ++k) {
       MG_MB_SWITCH(M.mb[l], launchk(st, gl, kT, 0, k_chebl<MB>, M.nc[l], (const int*)M.rowptr[l],
@@ -1188,17 +1510,28 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
     launchk(st, g0, kT, 0, k_pro0<float>, M.N, M.mb[1], (const float*)M.P[0], (const int*)M.agg[0],
             (const float*)W.x[1][cur[1]], W.x[0][cur[0]], flag);
   for (int k = 0; k < kMgDegFine; ++k) {
-    launchk(st, g0, kT, 0, k_cheb0, F, (const float*)W.a0off, (const float*)W.a0diag, (const float*)W.a0dinv,
-            (const float*)W.b[0], (const float*)W.x[0][cur[0]], W.x[0][1 - cur[0]], W.d[0], (const float*)W.coef, k,
-            flag);
+    if (cg_beta && k + 1 == kMgDegFine)
+      launchk(st, blocks_for(M.N, kMaxRedBlocks), kT, 0, k_cheb0_beta, F, (const float*)W.a0off,
+              (const float*)W.a0diag, (const float*)W.a0dinv, (const float*)W.b[0], (const float*)W.x[0][cur[0]],
+              W.x[0][1 - cur[0]], W.d[0], (const float*)W.coef, k, (const double*)W.kr, (const float*)W.z[0], W.part,
+              W.sc);
+    else
+      launchk(st, g0, kT, 0, k_cheb0, F, (const float*)W.a0off, (const float*)W.a0diag, (const float*)W.a0dinv,
+              (const float*)W.b[0], (const float*)W.x[0][cur[0]], W.x[0][1 - cur[0]], W.d[0], (const float*)W.coef,
+              k, flag);
     cur[0] ^= 1;
   }
   return cur[0];
 }
 
 int mg_vcycle_kernels(const MgDev& M) {
-  const int C = M.L - 1;
-  return (kMgDegFine - 1) + 2 + (C - 1) * (kMgDegCoarse + 1) + 1 + (C - 1) * (1 + kMgDegCoarse) + 1 + kMgDegFine;
+  const int C = M.L - 1, tl = mg_tail_level(M);
+  const int level0 = (kMgDegFine - 1) + 2 + 1 + kMgDegFine;   // smoothing, residual, restriction, prolongation
+  if (tl == 0) return level0 + (C - 1) * (kMgDegCoarse + 1) + 1 + (C - 1) * (1 + kMgDegCoarse);
+  // levels 1 .. tl-1 run their own kernels: down smoothing and residual, the restrictions between them, and on the
+  // way up the prolongations between them and the smoothing; the tail is one more
+  const int own = tl - 1;
+  return level0 + 2 * own * kMgDegCoarse + 2 * (own - 1) + 1;
 }
 
 namespace {
@@ -1249,55 +1582,53 @@ cudaError_t capture_plain(cudaStream_t st, Body&& body, cudaGraphExec_t* out) {
 
 }  // namespace
 
-// Preconditioned CG for A dx = -b (b = W.kb, FP64; dx -> W.kx) as two graphs: out[0] the start (x = 0, r = -b, first
-// V-cycle), out[1] the conditional while loop over the iterations (beta, p and q, x and r with the convergence test,
-// V-cycle). The tolerance and iteration cap are read from W.sc at run time.
+// Preconditioned CG for A dx = -b (b = W.kb, FP64; dx -> W.kx) as two graphs: out[0] the start (x = 0, r = -b with
+// the first smoothing step of the first V-cycle), out[1] the conditional while loop over the iterations (V-cycle with
+// beta in its last step, p and q, x and r with the convergence test). The tolerance and iteration cap are read from
+// W.sc at run time.
 cudaError_t mg_capture_pcg(cudaStream_t st, const MgDev& M, const FineDev& F, MgWork& W, const double* Tval,
                            const double* diagT, cudaGraphExec_t* out) {
   const int gr = blocks_for(M.N, kMaxRedBlocks);
-  int zi = 0;
   cudaError_t e = capture_plain(st, [&]() {
     launchk(st, gr, kT, 0, k_pcg_init, M.N, (const double*)W.kb, -1.0, diagT, W.kx, W.kr, W.b[0],
             (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.coef, W.part, W.sc);
-    zi = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
   }, &out[0]);
   if (e != cudaSuccess) return e;
-  const float* z = W.x[0][zi];
+  // the convergence test is the body's last kernel, so nothing runs after it; the V-cycle kernels need no stop flag
+  // (they only write the preconditioner's scratch and z)
   return capture_while(st, [&](cudaGraphConditionalHandle h) {
-    launchk(st, gr, kT, 0, k_pcg_beta, M.N, (const double*)W.kr, z, (const float*)W.z[0], W.part, W.sc);
+    const float* z = W.x[0][mg_enqueue_vcycle(st, M, F, W, nullptr, true)];   // its last step gives beta
     launchk(st, gr, kT, 0, k_pcg_pq, F, Tval, diagT, z, W.z[0], W.kp, W.kq, W.part, W.sc);
     launchk(st, gr, kT, 0, k_pcg_update, M.N, (const double*)W.kp, (const double*)W.kq, diagT, W.kx, W.kr, W.b[0],
             (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.coef, W.part, W.sc, h);
-    mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
   }, &out[1]);
 }
 
 // Right-preconditioned BiCGStab for J dx = -b (J: jd diagonal, Joff off-diagonal in the SELL layout; b = W.kb;
-// dx -> W.kx; stopping on ||W r|| with W^2 = wgt). out[0] the start (with p^ = B p), out[1] the loop: v = J p^, s,
-// s^ = B s, t = J s^, x and r with the test, p, p^ = B p.
+// dx -> W.kx; stopping on ||W r|| with W^2 = wgt). out[0] the start (r, r^, p = r with the first smoothing step of
+// p^ = B p), out[1] the loop: p (from the second iteration on), p^ = B p, v = J p^, s, s^ = B s, t = J s^, then x
+// and r with the convergence test as the last kernel.
 cudaError_t mg_capture_bicgstab(cudaStream_t st, const MgDev& M, const FineDev& F, MgWork& W, const double* jd,
                                 const double* Joff, const double* wgt, cudaGraphExec_t* out) {
   const int gr = blocks_for(M.N, kMaxRedBlocks);
-  int zi = 0;
   cudaError_t e = capture_plain(st, [&]() {
     launchk(st, gr, kT, 0, k_bicg_init, M.N, (const double*)W.kb, -1.0, wgt, W.kx, W.kr, W.krh, W.kp, W.b[0],
             (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.coef, W.part, W.sc);
-    zi = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
   }, &out[0]);
   if (e != cudaSuccess) return e;
   return capture_while(st, [&](cudaGraphConditionalHandle h) {
-    launchk(st, gr, kT, 0, k_bicg_v, F, Joff, jd, (const float*)W.x[0][zi], W.kpp, W.kv, (const double*)W.krh,
+    launchk(st, gr, kT, 0, k_bicg_p, M.N, (const double*)W.kr, (const double*)W.kv, W.kp, W.b[0],
+            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.coef, W.sc);
+    const int zp = mg_enqueue_vcycle(st, M, F, W, nullptr, false);
+    launchk(st, gr, kT, 0, k_bicg_v, F, Joff, jd, (const float*)W.x[0][zp], W.kpp, W.kv, (const double*)W.krh,
             W.part, W.sc);
     launchk(st, gr, kT, 0, k_bicg_s, M.N, (const double*)W.kr, (const double*)W.kv, W.ks, W.b[0],
             (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.coef, W.sc);
-    const int zs = mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
+    const int zs = mg_enqueue_vcycle(st, M, F, W, nullptr, false);
     launchk(st, gr, kT, 0, k_bicg_t, F, Joff, jd, (const float*)W.x[0][zs], (const double*)W.ks, W.kt, W.part,
             W.sc);
     launchk(st, gr, kT, 0, k_bicg_x, M.N, (const double*)W.kpp, (const float*)W.x[0][zs], (const double*)W.ks,
             (const double*)W.kt, (const double*)W.krh, wgt, W.kx, W.kr, W.part, W.sc, h);
-    launchk(st, gr, kT, 0, k_bicg_p, M.N, (const double*)W.kr, (const double*)W.kv, W.kp, W.b[0],
-            (const float*)W.a0dinv, W.x[0][0], W.d[0], (const float*)W.coef, W.sc);
-    mg_enqueue_vcycle(st, M, F, W, &W.sc->done);
   }, &out[1]);
 }
 
@@ -1307,17 +1638,20 @@ cudaError_t mg_capture_apply(cudaStream_t st, const MgDev& M, const FineDev& F, 
     const int g0 = blocks_for(M.N, 4096);
     launchk(st, g0, kT, 0, k_apply_in, M.N, (const double*)W.kb, W.b[0], (const float*)W.a0dinv, W.x[0][0], W.d[0],
             (const float*)W.coef);
-    const int zi = mg_enqueue_vcycle(st, M, F, W, nullptr);
+    const int zi = mg_enqueue_vcycle(st, M, F, W, nullptr, false);
     launchk(st, g0, kT, 0, k_apply_out, M.N, (const float*)W.x[0][zi], W.kx);
   }, out);
 }
 
 void mg_set_smem_limits() {
-  static bool done = false;
-  if (done) return;
-  cudaFuncSetAttribute(k_coarse_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (kMgMaxCoarse * kMgMaxCoarse + kMgMaxCoarse) * (int)sizeof(double));
-  done = true;
+  static const bool once = [] {   // thread-safe one-time initialisation
+    cudaFuncSetAttribute(k_coarse_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (kMgMaxCoarse * kMgMaxCoarse + kMgMaxCoarse) * (int)sizeof(double));
+    cudaFuncSetAttribute(k_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem);
+    cudaFuncSetAttribute(k_small<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem);
+    return true;
+  }();
+  (void)once;
 }
 
 }  // namespace nlmg

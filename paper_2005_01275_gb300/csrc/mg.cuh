@@ -25,6 +25,10 @@ constexpr int kMgDegFine = 2;       // Chebyshev steps before and after the coar
 constexpr int kMgDegCoarse = 2;     // the same on levels 1 .. L-2
 constexpr double kMgAlpha = 4.0;    // Chebyshev interval [lam / alpha, lam]
 constexpr int kMgMaxDeg = 4;        // Chebyshev steps per smoothing at most (coefficient table size)
+constexpr int kTailThreads = 1024;  // threads of the small-level kernel (k_small, one block)
+constexpr int kTailMaxCells = 1024; // it starts at the first level l >= 2 with at most this many cells ...
+constexpr size_t kTailSmem = 200 * 1024;   // ... whose data from there on fit this much shared memory
+constexpr int kTailMaxCopies = 8 * kMgMaxLevels;
 
 // Static structure of the preconditioner (host side, built once per hierarchy).
 struct MgHost {
@@ -57,6 +61,26 @@ struct MgScal {
   unsigned cnt[8];   // arrival counters of the reductions (each reset by its last block)
 };
 
+// One contiguous source array of the small-level kernel's copy-in: 16-byte chunks c0 .. to shared byte offset dst.
+struct MgTailCopy {
+  const void* src;
+  unsigned dst, c0;
+};
+
+// What the small-level kernel reads, as one device-resident table per context: the level data, its shared-memory
+// layout (byte offsets) and copy list (index 0 with FP32 transfers, 1 with BF16).
+struct MgTailTab {
+  MgDev M;
+  float *d[kMgMaxLevels] = {nullptr}, *x[kMgMaxLevels][2] = {{nullptr}};   // global vectors (level t-1 is used)
+  int t = 0;
+  unsigned o_P[kMgMaxLevels] = {0}, o_choff[kMgMaxLevels] = {0}, o_ch[kMgMaxLevels] = {0}, o_agg[kMgMaxLevels] = {0};
+  unsigned o_rowptr[kMgMaxLevels] = {0}, o_col[kMgMaxLevels] = {0}, o_aval[kMgMaxLevels] = {0},
+           o_dinv[kMgMaxLevels] = {0}, o_b[kMgMaxLevels] = {0}, o_d[kMgMaxLevels] = {0},
+           o_x[kMgMaxLevels][2] = {{0}}, o_cinv = 0, o_coef = 0;
+  int ncopies[2] = {0, 0}, nchunks[2] = {0, 0};
+  MgTailCopy cp[2][kTailMaxCopies];
+};
+
 // Per-context work buffers.
 struct MgWork {
   float *a0off = nullptr, *a0diag = nullptr, *a0dinv = nullptr;
@@ -73,6 +97,8 @@ struct MgWork {
   MgScal* sc = nullptr;
   MgScal* h_sc = nullptr;                                // pinned copy
   cudaGraphExec_t g_pcg[2] = {nullptr, nullptr}, g_bicg[2] = {nullptr, nullptr}, g_apply = nullptr;
+  MgTailTab* tail = nullptr;   // device copy for the small-level kernel (mg_fill_tail)
+  size_t tail_smem = 0;        // its dynamic shared memory
   int bf16 = 0;            // transfers in BF16 (FP32 accumulation) in the setup and V-cycle enqueued next
   int graphs_bf16 = -1;    // the transfer type the captured graphs use (-1: none captured)
 };
@@ -92,8 +118,18 @@ void mg_enqueue_setup(cudaStream_t st, const MgDev& M, const FineDev& F, const M
 
 // Enqueues one V-cycle z = B r on stream st for an FP32 right-hand side already in W.b[0] with the first pre-smoothing
 // step fused by the caller (x[0][0], d[0] hold it); returns the index i of the level-0 buffer W.x[0][i] that holds z;
-// `flag` (may be null) is a device int that makes every kernel return at once when non-zero.
-int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const MgWork& W, const int* flag);
+// `flag` (may be null) is a device int that makes every kernel return at once when non-zero. With cg_beta the last
+// step also forms the flexible CG step length from W.kr, z and z_old = W.z[0] (into W.sc).
+int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const MgWork& W, const int* flag,
+                      bool cg_beta);
+
+// Writes W.tail (device memory of sizeof(MgTailTab), allocated by the caller) from M and W, on stream st, and sets
+// W.tail_smem. Every array it lists must be allocated in whole 16-byte units.
+void mg_fill_tail(cudaStream_t st, const MgDev& M, MgWork& W);
+
+// First level the small-level kernel takes over (levels t .. L-1 and the transfers to and from t-1 in one launch of
+// one thread block, out of shared memory), or 0 if the V-cycle runs one kernel per phase throughout.
+int mg_tail_level(const MgDev& M);
 
 // Kernels in one V-cycle after its fused first step (for the launch counts of graph replays).
 int mg_vcycle_kernels(const MgDev& M);

@@ -181,22 +181,25 @@ struct nlmg_ctx {
     prof.used = 0;
   }
 
+  // device arrays are allocated in whole 16-byte units (kernels may copy them in 16-byte chunks)
+  static size_t whole16(size_t bytes) { return (std::max<size_t>(bytes, 1) + 15) & ~(size_t)15; }
   template <class T>
   T* dalloc(size_t n) {
     void* p = nullptr;
-    if (n == 0) n = 1;
-    CK(cudaMalloc(&p, n * sizeof(T)));
+    const size_t bytes = whole16(n * sizeof(T));
+    CK(cudaMalloc(&p, bytes));
     allocs.push_back(p);
-    own_bytes += n * sizeof(T);
+    own_bytes += bytes;
     return (T*)p;
   }
   // read-only data of the hierarchy: owned by the shared part
   template <class T>
   T* upload(const std::vector<T>& v) {
     void* p = nullptr;
-    CK(cudaMalloc(&p, std::max<size_t>(v.size(), 1) * sizeof(T)));
+    const size_t bytes = whole16(v.size() * sizeof(T));
+    CK(cudaMalloc(&p, bytes));
     sh->allocs.push_back(p);
-    sh->bytes += std::max<size_t>(v.size(), 1) * sizeof(T);
+    sh->bytes += bytes;
     if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
     return (T*)p;
@@ -1134,6 +1137,9 @@ void alloc_mg(nlmg_ctx* c) {
   W.sc = c->dalloc<MgScal>(1);
   CK(cudaMemsetAsync(W.sc, 0, sizeof(MgScal), c->st));
   CK(cudaMallocHost(&W.h_sc, sizeof(MgScal)));
+  W.tail = c->dalloc<MgTailTab>(1);
+  mg_fill_tail(c->st, M, W);
+  CK(cudaGetLastError());
   mg_set_smem_limits();
 }
 
@@ -1189,9 +1195,9 @@ int mg_pcg(nlmg_ctx* c, const double* R, const double* kap) {
   c->prof_end(pi);
   const int it = mg_finish(c, "multigrid-preconditioned CG");
   const int V = mg_vcycle_kernels(M);
-  count_launch(1 + V + std::max(it, 1) * (3 + V));   // the start, then one loop body per iteration
+  count_launch(1 + std::max(it, 1) * (2 + V));   // the start, then one loop body per iteration
   if (pi >= 0) {
-    c->prof.bytes[5] += (double)(it + 1) * (c->sh->mg_bytes_vcycle + c->sh->mg_bytes_iter);
+    c->prof.bytes[5] += (double)it * (c->sh->mg_bytes_vcycle + c->sh->mg_bytes_iter);
     c->prof.bytes[7] += c->sh->mg_bytes_setup;
   }
   c->lin_iters += it;
@@ -1218,9 +1224,9 @@ int mg_bicgstab(nlmg_ctx* c, const double* R, const double* kap) {
   c->prof_end(pi);
   const int it = mg_finish(c, "multigrid-preconditioned BiCGStab");
   const int V = mg_vcycle_kernels(M);
-  count_launch(1 + V + std::max(it, 1) * (5 + 2 * V));
+  count_launch(1 + std::max(it, 1) * (5 + 2 * V));
   if (pi >= 0) {
-    c->prof.bytes[6] += (double)(2 * it + 1) * c->sh->mg_bytes_vcycle + (double)it * 2.0 * c->sh->mg_bytes_iter;
+    c->prof.bytes[6] += (double)(2 * it) * c->sh->mg_bytes_vcycle + (double)it * 2.0 * c->sh->mg_bytes_iter;
     c->prof.bytes[7] += c->sh->mg_bytes_setup;
   }
   c->lin_iters += it;

@@ -87,7 +87,7 @@ def test_set_options_keeps_the_hierarchy_fixed(nlmg_lib):
     assert ctx.opts.smoother == nlmg_lib.SMOOTH_PICARD_NEWTON and ctx.opts.newton_switch == 1e-3
     ctx.set_options(cascadic=1)
     assert ctx.opts.cascadic == 1
-    for bad in (dict(n_levels=3), dict(modes=(ctypes.c_int32 * 8)(3, 3, 3, 3, 3, 3, 3, 3)), dict(lin_precision=2),
+    for bad in (dict(n_levels=3), dict(modes=(ctypes.c_int32 * 8)(3, 3, 3, 3, 3, 3, 3, 3)), dict(lin_precision=3),
                 dict(omega=0.0), dict(smoother=3), dict(newton_switch=-1.0), dict(newton_switch=float("nan")),
                 dict(newton_lin_tol=0.0), dict(flux_modes=(ctypes.c_int32 * 8)(2, 1, 1, 1, 1, 1, 1, 1)), dict(cascadic=2)):
         with pytest.raises(nlmg_lib.NlmgError):
