@@ -69,6 +69,13 @@ struct LevelDev {
   int* if_cell = nullptr;                          // per interface slot: its cell
   int* slot_cell = nullptr;                        // per local flux slot: its cell
   int* p_cell = nullptr;                           // per pressure unknown: its cell
+  // H over the lambdas as a SELL-32 matrix (for the memory-resident pipelined CG of large levels): per slice of 32
+  // lambdas its width and first entry; per entry (slice-major, lane fastest) the column lambda and the Hc indices of
+  // its contributions from the row lambda's first and second slot (-1: none); per lambda the cells of its two slots.
+  // Entry (l, m) = kappa_c0 Hc[i0] + kappa_c1 Hc[i1].
+  int hs_n = 0;
+  int *hs_w = nullptr, *hs_off = nullptr, *hs_col = nullptr, *hs_i0 = nullptr, *hs_i1 = nullptr;
+  int *lam_c0 = nullptr, *lam_c1 = nullptr;
 };
 
 // Transfer between level l and l+1

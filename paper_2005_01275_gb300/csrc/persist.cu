@@ -495,10 +495,43 @@ __device__ __forceinline__ T hyb_row_product(const LevelDev& L, const T* __restr
 // double-buffered. Per iteration: n = H m; z = n + beta z; q = m + beta q; s = w + beta s; p = u + beta p;
 // lam += alpha p; r -= alpha s; u -= alpha q; w -= alpha z; then gamma = (r, u), delta = (w, u), (r, r) in one
 // reduction, from which the last step derives the next beta and alpha.
+// (H v)_l from the assembled SELL form (one thread per lambda, the 32 lambdas of a slice read their entries
+// coalesced); the entries, then the gathered v, are loaded eight at a time before the products. hsv was written
+// earlier in the launch, so it is read through L2.
 template <class T>
-__device__ bool hyb_pipe_loop(const LevelDev& L, const T* __restrict__ Hc, const double* kapc, T* lam, T* lr, T* lu,
-                              T* pp, T* lq, T* ldinv, const HybPipeBufs<T>& P, Grid& g, int gsz, double tol2,
-                              double rr0, int maxit, int& it_out, double& rr_out) {
+__device__ __forceinline__ T sell_h_product(const LevelDev& L, const T* hsv, const T* v, int l, bool act) {
+  T h = (T)0;
+  if (act) {
+    const int w = L.hs_w[l >> 5];
+    const int e0 = L.hs_off[l >> 5] + (l & 31);
+    for (int j0 = 0; j0 < w; j0 += 8) {
+      T hv[8], xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + 32 * (j0 + u);
+        const bool in = j0 + u < w;
+        hv[u] = in ? __ldcg(&hsv[e]) : (T)0;
+        xv[u] = in ? __ldcg(&v[L.hs_col[e]]) : (T)0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) h = fma(hv[u], xv[u], h);
+    }
+  }
+  return h;
+}
+
+// H v of lambda l in the memory-resident loop: SELL form if assembled (gsz = 1), else the per-cell blocks.
+template <class T>
+__device__ __forceinline__ T h_product(const LevelDev& L, const T* __restrict__ Hc, const T* hsv, const double* kapc,
+                                       const T* v, int l, int gi, int gsz, bool act) {
+  if (hsv) return sell_h_product<T>(L, hsv, v, l, act);
+  return hyb_row_product<T>(L, Hc, kapc, v, l, gi, gsz, act);
+}
+
+template <class T>
+__device__ bool hyb_pipe_loop(const LevelDev& L, const T* __restrict__ Hc, const T* hsv, const double* kapc, T* lam,
+                              T* lr, T* lu, T* pp, T* lq, T* ldinv, const HybPipeBufs<T>& P, Grid& g, int gsz,
+                              double tol2, double rr0, int maxit, int& it_out, double& rr_out) {
   const long total = (long)L.nlam * gsz;
   const int lane = threadIdx.x & 31;
   const long stride = (long)gridDim.x * blockDim.x;
@@ -511,7 +544,7 @@ __device__ bool hyb_pipe_loop(const LevelDev& L, const T* __restrict__ Hc, const
       const bool act = t < total;
       const int l = act ? (int)(t / gsz) : 0;
       const int gi = lane & (gsz - 1);
-      const T w = hyb_row_product<T>(L, Hc, kapc, lu, l, gi, gsz, act);
+      const T w = h_product<T>(L, Hc, hsv, kapc, lu, l, gi, gsz, act);
       if (act && gi == 0) {
         const T r = lr[l], u = lu[l];
         P.w[l] = w;
@@ -547,7 +580,7 @@ __device__ bool hyb_pipe_loop(const LevelDev& L, const T* __restrict__ Hc, const
       const bool act = t < total;
       const int l = act ? (int)(t / gsz) : 0;
       const int gi = lane & (gsz - 1);
-      const T n = hyb_row_product<T>(L, Hc, kapc, mc, l, gi, gsz, act);
+      const T n = h_product<T>(L, Hc, hsv, kapc, mc, l, gi, gsz, act);
       if (act && gi == 0) {
         const T w = P.w[l], m = ldinv[l] * w;
         const T z = n + b * P.z[l];
@@ -958,7 +991,7 @@ __device__ bool hyb_solve_dev(const LevelDev& L, const T* __restrict__ Hc, const
                               const double* kapc, const double* bs, const double* bp, T* ylam, T* ydiag, T* lam,
                               T* lr, T* lz, T* pa, T* pb, T* lq, T* ldinv, double* dsig, double* dp, Grid& g,
                               double tol, int maxit, int gsz, int& iters, double& rr0_out, double& rr_out,
-                              const HybPipeBufs<T>* pipe = nullptr, int gsz_reg = 0) {
+                              const HybPipeBufs<T>* pipe = nullptr, int gsz_reg = 0, T* hsv = nullptr) {
   // phase 0: per interface slot k of cell c, u_k = kappa A[k,:] bhat + B[k,:] b_p (signed) and kappa Hc[k,k]
   GSTRIDE(k, L.nif) {
     const int c = L.if_cell[k];
@@ -973,6 +1006,17 @@ __device__ bool hyb_solve_dev(const LevelDev& L, const T* __restrict__ Hc, const
     ylam[k] = (T)L.if_sign[k] * ((T)kp * a1 + a2_);
     const int k0 = L.if_off[c], ni = L.if_off[c + 1] - k0;
     ydiag[k] = (T)kp * Hc[L.hc_off[c] + (k - k0) * ni + (k - k0)];
+  }
+  if (hsv) {   // the SELL form of H at this kappa (padding entries have no contribution: 0)
+    GSTRIDE(l, L.nlam) {
+      const T k0 = (T)__ldcg(&kapc[L.lam_c0[l]]), k1 = (T)__ldcg(&kapc[L.lam_c1[l]]);
+      const int w = L.hs_w[l >> 5];
+      int e = L.hs_off[l >> 5] + (l & 31);
+      for (int j = 0; j < w; ++j, e += 32) {
+        const int a = L.hs_i0[e], b = L.hs_i1[e];
+        hsv[e] = (a >= 0 ? k0 * Hc[a] : (T)0) + (b >= 0 ? k1 * Hc[b] : (T)0);
+      }
+    }
   }
   if (!grid_barrier(g)) return false;
   T u0 = (T)0, u1 = (T)0;   // per-thread partial sums in T, block and grid sums in FP64
@@ -1000,7 +1044,8 @@ __device__ bool hyb_solve_dev(const LevelDev& L, const T* __restrict__ Hc, const
     if (!hyb_pipe_loop_reg<T>(L, Hc, kapc, lam, lr, lz, ldinv, *pipe, g, gsz_reg, tol2, rr0, maxit, it, rr))
       return false;
   } else if (pipe) {
-    if (!hyb_pipe_loop<T>(L, Hc, kapc, lam, lr, lz, pp, lq, ldinv, *pipe, g, gsz, tol2, rr0, maxit, it, rr))
+    if (!hyb_pipe_loop<T>(L, Hc, hsv, kapc, lam, lr, lz, pp, lq, ldinv, *pipe, g, hsv ? 1 : gsz, tol2, rr0, maxit,
+                          it, rr))
       return false;
   }
   while (!pipe && rr0 > 0.0 && rr > tol2 && it < maxit) {
@@ -1294,7 +1339,8 @@ __global__ void __launch_bounds__(kPThreads, 1) kp_coarse_step(LevelDev L, const
     double rr0 = 0.0, rr = 0.0;
     if (!hyb_solve_dev<T>(L, Hc, Sinv, B.kapc, B.nb, B.nb + L.nflux, B.ylam, B.ydiag, B.lam, B.lr, B.lz, B.pa,
                           B.pb, B.lq, B.ldinv, B.dx, B.dx + L.nflux, g, P.lin_tol, P.maxit, gsz, it, rr0, rr,
-                          B.pipe.w ? &B.pipe : nullptr, gsz_reg))
+                          B.pipe.w ? &B.pipe : nullptr, gsz_reg,
+                          B.pipe.w && gsz_reg == 0 && L.hs_n > 0 ? B.hsv : nullptr))
       return;
     iters += it;
     if (!isfinite(rr)) {
@@ -1444,8 +1490,12 @@ template cudaError_t launch_fine_cg<float>(cudaStream_t, const FineDev&, const f
 template <class T>
 cudaError_t launch_coarse_step(cudaStream_t st, const LevelDev& L, const T* Hc, const T* Sinv,
                                const CoarseStepBufs<T>& B, const CoarseStepParams& P, double* partial, GridSync gs,
-                               CoarseStepResult* res) {
-  int gsz = 1;
+                               CoarseStepResult* res, bool* sell) {
+  // lanes per lambda in the memory-resident loop: at least 4 (each reads a quarter of the ~14-entry rows, so the
+  // group's loads of a row are coalesced and its chain of dependent loads short; measured on the 128^3 workload's
+  // first coarse level, 229,538 lambdas: 164 us per iteration with 1 lane, 83 with 4, 123 with 8), and more on small
+  // levels, so that they still occupy every SM
+  int gsz = 4;
   while (gsz < 32 && (long)L.nlam * gsz < 65536) gsz *= 2;
   long items = (long)L.nlam * gsz;
   for (long v : {(long)L.nif, (long)L.nyl, (long)L.np, (long)L.nflux + L.np, (long)L.nc})
@@ -1460,13 +1510,14 @@ cudaError_t launch_coarse_step(cudaStream_t st, const LevelDev& L, const T* Hc, 
     gsz_reg = 1;
     while (gsz_reg < 32 && (long)L.nlam * gsz_reg * 2 <= lanes) gsz_reg *= 2;
   }
+  if (sell) *sell = B.pipe.w && gsz_reg == 0 && B.hsv && L.hs_n > 0;
   void* args[] = {(void*)&L, (void*)&Hc, (void*)&Sinv, (void*)&B, (void*)&P, (void*)&partial, (void*)&gs,
                   (void*)&gsz, (void*)&gsz_reg, (void*)&res};
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
 }
 template cudaError_t launch_coarse_step<double>(cudaStream_t, const LevelDev&, const double*, const double*,
                                                 const CoarseStepBufs<double>&, const CoarseStepParams&, double*,
-                                                GridSync, CoarseStepResult*);
+                                                GridSync, CoarseStepResult*, bool*);
 
 // ---- failure detection: the bounded grid barrier on its own ---------------------------------------------------
 // Every block except `absent` waits at one grid barrier whose spin limit is `spin_limit` (1024-spin granularity);

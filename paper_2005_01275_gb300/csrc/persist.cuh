@@ -73,6 +73,7 @@ struct CoarseStepBufs {
   LinParts base, dir;                             // linear parts at x and along dx (Algorithm 1's trials)
   T *ylam, *ydiag, *lam, *lr, *lz, *pa, *pb, *lq, *ldinv;   // hybridized CG (nif / nlam)
   HybPipeBufs<T> pipe;   // set: pipelined hybridized CG (one grid synchronisation per iteration)
+  T* hsv = nullptr;      // L.hs_n values of the assembled H (memory-resident pipelined CG), or null
 };
 
 struct CoarseStepParams {
@@ -101,11 +102,12 @@ struct CoarseStepResult {
 
 // One launch: [Algorithm 1 along a given correction], up to nsteps coarse Picard steps (frozen-kappa hybridized
 // solve, clamp on Pi~ dp, Algorithm 1), leaving the residual r = A(x) - b (and -r, kappa per cell) at the final x;
-// every decision is taken on the device.
+// every decision is taken on the device. The hybridized CG runs on the assembled SELL form of H (B.hsv, L.hs_*) when
+// its pipelined form is memory resident on this grid; *sell (may be null) tells whether it did.
 template <class T>
 cudaError_t launch_coarse_step(cudaStream_t st, const LevelDev& L, const T* Hc, const T* Sinv,
                                const CoarseStepBufs<T>& B, const CoarseStepParams& P, double* partial, GridSync gs,
-                               CoarseStepResult* res);
+                               CoarseStepResult* res, bool* sell = nullptr);
 
 
 // Failure-detection check: a cooperative launch of min(blocks, co-resident) blocks in which every block but `absent`

@@ -47,6 +47,7 @@ struct CoarseBuf {
   double *ylam = nullptr, *ydiag = nullptr, *lam = nullptr, *lr = nullptr, *lz = nullptr, *lpa = nullptr, *lpb = nullptr,
          *lq = nullptr, *ldinv = nullptr, *xi = nullptr;
   double *hw = nullptr, *hz = nullptr, *hs = nullptr, *hma = nullptr, *hmb = nullptr;   // pipelined hybridized CG
+  double* hsv = nullptr;    // values of the SELL form of H
   LinParts base{}, dir{};   // linear parts of the operator at x and along dx (fused coarse step)
   double rn = 0.0;  // ||A(x) - b|| at the current x (valid after coarse_res)
 };
@@ -80,7 +81,7 @@ struct Shared {
   std::vector<LevelDev> LD;
   std::vector<TransferDev> TD;
   long long nnz_real = 0;
-  double hyb_bytes_per_iter[8] = {0};
+  double hyb_bytes_per_iter[8] = {0}, hyb_bytes_per_iter_sell[8] = {0};
   double coarse_res_bytes[8] = {0};   // algorithmic bytes of one coarse operator evaluation per level
   // algorithmic flops (FMA = 2) per level: one hybridized CG iteration, the fixed work of one hybridized solve
   // (right-hand side per interface slot, local recovery), one coarse operator evaluation
@@ -404,6 +405,72 @@ void upload_level(nlmg_ctx* c, int l) {
   D.if_cell = c->upload(ifc);
   D.slot_cell = c->upload(slc);
   D.p_cell = c->upload(pc);
+  // H as a SELL-32 matrix over the lambdas: row l takes the Hc row of each of its two slots k (cell c_k, columns the
+  // lambdas of c_k's interface slots); a column met from both slots (l itself, or another lambda of the same
+  // interface) gets both contributions
+  {
+    const int nsl = (nlam + 31) / 32;
+    std::vector<int> lc0(nlam), lc1(nlam), rlen(nlam, 0), roff(nlam + 1, 0);
+    std::vector<int> rcol, ri0, ri1;
+    rcol.reserve((size_t)nlam * 28);
+    ri0.reserve((size_t)nlam * 28);
+    ri1.reserve((size_t)nlam * 28);
+    for (int l = 0; l < nlam; ++l) {
+      const size_t start = rcol.size();
+      for (int side = 0; side < 2; ++side) {
+        const int k = side == 0 ? ly0[l] : ly1[l];
+        if (k < 0) throw Error(NLMG_EINVAL, "a coarse interface unknown without two cells");
+        const int cc = ifc[k], k0 = if_off[cc], ni = if_off[cc + 1] - k0;
+        (side == 0 ? lc0 : lc1)[l] = cc;
+        for (int j = 0; j < ni; ++j) {
+          const int m = if_lam[k0 + j], idx = hc_off[cc] + (k - k0) * ni + j;
+          size_t q = start;
+          while (q < rcol.size() && rcol[q] != m) ++q;
+          if (q == rcol.size()) {
+            rcol.push_back(m);
+            ri0.push_back(-1);
+            ri1.push_back(-1);
+          }
+          (side == 0 ? ri0 : ri1)[q] = idx;
+        }
+      }
+      rlen[l] = (int)(rcol.size() - start);
+      roff[l + 1] = (int)rcol.size();
+    }
+    std::vector<int> hw(nsl, 0), hoff(nsl + 1, 0);
+    for (int s = 0; s < nsl; ++s) {
+      int w = 0;
+      for (int l = 32 * s; l < std::min(nlam, 32 * s + 32); ++l) w = std::max(w, rlen[l]);
+      hw[s] = w;
+      hoff[s + 1] = hoff[s] + 32 * w;
+    }
+    const int E = nsl ? hoff[nsl] : 0;
+    std::vector<int> hcol(E), hi0(E, -1), hi1(E, -1);
+    for (int s = 0; s < nsl; ++s)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int l = 32 * s + lane;
+        for (int j = 0; j < hw[s]; ++j) {
+          const int e = hoff[s] + lane + 32 * j;
+          if (l < nlam && j < rlen[l]) {
+            hcol[e] = rcol[roff[l] + j];
+            hi0[e] = ri0[roff[l] + j];
+            hi1[e] = ri1[roff[l] + j];
+          } else {
+            hcol[e] = l < nlam ? l : 0;   // padding: no contribution
+          }
+        }
+      }
+    D.hs_n = E;
+    D.hs_w = c->upload(hw);
+    D.hs_off = c->upload(hoff);
+    D.hs_col = c->upload(hcol);
+    D.hs_i0 = c->upload(hi0);
+    D.hs_i1 = c->upload(hi1);
+    D.lam_c0 = c->upload(lc0);
+    D.lam_c1 = c->upload(lc1);
+    // one CG iteration on the SELL form: entries (value, column) and the gathered vector, plus the lambda vectors
+    c->sh->hyb_bytes_per_iter_sell[l] = 20.0 * E + 136.0 * nlam;
+  }
   // algorithmic bytes of one CG iteration of the hybridized solve: H blocks, their lambda ids, the per-interface
   // buffer written and read, the lambda vectors (z, p_old gathered once; CG update 5 reads + 3 writes)
   c->sh->hyb_bytes_per_iter[l] = 8.0 * (double)Hc.size() + 12.0 * D.nif + 8.0 * D.nc + 16.0 * D.nif + 136.0 * nlam;
@@ -458,6 +525,7 @@ void alloc_level(nlmg_ctx* c, int l) {
   B.ldinv = c->dalloc<double>(nlam);
   B.xi = c->dalloc<double>(nlam);
   for (double** pp : {&B.hw, &B.hz, &B.hs, &B.hma, &B.hmb}) *pp = c->dalloc<double>(nlam);
+  B.hsv = c->dalloc<double>((size_t)D.hs_n);
   for (LinParts* lp : {&B.base, &B.dir}) {
     lp->ms = c->dalloc<double>(D.nyl);
     lp->ds = c->dalloc<double>(D.nyl);
@@ -977,8 +1045,10 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
   const bool pipe = P.lin_tol >= 1e-6;
   CoarseStepBufs<double> Bd{B.x, B.b, B.r, B.nb, B.dx, B.kapc, B.base, B.dir, B.ylam, B.ydiag,
                             B.lam, B.lr, B.lz, B.lpa, B.lpb, B.lq, B.ldinv,
-                            pipe ? HybPipeBufs<double>{B.hw, B.hz, B.hs, B.hma, B.hmb} : HybPipeBufs<double>{}};
-  CK(launch_coarse_step<double>(c->st, L, L.Hc, L.Sinv, Bd, P, c->d_partial, gs, dres));
+                            pipe ? HybPipeBufs<double>{B.hw, B.hz, B.hs, B.hma, B.hmb} : HybPipeBufs<double>{},
+                            B.hsv};
+  bool sell = false;
+  CK(launch_coarse_step<double>(c->st, L, L.Hc, L.Sinv, Bd, P, c->d_partial, gs, dres, &sell));
   c->prof_end(pi);
   count_launch(1);
   CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(PcgResult) + sizeof(CoarseStepResult), cudaMemcpyDeviceToHost,
@@ -992,7 +1062,8 @@ void coarse_step(nlmg_ctx* c, int l, bool backtrack_first, int nsteps, bool coar
                                     std::to_string(l));
   B.rn = R.rn;
   if (pi >= 0) {
-    c->prof.bytes[kid] += (double)R.iters * c->sh->hyb_bytes_per_iter[l] +
+    const double per_iter = sell ? c->sh->hyb_bytes_per_iter_sell[l] : c->sh->hyb_bytes_per_iter[l];
+    c->prof.bytes[kid] += (double)R.iters * per_iter +
                           (double)R.res_evals * c->sh->coarse_res_bytes[l] +
                           (double)(R.trials + R.steps + 1) * c->sh->coarse_trial_bytes[l];
     c->prof.flops[kid] += (double)R.iters * c->sh->hyb_flops_per_iter[l] +
