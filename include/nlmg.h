@@ -121,7 +121,12 @@ typedef struct {
                                 option when set at setup: the setup then coarsens beyond n_levels, for the
                                 preconditioner only, until the coarsest level has at most 128 pressure unknowns (the
                                 FAS cycles still use n_levels levels); a context set up with 0 cannot switch to 1 */
-  int32_t reserved[3];
+  int32_t mg_row_cells;      /* multigrid preconditioner (lin_precond = 1): block levels with at least this many cells
+                                run their smoothing steps and residuals one thread per cell component (vector loads
+                                of the block rows, every lane busy: for large levels, bandwidth bound); smaller levels
+                                one warp per cell (shorter dependent chains: for small, latency-bound levels). Only
+                                the order of the sums differs. Default 16384; 0: every level row-parallel; >= 0 */
+  int32_t reserved[2];
 } nlmg_options;
 
 typedef struct {

@@ -719,6 +719,174 @@ __global__ void k_prol(int nc, int mbf, int mb, const PT* __restrict__ Pl, const
                        agg, e, x);
 }
 
+// MB consecutive floats from p into v: 16-byte loads when MB % 4 == 0, 8-byte loads when MB is even (the caller
+// guarantees p is aligned accordingly: every array here is its own allocation, and a block row or a cell's vector
+// segment starts at a multiple of MB floats).
+template <int MB>
+__device__ __forceinline__ void ld_seg(const float* p, float (&v)[MB]) {
+  if constexpr (MB % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < MB / 4; ++k) {
+      const float4 t = reinterpret_cast<const float4*>(p)[k];
+      v[4 * k] = t.x;
+      v[4 * k + 1] = t.y;
+      v[4 * k + 2] = t.z;
+      v[4 * k + 3] = t.w;
+    }
+  } else if constexpr (MB % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < MB / 2; ++k) {
+      const float2 t = reinterpret_cast<const float2*>(p)[k];
+      v[2 * k] = t.x;
+      v[2 * k + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < MB; ++k) v[k] = p[k];
+  }
+}
+
+// Row-parallel forms of the block-level smoothing step and residual (the per-level kernels of the V-cycle; the
+// shared-memory tail keeps the warp-per-cell bodies above): one thread per cell component, cell c = 32 g + t / MB and
+// component u = t % MB for thread t of a block of 32 MB threads, so a block holds whole cells; blocks take groups g
+// gridDim.x apart. A thread reads row u of each block of the cell's row in block order and the block column's x
+// segment, with vector loads, the column indices of kRowBatch blocks before their entries. The warp-per-cell form
+// leaves 8 - MB of every 8 lanes idle and runs one cell per warp; here every lane is busy and a warp covers 32 / MB
+// cells.
+template <int MB>
+__device__ __forceinline__ float row_ax_u(int c, int u, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                          const float* __restrict__ aval, const float* __restrict__ x) {
+  constexpr int RB = MB <= 4 ? 8 : 4;
+  float ax = 0.0f;
+  const int q1 = rowptr[c + 1];
+  for (int qb = rowptr[c]; qb < q1; qb += RB) {
+    int cq[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) cq[j] = qb + j < q1 ? col[qb + j] : -1;
+    float a[RB][MB], xv[RB][MB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      if (cq[j] >= 0) {
+        ld_seg<MB>(aval + ((size_t)(qb + j) * MB + u) * MB, a[j]);
+        ld_seg<MB>(x + (size_t)cq[j] * MB, xv[j]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < MB; ++v) a[j][v] = xv[j][v] = 0.0f;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+#pragma unroll
+      for (int v = 0; v < MB; ++v) ax = fmaf(a[j][v], xv[j][v], ax);
+  }
+  return ax;
+}
+
+template <int MB>
+__global__ void __launch_bounds__(32 * MB) k_chebr(int nc, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                                   const float* __restrict__ aval, const float* __restrict__ dinv,
+                                                   const float* __restrict__ b, const float* __restrict__ xin,
+                                                   float* __restrict__ xout, float* __restrict__ d,
+                                                   const float* __restrict__ lam, int l, int k, const int* done) {
+  pdl_start();
+  if (stop(done)) return;
+  float c1, c2;
+  cheb_tab(lam, l, k, c1, c2);
+  __shared__ float rs[32 * MB];
+  const int cl = threadIdx.x / MB, u = threadIdx.x - cl * MB;
+  const int groups = (nc + 31) / 32;
+  for (int g = blockIdx.x; g < groups; g += gridDim.x) {   // the same trip count in every thread of the block
+    const int c = g * 32 + cl;
+    const bool act = c < nc;
+    const size_t i = (size_t)c * MB + u;
+    float res = 0.0f, dv[MB];
+    if (act) {
+      ld_seg<MB>(dinv + i * MB, dv);
+      res = b[i] - row_ax_u<MB>(c, u, rowptr, col, aval, xin);
+    }
+    rs[threadIdx.x] = res;
+    __syncthreads();
+    if (act) {
+      float s = 0.0f;
+#pragma unroll
+      for (int v = 0; v < MB; ++v) s = fmaf(dv[v], rs[cl * MB + v], s);
+      const float dn = (k == 0 ? 0.0f : c1 * d[i]) + c2 * s;
+      d[i] = dn;
+      xout[i] = xin[i] + dn;
+    }
+    __syncthreads();
+  }
+}
+
+template <int MB>
+__global__ void __launch_bounds__(32 * MB) k_resr(int nc, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                                  const float* __restrict__ aval, const float* __restrict__ b,
+                                                  const float* __restrict__ x, float* __restrict__ res,
+                                                  const int* done) {
+  pdl_start();
+  if (stop(done)) return;
+  const long rows = (long)nc * MB;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / MB), u = (int)(i - (long)c * MB);
+    res[i] = b[i] - row_ax_u<MB>(c, u, rowptr, col, aval, x);
+  }
+}
+
+// Level-0 restriction with float transfers and MB modes per aggregate: restr_body's work split and order (one warp
+// per aggregate, a lane per child, children t and t + 32 together), with the child's MB transfer entries read by
+// vector loads and the aggregate's block-inverse row (for the fused first smoothing step) requested before the
+// products. Same sums in the same order, so the same values as the generic kernel.
+template <int MB>
+__global__ void k_restr0(const float* __restrict__ res, const float* __restrict__ P, const int* __restrict__ ch_off,
+                         const int* __restrict__ ch, int ncc, float* __restrict__ bc, const float* __restrict__ dinvc,
+                         float* __restrict__ xc, float* __restrict__ dc, const float* __restrict__ lam, int first,
+                         const int* done) {
+  pdl_start();
+  if (stop(done)) return;
+  float c1 = 0.0f, c2 = 0.0f;
+  if (first) cheb_tab(lam, 1, 0, c1, c2);
+  const int lane = threadIdx.x & 31;
+  for (int A = gwarp(); A < ncc; A += nwarps()) {
+    float dv[MB];
+    if (first && lane < MB) ld_seg<MB>(dinvc + ((size_t)A * MB + lane) * MB, dv);
+    float acc[MB];
+#pragma unroll
+    for (int j = 0; j < MB; ++j) acc[j] = 0.0f;
+    const int t1 = ch_off[A + 1];
+    for (int t = ch_off[A] + lane; t < t1; t += 64) {
+      const bool two = t + 32 < t1;
+      const int ca = ch[t], cb = two ? ch[t + 32] : ca;
+      const float ra = res[ca], rb = res[cb];
+      float Pa[MB], Pb[MB];
+      ld_seg<MB>(P + (size_t)ca * MB, Pa);
+      ld_seg<MB>(P + (size_t)cb * MB, Pb);
+#pragma unroll
+      for (int j = 0; j < MB; ++j) acc[j] = fmaf(Pa[j], ra, acc[j]);
+      if (two) {
+#pragma unroll
+        for (int j = 0; j < MB; ++j) acc[j] = fmaf(Pb[j], rb, acc[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < MB; ++j) acc[j] = warp_sum(acc[j]);
+    if (lane < MB) {
+      float bj = 0.0f;
+#pragma unroll
+      for (int j = 0; j < MB; ++j)
+        if (j == lane) bj = acc[j];
+      bc[(size_t)A * MB + lane] = bj;
+      if (first) {
+        float s = 0.0f;
+#pragma unroll
+        for (int v = 0; v < MB; ++v) s = fmaf(dv[v], acc[v], s);
+        const float dn = c2 * s;
+        dc[(size_t)A * MB + lane] = dn;
+        xc[(size_t)A * MB + lane] = dn;
+      }
+    }
+  }
+}
+
 // The small levels of one V-cycle in one launch of one thread block, out of shared memory: from the restriction of
 // level t-1's residual (W.d[t-1], global) to the prolongation into level t-1 (W.x[t-1][cur_prev], global), the
 // smoothing, residuals and transfers of levels t .. C-1 and the coarsest solve run as phases separated by
@@ -1264,6 +1432,35 @@ void launchk(cudaStream_t st, int grid, int block, size_t smem, void (*k)(KArgs.
 }
 
 inline int warps_grid(long warps) { return blocks_for(warps * 32, 65535); }
+// blocks of the row-parallel block-level kernels: one per group of 32 cells
+inline int row_grid(int nc) { return (int)std::min<long>((nc + 31) / 32, 1 << 20); }
+
+// One Chebyshev step k, and the residual, of block level l: row-parallel from W.row_cells cells up, else one warp per
+// cell.
+void cheb_level(cudaStream_t st, const MgDev& M, const MgWork& W, int l, int k, int cur, const int* flag) {
+  if (M.nc[l] >= W.row_cells) {
+    MG_MB_SWITCH(M.mb[l], launchk(st, row_grid(M.nc[l]), 32 * MB, 0, k_chebr<MB>, M.nc[l], (const int*)M.rowptr[l],
+                                  (const int*)M.col[l], (const float*)W.aval[l], (const float*)W.dinv[l],
+                                  (const float*)W.b[l], (const float*)W.x[l][cur], W.x[l][1 - cur], W.d[l],
+                                  (const float*)W.coef, l, k, flag));
+  } else {
+    MG_MB_SWITCH(M.mb[l], launchk(st, warps_grid(M.nc[l]), kT, 0, k_chebl<MB>, M.nc[l], (const int*)M.rowptr[l],
+                                  (const int*)M.col[l], (const float*)W.aval[l], (const float*)W.dinv[l],
+                                  (const float*)W.b[l], (const float*)W.x[l][cur], W.x[l][1 - cur], W.d[l],
+                                  (const float*)W.coef, l, k, flag));
+  }
+}
+void res_level(cudaStream_t st, const MgDev& M, const MgWork& W, int l, int cur, const int* flag) {
+  if (M.nc[l] >= W.row_cells) {
+    MG_MB_SWITCH(M.mb[l], launchk(st, row_grid(M.nc[l]), 32 * MB, 0, k_resr<MB>, M.nc[l], (const int*)M.rowptr[l],
+                                  (const int*)M.col[l], (const float*)W.aval[l], (const float*)W.b[l],
+                                  (const float*)W.x[l][cur], W.d[l], flag));
+  } else {
+    MG_MB_SWITCH(M.mb[l], launchk(st, warps_grid(M.nc[l]), kT, 0, k_resl<MB>, M.nc[l], (const int*)M.rowptr[l],
+                                  (const int*)M.col[l], (const float*)W.aval[l], (const float*)W.b[l],
+                                  (const float*)W.x[l][cur], W.d[l], flag));
+  }
+}
 
 }  // namespace
 
@@ -1446,21 +1643,16 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
             (const __nv_bfloat16*)M.Pb[0], (const int*)M.ch_off[0], (const int*)M.ch[0], M.nc[1], M.mb[1], W.b[1],
             (const float*)W.dinv[1], W.x[1][0], W.d[1], (const float*)W.coef, 1, C > 1 ? 1 : 0, flag);
   else
-    launchk(st, warps_grid(M.nc[1]), kT, 0, k_restr<float>, 1, (const float*)W.d[0], (const float*)M.P[0],
-            (const int*)M.ch_off[0], (const int*)M.ch[0], M.nc[1], M.mb[1], W.b[1], (const float*)W.dinv[1],
-            W.x[1][0], W.d[1], (const float*)W.coef, 1, C > 1 ? 1 : 0, flag);
+    MG_MB_SWITCH(M.mb[1], launchk(st, warps_grid(M.nc[1]), kT, 0, k_restr0<MB>, (const float*)W.d[0],
+                                  (const float*)M.P[0], (const int*)M.ch_off[0], (const int*)M.ch[0], M.nc[1], W.b[1],
+                                  (const float*)W.dinv[1], W.x[1][0], W.d[1], (const float*)W.coef, C > 1 ? 1 : 0,
+                                  flag));
   for (int l = 1; l < C && l <= top; ++l) {
-    const int gl = warps_grid(M.nc[l]);
     for (int k = 1; k < kMgDegCoarse; ++k) {
-      MG_MB_SWITCH(M.mb[l], launchk(st, gl, kT, 0, k_chebl<MB>, M.nc[l], (const int*)M.rowptr[l],
-                                    (const int*)M.col[l], (const float*)W.aval[l], (const float*)W.dinv[l],
-                                    (const float*)W.b[l], (const float*)W.x[l][cur[l]], W.x[l][1 - cur[l]], W.d[l],
-                                    (const float*)W.coef, l, k, flag));
+      cheb_level(st, M, W, l, k, cur[l], flag);
       cur[l] ^= 1;
     }
-    MG_MB_SWITCH(M.mb[l], launchk(st, gl, kT, 0, k_resl<MB>, M.nc[l], (const int*)M.rowptr[l],
-                                  (const int*)M.col[l], (const float*)W.aval[l], (const float*)W.b[l],
-                                  (const float*)W.x[l][cur[l]], W.d[l], flag));
+    res_level(st, M, W, l, cur[l], flag);
     if (l == top) break;   // the tail restricts from here
     if (W.bf16)
       launchk(st, warps_grid(M.nc[l + 1]), kT, 0, k_restr<__nv_bfloat16>, M.mb[l], (const float*)W.d[l],
@@ -1494,12 +1686,8 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
                 (const float*)M.P[l], (const int*)M.agg[l], (const float*)W.x[l + 1][cur[l + 1]], W.x[l][cur[l]],
                 flag);
     }
-    const int gl = warps_grid(M.nc[l]);
     for (int k = 0; k < kMgDegCoarse; ++k) {
-      MG_MB_SWITCH(M.mb[l], launchk(st, gl, kT, 0, k_chebl<MB>, M.nc[l], (const int*)M.rowptr[l],
-                                    (const int*)M.col[l], (const float*)W.aval[l], (const float*)W.dinv[l],
-                                    (const float*)W.b[l], (const float*)W.x[l][cur[l]], W.x[l][1 - cur[l]], W.d[l],
-                                    (const float*)W.coef, l, k, flag));
+      cheb_level(st, M, W, l, k, cur[l], flag);
       cur[l] ^= 1;
     }
   }

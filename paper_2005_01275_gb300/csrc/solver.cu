@@ -1214,12 +1214,13 @@ void alloc_mg(nlmg_ctx* c) {
   mg_set_smem_limits();
 }
 
-// Transfers of the preconditioner in BF16 (lin_precision = 2) or FP32; graphs captured with the other type are
-// dropped and captured again.
+// Transfers of the preconditioner in BF16 (lin_precision = 2) or FP32, and the level size from which the block levels
+// run row-parallel (mg_row_cells); graphs captured with other choices are dropped and captured again.
 void mg_select_precision(nlmg_ctx* c) {
   MgWork& W = c->mg;
   W.bf16 = c->opt.lin_precision == 2 ? 1 : 0;
-  if (W.graphs_bf16 != -1 && W.graphs_bf16 != W.bf16) {
+  W.row_cells = c->opt.mg_row_cells;
+  if ((W.graphs_bf16 != -1 && W.graphs_bf16 != W.bf16) || (W.graphs_row_cells != -1 && W.graphs_row_cells != W.row_cells)) {
     for (cudaGraphExec_t* g : {&W.g_pcg[0], &W.g_pcg[1], &W.g_bicg[0], &W.g_bicg[1], &W.g_apply})
       if (*g) {
         CK(cudaGraphExecDestroy(*g));
@@ -1227,6 +1228,7 @@ void mg_select_precision(nlmg_ctx* c) {
       }
   }
   W.graphs_bf16 = W.bf16;
+  W.graphs_row_cells = W.row_cells;
 }
 
 // Reads the scalars of the last multigrid Krylov solve; throws on a non-finite value.
@@ -1471,6 +1473,7 @@ void nlmg_default_options(nlmg_options* o) {
   o->setup_threads = 0;
   o->newton_switch = 1e-3;
   o->newton_lin_tol = 1e-2;
+  o->mg_row_cells = 16384;
 }
 
 static thread_local std::string g_setup_error;   // message of the calling thread's last failed setup
@@ -1480,7 +1483,7 @@ static bool solver_options_ok(const nlmg_options& o) {
   return (o.lin_precond == 0 || o.lin_precond == 1) && o.nu_pre >= 0 && o.nu_post >= 0 && o.bt_nmax >= 0 && o.omega > 0 && o.coarsest_steps >= 0 &&
          (o.lin_precision == 0 || o.lin_precision == 1 || o.lin_precision == 2) && o.max_sms >= 0 && o.smoother >= NLMG_SMOOTH_PICARD &&
          o.smoother <= NLMG_SMOOTH_PICARD_NEWTON && o.newton_switch >= 0.0 && o.newton_lin_tol > 0.0 &&
-         (o.cascadic == 0 || o.cascadic == 1);
+         (o.cascadic == 0 || o.cascadic == 1) && o.mg_row_cells >= 0;
 }
 
 static nlmg_status setup_impl(const nlmg_mesh* mesh, const nlmg_kappa* kappa, const nlmg_options* opt,

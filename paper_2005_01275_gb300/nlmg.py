@@ -41,7 +41,8 @@ class Options(C.Structure):
                 ("coarse_lin_tol", C.c_double), ("lin_precision", C.c_int32),
                 ("setup_threads", C.c_int32), ("max_sms", C.c_int32), ("newton_switch", C.c_double),
                 ("newton_lin_tol", C.c_double), ("coarsest_lin_tol", C.c_double), ("flux_modes", C.c_int32 * 8),
-                ("cascadic", C.c_int32), ("lin_precond", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("cascadic", C.c_int32), ("lin_precond", C.c_int32), ("mg_row_cells", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class Report(C.Structure):
@@ -175,7 +176,7 @@ def options_from_dict(d):
     keep = {k: d[k] for k in ("n_levels", "agg_size", "modes", "nu_pre", "nu_post", "omega", "bt_nmax", "bt_theta",
                               "dp_clamp", "coarsest_steps", "coarsest_tol", "lin_tol", "lin_maxit", "coarse_lin_tol",
                               "lin_precision", "max_sms", "newton_switch", "newton_lin_tol", "coarsest_lin_tol",
-                              "setup_threads", "flux_modes", "cascadic", "lin_precond") if k in d}
+                              "setup_threads", "flux_modes", "cascadic", "lin_precond", "mg_row_cells") if k in d}
     if "lin_tol" in d and "coarse_lin_tol" not in d:
         keep["coarse_lin_tol"] = d["lin_tol"]       # one tolerance given: use it on every level
     if "lin_tol" in d and "newton_lin_tol" not in d:

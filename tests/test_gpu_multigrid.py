@@ -67,6 +67,38 @@ def test_preconditioned_cg_update(nlmg_lib, name, scale, upd):
         assert abs(it - it_ref) <= 1 + it_ref // 10, (name, tol, it, it_ref)
 
 
+@pytest.mark.parametrize("name,scale,upd", CASES, ids=[c[0] for c in CASES])
+def test_row_parallel_block_levels(nlmg_lib, name, scale, upd):
+    """mg_row_cells = 0: every block level outside the shared-memory tail runs the row-parallel smoothing and
+    residual kernels (one thread per cell component). One application still equals the oracle's cycle, and the
+    warp-per-cell form to FP32 rounding (only the order of the sums differs); the preconditioned CG update still
+    meets its tolerance on the oracle's matrix, and a FAS solve reaches p*."""
+    pr, ctx = _case(nlmg_lib, name, scale, **upd)
+    rng = np.random.default_rng(65)
+    p = rng.uniform(0, 1, pr.mesh.n_cells)
+    A = newton.picard_matrix(pr.mesh, pr.kappa_kind, pr.kappa_a, p).tocsr()
+    H, lv = _oracle_levels(pr, A)
+    r = rng.uniform(-1, 1, pr.mesh.n_cells)
+    z_warp = ctx.precond_apply(p, r)
+    ctx.set_options(mg_row_cells=0)
+    z_row = ctx.precond_apply(p, r)
+    ref = precond.vcycle(lv, H, r)
+    assert np.linalg.norm(z_row - ref) <= 2e-4 * np.linalg.norm(ref), name
+    assert np.linalg.norm(z_row - z_warp) <= 1e-5 * np.linalg.norm(z_warp), name
+    if name == "chan3d_64":   # level 1 (64 cells) runs its own kernels here: the other form really ran
+        assert not np.array_equal(z_row, z_warp)
+    R = tpfa.reduced_residual(pr.mesh, pr.kappa_kind, pr.kappa_a, p, pr.f_cell, pr.g_face)
+    S = 1.0 / np.sqrt(A.diagonal())
+    ctx.set_options(mg_row_cells=0, lin_tol=1e-8, lin_maxit=500)
+    dx, it = ctx.picard_update(0, p)
+    assert np.linalg.norm(S * (A @ dx + R)) <= 1e-8 * (1 + 1e-6) * np.linalg.norm(S * R), name
+    ctx.set_options(mg_row_cells=0, smoother="picard_newton")
+    pstar, _ = newton.solve(pr.mesh, pr.kappa_kind, pr.kappa_a, pr.f_cell, pr.g_face, dp_clamp=pr.opts["dp_clamp"])
+    ps, rep, st = ctx.solve(pr.f_cell, pr.g_face, tol_rel=1e-12, tol_abs=1e-300, max_cycles=80)
+    assert st == 0, (name, rep)
+    assert np.linalg.norm(ps - pstar) <= 1e-10 * np.linalg.norm(pstar), name
+
+
 def test_preconditioned_bicgstab_newton_update(nlmg_lib):
     pr, ctx = _case(nlmg_lib, "chan3d_64", 16, n_levels=3, agg_size=[64, 8, 8], modes=[4, 4, 4])
     # an iterate of the kind a solve meets (at random pressures the Jacobian is far from an M-matrix)
