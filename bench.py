@@ -203,8 +203,8 @@ def cpu_baseline_dict(full_cells, smoother):
                          "cycles": m["cycles"], "threads_busy": m["threads"]}}
 
 
-def serving_requests(n, seed=4):
-    """Requests shaped like the serving workload: sizes log-uniform in [4096, 65536] cells, 2D or 3D by a fair coin,
+def serving_requests(n, seed=4, lo=4096, hi=262144):
+    """Requests shaped like the serving workload: sizes log-uniform in [lo, hi] cells, 2D or 3D by a fair coin,
     each with its own log-normal K (sigma 1, correlation 4 cells), Dirichlet data g_L ~ U[0.5, 1.5],
     g_R ~ U[-0.5, 0.5], kappa = exp(a p) with a ~ U[0.5, 2]."""
     import numpy as np
@@ -212,7 +212,7 @@ def serving_requests(n, seed=4):
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
-        cells = float(np.exp(rng.uniform(np.log(4096), np.log(65536))))
+        cells = float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
         if rng.uniform() < 0.5:
             side = int(round(cells ** 0.5))
             shape = (side, side)
@@ -263,14 +263,18 @@ def _serve(nlmg, reqs, arrivals=None, hierarchy_cache=8):
             "hierarchies_reused": int(reused)}
 
 
-def run_serving(nlmg, n, smoother):
+def run_serving(nlmg, n, smoother, n_seq=48, n_reuse=24):
     """The request loop (FP32 inner CG in the FP64 FAS, up to 8 requests in flight): a burst of n requests of their
-    own meshes, then the same requests arriving as a Poisson stream at 0.8 of the burst's throughput, then n
-    requests on one mesh and K with their own nonlinearity parameter and data (hierarchy reuse). Against: the same
-    requests one at a time on a plain FP64 context each, setup included and excluded."""
+    own meshes (sizes log-uniform in 4k-256k cells), then the same requests arriving as a Poisson stream at 0.8 of
+    the burst's throughput, then n_reuse requests on one mesh and K with their own nonlinearity parameter and data
+    (hierarchy reuse). Against: the first n_seq requests one at a time on a plain FP64 context each, setup included
+    and excluded (a sample: the whole stream one by one would take minutes)."""
     import numpy as np
     from synth.grids import cartesian_mesh, lognormal_field, default_options, multi_rhs_rows
-    reqs = [(m, a, dict(o, lin_precision=1, smoother=smoother), f, g) for m, a, o, f, g in serving_requests(n)]
+    t0 = time.perf_counter()
+    gen = serving_requests(n)
+    reqs = [(m, a, dict(o, lin_precision=1, smoother=smoother), f, g) for m, a, o, f, g in gen]
+    gen_s = time.perf_counter() - t0
     burst = _serve(nlmg, reqs)
     rng = np.random.default_rng(7)
     rate = 0.8 * burst["solves_per_s"]
@@ -278,7 +282,8 @@ def run_serving(nlmg, n, smoother):
     poisson = _serve(nlmg, reqs, arrivals=arrivals)
     poisson["arrival_rate_per_s"] = rate
     seq_solve_ms, seq_total_s = 0.0, 0.0
-    for m, a, o, f, g in serving_requests(n):
+    n_seq = min(n_seq, n)
+    for m, a, o, f, g in gen[:n_seq]:
         t1 = time.perf_counter()
         ctx = nlmg.Context(m, 0, a, dict(o, smoother=smoother))
         _, rep, st = ctx.solve(f, g, max_cycles=60)
@@ -288,19 +293,27 @@ def run_serving(nlmg, n, smoother):
     # one reservoir: a 40^3 mesh and K, per request its own kappa = exp(a p), clamp and data
     side = 40
     mesh = cartesian_mesh((side,) * 3, lognormal_field((side,) * 3, 1.0, 4.0, seed=11))
-    F, G = multi_rhs_rows(mesh, n, seed=12)
-    alphas = rng.uniform(0.5, 2.0, n)
+    F, G = multi_rhs_rows(mesh, n_reuse, seed=12)
+    alphas = rng.uniform(0.5, 2.0, n_reuse)
     base = default_options(n_levels=3, agg_size=[64, 8], modes=[4, 4], lin_precision=1, smoother=smoother)
     shared = [(mesh, float(a), dict(base, dp_clamp=float(np.log(1.5) / a)), F[i], G[i]) for i, a in enumerate(alphas)]
     reuse = _serve(nlmg, shared)
     no_reuse = _serve(nlmg, shared, hierarchy_cache=0)
-    return {"requests": n, "sizes_cells": [int(r[0].n_cells) for r in reqs], "burst": burst, "poisson": poisson,
-            "sequential_fp64_solves_per_s_incl_setup": n / seq_total_s,
-            "sequential_fp64_solves_per_s_excl_setup": n / (seq_solve_ms / 1e3),
+    sizes = np.array([r[0].n_cells for r in reqs])
+    return {"requests": n, "sizes_cells": {"min": int(sizes.min()), "median": int(np.median(sizes)),
+                                           "mean": int(sizes.mean()), "max": int(sizes.max()),
+                                           "three_d": int(sum(len(r[0].shape) == 3 for r in reqs))},
+            "generate_s": gen_s, "burst": burst, "poisson": poisson,
+            "sequential_fp64_sample": {
+                "requests": n_seq, "mean_cells": int(sizes[:n_seq].mean()),
+                "solves_per_s_incl_setup": n_seq / seq_total_s,
+                "solves_per_s_excl_setup": n_seq / (seq_solve_ms / 1e3),
+                "what": "the first requests of the stream one after the other, each on its own plain FP64 context"},
             "one_mesh_with_hierarchy_reuse": reuse, "one_mesh_without_reuse": no_reuse,
-            "what": "each request its own mesh and hierarchy (sizes log-uniform 4k-65k cells, 2D/3D) unless noted; "
-                    "latency = submit -> result; FP32 CG inside the FP64 FAS; max 8 in flight; level-0 "
-                    "smoother: " + smoother}
+            "one_mesh_requests": n_reuse,
+            "what": "each request its own mesh and hierarchy (sizes log-uniform 4k-256k cells, 2D/3D) unless noted; "
+                    "latency = submit -> result; FP32 CG inside the FP64 FAS; max 8 in flight, admission by the "
+                    "estimated device bytes against a 32 GiB budget; level-0 smoother: " + smoother}
 
 
 def run_baselines(nlmg, pr, ctx):
@@ -549,8 +562,8 @@ def run_batched(nlmg, pr, args, world, dist, dev, flush, local_rank):
 def run_cfg5(nlmg, args, fp64_peak, hbm_peak, hbm_kind):
     """The 256^3 channelized workload (16.8M cells, 8 decades, 5 levels of 64- then 8-cell aggregates, 6 modes):
     plain FP64 (one context, Jacobi-preconditioned persistent Krylov kernels, one row) against the batched mixed form
-    (args.cfg5 rows of synth.grids.multi_rhs_rows on two contexts, FP32 multigrid V-cycle inside FP64 Krylov
-    iterations), device-resident rows. Every row's relative residual is recomputed in FP64 by the library's residual
+    (args.cfg5 rows of synth.grids.multi_rhs_rows on two contexts, FP32 multigrid V-cycle with BF16 transfers inside
+    FP64 Krylov iterations), device-resident rows. Every row's relative residual is recomputed in FP64 by the library's residual
     call; the mixed row 0 is compared with the FP64 one."""
     import numpy as np
     import torch
@@ -579,8 +592,8 @@ def run_cfg5(nlmg, args, fp64_peak, hbm_peak, hbm_kind):
         out["plain_fp64"] = {"solves_per_s": 1e3 / rep["solve_ms"], "ms": rep["solve_ms"], "cycles": rep["cycles"],
                              "status": int(st), "rel_residual": rep["res"] / rep["res0"],
                              "lin_iters_level": rep["lin_iters_level"][:5]}
-        # batched mixed
-        ctx.set_options(lin_precond=1)
+        # batched mixed: FP32 V-cycle with BF16 transfers (FP32 accumulation) inside FP64 Krylov iterations
+        ctx.set_options(lin_precond=1, lin_precision=2)
         ctx.profile(True)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -755,13 +768,27 @@ def run_gpu(args, rank, world, local_rank):
                  "what": "same FP64 FAS (residuals, transfers, coarse operators, convergence test in FP64); the CG "
                          "solves inside the Picard steps in FP32 (tolerances floored at 1e-6); the Newton steps' "
                          "BiCGStab stays FP64"}
-    baselines = run_baselines(nlmg, pr, ctx) if (args.baselines and world == 1) else None
-    multi = run_multi_rhs(nlmg, pr, ctx, args.multi_rhs, args.streams) if (args.multi_rhs > 0 and world == 1) \
+    walls = {}
+
+    def timed(name, fn):
+        t1 = time.perf_counter()
+        r = fn()
+        walls[name] = round(time.perf_counter() - t1, 1)
+        return r
+
+    baselines = timed("single_level_baselines", lambda: run_baselines(nlmg, pr, ctx)) \
+        if (args.baselines and world == 1) else None
+    multi = timed("multi_rhs", lambda: run_multi_rhs(nlmg, pr, ctx, args.multi_rhs, args.streams)) \
+        if (args.multi_rhs > 0 and world == 1) else None
+    serving = timed("serving", lambda: run_serving(nlmg, args.serving, args.smoother)) \
+        if (args.serving > 0 and world == 1) else None
+    voronoi = timed("voronoi", lambda: run_voronoi(nlmg, args.voronoi, max(1, min(5, args.steps // 2)), args.smoother,
+                                                   fp64_peak_gflops, peak, peak_kind)) \
+        if (args.voronoi > 0 and world == 1) else None
+    cpu = timed("cpu_baseline", lambda: cpu_baseline_dict(N, args.smoother)) if (args.cpu_baseline and world == 1) \
         else None
-    serving = run_serving(nlmg, args.serving, args.smoother) if (args.serving > 0 and world == 1) else None
-    voronoi = run_voronoi(nlmg, args.voronoi, max(1, min(5, args.steps // 2)), args.smoother, fp64_peak_gflops,
-                          peak, peak_kind) if (args.voronoi > 0 and world == 1) else None
-    cpu = cpu_baseline_dict(N, args.smoother) if (args.cpu_baseline and world == 1) else None
+    cfg5 = timed("cfg5", lambda: run_cfg5(nlmg, args, fp64_peak_gflops, peak, peak_kind)) \
+        if (args.cfg5 > 0 and world == 1) else None
     head_roof = roofline(head["prof"], head["prof_dev_ms"], fp64_peak_gflops, peak, peak_kind, False)
     head_roof["measured_on"] = ("the batch's first context (it solves its share of the rows on its own stream, "
                                 "side by side with the other contexts); share_of_solve relative to its rows")
@@ -806,7 +833,8 @@ def run_gpu(args, rank, world, local_rank):
         "serving": serving,
         "voronoi": voronoi,
         "cpu_baseline": cpu,
-        "cfg5": run_cfg5(nlmg, args, fp64_peak_gflops, peak, peak_kind) if (args.cfg5 > 0 and world == 1) else None,
+        "cfg5": cfg5,
+        "section_wall_s": walls,
         "e2e": head["e2e"],
         "gpu_launches": head["gpu_launches"],
         "clocks": head["clocks"],
@@ -828,7 +856,7 @@ def main():
     ap.add_argument("--lin-tol", type=float, default=None, help="level-0 CG tolerance (default: library's)")
     ap.add_argument("--coarse-lin-tol", type=float, default=None, help="coarse CG tolerance")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false", help="skip the FP32-CG variant")
-    ap.add_argument("--serving", type=int, default=24, help="requests in the serving run (0 = skip)")
+    ap.add_argument("--serving", type=int, default=512, help="requests in the serving run (0 = skip)")
     ap.add_argument("--multi-rhs", type=int, default=16, help="right-hand sides in the multi-RHS run (0 = skip)")
     ap.add_argument("--streams", type=int, default=8, help="contexts (streams) of the multi-RHS solve")
     ap.add_argument("--smoother", default="picard_newton", choices=["picard", "picard_newton"],

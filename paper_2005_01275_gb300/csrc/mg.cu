@@ -746,6 +746,22 @@ __device__ __forceinline__ void ld_seg(const float* p, float (&v)[MB]) {
   }
 }
 
+// MB consecutive BF16 transfer entries from p, widened to float: 4-byte pair loads when MB is even.
+template <int MB>
+__device__ __forceinline__ void ld_seg(const __nv_bfloat16* p, float (&v)[MB]) {
+  if constexpr (MB % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < MB / 2; ++k) {
+      const float2 t = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(p)[k]);
+      v[2 * k] = t.x;
+      v[2 * k + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < MB; ++k) v[k] = __bfloat162float(p[k]);
+  }
+}
+
 // Row-parallel forms of the block-level smoothing step and residual (the per-level kernels of the V-cycle; the
 // shared-memory tail keeps the warp-per-cell bodies above): one thread per cell component, cell c = 32 g + t / MB and
 // component u = t % MB for thread t of a block of 32 MB threads, so a block holds whole cells; blocks take groups g
@@ -832,12 +848,12 @@ __global__ void __launch_bounds__(32 * MB) k_resr(int nc, const int* __restrict_
   }
 }
 
-// Level-0 restriction with float transfers and MB modes per aggregate: restr_body's work split and order (one warp
-// per aggregate, a lane per child, children t and t + 32 together), with the child's MB transfer entries read by
-// vector loads and the aggregate's block-inverse row (for the fused first smoothing step) requested before the
+// Level-0 restriction with MB modes per aggregate (FP32 or BF16 transfers): restr_body's work split and order (one
+// warp per aggregate, a lane per child, children t and t + 32 together), with the child's MB transfer entries read
+// by vector loads and the aggregate's block-inverse row (for the fused first smoothing step) requested before the
 // products. Same sums in the same order, so the same values as the generic kernel.
-template <int MB>
-__global__ void k_restr0(const float* __restrict__ res, const float* __restrict__ P, const int* __restrict__ ch_off,
+template <class PT, int MB>
+__global__ void k_restr0(const float* __restrict__ res, const PT* __restrict__ P, const int* __restrict__ ch_off,
                          const int* __restrict__ ch, int ncc, float* __restrict__ bc, const float* __restrict__ dinvc,
                          float* __restrict__ xc, float* __restrict__ dc, const float* __restrict__ lam, int first,
                          const int* done) {
@@ -1628,7 +1644,7 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
   const int tl = mg_tail_level(M);
   const int top = tl > 0 ? tl - 1 : C;   // levels 1 .. top-1 restrict with their own kernels
   int cur[kMgMaxLevels] = {0};
-  const int g0 = blocks_for(M.N, 4096);
+  const int g0 = blocks_for(M.N, W.grid0);
   // down: level-0 smoothing, residual into d[0] (dead until the post-smoothing rewrites it), restriction
   for (int k = 1; k < kMgDegFine; ++k) {
     launchk(st, g0, kT, 0, k_cheb0, F, (const float*)W.a0off, (const float*)W.a0diag, (const float*)W.a0dinv,
@@ -1638,15 +1654,17 @@ int mg_enqueue_vcycle(cudaStream_t st, const MgDev& M, const FineDev& F, const M
   }
   launchk(st, g0, kT, 0, k_res0, F, (const float*)W.a0off, (const float*)W.a0diag, (const float*)W.b[0],
           (const float*)W.x[0][cur[0]], W.d[0], flag);
-  if (W.bf16)
-    launchk(st, warps_grid(M.nc[1]), kT, 0, k_restr<__nv_bfloat16>, 1, (const float*)W.d[0],
-            (const __nv_bfloat16*)M.Pb[0], (const int*)M.ch_off[0], (const int*)M.ch[0], M.nc[1], M.mb[1], W.b[1],
-            (const float*)W.dinv[1], W.x[1][0], W.d[1], (const float*)W.coef, 1, C > 1 ? 1 : 0, flag);
-  else
-    MG_MB_SWITCH(M.mb[1], launchk(st, warps_grid(M.nc[1]), kT, 0, k_restr0<MB>, (const float*)W.d[0],
+  if (W.bf16) {
+    MG_MB_SWITCH(M.mb[1], launchk(st, warps_grid(M.nc[1]), kT, 0, k_restr0<__nv_bfloat16, MB>, (const float*)W.d[0],
+                                  (const __nv_bfloat16*)M.Pb[0], (const int*)M.ch_off[0], (const int*)M.ch[0], M.nc[1],
+                                  W.b[1], (const float*)W.dinv[1], W.x[1][0], W.d[1], (const float*)W.coef,
+                                  C > 1 ? 1 : 0, flag));
+  } else {
+    MG_MB_SWITCH(M.mb[1], launchk(st, warps_grid(M.nc[1]), kT, 0, k_restr0<float, MB>, (const float*)W.d[0],
                                   (const float*)M.P[0], (const int*)M.ch_off[0], (const int*)M.ch[0], M.nc[1], W.b[1],
                                   (const float*)W.dinv[1], W.x[1][0], W.d[1], (const float*)W.coef, C > 1 ? 1 : 0,
                                   flag));
+  }
   for (int l = 1; l < C && l <= top; ++l) {
     for (int k = 1; k < kMgDegCoarse; ++k) {
       cheb_level(st, M, W, l, k, cur[l], flag);
@@ -1823,7 +1841,7 @@ cudaError_t mg_capture_bicgstab(cudaStream_t st, const MgDev& M, const FineDev& 
 // One V-cycle z = B b for parity tests: b = W.kb (FP64) -> W.kx (FP64).
 cudaError_t mg_capture_apply(cudaStream_t st, const MgDev& M, const FineDev& F, MgWork& W, cudaGraphExec_t* out) {
   return capture_plain(st, [&]() {
-    const int g0 = blocks_for(M.N, 4096);
+    const int g0 = blocks_for(M.N, W.grid0);
     launchk(st, g0, kT, 0, k_apply_in, M.N, (const double*)W.kb, W.b[0], (const float*)W.a0dinv, W.x[0][0], W.d[0],
             (const float*)W.coef);
     const int zi = mg_enqueue_vcycle(st, M, F, W, nullptr, false);

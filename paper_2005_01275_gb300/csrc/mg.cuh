@@ -101,6 +101,7 @@ struct MgWork {
   size_t tail_smem = 0;        // its dynamic shared memory
   int bf16 = 0;            // transfers in BF16 (FP32 accumulation) in the setup and V-cycle enqueued next
   int graphs_bf16 = -1;    // the transfer type the captured graphs use (-1: none captured)
+  int grid0 = 4096;        // blocks of the level-0 streaming kernels: one full wave, SMs x 8 blocks of 256 threads
   int row_cells = 16384;   // block levels with at least this many cells run the row-parallel kernels
   int graphs_row_cells = -1;   // the row_cells the captured graphs use (-1: none captured)
 };

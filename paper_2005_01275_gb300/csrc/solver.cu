@@ -1183,6 +1183,12 @@ void alloc_mg(nlmg_ctx* c) {
   if (M.L == 0) return;
   MgWork& W = c->mg;
   const int N = c->F.N;
+  {
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    W.grid0 = std::max(1, sms) * 8;   // the level-0 kernels use at most 32 registers: 8 blocks of 256 per SM
+  }
   W.a0off = c->dalloc<float>(c->F.nnz);
   W.a0diag = c->dalloc<float>(N);
   W.a0dinv = c->dalloc<float>(N);
