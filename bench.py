@@ -330,8 +330,24 @@ def run_baselines(nlmg, pr, ctx):
                          "lin_iters": rep["lin_iters"], "cap": cap}
         except nlmg.NlmgError as e:
             out[name] = {"status": "error", "what": str(e)[:160], "cap": cap}
+    # single-level Picard and FAS with the same multigrid-preconditioned level-0 CG (the paper's single-level solvers
+    # use AMG-preconditioned Krylov methods): one context set up with lin_precond = 1, one timed solve after a warm-up
+    try:
+        mctx = nlmg.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, dict(pr.opts, lin_precond=1))
+        for name, kw, cap in (("picard_mg", dict(picard_only=True), 400), ("fas_mg", {}, 60)):
+            mctx.solve(pr.f_cell, pr.g_face, max_cycles=cap, allow_noconv=True, **kw)
+            _, rep, st = mctx.solve(pr.f_cell, pr.g_face, max_cycles=cap, allow_noconv=True, **kw)
+            out[name] = {"status": nlmg.STATUS_NAMES.get(int(st), str(st)), "iterations": rep["cycles"],
+                         "ms": rep["solve_ms"], "solves_per_s": 1e3 / rep["solve_ms"] if rep["solve_ms"] else None,
+                         "rel_residual": rep["res"] / rep["res0"] if rep["res0"] else None,
+                         "lin_iters": rep["lin_iters"], "cap": cap}
+        mctx.close()
+    except nlmg.NlmgError as e:
+        out["picard_mg"] = {"status": "error", "what": str(e)[:160]}
     out["what"] = ("single-level solvers from p = 0 on the same workload and GPU (the FAS line is the bench value); "
-                   "a Newton iteration from p = 0 is outside its region of fast convergence on this channelized case")
+                   "a Newton iteration from p = 0 is outside its region of fast convergence on this channelized case; "
+                   "picard_mg and fas_mg: single-level Picard and FAS, both with the multigrid-preconditioned level-0 "
+                   "CG (lin_precond = 1)")
     return out
 
 
@@ -627,6 +643,46 @@ def run_cfg5(nlmg, args, fp64_peak, hbm_peak, hbm_kind):
     return out
 
 
+def run_vcycle_probe(side):
+    """The multigrid preconditioner alone on the channelized generator of the 256^3 workload at side^3 (5 levels,
+    6 modes): three applications of one V-cycle (the kernels a launch list captures), then the time of one iteration of
+    the preconditioned level-0 CG (CUDA events: the slope between 2 and 22 iterations at a fixed frozen matrix). One
+    JSON line."""
+    import numpy as np
+    from paper_2005_01275_gb300 import build, nlmg
+    from synth.grids import problem_config
+    build.build()
+    t0 = time.perf_counter()
+    pr = problem_config("chan3d_256", scale=side)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctx = nlmg.Context(pr.mesh, pr.kappa_kind, pr.kappa_a, dict(pr.opts, lin_precond=1))
+    setup_s = time.perf_counter() - t0
+    ctx.set_data(pr.f_cell, pr.g_face)
+    rng = np.random.default_rng(1)
+    p = rng.uniform(0, 1, pr.mesh.n_cells)
+    for _ in range(3):
+        z = ctx.precond_apply(p, rng.uniform(-1, 1, pr.mesh.n_cells))
+    per = {}
+    for k in (2, 22):
+        ctx.set_options(lin_tol=1e-30, lin_maxit=k)
+        ctx.picard_update(0, p)
+        ctx.profile(True)
+        for _ in range(3):
+            ctx.picard_update(0, p)
+        n, ms, by, fl = ctx.profile_read(5)
+        ctx.profile(False)
+        per[k] = (ms / n, by / n)
+    us = (per[22][0] - per[2][0]) / 20 * 1e3
+    byt = (per[22][1] - per[2][1]) / 20
+    print(json.dumps({"vcycle_probe": {"side": side, "cells": int(pr.mesh.n_cells), "generate_s": gen_s,
+                                       "setup_s": setup_s, "levels": [ctx.level_info(l) for l in range(ctx.n_levels())],
+                                       "us_per_cg_iteration": us, "bytes_per_cg_iteration": byt,
+                                       "GBs": byt / (us / 1e6) / 1e9, "z_norm": float(np.linalg.norm(z))}}))
+    ctx.close()
+    return 0
+
+
 def run_gpu(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -875,7 +931,12 @@ def main():
                     help="rows of the 256^3 batched section (0 = skip); its plain FP64 reference is one row")
     ap.add_argument("--voronoi", type=int, default=100,
                     help="lattice side of the unstructured Voronoi section (100 = 1M cells, the default; 0 = skip)")
+    ap.add_argument("--vcycle", type=int, default=0,
+                    help="only time the multigrid-preconditioned level-0 CG on the 256^3 generator at this side "
+                         "(per iteration, and three V-cycle applications): the command the V-cycle launch lists use")
     args = ap.parse_args()
+    if args.vcycle > 0:
+        return run_vcycle_probe(args.vcycle)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if "RANK" in os.environ else 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

@@ -80,7 +80,7 @@ struct Hierarchy {
 // Deterministic greedy aggregation (the rule documented with nlmg_setup).
 std::vector<int> aggregate_graph(int n, const std::vector<int>& nb_off, const std::vector<int>& nb, int target);
 
-Level make_level0(const FineMesh& fm);
+Level make_level0(const FineMesh& fm, int threads = 1);
 // Builds levels 1.. and the transfers; returns false and sets err on failure.
 bool build_hierarchy(const FineMesh& fm, const Options& opt, Hierarchy& H, std::string& err);
 

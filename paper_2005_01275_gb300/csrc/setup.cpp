@@ -449,48 +449,74 @@ std::vector<int> aggregate_graph(int n, const std::vector<int>& nb_off, const st
   return agg;
 }
 
-Level make_level0(const FineMesh& fm) {
+Level make_level0(const FineMesh& fm, int threads) {
+  // Flux unknowns are the non-Neumann faces in face order, so appending each face's id to its owners' lists in face
+  // order leaves every cell's list sorted; the lists are laid out by counting (no per-cell containers) and the local
+  // matrices filled cell-parallel.
   Level L;
-  L.n_cells = fm.n_cells;
-  std::vector<std::vector<std::pair<int, int>>> per(fm.n_cells);
+  const int n = fm.n_cells;
+  L.n_cells = n;
+  std::vector<int> cnt(n, 0);
+  int nf = 0;
   for (int f = 0; f < fm.n_faces; ++f) {
     if (fm.bc[f] == 2) continue;
-    int j = L.n_flux++;
-    L.face_of_flux.push_back(f);
-    bool itf = fm.bc[f] == 0;
-    L.fkind.push_back(itf ? KIND_IFACE : KIND_BDRY);
-    L.fown0.push_back(fm.fk[f]);
-    L.fown1.push_back(itf ? fm.fl[f] : -1);
-    per[fm.fk[f]].push_back({j, 0});
-    if (itf) per[fm.fl[f]].push_back({j, 1});
+    ++nf;
+    cnt[fm.fk[f]]++;
+    if (fm.bc[f] == 0) cnt[fm.fl[f]]++;
   }
-  L.m.assign(fm.n_cells, 1);
-  L.p_off.resize(fm.n_cells + 1);
-  L.loc_off.assign(1, 0);
-  L.mat_off.assign(1, 0);
-  L.dmat_off.assign(1, 0);
-  for (int c = 0; c < fm.n_cells; ++c) {
-    L.p_off[c] = c;
-    auto& it = per[c];
-    std::sort(it.begin(), it.end());
-    int nl = (int)it.size();
-    for (auto& e : it) L.loc.push_back(e.first);
-    size_t mo = L.Mloc.size();
-    L.Mloc.resize(mo + (size_t)nl * nl, 0.0);
-    for (int s = 0; s < nl; ++s) {
-      int f = L.face_of_flux[it[s].first];
-      double ups = it[s].second == 0 ? fm.ups0[f] : fm.ups1[f];
-      L.Mloc[mo + (size_t)s * nl + s] = 1.0 / ups;
-      L.Dloc.push_back(it[s].second == 0 ? -1.0 : 1.0);
+  L.n_flux = nf;
+  L.face_of_flux.resize(nf);
+  L.fkind.resize(nf);
+  L.fown0.resize(nf);
+  L.fown1.resize(nf);
+  L.loc_off.assign(n + 1, 0);
+  L.mat_off.assign(n + 1, 0);
+  for (int c = 0; c < n; ++c) {
+    L.loc_off[c + 1] = L.loc_off[c] + cnt[c];
+    L.mat_off[c + 1] = L.mat_off[c] + cnt[c] * cnt[c];
+  }
+  L.dmat_off = L.loc_off;   // one pressure unknown per cell
+  L.loc.resize(L.loc_off[n]);
+  std::vector<int8_t> side(L.loc_off[n]);   // 0: the cell is the face's first owner
+  {
+    std::vector<int> fill(L.loc_off.begin(), L.loc_off.end() - 1);
+    int j = 0;
+    for (int f = 0; f < fm.n_faces; ++f) {
+      if (fm.bc[f] == 2) continue;
+      const bool itf = fm.bc[f] == 0;
+      L.face_of_flux[j] = f;
+      L.fkind[j] = itf ? KIND_IFACE : KIND_BDRY;
+      L.fown0[j] = fm.fk[f];
+      L.fown1[j] = itf ? fm.fl[f] : -1;
+      L.loc[fill[fm.fk[f]]] = j;
+      side[fill[fm.fk[f]]++] = 0;
+      if (itf) {
+        L.loc[fill[fm.fl[f]]] = j;
+        side[fill[fm.fl[f]]++] = 1;
+      }
+      ++j;
     }
-    L.loc_off.push_back((int)L.loc.size());
-    L.mat_off.push_back((int)L.Mloc.size());
-    L.dmat_off.push_back((int)L.Dloc.size());
   }
-  L.p_off[fm.n_cells] = fm.n_cells;
-  L.w.assign(fm.n_cells, 1.0);
+  L.Mloc.assign((size_t)L.mat_off[n], 0.0);
+  L.Dloc.assign((size_t)L.loc_off[n], 0.0);
+  parallel_for(n, threads, [&](int b, int e, int) {
+    for (int c = b; c < e; ++c) {
+      const int k0 = L.loc_off[c], nl = L.loc_off[c + 1] - k0;
+      const size_t mo = (size_t)L.mat_off[c];
+      for (int s = 0; s < nl; ++s) {
+        const int f = L.face_of_flux[L.loc[k0 + s]];
+        const double ups = side[k0 + s] == 0 ? fm.ups0[f] : fm.ups1[f];
+        L.Mloc[mo + (size_t)s * nl + s] = 1.0 / ups;
+        L.Dloc[k0 + s] = side[k0 + s] == 0 ? -1.0 : 1.0;
+      }
+    }
+  });
+  L.m.assign(n, 1);
+  L.p_off.resize(n + 1);
+  for (int c = 0; c <= n; ++c) L.p_off[c] = c;
+  L.w.assign(n, 1.0);
   L.vol = fm.vol;
-  L.ones.assign(fm.n_cells, 1.0);
+  L.ones.assign(n, 1.0);
   return L;
 }
 
@@ -499,17 +525,35 @@ static bool coarsen(const Level& L, int target, int modes, int flux_modes, int t
                     const EigBatchFn& eig_fn, Level& C, Transfer& T, std::string& err) {
   const int n = L.n_cells;
   // ---- cell graph ----------------------------------------------------------------------------------------------
-  std::vector<std::vector<int>> nbv(n);
-  for (int i = 0; i < L.n_flux; ++i)
-    if (L.fkind[i] == KIND_IFACE) {
-      nbv[L.fown0[i]].push_back(L.fown1[i]);
-      nbv[L.fown1[i]].push_back(L.fown0[i]);
-    }
+  // adjacency lists by counting, then each list sorted and made unique (cell-parallel) and compacted
   std::vector<int> nb_off(n + 1, 0), nb;
-  for (int v = 0; v < n; ++v) {
-    sort_unique(nbv[v]);
-    nb_off[v + 1] = nb_off[v] + (int)nbv[v].size();
-    nb.insert(nb.end(), nbv[v].begin(), nbv[v].end());
+  {
+    std::vector<int> raw_off(n + 1, 0);
+    for (int i = 0; i < L.n_flux; ++i)
+      if (L.fkind[i] == KIND_IFACE) {
+        raw_off[L.fown0[i] + 1]++;
+        raw_off[L.fown1[i] + 1]++;
+      }
+    for (int v = 0; v < n; ++v) raw_off[v + 1] += raw_off[v];
+    std::vector<int> raw(raw_off[n]), fill(raw_off.begin(), raw_off.end() - 1), len(n, 0);
+    for (int i = 0; i < L.n_flux; ++i)
+      if (L.fkind[i] == KIND_IFACE) {
+        raw[fill[L.fown0[i]]++] = L.fown1[i];
+        raw[fill[L.fown1[i]]++] = L.fown0[i];
+      }
+    parallel_for(n, threads, [&](int b, int e, int) {
+      for (int v = b; v < e; ++v) {
+        int* lo = raw.data() + raw_off[v];
+        int* hi = raw.data() + raw_off[v + 1];
+        std::sort(lo, hi);
+        len[v] = (int)(std::unique(lo, hi) - lo);
+      }
+    });
+    for (int v = 0; v < n; ++v) nb_off[v + 1] = nb_off[v] + len[v];
+    nb.resize(nb_off[n]);
+    parallel_for(n, threads, [&](int b, int e, int) {
+      for (int v = b; v < e; ++v) std::copy(raw.begin() + raw_off[v], raw.begin() + raw_off[v] + len[v], nb.begin() + nb_off[v]);
+    });
   }
   T.agg_of = aggregate_graph(n, nb_off, nb, target);
   int na = 0;
@@ -1064,21 +1108,48 @@ static bool coarsen(const Level& L, int target, int modes, int flux_modes, int t
         for (auto& x : qrow[J]) { T.Qs.col[o] = x.first; T.Qs.val[o] = x.second; ++o; }
       }
     });
-    // transpose by counting: row i of P_sigma lists its coarse columns J in ascending order
+    // transpose: row i of P_sigma lists its coarse columns J in ascending order. Counted and filled in parallel
+    // (relaxed atomic counters), then every row sorted by J: each (i, J) occurs once, so the layout does not depend on
+    // the order the threads took
     T.Ps.nrows = L.n_flux;
     T.Ps.ncols = nC;
     T.Ps.off.assign(L.n_flux + 1, 0);
-    for (int i : T.PsT.col) T.Ps.off[i + 1]++;
-    for (int i = 0; i < L.n_flux; ++i) T.Ps.off[i + 1] += T.Ps.off[i];
+    {
+      std::vector<int> cnt(L.n_flux, 0);
+      parallel_for(nC, threads, [&](int b, int e, int) {
+        for (int J = b; J < e; ++J)
+          for (int q = T.PsT.off[J]; q < T.PsT.off[J + 1]; ++q)
+            __atomic_fetch_add(&cnt[T.PsT.col[q]], 1, __ATOMIC_RELAXED);
+      });
+      for (int i = 0; i < L.n_flux; ++i) T.Ps.off[i + 1] = T.Ps.off[i] + cnt[i];
+    }
     T.Ps.col.resize(T.PsT.col.size());
     T.Ps.val.resize(T.PsT.col.size());
-    std::vector<int> fill(T.Ps.off.begin(), T.Ps.off.end() - 1);
-    for (int J = 0; J < nC; ++J)
-      for (int q = T.PsT.off[J]; q < T.PsT.off[J + 1]; ++q) {
-        int pos = fill[T.PsT.col[q]]++;
-        T.Ps.col[pos] = J;
-        T.Ps.val[pos] = T.PsT.val[q];
-      }
+    {
+      std::vector<int> fill(T.Ps.off.begin(), T.Ps.off.end() - 1);
+      parallel_for(nC, threads, [&](int b, int e, int) {
+        for (int J = b; J < e; ++J)
+          for (int q = T.PsT.off[J]; q < T.PsT.off[J + 1]; ++q) {
+            const int pos = __atomic_fetch_add(&fill[T.PsT.col[q]], 1, __ATOMIC_RELAXED);
+            T.Ps.col[pos] = J;
+            T.Ps.val[pos] = T.PsT.val[q];
+          }
+      });
+    }
+    parallel_for(L.n_flux, threads, [&](int b, int e, int) {
+      for (int i = b; i < e; ++i)   // insertion sort of the row by column (rows hold a few tens of entries)
+        for (int k = T.Ps.off[i] + 1; k < T.Ps.off[i + 1]; ++k) {
+          const int cj = T.Ps.col[k];
+          const double vj = T.Ps.val[k];
+          int t = k - 1;
+          for (; t >= T.Ps.off[i] && T.Ps.col[t] > cj; --t) {
+            T.Ps.col[t + 1] = T.Ps.col[t];
+            T.Ps.val[t + 1] = T.Ps.val[t];
+          }
+          T.Ps.col[t + 1] = cj;
+          T.Ps.val[t + 1] = vj;
+        }
+    });
   }
   // static local matrices, divergence blocks, Pi~ weights
   C.mat_off.assign(na + 1, 0);
@@ -1180,7 +1251,7 @@ bool build_hierarchy(const FineMesh& fm, const Options& opt, Hierarchy& H, std::
   int threads = opt.threads > 0 ? opt.threads : (int)std::max(1u, std::thread::hardware_concurrency());
   H.levels.clear();
   H.transfers.clear();
-  H.levels.push_back(make_level0(fm));
+  H.levels.push_back(make_level0(fm, threads));
   for (int l = 0; l + 1 < opt.n_levels; ++l) {
     Level C;
     Transfer T;
