@@ -20,7 +20,9 @@ Jacobian of the reduced TPFA residual (the reduced form of eq. jacobian_system).
 NEWTON_KEEP = 1/2 of the residual it started from shows that the iterate is outside Newton's region of fast
 convergence: the rest of the solve then takes Picard steps (the switch is not tried again).
 Every update then passes through the pressure-change clamp (Sec. 4.1: max |dp| <= dp_clamp) and Algorithm 1. Smoothing on coarse levels is one Picard
-step (Sec. 3.3.1) followed by the clamp (applied to the aggregate means Pi~ dp) and Algorithm 1.
+step (Sec. 3.3.1) followed by the clamp (applied to the aggregate means Pi~ dp) and Algorithm 1; with the option
+coarse_smoother = "newton" it is one Newton step instead (Sec. 3.3.2, Props. 2-3: the Jacobian of the coarse operator
+assembled without visiting finer levels), with the same clamp and Algorithm 1.
 Residual comparisons in Algorithm 1 use the Euclidean norm of the level residual, with a strict ">".
 """
 from __future__ import annotations
@@ -82,6 +84,7 @@ class Stats:
     early_exit: bool = False
     fine_evals: int = 0
     newton_steps: int = 0
+    coarse_newton_steps: int = 0
 
 
 class FAS:
@@ -95,6 +98,7 @@ class FAS:
         self.a_lev = level_params(H, mesh, kind, a)
         self.r0_ref = 0.0         # ||R(p_0)|| of the current solve (set by vcycle; 0: no Newton step)
         self.newton_off = False   # set once a Newton step reduced the residual by less than NEWTON_KEEP
+        self.coarse_newton_now = False   # coarse_smoother = "picard_newton": Newton on the coarse levels this cycle
 
     # ---- level 0 (reduced form) --------------------------------------------------------------------------------
     def R(self, p):
@@ -183,6 +187,32 @@ class FAS:
         xn, rn, _, _ = backtracking(nrm, x, dx, r_x, o["bt_nmax"], o["bt_theta"])
         return xn, rn
 
+    def newton_smooth(self, l, x, b, r_x=None):
+        """One coarse Newton smoothing step (Sec. 3.3.2 on level l >= 1): the update of eq. jacobian_system with the
+        Jacobian of Props. 2-3 (oracle.coarse.jacobian), then the clamp on Pi~ dp and Algorithm 1, as for Picard."""
+        lev = self.H.levels[l]
+        o = self.o
+        s, p = self.split(l, x)
+        dx = coarse.newton_update(lev, self.kind, self.a_lev[l], s, p, b)
+        self.stats.coarse_newton_steps += 1
+        if o["dp_clamp"] > 0:
+            mx = np.max(np.abs(coarse.pbar(lev, dx[lev.n_flux:])))
+            if mx > o["dp_clamp"]:
+                dx = dx * (o["dp_clamp"] / mx)
+        nrm = lambda y: float(np.linalg.norm(self.res(l, y, b)))
+        r_x = nrm(x) if r_x is None else r_x
+        xn, rn, _, _ = backtracking(nrm, x, dx, r_x, o["bt_nmax"], o["bt_theta"])
+        return xn, rn
+
+    def coarse_smooth(self, l, x, b, r_x=None):
+        """The coarse smoothing step: Picard (default); with coarse_smoother = "newton", Newton (FAS-Newton on every
+        coarse level, Sec. 3.3.2); with "picard_newton", Newton once the level-0 smoother has switched to Newton
+        steps in this cycle (the fine residual below newton_switch times the initial one, no failed Newton step)."""
+        cs = self.o.get("coarse_smoother", "picard")
+        if cs == "newton" or (cs == "picard_newton" and self.coarse_newton_now):
+            return self.newton_smooth(l, x, b, r_x)
+        return self.picard_smooth(l, x, b, r_x)
+
     def coarsest(self, l, x, b):
         o = self.o
         r = float(np.linalg.norm(self.res(l, x, b)))
@@ -191,7 +221,7 @@ class FAS:
         for _ in range(o["coarsest_steps"]):
             if r <= rel * r0 or r <= o["tol_abs"]:
                 break
-            x, r = self.picard_smooth(l, x, b, r)
+            x, r = self.coarse_smooth(l, x, b, r)
         return x
 
     def cycle_coarse(self, l, x, b):
@@ -199,7 +229,7 @@ class FAS:
         if l == len(self.H.levels) - 1:
             return self.coarsest(l, x, b)
         lev, tr, levc = self.H.levels[l], self.H.transfers[l], self.H.levels[l + 1]
-        x, _ = self.picard_smooth(l, x, b)
+        x, _ = self.coarse_smooth(l, x, b)
         s, p = self.split(l, x)
         r = self.res(l, x, b)
         rs, rp = r[:lev.n_flux], r[lev.n_flux:]
@@ -211,7 +241,7 @@ class FAS:
         dx = np.concatenate([tr.Psigma @ e[:levc.n_flux], tr.Pp @ e[levc.n_flux:]])
         nrm = lambda y: float(np.linalg.norm(self.res(l, y, b)))
         x, _, _, _ = backtracking(nrm, x, dx, nrm(x), self.o["bt_nmax"], self.o["bt_theta"])
-        x, _ = self.picard_smooth(l, x, b)
+        x, _ = self.coarse_smooth(l, x, b)
         return x
 
     def vcycle(self, p, r0):
@@ -222,6 +252,7 @@ class FAS:
         p, rn = self.smooth0(p, o["nu_pre"])
         if rn <= o["tol_rel"] * r0 or rn <= o["tol_abs"]:
             return p, rn, True
+        self.coarse_newton_now = (not self.newton_off and rn <= o.get("newton_switch", 1e-3) * r0)
         if len(H.levels) == 1:
             p, rn = self.smooth0(p, o["nu_post"], rn)
             return p, rn, False
@@ -273,7 +304,7 @@ class FAS:
             for _ in range(o["coarsest_steps"]):
                 if r <= rel * r_in or r <= o["tol_abs"]:
                     break
-                x, r = self.picard_smooth(l, x, b, r)
+                x, r = self.coarse_smooth(l, x, b, r)
             return x
 
         ys = [None] * L
