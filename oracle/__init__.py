@@ -10,9 +10,13 @@ Modules:
   newton     - brute-force damped Newton with a sparse direct solve: the definitional solution p*
   aggregation- deterministic greedy graph aggregation (stands in for METIS, Sec. 3.1 / App. A.1)
   hierarchy  - spectral pressure bases, coarse flux space, Q, D, static local M, Pi~ weights (App. A, B)
-  coarse     - level operators A^l(x) (eq. structure, Prop. 1) and the Picard step (eq. picardian_system)
+  coarse     - level operators A^l(x) (eq. structure, Prop. 1), the Picard step (eq. picardian_system) and the
+               coarse Newton Jacobian (Sec. 3.3.2, Props. 2-3, eq. jacobian_matrix)
   fas        - Algorithm 1 (backtracking), the level-0 smoothers (Picard, Picard-then-Newton, nonlinear Jacobi),
-               Algorithm 2 (FAS V-cycle) and the nonlinear cascadic start (Sec. 4.2)
+               the coarse smoothers (Picard, Newton), Algorithm 2 (FAS V-cycle) and the nonlinear cascadic start
+               (Sec. 4.2)
+  krylov     - fixed-length Jacobi-PCG, BiCGStab and the hybridized coarse solve of Sec. 3.4 (step-parity references)
+  precond    - the linear multigrid V-cycle that preconditions the level-0 Krylov solves (Sec. 3.4's AMG stand-in)
 The single-level Picard and Newton iterations of Sec. 2.2 have no module of their own: newton.solve is that
 iteration (Picard steps, then Newton steps, each solved exactly) run to its limit p*, the value the library's
 single-level baselines are compared with.
