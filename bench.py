@@ -342,7 +342,7 @@ def run_baselines(nlmg, pr, ctx):
                          "rel_residual": rep["res"] / rep["res0"] if rep["res0"] else None,
                          "lin_iters": rep["lin_iters"], "cap": cap}
         mctx.close()
-    except nlmg.NlmgError as e:
+    except Exception as e:   # a comparison section: reported, never fatal to the bench line
         out["picard_mg"] = {"status": "error", "what": str(e)[:160]}
     out["what"] = ("single-level solvers from p = 0 on the same workload and GPU (the FAS line is the bench value); "
                    "a Newton iteration from p = 0 is outside its region of fast convergence on this channelized case; "
